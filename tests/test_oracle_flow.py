@@ -1,0 +1,128 @@
+"""Physics pins of the oracle's streaming, boundary conditions, free-surface
+boundary condition and momentum exchange (Sections 2.1 and 2.2), each against
+a closed form of the continuum problem."""
+import numpy as np
+import pytest
+
+import oracle as O
+
+
+def test_open_channel_half_poiseuille():
+    """Gravity-driven film on a no-slip floor with a free surface on top:
+    u(z) = (g_x / nu) (H z - z^2 / 2), H the liquid volume per column."""
+    gx, om, nz = 1e-6, 1.0, 24
+    o = O.Oracle(O.OracleParams(nx=1, ny=1, nz=nz, periodic=(1, 1, 0), omega=om, g=(gx, 0, 0),
+                                liquid_height=16.0))
+    o.step(6000)
+    u = o.get(O.F_U)[0, :, 0, 0]
+    t = o.get(O.F_TYPE)[:, 0, 0]
+    H = o.get(O.F_PHI)[:, 0, 0].sum()
+    nu = (1 / om - 0.5) / 3
+    z = np.arange(nz) + 0.5
+    ua = gx / nu * (H * z - z * z / 2)
+    liq = t == O.LIQUID
+    err = np.sqrt(np.sum((u[liq] - ua[liq]) ** 2) / np.sum(ua[liq] ** 2))
+    assert err < 0.005
+
+
+def test_hydrostatic_column_under_flat_surface():
+    """At rest, rho(z) = rho_gas exp(3 |g_z| (H - z)) (pressure c_s^2 rho equals
+    the gas pressure at the surface), and spurious currents vanish."""
+    gz, nz = -1e-5, 40
+    o = O.Oracle(O.OracleParams(nx=2, ny=2, nz=nz, periodic=(1, 1, 0), omega=1.0, g=(0, 0, gz),
+                                liquid_height=30.0))
+    o.step(8000)
+    rho = o.get(O.F_RHO)[:, 0, 0]
+    t = o.get(O.F_TYPE)[:, 0, 0]
+    u = o.get(O.F_U)
+    liq = t == O.LIQUID
+    z = np.arange(nz) + 0.5
+    slope = np.polyfit(z[liq], np.log(rho[liq]), 1)[0]
+    assert abs(slope / (-3 * abs(gz)) - 1) < 1e-3
+    H = o.get(O.F_PHI)[:, 0, 0].sum()
+    pred = np.exp(3 * abs(gz) * (H - z))
+    assert np.abs(rho[liq] / pred[liq] - 1).max() < 1e-6
+    assert np.abs(u[:, liq]).max() < 1e-6
+
+
+def test_moving_boundary_couette_and_momentum_exchange():
+    """A fixed particle with a prescribed surface velocity U (a huge sphere,
+    locally a plane at z = 16) over a no-slip floor: linear Couette profile
+    u = U z / 16, and the momentum-exchange force on the particle equals the
+    wall shear stress times the area, F_x = -nu U / 16 * (n_x n_y)."""
+    U, om, nz, Hs, R = 0.01, 1.0, 24, 16.0, 200.0
+    o = O.Oracle(O.OracleParams(nx=4, ny=4, nz=nz, periodic=(1, 1, 0), omega=om, liquid_height=1e9))
+    o.add_spheres([[2.0, 2.0, Hs + R]], [R], [1])
+    o.set(O.P_U, np.array([[U, 0.0, 0.0]]))
+    o.step(3000)
+    u = o.get(O.F_U)[0, :, 0, 0]
+    t = o.get(O.F_TYPE)[:, 0, 0]
+    liq = t == O.LIQUID
+    assert liq.sum() == 16 and (t[16:] == O.SOLID).all()
+    z = np.arange(nz) + 0.5
+    assert np.abs(u[liq] - U * z[liq] / Hs).max() < 1e-6 * U
+    F = o.get(O.P_F)[0]
+    nu = (1 / om - 0.5) / 3
+    assert abs(F[0] / (-nu * U / Hs * 16) - 1) < 1e-6
+    assert abs(F[1]) < 1e-12
+
+
+def test_hasimoto_drag_of_periodic_sphere_array():
+    """Stokes drag on a simple-cubic array of fixed spheres (Hasimoto 1959):
+    F = 6 pi mu r U K(c), 1/K = 1 - 1.7601 c^(1/3) + c - 1.5593 c^2, with U the
+    superficial velocity. The run starts from the expected terminal flow so
+    that the drag is quasi-steady after a few hundred steps; r = 3 cells
+    carries the usual few-per-cent voxelisation offset."""
+    L, r, om, gx = 24, 3.0, 1.0, 1e-6
+    o = O.Oracle(O.OracleParams(nx=L, ny=L, nz=L, periodic=(1, 1, 1), omega=om, g=(gx, 0, 0),
+                                liquid_height=1e9))
+    o.add_spheres([[L / 2, L / 2, L / 2]], [r], [1])
+    nu = (1 / om - 0.5) / 3
+    c = (4 / 3) * np.pi * r ** 3 / L ** 3
+    K = 1 / (1 - 1.7601 * c ** (1 / 3) + c - 1.5593 * c ** 2)
+    fl = o.get(O.F_TYPE) == O.LIQUID
+    U0 = gx * fl.sum() / (6 * np.pi * nu * r * K) * L ** 3 / fl.sum()
+    f = np.broadcast_to(O.feq(1.0, [U0, 0, 0])[:, None, None, None], (27,) + o.shape).copy()
+    o.set(O.F_PDF, f)
+    o.step(400)
+    F = o.get(O.P_F)[0, 0]
+    u = o.get(O.F_U)[0]
+    rho = o.get(O.F_RHO)
+    Ubar = (rho[fl] * u[fl]).sum() / L ** 3
+    ratio = F / (6 * np.pi * nu * r * Ubar) / K
+    assert abs(ratio - 1) < 0.1, ratio
+
+
+def _wave_period_ratio(lam):
+    s = lam / 64
+    h0, a, gz = 16 * s, 2.0 * s, -1e-4 / s
+    nz = int(26 * s)
+    o = O.Oracle(O.OracleParams(nx=lam, ny=1, nz=nz, periodic=(1, 1, 0), omega=1.97, g=(0, 0, gz),
+                                liquid_height=h0))
+    x = np.arange(lam) + 0.5
+    k = 2 * np.pi / lam
+    o.init_surface((h0 + a * np.cos(k * x))[None, :])
+    every = max(1, int(10 * s))
+    ts, eta = [], []
+    for st in range(0, int(3000 * s), every):
+        o.step(every)
+        col = o.get(O.F_PHI)[:, 0, :].sum(axis=0)
+        ts.append(st + every)
+        eta.append(2 / lam * np.sum((col - col.mean()) * np.cos(k * x)))
+    eta, ts = np.array(eta), np.array(ts)
+    zc = [ts[i] + (ts[i + 1] - ts[i]) * eta[i] / (eta[i] - eta[i + 1])
+          for i in range(len(eta) - 1) if eta[i] * eta[i + 1] < 0]
+    assert len(zc) >= 3 and o.violations == 0
+    T = 2 * np.mean(np.diff(zc[:3]))
+    return T / (2 * np.pi / np.sqrt(abs(gz) * k * np.tanh(k * h0)))
+
+
+def test_standing_gravity_wave_dispersion():
+    """Standing gravity wave, omega^2 = g k tanh(k h): the period approaches
+    the linear dispersion relation as the wave is resolved by more cells (the
+    free-surface boundary condition places the surface at interface-cell
+    centres, so the error is first order in the cell size)."""
+    r32 = _wave_period_ratio(32)
+    r64 = _wave_period_ratio(64)
+    assert abs(r64 - 1) < 0.1
+    assert abs(r64 - 1) < 0.5 * abs(r32 - 1)
