@@ -1,0 +1,229 @@
+/*
+ * fslbm.h - C ABI of the GB300 (sm_103a) implementation of one time step of
+ * the coupled free-surface lattice Boltzmann / discrete-element method of
+ * Schwarzmeier et al., "Particle-resolved simulation of antidunes in
+ * free-surface flows" (Section 2).
+ *
+ * One time step (Section 2; step order as documented with fslbm_step):
+ *   - D3Q27 cumulant collision, all rates 1 except the shear rate omega,
+ *     nu = (1/omega - 1/2)/3, with gravity forcing (Section 2.1);
+ *   - streaming with halfway bounce-back at no-slip walls (Section 2.1);
+ *   - free-surface (volume-of-fluid) update: gas-pressure boundary condition
+ *     at interface cells, interface mass exchange, cell conversion and excess
+ *     mass redistribution (Section 2.1);
+ *   - geometrically resolved spheres: moving bounce-back and momentum-exchange
+ *     force/torque, explicit particle-to-grid mapping (Section 2.2);
+ *   - DEM contact (restitution, collision time, Poisson ratio, friction) and
+ *     Newton-Euler integration (Section 2.2).
+ *
+ * Conventions
+ *   - Lattice units: cell size 1, time step 1, reference density 1
+ *     (Section 2.1). Cell (x,y,z) has its centre at (x+1/2, y+1/2, z+1/2);
+ *     linear index x + nx*(y + ny*z) (x fastest).
+ *   - Directions q = (cx+1) + 3(cy+1) + 9(cz+1), c in {-1,0,1}^3.
+ *   - Cell types: 0 gas, 1 liquid, 2 interface, 3 solid (particle).
+ *   - Ownership: the library owns every device buffer it allocates; callers
+ *     own what they pass in. Calls are ordered on the CUDA stream given to
+ *     fslbm_create. fslbm_step only enqueues work; fslbm_get_fields,
+ *     fslbm_set_fields, fslbm_reduce and fslbm_sync synchronise the stream.
+ *   - Errors: every call returns 0 or a negative FSLBM_E* code; no exception
+ *     or abort crosses the ABI. Errors detected on the device (capacity
+ *     overflow, non-finite values, an exhausted wait) are recorded in a sticky
+ *     device error word that the next synchronising call returns; once set it
+ *     stays set until fslbm_destroy.
+ *   - Thread safety: one handle must not be used from two threads at once.
+ */
+#ifndef FSLBM_H
+#define FSLBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FSLBM_ABI_VERSION 1
+
+#define FSLBM_OK 0
+#define FSLBM_EINVAL (-1)      /* invalid argument or parameter */
+#define FSLBM_ENOMEM (-2)      /* device allocation failed */
+#define FSLBM_ECAPACITY (-3)   /* a fixed-capacity device list overflowed */
+#define FSLBM_ENAN (-4)        /* non-finite value detected */
+#define FSLBM_EDEVICE (-5)     /* CUDA runtime error */
+#define FSLBM_ESTATE (-6)      /* call not valid in the current state */
+#define FSLBM_EINVARIANT (-7)  /* a liquid cell touched a gas cell */
+
+/* boundary flags: a set bit makes the axis periodic, a clear bit puts no-slip
+ * walls (halfway bounce-back, Section 2.1) on both of its faces */
+#define FSLBM_PERIODIC_X 1u
+#define FSLBM_PERIODIC_Y 2u
+#define FSLBM_PERIODIC_Z 4u
+
+/* PDF storage (all arithmetic is FP32; the stored value is f_i - w_i) */
+#define FSLBM_STORE_FP32 0
+#define FSLBM_STORE_FP16 1
+#define FSLBM_STORE_BF16 2
+
+#define FSLBM_GAS 0
+#define FSLBM_LIQUID 1
+#define FSLBM_INTERFACE 2
+#define FSLBM_SOLID 3
+
+typedef struct fslbm fslbm;
+
+/* Parameters of the problem statement (Sections 2.1, 2.2, 3.1), lattice
+ * units. Fill with fslbm_default_params, then override. */
+typedef struct {
+    uint32_t struct_size;        /* sizeof(fslbm_params), ABI check */
+    int32_t nx, ny, nz;          /* lattice size, each >= 1 */
+    uint32_t bc_flags;           /* FSLBM_PERIODIC_* bits */
+    double omega;                /* shear relaxation rate, 0 < omega < 2 */
+    double g[3];                 /* body acceleration (gravity incl. slope forcing) */
+    double rho_gas;              /* gas pressure p_g = rho_gas / 3 */
+    double sigma;                /* surface tension; only 0 is supported */
+    double liquid_height;        /* initial flat free surface height (cells) */
+    int32_t init_profile;        /* 0: fluid at rest */
+    int32_t storage;             /* FSLBM_STORE_* */
+    int32_t normal_model;        /* 0: finite-difference (Parker-Youngs) normal */
+    int32_t reconstruct_normal;  /* 1: also rebuild PDFs with n.c_i < -eps_normal */
+    double eps_conv;             /* conversion hysteresis on the fill level */
+    double eps_normal;           /* margin of the normal-based reconstruction */
+    double rho_p;                /* particle density (liquid reference 1) */
+    double restitution;          /* DEM coefficient of restitution, 0 < e <= 1 */
+    double friction;             /* Coulomb friction coefficient */
+    double poisson;              /* Poisson ratio of the particle material */
+    double collision_time;       /* DEM collision time T_c (time steps) */
+    int32_t dem_substeps;        /* DEM sub-steps per LBM step, >= 1 */
+    int32_t reserved0;
+    int64_t capacity_particles;  /* maximum number of spheres (0: 65536) */
+    int64_t capacity_interface;  /* maximum interface cells (0: ncells/4 + 4096) */
+} fslbm_params;
+
+/* Fills *p with defaults: periodic x, walls in y and z, omega = 1/0.51,
+ * g = 0, rho_gas = 1, eps_conv = eps_normal = 1e-2, reconstruct_normal = 1,
+ * rho_p = 2.55, e = 0.88, mu = 0.5, nu_p = 0.22, T_c = 24, 10 sub-steps. */
+void fslbm_default_params(fslbm_params* p);
+
+/* Creates a simulation on the current CUDA device. `cuda_stream` is a
+ * cudaStream_t (NULL: the legacy default stream); every later call is
+ * ordered on it. The fluid starts flat at rest (Section 3.1): cells below
+ * liquid_height liquid, the layer holding or touching the surface interface
+ * with its fill level, gas above; hydrostatic density rho_gas
+ * exp(3 |g_z| (H - z)). Returns FSLBM_EINVAL for bad parameters (including
+ * sigma != 0 and normal_model != 0), FSLBM_ENOMEM if the device buffers do
+ * not fit. On success *out owns every device buffer of the run. */
+int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out);
+
+/* Adds n spheres (Section 2.2): centres xyz[3n], radii radius[n] (> 0 and
+ * < half of every periodic extent), fixed[n] (1: never integrated, velocity
+ * kept as set; NULL: all mobile). Pointers are host memory unless on_device
+ * is 1. Cells whose centre lies inside a sphere become solid; their fluid is
+ * removed. Must be called before the first fslbm_step; may be called once. */
+int fslbm_add_spheres(fslbm* s, int64_t n, const double* xyz, const double* radius,
+                      const uint8_t* fixed, int on_device);
+
+/* Re-initialises the liquid from a free-surface height per column,
+ * height_xy[y*nx + x] (host or device per on_device), with the rule of
+ * fslbm_create applied column by column; solid cells are kept. Valid before
+ * the first fslbm_step only. */
+int fslbm_init_surface(fslbm* s, const double* height_xy, int on_device);
+
+/* Advances n_steps time steps. Each step (Section 2):
+ *   1 stream with boundary conditions, momentum exchange, interface mass
+ *     exchange, cumulant collision;
+ *   2 interface normals; conversion candidates (fill level beyond
+ *     1 + eps_conv or below -eps_conv, or no gas / no liquid neighbour);
+ *     filling wins over emptying; gas neighbours of filled cells and liquid
+ *     neighbours of emptied cells become interface cells; excess mass is
+ *     spread over interface neighbours along the normal;
+ *   3 hydrodynamic force averaged over two steps, DEM sub-steps;
+ *   4 particle re-mapping (covered cells give their mass to a pool,
+ *     uncovered cells are refilled from it);
+ *   5 the pool is spread over all interface cells; normals for the next step.
+ * Asynchronous on the stream; returns the sticky error word as of the call
+ * (a device error raised by these steps is returned by a later call). */
+int fslbm_step(fslbm* s, int64_t n_steps);
+
+/* Field selection bits for fslbm_get_fields / fslbm_set_fields. dst[k] /
+ * src[k] is the buffer of the k-th selected field in increasing bit order.
+ * Layouts (N = nx*ny*nz, np = number of spheres):
+ *   PDF     double [27][N]   post-collision PDFs f*_q, 0 outside liquid/interface
+ *   TYPE    uint8  [N]       cell type
+ *   MASS    double [N]       liquid: rho, interface: m, else 0
+ *   PHI     double [N]       fill level (liquid 1, interface m/rho, else 0)
+ *   RHO     double [N]       density of liquid/interface cells, else 0
+ *   U       double [3][N]    velocity of the last collision (liquid/interface)
+ *   NORMAL  double [3][N]    interface normal (toward the gas), else 0
+ *   OWNER   int32  [N]       owning sphere of solid cells, else -1
+ *   P_X, P_U, P_OMEGA, P_F, P_T  double [np][3]  centre, velocity, angular
+ *            velocity, hydrodynamic force and torque of the last step
+ *   P_R     double [np]      radius                                       */
+#define FSLBM_FIELD_PDF (1u << 0)
+#define FSLBM_FIELD_TYPE (1u << 1)
+#define FSLBM_FIELD_MASS (1u << 2)
+#define FSLBM_FIELD_PHI (1u << 3)
+#define FSLBM_FIELD_RHO (1u << 4)
+#define FSLBM_FIELD_U (1u << 5)
+#define FSLBM_FIELD_NORMAL (1u << 6)
+#define FSLBM_FIELD_OWNER (1u << 7)
+#define FSLBM_FIELD_P_X (1u << 16)
+#define FSLBM_FIELD_P_U (1u << 17)
+#define FSLBM_FIELD_P_OMEGA (1u << 18)
+#define FSLBM_FIELD_P_F (1u << 19)
+#define FSLBM_FIELD_P_T (1u << 20)
+#define FSLBM_FIELD_P_R (1u << 21)
+
+/* Copies the selected fields into dst (device pointers if dst_on_device,
+ * else host). Synchronises the stream; returns the sticky error word. */
+int fslbm_get_fields(fslbm* s, uint32_t field_mask, void* const* dst, int dst_on_device);
+
+/* Overwrites the selected fields from src (host unless src_on_device).
+ * Supported: PDF (densities, velocities and liquid masses follow from it),
+ * MASS (interface masses; fill levels and normals are recomputed), P_U,
+ * P_OMEGA. Synchronises the stream. */
+int fslbm_set_fields(fslbm* s, uint32_t field_mask, const void* const* src, int src_on_device);
+
+/* FP64 diagnostics (Section 3.2): out[0] liquid mass (sum over liquid rho +
+ * sum over interface m + mass pool), out[1..3] fluid momentum, out[4]
+ * fill-weighted bulk velocity sum phi rho u_x / sum phi rho, out[5] number of
+ * interface cells, out[6] bedload rate of Eq. (1) sum u_x,p V_p / (L_x L_y),
+ * out[7] mass pool. Synchronises the stream. */
+int fslbm_reduce(fslbm* s, double out[8]);
+
+/* Waits for the stream; returns the sticky error word. */
+int fslbm_sync(fslbm* s);
+
+/* Number of completed steps and of spheres. */
+int64_t fslbm_steps_done(const fslbm* s);
+int64_t fslbm_num_spheres(const fslbm* s);
+
+/* Number of reads where a liquid cell found a gas neighbour (the liquid/gas
+ * separation the conversion rules maintain was broken; the PDF was rebuilt
+ * from the gas pressure as at an interface cell). Synchronises the stream. */
+int64_t fslbm_invariant_violations(fslbm* s);
+
+/* Measurement hooks for the benchmark. fslbm_timing(s, 1) clears and starts
+ * recording a pair of CUDA events around every stream-collide sweep (the
+ * dominant kernel pair: bulk-cell and boundary-cell kernels) that fslbm_step
+ * enqueues, and counting the kernel launches it enqueues; fslbm_timing(s, 0)
+ * stops recording. fslbm_timing_read waits for the stream and returns the
+ * summed sweep time in milliseconds, the number of sweeps and the number of
+ * kernel launches since the last start. */
+int fslbm_timing(fslbm* s, int on);
+int fslbm_timing_read(fslbm* s, double* sweep_ms, int64_t* sweeps, int64_t* kernel_launches);
+
+/* Number of cells of each type (gas, liquid, interface, solid) in
+ * counts[0..3]. Synchronises the stream. */
+int fslbm_cell_counts(fslbm* s, int64_t counts[4]);
+
+/* Releases every device buffer of the run. NULL is ignored. */
+void fslbm_destroy(fslbm* s);
+
+/* Static description of an error code. */
+const char* fslbm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FSLBM_H */

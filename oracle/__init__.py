@@ -88,6 +88,7 @@ def lib():
         L.orc_collide.argtypes = [dp, dp, ctypes.c_double, dp]
         L.orc_feq.argtypes = [ctypes.c_double, dp, dp]
         L.orc_normal_stencil.argtypes = [dp, dp]
+        L.orc_threads.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -216,6 +217,10 @@ class Oracle:
         out = np.zeros(8, np.float64)
         lib().orc_reduce(self._h, _dp(out))
         return out
+
+
+def threads() -> int:
+    return int(lib().orc_threads())
 
 
 def collide(f: np.ndarray, g, omega: float) -> np.ndarray:

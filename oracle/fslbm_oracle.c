@@ -683,6 +683,7 @@ static void dem_substep(orc* o, const double* Fhyd, const double* Thyd, double d
             for (int a = 0; a < 3; ++a) vrel[a] = o->U[3 * i + a] - o->U[3 * j + a] + wn[a];
             double meff = o->M[i] * o->M[j] / (o->M[i] + o->M[j]);
             orc_hist* h = hist_find(o, i, j, 1);
+            if (!h) continue;                  /* history table full */
             double Fc[3], Ft[3];
             contact_force(o, meff, n, delta, vrel, h->xi, dts, Fc, Ft);
             double ri_n[3] = {o->R[i] * n[0], o->R[i] * n[1], o->R[i] * n[2]};
@@ -721,6 +722,7 @@ static void dem_substep(orc* o, const double* Fhyd, const double* Thyd, double d
                 double vrel[3];
                 for (int b = 0; b < 3; ++b) vrel[b] = o->U[3 * i + b] + wn[b];
                 orc_hist* h = hist_find(o, i, wid, 1);
+                if (!h) continue;
                 double Fc[3], Ft[3];
                 contact_force(o, o->M[i], n, delta, vrel, h->xi, dts, Fc, Ft);
                 double ri_n[3] = {o->R[i] * n[0], o->R[i] * n[1], o->R[i] * n[2]};
@@ -1174,6 +1176,19 @@ int orc_set(orc* o, int which, const void* src)
     case P_X: memcpy(o->X, src, sizeof(double) * 3 * o->np); return 0;
     default: return -1;
     }
+}
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+/* number of threads the parallel loops use */
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 long orc_ncells(const orc* o) { return o->n; }

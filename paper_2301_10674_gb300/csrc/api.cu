@@ -1,0 +1,566 @@
+// C ABI of the free-surface LBM / DEM step (declared in include/fslbm.h):
+// parameter checks, device buffers, and the per-step kernel sequence.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fslbm_dev.cuh"
+
+namespace fsl {
+void launch_export_owner(const Dev& s, int* out, cudaStream_t st);
+}
+
+using namespace fsl;
+
+struct fslbm {
+    Dev d;
+    fslbm_params p;
+    cudaStream_t st;
+    int64_t steps;
+    int last_parity;   // layout of the stored post-collision PDFs (1 initially)
+    int have_prev;
+    bool spheres_added;
+    std::vector<void*> allocs;
+    double* stage;     // n doubles of staging for export/import
+    double* red;       // 8 doubles for reductions
+    int host_err;
+    size_t elem;
+    // measurement hooks
+    bool timing;
+    std::vector<cudaEvent_t> ev;   // start/end pairs of stream-collide sweeps
+    size_t ev_used;
+    int64_t launches;
+    unsigned long long* counts4;
+};
+
+namespace {
+
+template <class T>
+T* dalloc(fslbm* s, size_t count, bool& ok) {
+    if (!ok) return nullptr;
+    void* ptr = nullptr;
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = sizeof(T);
+    if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+        ok = false;
+        cudaGetLastError();
+        return nullptr;
+    }
+    s->allocs.push_back(ptr);
+    return static_cast<T*>(ptr);
+}
+
+void* dalloc_bytes(fslbm* s, size_t bytes, bool& ok) { return dalloc<uint8_t>(s, bytes, ok); }
+
+int map_device_error(int bits) {
+    if (bits & ERR_NAN) return FSLBM_ENAN;
+    if (bits & (ERR_CAPACITY | ERR_HISTORY | ERR_DISPLACEMENT)) return FSLBM_ECAPACITY;
+    if (bits & ERR_INVARIANT) return FSLBM_EINVARIANT;
+    return FSLBM_OK;
+}
+
+// waits for the stream, folds CUDA and device errors into the sticky code
+int sync_check(fslbm* s) {
+    cudaError_t e = cudaStreamSynchronize(s->st);
+    if (e != cudaSuccess) {
+        if (!s->host_err) s->host_err = FSLBM_EDEVICE;
+        return s->host_err;
+    }
+    int bits = 0;
+    if (cudaMemcpy(&bits, s->d.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        if (!s->host_err) s->host_err = FSLBM_EDEVICE;
+        return s->host_err;
+    }
+    if (!s->host_err) s->host_err = map_device_error(bits);
+    return s->host_err;
+}
+
+int launch_check(fslbm* s) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess && !s->host_err) s->host_err = FSLBM_EDEVICE;
+    return s->host_err;
+}
+
+cudaMemcpyKind kind_to(int on_device) { return on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
+cudaMemcpyKind kind_from(int on_device) { return on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
+
+}  // namespace
+
+extern "C" {
+
+void fslbm_default_params(fslbm_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->struct_size = sizeof(fslbm_params);
+    p->nx = p->ny = p->nz = 1;
+    p->bc_flags = FSLBM_PERIODIC_X;
+    p->omega = 1.0 / 0.51;
+    p->rho_gas = 1.0;
+    p->liquid_height = 0.0;
+    p->storage = FSLBM_STORE_FP32;
+    p->normal_model = 0;
+    p->reconstruct_normal = 1;
+    p->eps_conv = 1e-2;
+    p->eps_normal = 1e-2;
+    p->rho_p = 2.55;
+    p->restitution = 0.88;
+    p->friction = 0.5;
+    p->poisson = 0.22;
+    p->collision_time = 24.0;
+    p->dem_substeps = 10;
+}
+
+const char* fslbm_strerror(int code) {
+    switch (code) {
+    case FSLBM_OK: return "ok";
+    case FSLBM_EINVAL: return "invalid argument";
+    case FSLBM_ENOMEM: return "device allocation failed";
+    case FSLBM_ECAPACITY: return "device list capacity exceeded";
+    case FSLBM_ENAN: return "non-finite value in the state";
+    case FSLBM_EDEVICE: return "CUDA runtime error";
+    case FSLBM_ESTATE: return "call not valid in the current state";
+    case FSLBM_EINVARIANT: return "liquid cell next to a gas cell";
+    default: return "unknown error";
+    }
+}
+
+int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
+    if (!p || !out) return FSLBM_EINVAL;
+    *out = nullptr;
+    if (p->struct_size != sizeof(fslbm_params)) return FSLBM_EINVAL;
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return FSLBM_EINVAL;
+    const long long n = (long long)p->nx * p->ny * p->nz;
+    if (n >= (1LL << 31)) return FSLBM_EINVAL;
+    if (!(p->omega > 0.0 && p->omega < 2.0)) return FSLBM_EINVAL;
+    if (p->sigma != 0.0 || p->normal_model != 0 || p->init_profile != 0) return FSLBM_EINVAL;
+    if (p->storage < 0 || p->storage > 2) return FSLBM_EINVAL;
+    if (p->dem_substeps < 1 || !(p->restitution > 0.0 && p->restitution <= 1.0)) return FSLBM_EINVAL;
+    if (!(p->collision_time > 0.0) || !(p->rho_p > 0.0) || !(p->rho_gas > 0.0)) return FSLBM_EINVAL;
+    if (!(p->poisson >= 0.0 && p->poisson < 1.0) || !(p->friction >= 0.0)) return FSLBM_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(p->g[a])) return FSLBM_EINVAL;
+    if (!std::isfinite(p->liquid_height) || p->eps_conv < 0.0 || p->eps_normal < 0.0) return FSLBM_EINVAL;
+
+    fslbm* s = new (std::nothrow) fslbm();
+    if (!s) return FSLBM_ENOMEM;
+    s->p = *p;
+    s->st = static_cast<cudaStream_t>(cuda_stream);
+    s->steps = 0;
+    s->last_parity = 1;
+    s->have_prev = 0;
+    s->spheres_added = false;
+    s->host_err = 0;
+    s->timing = false;
+    s->ev_used = 0;
+    s->launches = 0;
+    s->counts4 = nullptr;
+    Dev& d = s->d;
+    std::memset(&d, 0, sizeof(d));
+    d.nx = p->nx; d.ny = p->ny; d.nz = p->nz;
+    d.per_x = (p->bc_flags & FSLBM_PERIODIC_X) ? 1 : 0;
+    d.per_y = (p->bc_flags & FSLBM_PERIODIC_Y) ? 1 : 0;
+    d.per_z = (p->bc_flags & FSLBM_PERIODIC_Z) ? 1 : 0;
+    d.n = n;
+    d.omega = (float)p->omega;
+    d.gx = (float)p->g[0]; d.gy = (float)p->g[1]; d.gz = (float)p->g[2];
+    d.gxd = p->g[0]; d.gyd = p->g[1]; d.gzd = p->g[2];
+    d.rho_gas = (float)p->rho_gas;
+    d.eps_conv = (float)p->eps_conv;
+    d.eps_normal = (float)p->eps_normal;
+    d.recon_normal = p->reconstruct_normal;
+    d.storage = p->storage;
+    d.rho_p = p->rho_p;
+    d.restitution = p->restitution;
+    d.friction = p->friction;
+    d.poisson = p->poisson;
+    d.collision_time = p->collision_time;
+    const double le = std::log(p->restitution);
+    const double pi = 3.14159265358979323846;
+    d.kn_coef = (pi * pi + le * le) / (p->collision_time * p->collision_time);
+    d.dn_coef = -2.0 * le / p->collision_time;
+    d.kt_ratio = 2.0 * (1.0 - p->poisson) / (2.0 - p->poisson);
+    d.dem_substeps = p->dem_substeps;
+    s->elem = p->storage == FSLBM_STORE_FP32 ? 4 : 2;
+
+    bool ok = true;
+    d.f = dalloc_bytes(s, (size_t)27 * n * s->elem, ok);
+    d.fs = dalloc_bytes(s, (size_t)27 * n * s->elem, ok);
+    d.flags = dalloc<uint8_t>(s, n + 4, ok);   // word-granular atomics on the last bytes
+    d.mass = dalloc<float>(s, n, ok);
+    d.phi = dalloc<float>(s, n, ok);
+    d.ru = dalloc<float4>(s, n, ok);
+    d.nrm = dalloc<float4>(s, n, ok);
+    d.nrm1 = dalloc<float4>(s, n, ok);
+    d.owner = dalloc<int>(s, n, ok);
+    d.conv = dalloc<uint8_t>(s, n, ok);
+    d.exscale = dalloc<float>(s, n, ok);
+    long long cap = p->capacity_interface > 0 ? p->capacity_interface : n / 4 + 4096;
+    if (cap > n) cap = n;
+    d.wl_cap = (int)cap;
+    d.nl_cap = (int)cap;
+    d.wl = dalloc<int>(s, cap, ok);
+    d.nl = dalloc<int>(s, cap, ok);
+    long long tcap = n / 8 + 4096;
+    if (tcap > n) tcap = n;
+    d.tl_cap = (int)tcap;
+    d.tl = dalloc<int>(s, tcap, ok);
+    d.tl_info = dalloc<int>(s, 2 * tcap, ok);
+    int* counts = dalloc<int>(s, 8, ok);
+    if (ok) {
+        d.wl_count = counts;
+        d.nl_count = counts + 1;
+        d.tl_count = counts + 2;
+        d.zmax_cell = counts + 3;
+        d.err = counts + 4;
+    }
+    double* dd = dalloc<double>(s, 4, ok);
+    if (ok) {
+        d.pool = dd;
+        d.pool_share = dd + 1;
+    }
+    d.viol = dalloc<unsigned long long>(s, 1, ok);
+    d.fixkey = dalloc<unsigned long long>(s, n, ok);
+    d.fixowner = dalloc<int>(s, n, ok);
+    long long pc = p->capacity_particles > 0 ? p->capacity_particles : 65536;
+    d.np_cap = (int)pc;
+    d.X = dalloc<double>(s, 3 * pc, ok); d.U = dalloc<double>(s, 3 * pc, ok); d.W = dalloc<double>(s, 3 * pc, ok);
+    d.X2 = dalloc<double>(s, 3 * pc, ok); d.U2 = dalloc<double>(s, 3 * pc, ok); d.W2 = dalloc<double>(s, 3 * pc, ok);
+    d.R = dalloc<double>(s, pc, ok); d.M = dalloc<double>(s, pc, ok); d.I = dalloc<double>(s, pc, ok);
+    d.fixed = dalloc<uint8_t>(s, pc, ok);
+    d.Fh = dalloc<double>(s, 3 * pc, ok); d.Th = dalloc<double>(s, 3 * pc, ok);
+    d.Fp = dalloc<double>(s, 3 * pc, ok); d.Tp = dalloc<double>(s, 3 * pc, ok);
+    d.Fa = dalloc<double>(s, 3 * pc, ok); d.Ta = dalloc<double>(s, 3 * pc, ok);
+    d.hist_partner = dalloc<int>(s, pc * HIST_SLOTS, ok);
+    d.hist_xi = dalloc<double>(s, pc * HIST_SLOTS * 3, ok);
+    d.g_of = dalloc<int>(s, pc, ok);
+    d.g_list = dalloc<int>(s, pc, ok);
+    s->stage = dalloc<double>(s, n > 8 ? n : 8, ok);
+    s->red = dalloc<double>(s, 8, ok);
+    if (!ok) {
+        fslbm_destroy(s);
+        return FSLBM_ENOMEM;
+    }
+    cudaStream_t st = s->st;
+    cudaMemsetAsync(d.f, 0, (size_t)27 * n * s->elem, st);
+    cudaMemsetAsync(d.fs, 0, (size_t)27 * n * s->elem, st);
+    cudaMemsetAsync(d.conv, 0, n, st);
+    cudaMemsetAsync(d.exscale, 0, n * sizeof(float), st);
+    cudaMemsetAsync(d.nrm1, 0, n * sizeof(float4), st);
+    cudaMemsetAsync(counts, 0, 8 * sizeof(int), st);
+    cudaMemsetAsync(dd, 0, 4 * sizeof(double), st);
+    cudaMemsetAsync(d.viol, 0, sizeof(unsigned long long), st);
+    cudaMemsetAsync(d.fixowner, 0xff, n * sizeof(int), st);
+    launch_init_flat(d, p->liquid_height, st);
+    launch_classify(d, st);
+    launch_normals(d, d.nrm, st);
+    if (launch_check(s) || sync_check(s)) {
+        int e = s->host_err;
+        fslbm_destroy(s);
+        return e ? e : FSLBM_EDEVICE;
+    }
+    *out = s;
+    return FSLBM_OK;
+}
+
+int fslbm_add_spheres(fslbm* s, int64_t n, const double* xyz, const double* radius, const uint8_t* fixed,
+                      int on_device) {
+    if (!s || n < 0 || (n > 0 && (!xyz || !radius))) return FSLBM_EINVAL;
+    if (s->spheres_added || s->steps > 0) return FSLBM_ESTATE;
+    if (n > s->d.np_cap) return FSLBM_ECAPACITY;
+    Dev& d = s->d;
+    std::vector<double> X(3 * n), R(n);
+    std::vector<uint8_t> F(n, 0);
+    if (n > 0) {
+        cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+        if (cudaMemcpy(X.data(), xyz, sizeof(double) * 3 * n, k) != cudaSuccess ||
+            cudaMemcpy(R.data(), radius, sizeof(double) * n, k) != cudaSuccess ||
+            (fixed && cudaMemcpy(F.data(), fixed, n, k) != cudaSuccess)) {
+            cudaGetLastError();
+            return FSLBM_EINVAL;
+        }
+    }
+    const int L[3] = {d.nx, d.ny, d.nz};
+    const int per[3] = {d.per_x, d.per_y, d.per_z};
+    double rmax = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!(R[i] > 0.0) || !std::isfinite(R[i])) return FSLBM_EINVAL;
+        for (int a = 0; a < 3; ++a) {
+            double v = X[3 * i + a];
+            if (!std::isfinite(v)) return FSLBM_EINVAL;
+            if (per[a]) {
+                if (R[i] >= 0.5 * L[a]) return FSLBM_EINVAL;
+                v -= L[a] * std::floor(v / L[a]);
+                X[3 * i + a] = v;
+            }
+        }
+        if (R[i] > rmax) rmax = R[i];
+    }
+    // particle grid: cells at least one diameter plus a skin wide
+    const double h = 2.0 * rmax + 1.0;
+    int gn[3];
+    double gh[3];
+    for (int a = 0; a < 3; ++a) {
+        gn[a] = (int)std::floor(L[a] / h);
+        if (gn[a] < 1) gn[a] = 1;
+        gh[a] = (double)L[a] / gn[a];
+    }
+    d.gnx = gn[0]; d.gny = gn[1]; d.gnz = gn[2];
+    d.ghx = gh[0]; d.ghy = gh[1]; d.ghz = gh[2];
+    d.r_max = rmax;
+    const long long G = (long long)gn[0] * gn[1] * gn[2];
+    bool ok = true;
+    d.g_count = dalloc<int>(s, G, ok);
+    d.g_start = dalloc<int>(s, G, ok);
+    d.g_cursor = dalloc<int>(s, G, ok);
+    if (!ok) return FSLBM_ENOMEM;
+    d.np = (int)n;
+    cudaStream_t st = s->st;
+    if (n > 0) {
+        cudaMemcpyAsync(d.X, X.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(d.R, R.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(d.fixed, F.data(), n, cudaMemcpyHostToDevice, st);
+        launch_particles_add(d, 0, (int)n, st);
+        launch_classify(d, st);
+        launch_normals(d, d.nrm, st);
+    }
+    s->spheres_added = true;
+    launch_check(s);
+    return sync_check(s);
+}
+
+int fslbm_init_surface(fslbm* s, const double* height_xy, int on_device) {
+    if (!s || !height_xy) return FSLBM_EINVAL;
+    if (s->steps > 0) return FSLBM_ESTATE;
+    Dev& d = s->d;
+    const size_t cnt = (size_t)d.nx * d.ny;
+    cudaMemcpyAsync(s->stage, height_xy, cnt * sizeof(double), kind_from(on_device), s->st);
+    launch_init_surface(d, s->stage, s->st);
+    launch_classify(d, s->st);
+    launch_normals(d, d.nrm, s->st);
+    launch_check(s);
+    return sync_check(s);
+}
+
+int fslbm_step(fslbm* s, int64_t n_steps) {
+    if (!s || n_steps < 0) return FSLBM_EINVAL;
+    if (s->host_err) return s->host_err;
+    Dev& d = s->d;
+    cudaStream_t st = s->st;
+    for (int64_t k = 0; k < n_steps; ++k) {
+        const int parity = (int)(s->steps & 1);
+        if (d.np > 0) {
+            cudaMemsetAsync(d.Fh, 0, sizeof(double) * 3 * d.np, st);
+            cudaMemsetAsync(d.Th, 0, sizeof(double) * 3 * d.np, st);
+        }
+        int nl = 0;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (s->timing) {
+            if (s->ev_used + 2 > s->ev.size()) {
+                for (int j = 0; j < 64; ++j) {
+                    cudaEvent_t e;
+                    cudaEventCreate(&e);
+                    s->ev.push_back(e);
+                }
+            }
+            e0 = s->ev[s->ev_used++];
+            e1 = s->ev[s->ev_used++];
+            cudaEventRecord(e0, st);
+        }
+        nl += launch_stream_collide(d, parity, st);
+        if (s->timing) cudaEventRecord(e1, st);
+        nl += launch_conversion(d, parity, st);
+        if (d.np > 0) nl += launch_particles_step(d, s->have_prev, parity, st);
+        nl += launch_classify(d, st);
+        nl += launch_pool_spread(d, st);
+        nl += launch_normals(d, d.nrm, st);
+        if (s->timing) s->launches += nl;
+        s->last_parity = parity;
+        s->have_prev = 1;
+        s->steps++;
+    }
+    return launch_check(s);
+}
+
+int fslbm_get_fields(fslbm* s, uint32_t mask, void* const* dst, int dst_on_device) {
+    if (!s || !dst) return FSLBM_EINVAL;
+    Dev& d = s->d;
+    cudaStream_t st = s->st;
+    const long long n = d.n;
+    int k = 0;
+    for (int bit = 0; bit < 32; ++bit) {
+        uint32_t b = 1u << bit;
+        if (!(mask & b)) continue;
+        void* out = dst[k++];
+        if (!out) return FSLBM_EINVAL;
+        switch (b) {
+        case FSLBM_FIELD_PDF:
+            for (int q = 0; q < 27; ++q) {
+                // one direction at a time through the n-double staging buffer
+                launch_export(d, s->last_parity, FSLBM_FIELD_PDF | (uint32_t)(q << 8), s->stage, st);
+                cudaMemcpyAsync(static_cast<double*>(out) + (size_t)q * n, s->stage, n * sizeof(double),
+                                kind_to(dst_on_device), st);
+            }
+            break;
+        case FSLBM_FIELD_TYPE:
+            launch_export_type(d, reinterpret_cast<uint8_t*>(s->stage), st);
+            cudaMemcpyAsync(out, s->stage, n, kind_to(dst_on_device), st);
+            break;
+        case FSLBM_FIELD_OWNER:
+            launch_export_owner(d, reinterpret_cast<int*>(s->stage), st);
+            cudaMemcpyAsync(out, s->stage, n * sizeof(int), kind_to(dst_on_device), st);
+            break;
+        case FSLBM_FIELD_MASS:
+        case FSLBM_FIELD_PHI:
+        case FSLBM_FIELD_RHO:
+            launch_export(d, s->last_parity, b, s->stage, st);
+            cudaMemcpyAsync(out, s->stage, n * sizeof(double), kind_to(dst_on_device), st);
+            break;
+        case FSLBM_FIELD_U:
+        case FSLBM_FIELD_NORMAL:
+            for (int a = 0; a < 3; ++a) {
+                launch_export(d, s->last_parity, b | (uint32_t)(a << 8), s->stage, st);
+                cudaMemcpyAsync(static_cast<double*>(out) + (size_t)a * n, s->stage, n * sizeof(double),
+                                kind_to(dst_on_device), st);
+            }
+            break;
+        case FSLBM_FIELD_P_X:
+            cudaMemcpyAsync(out, d.X, sizeof(double) * 3 * d.np, kind_to(dst_on_device), st);
+            break;
+        case FSLBM_FIELD_P_U:
+            cudaMemcpyAsync(out, d.U, sizeof(double) * 3 * d.np, kind_to(dst_on_device), st);
+            break;
+        case FSLBM_FIELD_P_OMEGA:
+            cudaMemcpyAsync(out, d.W, sizeof(double) * 3 * d.np, kind_to(dst_on_device), st);
+            break;
+        case FSLBM_FIELD_P_F:
+            cudaMemcpyAsync(out, d.Fh, sizeof(double) * 3 * d.np, kind_to(dst_on_device), st);
+            break;
+        case FSLBM_FIELD_P_T:
+            cudaMemcpyAsync(out, d.Th, sizeof(double) * 3 * d.np, kind_to(dst_on_device), st);
+            break;
+        case FSLBM_FIELD_P_R:
+            cudaMemcpyAsync(out, d.R, sizeof(double) * d.np, kind_to(dst_on_device), st);
+            break;
+        default:
+            return FSLBM_EINVAL;
+        }
+    }
+    launch_check(s);
+    return sync_check(s);
+}
+
+int fslbm_set_fields(fslbm* s, uint32_t mask, const void* const* src, int src_on_device) {
+    if (!s || !src) return FSLBM_EINVAL;
+    Dev& d = s->d;
+    cudaStream_t st = s->st;
+    const long long n = d.n;
+    int k = 0;
+    for (int bit = 0; bit < 32; ++bit) {
+        uint32_t b = 1u << bit;
+        if (!(mask & b)) continue;
+        const void* in = src[k++];
+        if (!in) return FSLBM_EINVAL;
+        switch (b) {
+        case FSLBM_FIELD_PDF:
+            for (int q = 0; q < 27; ++q) {
+                cudaMemcpyAsync(s->stage, static_cast<const double*>(in) + (size_t)q * n, n * sizeof(double),
+                                kind_from(src_on_device), st);
+                launch_import_pdf(d, s->last_parity | (q << 8), s->stage, st);
+            }
+            launch_import_pdf(d, s->last_parity | (27 << 8), nullptr, st);
+            break;
+        case FSLBM_FIELD_MASS:
+            cudaMemcpyAsync(s->stage, in, n * sizeof(double), kind_from(src_on_device), st);
+            launch_import_mass(d, s->stage, st);
+            launch_normals(d, d.nrm, st);
+            break;
+        case FSLBM_FIELD_P_U:
+            cudaMemcpyAsync(d.U, in, sizeof(double) * 3 * d.np, kind_from(src_on_device), st);
+            break;
+        case FSLBM_FIELD_P_OMEGA:
+            cudaMemcpyAsync(d.W, in, sizeof(double) * 3 * d.np, kind_from(src_on_device), st);
+            break;
+        default:
+            return FSLBM_EINVAL;
+        }
+    }
+    launch_check(s);
+    return sync_check(s);
+}
+
+int fslbm_reduce(fslbm* s, double out[8]) {
+    if (!s || !out) return FSLBM_EINVAL;
+    launch_reduce(s->d, s->last_parity, s->red, s->st);
+    cudaMemcpyAsync(out, s->red, 8 * sizeof(double), cudaMemcpyDeviceToHost, s->st);
+    launch_check(s);
+    return sync_check(s);
+}
+
+int fslbm_sync(fslbm* s) {
+    if (!s) return FSLBM_EINVAL;
+    launch_check(s);
+    return sync_check(s);
+}
+
+int64_t fslbm_steps_done(const fslbm* s) { return s ? s->steps : -1; }
+int64_t fslbm_num_spheres(const fslbm* s) { return s ? s->d.np : -1; }
+
+int64_t fslbm_invariant_violations(fslbm* s) {
+    if (!s) return -1;
+    unsigned long long v = 0;
+    cudaStreamSynchronize(s->st);
+    cudaMemcpy(&v, s->d.viol, sizeof(v), cudaMemcpyDeviceToHost);
+    return (int64_t)v;
+}
+
+int fslbm_timing(fslbm* s, int on) {
+    if (!s) return FSLBM_EINVAL;
+    s->timing = on != 0;
+    if (on) {
+        cudaStreamSynchronize(s->st);
+        s->ev_used = 0;
+        s->launches = 0;
+    }
+    return launch_check(s);
+}
+
+int fslbm_timing_read(fslbm* s, double* sweep_ms, int64_t* sweeps, int64_t* kernel_launches) {
+    if (!s) return FSLBM_EINVAL;
+    int rc = sync_check(s);
+    double total = 0.0;
+    for (size_t k = 0; k + 1 < s->ev_used; k += 2) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, s->ev[k], s->ev[k + 1]) == cudaSuccess) total += ms;
+    }
+    if (sweep_ms) *sweep_ms = total;
+    if (sweeps) *sweeps = (int64_t)(s->ev_used / 2);
+    if (kernel_launches) *kernel_launches = s->launches;
+    return rc;
+}
+
+int fslbm_cell_counts(fslbm* s, int64_t counts[4]) {
+    if (!s || !counts) return FSLBM_EINVAL;
+    if (!s->counts4) {
+        bool ok = true;
+        s->counts4 = dalloc<unsigned long long>(s, 4, ok);
+        if (!ok) return FSLBM_ENOMEM;
+    }
+    launch_cell_counts(s->d, s->counts4, s->st);
+    unsigned long long h[4] = {0, 0, 0, 0};
+    cudaMemcpyAsync(h, s->counts4, sizeof(h), cudaMemcpyDeviceToHost, s->st);
+    int rc = sync_check(s);
+    for (int k = 0; k < 4; ++k) counts[k] = (int64_t)h[k];
+    return rc;
+}
+
+void fslbm_destroy(fslbm* s) {
+    if (!s) return;
+    cudaStreamSynchronize(s->st);
+    for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
+    for (void* p : s->allocs) cudaFree(p);
+    delete s;
+}
+
+}  // extern "C"

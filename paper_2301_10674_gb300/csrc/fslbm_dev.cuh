@@ -1,0 +1,365 @@
+// Device-side definitions shared by the CUDA translation units of the
+// free-surface LBM / DEM step: lattice constants, the state handed to every
+// kernel, PDF storage formats, AA-pattern slot arithmetic and the cumulant
+// collision (Section 2.1 of Schwarzmeier et al., "Particle-resolved simulation
+// of antidunes in free-surface flows").
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fslbm.h"
+
+namespace fsl {
+
+constexpr int Q = 27;
+
+// direction q = (cx+1) + 3(cy+1) + 9(cz+1)
+__host__ __device__ constexpr int cx(int q) { return q % 3 - 1; }
+__host__ __device__ constexpr int cy(int q) { return (q / 3) % 3 - 1; }
+__host__ __device__ constexpr int cz(int q) { return q / 9 - 1; }
+__host__ __device__ constexpr int opp(int q) { return 26 - q; }
+__host__ __device__ constexpr int nnz(int q) {
+    return (cx(q) != 0) + (cy(q) != 0) + (cz(q) != 0);
+}
+// D3Q27 weights: 8/27 rest, 2/27 faces, 1/54 edges, 1/216 corners
+__host__ __device__ constexpr float wq(int q) {
+    return nnz(q) == 0 ? 8.f / 27.f : nnz(q) == 1 ? 2.f / 27.f : nnz(q) == 2 ? 1.f / 54.f : 1.f / 216.f;
+}
+__host__ __device__ constexpr double wqd(int q) {
+    return nnz(q) == 0 ? 8.0 / 27.0 : nnz(q) == 1 ? 2.0 / 27.0 : nnz(q) == 2 ? 1.0 / 54.0 : 1.0 / 216.0;
+}
+
+// cell flag byte
+enum : uint8_t {
+    T_GAS = 0, T_LIQ = 1, T_IFC = 2, T_SOL = 3, TYPE_MASK = 3,
+    F_BULK = 4,      // liquid, all 26 neighbours inside the domain and liquid
+    F_NEW = 8,       // gas cell becoming interface (filling)
+    F_EMPTIED = 16,  // liquid cell becoming interface (emptying)
+};
+// conversion codes
+enum : uint8_t { CV_TO_LIQ = 1, CV_TO_GAS = 2, CV_EVEN = 4 };
+
+// error bits of the sticky device word (mapped to FSLBM_E* on the host)
+enum : int { ERR_CAPACITY = 1, ERR_NAN = 2, ERR_INVARIANT = 4, ERR_HISTORY = 8, ERR_DISPLACEMENT = 16 };
+
+constexpr int HIST_SLOTS = 16;   // tangential-spring history slots per particle
+
+struct Dev {
+    // lattice
+    int nx, ny, nz;
+    int per_x, per_y, per_z;
+    long long n;
+    // LBM parameters
+    float omega, gx, gy, gz;
+    float rho_gas, eps_conv, eps_normal;
+    int recon_normal;
+    int storage;
+    // PDFs (f - w), AA pattern, direction-major [27][n]; side buffer of the
+    // interface cells' own post-collision PDFs (same format)
+    void* f;
+    void* fs;
+    uint8_t* flags;
+    float* mass;       // interface mass m
+    float* phi;        // interface fill level
+    float4* ru;        // (rho, ux, uy, uz) of the last collision, interface cells
+    float4* nrm;       // interface normal used by the next step's boundary condition
+    float4* nrm1;      // interface normal of the current fill levels (excess weights)
+    int* owner;        // owning particle of solid cells
+    uint8_t* conv;     // conversion code of interface cells (0 outside a step)
+    float* exscale;    // excess mass per unit weight of converting cells
+    // work lists (device counts)
+    int* wl; int* wl_count; int wl_cap;        // interface cells
+    int* nl; int* nl_count; int nl_cap;        // cells becoming interface this step
+    int* tl; int* tl_count; int tl_cap;        // particle map transitions
+    int* tl_info;                               // per transition: new owner / new type
+    double* pool;
+    double* pool_share;
+    int* err;
+    unsigned long long* viol;
+    // particles (FP64 state)
+    int np, np_cap;
+    double* X; double* U; double* W;            // current state
+    double* X2; double* U2; double* W2;         // sub-step ping-pong
+    double* R; double* M; double* I;
+    uint8_t* fixed;
+    double* Fh; double* Th;                     // momentum exchange of this step
+    double* Fp; double* Tp;                     // previous step
+    double* Fa; double* Ta;                     // two-step average
+    int* hist_partner;                          // [np_cap][HIST_SLOTS]
+    double* hist_xi;                            // [np_cap][HIST_SLOTS][3]
+    double rho_p, restitution, friction, poisson, collision_time;
+    double kn_coef, dn_coef, kt_ratio;          // contact law constants (host-computed)
+    double gxd, gyd, gzd;
+    int dem_substeps;
+    // particle grid (DEM neighbours and the particle-to-cell map)
+    int gnx, gny, gnz;
+    double ghx, ghy, ghz;
+    int* g_count; int* g_start; int* g_cursor; int* g_list; int* g_of;
+    double r_max;
+    int* zmax_cell;
+    // static map of the fixed particles
+    unsigned long long* fixkey;
+    int* fixowner;
+};
+
+// ---------------------------------------------------------------- storage
+template <typename S> struct Store;
+template <> struct Store<float> {
+    __device__ static __forceinline__ float ld(const float* p) { return *p; }
+    __device__ static __forceinline__ void st(float* p, float v) { *p = v; }
+};
+template <> struct Store<__half> {
+    __device__ static __forceinline__ float ld(const __half* p) { return __half2float(*p); }
+    __device__ static __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+};
+template <> struct Store<__nv_bfloat16> {
+    __device__ static __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+    __device__ static __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+__device__ __forceinline__ float ld_any(const Dev& s, const void* base, long long i) {
+    if (s.storage == FSLBM_STORE_FP32) return static_cast<const float*>(base)[i];
+    if (s.storage == FSLBM_STORE_FP16) return __half2float(static_cast<const __half*>(base)[i]);
+    return __bfloat162float(static_cast<const __nv_bfloat16*>(base)[i]);
+}
+__device__ __forceinline__ void st_any(const Dev& s, void* base, long long i, float v) {
+    if (s.storage == FSLBM_STORE_FP32) static_cast<float*>(base)[i] = v;
+    else if (s.storage == FSLBM_STORE_FP16) static_cast<__half*>(base)[i] = __float2half_rn(v);
+    else static_cast<__nv_bfloat16*>(base)[i] = __float2bfloat16_rn(v);
+}
+
+// ---------------------------------------------------------------- geometry
+__host__ __device__ __forceinline__ void coords(const Dev& s, long long c, int& x, int& y, int& z) {
+    x = (int)(c % s.nx);
+    long long r = c / s.nx;
+    y = (int)(r % s.ny);
+    z = (int)(r / s.ny);
+}
+
+// coordinate of x + d along an axis of length L: wrapped if periodic, -1 if
+// it lies beyond a wall face
+__device__ __forceinline__ int shift(int x, int d, int L, int periodic) {
+    int v = x + d;
+    if (v < 0) return periodic ? v + L : -1;
+    if (v >= L) return periodic ? v - L : -1;
+    return v;
+}
+
+// neighbour of (x,y,z) at offset (dx,dy,dz); -1 beyond a wall
+__device__ __forceinline__ long long nbr(const Dev& s, int x, int y, int z, int dx, int dy, int dz) {
+    int a = shift(x, dx, s.nx, s.per_x);
+    int b = shift(y, dy, s.ny, s.per_y);
+    int c = shift(z, dz, s.nz, s.per_z);
+    if (a < 0 || b < 0 || c < 0) return -1;
+    return (long long)a + (long long)s.nx * ((long long)b + (long long)s.ny * c);
+}
+
+// AA pattern. After an even step the post-collision PDF f*_q(x) sits in slot
+// (opp(q), x); after an odd step (and initially) it sits in slot
+// (q, x + c_q), or (opp(q), x) when x + c_q lies beyond a wall.
+__device__ __forceinline__ long long fstar_slot(const Dev& s, int q, int x, int y, int z, long long cell,
+                                                int last_parity) {
+    if (last_parity == 0) return (long long)opp(q) * s.n + cell;
+    long long t = nbr(s, x, y, z, cx(q), cy(q), cz(q));
+    if (t < 0) return (long long)opp(q) * s.n + cell;
+    return (long long)q * s.n + t;
+}
+
+// ---------------------------------------------------------------- collision
+// Central moments per axis on deviations from the rest state. A column of
+// three values (c = -1, 0, +1) whose rest part is R (1/6, 2/3, 1/6) maps to
+// moments (k0, k1, k2) about u whose rest part is (R, 0, R/3); only the
+// deviations are carried, so FP32 resolves them to their own precision.
+__device__ __forceinline__ void fwd_axis(float& a, float& b, float& c, float u, float R) {
+    float k0 = a + b + c;
+    float d = c - a;
+    float sm = c + a;
+    float K = R + k0;
+    a = k0;
+    b = d - u * K;
+    c = sm - 2.f * u * d + u * u * K;
+}
+__device__ __forceinline__ void bwd_axis(float& a, float& b, float& c, float u, float R) {
+    float k0 = a, k1 = b, k2 = c;
+    float K = R + k0;
+    float uu = u * u;
+    b = k0 - uu * K - 2.f * u * k1 - k2;
+    a = 0.5f * ((uu - u) * K + (2.f * u - 1.f) * k1 + k2);
+    c = 0.5f * ((uu + u) * K + (2.f * u + 1.f) * k1 + k2);
+}
+
+__device__ __forceinline__ float w1(int i) { return i == 1 ? 2.f / 3.f : 1.f / 6.f; }
+__device__ __forceinline__ float mrest(int i) { return i == 0 ? 1.f : (i == 1 ? 0.f : 1.f / 3.f); }
+
+// D3Q27 cumulant collision on f - w (in place). All relaxation rates are 1
+// except omega for the shear parts of the second-order moments; the trace
+// relaxes to rho; orders 3..6 take the Gaussian closure (all higher
+// cumulants zero); the body force rho g enters through the half-shifted
+// velocity and the sign flip of the first-order central moments. Returns
+// rho and u (the collision velocity).
+__device__ __forceinline__ void collide(float (&f)[27], float omega, float gx, float gy, float gz,
+                                        float& rho_out, float& ux_out, float& uy_out, float& uz_out) {
+    float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+        drho += f[q];
+        if (cx(q)) jx += cx(q) * f[q];
+        if (cy(q)) jy += cy(q) * f[q];
+        if (cz(q)) jz += cz(q) * f[q];
+    }
+    const float rho = 1.f + drho;
+    const float inv = 1.f / rho;
+    const float Fx = rho * gx, Fy = rho * gy, Fz = rho * gz;
+    const float ux = (jx + 0.5f * Fx) * inv;
+    const float uy = (jy + 0.5f * Fy) * inv;
+    const float uz = (jz + 0.5f * Fz) * inv;
+    // forward: z, then y, then x
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            fwd_axis(f[a + 3 * b], f[a + 3 * b + 9], f[a + 3 * b + 18], uz, w1(a) * w1(b));
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            fwd_axis(f[a + 9 * c], f[a + 3 + 9 * c], f[a + 6 + 9 * c], uy, w1(a) * mrest(c));
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            fwd_axis(f[3 * b + 9 * c], f[1 + 3 * b + 9 * c], f[2 + 3 * b + 9 * c], ux, mrest(b) * mrest(c));
+    // m[a + 3b + 9c]: central-moment deviation of orders (a, b, c)
+    const float om1 = 1.f - omega;
+    const float Dxy = om1 * (f[2] - f[6]);
+    const float Dxz = om1 * (f[2] - f[18]);
+    const float k200 = (Dxy + Dxz + drho) * (1.f / 3.f);
+    const float k020 = (Dxz - 2.f * Dxy + drho) * (1.f / 3.f);
+    const float k002 = (Dxy - 2.f * Dxz + drho) * (1.f / 3.f);
+    const float k110 = om1 * f[4];
+    const float k101 = om1 * f[10];
+    const float k011 = om1 * f[12];
+    const float sxx = (k200 - drho * (1.f / 3.f)) * inv;
+    const float syy = (k020 - drho * (1.f / 3.f)) * inv;
+    const float szz = (k002 - drho * (1.f / 3.f)) * inv;
+    const float Sxy = k110 * inv, Sxz = k101 * inv, Syz = k011 * inv;
+    const float third = 1.f / 3.f;
+    f[0] = drho;
+    f[1] = 0.5f * Fx;
+    f[3] = 0.5f * Fy;
+    f[9] = 0.5f * Fz;
+    f[2] = k200; f[6] = k020; f[18] = k002;
+    f[4] = k110; f[10] = k101; f[12] = k011;
+    f[5] = f[11] = f[7] = f[15] = f[19] = f[21] = f[13] = 0.f;
+    f[8] = drho * (1.f / 9.f) + rho * ((sxx + syy) * third + sxx * syy + 2.f * Sxy * Sxy);
+    f[20] = drho * (1.f / 9.f) + rho * ((sxx + szz) * third + sxx * szz + 2.f * Sxz * Sxz);
+    f[24] = drho * (1.f / 9.f) + rho * ((syy + szz) * third + syy * szz + 2.f * Syz * Syz);
+    f[14] = rho * ((third + sxx) * Syz + 2.f * Sxy * Sxz);
+    f[16] = rho * ((third + syy) * Sxz + 2.f * Sxy * Syz);
+    f[22] = rho * ((third + szz) * Sxy + 2.f * Sxz * Syz);
+    f[17] = f[23] = f[25] = 0.f;
+    f[26] = drho * (1.f / 27.f)
+            + rho * ((sxx + syy + szz) * (1.f / 9.f) + (sxx * syy + sxx * szz + syy * szz) * third
+                     + sxx * syy * szz
+                     + 2.f * ((third + sxx) * Syz * Syz + (third + syy) * Sxz * Sxz + (third + szz) * Sxy * Sxy)
+                     + 8.f * Sxy * Sxz * Syz);
+    // backward: x, then y, then z
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            bwd_axis(f[3 * b + 9 * c], f[1 + 3 * b + 9 * c], f[2 + 3 * b + 9 * c], ux, mrest(b) * mrest(c));
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            bwd_axis(f[a + 9 * c], f[a + 3 + 9 * c], f[a + 6 + 9 * c], uy, w1(a) * mrest(c));
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            bwd_axis(f[a + 3 * b], f[a + 3 * b + 9], f[a + 3 * b + 18], uz, w1(a) * w1(b));
+    rho_out = rho;
+    ux_out = ux;
+    uy_out = uy;
+    uz_out = uz;
+}
+
+// second-order equilibrium minus the weight: w_q [(rho - 1) + rho (3 cu +
+// 9/2 cu^2 - 3/2 u^2)]
+__device__ __forceinline__ float feq_dev(int q, float rho, float ux, float uy, float uz) {
+    float cu = cx(q) * ux + cy(q) * uy + cz(q) * uz;
+    float uu = ux * ux + uy * uy + uz * uz;
+    return wq(q) * ((rho - 1.f) + rho * (3.f * cu + 4.5f * cu * cu - 1.5f * uu));
+}
+
+__device__ __forceinline__ void set_error(const Dev& s, int bit) { atomicOr(s.err, bit); }
+
+// byte-granular atomic OR on the flag array; returns the previous byte
+__device__ __forceinline__ uint8_t flag_or(uint8_t* flags, long long i, uint8_t bits) {
+    uintptr_t addr = reinterpret_cast<uintptr_t>(flags + i);
+    unsigned int* word = reinterpret_cast<unsigned int*>(addr & ~uintptr_t(3));
+    unsigned int sh = 8u * (unsigned int)(addr & 3);
+    unsigned int old = atomicOr(word, (unsigned int)bits << sh);
+    return (uint8_t)((old >> sh) & 0xffu);
+}
+
+// post-collision PDFs of a cell read from the AA layout (outside the
+// stream-collide kernel, where no slot is being rewritten)
+__device__ __forceinline__ void load_fstar(const Dev& s, long long cell, int last_parity, float (&f)[27]) {
+    int x, y, z;
+    coords(s, cell, x, y, z);
+#pragma unroll
+    for (int q = 0; q < 27; ++q) f[q] = ld_any(s, s.f, fstar_slot(s, q, x, y, z, cell, last_parity));
+}
+__device__ __forceinline__ void store_fstar(const Dev& s, long long cell, int last_parity, const float (&f)[27]) {
+    int x, y, z;
+    coords(s, cell, x, y, z);
+#pragma unroll
+    for (int q = 0; q < 27; ++q) st_any(s, s.f, fstar_slot(s, q, x, y, z, cell, last_parity), f[q]);
+}
+// density and collision velocity from post-collision PDFs (f - w):
+// rho = 1 + sum, u = (sum c f* - rho g / 2) / rho
+__device__ __forceinline__ void post_moments(const Dev& s, const float (&f)[27], float& rho, float& ux, float& uy,
+                                             float& uz) {
+    float d = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+        d += f[q];
+        jx += cx(q) * f[q];
+        jy += cy(q) * f[q];
+        jz += cz(q) * f[q];
+    }
+    rho = 1.f + d;
+    float inv = 1.f / rho;
+    ux = (jx - 0.5f * rho * s.gx) * inv;
+    uy = (jy - 0.5f * rho * s.gy) * inv;
+    uz = (jz - 0.5f * rho * s.gz) * inv;
+}
+
+// ---------------------------------------------------------------- launchers
+// (defined in the translation units, called from the host orchestration)
+// launchers used inside a time step return the number of kernels enqueued
+int launch_stream_collide(const Dev& s, int parity, cudaStream_t st);
+int launch_classify(const Dev& s, cudaStream_t st);
+int launch_normals(const Dev& s, float4* out, cudaStream_t st);
+int launch_conversion(const Dev& s, int last_parity, cudaStream_t st);
+int launch_pool_spread(const Dev& s, cudaStream_t st);
+void launch_cell_counts(const Dev& s, unsigned long long* out, cudaStream_t st);
+void launch_init_flat(const Dev& s, double H, cudaStream_t st);
+void launch_init_surface(const Dev& s, const double* H, cudaStream_t st);
+int launch_particles_step(const Dev& s, int have_prev, int last_parity, cudaStream_t st);
+void launch_particles_add(const Dev& s, int first, int count, cudaStream_t st);
+int launch_grid_build(const Dev& s, cudaStream_t st);
+void launch_export(const Dev& s, int last_parity, uint32_t which, double* out, cudaStream_t st);
+void launch_export_type(const Dev& s, uint8_t* out, cudaStream_t st);
+void launch_import_pdf(const Dev& s, int last_parity, const double* in, cudaStream_t st);
+void launch_import_mass(const Dev& s, const double* in, cudaStream_t st);
+void launch_reduce(const Dev& s, int last_parity, double* out, cudaStream_t st);
+
+inline int blocks_for(long long n, int threads) { return (int)((n + threads - 1) / threads); }
+
+}  // namespace fsl

@@ -1,0 +1,194 @@
+// Field export/import in the canonical layout of the C ABI (direction-major
+// post-collision PDFs, FP64 scalars) and the FP64 diagnostic reductions of
+// Section 3.2 (liquid mass, momentum, bulk velocity, interface count,
+// bedload rate of Eq. (1)).
+#include "fslbm_dev.cuh"
+
+namespace fsl {
+
+__device__ __forceinline__ bool fluid(uint8_t fl) {
+    int t = fl & TYPE_MASK;
+    return t == T_LIQ || t == T_IFC;
+}
+
+// which & 0xff: FSLBM_FIELD_PDF, MASS, PHI, RHO, U or NORMAL; which >> 8: the
+// direction (PDF) or component (U, NORMAL) written to out[0..n)
+__global__ void k_export(Dev s, int last_parity, uint32_t which, double* out) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= s.n) return;
+    const uint8_t fl = s.flags[c];
+    const int t = fl & TYPE_MASK;
+    const uint32_t field = which & 0xffu;
+    const int sub = (int)(which >> 8);
+    if (field == FSLBM_FIELD_PDF) {
+        if (!fluid(fl)) { out[c] = 0.0; return; }
+        int x, y, z;
+        coords(s, c, x, y, z);
+        out[c] = wqd(sub) + (double)ld_any(s, s.f, fstar_slot(s, sub, x, y, z, c, last_parity));
+        return;
+    }
+    if (field == FSLBM_FIELD_NORMAL) {
+        float4 v = t == T_IFC ? s.nrm[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+        out[c] = sub == 0 ? v.x : (sub == 1 ? v.y : v.z);
+        return;
+    }
+    if (field == FSLBM_FIELD_PHI) {
+        out[c] = t == T_LIQ ? 1.0 : (t == T_IFC ? (double)s.phi[c] : 0.0);
+        return;
+    }
+    double rho = 0.0, u[3] = {0, 0, 0};
+    if (fluid(fl)) {
+        float f[27];
+        load_fstar(s, c, last_parity, f);
+        double d = 0, j[3] = {0, 0, 0};
+        for (int q = 0; q < 27; ++q) {
+            d += f[q];
+            j[0] += cx(q) * (double)f[q];
+            j[1] += cy(q) * (double)f[q];
+            j[2] += cz(q) * (double)f[q];
+        }
+        rho = 1.0 + d;
+        u[0] = (j[0] - 0.5 * rho * s.gxd) / rho;
+        u[1] = (j[1] - 0.5 * rho * s.gyd) / rho;
+        u[2] = (j[2] - 0.5 * rho * s.gzd) / rho;
+    }
+    if (field == FSLBM_FIELD_MASS) out[c] = t == T_LIQ ? rho : (t == T_IFC ? (double)s.mass[c] : 0.0);
+    else if (field == FSLBM_FIELD_RHO) out[c] = rho;
+    else if (field == FSLBM_FIELD_U) out[c] = u[sub];
+}
+
+__global__ void k_export_type(Dev s, uint8_t* out) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < s.n) out[c] = s.flags[c] & TYPE_MASK;
+}
+__global__ void k_export_owner(Dev s, int* out) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < s.n) out[c] = (s.flags[c] & TYPE_MASK) == T_SOL ? s.owner[c] : -1;
+}
+
+void launch_export(const Dev& s, int last_parity, uint32_t which, double* out, cudaStream_t st) {
+    k_export<<<blocks_for(s.n, 128), 128, 0, st>>>(s, last_parity, which, out);
+}
+void launch_export_type(const Dev& s, uint8_t* out, cudaStream_t st) {
+    k_export_type<<<blocks_for(s.n, 256), 256, 0, st>>>(s, out);
+}
+void launch_export_owner(const Dev& s, int* out, cudaStream_t st) {
+    k_export_owner<<<blocks_for(s.n, 256), 256, 0, st>>>(s, out);
+}
+
+// arg & 1: layout parity, arg >> 8: direction q. For q < 27 the PDF f*_q
+// (double, canonical) becomes f - w in its AA slot (and in the side buffer of
+// interface cells); q == 27 refreshes (rho, u) and phi of interface cells.
+__global__ void k_import_pdf(Dev s, int arg, const double* in) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= s.n) return;
+    const uint8_t fl = s.flags[c];
+    if (!fluid(fl)) return;
+    const int last_parity = arg & 1;
+    const int q = arg >> 8;
+    const bool ifc = (fl & TYPE_MASK) == T_IFC;
+    if (q < 27) {
+        int x, y, z;
+        coords(s, c, x, y, z);
+        const float v = (float)(in[c] - wqd(q));
+        st_any(s, s.f, fstar_slot(s, q, x, y, z, c, last_parity), v);
+        if (ifc) st_any(s, s.fs, (long long)q * s.n + c, v);
+        return;
+    }
+    if (!ifc) return;
+    float f[27];
+    for (int k = 0; k < 27; ++k) f[k] = ld_any(s, s.fs, (long long)k * s.n + c);
+    float rho, ux, uy, uz;
+    post_moments(s, f, rho, ux, uy, uz);
+    s.ru[c] = make_float4(rho, ux, uy, uz);
+    s.phi[c] = s.mass[c] / rho;
+}
+void launch_import_pdf(const Dev& s, int arg, const double* in, cudaStream_t st) {
+    k_import_pdf<<<blocks_for(s.n, 128), 128, 0, st>>>(s, arg, in);
+}
+
+__global__ void k_import_mass(Dev s, const double* in) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= s.n) return;
+    if ((s.flags[c] & TYPE_MASK) != T_IFC) return;
+    s.mass[c] = (float)in[c];
+    s.phi[c] = (float)(in[c] / (double)s.ru[c].x);
+}
+void launch_import_mass(const Dev& s, const double* in, cudaStream_t st) {
+    k_import_mass<<<blocks_for(s.n, 256), 256, 0, st>>>(s, in);
+}
+
+// ------------------------------------------------------------ reductions
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    return v;
+}
+
+__global__ void k_reduce_cells(Dev s, int last_parity, double* out) {
+    __shared__ double sh[6][8];
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < s.n;
+         c += (long long)gridDim.x * blockDim.x) {
+        const uint8_t fl = s.flags[c];
+        if (!fluid(fl)) continue;
+        const int t = fl & TYPE_MASK;
+        float f[27];
+        load_fstar(s, c, last_parity, f);
+        double d = 0, j[3] = {0, 0, 0};
+        bool finite = true;
+        for (int q = 0; q < 27; ++q) {
+            finite &= isfinite(f[q]);
+            d += f[q];
+            j[0] += cx(q) * (double)f[q];
+            j[1] += cy(q) * (double)f[q];
+            j[2] += cz(q) * (double)f[q];
+        }
+        if (!finite) set_error(s, ERR_NAN);
+        const double rho = 1.0 + d;
+        const double mx = j[0] - 0.5 * rho * s.gxd;   // rho u
+        const double phi = t == T_LIQ ? 1.0 : (double)s.phi[c];
+        acc[0] += t == T_LIQ ? rho : (double)s.mass[c];
+        acc[1] += mx;
+        acc[2] += j[1] - 0.5 * rho * s.gyd;
+        acc[3] += j[2] - 0.5 * rho * s.gzd;
+        acc[4] += phi * mx;
+        acc[5] += phi * rho;
+        if (t == T_IFC && !isfinite(s.mass[c])) set_error(s, ERR_NAN);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int k = 0; k < 6; ++k) {
+        double v = warp_sum(acc[k]);
+        if (lane == 0) sh[k][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double v = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[threadIdx.x][w];
+        atomicAdd(&out[threadIdx.x], v);
+    }
+}
+
+__global__ void k_reduce_final(Dev s, double* out) {
+    // out[0..5] hold: mass, mom x, y, z, sum phi rho u_x, sum phi rho
+    double qb = 0.0;
+    for (int p = 0; p < s.np; ++p) {
+        double r = s.R[p];
+        qb += s.U[3 * p] * (4.0 / 3.0) * 3.14159265358979323846 * r * r * r;
+        if (!isfinite(s.X[3 * p]) || !isfinite(s.U[3 * p])) set_error(s, ERR_NAN);
+    }
+    double num = out[4], den = out[5];
+    out[0] += *s.pool;
+    out[4] = den > 0 ? num / den : 0.0;
+    out[5] = (double)*s.wl_count;
+    out[6] = qb / ((double)s.nx * (double)s.ny);
+    out[7] = *s.pool;
+    if (!isfinite(*s.pool)) set_error(s, ERR_NAN);
+}
+
+void launch_reduce(const Dev& s, int last_parity, double* out, cudaStream_t st) {
+    cudaMemsetAsync(out, 0, 8 * sizeof(double), st);
+    k_reduce_cells<<<152 * 8, 256, 0, st>>>(s, last_parity, out);
+    k_reduce_final<<<1, 1, 0, st>>>(s, out);
+}
+
+}  // namespace fsl

@@ -1,0 +1,559 @@
+// Geometrically resolved spheres (Section 2.2): two-step averaging of the
+// momentum-exchange force, DEM sub-steps (linear spring-dashpot contacts
+// parameterised by the restitution coefficient and the collision time,
+// tangential spring with Coulomb limit, walls, gravity; semi-implicit
+// Newton-Euler), the particle grid, and the particle-to-cell map with the
+// cells it covers and uncovers. Particle state and forces are FP64; the map
+// test is evaluated in FP64 without fused multiply-add so that cell types do
+// not depend on contraction choices.
+#include <limits.h>
+
+#include "fslbm_dev.cuh"
+
+namespace fsl {
+
+constexpr int HIST_EMPTY = INT_MIN;
+
+// ------------------------------------------------------------ particle grid
+__device__ __forceinline__ int gcoord(double v, double h, int g) {
+    int k = (int)floor(v / h);
+    return k < 0 ? 0 : (k >= g ? g - 1 : k);
+}
+
+__global__ void k_grid_count(Dev s) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= s.np) return;
+    int a = gcoord(s.X[3 * p], s.ghx, s.gnx);
+    int b = gcoord(s.X[3 * p + 1], s.ghy, s.gny);
+    int c = gcoord(s.X[3 * p + 2], s.ghz, s.gnz);
+    int g = a + s.gnx * (b + s.gny * c);
+    s.g_of[p] = g;
+    atomicAdd(&s.g_count[g], 1);
+}
+
+// exclusive scan of the grid counts by one block
+__global__ void k_grid_scan(Dev s, int G) {
+    __shared__ int part[1024];
+    const int t = threadIdx.x;
+    const int chunk = (G + blockDim.x - 1) / blockDim.x;
+    const int lo = t * chunk, hi = min(G, lo + chunk);
+    int sum = 0;
+    for (int i = lo; i < hi; ++i) sum += s.g_count[i];
+    part[t] = sum;
+    __syncthreads();
+    for (int off = 1; off < blockDim.x; off <<= 1) {
+        int v = t >= off ? part[t - off] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int run = part[t] - sum;
+    for (int i = lo; i < hi; ++i) {
+        s.g_start[i] = run;
+        s.g_cursor[i] = run;
+        run += s.g_count[i];
+    }
+}
+
+__global__ void k_grid_fill(Dev s) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= s.np) return;
+    int pos = atomicAdd(&s.g_cursor[s.g_of[p]], 1);
+    s.g_list[pos] = p;
+}
+
+// particles of a grid cell in index order (deterministic summation order)
+__global__ void k_grid_sort(Dev s, int G) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    int b = s.g_start[g], e = b + s.g_count[g];
+    for (int i = b + 1; i < e; ++i) {
+        int v = s.g_list[i];
+        int j = i - 1;
+        while (j >= b && s.g_list[j] > v) {
+            s.g_list[j + 1] = s.g_list[j];
+            --j;
+        }
+        s.g_list[j + 1] = v;
+    }
+}
+
+int launch_grid_build(const Dev& s, cudaStream_t st) {
+    const int G = s.gnx * s.gny * s.gnz;
+    cudaMemsetAsync(s.g_count, 0, sizeof(int) * G, st);
+    k_grid_count<<<blocks_for(s.np, 128), 128, 0, st>>>(s);
+    k_grid_scan<<<1, 1024, 0, st>>>(s, G);
+    k_grid_fill<<<blocks_for(s.np, 128), 128, 0, st>>>(s);
+    k_grid_sort<<<blocks_for(G, 128), 128, 0, st>>>(s, G);
+    return 4;
+}
+
+// distinct grid coordinates within [k0, k1] along one axis
+struct GRange {
+    int v[3];
+    int n;
+};
+__device__ __forceinline__ GRange grange(int k0, int k1, int g, int periodic) {
+    GRange r;
+    r.n = 0;
+    if (periodic && k1 - k0 + 1 >= g) {
+        for (int k = 0; k < g && r.n < 3; ++k) r.v[r.n++] = k;
+        return r;
+    }
+    for (int k = k0; k <= k1 && r.n < 3; ++k) {
+        int kk = k;
+        if (kk < 0 || kk >= g) {
+            if (!periodic) continue;
+            kk = (kk % g + g) % g;
+        }
+        r.v[r.n++] = kk;
+    }
+    return r;
+}
+
+// ------------------------------------------------------------ DEM
+__global__ void k_force_avg(Dev s, int have_prev) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 3 * s.np) return;
+    double fh = s.Fh[k], th = s.Th[k];
+    s.Fa[k] = have_prev ? 0.5 * (fh + s.Fp[k]) : fh;
+    s.Ta[k] = have_prev ? 0.5 * (th + s.Tp[k]) : th;
+    s.Fp[k] = fh;
+    s.Tp[k] = th;
+}
+
+__device__ __forceinline__ void cross3(const double a[3], const double b[3], double c[3]) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// linear spring-dashpot with tangential history; returns the force on the
+// particle, updates xi; n points from the particle to its partner
+__device__ void contact(const Dev& s, double meff, const double n[3], double delta, const double vrel[3],
+                        double* xi, double dts, double F[3], double Ft[3]) {
+    const double kn = meff * s.kn_coef;
+    const double dn = meff * s.dn_coef;
+    const double kt = kn * s.kt_ratio;
+    const double dt_ = dn;
+    double vn = vrel[0] * n[0] + vrel[1] * n[1] + vrel[2] * n[2];
+    double vt[3] = {vrel[0] - vn * n[0], vrel[1] - vn * n[1], vrel[2] - vn * n[2]};
+    double fn = kn * delta + dn * vn;
+    double xn = xi[0] * n[0] + xi[1] * n[1] + xi[2] * n[2];
+    for (int a = 0; a < 3; ++a) xi[a] = xi[a] - xn * n[a] + vt[a] * dts;
+    for (int a = 0; a < 3; ++a) Ft[a] = -kt * xi[a] - dt_ * vt[a];
+    double ftl = sqrt(Ft[0] * Ft[0] + Ft[1] * Ft[1] + Ft[2] * Ft[2]);
+    double lim = s.friction * fabs(fn);
+    if (ftl > lim && ftl > 0.0) {
+        for (int a = 0; a < 3; ++a) {
+            Ft[a] = lim * Ft[a] / ftl;
+            xi[a] = -(Ft[a] + dt_ * vt[a]) / kt;
+        }
+    }
+    for (int a = 0; a < 3; ++a) F[a] = -fn * n[a] + Ft[a];
+}
+
+__device__ __forceinline__ int hist_slot(const Dev& s, int p, int partner, unsigned& seen) {
+    int* hp = s.hist_partner + (long long)p * HIST_SLOTS;
+    int freeslot = -1;
+    for (int k = 0; k < HIST_SLOTS; ++k) {
+        int v = hp[k];
+        if (v == partner) {
+            seen |= 1u << k;
+            return k;
+        }
+        if (v == HIST_EMPTY && freeslot < 0) freeslot = k;
+    }
+    if (freeslot < 0) {
+        set_error(s, ERR_HISTORY);
+        return -1;
+    }
+    hp[freeslot] = partner;
+    double* xi = s.hist_xi + ((long long)p * HIST_SLOTS + freeslot) * 3;
+    xi[0] = xi[1] = xi[2] = 0.0;
+    seen |= 1u << freeslot;
+    return freeslot;
+}
+
+__device__ __forceinline__ double wrapd(double d, int L, int periodic) {
+    if (periodic) d -= (double)L * rint(d / (double)L);
+    return d;
+}
+
+__global__ void k_dem_substep(Dev s, const double* __restrict__ Xa, const double* __restrict__ Ua,
+                              const double* __restrict__ Wa, double* Xb, double* Ub, double* Wb, double dts,
+                              int last) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= s.np) return;
+    double X[3] = {Xa[3 * p], Xa[3 * p + 1], Xa[3 * p + 2]};
+    double U[3] = {Ua[3 * p], Ua[3 * p + 1], Ua[3 * p + 2]};
+    double W[3] = {Wa[3 * p], Wa[3 * p + 1], Wa[3 * p + 2]};
+    if (s.fixed[p]) {
+        for (int a = 0; a < 3; ++a) { Xb[3 * p + a] = X[a]; Ub[3 * p + a] = U[a]; Wb[3 * p + a] = W[a]; }
+        return;
+    }
+    const double ri = s.R[p], mi = s.M[p], Ii = s.I[p];
+    double F[3] = {s.Fa[3 * p] + mi * s.gxd, s.Fa[3 * p + 1] + mi * s.gyd, s.Fa[3 * p + 2] + mi * s.gzd};
+    double T[3] = {s.Ta[3 * p], s.Ta[3 * p + 1], s.Ta[3 * p + 2]};
+    unsigned seen = 0;
+    const int g = s.g_of[p];
+    const int ga = g % s.gnx, gb = (g / s.gnx) % s.gny, gc = g / (s.gnx * s.gny);
+    GRange ra = grange(ga - 1, ga + 1, s.gnx, s.per_x);
+    GRange rb = grange(gb - 1, gb + 1, s.gny, s.per_y);
+    GRange rc = grange(gc - 1, gc + 1, s.gnz, s.per_z);
+    for (int ic = 0; ic < rc.n; ++ic)
+        for (int ib = 0; ib < rb.n; ++ib)
+            for (int ia = 0; ia < ra.n; ++ia) {
+                int gg = ra.v[ia] + s.gnx * (rb.v[ib] + s.gny * rc.v[ic]);
+                int b = s.g_start[gg], e = b + s.g_count[gg];
+                for (int k = b; k < e; ++k) {
+                    int j = s.g_list[k];
+                    if (j == p) continue;
+                    double d[3] = {wrapd(Xa[3 * j] - X[0], s.nx, s.per_x), wrapd(Xa[3 * j + 1] - X[1], s.ny, s.per_y),
+                                   wrapd(Xa[3 * j + 2] - X[2], s.nz, s.per_z)};
+                    double dist2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                    double rs = ri + s.R[j];
+                    if (dist2 >= rs * rs) continue;
+                    double dist = sqrt(dist2);
+                    double n[3] = {d[0] / dist, d[1] / dist, d[2] / dist};
+                    double delta = rs - dist;
+                    double wsum[3], wn[3];
+                    for (int a = 0; a < 3; ++a) wsum[a] = ri * W[a] + s.R[j] * Wa[3 * j + a];
+                    cross3(wsum, n, wn);
+                    double vrel[3];
+                    for (int a = 0; a < 3; ++a) vrel[a] = U[a] - Ua[3 * j + a] + wn[a];
+                    double mj = s.M[j];
+                    double meff = mi * mj / (mi + mj);
+                    int slot = hist_slot(s, p, j, seen);
+                    if (slot < 0) continue;
+                    double* xi = s.hist_xi + ((long long)p * HIST_SLOTS + slot) * 3;
+                    double Fc[3], Ft[3];
+                    contact(s, meff, n, delta, vrel, xi, dts, Fc, Ft);
+                    double rn[3] = {ri * n[0], ri * n[1], ri * n[2]}, tq[3];
+                    cross3(rn, Ft, tq);
+                    for (int a = 0; a < 3; ++a) { F[a] += Fc[a]; T[a] += tq[a]; }
+                }
+            }
+    // walls on non-periodic axes
+    const int L[3] = {s.nx, s.ny, s.nz};
+    const int per[3] = {s.per_x, s.per_y, s.per_z};
+    for (int a = 0; a < 3; ++a) {
+        if (per[a]) continue;
+        for (int side = 0; side < 2; ++side) {
+            double dist = side == 0 ? X[a] : (L[a] - X[a]);
+            double delta = ri - dist;
+            if (delta <= 0.0) continue;
+            double n[3] = {0, 0, 0};
+            n[a] = side == 0 ? -1.0 : 1.0;
+            double rw[3] = {ri * W[0], ri * W[1], ri * W[2]}, wn[3];
+            cross3(rw, n, wn);
+            double vrel[3] = {U[0] + wn[0], U[1] + wn[1], U[2] + wn[2]};
+            int slot = hist_slot(s, p, -1 - (2 * a + side), seen);
+            if (slot < 0) continue;
+            double* xi = s.hist_xi + ((long long)p * HIST_SLOTS + slot) * 3;
+            double Fc[3], Ft[3];
+            contact(s, mi, n, delta, vrel, xi, dts, Fc, Ft);
+            double rn[3] = {ri * n[0], ri * n[1], ri * n[2]}, tq[3];
+            cross3(rn, Ft, tq);
+            for (int b = 0; b < 3; ++b) { F[b] += Fc[b]; T[b] += tq[b]; }
+        }
+    }
+    // contacts that ended release their history
+    int* hp = s.hist_partner + (long long)p * HIST_SLOTS;
+    for (int k = 0; k < HIST_SLOTS; ++k)
+        if (!(seen & (1u << k))) hp[k] = HIST_EMPTY;
+    // semi-implicit Euler
+    for (int a = 0; a < 3; ++a) {
+        U[a] += dts * F[a] / mi;
+        W[a] += dts * T[a] / Ii;
+        double x = X[a] + dts * U[a];
+        if (per[a]) x -= L[a] * floor(x / L[a]);
+        X[a] = x;
+        Xb[3 * p + a] = X[a];
+        Ub[3 * p + a] = U[a];
+        Wb[3 * p + a] = W[a];
+    }
+    if (last) atomicMax(s.zmax_cell, (int)ceil(X[2] + ri) + 2);
+}
+
+// ------------------------------------------------------------ particle map
+__device__ __forceinline__ double map_metric(double kx, double ky, double kz, const double* Xp, double r) {
+    // ((dx^2 + dy^2) + dz^2) - r^2, rounded step by step (no contraction)
+    double dx = __dsub_rn(kx, Xp[0]);
+    double dy = __dsub_rn(ky, Xp[1]);
+    double dz = __dsub_rn(kz, Xp[2]);
+    double s2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    return __dsub_rn(s2, __dmul_rn(r, r));
+}
+
+// unwrapped cell-centre coordinate of the periodic image nearest to X
+__device__ __forceinline__ double image_centre(int k, double X, int L, int periodic) {
+    double c = k + 0.5;
+    if (periodic) {
+        if (c - X > 0.5 * L) c = (k - L) + 0.5;
+        else if (X - c > 0.5 * L) c = (k + L) + 0.5;
+    }
+    return c;
+}
+
+// best covering particle (lowest metric, then lowest index) among the
+// particles of the selected kind near cell (x, y, z)
+__device__ void best_cover(const Dev& s, int x, int y, int z, int want_fixed, double& best, int& bestp) {
+    const double rm = s.r_max;
+    const double xc = x + 0.5, yc = y + 0.5, zc = z + 0.5;
+    GRange ra = grange((int)floor((xc - rm) / s.ghx), (int)floor((xc + rm) / s.ghx), s.gnx, s.per_x);
+    GRange rb = grange((int)floor((yc - rm) / s.ghy), (int)floor((yc + rm) / s.ghy), s.gny, s.per_y);
+    GRange rc = grange((int)floor((zc - rm) / s.ghz), (int)floor((zc + rm) / s.ghz), s.gnz, s.per_z);
+    for (int ic = 0; ic < rc.n; ++ic)
+        for (int ib = 0; ib < rb.n; ++ib)
+            for (int ia = 0; ia < ra.n; ++ia) {
+                int gg = ra.v[ia] + s.gnx * (rb.v[ib] + s.gny * rc.v[ic]);
+                int b = s.g_start[gg], e = b + s.g_count[gg];
+                for (int k = b; k < e; ++k) {
+                    int p = s.g_list[k];
+                    if ((s.fixed[p] != 0) != (want_fixed != 0)) continue;
+                    const double* Xp = s.X + 3 * p;
+                    double r = s.R[p];
+                    // cheap reject in FP32 with a safe margin
+                    float fx = (float)(xc - Xp[0]), fy = (float)(yc - Xp[1]), fz = (float)(zc - Xp[2]);
+                    if (s.per_x) fx -= (float)s.nx * rintf(fx / (float)s.nx);
+                    if (s.per_y) fy -= (float)s.ny * rintf(fy / (float)s.ny);
+                    if (s.per_z) fz -= (float)s.nz * rintf(fz / (float)s.nz);
+                    float d2 = fx * fx + fy * fy + fz * fz;
+                    float rr = (float)r;
+                    if (d2 > rr * rr + 1e-2f * (1.f + rr * rr)) continue;
+                    double m = map_metric(image_centre(x, Xp[0], s.nx, s.per_x), image_centre(y, Xp[1], s.ny, s.per_y),
+                                          image_centre(z, Xp[2], s.nz, s.per_z), Xp, r);
+                    if (m > 0.0) continue;
+                    if (m < best || (m == best && p < bestp)) {
+                        best = m;
+                        bestp = p;
+                    }
+                }
+            }
+}
+
+__global__ void k_fixed_map(Dev s) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= s.n) return;
+    int x, y, z;
+    coords(s, c, x, y, z);
+    double best = __longlong_as_double(0x7ff0000000000000LL);
+    int bestp = -1;
+    best_cover(s, x, y, z, 1, best, bestp);
+    reinterpret_cast<double*>(s.fixkey)[c] = best;
+    s.fixowner[c] = bestp;
+}
+
+// new owner of each cell; at set-up covered cells simply become solid,
+// during a run every change is listed for the transition pass
+__global__ void k_remap(Dev s, int init_mode) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= s.n) return;
+    int x, y, z;
+    coords(s, c, x, y, z);
+    if (z > *s.zmax_cell) return;
+    double best = reinterpret_cast<const double*>(s.fixkey)[c];
+    int bestp = s.fixowner[c];
+    best_cover(s, x, y, z, 0, best, bestp);
+    const uint8_t t0 = s.flags[c] & TYPE_MASK;
+    if (init_mode) {
+        if (bestp >= 0) {
+            s.flags[c] = T_SOL;
+            s.owner[c] = bestp;
+            s.mass[c] = 0.f;
+            s.phi[c] = 0.f;
+        }
+        return;
+    }
+    const bool was = t0 == T_SOL;
+    if ((bestp >= 0) != was || (was && bestp != s.owner[c])) {
+        int k = atomicAdd(s.tl_count, 1);
+        if (k < s.tl_cap) {
+            s.tl[k] = (int)c;
+            s.tl_info[2 * k] = bestp;
+        } else {
+            set_error(s, ERR_CAPACITY);
+        }
+    }
+}
+
+#define FOR_TL(i)                                                                             \
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x, _cnt = min(*s.tl_count, s.tl_cap); i < _cnt; \
+         i += gridDim.x * blockDim.x)
+
+enum : int { NT_UNCOVERED_LIQ = 0x100 };
+
+// covered cells give their mass to the pool; uncovered cells become liquid
+// (interface next to gas, gas without fluid neighbours) with f_eq(mean rho,
+// u_b) and take their mass from the pool (snapshot of the cell types)
+__global__ void k_transitions(Dev s, int last_parity) {
+    FOR_TL(i) {
+        const int c = s.tl[i];
+        const int o1 = s.tl_info[2 * i];
+        const int t0 = s.flags[c] & TYPE_MASK;
+        int nt;
+        if (o1 >= 0) {
+            if (t0 == T_LIQ) {
+                float f[27];
+                load_fstar(s, c, last_parity, f);
+                float d = 0.f;
+                for (int q = 0; q < 27; ++q) d += f[q];
+                atomicAdd(s.pool, (double)(1.f + d));
+            } else if (t0 == T_IFC) {
+                atomicAdd(s.pool, (double)s.mass[c]);
+            }
+            nt = T_SOL;
+        } else {
+            int x, y, z;
+            coords(s, c, x, y, z);
+            float rs = 0.f;
+            int cnt = 0;
+            bool gas = false;
+            for (int q = 0; q < 27; ++q) {
+                if (q == 13) continue;
+                long long nb = nbr(s, x, y, z, cx(q), cy(q), cz(q));
+                if (nb < 0) continue;
+                int tn = s.flags[nb] & TYPE_MASK;
+                if (tn == T_IFC) { rs += s.ru[nb].x; cnt++; }
+                else if (tn == T_LIQ) {
+                    float g[27];
+                    load_fstar(s, nb, last_parity, g);
+                    float d = 0.f;
+                    for (int k = 0; k < 27; ++k) d += g[k];
+                    rs += 1.f + d;
+                    cnt++;
+                }
+                if (tn == T_GAS) gas = true;
+            }
+            if (cnt == 0) {
+                nt = T_GAS;
+            } else {
+                const float rb = rs / cnt;
+                int po = s.owner[c];
+                if (po < 0 || po >= s.np) {
+                    set_error(s, ERR_INVARIANT);
+                    po = 0;
+                }
+                const double* Xp = s.X + 3 * po;
+                double d[3] = {wrapd(x + 0.5 - Xp[0], s.nx, s.per_x), wrapd(y + 0.5 - Xp[1], s.ny, s.per_y),
+                               wrapd(z + 0.5 - Xp[2], s.nz, s.per_z)};
+                const double* Up = s.U + 3 * po;
+                const double* Wp = s.W + 3 * po;
+                double ub[3] = {Up[0] + (Wp[1] * d[2] - Wp[2] * d[1]), Up[1] + (Wp[2] * d[0] - Wp[0] * d[2]),
+                                Up[2] + (Wp[0] * d[1] - Wp[1] * d[0])};
+                float f[27];
+                for (int q = 0; q < 27; ++q) f[q] = feq_dev(q, rb, (float)ub[0], (float)ub[1], (float)ub[2]);
+                store_fstar(s, c, last_parity, f);
+                for (int q = 0; q < 27; ++q) st_any(s, s.fs, (long long)q * s.n + c, f[q]);
+                s.ru[c] = make_float4(rb, (float)ub[0], (float)ub[1], (float)ub[2]);
+                if (gas) {
+                    nt = T_IFC;
+                    s.mass[c] = 0.f;
+                } else {
+                    nt = T_LIQ | NT_UNCOVERED_LIQ;
+                    s.mass[c] = rb;
+                    atomicAdd(s.pool, -(double)rb);
+                }
+            }
+        }
+        s.tl_info[2 * i + 1] = nt;
+    }
+}
+
+__global__ void k_apply_transitions(Dev s) {
+    FOR_TL(i) {
+        const int c = s.tl[i];
+        const int nt = s.tl_info[2 * i + 1];
+        const int t = nt & TYPE_MASK;
+        s.flags[c] = (uint8_t)t;
+        if (t == T_SOL) {
+            s.owner[c] = s.tl_info[2 * i];
+            s.mass[c] = 0.f;
+            s.phi[c] = 0.f;
+        } else {
+            s.owner[c] = -1;
+            if (t == T_GAS) { s.mass[c] = 0.f; s.phi[c] = 0.f; }
+            else if (t == T_IFC) s.phi[c] = s.mass[c] / s.ru[c].x;
+        }
+    }
+}
+
+// an uncovered liquid cell that ended next to a gas cell becomes interface
+__global__ void k_repair(Dev s) {
+    FOR_TL(i) {
+        if (!(s.tl_info[2 * i + 1] & NT_UNCOVERED_LIQ)) continue;
+        const int c = s.tl[i];
+        int x, y, z;
+        coords(s, c, x, y, z);
+        for (int q = 0; q < 27; ++q) {
+            if (q == 13) continue;
+            long long nb = nbr(s, x, y, z, cx(q), cy(q), cz(q));
+            if (nb >= 0 && (s.flags[nb] & TYPE_MASK) == T_GAS) {
+                s.flags[c] = T_IFC;
+                s.phi[c] = s.mass[c] / s.ru[c].x;
+                break;
+            }
+        }
+    }
+}
+
+__global__ void k_copy3(const double* a, double* b, int n3) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n3) b[k] = a[k];
+}
+
+int launch_particles_step(const Dev& s, int have_prev, int last_parity, cudaStream_t st) {
+    if (s.np == 0) return 0;
+    int launches = 0;
+    const int n3 = 3 * s.np;
+    const int ns = s.dem_substeps;
+    k_force_avg<<<blocks_for(n3, 128), 128, 0, st>>>(s, have_prev);
+    cudaMemsetAsync(s.zmax_cell, 0, sizeof(int), st);
+    launches += 1 + ns;
+    const double dts = 1.0 / ns;
+    for (int k = 0; k < ns; ++k) {
+        const bool ev = (k % 2) == 0;
+        k_dem_substep<<<blocks_for(s.np, 64), 64, 0, st>>>(s, ev ? s.X : s.X2, ev ? s.U : s.U2, ev ? s.W : s.W2,
+                                                          ev ? s.X2 : s.X, ev ? s.U2 : s.U, ev ? s.W2 : s.W, dts,
+                                                          k == ns - 1);
+    }
+    if (ns % 2 == 1) {
+        k_copy3<<<blocks_for(n3, 256), 256, 0, st>>>(s.X2, s.X, n3);
+        k_copy3<<<blocks_for(n3, 256), 256, 0, st>>>(s.U2, s.U, n3);
+        k_copy3<<<blocks_for(n3, 256), 256, 0, st>>>(s.W2, s.W, n3);
+        launches += 3;
+    }
+    launches += launch_grid_build(s, st);
+    cudaMemsetAsync(s.tl_count, 0, sizeof(int), st);
+    k_remap<<<blocks_for(s.n, 256), 256, 0, st>>>(s, 0);
+    k_transitions<<<152 * 4, 128, 0, st>>>(s, last_parity);
+    k_apply_transitions<<<152 * 4, 256, 0, st>>>(s);
+    k_repair<<<152 * 4, 256, 0, st>>>(s);
+    return launches + 4;
+}
+
+__global__ void k_init_particles(Dev s, int first, int count, double rho_p) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    int p = first + k;
+    double r = s.R[p];
+    s.M[p] = rho_p * (4.0 / 3.0) * 3.14159265358979323846 * r * r * r;
+    s.I[p] = 0.4 * s.M[p] * r * r;
+    for (int a = 0; a < 3; ++a) {
+        s.U[3 * p + a] = s.W[3 * p + a] = 0.0;
+        s.Fh[3 * p + a] = s.Th[3 * p + a] = s.Fp[3 * p + a] = s.Tp[3 * p + a] = 0.0;
+        s.Fa[3 * p + a] = s.Ta[3 * p + a] = 0.0;
+    }
+    for (int j = 0; j < HIST_SLOTS; ++j) s.hist_partner[(long long)p * HIST_SLOTS + j] = HIST_EMPTY;
+    atomicMax(s.zmax_cell, (int)ceil(s.X[3 * p + 2] + r) + 2);
+}
+
+void launch_particles_add(const Dev& s, int first, int count, cudaStream_t st) {
+    k_init_particles<<<blocks_for(count, 128), 128, 0, st>>>(s, first, count, s.rho_p);
+    launch_grid_build(s, st);
+    k_fixed_map<<<blocks_for(s.n, 256), 256, 0, st>>>(s);
+    k_remap<<<blocks_for(s.n, 256), 256, 0, st>>>(s, 1);
+}
+
+}  // namespace fsl

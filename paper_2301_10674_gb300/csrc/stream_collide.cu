@@ -1,0 +1,286 @@
+// Fused stream + boundary conditions + mass exchange + cumulant collision
+// (Sections 2.1 and 2.2), in place with the AA pattern. One thread per cell.
+//
+// Even step: each cell reads its own slots (q, x), writes (opp(q), x).
+// Odd step: each cell reads (opp(q), x - c_q), writes (q, x + c_q).
+// Every boundary condition is applied where a PDF is read: the value a cell
+// needs for bounce-back or reconstruction is its own post-collision PDF
+// f*_opp(q)(x), which sits in a slot no running cell touches (the slot of a
+// solid/gas neighbour, or of the cell itself across a wall face). Interface
+// cells read it from a side buffer instead, because the normal-based
+// reconstruction also replaces PDFs pulled from fluid neighbours, whose slots
+// are being rewritten.
+//
+// Two kernels share the work: a lean one for bulk liquid cells (all 26
+// neighbours liquid) and a general one for every other liquid or interface
+// cell.
+#include "fslbm_dev.cuh"
+
+namespace fsl {
+
+template <typename S, int PAR>
+__global__ void __launch_bounds__(256) k_bulk(Dev s) {
+    const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= s.n) return;
+    if (!(s.flags[cell] & F_BULK)) return;
+    int x, y, z;
+    coords(s, cell, x, y, z);
+    S* f = static_cast<S*>(s.f);
+    const long long n = s.n;
+    float v[27];
+    // bulk cells have every neighbour inside the domain
+    int xs[3] = {x == 0 ? s.nx - 1 : x - 1, x, x == s.nx - 1 ? 0 : x + 1};
+    int ys[3] = {y == 0 ? s.ny - 1 : y - 1, y, y == s.ny - 1 ? 0 : y + 1};
+    int zs[3] = {z == 0 ? s.nz - 1 : z - 1, z, z == s.nz - 1 ? 0 : z + 1};
+    if (PAR == 0) {
+#pragma unroll
+        for (int q = 0; q < 27; ++q) v[q] = Store<S>::ld(f + (long long)q * n + cell);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 27; ++q) {
+            long long src = xs[1 - cx(q)] + (long long)s.nx * (ys[1 - cy(q)] + (long long)s.ny * zs[1 - cz(q)]);
+            v[q] = Store<S>::ld(f + (long long)opp(q) * n + src);
+        }
+    }
+    float rho, ux, uy, uz;
+    collide(v, s.omega, s.gx, s.gy, s.gz, rho, ux, uy, uz);
+    if (PAR == 0) {
+#pragma unroll
+        for (int q = 0; q < 27; ++q) Store<S>::st(f + (long long)opp(q) * n + cell, v[q]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 27; ++q) {
+            long long dst = xs[1 + cx(q)] + (long long)s.nx * (ys[1 + cy(q)] + (long long)s.ny * zs[1 + cz(q)]);
+            Store<S>::st(f + (long long)q * n + dst, v[q]);
+        }
+    }
+}
+
+// Warp segmented reduction of per-lane (key, F, T) for runs of equal keys,
+// then one FP64 atomic per run and component.
+__device__ __forceinline__ void flush_mem(const Dev& s, int key, float (&F)[3], float (&T)[3]) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    if (!__any_sync(full, key >= 0)) return;
+    int kprev = __shfl_up_sync(full, key, 1);
+    bool head = (lane == 0) || (kprev != key);
+    unsigned heads = __ballot_sync(full, head);
+    unsigned below = heads & ((2u << lane) - 1u);
+    int start = 31 - __clz(below);
+    float v[6] = {F[0], F[1], F[2], T[0], T[1], T[2]};
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            float t = __shfl_up_sync(full, v[k], off);
+            if (lane - off >= start) v[k] += t;
+        }
+    }
+    int knext = __shfl_down_sync(full, key, 1);
+    bool tail = (lane == 31) || (knext != key);
+    if (tail && key >= 0) {
+        atomicAdd(&s.Fh[3 * key + 0], (double)v[0]);
+        atomicAdd(&s.Fh[3 * key + 1], (double)v[1]);
+        atomicAdd(&s.Fh[3 * key + 2], (double)v[2]);
+        atomicAdd(&s.Th[3 * key + 0], (double)v[3]);
+        atomicAdd(&s.Th[3 * key + 1], (double)v[4]);
+        atomicAdd(&s.Th[3 * key + 2], (double)v[5]);
+    }
+}
+
+__device__ __forceinline__ float min_image(float d, int L, int periodic) {
+    if (periodic) d -= (float)L * rintf(d / (float)L);
+    return d;
+}
+
+template <typename S, int PAR>
+__global__ void __launch_bounds__(256) k_general(Dev s) {
+    const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool inrange = cell < s.n;
+    const uint8_t fl = inrange ? s.flags[cell] : (uint8_t)0;
+    const int t = fl & TYPE_MASK;
+    const bool work = inrange && !(fl & F_BULK) && (t == T_LIQ || t == T_IFC);
+    int key = -1;
+    float F[3] = {0.f, 0.f, 0.f}, T[3] = {0.f, 0.f, 0.f};
+    if (work) {
+        int x, y, z;
+        coords(s, cell, x, y, z);
+        S* f = static_cast<S*>(s.f);
+        S* fs = static_cast<S*>(s.fs);
+        const long long n = s.n;
+        const bool ifc = (t == T_IFC);
+        int xs[3] = {shift(x, -1, s.nx, s.per_x), x, shift(x, 1, s.nx, s.per_x)};
+        int ys[3] = {shift(y, -1, s.ny, s.per_y), y, shift(y, 1, s.ny, s.per_y)};
+        int zs[3] = {shift(z, -1, s.nz, s.per_z), z, shift(z, 1, s.nz, s.per_z)};
+        float phix = 0.f, mx = 0.f, dm = 0.f;
+        float4 nn = make_float4(0.f, 0.f, 0.f, 0.f);
+        float urx = 0.f, ury = 0.f, urz = 0.f, uur = 0.f;
+        const float rhoG = s.rho_gas;
+        if (ifc) {
+            phix = s.phi[cell];
+            mx = s.mass[cell];
+            nn = s.nrm[cell];
+            float d = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+            for (int q = 0; q < 27; ++q) {
+                float fq = Store<S>::ld(fs + (long long)q * n + cell);
+                d += fq;
+                jx += cx(q) * fq;
+                jy += cy(q) * fq;
+                jz += cz(q) * fq;
+            }
+            float rr = 1.f + d;
+            urx = (jx - 0.5f * rr * s.gx) / rr;
+            ury = (jy - 0.5f * rr * s.gy) / rr;
+            urz = (jz - 0.5f * rr * s.gz) / rr;
+            uur = urx * urx + ury * ury + urz * urz;
+        }
+        float v[27];
+        int viol = 0;
+#pragma unroll
+        for (int q = 0; q < 27; ++q) {
+            const int sx = xs[1 - cx(q)], sy = ys[1 - cy(q)], sz = zs[1 - cz(q)];
+            float val;
+            if (sx < 0 || sy < 0 || sz < 0) {
+                // wall face: halfway bounce-back, f*_opp(q)(x) is in slot (q, x)
+                val = ifc ? Store<S>::ld(fs + (long long)opp(q) * n + cell) : Store<S>::ld(f + (long long)q * n + cell);
+            } else {
+                const long long src = sx + (long long)s.nx * (sy + (long long)s.ny * sz);
+                const int ts = s.flags[src] & TYPE_MASK;
+                const int p = ts == T_SOL ? s.owner[src] : -1;
+                if (ts == T_SOL && (p < 0 || p >= s.np)) {
+                    // a solid cell without a valid owner: plain bounce-back
+                    set_error(s, ERR_INVARIANT);
+                    val = ifc ? Store<S>::ld(fs + (long long)opp(q) * n + cell)
+                              : Store<S>::ld(f + (PAR == 0 ? (long long)opp(q) * n + src : (long long)q * n + cell));
+                } else if (ts == T_SOL) {
+                    // moving bounce-back and momentum exchange (Section 2.2)
+                    const float fo = ifc ? Store<S>::ld(fs + (long long)opp(q) * n + cell)
+                                         : Store<S>::ld(f + (PAR == 0 ? (long long)opp(q) * n + src
+                                                                          : (long long)q * n + cell));
+                    const double* Xp = s.X + 3 * p;
+                    float dx = (float)((double)(x + 0.5f - 0.5f * cx(q)) - Xp[0]);
+                    float dy = (float)((double)(y + 0.5f - 0.5f * cy(q)) - Xp[1]);
+                    float dz = (float)((double)(z + 0.5f - 0.5f * cz(q)) - Xp[2]);
+                    dx = min_image(dx, s.nx, s.per_x);
+                    dy = min_image(dy, s.ny, s.per_y);
+                    dz = min_image(dz, s.nz, s.per_z);
+                    const double* Up = s.U + 3 * p;
+                    const double* Wp = s.W + 3 * p;
+                    const float wx = (float)Wp[0], wy = (float)Wp[1], wz = (float)Wp[2];
+                    const float ubx = (float)Up[0] + (wy * dz - wz * dy);
+                    const float uby = (float)Up[1] + (wz * dx - wx * dz);
+                    const float ubz = (float)Up[2] + (wx * dy - wy * dx);
+                    const float cu = cx(q) * ubx + cy(q) * uby + cz(q) * ubz;
+                    val = fo + 6.f * wq(q) * cu;
+                    // force on the particle: -c_q (f*_opp + f_q) - u_b (f*_opp - f_q)
+                    // with zero-centred PDFs
+                    const float sum = fo + val, dif = fo - val;
+                    const float Fx = -cx(q) * sum - ubx * dif;
+                    const float Fy = -cy(q) * sum - uby * dif;
+                    const float Fz = -cz(q) * sum - ubz * dif;
+                    if (key != p) {
+                        if (key >= 0) {
+                            atomicAdd(&s.Fh[3 * key + 0], (double)F[0]);
+                            atomicAdd(&s.Fh[3 * key + 1], (double)F[1]);
+                            atomicAdd(&s.Fh[3 * key + 2], (double)F[2]);
+                            atomicAdd(&s.Th[3 * key + 0], (double)T[0]);
+                            atomicAdd(&s.Th[3 * key + 1], (double)T[1]);
+                            atomicAdd(&s.Th[3 * key + 2], (double)T[2]);
+                        }
+                        key = p;
+                        F[0] = F[1] = F[2] = T[0] = T[1] = T[2] = 0.f;
+                    }
+                    F[0] += Fx; F[1] += Fy; F[2] += Fz;
+                    T[0] += dy * Fz - dz * Fy;
+                    T[1] += dz * Fx - dx * Fz;
+                    T[2] += dx * Fy - dy * Fx;
+                } else {
+                    const bool fluid_src = (ts == T_LIQ || ts == T_IFC);
+                    bool rebuild = (ts == T_GAS);
+                    if (!rebuild && ifc && s.recon_normal) {
+                        const float nc = nn.x * cx(q) + nn.y * cy(q) + nn.z * cz(q);
+                        rebuild = nc < -s.eps_normal;
+                    }
+                    float pulled = 0.f;
+                    if (fluid_src)
+                        pulled = Store<S>::ld(f + (PAR == 0 ? (long long)q * n + cell : (long long)opp(q) * n + src));
+                    if (rebuild) {
+                        // gas-pressure boundary condition (Section 2.1):
+                        // f_q = feq_q(rhoG, u) + feq_opp(rhoG, u) - f*_opp(x)
+                        float fo;
+                        if (ifc) {
+                            fo = Store<S>::ld(fs + (long long)opp(q) * n + cell);
+                        } else {
+                            viol = 1;
+                            fo = Store<S>::ld(f + (PAR == 0 ? (long long)opp(q) * n + src : (long long)q * n + cell));
+                        }
+                        const float cu = cx(q) * urx + cy(q) * ury + cz(q) * urz;
+                        val = wq(q) * (2.f * (rhoG - 1.f) + rhoG * (9.f * cu * cu - 3.f * uur)) - fo;
+                    } else {
+                        val = pulled;
+                    }
+                    if (ifc && fluid_src) {
+                        // interface mass exchange with the post-collision PDFs
+                        const float sc = (ts == T_LIQ) ? 1.f : 0.5f * (phix + s.phi[src]);
+                        dm += sc * (pulled - Store<S>::ld(fs + (long long)opp(q) * n + cell));
+                    }
+                }
+            }
+            v[q] = val;
+        }
+        if (viol) atomicAdd(s.viol, 1ull);
+        float rho, ux, uy, uz;
+        collide(v, s.omega, s.gx, s.gy, s.gz, rho, ux, uy, uz);
+        if (PAR == 0) {
+#pragma unroll
+            for (int q = 0; q < 27; ++q) Store<S>::st(f + (long long)opp(q) * n + cell, v[q]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 27; ++q) {
+                const int tx = xs[1 + cx(q)], ty = ys[1 + cy(q)], tz = zs[1 + cz(q)];
+                long long dst;
+                int qq;
+                if (tx < 0 || ty < 0 || tz < 0) {
+                    dst = cell;
+                    qq = opp(q);
+                } else {
+                    dst = tx + (long long)s.nx * (ty + (long long)s.ny * tz);
+                    qq = q;
+                }
+                Store<S>::st(f + (long long)qq * n + dst, v[q]);
+            }
+        }
+        if (ifc) {
+#pragma unroll
+            for (int q = 0; q < 27; ++q) Store<S>::st(fs + (long long)q * n + cell, v[q]);
+            // the fill level phi = m / rho is refreshed after the sweep: the
+            // neighbours read the old phi in the mass exchange above
+            s.mass[cell] = mx + dm;
+            s.ru[cell] = make_float4(rho, ux, uy, uz);
+        }
+    }
+    flush_mem(s, key, F, T);
+}
+
+template <typename S>
+static void launch_typed(const Dev& s, int parity, cudaStream_t st) {
+    const int th = 256;
+    const int bl = blocks_for(s.n, th);
+    if (parity == 0) {
+        k_bulk<S, 0><<<bl, th, 0, st>>>(s);
+        k_general<S, 0><<<bl, th, 0, st>>>(s);
+    } else {
+        k_bulk<S, 1><<<bl, th, 0, st>>>(s);
+        k_general<S, 1><<<bl, th, 0, st>>>(s);
+    }
+}
+
+int launch_stream_collide(const Dev& s, int parity, cudaStream_t st) {
+    if (s.storage == FSLBM_STORE_FP32) launch_typed<float>(s, parity, st);
+    else if (s.storage == FSLBM_STORE_FP16) launch_typed<__half>(s, parity, st);
+    else launch_typed<__nv_bfloat16>(s, parity, st);
+    return 2;
+}
+
+}  // namespace fsl

@@ -1,0 +1,500 @@
+// Free-surface (volume-of-fluid) update after the stream-collide sweep
+// (Section 2.1): fill levels, interface normals, conversion of interface
+// cells, filling/emptying of their neighbours, excess-mass redistribution,
+// the FP64 mass pool, and the interface work list. Every kernel below works
+// on the device-counted list of interface cells (or of cells becoming
+// interface), so its cost scales with the surface, not the lattice; each
+// cell computes its own result from a snapshot of its neighbourhood, so no
+// result depends on thread order.
+#include "fslbm_dev.cuh"
+
+namespace fsl {
+
+constexpr int LIST_THREADS = 256;
+constexpr int LIST_BLOCKS = 152 * 4;
+
+#define FOR_LIST(i, countp)                                                       \
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x, _cnt = *(countp); i < _cnt; \
+         i += gridDim.x * blockDim.x)
+
+__device__ __forceinline__ bool is_fluid(int t) { return t == T_LIQ || t == T_IFC; }
+
+// ------------------------------------------------------------ fill levels
+__global__ void k_update_phi(Dev s) {
+    FOR_LIST(i, s.wl_count) {
+        int c = s.wl[i];
+        s.phi[c] = s.mass[c] / s.ru[c].x;
+    }
+}
+
+// Parker-Youngs normal: gradient sum_c w(c) c phi(x+c) with weights 4 (face),
+// 2 (edge), 1 (corner); solid and wall neighbours take the centre value;
+// n = -grad/|grad| points toward the gas.
+__device__ float4 py_normal(const Dev& s, long long c) {
+    int x, y, z;
+    coords(s, c, x, y, z);
+    const int t0 = s.flags[c] & TYPE_MASK;
+    const float p0 = t0 == T_LIQ ? 1.f : (t0 == T_IFC ? s.phi[c] : 0.f);
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+        if (q == 13) continue;
+        const float w = nnz(q) == 1 ? 4.f : (nnz(q) == 2 ? 2.f : 1.f);
+        long long nb = nbr(s, x, y, z, cx(q), cy(q), cz(q));
+        float v;
+        if (nb < 0) v = p0;
+        else {
+            int tn = s.flags[nb] & TYPE_MASK;
+            v = tn == T_LIQ ? 1.f : (tn == T_IFC ? s.phi[nb] : (tn == T_GAS ? 0.f : p0));
+        }
+        gx += w * cx(q) * v;
+        gy += w * cy(q) * v;
+        gz += w * cz(q) * v;
+    }
+    float len = sqrtf(gx * gx + gy * gy + gz * gz);
+    if (len > 0.f) return make_float4(-gx / len, -gy / len, -gz / len, 0.f);
+    return make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__global__ void k_normals(Dev s, float4* out) {
+    FOR_LIST(i, s.wl_count) {
+        int c = s.wl[i];
+        out[c] = py_normal(s, c);
+    }
+}
+
+// ------------------------------------------------------------ conversion
+// candidates: fill level beyond 1 + eps or below -eps, or isolation (no gas
+// neighbour -> liquid, no liquid neighbour -> gas)
+__global__ void k_candidates(Dev s) {
+    FOR_LIST(i, s.wl_count) {
+        int c = s.wl[i];
+        int x, y, z;
+        coords(s, c, x, y, z);
+        bool has_gas = false, has_liq = false;
+        for (int q = 0; q < 27; ++q) {
+            if (q == 13) continue;
+            long long nb = nbr(s, x, y, z, cx(q), cy(q), cz(q));
+            if (nb < 0) continue;
+            int tn = s.flags[nb] & TYPE_MASK;
+            has_gas |= tn == T_GAS;
+            has_liq |= tn == T_LIQ;
+        }
+        float ph = s.phi[c];
+        uint8_t cv = 0;
+        if (ph > 1.f + s.eps_conv) cv = CV_TO_LIQ;
+        else if (ph < -s.eps_conv) cv = CV_TO_GAS;
+        else if (!has_gas) cv = CV_TO_LIQ;
+        else if (!has_liq) cv = CV_TO_GAS;
+        s.conv[c] = cv;
+    }
+}
+
+// filling wins: a to-gas cell next to a to-liquid cell stays interface
+__global__ void k_conflict(Dev s) {
+    FOR_LIST(i, s.wl_count) {
+        int c = s.wl[i];
+        if (s.conv[c] != CV_TO_GAS) continue;
+        int x, y, z;
+        coords(s, c, x, y, z);
+        bool clash = false;
+        for (int q = 0; q < 27 && !clash; ++q) {
+            if (q == 13) continue;
+            long long nb = nbr(s, x, y, z, cx(q), cy(q), cz(q));
+            if (nb >= 0 && s.conv[nb] == CV_TO_LIQ) clash = true;
+        }
+        if (clash) s.conv[c] = 0;
+    }
+}
+
+__device__ __forceinline__ void list_push(const Dev& s, int* list, int* count, int cap, int v) {
+    int k = atomicAdd(count, 1);
+    if (k < cap) list[k] = v;
+    else set_error(s, ERR_CAPACITY);
+}
+
+// gas neighbours of filled cells and liquid neighbours of emptied cells
+// become interface cells; each is listed once (first setter of its mark)
+__global__ void k_mark(Dev s) {
+    FOR_LIST(i, s.wl_count) {
+        int c = s.wl[i];
+        uint8_t cv = s.conv[c];
+        if (!cv) continue;
+        int x, y, z;
+        coords(s, c, x, y, z);
+        for (int q = 0; q < 27; ++q) {
+            if (q == 13) continue;
+            long long nb = nbr(s, x, y, z, cx(q), cy(q), cz(q));
+            if (nb < 0) continue;
+            int tn = s.flags[nb] & TYPE_MASK;
+            uint8_t bit = 0;
+            if (cv == CV_TO_LIQ && tn == T_GAS) bit = F_NEW;
+            if (cv == CV_TO_GAS && tn == T_LIQ) bit = F_EMPTIED;
+            if (!bit) continue;
+            uint8_t old = flag_or(s.flags, nb, bit);
+            if (!(old & bit)) list_push(s, s.nl, s.nl_count, s.nl_cap, (int)nb);
+        }
+    }
+}
+
+// new interface cells: from gas, f* = f_eq(mean rho, mean u) of the liquid
+// and interface neighbours (cell types of the snapshot) with m = 0; from
+// liquid, PDFs kept and m = rho. Both get their own PDFs in the side buffer.
+__global__ void k_init_new(Dev s, int last_parity) {
+    FOR_LIST(i, s.nl_count) {
+        if (i >= s.nl_cap) break;
+        const int c = s.nl[i];
+        const uint8_t fl = s.flags[c];
+        float f[27];
+        float rho, ux, uy, uz;
+        if (fl & F_NEW) {
+            int x, y, z;
+            coords(s, c, x, y, z);
+            float rs = 0.f, us = 0.f, vs = 0.f, ws = 0.f;
+            int cnt = 0;
+            for (int q = 0; q < 27; ++q) {
+                if (q == 13) continue;
+                long long nb = nbr(s, x, y, z, cx(q), cy(q), cz(q));
+                if (nb < 0) continue;
+                int tn = s.flags[nb] & TYPE_MASK;
+                if (tn == T_IFC) {
+                    float4 r = s.ru[nb];
+                    rs += r.x; us += r.y; vs += r.z; ws += r.w;
+                    cnt++;
+                } else if (tn == T_LIQ) {
+                    float g[27];
+                    load_fstar(s, nb, last_parity, g);
+                    float r0, a, b, d;
+                    post_moments(s, g, r0, a, b, d);
+                    rs += r0; us += a; vs += b; ws += d;
+                    cnt++;
+                }
+            }
+            float inv = cnt ? 1.f / cnt : 0.f;
+            rho = cnt ? rs * inv : s.rho_gas;
+            ux = us * inv; uy = vs * inv; uz = ws * inv;
+#pragma unroll
+            for (int q = 0; q < 27; ++q) f[q] = feq_dev(q, rho, ux, uy, uz);
+            store_fstar(s, c, last_parity, f);
+            s.mass[c] = 0.f;
+        } else {
+            load_fstar(s, c, last_parity, f);
+            post_moments(s, f, rho, ux, uy, uz);
+            s.mass[c] = rho;
+        }
+        for (int q = 0; q < 27; ++q) st_any(s, s.fs, (long long)q * s.n + c, f[q]);
+        s.ru[c] = make_float4(rho, ux, uy, uz);
+    }
+}
+
+__device__ __forceinline__ bool is_receiver(const Dev& s, long long c) {
+    uint8_t fl = s.flags[c];
+    if (fl & (F_NEW | F_EMPTIED)) return true;
+    return (fl & TYPE_MASK) == T_IFC && (s.conv[c] & 3) == 0;
+}
+
+// excess mass of converting cells: m - rho (to liquid, m := rho) or m (to
+// gas, m := 0), spread over interface neighbours with weights max(0, n.c)
+// (filled) or max(0, -n.c) (emptied), evenly if all weights vanish, into the
+// FP64 pool if there is no interface neighbour
+__global__ void k_excess_prep(Dev s) {
+    FOR_LIST(i, s.wl_count) {
+        int c = s.wl[i];
+        uint8_t cv = s.conv[c];
+        if (!cv) continue;
+        float rho = s.ru[c].x;
+        float m = s.mass[c];
+        float ex;
+        if (cv == CV_TO_LIQ) { ex = m - rho; s.mass[c] = rho; }
+        else { ex = m; s.mass[c] = 0.f; }
+        float sg = cv == CV_TO_LIQ ? 1.f : -1.f;
+        float4 n1 = s.nrm1[c];
+        int x, y, z;
+        coords(s, c, x, y, z);
+        float wsum = 0.f;
+        int nrec = 0;
+        for (int q = 0; q < 27; ++q) {
+            if (q == 13) continue;
+            long long nb = nbr(s, x, y, z, cx(q), cy(q), cz(q));
+            if (nb < 0 || !is_receiver(s, nb)) continue;
+            float w = sg * (n1.x * cx(q) + n1.y * cy(q) + n1.z * cz(q));
+            wsum += w > 0.f ? w : 0.f;
+            nrec++;
+        }
+        if (nrec == 0) {
+            atomicAdd(s.pool, (double)ex);
+            s.exscale[c] = 0.f;
+        } else if (wsum > 0.f) {
+            s.exscale[c] = ex / wsum;
+        } else {
+            s.exscale[c] = ex / (float)nrec;
+            s.conv[c] = cv | CV_EVEN;
+        }
+    }
+}
+
+__device__ void gather_excess(const Dev& s, int c) {
+    if (!is_receiver(s, c)) return;
+    int x, y, z;
+    coords(s, c, x, y, z);
+    float add = 0.f;
+    for (int q = 0; q < 27; ++q) {
+        if (q == 13) continue;
+        long long nb = nbr(s, x, y, z, cx(q), cy(q), cz(q));
+        if (nb < 0) continue;
+        uint8_t cv = s.conv[nb];
+        if (!(cv & 3)) continue;
+        float w;
+        if (cv & CV_EVEN) w = 1.f;
+        else {
+            // direction from the converting cell to this receiver is -c_q
+            float4 n1 = s.nrm1[nb];
+            float sg = (cv & 3) == CV_TO_LIQ ? 1.f : -1.f;
+            w = -sg * (n1.x * cx(q) + n1.y * cy(q) + n1.z * cz(q));
+            w = w > 0.f ? w : 0.f;
+        }
+        add += s.exscale[nb] * w;
+    }
+    s.mass[c] += add;
+}
+
+__global__ void k_excess_gather(Dev s) {
+    FOR_LIST(i, s.wl_count) gather_excess(s, s.wl[i]);
+    const int cap = s.nl_cap;
+    FOR_LIST(i, s.nl_count) {
+        if (i >= cap) break;
+        gather_excess(s, s.nl[i]);
+    }
+}
+
+__global__ void k_finalize_old(Dev s) {
+    FOR_LIST(i, s.wl_count) {
+        int c = s.wl[i];
+        uint8_t cv = s.conv[c] & 3;
+        if (cv == CV_TO_LIQ) {
+            s.flags[c] = T_LIQ;
+        } else if (cv == CV_TO_GAS) {
+            s.flags[c] = T_GAS;
+            s.mass[c] = 0.f;
+            s.phi[c] = 0.f;
+        } else {
+            s.phi[c] = s.mass[c] / s.ru[c].x;
+        }
+    }
+}
+__global__ void k_finalize_new(Dev s) {
+    const int cap = s.nl_cap;
+    FOR_LIST(i, s.nl_count) {
+        if (i >= cap) break;
+        int c = s.nl[i];
+        s.flags[c] = T_IFC;
+        s.phi[c] = s.mass[c] / s.ru[c].x;
+    }
+}
+__global__ void k_clear_conv(Dev s) {
+    FOR_LIST(i, s.wl_count) s.conv[s.wl[i]] = 0;
+}
+
+int launch_normals(const Dev& s, float4* out, cudaStream_t st) {
+    k_normals<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(s, out);
+    return 1;
+}
+
+int launch_conversion(const Dev& s, int last_parity, cudaStream_t st) {
+    k_update_phi<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(s);
+    k_normals<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(s, s.nrm1);
+    k_candidates<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(s);
+    k_conflict<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(s);
+    cudaMemsetAsync(s.nl_count, 0, sizeof(int), st);
+    k_mark<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(s);
+    k_init_new<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(s, last_parity);
+    k_excess_prep<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(s);
+    k_excess_gather<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(s);
+    k_finalize_old<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(s);
+    k_finalize_new<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(s);
+    k_clear_conv<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(s);
+    return 12;
+}
+
+// ------------------------------------------------------------ work list
+// Recomputes the bulk bit of every cell and lists the interface cells
+// (warp-aggregated append).
+__global__ void k_classify(Dev s) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool in = c < s.n;
+    int t = 0;
+    if (in) {
+        t = s.flags[c] & TYPE_MASK;
+        bool bulk = false;
+        if (t == T_LIQ) {
+            int x, y, z;
+            coords(s, c, x, y, z);
+            bulk = true;
+            for (int q = 0; q < 27 && bulk; ++q) {
+                if (q == 13) continue;
+                long long nb = nbr(s, x, y, z, cx(q), cy(q), cz(q));
+                if (nb < 0 || (s.flags[nb] & TYPE_MASK) != T_LIQ) bulk = false;
+            }
+        }
+        s.flags[c] = (uint8_t)(t | (bulk ? F_BULK : 0));
+    }
+    const bool ifc = in && t == T_IFC;
+    const unsigned full = 0xffffffffu;
+    unsigned m = __ballot_sync(full, ifc);
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    int leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(s.wl_count, __popc(m));
+    base = __shfl_sync(full, base, leader);
+    if (ifc) {
+        int k = base + __popc(m & ((1u << lane) - 1u));
+        if (k < s.wl_cap) s.wl[k] = (int)c;
+        else set_error(s, ERR_CAPACITY);
+    }
+}
+
+__global__ void k_clamp_count(Dev s) {
+    if (*s.wl_count > s.wl_cap) *s.wl_count = s.wl_cap;
+}
+
+int launch_classify(const Dev& s, cudaStream_t st) {
+    cudaMemsetAsync(s.wl_count, 0, sizeof(int), st);
+    k_classify<<<blocks_for(s.n, 256), 256, 0, st>>>(s);
+    k_clamp_count<<<1, 1, 0, st>>>(s);
+    return 2;
+}
+
+__global__ void k_cell_counts(Dev s, unsigned long long* out) {
+    __shared__ unsigned long long sh[4];
+    if (threadIdx.x < 4) sh[threadIdx.x] = 0;
+    __syncthreads();
+    unsigned long long loc[4] = {0, 0, 0, 0};
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < s.n;
+         c += (long long)gridDim.x * blockDim.x)
+        loc[s.flags[c] & TYPE_MASK]++;
+    for (int k = 0; k < 4; ++k) atomicAdd(&sh[k], loc[k]);
+    __syncthreads();
+    if (threadIdx.x < 4) atomicAdd(&out[threadIdx.x], sh[threadIdx.x]);
+}
+
+void launch_cell_counts(const Dev& s, unsigned long long* out, cudaStream_t st) {
+    cudaMemsetAsync(out, 0, 4 * sizeof(unsigned long long), st);
+    k_cell_counts<<<152 * 4, 256, 0, st>>>(s, out);
+}
+
+// ------------------------------------------------------------ mass pool
+__global__ void k_pool_prepare(Dev s) {
+    int cnt = *s.wl_count;
+    double p = *s.pool;
+    if (cnt > 0 && p != 0.0) {
+        *s.pool_share = p / (double)cnt;
+        *s.pool = 0.0;
+    } else {
+        *s.pool_share = 0.0;
+    }
+}
+__global__ void k_pool_spread(Dev s) {
+    const double share = *s.pool_share;
+    if (share == 0.0) return;
+    FOR_LIST(i, s.wl_count) {
+        int c = s.wl[i];
+        float m = (float)((double)s.mass[c] + share);
+        s.mass[c] = m;
+        s.phi[c] = m / s.ru[c].x;
+    }
+}
+
+int launch_pool_spread(const Dev& s, cudaStream_t st) {
+    k_pool_prepare<<<1, 1, 0, st>>>(s);
+    k_pool_spread<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(s);
+    return 2;
+}
+
+// ------------------------------------------------------------ initial state
+__device__ __forceinline__ float clamp01(double v) { return (float)(v < 0 ? 0 : (v > 1 ? 1 : v)); }
+
+__device__ void init_cell(const Dev& s, long long c, int t, double H, double fill) {
+    int x, y, z;
+    coords(s, c, x, y, z);
+    s.flags[c] = (uint8_t)t;
+    s.owner[c] = -1;
+    s.conv[c] = 0;
+    s.mass[c] = 0.f;
+    s.phi[c] = 0.f;
+    s.ru[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    s.nrm[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (t == T_GAS) return;
+    double rho = (double)s.rho_gas * exp(3.0 * fabs((double)s.gzd) * (H - (z + 0.5)));
+    float f[27];
+#pragma unroll
+    for (int q = 0; q < 27; ++q) f[q] = (float)(wqd(q) * (rho - 1.0));
+    store_fstar(s, c, 1, f);
+    if (t == T_IFC)
+        for (int q = 0; q < 27; ++q) st_any(s, s.fs, (long long)q * s.n + c, f[q]);
+    s.ru[c] = make_float4((float)rho, 0.f, 0.f, 0.f);
+    double m = rho * fill;
+    s.mass[c] = (float)m;
+    s.phi[c] = (float)(m / rho);
+}
+
+// flat surface at height H: fill(k) = clamp(H - k, 0, 1); interface where
+// 0 < fill < 1 or where a full cell has gas directly above
+__global__ void k_init_flat(Dev s, double H) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= s.n) return;
+    int x, y, z;
+    coords(s, c, x, y, z);
+    double fk = H - z;
+    fk = fk < 0 ? 0 : (fk > 1 ? 1 : fk);
+    int t;
+    if (fk == 0.0) t = T_GAS;
+    else {
+        bool above_gas;
+        if (z + 1 < s.nz) {
+            double fa = H - (z + 1);
+            above_gas = fa <= 0.0;
+        } else {
+            above_gas = s.per_z ? (H <= 0.0) : false;
+        }
+        t = (fk < 1.0 || above_gas) ? T_IFC : T_LIQ;
+    }
+    init_cell(s, c, t, H, fk);
+}
+
+// surface height per column: gas where the fill is 0, liquid where it is 1
+// and no 26-neighbour is gas, interface otherwise; solid cells are kept
+__global__ void k_init_surface(Dev s, const double* Hxy) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= s.n) return;
+    if ((s.flags[c] & TYPE_MASK) == T_SOL) return;
+    int x, y, z;
+    coords(s, c, x, y, z);
+    const double H = Hxy[(long long)y * s.nx + x];
+    double fk = H - z;
+    fk = fk < 0 ? 0 : (fk > 1 ? 1 : fk);
+    int t;
+    if (fk == 0.0) t = T_GAS;
+    else {
+        bool gas_nb = false;
+        for (int q = 0; q < 27; ++q) {
+            if (q == 13) continue;
+            long long nb = nbr(s, x, y, z, cx(q), cy(q), cz(q));
+            if (nb < 0 || (s.flags[nb] & TYPE_MASK) == T_SOL) continue;
+            int bx, by, bz;
+            coords(s, nb, bx, by, bz);
+            if (Hxy[(long long)by * s.nx + bx] - bz <= 0.0) gas_nb = true;
+        }
+        t = (fk < 1.0 || gas_nb) ? T_IFC : T_LIQ;
+    }
+    init_cell(s, c, t, H, fk);
+}
+
+void launch_init_flat(const Dev& s, double H, cudaStream_t st) {
+    k_init_flat<<<blocks_for(s.n, 256), 256, 0, st>>>(s, H);
+}
+void launch_init_surface(const Dev& s, const double* H, cudaStream_t st) {
+    k_init_surface<<<blocks_for(s.n, 256), 256, 0, st>>>(s, H);
+}
+
+}  // namespace fsl

@@ -1,0 +1,216 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs. Cell types and particle maps must match exactly;
+FP32 PDFs within 1e-5 relative after one step and 1e-4 after 200 steps."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2301_10674_gb300 import fslbm as F
+from paper_2301_10674_gb300 import workloads as W
+
+from helpers import oracle_from_workload, pdf_rel_err, weights
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2301_10674_gb300 import build as B
+    B.build()
+    F.load()
+
+
+def _sim(w, storage=F.STORE_FP32, spheres=True):
+    return F.Simulation.from_workload(w, storage=storage, spheres=spheres)
+
+
+def _compare(sim, o, pdf_tol, check_particles=True):
+    tg = sim.get(F.FIELD_TYPE)
+    to = o.get(O.F_TYPE)
+    mism = int((tg != to).sum())
+    assert mism == 0, f"{mism} cell types differ"
+    og = sim.get(F.FIELD_OWNER)
+    oo = o.get(O.F_OWNER)
+    solid = to == O.SOLID
+    assert (og[solid] == oo[solid]).all()
+    err = pdf_rel_err(sim.get(F.FIELD_PDF), o.get(O.F_PDF), to)
+    assert err < pdf_tol, err
+    mg, mo = sim.get(F.FIELD_MASS), o.get(O.F_MASS)
+    ifc = to == O.INTERFACE
+    if ifc.any():
+        assert np.abs(mg[ifc] - mo[ifc]).max() < 50 * pdf_tol
+    if check_particles and o.nparticles:
+        xg, xo = sim.get(F.FIELD_P_X), o.get(O.P_X)
+        assert np.abs(xg - xo).max() < 1e-6
+    return err
+
+
+def _periodic_box(nx=10, ny=6, nz=5, g=(1e-4, -5e-5, 2e-5), omega=1.7, seed=3):
+    w = W.Workload(name="box", nx=nx, ny=ny, nz=nz, periodic=(1, 1, 1), tau=1 / omega, g=g,
+                   liquid_height=1e9, bed="none").generate()
+    rng = np.random.default_rng(seed)
+    f0 = weights()[:, None, None, None] * (1 + 0.05 * rng.standard_normal((27, nz, ny, nx)))
+    return w, f0
+
+
+def test_collide_stream_periodic_box():
+    """Random near-equilibrium PDFs in a fully periodic liquid box: one and
+    fifty steps of collision + streaming with forcing."""
+    w, f0 = _periodic_box()
+    sim = _sim(w)
+    o = oracle_from_workload(w)
+    sim.set(F.FIELD_PDF, f0)
+    o.set(O.F_PDF, f0)
+    sim.step(1)
+    o.step(1)
+    assert _compare(sim, o, 1e-5) < 1e-5
+    sim.step(49)
+    o.step(49)
+    assert _compare(sim, o, 1e-4) < 1e-4
+    sim.close()
+
+
+def test_walls_in_every_axis():
+    w, f0 = _periodic_box(nx=7, ny=5, nz=6, g=(1e-4, 0, -1e-4))
+    w.periodic = (0, 0, 0)
+    sim = _sim(w)
+    o = oracle_from_workload(w)
+    sim.set(F.FIELD_PDF, f0)
+    o.set(O.F_PDF, f0)
+    sim.step(1)
+    o.step(1)
+    _compare(sim, o, 1e-5)
+    sim.step(30)
+    o.step(30)
+    _compare(sim, o, 1e-4)
+    sim.close()
+
+
+def test_free_surface_without_particles():
+    """Wavy free surface over a no-slip floor: reconstruction, mass exchange,
+    conversions and excess mass, with exact cell types every 10 steps."""
+    w = W.tiny()
+    w.bed = "none"
+    w.generate()
+    sim = _sim(w)
+    o = oracle_from_workload(w)
+    h = 20.0 + 3.0 * np.cos(2 * np.pi * (np.arange(w.nx) + 0.5) / w.nx) \
+        + 1.0 * np.sin(2 * np.pi * (np.arange(w.ny)[:, None] + 0.5) / w.ny)
+    sim.init_surface(h)
+    o.init_surface(h)
+    _compare(sim, o, 1e-6)
+    sim.step(1)
+    o.step(1)
+    _compare(sim, o, 1e-5)
+    changed = 0
+    t0 = o.get(O.F_TYPE)
+    for _ in range(20):
+        sim.step(10)
+        o.step(10)
+        _compare(sim, o, 1e-4)
+        changed += int((o.get(O.F_TYPE) != t0).sum())
+    assert changed > 0
+    assert sim.violations == 0 and o.violations == 0
+    sim.close()
+
+
+def test_tiny_workload_200_steps():
+    """The 64x16x32 flume with its particle bed: one step, then 200 steps
+    with exact types and particle maps every 20 steps."""
+    w = W.tiny().generate()
+    sim = _sim(w)
+    o = oracle_from_workload(w)
+    _compare(sim, o, 1e-6)
+    sim.step(1)
+    o.step(1)
+    e1 = _compare(sim, o, 1e-5)
+    for _ in range(10):
+        sim.step(20)
+        o.step(20)
+        e = _compare(sim, o, 1e-4)
+    fg, fo = sim.get(F.FIELD_P_F), o.get(O.P_F)
+    scale = np.abs(fo).max()
+    assert np.abs(fg - fo).max() < 1e-3 * scale
+    rg, ro = sim.reduce(), o.reduce()
+    assert abs(rg[0] - ro[0]) / ro[0] < 1e-6
+    print("tiny pdf rel err after 1 / 201 steps:", e1, e)
+    sim.close()
+
+
+def test_moving_particles_cover_and_uncover_cells():
+    """Mobile spheres sinking through liquid cover and uncover cells; the
+    transitions (pool, refill, owner) must match the oracle exactly."""
+    w = W.Workload(name="drop", nx=24, ny=16, nz=24, tau=0.6, g=(0.0, 0.0, -2e-4), liquid_height=20.0,
+                   diameter=6.0, bed="none", seed=7).generate()
+    w.xyz = np.array([[6.3, 8.1, 12.2], [17.7, 7.6, 10.4], [12.0, 8.0, 3.05]])
+    w.radius = np.array([3.0, 2.6, 3.0])
+    w.fixed = np.array([0, 0, 1], np.uint8)
+    sim = _sim(w)
+    o = oracle_from_workload(w)
+    u0 = np.array([[0.02, 0.0, -0.01], [-0.015, 0.01, 0.0], [0.0, 0.0, 0.0]])
+    sim.set(F.FIELD_P_U, u0)
+    o.set(O.P_U, u0)
+    owners0 = o.get(O.F_OWNER)
+    for _ in range(12):
+        sim.step(10)
+        o.step(10)
+        _compare(sim, o, 1e-4)
+    assert (o.get(O.F_OWNER) != owners0).sum() > 20
+    sim.close()
+
+
+@pytest.mark.parametrize("storage,tol", [(F.STORE_FP16, 2e-3), (F.STORE_BF16, 2e-2)])
+def test_reduced_precision_storage(storage, tol):
+    """PDFs stored as f - w in FP16 / BF16 with FP32 arithmetic: one step of
+    the tiny flume within the storage rounding of the deviations."""
+    w = W.tiny().generate()
+    sim = _sim(w, storage=storage)
+    o = oracle_from_workload(w)
+    sim.step(1)
+    o.step(1)
+    tg, to = sim.get(F.FIELD_TYPE), o.get(O.F_TYPE)
+    assert (tg == to).all()
+    fg, fo = sim.get(F.FIELD_PDF), o.get(O.F_PDF)
+    fl = (to == 1) | (to == 2)
+    wq = weights()[:, None]
+    dev = np.abs(fg[:, fl] - fo[:, fl]) / wq
+    assert dev.max() < tol, dev.max()
+    sim.close()
+
+
+def test_mass_conservation_fp32_with_fixed_bed():
+    w = W.tiny().generate()
+    w.fixed[:] = 1
+    sim = _sim(w)
+    m0 = sim.reduce()[0]
+    sim.step(500)
+    m1 = sim.reduce()[0]
+    assert abs(m1 - m0) / m0 < 1e-6
+    assert sim.violations == 0
+    sim.close()
+
+
+def test_capacity_overflow_is_reported():
+    w = W.tiny()
+    w.bed = "none"
+    w.generate()
+    p = F.params_from_workload(w)
+    p.capacity_interface = 16
+    with pytest.raises(F.FslbmError) as e:
+        sim = F.Simulation(p)      # the initial interface layer alone overflows
+        sim.step(1)
+        sim.sync()
+    assert e.value.code == -3
+
+
+def test_non_finite_state_is_reported():
+    w, f0 = _periodic_box()
+    sim = _sim(w)
+    f0[5, 1, 2, 3] = np.nan
+    sim.set(F.FIELD_PDF, f0)
+    with pytest.raises(F.FslbmError) as e:
+        sim.reduce()
+    assert e.value.code == -4
+    sim.close()
