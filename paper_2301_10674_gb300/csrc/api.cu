@@ -229,6 +229,7 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     d.X2 = dalloc<double>(s, 3 * pc, ok); d.U2 = dalloc<double>(s, 3 * pc, ok); d.W2 = dalloc<double>(s, 3 * pc, ok);
     d.R = dalloc<double>(s, pc, ok); d.M = dalloc<double>(s, pc, ok); d.I = dalloc<double>(s, pc, ok);
     d.fixed = dalloc<uint8_t>(s, pc, ok);
+    d.Xr = dalloc<float4>(s, pc, ok);
     d.Fh = dalloc<double>(s, 3 * pc, ok); d.Th = dalloc<double>(s, 3 * pc, ok);
     d.Fp = dalloc<double>(s, 3 * pc, ok); d.Tp = dalloc<double>(s, 3 * pc, ok);
     d.Fa = dalloc<double>(s, 3 * pc, ok); d.Ta = dalloc<double>(s, 3 * pc, ok);

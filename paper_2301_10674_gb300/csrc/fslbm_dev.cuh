@@ -85,6 +85,7 @@ struct Dev {
     double* X2; double* U2; double* W2;         // sub-step ping-pong
     double* R; double* M; double* I;
     uint8_t* fixed;
+    float4* Xr;                                 // (X, Y, Z, r) in FP32, r < 0 for fixed spheres
     double* Fh; double* Th;                     // momentum exchange of this step
     double* Fp; double* Tp;                     // previous step
     double* Fa; double* Ta;                     // two-step average

@@ -273,7 +273,10 @@ __global__ void k_dem_substep(Dev s, const double* __restrict__ Xa, const double
         Ub[3 * p + a] = U[a];
         Wb[3 * p + a] = W[a];
     }
-    if (last) atomicMax(s.zmax_cell, (int)ceil(X[2] + ri) + 2);
+    if (last) {
+        atomicMax(s.zmax_cell, (int)ceil(X[2] + ri) + 2);
+        s.Xr[p] = make_float4((float)X[0], (float)X[1], (float)X[2], (float)ri);
+    }
 }
 
 // ------------------------------------------------------------ particle map
@@ -311,17 +314,18 @@ __device__ void best_cover(const Dev& s, int x, int y, int z, int want_fixed, do
                 int b = s.g_start[gg], e = b + s.g_count[gg];
                 for (int k = b; k < e; ++k) {
                     int p = s.g_list[k];
-                    if ((s.fixed[p] != 0) != (want_fixed != 0)) continue;
-                    const double* Xp = s.X + 3 * p;
-                    double r = s.R[p];
-                    // cheap reject in FP32 with a safe margin
-                    float fx = (float)(xc - Xp[0]), fy = (float)(yc - Xp[1]), fz = (float)(zc - Xp[2]);
+                    const float4 xr = s.Xr[p];
+                    if ((xr.w < 0.f) != (want_fixed != 0)) continue;
+                    // cheap reject in FP32 with a margin far above its rounding
+                    float fx = (float)xc - xr.x, fy = (float)yc - xr.y, fz = (float)zc - xr.z;
                     if (s.per_x) fx -= (float)s.nx * rintf(fx / (float)s.nx);
                     if (s.per_y) fy -= (float)s.ny * rintf(fy / (float)s.ny);
                     if (s.per_z) fz -= (float)s.nz * rintf(fz / (float)s.nz);
-                    float d2 = fx * fx + fy * fy + fz * fz;
-                    float rr = (float)r;
+                    const float d2 = fx * fx + fy * fy + fz * fz;
+                    const float rr = fabsf(xr.w);
                     if (d2 > rr * rr + 1e-2f * (1.f + rr * rr)) continue;
+                    const double* Xp = s.X + 3 * p;
+                    const double r = s.R[p];
                     double m = map_metric(image_centre(x, Xp[0], s.nx, s.per_x), image_centre(y, Xp[1], s.ny, s.per_y),
                                           image_centre(z, Xp[2], s.nz, s.per_z), Xp, r);
                     if (m > 0.0) continue;
@@ -547,6 +551,8 @@ __global__ void k_init_particles(Dev s, int first, int count, double rho_p) {
     }
     for (int j = 0; j < HIST_SLOTS; ++j) s.hist_partner[(long long)p * HIST_SLOTS + j] = HIST_EMPTY;
     atomicMax(s.zmax_cell, (int)ceil(s.X[3 * p + 2] + r) + 2);
+    s.Xr[p] = make_float4((float)s.X[3 * p], (float)s.X[3 * p + 1], (float)s.X[3 * p + 2],
+                          s.fixed[p] ? -(float)r : (float)r);
 }
 
 void launch_particles_add(const Dev& s, int first, int count, cudaStream_t st) {

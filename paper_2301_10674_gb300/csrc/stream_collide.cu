@@ -11,9 +11,9 @@
 // reconstruction also replaces PDFs pulled from fluid neighbours, whose slots
 // are being rewritten.
 //
-// Two kernels share the work: a lean one for bulk liquid cells (all 26
-// neighbours liquid) and a general one for every other liquid or interface
-// cell.
+// Three kernels share the work: a lean one for bulk liquid cells (all 26
+// neighbours liquid), one for the other liquid cells (walls, particle
+// links), and one for the interface cells of the interface list.
 #include "fslbm_dev.cuh"
 
 namespace fsl {
@@ -93,143 +93,106 @@ __device__ __forceinline__ float min_image(float d, int L, int periodic) {
     return d;
 }
 
+// particle surface velocity at a link midpoint and the link force
+// (Section 2.2): f_q = f*_opp + 6 w_q c_q.u_b, force on the particle
+// -c_q (f*_opp + f_q) - u_b (f*_opp - f_q) with zero-centred PDFs; torque
+// about the centre. Accumulated per owner; a change of owner flushes.
+__device__ __forceinline__ float particle_link(const Dev& s, int q, int x, int y, int z, int p, float fo, int& key,
+                                               float (&F)[3], float (&T)[3]) {
+    const double* Xp = s.X + 3 * p;
+    float dx = (float)((double)(x + 0.5f - 0.5f * cx(q)) - Xp[0]);
+    float dy = (float)((double)(y + 0.5f - 0.5f * cy(q)) - Xp[1]);
+    float dz = (float)((double)(z + 0.5f - 0.5f * cz(q)) - Xp[2]);
+    dx = min_image(dx, s.nx, s.per_x);
+    dy = min_image(dy, s.ny, s.per_y);
+    dz = min_image(dz, s.nz, s.per_z);
+    const double* Up = s.U + 3 * p;
+    const double* Wp = s.W + 3 * p;
+    const float wx = (float)Wp[0], wy = (float)Wp[1], wz = (float)Wp[2];
+    const float ubx = (float)Up[0] + (wy * dz - wz * dy);
+    const float uby = (float)Up[1] + (wz * dx - wx * dz);
+    const float ubz = (float)Up[2] + (wx * dy - wy * dx);
+    const float cu = cx(q) * ubx + cy(q) * uby + cz(q) * ubz;
+    const float val = fo + 6.f * wq(q) * cu;
+    const float sum = fo + val, dif = fo - val;
+    const float Fx = -cx(q) * sum - ubx * dif;
+    const float Fy = -cy(q) * sum - uby * dif;
+    const float Fz = -cz(q) * sum - ubz * dif;
+    if (key != p) {
+        if (key >= 0) {
+            atomicAdd(&s.Fh[3 * key + 0], (double)F[0]);
+            atomicAdd(&s.Fh[3 * key + 1], (double)F[1]);
+            atomicAdd(&s.Fh[3 * key + 2], (double)F[2]);
+            atomicAdd(&s.Th[3 * key + 0], (double)T[0]);
+            atomicAdd(&s.Th[3 * key + 1], (double)T[1]);
+            atomicAdd(&s.Th[3 * key + 2], (double)T[2]);
+        }
+        key = p;
+        F[0] = F[1] = F[2] = T[0] = T[1] = T[2] = 0.f;
+    }
+    F[0] += Fx; F[1] += Fy; F[2] += Fz;
+    T[0] += dy * Fz - dz * Fy;
+    T[1] += dz * Fx - dx * Fz;
+    T[2] += dx * Fy - dy * Fx;
+    return val;
+}
+
+// Liquid cells that are not bulk: walls and particle links. All neighbour
+// types are read first, then all 27 PDF loads are issued from computed
+// addresses (no load sits behind a branch), then the particle links.
 template <typename S, int PAR>
-__global__ void __launch_bounds__(256) k_general(Dev s) {
+__global__ void __launch_bounds__(256) k_boundary(Dev s) {
     const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool inrange = cell < s.n;
     const uint8_t fl = inrange ? s.flags[cell] : (uint8_t)0;
-    const int t = fl & TYPE_MASK;
-    const bool work = inrange && !(fl & F_BULK) && (t == T_LIQ || t == T_IFC);
+    const bool work = inrange && (fl & (TYPE_MASK | F_BULK)) == T_LIQ;
     int key = -1;
     float F[3] = {0.f, 0.f, 0.f}, T[3] = {0.f, 0.f, 0.f};
     if (work) {
         int x, y, z;
         coords(s, cell, x, y, z);
         S* f = static_cast<S*>(s.f);
-        S* fs = static_cast<S*>(s.fs);
         const long long n = s.n;
-        const bool ifc = (t == T_IFC);
-        int xs[3] = {shift(x, -1, s.nx, s.per_x), x, shift(x, 1, s.nx, s.per_x)};
-        int ys[3] = {shift(y, -1, s.ny, s.per_y), y, shift(y, 1, s.ny, s.per_y)};
-        int zs[3] = {shift(z, -1, s.nz, s.per_z), z, shift(z, 1, s.nz, s.per_z)};
-        float phix = 0.f, mx = 0.f, dm = 0.f;
-        float4 nn = make_float4(0.f, 0.f, 0.f, 0.f);
-        float urx = 0.f, ury = 0.f, urz = 0.f, uur = 0.f;
-        const float rhoG = s.rho_gas;
-        if (ifc) {
-            phix = s.phi[cell];
-            mx = s.mass[cell];
-            nn = s.nrm[cell];
-            float d = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-            for (int q = 0; q < 27; ++q) {
-                float fq = Store<S>::ld(fs + (long long)q * n + cell);
-                d += fq;
-                jx += cx(q) * fq;
-                jy += cy(q) * fq;
-                jz += cz(q) * fq;
-            }
-            float rr = 1.f + d;
-            urx = (jx - 0.5f * rr * s.gx) / rr;
-            ury = (jy - 0.5f * rr * s.gy) / rr;
-            urz = (jz - 0.5f * rr * s.gz) / rr;
-            uur = urx * urx + ury * ury + urz * urz;
-        }
-        float v[27];
-        int viol = 0;
+        const int xs[3] = {shift(x, -1, s.nx, s.per_x), x, shift(x, 1, s.nx, s.per_x)};
+        const int ys[3] = {shift(y, -1, s.ny, s.per_y), y, shift(y, 1, s.ny, s.per_y)};
+        const int zs[3] = {shift(z, -1, s.nz, s.per_z), z, shift(z, 1, s.nz, s.per_z)};
+        unsigned wallm = 0, solidm = 0, gasm = 0;
 #pragma unroll
         for (int q = 0; q < 27; ++q) {
             const int sx = xs[1 - cx(q)], sy = ys[1 - cy(q)], sz = zs[1 - cz(q)];
-            float val;
             if (sx < 0 || sy < 0 || sz < 0) {
-                // wall face: halfway bounce-back, f*_opp(q)(x) is in slot (q, x)
-                val = ifc ? Store<S>::ld(fs + (long long)opp(q) * n + cell) : Store<S>::ld(f + (long long)q * n + cell);
+                wallm |= 1u << q;
             } else {
-                const long long src = sx + (long long)s.nx * (sy + (long long)s.ny * sz);
-                const int ts = s.flags[src] & TYPE_MASK;
-                const int p = ts == T_SOL ? s.owner[src] : -1;
-                if (ts == T_SOL && (p < 0 || p >= s.np)) {
-                    // a solid cell without a valid owner: plain bounce-back
-                    set_error(s, ERR_INVARIANT);
-                    val = ifc ? Store<S>::ld(fs + (long long)opp(q) * n + cell)
-                              : Store<S>::ld(f + (PAR == 0 ? (long long)opp(q) * n + src : (long long)q * n + cell));
-                } else if (ts == T_SOL) {
-                    // moving bounce-back and momentum exchange (Section 2.2)
-                    const float fo = ifc ? Store<S>::ld(fs + (long long)opp(q) * n + cell)
-                                         : Store<S>::ld(f + (PAR == 0 ? (long long)opp(q) * n + src
-                                                                          : (long long)q * n + cell));
-                    const double* Xp = s.X + 3 * p;
-                    float dx = (float)((double)(x + 0.5f - 0.5f * cx(q)) - Xp[0]);
-                    float dy = (float)((double)(y + 0.5f - 0.5f * cy(q)) - Xp[1]);
-                    float dz = (float)((double)(z + 0.5f - 0.5f * cz(q)) - Xp[2]);
-                    dx = min_image(dx, s.nx, s.per_x);
-                    dy = min_image(dy, s.ny, s.per_y);
-                    dz = min_image(dz, s.nz, s.per_z);
-                    const double* Up = s.U + 3 * p;
-                    const double* Wp = s.W + 3 * p;
-                    const float wx = (float)Wp[0], wy = (float)Wp[1], wz = (float)Wp[2];
-                    const float ubx = (float)Up[0] + (wy * dz - wz * dy);
-                    const float uby = (float)Up[1] + (wz * dx - wx * dz);
-                    const float ubz = (float)Up[2] + (wx * dy - wy * dx);
-                    const float cu = cx(q) * ubx + cy(q) * uby + cz(q) * ubz;
-                    val = fo + 6.f * wq(q) * cu;
-                    // force on the particle: -c_q (f*_opp + f_q) - u_b (f*_opp - f_q)
-                    // with zero-centred PDFs
-                    const float sum = fo + val, dif = fo - val;
-                    const float Fx = -cx(q) * sum - ubx * dif;
-                    const float Fy = -cy(q) * sum - uby * dif;
-                    const float Fz = -cz(q) * sum - ubz * dif;
-                    if (key != p) {
-                        if (key >= 0) {
-                            atomicAdd(&s.Fh[3 * key + 0], (double)F[0]);
-                            atomicAdd(&s.Fh[3 * key + 1], (double)F[1]);
-                            atomicAdd(&s.Fh[3 * key + 2], (double)F[2]);
-                            atomicAdd(&s.Th[3 * key + 0], (double)T[0]);
-                            atomicAdd(&s.Th[3 * key + 1], (double)T[1]);
-                            atomicAdd(&s.Th[3 * key + 2], (double)T[2]);
-                        }
-                        key = p;
-                        F[0] = F[1] = F[2] = T[0] = T[1] = T[2] = 0.f;
-                    }
-                    F[0] += Fx; F[1] += Fy; F[2] += Fz;
-                    T[0] += dy * Fz - dz * Fy;
-                    T[1] += dz * Fx - dx * Fz;
-                    T[2] += dx * Fy - dy * Fx;
-                } else {
-                    const bool fluid_src = (ts == T_LIQ || ts == T_IFC);
-                    bool rebuild = (ts == T_GAS);
-                    if (!rebuild && ifc && s.recon_normal) {
-                        const float nc = nn.x * cx(q) + nn.y * cy(q) + nn.z * cz(q);
-                        rebuild = nc < -s.eps_normal;
-                    }
-                    float pulled = 0.f;
-                    if (fluid_src)
-                        pulled = Store<S>::ld(f + (PAR == 0 ? (long long)q * n + cell : (long long)opp(q) * n + src));
-                    if (rebuild) {
-                        // gas-pressure boundary condition (Section 2.1):
-                        // f_q = feq_q(rhoG, u) + feq_opp(rhoG, u) - f*_opp(x)
-                        float fo;
-                        if (ifc) {
-                            fo = Store<S>::ld(fs + (long long)opp(q) * n + cell);
-                        } else {
-                            viol = 1;
-                            fo = Store<S>::ld(f + (PAR == 0 ? (long long)opp(q) * n + src : (long long)q * n + cell));
-                        }
-                        const float cu = cx(q) * urx + cy(q) * ury + cz(q) * urz;
-                        val = wq(q) * (2.f * (rhoG - 1.f) + rhoG * (9.f * cu * cu - 3.f * uur)) - fo;
-                    } else {
-                        val = pulled;
-                    }
-                    if (ifc && fluid_src) {
-                        // interface mass exchange with the post-collision PDFs
-                        const float sc = (ts == T_LIQ) ? 1.f : 0.5f * (phix + s.phi[src]);
-                        dm += sc * (pulled - Store<S>::ld(fs + (long long)opp(q) * n + cell));
-                    }
-                }
+                const int ts = s.flags[sx + (long long)s.nx * (sy + (long long)s.ny * sz)] & TYPE_MASK;
+                if (ts == T_SOL) solidm |= 1u << q;
+                else if (ts == T_GAS) gasm |= 1u << q;
             }
-            v[q] = val;
         }
-        if (viol) atomicAdd(s.viol, 1ull);
+        float v[27];
+#pragma unroll
+        for (int q = 0; q < 27; ++q) {
+            const int sx = xs[1 - cx(q)], sy = ys[1 - cy(q)], sz = zs[1 - cz(q)];
+            const bool wall = (wallm >> q) & 1u;
+            const bool fluid_src = !(((wallm | solidm | gasm) >> q) & 1u);
+            const long long src = wall ? cell : sx + (long long)s.nx * (sy + (long long)s.ny * sz);
+            long long a;
+            if (PAR == 0) a = (fluid_src || wall) ? (long long)q * n + cell : (long long)opp(q) * n + src;
+            else a = fluid_src ? (long long)opp(q) * n + src : (long long)q * n + cell;
+            v[q] = Store<S>::ld(f + a);
+        }
+        // a liquid cell must not touch gas; if it does, the gas-side PDF is
+        // bounced back and the event counted
+        if (gasm) atomicAdd(s.viol, 1ull);
+        if (solidm) {
+#pragma unroll
+            for (int q = 0; q < 27; ++q) {
+                if (!((solidm >> q) & 1u)) continue;
+                const int sx = xs[1 - cx(q)], sy = ys[1 - cy(q)], sz = zs[1 - cz(q)];
+                const int p = s.owner[sx + (long long)s.nx * (sy + (long long)s.ny * sz)];
+                if (p < 0 || p >= s.np) { set_error(s, ERR_INVARIANT); continue; }
+                v[q] = particle_link(s, q, x, y, z, p, v[q], key, F, T);
+            }
+        }
         float rho, ux, uy, uz;
         collide(v, s.omega, s.gx, s.gy, s.gz, rho, ux, uy, uz);
         if (PAR == 0) {
@@ -239,40 +202,150 @@ __global__ void __launch_bounds__(256) k_general(Dev s) {
 #pragma unroll
             for (int q = 0; q < 27; ++q) {
                 const int tx = xs[1 + cx(q)], ty = ys[1 + cy(q)], tz = zs[1 + cz(q)];
-                long long dst;
-                int qq;
-                if (tx < 0 || ty < 0 || tz < 0) {
-                    dst = cell;
-                    qq = opp(q);
-                } else {
-                    dst = tx + (long long)s.nx * (ty + (long long)s.ny * tz);
-                    qq = q;
-                }
-                Store<S>::st(f + (long long)qq * n + dst, v[q]);
+                const bool out = tx < 0 || ty < 0 || tz < 0;
+                const long long a = out ? (long long)opp(q) * n + cell
+                                        : (long long)q * n + tx + (long long)s.nx * (ty + (long long)s.ny * tz);
+                Store<S>::st(f + a, v[q]);
             }
-        }
-        if (ifc) {
-#pragma unroll
-            for (int q = 0; q < 27; ++q) Store<S>::st(fs + (long long)q * n + cell, v[q]);
-            // the fill level phi = m / rho is refreshed after the sweep: the
-            // neighbours read the old phi in the mass exchange above
-            s.mass[cell] = mx + dm;
-            s.ru[cell] = make_float4(rho, ux, uy, uz);
         }
     }
     flush_mem(s, key, F, T);
+}
+
+// Interface cells, from the interface list: gas-pressure reconstruction
+// (Section 2.1), mass exchange, particle links, collision; the cell's own
+// post-collision PDFs come from and go to the side buffer.
+template <typename S, int PAR>
+__global__ void __launch_bounds__(128) k_interface(Dev s) {
+    const int count = min(*s.wl_count, s.wl_cap);
+    const int stride = gridDim.x * blockDim.x;
+    for (int base = blockIdx.x * blockDim.x; base < count; base += stride) {
+        const int i = base + threadIdx.x;
+        const bool work = i < count;
+        int key = -1;
+        float F[3] = {0.f, 0.f, 0.f}, T[3] = {0.f, 0.f, 0.f};
+        if (work) {
+            const long long cell = s.wl[i];
+            int x, y, z;
+            coords(s, cell, x, y, z);
+            S* f = static_cast<S*>(s.f);
+            S* fs = static_cast<S*>(s.fs);
+            const long long n = s.n;
+            const int xs[3] = {shift(x, -1, s.nx, s.per_x), x, shift(x, 1, s.nx, s.per_x)};
+            const int ys[3] = {shift(y, -1, s.ny, s.per_y), y, shift(y, 1, s.ny, s.per_y)};
+            const int zs[3] = {shift(z, -1, s.nz, s.per_z), z, shift(z, 1, s.nz, s.per_z)};
+            unsigned wallm = 0, solidm = 0, gasm = 0, liqm = 0;
+#pragma unroll
+            for (int q = 0; q < 27; ++q) {
+                const int sx = xs[1 - cx(q)], sy = ys[1 - cy(q)], sz = zs[1 - cz(q)];
+                if (sx < 0 || sy < 0 || sz < 0) {
+                    wallm |= 1u << q;
+                } else {
+                    const int ts = s.flags[sx + (long long)s.nx * (sy + (long long)s.ny * sz)] & TYPE_MASK;
+                    if (ts == T_SOL) solidm |= 1u << q;
+                    else if (ts == T_GAS) gasm |= 1u << q;
+                    else if (ts == T_LIQ) liqm |= 1u << q;
+                }
+            }
+            const float phix = s.phi[cell];
+            const float mx = s.mass[cell];
+            const float4 nn = s.nrm[cell];
+            float fo[27];
+#pragma unroll
+            for (int q = 0; q < 27; ++q) fo[q] = Store<S>::ld(fs + (long long)q * n + cell);
+            float v[27];
+#pragma unroll
+            for (int q = 0; q < 27; ++q) {
+                const int sx = xs[1 - cx(q)], sy = ys[1 - cy(q)], sz = zs[1 - cz(q)];
+                const bool fluid_src = !(((wallm | solidm | gasm) >> q) & 1u);
+                const long long src = fluid_src ? sx + (long long)s.nx * (sy + (long long)s.ny * sz) : cell;
+                const long long a = PAR == 0 ? (long long)q * n + cell : (long long)opp(q) * n + src;
+                v[q] = fluid_src ? Store<S>::ld(f + a) : 0.f;
+            }
+            // own collision velocity from the post-collision PDFs
+            float d = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+            for (int q = 0; q < 27; ++q) {
+                d += fo[q];
+                jx += cx(q) * fo[q];
+                jy += cy(q) * fo[q];
+                jz += cz(q) * fo[q];
+            }
+            const float rr = 1.f + d;
+            const float urx = (jx - 0.5f * rr * s.gx) / rr;
+            const float ury = (jy - 0.5f * rr * s.gy) / rr;
+            const float urz = (jz - 0.5f * rr * s.gz) / rr;
+            const float uur = urx * urx + ury * ury + urz * urz;
+            const float rhoG = s.rho_gas;
+            float dm = 0.f;
+#pragma unroll
+            for (int q = 0; q < 27; ++q) {
+                const float fob = fo[opp(q)];
+                if ((wallm >> q) & 1u) {
+                    v[q] = fob;
+                    continue;
+                }
+                const int sx = xs[1 - cx(q)], sy = ys[1 - cy(q)], sz = zs[1 - cz(q)];
+                const long long src = sx + (long long)s.nx * (sy + (long long)s.ny * sz);
+                if ((solidm >> q) & 1u) {
+                    const int p = s.owner[src];
+                    if (p < 0 || p >= s.np) { set_error(s, ERR_INVARIANT); v[q] = fob; continue; }
+                    v[q] = particle_link(s, q, x, y, z, p, fob, key, F, T);
+                    continue;
+                }
+                const bool gas = (gasm >> q) & 1u;
+                if (!gas) {
+                    // fluid source: mass exchange with the pulled post-collision PDF
+                    const bool liq = (liqm >> q) & 1u;
+                    const float sc = liq ? 1.f : 0.5f * (phix + s.phi[src]);
+                    dm += sc * (v[q] - fob);
+                }
+                bool rebuild = gas;
+                if (!rebuild && s.recon_normal) rebuild = (nn.x * cx(q) + nn.y * cy(q) + nn.z * cz(q)) < -s.eps_normal;
+                if (rebuild) {
+                    const float cu = cx(q) * urx + cy(q) * ury + cz(q) * urz;
+                    v[q] = wq(q) * (2.f * (rhoG - 1.f) + rhoG * (9.f * cu * cu - 3.f * uur)) - fob;
+                }
+            }
+            float rho, ux, uy, uz;
+            collide(v, s.omega, s.gx, s.gy, s.gz, rho, ux, uy, uz);
+            if (PAR == 0) {
+#pragma unroll
+                for (int q = 0; q < 27; ++q) Store<S>::st(f + (long long)opp(q) * n + cell, v[q]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 27; ++q) {
+                    const int tx = xs[1 + cx(q)], ty = ys[1 + cy(q)], tz = zs[1 + cz(q)];
+                    const bool out = tx < 0 || ty < 0 || tz < 0;
+                    const long long a = out ? (long long)opp(q) * n + cell
+                                            : (long long)q * n + tx + (long long)s.nx * (ty + (long long)s.ny * tz);
+                    Store<S>::st(f + a, v[q]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 27; ++q) Store<S>::st(fs + (long long)q * n + cell, v[q]);
+            // phi = m / rho is refreshed after the sweep: neighbours read the
+            // old phi in their mass exchange
+            s.mass[cell] = mx + dm;
+            s.ru[cell] = make_float4(rho, ux, uy, uz);
+        }
+        flush_mem(s, key, F, T);
+    }
 }
 
 template <typename S>
 static void launch_typed(const Dev& s, int parity, cudaStream_t st) {
     const int th = 256;
     const int bl = blocks_for(s.n, th);
+    const int ib = 152 * 8;
     if (parity == 0) {
         k_bulk<S, 0><<<bl, th, 0, st>>>(s);
-        k_general<S, 0><<<bl, th, 0, st>>>(s);
+        k_boundary<S, 0><<<bl, th, 0, st>>>(s);
+        k_interface<S, 0><<<ib, 128, 0, st>>>(s);
     } else {
         k_bulk<S, 1><<<bl, th, 0, st>>>(s);
-        k_general<S, 1><<<bl, th, 0, st>>>(s);
+        k_boundary<S, 1><<<bl, th, 0, st>>>(s);
+        k_interface<S, 1><<<ib, 128, 0, st>>>(s);
     }
 }
 
@@ -280,7 +353,7 @@ int launch_stream_collide(const Dev& s, int parity, cudaStream_t st) {
     if (s.storage == FSLBM_STORE_FP32) launch_typed<float>(s, parity, st);
     else if (s.storage == FSLBM_STORE_FP16) launch_typed<__half>(s, parity, st);
     else launch_typed<__nv_bfloat16>(s, parity, st);
-    return 2;
+    return 3;
 }
 
 }  // namespace fsl

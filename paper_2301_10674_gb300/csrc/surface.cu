@@ -329,11 +329,18 @@ __global__ void k_classify(Dev s) {
         if (t == T_LIQ) {
             int x, y, z;
             coords(s, c, x, y, z);
-            bulk = true;
-            for (int q = 0; q < 27 && bulk; ++q) {
-                if (q == 13) continue;
-                long long nb = nbr(s, x, y, z, cx(q), cy(q), cz(q));
-                if (nb < 0 || (s.flags[nb] & TYPE_MASK) != T_LIQ) bulk = false;
+            const int xs[3] = {shift(x, -1, s.nx, s.per_x), x, shift(x, 1, s.nx, s.per_x)};
+            const int ys[3] = {shift(y, -1, s.ny, s.per_y), y, shift(y, 1, s.ny, s.per_y)};
+            const int zs[3] = {shift(z, -1, s.nz, s.per_z), z, shift(z, 1, s.nz, s.per_z)};
+            bool inside = xs[0] >= 0 && xs[2] >= 0 && ys[0] >= 0 && ys[2] >= 0 && zs[0] >= 0 && zs[2] >= 0;
+            if (inside) {
+                unsigned all = T_LIQ;
+#pragma unroll
+                for (int q = 0; q < 27; ++q) {
+                    if (q == 13) continue;
+                    all &= (unsigned)(s.flags[xs[1 + cx(q)] + (long long)s.nx * (ys[1 + cy(q)] + (long long)s.ny * zs[1 + cz(q)])] & TYPE_MASK) == T_LIQ ? T_LIQ : 0u;
+                }
+                bulk = all == T_LIQ;
             }
         }
         s.flags[c] = (uint8_t)(t | (bulk ? F_BULK : 0));
