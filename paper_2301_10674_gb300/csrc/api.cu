@@ -214,6 +214,8 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
         d.tl_count = counts + 2;
         d.zmax_cell = counts + 3;
         d.err = counts + 4;
+        d.act_count = counts + 5;
+        d.dl_count = counts + 6;
     }
     double* dd = dalloc<double>(s, 4, ok);
     if (ok) {
@@ -230,12 +232,25 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     d.R = dalloc<double>(s, pc, ok); d.M = dalloc<double>(s, pc, ok); d.I = dalloc<double>(s, pc, ok);
     d.fixed = dalloc<uint8_t>(s, pc, ok);
     d.Xr = dalloc<float4>(s, pc, ok);
+    d.Xi = dalloc<int4>(s, pc, ok);
+    d.Xfr = dalloc<float4>(s, pc, ok);
+    d.Uf = dalloc<float4>(s, pc, ok);
+    d.Wf = dalloc<float4>(s, pc, ok);
     d.Fh = dalloc<double>(s, 3 * pc, ok); d.Th = dalloc<double>(s, 3 * pc, ok);
     d.Fp = dalloc<double>(s, 3 * pc, ok); d.Tp = dalloc<double>(s, 3 * pc, ok);
     d.Fa = dalloc<double>(s, 3 * pc, ok); d.Ta = dalloc<double>(s, 3 * pc, ok);
     d.hist_partner = dalloc<int>(s, pc * HIST_SLOTS, ok);
     d.hist_xi = dalloc<double>(s, pc * HIST_SLOTS * 3, ok);
     d.g_of = dalloc<int>(s, pc, ok);
+    d.Xm = dalloc<double>(s, 3 * pc, ok);
+    d.margin = dalloc<float>(s, pc, ok);
+    d.shared = dalloc<int>(s, pc, ok);
+    d.act = dalloc<int>(s, pc, ok);
+    d.dirty = dalloc<uint8_t>(s, n + 4, ok);
+    long long dcap = n / 4 + 4096;
+    if (dcap > n) dcap = n;
+    d.dl_cap = (int)dcap;
+    d.dl = dalloc<int>(s, dcap, ok);
     d.g_list = dalloc<int>(s, pc, ok);
     s->stage = dalloc<double>(s, n > 8 ? n : 8, ok);
     s->red = dalloc<double>(s, 8, ok);
@@ -252,6 +267,7 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     cudaMemsetAsync(counts, 0, 8 * sizeof(int), st);
     cudaMemsetAsync(dd, 0, 4 * sizeof(double), st);
     cudaMemsetAsync(d.viol, 0, sizeof(unsigned long long), st);
+    cudaMemsetAsync(d.dirty, 0, n + 4, st);
     cudaMemsetAsync(d.fixowner, 0xff, n * sizeof(int), st);
     launch_init_flat(d, p->liquid_height, st);
     launch_classify(d, st);
@@ -487,6 +503,7 @@ int fslbm_set_fields(fslbm* s, uint32_t mask, const void* const* src, int src_on
             return FSLBM_EINVAL;
         }
     }
+    if (mask & (FSLBM_FIELD_P_U | FSLBM_FIELD_P_OMEGA)) launch_particle_copies(d, st);
     launch_check(s);
     return sync_check(s);
 }

@@ -86,6 +86,9 @@ struct Dev {
     double* R; double* M; double* I;
     uint8_t* fixed;
     float4* Xr;                                 // (X, Y, Z, r) in FP32, r < 0 for fixed spheres
+    int4* Xi;                                   // floor of the centre ...
+    float4* Xfr;                                // ... and the fraction, for exact FP32 link offsets
+    float4* Uf; float4* Wf;                     // FP32 copies of U and Omega for the links
     double* Fh; double* Th;                     // momentum exchange of this step
     double* Fp; double* Tp;                     // previous step
     double* Fa; double* Ta;                     // two-step average
@@ -101,6 +104,14 @@ struct Dev {
     int* g_count; int* g_start; int* g_cursor; int* g_list; int* g_of;
     double r_max;
     int* zmax_cell;
+    // incremental re-mapping: position of the last map, margin to the nearest
+    // cell centre, shared-cell flag, active particles and their cells
+    double* Xm;
+    float* margin;
+    int* shared;
+    int* act; int* act_count;
+    uint8_t* dirty;
+    int* dl; int* dl_count; int dl_cap;
     // static map of the fixed particles
     unsigned long long* fixkey;
     int* fixowner;
@@ -354,6 +365,7 @@ void launch_init_flat(const Dev& s, double H, cudaStream_t st);
 void launch_init_surface(const Dev& s, const double* H, cudaStream_t st);
 int launch_particles_step(const Dev& s, int have_prev, int last_parity, cudaStream_t st);
 void launch_particles_add(const Dev& s, int first, int count, cudaStream_t st);
+void launch_particle_copies(const Dev& s, cudaStream_t st);
 int launch_grid_build(const Dev& s, cudaStream_t st);
 void launch_export(const Dev& s, int last_parity, uint32_t which, double* out, cudaStream_t st);
 void launch_export_type(const Dev& s, uint8_t* out, cudaStream_t st);

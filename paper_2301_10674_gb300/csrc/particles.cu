@@ -175,8 +175,21 @@ __device__ __forceinline__ int hist_slot(const Dev& s, int p, int partner, unsig
     return freeslot;
 }
 
+// minimal image of a displacement along a periodic axis (|d| < 1.5 L)
 __device__ __forceinline__ double wrapd(double d, int L, int periodic) {
-    if (periodic) d -= (double)L * rint(d / (double)L);
+    if (periodic) {
+        const double h = 0.5 * L;
+        if (d > h) d -= L;
+        else if (d < -h) d += L;
+    }
+    return d;
+}
+__device__ __forceinline__ float wrapf(float d, int L, int periodic) {
+    if (periodic) {
+        const float h = 0.5f * L;
+        if (d > h) d -= L;
+        else if (d < -h) d += L;
+    }
     return d;
 }
 
@@ -193,6 +206,7 @@ __global__ void k_dem_substep(Dev s, const double* __restrict__ Xa, const double
         return;
     }
     const double ri = s.R[p], mi = s.M[p], Ii = s.I[p];
+    const float4 xri = s.Xr[p];   // position at the start of the LBM step (FP32)
     double F[3] = {s.Fa[3 * p] + mi * s.gxd, s.Fa[3 * p + 1] + mi * s.gyd, s.Fa[3 * p + 2] + mi * s.gzd};
     double T[3] = {s.Ta[3 * p], s.Ta[3 * p + 1], s.Ta[3 * p + 2]};
     unsigned seen = 0;
@@ -209,6 +223,13 @@ __global__ void k_dem_substep(Dev s, const double* __restrict__ Xa, const double
                 for (int k = b; k < e; ++k) {
                     int j = s.g_list[k];
                     if (j == p) continue;
+                    // FP32 reject with half a cell of slack for the motion
+                    // within one LBM step
+                    const float4 xrj = s.Xr[j];
+                    const float ex = wrapf(xrj.x - xri.x, s.nx, s.per_x), ey = wrapf(xrj.y - xri.y, s.ny, s.per_y),
+                                ez = wrapf(xrj.z - xri.z, s.nz, s.per_z);
+                    const float reach = fabsf(xri.w) + fabsf(xrj.w) + 0.5f;
+                    if (ex * ex + ey * ey + ez * ez > reach * reach) continue;
                     double d[3] = {wrapd(Xa[3 * j] - X[0], s.nx, s.per_x), wrapd(Xa[3 * j + 1] - X[1], s.ny, s.per_y),
                                    wrapd(Xa[3 * j + 2] - X[2], s.nz, s.per_z)};
                     double dist2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
@@ -273,10 +294,25 @@ __global__ void k_dem_substep(Dev s, const double* __restrict__ Xa, const double
         Ub[3 * p + a] = U[a];
         Wb[3 * p + a] = W[a];
     }
-    if (last) {
-        atomicMax(s.zmax_cell, (int)ceil(X[2] + ri) + 2);
-        s.Xr[p] = make_float4((float)X[0], (float)X[1], (float)X[2], (float)ri);
-    }
+    if (last) atomicMax(s.zmax_cell, (int)ceil(X[2] + ri) + 2);
+}
+
+// FP32 copies of the particle state used by the lattice kernels
+__global__ void k_particle_copies(Dev s) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= s.np) return;
+    const double X = s.X[3 * p], Y = s.X[3 * p + 1], Z = s.X[3 * p + 2];
+    const double r = s.R[p];
+    s.Xr[p] = make_float4((float)X, (float)Y, (float)Z, s.fixed[p] ? -(float)r : (float)r);
+    const double fx = floor(X), fy = floor(Y), fz = floor(Z);
+    s.Xi[p] = make_int4((int)fx, (int)fy, (int)fz, 0);
+    s.Xfr[p] = make_float4((float)(X - fx), (float)(Y - fy), (float)(Z - fz), 0.f);
+    s.Uf[p] = make_float4((float)s.U[3 * p], (float)s.U[3 * p + 1], (float)s.U[3 * p + 2], 0.f);
+    s.Wf[p] = make_float4((float)s.W[3 * p], (float)s.W[3 * p + 1], (float)s.W[3 * p + 2], 0.f);
+}
+
+void launch_particle_copies(const Dev& s, cudaStream_t st) {
+    if (s.np > 0) k_particle_copies<<<blocks_for(s.np, 128), 128, 0, st>>>(s);
 }
 
 // ------------------------------------------------------------ particle map
@@ -300,8 +336,10 @@ __device__ __forceinline__ double image_centre(int k, double X, int L, int perio
 }
 
 // best covering particle (lowest metric, then lowest index) among the
-// particles of the selected kind near cell (x, y, z)
-__device__ void best_cover(const Dev& s, int x, int y, int z, int want_fixed, double& best, int& bestp) {
+// particles of the selected kind near cell (x, y, z); every covering mobile
+// particle of a cell covered more than once is flagged as sharing cells
+__device__ void best_cover(const Dev& s, int x, int y, int z, int want_fixed, double& best, int& bestp,
+                           int* ncover = nullptr, int* cov = nullptr) {
     const double rm = s.r_max;
     const double xc = x + 0.5, yc = y + 0.5, zc = z + 0.5;
     GRange ra = grange((int)floor((xc - rm) / s.ghx), (int)floor((xc + rm) / s.ghx), s.gnx, s.per_x);
@@ -329,6 +367,10 @@ __device__ void best_cover(const Dev& s, int x, int y, int z, int want_fixed, do
                     double m = map_metric(image_centre(x, Xp[0], s.nx, s.per_x), image_centre(y, Xp[1], s.ny, s.per_y),
                                           image_centre(z, Xp[2], s.nz, s.per_z), Xp, r);
                     if (m > 0.0) continue;
+                    if (ncover) {
+                        if (*ncover < 4) cov[*ncover] = p;
+                        (*ncover)++;
+                    }
                     if (m < best || (m == best && p < bestp)) {
                         best = m;
                         bestp = p;
@@ -349,17 +391,18 @@ __global__ void k_fixed_map(Dev s) {
     s.fixowner[c] = bestp;
 }
 
-// new owner of each cell; at set-up covered cells simply become solid,
-// during a run every change is listed for the transition pass
-__global__ void k_remap(Dev s, int init_mode) {
-    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= s.n) return;
+// new owner of a cell; at set-up covered cells simply become solid, during a
+// run every change is listed for the transition pass
+__device__ void remap_cell(const Dev& s, long long c, int init_mode) {
     int x, y, z;
     coords(s, c, x, y, z);
-    if (z > *s.zmax_cell) return;
     double best = reinterpret_cast<const double*>(s.fixkey)[c];
     int bestp = s.fixowner[c];
-    best_cover(s, x, y, z, 0, best, bestp);
+    int ncover = bestp >= 0 ? 1 : 0;
+    int cov[4];
+    best_cover(s, x, y, z, 0, best, bestp, &ncover, cov);
+    if (ncover > 1)
+        for (int k = 0; k < min(ncover, 4); ++k) s.shared[cov[k]] = 1;
     const uint8_t t0 = s.flags[c] & TYPE_MASK;
     if (init_mode) {
         if (bestp >= 0) {
@@ -379,6 +422,117 @@ __global__ void k_remap(Dev s, int init_mode) {
         } else {
             set_error(s, ERR_CAPACITY);
         }
+    }
+}
+
+__global__ void k_remap_all(Dev s, int init_mode) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= s.n) return;
+    int x, y, z;
+    coords(s, c, x, y, z);
+    if (z > *s.zmax_cell) return;
+    remap_cell(s, c, init_mode);
+}
+
+// A mobile particle needs re-mapping when it moved at least its margin (the
+// distance from its surface to the nearest cell centre at the last map) or
+// when it shares a cell with another particle (ownership by metric).
+__global__ void k_active(Dev s) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= s.np || s.fixed[p]) return;
+    const double dx = s.X[3 * p] - s.Xm[3 * p], dy = s.X[3 * p + 1] - s.Xm[3 * p + 1],
+                 dz = s.X[3 * p + 2] - s.Xm[3 * p + 2];
+    const double d = sqrt(dx * dx + dy * dy + dz * dz);
+    if (s.shared[p] || !(d < (double)s.margin[p])) {
+        s.shared[p] = 0;
+        int k = atomicAdd(s.act_count, 1);
+        s.act[k] = p;
+    }
+}
+
+__device__ __forceinline__ void bbox_axis(double a, double b, double r, int L, int periodic, int& lo, int& hi) {
+    double mn = a < b ? a : b, mx = a < b ? b : a;
+    lo = (int)floor(mn - r - 0.5) - 1;
+    hi = (int)ceil(mx + r - 0.5) + 1;
+    if (!periodic) {
+        lo = lo < 0 ? 0 : lo;
+        hi = hi > L - 1 ? L - 1 : hi;
+    } else if (hi - lo + 1 > L) {
+        lo = 0;
+        hi = L - 1;
+    }
+}
+
+// cells of the old and the new bounding box of every active particle join
+// the dirty list (each once)
+__global__ void k_dirty(Dev s) {
+    if ((int)blockIdx.x >= *s.act_count) return;
+    const int p = s.act[blockIdx.x];
+    const double r = s.R[p];
+    int lo[3], hi[3];
+    bbox_axis(s.Xm[3 * p], s.X[3 * p], r, s.nx, s.per_x, lo[0], hi[0]);
+    bbox_axis(s.Xm[3 * p + 1], s.X[3 * p + 1], r, s.ny, s.per_y, lo[1], hi[1]);
+    bbox_axis(s.Xm[3 * p + 2], s.X[3 * p + 2], r, s.nz, s.per_z, lo[2], hi[2]);
+    const int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
+    const int tot = ex * ey * ez;
+    for (int k = threadIdx.x; k < tot; k += blockDim.x) {
+        int a = lo[0] + k % ex, b = lo[1] + (k / ex) % ey, c = lo[2] + k / (ex * ey);
+        a = (a % s.nx + s.nx) % s.nx;
+        b = (b % s.ny + s.ny) % s.ny;
+        c = (c % s.nz + s.nz) % s.nz;
+        const long long cell = a + (long long)s.nx * (b + (long long)s.ny * c);
+        const uint8_t old = flag_or(s.dirty, cell, 1);
+        if (!(old & 1)) {
+            int j = atomicAdd(s.dl_count, 1);
+            if (j < s.dl_cap) s.dl[j] = (int)cell;
+            else set_error(s, ERR_CAPACITY);
+        }
+    }
+}
+
+__global__ void k_remap_list(Dev s) {
+    const int cnt = min(*s.dl_count, s.dl_cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+        const int c = s.dl[i];
+        s.dirty[c] = 0;
+        remap_cell(s, c, 0);
+    }
+}
+
+// new margin of each active particle: min over the cells of its box of
+// | |x_c - X| - r |, shrunk by a safety factor for the FP32 evaluation
+__global__ void k_margin(Dev s) {
+    if ((int)blockIdx.x >= *s.act_count) return;
+    const int p = s.act[blockIdx.x];
+    const double r = s.R[p];
+    const double X0 = s.X[3 * p], X1 = s.X[3 * p + 1], X2 = s.X[3 * p + 2];
+    int lo[3], hi[3];
+    bbox_axis(X0, X0, r, s.nx, s.per_x, lo[0], hi[0]);
+    bbox_axis(X1, X1, r, s.ny, s.per_y, lo[1], hi[1]);
+    bbox_axis(X2, X2, r, s.nz, s.per_z, lo[2], hi[2]);
+    lo[0] -= 1; hi[0] += 1; lo[1] -= 1; hi[1] += 1; lo[2] -= 1; hi[2] += 1;
+    const int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
+    const int tot = ex * ey * ez;
+    float m = 1e30f;
+    for (int k = threadIdx.x; k < tot; k += blockDim.x) {
+        const float a = (float)((lo[0] + k % ex) + 0.5 - X0);
+        const float b = (float)((lo[1] + (k / ex) % ey) + 0.5 - X1);
+        const float c = (float)((lo[2] + k / (ex * ey)) + 0.5 - X2);
+        const float d = fabsf(sqrtf(a * a + b * b + c * c) - (float)r);
+        m = fminf(m, d);
+    }
+    __shared__ float red[256];
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] = fminf(red[threadIdx.x], red[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        s.margin[p] = 0.5f * red[0] - 1e-4f;
+        s.Xm[3 * p] = X0;
+        s.Xm[3 * p + 1] = X1;
+        s.Xm[3 * p + 2] = X2;
     }
 }
 
@@ -528,13 +682,19 @@ int launch_particles_step(const Dev& s, int have_prev, int last_parity, cudaStre
         k_copy3<<<blocks_for(n3, 256), 256, 0, st>>>(s.W2, s.W, n3);
         launches += 3;
     }
-    launches += launch_grid_build(s, st);
+    k_particle_copies<<<blocks_for(s.np, 128), 128, 0, st>>>(s);
+    launches += 1 + launch_grid_build(s, st);
     cudaMemsetAsync(s.tl_count, 0, sizeof(int), st);
-    k_remap<<<blocks_for(s.n, 256), 256, 0, st>>>(s, 0);
+    cudaMemsetAsync(s.act_count, 0, sizeof(int), st);
+    cudaMemsetAsync(s.dl_count, 0, sizeof(int), st);
+    k_active<<<blocks_for(s.np, 128), 128, 0, st>>>(s);
+    k_dirty<<<s.np, 256, 0, st>>>(s);
+    k_remap_list<<<152 * 8, 128, 0, st>>>(s);
+    k_margin<<<s.np, 256, 0, st>>>(s);
     k_transitions<<<152 * 4, 128, 0, st>>>(s, last_parity);
     k_apply_transitions<<<152 * 4, 256, 0, st>>>(s);
     k_repair<<<152 * 4, 256, 0, st>>>(s);
-    return launches + 4;
+    return launches + 7;
 }
 
 __global__ void k_init_particles(Dev s, int first, int count, double rho_p) {
@@ -550,16 +710,18 @@ __global__ void k_init_particles(Dev s, int first, int count, double rho_p) {
         s.Fa[3 * p + a] = s.Ta[3 * p + a] = 0.0;
     }
     for (int j = 0; j < HIST_SLOTS; ++j) s.hist_partner[(long long)p * HIST_SLOTS + j] = HIST_EMPTY;
+    s.margin[p] = 0.f;
+    s.shared[p] = 1;
+    for (int a = 0; a < 3; ++a) s.Xm[3 * p + a] = s.X[3 * p + a];
     atomicMax(s.zmax_cell, (int)ceil(s.X[3 * p + 2] + r) + 2);
-    s.Xr[p] = make_float4((float)s.X[3 * p], (float)s.X[3 * p + 1], (float)s.X[3 * p + 2],
-                          s.fixed[p] ? -(float)r : (float)r);
 }
 
 void launch_particles_add(const Dev& s, int first, int count, cudaStream_t st) {
     k_init_particles<<<blocks_for(count, 128), 128, 0, st>>>(s, first, count, s.rho_p);
+    k_particle_copies<<<blocks_for(s.np, 128), 128, 0, st>>>(s);
     launch_grid_build(s, st);
     k_fixed_map<<<blocks_for(s.n, 256), 256, 0, st>>>(s);
-    k_remap<<<blocks_for(s.n, 256), 256, 0, st>>>(s, 1);
+    k_remap_all<<<blocks_for(s.n, 256), 256, 0, st>>>(s, 1);
 }
 
 }  // namespace fsl

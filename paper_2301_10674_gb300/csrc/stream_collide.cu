@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(256) k_bulk(Dev s) {
 
 // Warp segmented reduction of per-lane (key, F, T) for runs of equal keys,
 // then one FP64 atomic per run and component.
-__device__ __forceinline__ void flush_mem(const Dev& s, int key, float (&F)[3], float (&T)[3]) {
+__device__ __forceinline__ void flush_mem(const Dev& s, int key, const float (&F)[3], const float (&T)[3]) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     if (!__any_sync(full, key >= 0)) return;
@@ -88,6 +88,40 @@ __device__ __forceinline__ void flush_mem(const Dev& s, int key, float (&F)[3], 
     }
 }
 
+// Per-thread momentum-exchange accumulator with two owner slots; a third
+// distinct owner goes straight to the FP64 accumulators.
+struct MemAcc {
+    int k0, k1;
+    float F0[3], T0[3], F1[3], T1[3];
+    __device__ __forceinline__ void init() {
+        k0 = k1 = -1;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) F0[a] = T0[a] = F1[a] = T1[a] = 0.f;
+    }
+    __device__ __forceinline__ void add(const Dev& s, int p, float fx, float fy, float fz, float tx, float ty,
+                                        float tz) {
+        if (k0 < 0 || k0 == p) {
+            k0 = p;
+            F0[0] += fx; F0[1] += fy; F0[2] += fz; T0[0] += tx; T0[1] += ty; T0[2] += tz;
+        } else if (k1 < 0 || k1 == p) {
+            k1 = p;
+            F1[0] += fx; F1[1] += fy; F1[2] += fz; T1[0] += tx; T1[1] += ty; T1[2] += tz;
+        } else {
+            atomicAdd(&s.Fh[3 * p + 0], (double)fx);
+            atomicAdd(&s.Fh[3 * p + 1], (double)fy);
+            atomicAdd(&s.Fh[3 * p + 2], (double)fz);
+            atomicAdd(&s.Th[3 * p + 0], (double)tx);
+            atomicAdd(&s.Th[3 * p + 1], (double)ty);
+            atomicAdd(&s.Th[3 * p + 2], (double)tz);
+        }
+    }
+    // all lanes of the warp must call this
+    __device__ __forceinline__ void flush(const Dev& s) {
+        flush_mem(s, k0, F0, T0);
+        flush_mem(s, k1, F1, T1);
+    }
+};
+
 __device__ __forceinline__ float min_image(float d, int L, int periodic) {
     if (periodic) d -= (float)L * rintf(d / (float)L);
     return d;
@@ -96,44 +130,36 @@ __device__ __forceinline__ float min_image(float d, int L, int periodic) {
 // particle surface velocity at a link midpoint and the link force
 // (Section 2.2): f_q = f*_opp + 6 w_q c_q.u_b, force on the particle
 // -c_q (f*_opp + f_q) - u_b (f*_opp - f_q) with zero-centred PDFs; torque
-// about the centre. Accumulated per owner; a change of owner flushes.
-__device__ __forceinline__ float particle_link(const Dev& s, int q, int x, int y, int z, int p, float fo, int& key,
-                                               float (&F)[3], float (&T)[3]) {
-    const double* Xp = s.X + 3 * p;
-    float dx = (float)((double)(x + 0.5f - 0.5f * cx(q)) - Xp[0]);
-    float dy = (float)((double)(y + 0.5f - 0.5f * cy(q)) - Xp[1]);
-    float dz = (float)((double)(z + 0.5f - 0.5f * cz(q)) - Xp[2]);
-    dx = min_image(dx, s.nx, s.per_x);
-    dy = min_image(dy, s.ny, s.per_y);
-    dz = min_image(dz, s.nz, s.per_z);
-    const double* Up = s.U + 3 * p;
-    const double* Wp = s.W + 3 * p;
-    const float wx = (float)Wp[0], wy = (float)Wp[1], wz = (float)Wp[2];
-    const float ubx = (float)Up[0] + (wy * dz - wz * dy);
-    const float uby = (float)Up[1] + (wz * dx - wx * dz);
-    const float ubz = (float)Up[2] + (wx * dy - wy * dx);
+// about the centre. The offset from the centre is formed from the integer
+// part and the FP32 fraction of the centre, so it is exact to FP32 rounding
+// at any lattice size.
+__device__ __forceinline__ int wrap_int(int d, int L, int periodic) {
+    if (periodic) {
+        if (d > L / 2) d -= L;
+        else if (d < -L / 2) d += L;
+    }
+    return d;
+}
+
+__device__ __forceinline__ float particle_link(const Dev& s, int q, int x, int y, int z, int p, float fo,
+                                               MemAcc& acc) {
+    const int4 xi = s.Xi[p];
+    const float4 xf = s.Xfr[p];
+    const float dx = (float)wrap_int(x - xi.x, s.nx, s.per_x) + (0.5f - 0.5f * cx(q)) - xf.x;
+    const float dy = (float)wrap_int(y - xi.y, s.ny, s.per_y) + (0.5f - 0.5f * cy(q)) - xf.y;
+    const float dz = (float)wrap_int(z - xi.z, s.nz, s.per_z) + (0.5f - 0.5f * cz(q)) - xf.z;
+    const float4 Up = s.Uf[p];
+    const float4 Wp = s.Wf[p];
+    const float ubx = Up.x + (Wp.y * dz - Wp.z * dy);
+    const float uby = Up.y + (Wp.z * dx - Wp.x * dz);
+    const float ubz = Up.z + (Wp.x * dy - Wp.y * dx);
     const float cu = cx(q) * ubx + cy(q) * uby + cz(q) * ubz;
     const float val = fo + 6.f * wq(q) * cu;
     const float sum = fo + val, dif = fo - val;
     const float Fx = -cx(q) * sum - ubx * dif;
     const float Fy = -cy(q) * sum - uby * dif;
     const float Fz = -cz(q) * sum - ubz * dif;
-    if (key != p) {
-        if (key >= 0) {
-            atomicAdd(&s.Fh[3 * key + 0], (double)F[0]);
-            atomicAdd(&s.Fh[3 * key + 1], (double)F[1]);
-            atomicAdd(&s.Fh[3 * key + 2], (double)F[2]);
-            atomicAdd(&s.Th[3 * key + 0], (double)T[0]);
-            atomicAdd(&s.Th[3 * key + 1], (double)T[1]);
-            atomicAdd(&s.Th[3 * key + 2], (double)T[2]);
-        }
-        key = p;
-        F[0] = F[1] = F[2] = T[0] = T[1] = T[2] = 0.f;
-    }
-    F[0] += Fx; F[1] += Fy; F[2] += Fz;
-    T[0] += dy * Fz - dz * Fy;
-    T[1] += dz * Fx - dx * Fz;
-    T[2] += dx * Fy - dy * Fx;
+    acc.add(s, p, Fx, Fy, Fz, dy * Fz - dz * Fy, dz * Fx - dx * Fz, dx * Fy - dy * Fx);
     return val;
 }
 
@@ -146,8 +172,8 @@ __global__ void __launch_bounds__(256) k_boundary(Dev s) {
     const bool inrange = cell < s.n;
     const uint8_t fl = inrange ? s.flags[cell] : (uint8_t)0;
     const bool work = inrange && (fl & (TYPE_MASK | F_BULK)) == T_LIQ;
-    int key = -1;
-    float F[3] = {0.f, 0.f, 0.f}, T[3] = {0.f, 0.f, 0.f};
+    MemAcc acc;
+    acc.init();
     if (work) {
         int x, y, z;
         coords(s, cell, x, y, z);
@@ -190,7 +216,7 @@ __global__ void __launch_bounds__(256) k_boundary(Dev s) {
                 const int sx = xs[1 - cx(q)], sy = ys[1 - cy(q)], sz = zs[1 - cz(q)];
                 const int p = s.owner[sx + (long long)s.nx * (sy + (long long)s.ny * sz)];
                 if (p < 0 || p >= s.np) { set_error(s, ERR_INVARIANT); continue; }
-                v[q] = particle_link(s, q, x, y, z, p, v[q], key, F, T);
+                v[q] = particle_link(s, q, x, y, z, p, v[q], acc);
             }
         }
         float rho, ux, uy, uz;
@@ -209,7 +235,7 @@ __global__ void __launch_bounds__(256) k_boundary(Dev s) {
             }
         }
     }
-    flush_mem(s, key, F, T);
+    acc.flush(s);
 }
 
 // Interface cells, from the interface list: gas-pressure reconstruction
@@ -222,8 +248,8 @@ __global__ void __launch_bounds__(128) k_interface(Dev s) {
     for (int base = blockIdx.x * blockDim.x; base < count; base += stride) {
         const int i = base + threadIdx.x;
         const bool work = i < count;
-        int key = -1;
-        float F[3] = {0.f, 0.f, 0.f}, T[3] = {0.f, 0.f, 0.f};
+        MemAcc acc;
+        acc.init();
         if (work) {
             const long long cell = s.wl[i];
             int x, y, z;
@@ -290,7 +316,7 @@ __global__ void __launch_bounds__(128) k_interface(Dev s) {
                 if ((solidm >> q) & 1u) {
                     const int p = s.owner[src];
                     if (p < 0 || p >= s.np) { set_error(s, ERR_INVARIANT); v[q] = fob; continue; }
-                    v[q] = particle_link(s, q, x, y, z, p, fob, key, F, T);
+                    v[q] = particle_link(s, q, x, y, z, p, fob, acc);
                     continue;
                 }
                 const bool gas = (gasm >> q) & 1u;
@@ -329,7 +355,7 @@ __global__ void __launch_bounds__(128) k_interface(Dev s) {
             s.mass[cell] = mx + dm;
             s.ru[cell] = make_float4(rho, ux, uy, uz);
         }
-        flush_mem(s, key, F, T);
+        acc.flush(s);
     }
 }
 
