@@ -247,8 +247,7 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     d.shared = dalloc<int>(s, pc, ok);
     d.act = dalloc<int>(s, pc, ok);
     d.dirty = dalloc<uint8_t>(s, n + 4, ok);
-    long long dcap = n / 4 + 4096;
-    if (dcap > n) dcap = n;
+    const long long dcap = n;   // the first re-map may touch every cell of the bed
     d.dl_cap = (int)dcap;
     d.dl = dalloc<int>(s, dcap, ok);
     d.g_list = dalloc<int>(s, pc, ok);
