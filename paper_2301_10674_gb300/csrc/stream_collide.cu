@@ -19,8 +19,8 @@
 namespace fsl {
 
 template <typename S, int PAR>
-__global__ void __launch_bounds__(256) k_bulk(Dev s) {
-    const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256, 3) k_bulk(Dev s) {
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= s.n) return;
     if (!(s.flags[cell] & F_BULK)) return;
     int x, y, z;
@@ -28,17 +28,19 @@ __global__ void __launch_bounds__(256) k_bulk(Dev s) {
     S* f = static_cast<S*>(s.f);
     const long long n = s.n;
     float v[27];
-    // bulk cells have every neighbour inside the domain
-    int xs[3] = {x == 0 ? s.nx - 1 : x - 1, x, x == s.nx - 1 ? 0 : x + 1};
-    int ys[3] = {y == 0 ? s.ny - 1 : y - 1, y, y == s.ny - 1 ? 0 : y + 1};
-    int zs[3] = {z == 0 ? s.nz - 1 : z - 1, z, z == s.nz - 1 ? 0 : z + 1};
     if (PAR == 0) {
 #pragma unroll
         for (int q = 0; q < 27; ++q) v[q] = Store<S>::ld(f + (long long)q * n + cell);
     } else {
+        // bulk cells have every neighbour inside the domain; only periodic
+        // axes wrap. Offsets of the x, y, z neighbours (-1, 0, +1):
+        const int sxy = s.nx * s.ny;
+        const int ox[3] = {x == 0 ? s.nx - 1 : -1, 0, x == s.nx - 1 ? 1 - s.nx : 1};
+        const int oy[3] = {y == 0 ? (s.ny - 1) * s.nx : -s.nx, 0, y == s.ny - 1 ? (1 - s.ny) * s.nx : s.nx};
+        const int oz[3] = {z == 0 ? (s.nz - 1) * sxy : -sxy, 0, z == s.nz - 1 ? (1 - s.nz) * sxy : sxy};
 #pragma unroll
         for (int q = 0; q < 27; ++q) {
-            long long src = xs[1 - cx(q)] + (long long)s.nx * (ys[1 - cy(q)] + (long long)s.ny * zs[1 - cz(q)]);
+            const int src = cell + ox[1 - cx(q)] + oy[1 - cy(q)] + oz[1 - cz(q)];
             v[q] = Store<S>::ld(f + (long long)opp(q) * n + src);
         }
     }
@@ -48,9 +50,13 @@ __global__ void __launch_bounds__(256) k_bulk(Dev s) {
 #pragma unroll
         for (int q = 0; q < 27; ++q) Store<S>::st(f + (long long)opp(q) * n + cell, v[q]);
     } else {
+        const int sxy = s.nx * s.ny;
+        const int ox[3] = {x == 0 ? s.nx - 1 : -1, 0, x == s.nx - 1 ? 1 - s.nx : 1};
+        const int oy[3] = {y == 0 ? (s.ny - 1) * s.nx : -s.nx, 0, y == s.ny - 1 ? (1 - s.ny) * s.nx : s.nx};
+        const int oz[3] = {z == 0 ? (s.nz - 1) * sxy : -sxy, 0, z == s.nz - 1 ? (1 - s.nz) * sxy : sxy};
 #pragma unroll
         for (int q = 0; q < 27; ++q) {
-            long long dst = xs[1 + cx(q)] + (long long)s.nx * (ys[1 + cy(q)] + (long long)s.ny * zs[1 + cz(q)]);
+            const int dst = cell + ox[1 + cx(q)] + oy[1 + cy(q)] + oz[1 + cz(q)];
             Store<S>::st(f + (long long)q * n + dst, v[q]);
         }
     }
@@ -168,6 +174,7 @@ __device__ __forceinline__ float particle_link(const Dev& s, int q, int x, int y
 // addresses (no load sits behind a branch), then the particle links.
 template <typename S, int PAR>
 __global__ void __launch_bounds__(256) k_boundary(Dev s) {
+    __shared__ float sv[27][256];
     const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool inrange = cell < s.n;
     const uint8_t fl = inrange ? s.flags[cell] : (uint8_t)0;
@@ -210,14 +217,21 @@ __global__ void __launch_bounds__(256) k_boundary(Dev s) {
         // bounced back and the event counted
         if (gasm) atomicAdd(s.viol, 1ull);
         if (solidm) {
+            // particle links: one copy of the link code in a loop over the
+            // solid directions, the cell's values staged in shared memory
 #pragma unroll
-            for (int q = 0; q < 27; ++q) {
-                if (!((solidm >> q) & 1u)) continue;
+            for (int q = 0; q < 27; ++q) sv[q][threadIdx.x] = v[q];
+            unsigned m = solidm;
+            while (m) {
+                const int q = __ffs(m) - 1;
+                m &= m - 1;
                 const int sx = xs[1 - cx(q)], sy = ys[1 - cy(q)], sz = zs[1 - cz(q)];
                 const int p = s.owner[sx + (long long)s.nx * (sy + (long long)s.ny * sz)];
                 if (p < 0 || p >= s.np) { set_error(s, ERR_INVARIANT); continue; }
-                v[q] = particle_link(s, q, x, y, z, p, v[q], acc);
+                sv[q][threadIdx.x] = particle_link(s, q, x, y, z, p, sv[q][threadIdx.x], acc);
             }
+#pragma unroll
+            for (int q = 0; q < 27; ++q) v[q] = sv[q][threadIdx.x];
         }
         float rho, ux, uy, uz;
         collide(v, s.omega, s.gx, s.gy, s.gz, rho, ux, uy, uz);
