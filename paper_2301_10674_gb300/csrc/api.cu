@@ -240,6 +240,8 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     d.Fp = dalloc<double>(s, 3 * pc, ok); d.Tp = dalloc<double>(s, 3 * pc, ok);
     d.Fa = dalloc<double>(s, 3 * pc, ok); d.Ta = dalloc<double>(s, 3 * pc, ok);
     d.hist_partner = dalloc<int>(s, pc * HIST_SLOTS, ok);
+    d.nb = dalloc<int>(s, pc * NB_SLOTS, ok);
+    d.nb_count = dalloc<int>(s, pc, ok);
     d.hist_xi = dalloc<double>(s, pc * HIST_SLOTS * 3, ok);
     d.g_of = dalloc<int>(s, pc, ok);
     d.Xm = dalloc<double>(s, 3 * pc, ok);

@@ -46,6 +46,7 @@ enum : uint8_t { CV_TO_LIQ = 1, CV_TO_GAS = 2, CV_EVEN = 4 };
 enum : int { ERR_CAPACITY = 1, ERR_NAN = 2, ERR_INVARIANT = 4, ERR_HISTORY = 8, ERR_DISPLACEMENT = 16 };
 
 constexpr int HIST_SLOTS = 16;   // tangential-spring history slots per particle
+constexpr int NB_SLOTS = 32;     // DEM neighbour-list slots per particle
 
 struct Dev {
     // lattice
@@ -92,6 +93,7 @@ struct Dev {
     double* Fh; double* Th;                     // momentum exchange of this step
     double* Fp; double* Tp;                     // previous step
     double* Fa; double* Ta;                     // two-step average
+    int* nb; int* nb_count;                     // DEM neighbour list [np_cap][NB_SLOTS]
     int* hist_partner;                          // [np_cap][HIST_SLOTS]
     double* hist_xi;                            // [np_cap][HIST_SLOTS][3]
     double rho_p, restitution, friction, poisson, collision_time;
@@ -212,15 +214,26 @@ __device__ __forceinline__ float mrest(int i) { return i == 0 ? 1.f : (i == 1 ? 
 // cumulants zero); the body force rho g enters through the half-shifted
 // velocity and the sign flip of the first-order central moments. Returns
 // rho and u (the collision velocity).
+//
+// Only rho, the momentum and the six second-order central moments survive
+// the collision, so they are formed directly from raw sums of the
+// deviations (kappa_ab = Pi_ab - u_a j_b - u_b j_a + rho u_a u_b, diagonal
+// taken relative to its rest value 1/3); the post-collision central moments
+// go back through the per-axis (chimera) transform.
 __device__ __forceinline__ void collide(float (&f)[27], float omega, float gx, float gy, float gz,
                                         float& rho_out, float& ux_out, float& uy_out, float& uz_out) {
     float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+    float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
 #pragma unroll
     for (int q = 0; q < 27; ++q) {
-        drho += f[q];
-        if (cx(q)) jx += cx(q) * f[q];
-        if (cy(q)) jy += cy(q) * f[q];
-        if (cz(q)) jz += cz(q) * f[q];
+        const float v = f[q];
+        drho += v;
+        if (cx(q)) { jx += cx(q) * v; pxx += v; }
+        if (cy(q)) { jy += cy(q) * v; pyy += v; }
+        if (cz(q)) { jz += cz(q) * v; pzz += v; }
+        if (cx(q) && cy(q)) pxy += cx(q) * cy(q) * v;
+        if (cx(q) && cz(q)) pxz += cx(q) * cz(q) * v;
+        if (cy(q) && cz(q)) pyz += cy(q) * cz(q) * v;
     }
     const float rho = 1.f + drho;
     const float inv = 1.f / rho;
@@ -228,32 +241,23 @@ __device__ __forceinline__ void collide(float (&f)[27], float omega, float gx, f
     const float ux = (jx + 0.5f * Fx) * inv;
     const float uy = (jy + 0.5f * Fy) * inv;
     const float uz = (jz + 0.5f * Fz) * inv;
-    // forward: z, then y, then x
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-            fwd_axis(f[a + 3 * b], f[a + 3 * b + 9], f[a + 3 * b + 18], uz, w1(a) * w1(b));
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-            fwd_axis(f[a + 9 * c], f[a + 3 + 9 * c], f[a + 6 + 9 * c], uy, w1(a) * mrest(c));
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int b = 0; b < 3; ++b)
-            fwd_axis(f[3 * b + 9 * c], f[1 + 3 * b + 9 * c], f[2 + 3 * b + 9 * c], ux, mrest(b) * mrest(c));
-    // m[a + 3b + 9c]: central-moment deviation of orders (a, b, c)
+    // central second-order moments (deviations of the diagonal from 1/3)
+    const float kxx = pxx - 2.f * ux * jx + rho * ux * ux;
+    const float kyy = pyy - 2.f * uy * jy + rho * uy * uy;
+    const float kzz = pzz - 2.f * uz * jz + rho * uz * uz;
+    const float kxy = pxy - ux * jy - uy * jx + rho * ux * uy;
+    const float kxz = pxz - ux * jz - uz * jx + rho * ux * uz;
+    const float kyz = pyz - uy * jz - uz * jy + rho * uy * uz;
+    // m[a + 3b + 9c]: post-collision central-moment deviation of orders (a, b, c)
     const float om1 = 1.f - omega;
-    const float Dxy = om1 * (f[2] - f[6]);
-    const float Dxz = om1 * (f[2] - f[18]);
+    const float Dxy = om1 * (kxx - kyy);
+    const float Dxz = om1 * (kxx - kzz);
     const float k200 = (Dxy + Dxz + drho) * (1.f / 3.f);
     const float k020 = (Dxz - 2.f * Dxy + drho) * (1.f / 3.f);
     const float k002 = (Dxy - 2.f * Dxz + drho) * (1.f / 3.f);
-    const float k110 = om1 * f[4];
-    const float k101 = om1 * f[10];
-    const float k011 = om1 * f[12];
+    const float k110 = om1 * kxy;
+    const float k101 = om1 * kxz;
+    const float k011 = om1 * kyz;
     const float sxx = (k200 - drho * (1.f / 3.f)) * inv;
     const float syy = (k020 - drho * (1.f / 3.f)) * inv;
     const float szz = (k002 - drho * (1.f / 3.f)) * inv;

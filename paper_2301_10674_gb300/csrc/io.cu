@@ -134,23 +134,23 @@ __global__ void k_reduce_cells(Dev s, int last_parity, double* out) {
         const int t = fl & TYPE_MASK;
         float f[27];
         load_fstar(s, c, last_parity, f);
-        double d = 0, j[3] = {0, 0, 0};
-        bool finite = true;
+        // per-cell sums of the deviations in FP32, accumulation in FP64
+        float d = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
         for (int q = 0; q < 27; ++q) {
-            finite &= isfinite(f[q]);
             d += f[q];
-            j[0] += cx(q) * (double)f[q];
-            j[1] += cy(q) * (double)f[q];
-            j[2] += cz(q) * (double)f[q];
+            jx += cx(q) * f[q];
+            jy += cy(q) * f[q];
+            jz += cz(q) * f[q];
         }
-        if (!finite) set_error(s, ERR_NAN);
-        const double rho = 1.0 + d;
-        const double mx = j[0] - 0.5 * rho * s.gxd;   // rho u
+        if (!isfinite(d) || !isfinite(jx) || !isfinite(jy) || !isfinite(jz)) set_error(s, ERR_NAN);
+        const double rho = 1.0 + (double)d;
+        const double mx = (double)jx - 0.5 * rho * s.gxd;   // rho u
         const double phi = t == T_LIQ ? 1.0 : (double)s.phi[c];
         acc[0] += t == T_LIQ ? rho : (double)s.mass[c];
         acc[1] += mx;
-        acc[2] += j[1] - 0.5 * rho * s.gyd;
-        acc[3] += j[2] - 0.5 * rho * s.gzd;
+        acc[2] += (double)jy - 0.5 * rho * s.gyd;
+        acc[3] += (double)jz - 0.5 * rho * s.gzd;
         acc[4] += phi * mx;
         acc[5] += phi * rho;
         if (t == T_IFC && !isfinite(s.mass[c])) set_error(s, ERR_NAN);
@@ -168,14 +168,28 @@ __global__ void k_reduce_cells(Dev s, int last_parity, double* out) {
     }
 }
 
-__global__ void k_reduce_final(Dev s, double* out) {
-    // out[0..5] hold: mass, mom x, y, z, sum phi rho u_x, sum phi rho
+// bedload of Eq. (1): sum u_x,p V_p, one block
+__global__ void k_reduce_particles(Dev s, double* out) {
+    __shared__ double sh[32];
     double qb = 0.0;
-    for (int p = 0; p < s.np; ++p) {
-        double r = s.R[p];
+    for (int p = threadIdx.x; p < s.np; p += blockDim.x) {
+        const double r = s.R[p];
         qb += s.U[3 * p] * (4.0 / 3.0) * 3.14159265358979323846 * r * r * r;
         if (!isfinite(s.X[3 * p]) || !isfinite(s.U[3 * p])) set_error(s, ERR_NAN);
     }
+    qb = warp_sum(qb);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = qb;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        out[6] = t;
+    }
+}
+
+__global__ void k_reduce_final(Dev s, double* out) {
+    // out[0..5] hold: mass, mom x, y, z, sum phi rho u_x, sum phi rho
+    const double qb = out[6];
     double num = out[4], den = out[5];
     out[0] += *s.pool;
     out[4] = den > 0 ? num / den : 0.0;
@@ -188,6 +202,7 @@ __global__ void k_reduce_final(Dev s, double* out) {
 void launch_reduce(const Dev& s, int last_parity, double* out, cudaStream_t st) {
     cudaMemsetAsync(out, 0, 8 * sizeof(double), st);
     k_reduce_cells<<<152 * 8, 256, 0, st>>>(s, last_parity, out);
+    k_reduce_particles<<<1, 1024, 0, st>>>(s, out);
     k_reduce_final<<<1, 1, 0, st>>>(s, out);
 }
 

@@ -193,6 +193,45 @@ __device__ __forceinline__ float wrapf(float d, int L, int periodic) {
     return d;
 }
 
+// Neighbour list of every mobile particle for the sub-steps of one LBM
+// step: particles whose surfaces are within half a cell (the motion within a
+// step is far below that).
+__global__ void k_dem_neighbours(Dev s) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= s.np) return;
+    int cnt = 0;
+    if (!s.fixed[p]) {
+        const float4 xri = s.Xr[p];
+        const int g = s.g_of[p];
+        const int ga = g % s.gnx, gb = (g / s.gnx) % s.gny, gc = g / (s.gnx * s.gny);
+        GRange ra = grange(ga - 1, ga + 1, s.gnx, s.per_x);
+        GRange rb = grange(gb - 1, gb + 1, s.gny, s.per_y);
+        GRange rc = grange(gc - 1, gc + 1, s.gnz, s.per_z);
+        for (int ic = 0; ic < rc.n; ++ic)
+            for (int ib = 0; ib < rb.n; ++ib)
+                for (int ia = 0; ia < ra.n; ++ia) {
+                    const int gg = ra.v[ia] + s.gnx * (rb.v[ib] + s.gny * rc.v[ic]);
+                    const int b = s.g_start[gg], e = b + s.g_count[gg];
+                    for (int k = b; k < e; ++k) {
+                        const int j = s.g_list[k];
+                        if (j == p) continue;
+                        const float4 xrj = s.Xr[j];
+                        const float ex = wrapf(xrj.x - xri.x, s.nx, s.per_x), ey = wrapf(xrj.y - xri.y, s.ny, s.per_y),
+                                    ez = wrapf(xrj.z - xri.z, s.nz, s.per_z);
+                        const float reach = fabsf(xri.w) + fabsf(xrj.w) + 0.5f;
+                        if (ex * ex + ey * ey + ez * ez > reach * reach) continue;
+                        if (cnt < NB_SLOTS) s.nb[(long long)p * NB_SLOTS + cnt] = j;
+                        cnt++;
+                    }
+                }
+        if (cnt > NB_SLOTS) {
+            set_error(s, ERR_HISTORY);
+            cnt = NB_SLOTS;
+        }
+    }
+    s.nb_count[p] = cnt;
+}
+
 __global__ void k_dem_substep(Dev s, const double* __restrict__ Xa, const double* __restrict__ Ua,
                               const double* __restrict__ Wa, double* Xb, double* Ub, double* Wb, double dts,
                               int last) {
@@ -206,55 +245,36 @@ __global__ void k_dem_substep(Dev s, const double* __restrict__ Xa, const double
         return;
     }
     const double ri = s.R[p], mi = s.M[p], Ii = s.I[p];
-    const float4 xri = s.Xr[p];   // position at the start of the LBM step (FP32)
     double F[3] = {s.Fa[3 * p] + mi * s.gxd, s.Fa[3 * p + 1] + mi * s.gyd, s.Fa[3 * p + 2] + mi * s.gzd};
     double T[3] = {s.Ta[3 * p], s.Ta[3 * p + 1], s.Ta[3 * p + 2]};
     unsigned seen = 0;
-    const int g = s.g_of[p];
-    const int ga = g % s.gnx, gb = (g / s.gnx) % s.gny, gc = g / (s.gnx * s.gny);
-    GRange ra = grange(ga - 1, ga + 1, s.gnx, s.per_x);
-    GRange rb = grange(gb - 1, gb + 1, s.gny, s.per_y);
-    GRange rc = grange(gc - 1, gc + 1, s.gnz, s.per_z);
-    for (int ic = 0; ic < rc.n; ++ic)
-        for (int ib = 0; ib < rb.n; ++ib)
-            for (int ia = 0; ia < ra.n; ++ia) {
-                int gg = ra.v[ia] + s.gnx * (rb.v[ib] + s.gny * rc.v[ic]);
-                int b = s.g_start[gg], e = b + s.g_count[gg];
-                for (int k = b; k < e; ++k) {
-                    int j = s.g_list[k];
-                    if (j == p) continue;
-                    // FP32 reject with half a cell of slack for the motion
-                    // within one LBM step
-                    const float4 xrj = s.Xr[j];
-                    const float ex = wrapf(xrj.x - xri.x, s.nx, s.per_x), ey = wrapf(xrj.y - xri.y, s.ny, s.per_y),
-                                ez = wrapf(xrj.z - xri.z, s.nz, s.per_z);
-                    const float reach = fabsf(xri.w) + fabsf(xrj.w) + 0.5f;
-                    if (ex * ex + ey * ey + ez * ez > reach * reach) continue;
-                    double d[3] = {wrapd(Xa[3 * j] - X[0], s.nx, s.per_x), wrapd(Xa[3 * j + 1] - X[1], s.ny, s.per_y),
-                                   wrapd(Xa[3 * j + 2] - X[2], s.nz, s.per_z)};
-                    double dist2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                    double rs = ri + s.R[j];
-                    if (dist2 >= rs * rs) continue;
-                    double dist = sqrt(dist2);
-                    double n[3] = {d[0] / dist, d[1] / dist, d[2] / dist};
-                    double delta = rs - dist;
-                    double wsum[3], wn[3];
-                    for (int a = 0; a < 3; ++a) wsum[a] = ri * W[a] + s.R[j] * Wa[3 * j + a];
-                    cross3(wsum, n, wn);
-                    double vrel[3];
-                    for (int a = 0; a < 3; ++a) vrel[a] = U[a] - Ua[3 * j + a] + wn[a];
-                    double mj = s.M[j];
-                    double meff = mi * mj / (mi + mj);
-                    int slot = hist_slot(s, p, j, seen);
-                    if (slot < 0) continue;
-                    double* xi = s.hist_xi + ((long long)p * HIST_SLOTS + slot) * 3;
-                    double Fc[3], Ft[3];
-                    contact(s, meff, n, delta, vrel, xi, dts, Fc, Ft);
-                    double rn[3] = {ri * n[0], ri * n[1], ri * n[2]}, tq[3];
-                    cross3(rn, Ft, tq);
-                    for (int a = 0; a < 3; ++a) { F[a] += Fc[a]; T[a] += tq[a]; }
-                }
-            }
+    const int nbc = s.nb_count[p];
+    for (int k = 0; k < nbc; ++k) {
+        const int j = s.nb[(long long)p * NB_SLOTS + k];
+        double d[3] = {wrapd(Xa[3 * j] - X[0], s.nx, s.per_x), wrapd(Xa[3 * j + 1] - X[1], s.ny, s.per_y),
+                       wrapd(Xa[3 * j + 2] - X[2], s.nz, s.per_z)};
+        double dist2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        double rs = ri + s.R[j];
+        if (dist2 >= rs * rs) continue;
+        double dist = sqrt(dist2);
+        double n[3] = {d[0] / dist, d[1] / dist, d[2] / dist};
+        double delta = rs - dist;
+        double wsum[3], wn[3];
+        for (int a = 0; a < 3; ++a) wsum[a] = ri * W[a] + s.R[j] * Wa[3 * j + a];
+        cross3(wsum, n, wn);
+        double vrel[3];
+        for (int a = 0; a < 3; ++a) vrel[a] = U[a] - Ua[3 * j + a] + wn[a];
+        double mj = s.M[j];
+        double meff = mi * mj / (mi + mj);
+        int slot = hist_slot(s, p, j, seen);
+        if (slot < 0) continue;
+        double* xi = s.hist_xi + ((long long)p * HIST_SLOTS + slot) * 3;
+        double Fc[3], Ft[3];
+        contact(s, meff, n, delta, vrel, xi, dts, Fc, Ft);
+        double rn[3] = {ri * n[0], ri * n[1], ri * n[2]}, tq[3];
+        cross3(rn, Ft, tq);
+        for (int a = 0; a < 3; ++a) { F[a] += Fc[a]; T[a] += tq[a]; }
+    }
     // walls on non-periodic axes
     const int L[3] = {s.nx, s.ny, s.nz};
     const int per[3] = {s.per_x, s.per_y, s.per_z};
@@ -391,18 +411,76 @@ __global__ void k_fixed_map(Dev s) {
     s.fixowner[c] = bestp;
 }
 
+// Mobile particles covering cell (x, y, z). The inside test is decided in
+// FP32 where |d^2 - r^2| exceeds a bound far above the FP32 rounding of the
+// offsets (the FP64 result has the same sign there) and in FP64 without
+// fused multiply-add otherwise. Returns the number of covering particles
+// (up to 4 are listed).
+__device__ int covering_mobile(const Dev& s, int x, int y, int z, int* cov) {
+    const double rm = s.r_max;
+    const double xc = x + 0.5, yc = y + 0.5, zc = z + 0.5;
+    GRange ra = grange((int)floor((xc - rm) / s.ghx), (int)floor((xc + rm) / s.ghx), s.gnx, s.per_x);
+    GRange rb = grange((int)floor((yc - rm) / s.ghy), (int)floor((yc + rm) / s.ghy), s.gny, s.per_y);
+    GRange rc = grange((int)floor((zc - rm) / s.ghz), (int)floor((zc + rm) / s.ghz), s.gnz, s.per_z);
+    int n = 0;
+    for (int ic = 0; ic < rc.n; ++ic)
+        for (int ib = 0; ib < rb.n; ++ib)
+            for (int ia = 0; ia < ra.n; ++ia) {
+                const int gg = ra.v[ia] + s.gnx * (rb.v[ib] + s.gny * rc.v[ic]);
+                const int b = s.g_start[gg], e = b + s.g_count[gg];
+                for (int k = b; k < e; ++k) {
+                    const int p = s.g_list[k];
+                    const float4 xr = s.Xr[p];
+                    if (xr.w < 0.f) continue;
+                    float fx = (float)xc - xr.x, fy = (float)yc - xr.y, fz = (float)zc - xr.z;
+                    if (s.per_x) fx -= (float)s.nx * rintf(fx / (float)s.nx);
+                    if (s.per_y) fy -= (float)s.ny * rintf(fy / (float)s.ny);
+                    if (s.per_z) fz -= (float)s.nz * rintf(fz / (float)s.nz);
+                    const float m32 = fx * fx + fy * fy + fz * fz - xr.w * xr.w;
+                    const float tol = 1e-3f * (1.f + xr.w * xr.w);
+                    if (m32 > tol) continue;
+                    if (m32 >= -tol) {
+                        const double* Xp = s.X + 3 * p;
+                        const double m = map_metric(image_centre(x, Xp[0], s.nx, s.per_x),
+                                                    image_centre(y, Xp[1], s.ny, s.per_y),
+                                                    image_centre(z, Xp[2], s.nz, s.per_z), Xp, s.R[p]);
+                        if (m > 0.0) continue;
+                    }
+                    if (n < 4) cov[n] = p;
+                    n++;
+                }
+            }
+    return n;
+}
+
 // new owner of a cell; at set-up covered cells simply become solid, during a
 // run every change is listed for the transition pass
 __device__ void remap_cell(const Dev& s, long long c, int init_mode) {
     int x, y, z;
     coords(s, c, x, y, z);
-    double best = reinterpret_cast<const double*>(s.fixkey)[c];
-    int bestp = s.fixowner[c];
-    int ncover = bestp >= 0 ? 1 : 0;
+    const int fo = s.fixowner[c];
     int cov[4];
-    best_cover(s, x, y, z, 0, best, bestp, &ncover, cov);
-    if (ncover > 1)
-        for (int k = 0; k < min(ncover, 4); ++k) s.shared[cov[k]] = 1;
+    const int nm = covering_mobile(s, x, y, z, cov);
+    if (nm > 4) set_error(s, ERR_CAPACITY);
+    int bestp;
+    if (nm + (fo >= 0) <= 1) {
+        bestp = nm ? cov[0] : fo;
+    } else {
+        // several covers: exact metrics decide (lowest, then lowest index)
+        double best = reinterpret_cast<const double*>(s.fixkey)[c];
+        bestp = fo;
+        for (int k = 0; k < min(nm, 4); ++k) {
+            const int p = cov[k];
+            const double* Xp = s.X + 3 * p;
+            const double m = map_metric(image_centre(x, Xp[0], s.nx, s.per_x), image_centre(y, Xp[1], s.ny, s.per_y),
+                                        image_centre(z, Xp[2], s.nz, s.per_z), Xp, s.R[p]);
+            if (m < best || (m == best && p < bestp)) {
+                best = m;
+                bestp = p;
+            }
+            s.shared[p] = 1;
+        }
+    }
     const uint8_t t0 = s.flags[c] & TYPE_MASK;
     if (init_mode) {
         if (bestp >= 0) {
@@ -667,8 +745,9 @@ int launch_particles_step(const Dev& s, int have_prev, int last_parity, cudaStre
     const int n3 = 3 * s.np;
     const int ns = s.dem_substeps;
     k_force_avg<<<blocks_for(n3, 128), 128, 0, st>>>(s, have_prev);
+    k_dem_neighbours<<<blocks_for(s.np, 128), 128, 0, st>>>(s);
     cudaMemsetAsync(s.zmax_cell, 0, sizeof(int), st);
-    launches += 1 + ns;
+    launches += 2 + ns;
     const double dts = 1.0 / ns;
     for (int k = 0; k < ns; ++k) {
         const bool ev = (k % 2) == 0;

@@ -147,18 +147,27 @@ __device__ __forceinline__ int wrap_int(int d, int L, int periodic) {
     return d;
 }
 
-__device__ __forceinline__ float particle_link(const Dev& s, int q, int x, int y, int z, int p, float fo,
-                                               MemAcc& acc) {
-    const int4 xi = s.Xi[p];
-    const float4 xf = s.Xfr[p];
-    const float dx = (float)wrap_int(x - xi.x, s.nx, s.per_x) + (0.5f - 0.5f * cx(q)) - xf.x;
-    const float dy = (float)wrap_int(y - xi.y, s.ny, s.per_y) + (0.5f - 0.5f * cy(q)) - xf.y;
-    const float dz = (float)wrap_int(z - xi.z, s.nz, s.per_z) + (0.5f - 0.5f * cz(q)) - xf.z;
-    const float4 Up = s.Uf[p];
-    const float4 Wp = s.Wf[p];
-    const float ubx = Up.x + (Wp.y * dz - Wp.z * dy);
-    const float uby = Up.y + (Wp.z * dx - Wp.x * dz);
-    const float ubz = Up.z + (Wp.x * dy - Wp.y * dx);
+struct PData {
+    int4 xi;
+    float4 xf, u, w;
+};
+__device__ __forceinline__ PData particle_data(const Dev& s, int p) {
+    PData d;
+    d.xi = s.Xi[p];
+    d.xf = s.Xfr[p];
+    d.u = s.Uf[p];
+    d.w = s.Wf[p];
+    return d;
+}
+
+__device__ __forceinline__ float particle_link(const Dev& s, int q, int x, int y, int z, int p, const PData& P,
+                                               float fo, MemAcc& acc) {
+    const float dx = (float)wrap_int(x - P.xi.x, s.nx, s.per_x) + (0.5f - 0.5f * cx(q)) - P.xf.x;
+    const float dy = (float)wrap_int(y - P.xi.y, s.ny, s.per_y) + (0.5f - 0.5f * cy(q)) - P.xf.y;
+    const float dz = (float)wrap_int(z - P.xi.z, s.nz, s.per_z) + (0.5f - 0.5f * cz(q)) - P.xf.z;
+    const float ubx = P.u.x + (P.w.y * dz - P.w.z * dy);
+    const float uby = P.u.y + (P.w.z * dx - P.w.x * dz);
+    const float ubz = P.u.z + (P.w.x * dy - P.w.y * dx);
     const float cu = cx(q) * ubx + cy(q) * uby + cz(q) * ubz;
     const float val = fo + 6.f * wq(q) * cu;
     const float sum = fo + val, dif = fo - val;
@@ -172,9 +181,12 @@ __device__ __forceinline__ float particle_link(const Dev& s, int q, int x, int y
 // Liquid cells that are not bulk: walls and particle links. All neighbour
 // types are read first, then all 27 PDF loads are issued from computed
 // addresses (no load sits behind a branch), then the particle links.
+constexpr int BOUNDARY_THREADS = 128;
+
 template <typename S, int PAR>
-__global__ void __launch_bounds__(256) k_boundary(Dev s) {
-    __shared__ float sv[27][256];
+__global__ void __launch_bounds__(BOUNDARY_THREADS) k_boundary(Dev s) {
+    __shared__ float sv[27][BOUNDARY_THREADS];
+    __shared__ int so[27][BOUNDARY_THREADS];
     const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool inrange = cell < s.n;
     const uint8_t fl = inrange ? s.flags[cell] : (uint8_t)0;
@@ -217,18 +229,31 @@ __global__ void __launch_bounds__(256) k_boundary(Dev s) {
         // bounced back and the event counted
         if (gasm) atomicAdd(s.viol, 1ull);
         if (solidm) {
-            // particle links: one copy of the link code in a loop over the
-            // solid directions, the cell's values staged in shared memory
+            // particle links: the owners of all solid directions are loaded
+            // together, the cell's values staged in shared memory, and one
+            // copy of the link code runs over the solid directions with the
+            // particle data cached per owner
 #pragma unroll
-            for (int q = 0; q < 27; ++q) sv[q][threadIdx.x] = v[q];
+            for (int q = 0; q < 27; ++q) {
+                sv[q][threadIdx.x] = v[q];
+                if ((solidm >> q) & 1u) {
+                    const int sx = xs[1 - cx(q)], sy = ys[1 - cy(q)], sz = zs[1 - cz(q)];
+                    so[q][threadIdx.x] = s.owner[sx + (long long)s.nx * (sy + (long long)s.ny * sz)];
+                }
+            }
+            int pc = -1;
+            PData P;
             unsigned m = solidm;
             while (m) {
                 const int q = __ffs(m) - 1;
                 m &= m - 1;
-                const int sx = xs[1 - cx(q)], sy = ys[1 - cy(q)], sz = zs[1 - cz(q)];
-                const int p = s.owner[sx + (long long)s.nx * (sy + (long long)s.ny * sz)];
+                const int p = so[q][threadIdx.x];
                 if (p < 0 || p >= s.np) { set_error(s, ERR_INVARIANT); continue; }
-                sv[q][threadIdx.x] = particle_link(s, q, x, y, z, p, sv[q][threadIdx.x], acc);
+                if (p != pc) {
+                    P = particle_data(s, p);
+                    pc = p;
+                }
+                sv[q][threadIdx.x] = particle_link(s, q, x, y, z, p, P, sv[q][threadIdx.x], acc);
             }
 #pragma unroll
             for (int q = 0; q < 27; ++q) v[q] = sv[q][threadIdx.x];
@@ -330,7 +355,7 @@ __global__ void __launch_bounds__(128) k_interface(Dev s) {
                 if ((solidm >> q) & 1u) {
                     const int p = s.owner[src];
                     if (p < 0 || p >= s.np) { set_error(s, ERR_INVARIANT); v[q] = fob; continue; }
-                    v[q] = particle_link(s, q, x, y, z, p, fob, acc);
+                    v[q] = particle_link(s, q, x, y, z, p, particle_data(s, p), fob, acc);
                     continue;
                 }
                 const bool gas = (gasm >> q) & 1u;
@@ -380,11 +405,11 @@ static void launch_typed(const Dev& s, int parity, cudaStream_t st) {
     const int ib = 152 * 8;
     if (parity == 0) {
         k_bulk<S, 0><<<bl, th, 0, st>>>(s);
-        k_boundary<S, 0><<<bl, th, 0, st>>>(s);
+        k_boundary<S, 0><<<blocks_for(s.n, BOUNDARY_THREADS), BOUNDARY_THREADS, 0, st>>>(s);
         k_interface<S, 0><<<ib, 128, 0, st>>>(s);
     } else {
         k_bulk<S, 1><<<bl, th, 0, st>>>(s);
-        k_boundary<S, 1><<<bl, th, 0, st>>>(s);
+        k_boundary<S, 1><<<blocks_for(s.n, BOUNDARY_THREADS), BOUNDARY_THREADS, 0, st>>>(s);
         k_interface<S, 1><<<ib, 128, 0, st>>>(s);
     }
 }
