@@ -197,9 +197,10 @@ int fslbm_sync(fslbm* s);
 int64_t fslbm_steps_done(const fslbm* s);
 int64_t fslbm_num_spheres(const fslbm* s);
 
-/* Number of reads where a liquid cell found a gas neighbour (the liquid/gas
- * separation the conversion rules maintain was broken; the PDF was rebuilt
- * from the gas pressure as at an interface cell). Synchronises the stream. */
+/* Checks the liquid/gas separation that the conversion rules maintain: adds
+ * the number of liquid cells that have a gas neighbour now to a running
+ * count and returns that count (0 while the separation holds). Synchronises
+ * the stream. */
 int64_t fslbm_invariant_violations(fslbm* s);
 
 /* Measurement hooks for the benchmark. fslbm_timing(s, 1) clears and starts

@@ -206,6 +206,8 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     if (tcap > n) tcap = n;
     d.tl_cap = (int)tcap;
     d.tl = dalloc<int>(s, tcap, ok);
+    d.sl_cap = (int)n;
+    d.sl = dalloc<int>(s, n, ok);
     d.tl_info = dalloc<int>(s, 2 * tcap, ok);
     int* counts = dalloc<int>(s, 8, ok);
     if (ok) {
@@ -216,6 +218,7 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
         d.err = counts + 4;
         d.act_count = counts + 5;
         d.dl_count = counts + 6;
+        d.sl_count = counts + 7;
     }
     double* dd = dalloc<double>(s, 4, ok);
     if (ok) {
@@ -529,6 +532,7 @@ int64_t fslbm_num_spheres(const fslbm* s) { return s ? s->d.np : -1; }
 int64_t fslbm_invariant_violations(fslbm* s) {
     if (!s) return -1;
     unsigned long long v = 0;
+    launch_check_invariant(s->d, s->st);
     cudaStreamSynchronize(s->st);
     cudaMemcpy(&v, s->d.viol, sizeof(v), cudaMemcpyDeviceToHost);
     return (int64_t)v;

@@ -35,7 +35,6 @@ __host__ __device__ constexpr double wqd(int q) {
 // cell flag byte
 enum : uint8_t {
     T_GAS = 0, T_LIQ = 1, T_IFC = 2, T_SOL = 3, TYPE_MASK = 3,
-    F_BULK = 4,      // liquid, all 26 neighbours inside the domain and liquid
     F_NEW = 8,       // gas cell becoming interface (filling)
     F_EMPTIED = 16,  // liquid cell becoming interface (emptying)
 };
@@ -75,6 +74,7 @@ struct Dev {
     int* wl; int* wl_count; int wl_cap;        // interface cells
     int* nl; int* nl_count; int nl_cap;        // cells becoming interface this step
     int* tl; int* tl_count; int tl_cap;        // particle map transitions
+    int* sl; int* sl_count; int sl_cap;        // solid cells with a fluid neighbour
     int* tl_info;                               // per transition: new owner / new type
     double* pool;
     double* pool_share;
@@ -361,6 +361,7 @@ __device__ __forceinline__ void post_moments(const Dev& s, const float (&f)[27],
 // launchers used inside a time step return the number of kernels enqueued
 int launch_stream_collide(const Dev& s, int parity, cudaStream_t st);
 int launch_classify(const Dev& s, cudaStream_t st);
+void launch_check_invariant(const Dev& s, cudaStream_t st);
 int launch_normals(const Dev& s, float4* out, cudaStream_t st);
 int launch_conversion(const Dev& s, int last_parity, cudaStream_t st);
 int launch_pool_spread(const Dev& s, cudaStream_t st);

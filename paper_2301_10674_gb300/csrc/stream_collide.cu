@@ -11,20 +11,25 @@
 // reconstruction also replaces PDFs pulled from fluid neighbours, whose slots
 // are being rewritten.
 //
-// Three kernels share the work: a lean one for bulk liquid cells (all 26
-// neighbours liquid), one for the other liquid cells (walls, particle
-// links), and one for the interface cells of the interface list.
+// Three kernels share the work: the particle links from the solid side
+// (they place the moving bounce-back values in the pull slots and gather the
+// momentum exchange), one lean pull-collide kernel for every liquid cell,
+// and one for the interface cells of the interface list.
 #include "fslbm_dev.cuh"
 
 namespace fsl {
 
+// All liquid cells. Every PDF is a plain pull: PDFs from fluid cells, and
+// from solid cells the bounce-back values k_solid_links placed in the pull
+// slots. Only wall faces need handling here, and they follow from the
+// coordinates: an even step reads its own slots (a wall-bound PDF came back
+// into (q, x) in the previous odd step), an odd step reads (q, x) across a
+// wall face and writes (opp(q), x) toward one.
 template <typename S, int PAR>
-__global__ void __launch_bounds__(256, 3) k_bulk(Dev s) {
+__global__ void __launch_bounds__(256, 3) k_liquid(Dev s) {
     const int cell = blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= s.n) return;
-    if (!(s.flags[cell] & F_BULK)) return;
-    int x, y, z;
-    coords(s, cell, x, y, z);
+    if ((s.flags[cell] & TYPE_MASK) != T_LIQ) return;
     S* f = static_cast<S*>(s.f);
     const long long n = s.n;
     float v[27];
@@ -32,16 +37,27 @@ __global__ void __launch_bounds__(256, 3) k_bulk(Dev s) {
 #pragma unroll
         for (int q = 0; q < 27; ++q) v[q] = Store<S>::ld(f + (long long)q * n + cell);
     } else {
-        // bulk cells have every neighbour inside the domain; only periodic
-        // axes wrap. Offsets of the x, y, z neighbours (-1, 0, +1):
+        int x, y, z;
+        coords(s, cell, x, y, z);
+        // neighbour offsets along each axis for -1, 0, +1; a wall face is
+        // marked by the bit of that side
         const int sxy = s.nx * s.ny;
-        const int ox[3] = {x == 0 ? s.nx - 1 : -1, 0, x == s.nx - 1 ? 1 - s.nx : 1};
-        const int oy[3] = {y == 0 ? (s.ny - 1) * s.nx : -s.nx, 0, y == s.ny - 1 ? (1 - s.ny) * s.nx : s.nx};
-        const int oz[3] = {z == 0 ? (s.nz - 1) * sxy : -sxy, 0, z == s.nz - 1 ? (1 - s.nz) * sxy : sxy};
+        unsigned wall = 0;
+        int ox[3] = {-1, 0, 1}, oy[3] = {-s.nx, 0, s.nx}, oz[3] = {-sxy, 0, sxy};
+        if (x == 0) { if (s.per_x) ox[0] = s.nx - 1; else wall |= 1u; }
+        if (x == s.nx - 1) { if (s.per_x) ox[2] = 1 - s.nx; else wall |= 2u; }
+        if (y == 0) { if (s.per_y) oy[0] = (s.ny - 1) * s.nx; else wall |= 4u; }
+        if (y == s.ny - 1) { if (s.per_y) oy[2] = (1 - s.ny) * s.nx; else wall |= 8u; }
+        if (z == 0) { if (s.per_z) oz[0] = (s.nz - 1) * sxy; else wall |= 16u; }
+        if (z == s.nz - 1) { if (s.per_z) oz[2] = (1 - s.nz) * sxy; else wall |= 32u; }
 #pragma unroll
         for (int q = 0; q < 27; ++q) {
+            // source x - c_q beyond a wall face?
+            const unsigned need = (cx(q) == 1 ? 1u : 0u) | (cx(q) == -1 ? 2u : 0u) | (cy(q) == 1 ? 4u : 0u) |
+                                  (cy(q) == -1 ? 8u : 0u) | (cz(q) == 1 ? 16u : 0u) | (cz(q) == -1 ? 32u : 0u);
             const int src = cell + ox[1 - cx(q)] + oy[1 - cy(q)] + oz[1 - cz(q)];
-            v[q] = Store<S>::ld(f + (long long)opp(q) * n + src);
+            const long long a = (wall & need) ? (long long)q * n + cell : (long long)opp(q) * n + src;
+            v[q] = Store<S>::ld(f + a);
         }
     }
     float rho, ux, uy, uz;
@@ -50,14 +66,25 @@ __global__ void __launch_bounds__(256, 3) k_bulk(Dev s) {
 #pragma unroll
         for (int q = 0; q < 27; ++q) Store<S>::st(f + (long long)opp(q) * n + cell, v[q]);
     } else {
+        int x, y, z;
+        coords(s, cell, x, y, z);
         const int sxy = s.nx * s.ny;
-        const int ox[3] = {x == 0 ? s.nx - 1 : -1, 0, x == s.nx - 1 ? 1 - s.nx : 1};
-        const int oy[3] = {y == 0 ? (s.ny - 1) * s.nx : -s.nx, 0, y == s.ny - 1 ? (1 - s.ny) * s.nx : s.nx};
-        const int oz[3] = {z == 0 ? (s.nz - 1) * sxy : -sxy, 0, z == s.nz - 1 ? (1 - s.nz) * sxy : sxy};
+        unsigned wall = 0;
+        int ox[3] = {-1, 0, 1}, oy[3] = {-s.nx, 0, s.nx}, oz[3] = {-sxy, 0, sxy};
+        if (x == 0) { if (s.per_x) ox[0] = s.nx - 1; else wall |= 1u; }
+        if (x == s.nx - 1) { if (s.per_x) ox[2] = 1 - s.nx; else wall |= 2u; }
+        if (y == 0) { if (s.per_y) oy[0] = (s.ny - 1) * s.nx; else wall |= 4u; }
+        if (y == s.ny - 1) { if (s.per_y) oy[2] = (1 - s.ny) * s.nx; else wall |= 8u; }
+        if (z == 0) { if (s.per_z) oz[0] = (s.nz - 1) * sxy; else wall |= 16u; }
+        if (z == s.nz - 1) { if (s.per_z) oz[2] = (1 - s.nz) * sxy; else wall |= 32u; }
 #pragma unroll
         for (int q = 0; q < 27; ++q) {
+            // target x + c_q beyond a wall face?
+            const unsigned need = (cx(q) == -1 ? 1u : 0u) | (cx(q) == 1 ? 2u : 0u) | (cy(q) == -1 ? 4u : 0u) |
+                                  (cy(q) == 1 ? 8u : 0u) | (cz(q) == -1 ? 16u : 0u) | (cz(q) == 1 ? 32u : 0u);
             const int dst = cell + ox[1 + cx(q)] + oy[1 + cy(q)] + oz[1 + cz(q)];
-            Store<S>::st(f + (long long)q * n + dst, v[q]);
+            const long long a = (wall & need) ? (long long)opp(q) * n + cell : (long long)q * n + dst;
+            Store<S>::st(f + a, v[q]);
         }
     }
 }
@@ -94,40 +121,6 @@ __device__ __forceinline__ void flush_mem(const Dev& s, int key, const float (&F
     }
 }
 
-// Per-thread momentum-exchange accumulator with two owner slots; a third
-// distinct owner goes straight to the FP64 accumulators.
-struct MemAcc {
-    int k0, k1;
-    float F0[3], T0[3], F1[3], T1[3];
-    __device__ __forceinline__ void init() {
-        k0 = k1 = -1;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) F0[a] = T0[a] = F1[a] = T1[a] = 0.f;
-    }
-    __device__ __forceinline__ void add(const Dev& s, int p, float fx, float fy, float fz, float tx, float ty,
-                                        float tz) {
-        if (k0 < 0 || k0 == p) {
-            k0 = p;
-            F0[0] += fx; F0[1] += fy; F0[2] += fz; T0[0] += tx; T0[1] += ty; T0[2] += tz;
-        } else if (k1 < 0 || k1 == p) {
-            k1 = p;
-            F1[0] += fx; F1[1] += fy; F1[2] += fz; T1[0] += tx; T1[1] += ty; T1[2] += tz;
-        } else {
-            atomicAdd(&s.Fh[3 * p + 0], (double)fx);
-            atomicAdd(&s.Fh[3 * p + 1], (double)fy);
-            atomicAdd(&s.Fh[3 * p + 2], (double)fz);
-            atomicAdd(&s.Th[3 * p + 0], (double)tx);
-            atomicAdd(&s.Th[3 * p + 1], (double)ty);
-            atomicAdd(&s.Th[3 * p + 2], (double)tz);
-        }
-    }
-    // all lanes of the warp must call this
-    __device__ __forceinline__ void flush(const Dev& s) {
-        flush_mem(s, k0, F0, T0);
-        flush_mem(s, k1, F1, T1);
-    }
-};
-
 __device__ __forceinline__ float min_image(float d, int L, int periodic) {
     if (periodic) d -= (float)L * rintf(d / (float)L);
     return d;
@@ -160,121 +153,74 @@ __device__ __forceinline__ PData particle_data(const Dev& s, int p) {
     return d;
 }
 
-__device__ __forceinline__ float particle_link(const Dev& s, int q, int x, int y, int z, int p, const PData& P,
-                                               float fo, MemAcc& acc) {
-    const float dx = (float)wrap_int(x - P.xi.x, s.nx, s.per_x) + (0.5f - 0.5f * cx(q)) - P.xf.x;
-    const float dy = (float)wrap_int(y - P.xi.y, s.ny, s.per_y) + (0.5f - 0.5f * cy(q)) - P.xf.y;
-    const float dz = (float)wrap_int(z - P.xi.z, s.nz, s.per_z) + (0.5f - 0.5f * cz(q)) - P.xf.z;
-    const float ubx = P.u.x + (P.w.y * dz - P.w.z * dy);
-    const float uby = P.u.y + (P.w.z * dx - P.w.x * dz);
-    const float ubz = P.u.z + (P.w.x * dy - P.w.y * dx);
-    const float cu = cx(q) * ubx + cy(q) * uby + cz(q) * ubz;
-    const float val = fo + 6.f * wq(q) * cu;
-    const float sum = fo + val, dif = fo - val;
-    const float Fx = -cx(q) * sum - ubx * dif;
-    const float Fy = -cy(q) * sum - uby * dif;
-    const float Fz = -cz(q) * sum - ubz * dif;
-    acc.add(s, p, Fx, Fy, Fz, dy * Fz - dz * Fy, dz * Fx - dx * Fz, dx * Fy - dy * Fx);
-    return val;
-}
-
-// Liquid cells that are not bulk: walls and particle links. All neighbour
-// types are read first, then all 27 PDF loads are issued from computed
-// addresses (no load sits behind a branch), then the particle links.
-constexpr int BOUNDARY_THREADS = 128;
-
+// Moving bounce-back and momentum exchange (Section 2.2), from the solid
+// side: for every surface solid cell s (owner p) and every fluid neighbour
+// x = s + c_q, the PDF x will pull from s in direction q is
+// f_q(x) = f*_opp(q)(x) + 6 w_q c_q.u_b, u_b the particle velocity at the
+// link midpoint. It is written into the slot x pulls in the coming sweep:
+// (q, x) before an even step, (opp(q), s) before an odd one; f*_opp(q)(x)
+// is read from (opp(q), s) or (q, x) respectively. The force on the
+// particle is -c_q (f*_opp + f_q) - u_b (f*_opp - f_q) with zero-centred
+// PDFs, the torque (x_b - X_p) x F; one owner per thread, so a warp
+// segmented reduction gathers them.
 template <typename S, int PAR>
-__global__ void __launch_bounds__(BOUNDARY_THREADS) k_boundary(Dev s) {
-    __shared__ float sv[27][BOUNDARY_THREADS];
-    __shared__ int so[27][BOUNDARY_THREADS];
-    const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool inrange = cell < s.n;
-    const uint8_t fl = inrange ? s.flags[cell] : (uint8_t)0;
-    const bool work = inrange && (fl & (TYPE_MASK | F_BULK)) == T_LIQ;
-    MemAcc acc;
-    acc.init();
-    if (work) {
-        int x, y, z;
-        coords(s, cell, x, y, z);
-        S* f = static_cast<S*>(s.f);
-        const long long n = s.n;
-        const int xs[3] = {shift(x, -1, s.nx, s.per_x), x, shift(x, 1, s.nx, s.per_x)};
-        const int ys[3] = {shift(y, -1, s.ny, s.per_y), y, shift(y, 1, s.ny, s.per_y)};
-        const int zs[3] = {shift(z, -1, s.nz, s.per_z), z, shift(z, 1, s.nz, s.per_z)};
-        unsigned wallm = 0, solidm = 0, gasm = 0;
-#pragma unroll
-        for (int q = 0; q < 27; ++q) {
-            const int sx = xs[1 - cx(q)], sy = ys[1 - cy(q)], sz = zs[1 - cz(q)];
-            if (sx < 0 || sy < 0 || sz < 0) {
-                wallm |= 1u << q;
+__global__ void __launch_bounds__(256) k_solid_links(Dev s) {
+    const int count = min(*s.sl_count, s.sl_cap);
+    const int stride = gridDim.x * blockDim.x;
+    for (int base = blockIdx.x * blockDim.x; base < count; base += stride) {
+        const int i = base + threadIdx.x;
+        int key = -1;
+        float F[3] = {0.f, 0.f, 0.f}, T[3] = {0.f, 0.f, 0.f};
+        if (i < count) {
+            const long long cell = s.sl[i];
+            int x, y, z;
+            coords(s, cell, x, y, z);
+            const int p = s.owner[cell];
+            if (p < 0 || p >= s.np) {
+                set_error(s, ERR_INVARIANT);
             } else {
-                const int ts = s.flags[sx + (long long)s.nx * (sy + (long long)s.ny * sz)] & TYPE_MASK;
-                if (ts == T_SOL) solidm |= 1u << q;
-                else if (ts == T_GAS) gasm |= 1u << q;
-            }
-        }
-        float v[27];
+                key = p;
+                const PData P = particle_data(s, p);
+                S* f = static_cast<S*>(s.f);
+                const long long n = s.n;
+                const int xs[3] = {shift(x, -1, s.nx, s.per_x), x, shift(x, 1, s.nx, s.per_x)};
+                const int ys[3] = {shift(y, -1, s.ny, s.per_y), y, shift(y, 1, s.ny, s.per_y)};
+                const int zs[3] = {shift(z, -1, s.nz, s.per_z), z, shift(z, 1, s.nz, s.per_z)};
+                // offset of the cell centre from the particle centre
+                const float ddx = (float)wrap_int(x - P.xi.x, s.nx, s.per_x) + 0.5f - P.xf.x;
+                const float ddy = (float)wrap_int(y - P.xi.y, s.ny, s.per_y) + 0.5f - P.xf.y;
+                const float ddz = (float)wrap_int(z - P.xi.z, s.nz, s.per_z) + 0.5f - P.xf.z;
 #pragma unroll
-        for (int q = 0; q < 27; ++q) {
-            const int sx = xs[1 - cx(q)], sy = ys[1 - cy(q)], sz = zs[1 - cz(q)];
-            const bool wall = (wallm >> q) & 1u;
-            const bool fluid_src = !(((wallm | solidm | gasm) >> q) & 1u);
-            const long long src = wall ? cell : sx + (long long)s.nx * (sy + (long long)s.ny * sz);
-            long long a;
-            if (PAR == 0) a = (fluid_src || wall) ? (long long)q * n + cell : (long long)opp(q) * n + src;
-            else a = fluid_src ? (long long)opp(q) * n + src : (long long)q * n + cell;
-            v[q] = Store<S>::ld(f + a);
-        }
-        // a liquid cell must not touch gas; if it does, the gas-side PDF is
-        // bounced back and the event counted
-        if (gasm) atomicAdd(s.viol, 1ull);
-        if (solidm) {
-            // particle links: the owners of all solid directions are loaded
-            // together, the cell's values staged in shared memory, and one
-            // copy of the link code runs over the solid directions with the
-            // particle data cached per owner
-#pragma unroll
-            for (int q = 0; q < 27; ++q) {
-                sv[q][threadIdx.x] = v[q];
-                if ((solidm >> q) & 1u) {
-                    const int sx = xs[1 - cx(q)], sy = ys[1 - cy(q)], sz = zs[1 - cz(q)];
-                    so[q][threadIdx.x] = s.owner[sx + (long long)s.nx * (sy + (long long)s.ny * sz)];
+                for (int q = 0; q < 27; ++q) {
+                    if (q == 13) continue;
+                    const int tx = xs[1 + cx(q)], ty = ys[1 + cy(q)], tz = zs[1 + cz(q)];
+                    if (tx < 0 || ty < 0 || tz < 0) continue;
+                    const long long xn = tx + (long long)s.nx * (ty + (long long)s.ny * tz);
+                    const int tn = s.flags[xn] & TYPE_MASK;
+                    if (tn != T_LIQ && tn != T_IFC) continue;
+                    const float dx = ddx + 0.5f * cx(q), dy = ddy + 0.5f * cy(q), dz = ddz + 0.5f * cz(q);
+                    const float ubx = P.u.x + (P.w.y * dz - P.w.z * dy);
+                    const float uby = P.u.y + (P.w.z * dx - P.w.x * dz);
+                    const float ubz = P.u.z + (P.w.x * dy - P.w.y * dx);
+                    const float cu = cx(q) * ubx + cy(q) * uby + cz(q) * ubz;
+                    const long long src = PAR == 0 ? (long long)opp(q) * n + cell : (long long)q * n + xn;
+                    const long long dst = PAR == 0 ? (long long)q * n + xn : (long long)opp(q) * n + cell;
+                    const float fo = Store<S>::ld(f + src);
+                    const float val = fo + 6.f * wq(q) * cu;
+                    Store<S>::st(f + dst, val);
+                    const float sum = fo + val, dif = fo - val;
+                    const float Fx = -cx(q) * sum - ubx * dif;
+                    const float Fy = -cy(q) * sum - uby * dif;
+                    const float Fz = -cz(q) * sum - ubz * dif;
+                    F[0] += Fx; F[1] += Fy; F[2] += Fz;
+                    T[0] += dy * Fz - dz * Fy;
+                    T[1] += dz * Fx - dx * Fz;
+                    T[2] += dx * Fy - dy * Fx;
                 }
             }
-            int pc = -1;
-            PData P;
-            unsigned m = solidm;
-            while (m) {
-                const int q = __ffs(m) - 1;
-                m &= m - 1;
-                const int p = so[q][threadIdx.x];
-                if (p < 0 || p >= s.np) { set_error(s, ERR_INVARIANT); continue; }
-                if (p != pc) {
-                    P = particle_data(s, p);
-                    pc = p;
-                }
-                sv[q][threadIdx.x] = particle_link(s, q, x, y, z, p, P, sv[q][threadIdx.x], acc);
-            }
-#pragma unroll
-            for (int q = 0; q < 27; ++q) v[q] = sv[q][threadIdx.x];
         }
-        float rho, ux, uy, uz;
-        collide(v, s.omega, s.gx, s.gy, s.gz, rho, ux, uy, uz);
-        if (PAR == 0) {
-#pragma unroll
-            for (int q = 0; q < 27; ++q) Store<S>::st(f + (long long)opp(q) * n + cell, v[q]);
-        } else {
-#pragma unroll
-            for (int q = 0; q < 27; ++q) {
-                const int tx = xs[1 + cx(q)], ty = ys[1 + cy(q)], tz = zs[1 + cz(q)];
-                const bool out = tx < 0 || ty < 0 || tz < 0;
-                const long long a = out ? (long long)opp(q) * n + cell
-                                        : (long long)q * n + tx + (long long)s.nx * (ty + (long long)s.ny * tz);
-                Store<S>::st(f + a, v[q]);
-            }
-        }
+        flush_mem(s, key, F, T);
     }
-    acc.flush(s);
 }
 
 // Interface cells, from the interface list: gas-pressure reconstruction
@@ -287,8 +233,6 @@ __global__ void __launch_bounds__(128) k_interface(Dev s) {
     for (int base = blockIdx.x * blockDim.x; base < count; base += stride) {
         const int i = base + threadIdx.x;
         const bool work = i < count;
-        MemAcc acc;
-        acc.init();
         if (work) {
             const long long cell = s.wl[i];
             int x, y, z;
@@ -322,10 +266,10 @@ __global__ void __launch_bounds__(128) k_interface(Dev s) {
 #pragma unroll
             for (int q = 0; q < 27; ++q) {
                 const int sx = xs[1 - cx(q)], sy = ys[1 - cy(q)], sz = zs[1 - cz(q)];
-                const bool fluid_src = !(((wallm | solidm | gasm) >> q) & 1u);
-                const long long src = fluid_src ? sx + (long long)s.nx * (sy + (long long)s.ny * sz) : cell;
+                const bool pull = !(((wallm | gasm) >> q) & 1u);   // fluid or solid source
+                const long long src = pull ? sx + (long long)s.nx * (sy + (long long)s.ny * sz) : cell;
                 const long long a = PAR == 0 ? (long long)q * n + cell : (long long)opp(q) * n + src;
-                v[q] = fluid_src ? Store<S>::ld(f + a) : 0.f;
+                v[q] = pull ? Store<S>::ld(f + a) : 0.f;
             }
             // own collision velocity from the post-collision PDFs
             float d = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
@@ -352,12 +296,9 @@ __global__ void __launch_bounds__(128) k_interface(Dev s) {
                 }
                 const int sx = xs[1 - cx(q)], sy = ys[1 - cy(q)], sz = zs[1 - cz(q)];
                 const long long src = sx + (long long)s.nx * (sy + (long long)s.ny * sz);
-                if ((solidm >> q) & 1u) {
-                    const int p = s.owner[src];
-                    if (p < 0 || p >= s.np) { set_error(s, ERR_INVARIANT); v[q] = fob; continue; }
-                    v[q] = particle_link(s, q, x, y, z, p, particle_data(s, p), fob, acc);
-                    continue;
-                }
+                // solid source: the pulled value is the bounce-back value
+                // placed by the link pass
+                if ((solidm >> q) & 1u) continue;
                 const bool gas = (gasm >> q) & 1u;
                 if (!gas) {
                     // fluid source: mass exchange with the pulled post-collision PDF
@@ -394,23 +335,21 @@ __global__ void __launch_bounds__(128) k_interface(Dev s) {
             s.mass[cell] = mx + dm;
             s.ru[cell] = make_float4(rho, ux, uy, uz);
         }
-        acc.flush(s);
     }
 }
 
 template <typename S>
 static void launch_typed(const Dev& s, int parity, cudaStream_t st) {
-    const int th = 256;
-    const int bl = blocks_for(s.n, th);
-    const int ib = 152 * 8;
+    const int bl = blocks_for(s.n, 256);
+    const int lb = 152 * 8;
     if (parity == 0) {
-        k_bulk<S, 0><<<bl, th, 0, st>>>(s);
-        k_boundary<S, 0><<<blocks_for(s.n, BOUNDARY_THREADS), BOUNDARY_THREADS, 0, st>>>(s);
-        k_interface<S, 0><<<ib, 128, 0, st>>>(s);
+        if (s.np > 0) k_solid_links<S, 0><<<lb, 256, 0, st>>>(s);
+        k_liquid<S, 0><<<bl, 256, 0, st>>>(s);
+        k_interface<S, 0><<<lb, 128, 0, st>>>(s);
     } else {
-        k_bulk<S, 1><<<bl, th, 0, st>>>(s);
-        k_boundary<S, 1><<<blocks_for(s.n, BOUNDARY_THREADS), BOUNDARY_THREADS, 0, st>>>(s);
-        k_interface<S, 1><<<ib, 128, 0, st>>>(s);
+        if (s.np > 0) k_solid_links<S, 1><<<lb, 256, 0, st>>>(s);
+        k_liquid<S, 1><<<bl, 256, 0, st>>>(s);
+        k_interface<S, 1><<<lb, 128, 0, st>>>(s);
     }
 }
 
@@ -418,7 +357,7 @@ int launch_stream_collide(const Dev& s, int parity, cudaStream_t st) {
     if (s.storage == FSLBM_STORE_FP32) launch_typed<float>(s, parity, st);
     else if (s.storage == FSLBM_STORE_FP16) launch_typed<__half>(s, parity, st);
     else launch_typed<__nv_bfloat16>(s, parity, st);
-    return 3;
+    return s.np > 0 ? 3 : 2;
 }
 
 }  // namespace fsl

@@ -316,57 +316,82 @@ int launch_conversion(const Dev& s, int last_parity, cudaStream_t st) {
     return 12;
 }
 
-// ------------------------------------------------------------ work list
-// Recomputes the bulk bit of every cell and lists the interface cells
-// (warp-aggregated append).
+// ------------------------------------------------------------ work lists
+__device__ __forceinline__ void warp_append(const Dev& s, bool pred, int* list, int* count, int cap, int v) {
+    const unsigned full = 0xffffffffu;
+    const unsigned m = __ballot_sync(full, pred);
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(count, __popc(m));
+    base = __shfl_sync(full, base, leader);
+    if (pred) {
+        const int k = base + __popc(m & ((1u << lane) - 1u));
+        if (k < cap) list[k] = v;
+        else set_error(s, ERR_CAPACITY);
+    }
+}
+
+// Lists the interface cells and the solid cells with a liquid or interface
+// neighbour (warp-aggregated appends).
 __global__ void k_classify(Dev s) {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool in = c < s.n;
     int t = 0;
+    bool surf = false;
     if (in) {
         t = s.flags[c] & TYPE_MASK;
-        bool bulk = false;
-        if (t == T_LIQ) {
+        if (t == T_SOL) {
             int x, y, z;
             coords(s, c, x, y, z);
             const int xs[3] = {shift(x, -1, s.nx, s.per_x), x, shift(x, 1, s.nx, s.per_x)};
             const int ys[3] = {shift(y, -1, s.ny, s.per_y), y, shift(y, 1, s.ny, s.per_y)};
             const int zs[3] = {shift(z, -1, s.nz, s.per_z), z, shift(z, 1, s.nz, s.per_z)};
-            bool inside = xs[0] >= 0 && xs[2] >= 0 && ys[0] >= 0 && ys[2] >= 0 && zs[0] >= 0 && zs[2] >= 0;
-            if (inside) {
-                unsigned all = T_LIQ;
+            unsigned any = 0;
 #pragma unroll
-                for (int q = 0; q < 27; ++q) {
-                    if (q == 13) continue;
-                    all &= (unsigned)(s.flags[xs[1 + cx(q)] + (long long)s.nx * (ys[1 + cy(q)] + (long long)s.ny * zs[1 + cz(q)])] & TYPE_MASK) == T_LIQ ? T_LIQ : 0u;
-                }
-                bulk = all == T_LIQ;
+            for (int q = 0; q < 27; ++q) {
+                if (q == 13) continue;
+                const int a = xs[1 + cx(q)], b = ys[1 + cy(q)], d = zs[1 + cz(q)];
+                if (a < 0 || b < 0 || d < 0) continue;
+                const int tn = s.flags[a + (long long)s.nx * (b + (long long)s.ny * d)] & TYPE_MASK;
+                any |= (tn == T_LIQ || tn == T_IFC) ? 1u : 0u;
             }
+            surf = any != 0;
         }
-        s.flags[c] = (uint8_t)(t | (bulk ? F_BULK : 0));
     }
-    const bool ifc = in && t == T_IFC;
-    const unsigned full = 0xffffffffu;
-    unsigned m = __ballot_sync(full, ifc);
-    if (!m) return;
-    const int lane = threadIdx.x & 31;
-    int leader = __ffs(m) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(s.wl_count, __popc(m));
-    base = __shfl_sync(full, base, leader);
-    if (ifc) {
-        int k = base + __popc(m & ((1u << lane) - 1u));
-        if (k < s.wl_cap) s.wl[k] = (int)c;
-        else set_error(s, ERR_CAPACITY);
+    warp_append(s, in && t == T_IFC, s.wl, s.wl_count, s.wl_cap, (int)c);
+    warp_append(s, surf, s.sl, s.sl_count, s.sl_cap, (int)c);
+}
+
+// liquid cells with a gas neighbour (the separation the conversion rules keep)
+__global__ void k_check_invariant(Dev s) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= s.n || (s.flags[c] & TYPE_MASK) != T_LIQ) return;
+    int x, y, z;
+    coords(s, c, x, y, z);
+    for (int q = 0; q < 27; ++q) {
+        if (q == 13) continue;
+        const long long nb = nbr(s, x, y, z, cx(q), cy(q), cz(q));
+        if (nb >= 0 && (s.flags[nb] & TYPE_MASK) == T_GAS) {
+            atomicAdd(s.viol, 1ull);
+            return;
+        }
     }
+}
+
+void launch_check_invariant(const Dev& s, cudaStream_t st) {
+    k_check_invariant<<<blocks_for(s.n, 256), 256, 0, st>>>(s);
 }
 
 __global__ void k_clamp_count(Dev s) {
     if (*s.wl_count > s.wl_cap) *s.wl_count = s.wl_cap;
+    if (*s.sl_count > s.sl_cap) *s.sl_count = s.sl_cap;
 }
 
 int launch_classify(const Dev& s, cudaStream_t st) {
     cudaMemsetAsync(s.wl_count, 0, sizeof(int), st);
+    cudaMemsetAsync(s.sl_count, 0, sizeof(int), st);
     k_classify<<<blocks_for(s.n, 256), 256, 0, st>>>(s);
     k_clamp_count<<<1, 1, 0, st>>>(s);
     return 2;
