@@ -323,6 +323,35 @@ __device__ __forceinline__ uint8_t flag_or(uint8_t* flags, long long i, uint8_t 
     return (uint8_t)((old >> sh) & 0xffu);
 }
 
+// Block-aggregated append to a device list: one atomic per block. Every
+// thread of the block must call it (it synchronises the block); blockDim.x
+// must be a multiple of 32 and at most 1024.
+__device__ __forceinline__ void block_append(const Dev& s, bool pred, int v, int* list, int* count, int cap) {
+    __shared__ int warp_n[32];
+    __shared__ int block_base;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned m = __ballot_sync(full, pred);
+    if (lane == 0) warp_n[wid] = __popc(m);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            const int c = warp_n[w];
+            warp_n[w] = tot;
+            tot += c;
+        }
+        block_base = tot ? atomicAdd(count, tot) : 0;
+    }
+    __syncthreads();
+    if (pred) {
+        const int k = block_base + warp_n[wid] + __popc(m & ((1u << lane) - 1u));
+        if (k < cap) list[k] = v;
+        else set_error(s, ERR_CAPACITY);
+    }
+    __syncthreads();
+}
+
 // post-collision PDFs of a cell read from the AA layout (outside the
 // stream-collide kernel, where no slot is being rewritten)
 __device__ __forceinline__ void load_fstar(const Dev& s, long long cell, int last_parity, float (&f)[27]) {

@@ -553,18 +553,19 @@ __global__ void k_dirty(Dev s) {
     bbox_axis(s.Xm[3 * p + 2], s.X[3 * p + 2], r, s.nz, s.per_z, lo[2], hi[2]);
     const int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
     const int tot = ex * ey * ez;
-    for (int k = threadIdx.x; k < tot; k += blockDim.x) {
-        int a = lo[0] + k % ex, b = lo[1] + (k / ex) % ey, c = lo[2] + k / (ex * ey);
-        a = (a % s.nx + s.nx) % s.nx;
-        b = (b % s.ny + s.ny) % s.ny;
-        c = (c % s.nz + s.nz) % s.nz;
-        const long long cell = a + (long long)s.nx * (b + (long long)s.ny * c);
-        const uint8_t old = flag_or(s.dirty, cell, 1);
-        if (!(old & 1)) {
-            int j = atomicAdd(s.dl_count, 1);
-            if (j < s.dl_cap) s.dl[j] = (int)cell;
-            else set_error(s, ERR_CAPACITY);
+    for (int k0 = 0; k0 < tot; k0 += blockDim.x) {
+        const int k = k0 + threadIdx.x;
+        bool first = false;
+        long long cell = 0;
+        if (k < tot) {
+            int a = lo[0] + k % ex, b = lo[1] + (k / ex) % ey, c = lo[2] + k / (ex * ey);
+            a = (a % s.nx + s.nx) % s.nx;
+            b = (b % s.ny + s.ny) % s.ny;
+            c = (c % s.nz + s.nz) % s.nz;
+            cell = a + (long long)s.nx * (b + (long long)s.ny * c);
+            first = !(flag_or(s.dirty, cell, 1) & 1);
         }
+        block_append(s, first, (int)cell, s.dl, s.dl_count, s.dl_cap);
     }
 }
 

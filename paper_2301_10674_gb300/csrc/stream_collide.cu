@@ -25,6 +25,40 @@ namespace fsl {
 // coordinates: an even step reads its own slots (a wall-bound PDF came back
 // into (q, x) in the previous odd step), an odd step reads (q, x) across a
 // wall face and writes (opp(q), x) toward one.
+// offsets of the x, y, z neighbours (-1, 0, +1) of a cell with the wall
+// faces it touches as bits (x-, x+, y-, y+, z-, z+)
+struct NbrOffsets {
+    int ox[3], oy[3], oz[3];
+    unsigned wall;
+};
+__device__ __forceinline__ NbrOffsets nbr_offsets(const Dev& s, int x, int y, int z) {
+    const int sxy = s.nx * s.ny;
+    NbrOffsets o;
+    o.wall = 0;
+    o.ox[0] = -1; o.ox[1] = 0; o.ox[2] = 1;
+    o.oy[0] = -s.nx; o.oy[1] = 0; o.oy[2] = s.nx;
+    o.oz[0] = -sxy; o.oz[1] = 0; o.oz[2] = sxy;
+    if (x == 0) { if (s.per_x) o.ox[0] = s.nx - 1; else o.wall |= 1u; }
+    if (x == s.nx - 1) { if (s.per_x) o.ox[2] = 1 - s.nx; else o.wall |= 2u; }
+    if (y == 0) { if (s.per_y) o.oy[0] = (s.ny - 1) * s.nx; else o.wall |= 4u; }
+    if (y == s.ny - 1) { if (s.per_y) o.oy[2] = (1 - s.ny) * s.nx; else o.wall |= 8u; }
+    if (z == 0) { if (s.per_z) o.oz[0] = (s.nz - 1) * sxy; else o.wall |= 16u; }
+    if (z == s.nz - 1) { if (s.per_z) o.oz[2] = (1 - s.nz) * sxy; else o.wall |= 32u; }
+    return o;
+}
+// wall bits a direction d crosses from a cell
+__host__ __device__ constexpr unsigned wall_bits(int dx, int dy, int dz) {
+    return (dx == -1 ? 1u : 0u) | (dx == 1 ? 2u : 0u) | (dy == -1 ? 4u : 0u) | (dy == 1 ? 8u : 0u) |
+           (dz == -1 ? 16u : 0u) | (dz == 1 ? 32u : 0u);
+}
+
+// All liquid cells. Every PDF is a plain pull: PDFs from fluid cells, and
+// from solid cells the bounce-back values k_solid_links placed in the pull
+// slots. Only wall faces need handling here, and they follow from the
+// coordinates: an even step reads its own slots (a wall-bound PDF came back
+// into (q, x) in the previous odd step), an odd step reads (q, x) across a
+// wall face and writes (opp(q), x) toward one. Interior cells of an odd step
+// use offsets that are the same for every thread.
 template <typename S, int PAR>
 __global__ void __launch_bounds__(256, 3) k_liquid(Dev s) {
     const int cell = blockIdx.x * blockDim.x + threadIdx.x;
@@ -36,54 +70,47 @@ __global__ void __launch_bounds__(256, 3) k_liquid(Dev s) {
     if (PAR == 0) {
 #pragma unroll
         for (int q = 0; q < 27; ++q) v[q] = Store<S>::ld(f + (long long)q * n + cell);
+        float rho, ux, uy, uz;
+        collide(v, s.omega, s.gx, s.gy, s.gz, rho, ux, uy, uz);
+#pragma unroll
+        for (int q = 0; q < 27; ++q) Store<S>::st(f + (long long)opp(q) * n + cell, v[q]);
+        return;
+    }
+    int x, y, z;
+    coords(s, cell, x, y, z);
+    const int sxy = s.nx * s.ny;
+    const bool interior = x > 0 && x < s.nx - 1 && y > 0 && y < s.ny - 1 && z > 0 && z < s.nz - 1;
+    if (interior) {
+        S* fc = f + cell;
+#pragma unroll
+        for (int q = 0; q < 27; ++q)
+            v[q] = Store<S>::ld(fc + ((long long)opp(q) * n - (cx(q) + s.nx * cy(q) + sxy * cz(q))));
     } else {
-        int x, y, z;
-        coords(s, cell, x, y, z);
-        // neighbour offsets along each axis for -1, 0, +1; a wall face is
-        // marked by the bit of that side
-        const int sxy = s.nx * s.ny;
-        unsigned wall = 0;
-        int ox[3] = {-1, 0, 1}, oy[3] = {-s.nx, 0, s.nx}, oz[3] = {-sxy, 0, sxy};
-        if (x == 0) { if (s.per_x) ox[0] = s.nx - 1; else wall |= 1u; }
-        if (x == s.nx - 1) { if (s.per_x) ox[2] = 1 - s.nx; else wall |= 2u; }
-        if (y == 0) { if (s.per_y) oy[0] = (s.ny - 1) * s.nx; else wall |= 4u; }
-        if (y == s.ny - 1) { if (s.per_y) oy[2] = (1 - s.ny) * s.nx; else wall |= 8u; }
-        if (z == 0) { if (s.per_z) oz[0] = (s.nz - 1) * sxy; else wall |= 16u; }
-        if (z == s.nz - 1) { if (s.per_z) oz[2] = (1 - s.nz) * sxy; else wall |= 32u; }
+        const NbrOffsets o = nbr_offsets(s, x, y, z);
 #pragma unroll
         for (int q = 0; q < 27; ++q) {
             // source x - c_q beyond a wall face?
-            const unsigned need = (cx(q) == 1 ? 1u : 0u) | (cx(q) == -1 ? 2u : 0u) | (cy(q) == 1 ? 4u : 0u) |
-                                  (cy(q) == -1 ? 8u : 0u) | (cz(q) == 1 ? 16u : 0u) | (cz(q) == -1 ? 32u : 0u);
-            const int src = cell + ox[1 - cx(q)] + oy[1 - cy(q)] + oz[1 - cz(q)];
-            const long long a = (wall & need) ? (long long)q * n + cell : (long long)opp(q) * n + src;
+            const int src = cell + o.ox[1 - cx(q)] + o.oy[1 - cy(q)] + o.oz[1 - cz(q)];
+            const long long a = (o.wall & wall_bits(-cx(q), -cy(q), -cz(q))) ? (long long)q * n + cell
+                                                                               : (long long)opp(q) * n + src;
             v[q] = Store<S>::ld(f + a);
         }
     }
     float rho, ux, uy, uz;
     collide(v, s.omega, s.gx, s.gy, s.gz, rho, ux, uy, uz);
-    if (PAR == 0) {
+    if (interior) {
+        S* fc = f + cell;
 #pragma unroll
-        for (int q = 0; q < 27; ++q) Store<S>::st(f + (long long)opp(q) * n + cell, v[q]);
+        for (int q = 0; q < 27; ++q)
+            Store<S>::st(fc + ((long long)q * n + (cx(q) + s.nx * cy(q) + sxy * cz(q))), v[q]);
     } else {
-        int x, y, z;
-        coords(s, cell, x, y, z);
-        const int sxy = s.nx * s.ny;
-        unsigned wall = 0;
-        int ox[3] = {-1, 0, 1}, oy[3] = {-s.nx, 0, s.nx}, oz[3] = {-sxy, 0, sxy};
-        if (x == 0) { if (s.per_x) ox[0] = s.nx - 1; else wall |= 1u; }
-        if (x == s.nx - 1) { if (s.per_x) ox[2] = 1 - s.nx; else wall |= 2u; }
-        if (y == 0) { if (s.per_y) oy[0] = (s.ny - 1) * s.nx; else wall |= 4u; }
-        if (y == s.ny - 1) { if (s.per_y) oy[2] = (1 - s.ny) * s.nx; else wall |= 8u; }
-        if (z == 0) { if (s.per_z) oz[0] = (s.nz - 1) * sxy; else wall |= 16u; }
-        if (z == s.nz - 1) { if (s.per_z) oz[2] = (1 - s.nz) * sxy; else wall |= 32u; }
+        const NbrOffsets o = nbr_offsets(s, x, y, z);
 #pragma unroll
         for (int q = 0; q < 27; ++q) {
             // target x + c_q beyond a wall face?
-            const unsigned need = (cx(q) == -1 ? 1u : 0u) | (cx(q) == 1 ? 2u : 0u) | (cy(q) == -1 ? 4u : 0u) |
-                                  (cy(q) == 1 ? 8u : 0u) | (cz(q) == -1 ? 16u : 0u) | (cz(q) == 1 ? 32u : 0u);
-            const int dst = cell + ox[1 + cx(q)] + oy[1 + cy(q)] + oz[1 + cz(q)];
-            const long long a = (wall & need) ? (long long)opp(q) * n + cell : (long long)q * n + dst;
+            const int dst = cell + o.ox[1 + cx(q)] + o.oy[1 + cy(q)] + o.oz[1 + cz(q)];
+            const long long a = (o.wall & wall_bits(cx(q), cy(q), cz(q))) ? (long long)opp(q) * n + cell
+                                                                           : (long long)q * n + dst;
             Store<S>::st(f + a, v[q]);
         }
     }
@@ -119,11 +146,6 @@ __device__ __forceinline__ void flush_mem(const Dev& s, int key, const float (&F
         atomicAdd(&s.Th[3 * key + 1], (double)v[4]);
         atomicAdd(&s.Th[3 * key + 2], (double)v[5]);
     }
-}
-
-__device__ __forceinline__ float min_image(float d, int L, int periodic) {
-    if (periodic) d -= (float)L * rintf(d / (float)L);
-    return d;
 }
 
 // particle surface velocity at a link midpoint and the link force
@@ -172,43 +194,55 @@ __global__ void __launch_bounds__(256) k_solid_links(Dev s) {
         int key = -1;
         float F[3] = {0.f, 0.f, 0.f}, T[3] = {0.f, 0.f, 0.f};
         if (i < count) {
-            const long long cell = s.sl[i];
+            const int cell = s.sl[i];
             int x, y, z;
             coords(s, cell, x, y, z);
             const int p = s.owner[cell];
+            S* f = static_cast<S*>(s.f);
+            const long long n = s.n;
+            const NbrOffsets o = nbr_offsets(s, x, y, z);
+            // phase 1: which neighbours are fluid (wall faces excluded)
+            unsigned fluidm = 0;
+#pragma unroll
+            for (int q = 0; q < 27; ++q) {
+                if (q == 13 || (o.wall & wall_bits(cx(q), cy(q), cz(q)))) continue;
+                const int xn = cell + o.ox[1 + cx(q)] + o.oy[1 + cy(q)] + o.oz[1 + cz(q)];
+                const int tn = s.flags[xn] & TYPE_MASK;
+                fluidm |= (tn == T_LIQ || tn == T_IFC) ? (1u << q) : 0u;
+            }
             if (p < 0 || p >= s.np) {
-                set_error(s, ERR_INVARIANT);
+                if (fluidm) set_error(s, ERR_INVARIANT);
+                fluidm = 0;
             } else {
                 key = p;
+            }
+            // phase 2: the post-collision PDFs the fluid neighbours send here
+            float fo[27];
+#pragma unroll
+            for (int q = 0; q < 27; ++q) {
+                const int xn = cell + o.ox[1 + cx(q)] + o.oy[1 + cy(q)] + o.oz[1 + cz(q)];
+                const long long a = PAR == 0 ? (long long)opp(q) * n + cell : (long long)q * n + xn;
+                fo[q] = ((fluidm >> q) & 1u) ? Store<S>::ld(f + a) : 0.f;
+            }
+            // phase 3: bounce-back values and momentum exchange
+            if (fluidm) {
                 const PData P = particle_data(s, p);
-                S* f = static_cast<S*>(s.f);
-                const long long n = s.n;
-                const int xs[3] = {shift(x, -1, s.nx, s.per_x), x, shift(x, 1, s.nx, s.per_x)};
-                const int ys[3] = {shift(y, -1, s.ny, s.per_y), y, shift(y, 1, s.ny, s.per_y)};
-                const int zs[3] = {shift(z, -1, s.nz, s.per_z), z, shift(z, 1, s.nz, s.per_z)};
-                // offset of the cell centre from the particle centre
                 const float ddx = (float)wrap_int(x - P.xi.x, s.nx, s.per_x) + 0.5f - P.xf.x;
                 const float ddy = (float)wrap_int(y - P.xi.y, s.ny, s.per_y) + 0.5f - P.xf.y;
                 const float ddz = (float)wrap_int(z - P.xi.z, s.nz, s.per_z) + 0.5f - P.xf.z;
 #pragma unroll
                 for (int q = 0; q < 27; ++q) {
-                    if (q == 13) continue;
-                    const int tx = xs[1 + cx(q)], ty = ys[1 + cy(q)], tz = zs[1 + cz(q)];
-                    if (tx < 0 || ty < 0 || tz < 0) continue;
-                    const long long xn = tx + (long long)s.nx * (ty + (long long)s.ny * tz);
-                    const int tn = s.flags[xn] & TYPE_MASK;
-                    if (tn != T_LIQ && tn != T_IFC) continue;
+                    if (!((fluidm >> q) & 1u)) continue;
+                    const int xn = cell + o.ox[1 + cx(q)] + o.oy[1 + cy(q)] + o.oz[1 + cz(q)];
                     const float dx = ddx + 0.5f * cx(q), dy = ddy + 0.5f * cy(q), dz = ddz + 0.5f * cz(q);
                     const float ubx = P.u.x + (P.w.y * dz - P.w.z * dy);
                     const float uby = P.u.y + (P.w.z * dx - P.w.x * dz);
                     const float ubz = P.u.z + (P.w.x * dy - P.w.y * dx);
                     const float cu = cx(q) * ubx + cy(q) * uby + cz(q) * ubz;
-                    const long long src = PAR == 0 ? (long long)opp(q) * n + cell : (long long)q * n + xn;
+                    const float val = fo[q] + 6.f * wq(q) * cu;
                     const long long dst = PAR == 0 ? (long long)q * n + xn : (long long)opp(q) * n + cell;
-                    const float fo = Store<S>::ld(f + src);
-                    const float val = fo + 6.f * wq(q) * cu;
                     Store<S>::st(f + dst, val);
-                    const float sum = fo + val, dif = fo - val;
+                    const float sum = fo[q] + val, dif = fo[q] - val;
                     const float Fx = -cx(q) * sum - ubx * dif;
                     const float Fy = -cy(q) * sum - uby * dif;
                     const float Fz = -cz(q) * sum - ubz * dif;

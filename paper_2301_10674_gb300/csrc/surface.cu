@@ -317,22 +317,6 @@ int launch_conversion(const Dev& s, int last_parity, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------ work lists
-__device__ __forceinline__ void warp_append(const Dev& s, bool pred, int* list, int* count, int cap, int v) {
-    const unsigned full = 0xffffffffu;
-    const unsigned m = __ballot_sync(full, pred);
-    if (!m) return;
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(m) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(count, __popc(m));
-    base = __shfl_sync(full, base, leader);
-    if (pred) {
-        const int k = base + __popc(m & ((1u << lane) - 1u));
-        if (k < cap) list[k] = v;
-        else set_error(s, ERR_CAPACITY);
-    }
-}
-
 // Lists the interface cells and the solid cells with a liquid or interface
 // neighbour (warp-aggregated appends).
 __global__ void k_classify(Dev s) {
@@ -360,8 +344,8 @@ __global__ void k_classify(Dev s) {
             surf = any != 0;
         }
     }
-    warp_append(s, in && t == T_IFC, s.wl, s.wl_count, s.wl_cap, (int)c);
-    warp_append(s, surf, s.sl, s.sl_count, s.sl_cap, (int)c);
+    block_append(s, in && t == T_IFC, (int)c, s.wl, s.wl_count, s.wl_cap);
+    block_append(s, surf, (int)c, s.sl, s.sl_count, s.sl_cap);
 }
 
 // liquid cells with a gas neighbour (the separation the conversion rules keep)
