@@ -252,6 +252,8 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     d.shared = dalloc<int>(s, pc, ok);
     d.act = dalloc<int>(s, pc, ok);
     d.dirty = dalloc<uint8_t>(s, n + 4, ok);
+    d.scratch_a = dalloc<uint8_t>(s, n, ok);
+    d.scratch_b = dalloc<uint8_t>(s, n, ok);
     const long long dcap = n;   // the first re-map may touch every cell of the bed
     d.dl_cap = (int)dcap;
     d.dl = dalloc<int>(s, dcap, ok);

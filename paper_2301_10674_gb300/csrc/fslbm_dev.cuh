@@ -113,6 +113,7 @@ struct Dev {
     int* shared;
     int* act; int* act_count;
     uint8_t* dirty;
+    uint8_t* scratch_a; uint8_t* scratch_b;     // byte fields for the neighbourhood OR
     int* dl; int* dl_count; int dl_cap;
     // static map of the fixed particles
     unsigned long long* fixkey;

@@ -512,16 +512,22 @@ __global__ void k_remap_all(Dev s, int init_mode) {
     remap_cell(s, c, init_mode);
 }
 
-// A mobile particle needs re-mapping when it moved at least its margin (the
-// distance from its surface to the nearest cell centre at the last map) or
-// when it shares a cell with another particle (ownership by metric).
+// Every mobile particle that moved since its last map (|dX| > 0) marks the
+// cells whose inside/outside status it can have changed: a cell changes only
+// if |x_c - X_new| - r lies within |dX| of zero (triangle inequality), so
+// the thin shell |  |x_c - X_new| - r | <= |dX| + 1e-3 is marked (the slack
+// covers the FP32 evaluation of the offsets, exact to ~1e-6 through the
+// integer-plus-fraction form of the centre). A particle that shares a cell
+// with another one marks its whole box, since the owner of a shared cell is
+// decided by comparing the two metrics.
 __global__ void k_active(Dev s) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= s.np || s.fixed[p]) return;
     const double dx = s.X[3 * p] - s.Xm[3 * p], dy = s.X[3 * p + 1] - s.Xm[3 * p + 1],
                  dz = s.X[3 * p + 2] - s.Xm[3 * p + 2];
     const double d = sqrt(dx * dx + dy * dy + dz * dz);
-    if (s.shared[p] || !(d < (double)s.margin[p])) {
+    if (s.shared[p] || d > 0.0) {
+        s.margin[p] = s.shared[p] ? -1.f : (float)d;   // shell half-width (negative: whole box)
         s.shared[p] = 0;
         int k = atomicAdd(s.act_count, 1);
         s.act[k] = p;
@@ -541,16 +547,21 @@ __device__ __forceinline__ void bbox_axis(double a, double b, double r, int L, i
     }
 }
 
-// cells of the old and the new bounding box of every active particle join
-// the dirty list (each once)
+// cells of the shell (or of the old and new boxes) of every active particle
+// join the dirty list, each once
 __global__ void k_dirty(Dev s) {
     if ((int)blockIdx.x >= *s.act_count) return;
     const int p = s.act[blockIdx.x];
     const double r = s.R[p];
+    const float w = s.margin[p];
+    const bool whole = w < 0.f;
     int lo[3], hi[3];
     bbox_axis(s.Xm[3 * p], s.X[3 * p], r, s.nx, s.per_x, lo[0], hi[0]);
     bbox_axis(s.Xm[3 * p + 1], s.X[3 * p + 1], r, s.ny, s.per_y, lo[1], hi[1]);
     bbox_axis(s.Xm[3 * p + 2], s.X[3 * p + 2], r, s.nz, s.per_z, lo[2], hi[2]);
+    const int4 xi = s.Xi[p];
+    const float4 xf = s.Xfr[p];
+    const float rf = (float)r, band = w + 1e-3f;
     const int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
     const int tot = ex * ey * ez;
     for (int k0 = 0; k0 < tot; k0 += blockDim.x) {
@@ -558,12 +569,19 @@ __global__ void k_dirty(Dev s) {
         bool first = false;
         long long cell = 0;
         if (k < tot) {
-            int a = lo[0] + k % ex, b = lo[1] + (k / ex) % ey, c = lo[2] + k / (ex * ey);
-            a = (a % s.nx + s.nx) % s.nx;
-            b = (b % s.ny + s.ny) % s.ny;
-            c = (c % s.nz + s.nz) % s.nz;
-            cell = a + (long long)s.nx * (b + (long long)s.ny * c);
-            first = !(flag_or(s.dirty, cell, 1) & 1);
+            const int ua = lo[0] + k % ex, ub = lo[1] + (k / ex) % ey, uc = lo[2] + k / (ex * ey);
+            bool mark = whole;
+            if (!whole) {
+                const float a = (float)(ua - xi.x) + 0.5f - xf.x;
+                const float b = (float)(ub - xi.y) + 0.5f - xf.y;
+                const float c = (float)(uc - xi.z) + 0.5f - xf.z;
+                mark = fabsf(sqrtf(a * a + b * b + c * c) - rf) <= band;
+            }
+            if (mark) {
+                const int a = (ua % s.nx + s.nx) % s.nx, b = (ub % s.ny + s.ny) % s.ny, c = (uc % s.nz + s.nz) % s.nz;
+                cell = a + (long long)s.nx * (b + (long long)s.ny * c);
+                first = !(flag_or(s.dirty, cell, 1) & 1);
+            }
         }
         block_append(s, first, (int)cell, s.dl, s.dl_count, s.dl_cap);
     }
@@ -578,41 +596,14 @@ __global__ void k_remap_list(Dev s) {
     }
 }
 
-// new margin of each active particle: min over the cells of its box of
-// | |x_c - X| - r |, shrunk by a safety factor for the FP32 evaluation
-__global__ void k_margin(Dev s) {
-    if ((int)blockIdx.x >= *s.act_count) return;
-    const int p = s.act[blockIdx.x];
-    const double r = s.R[p];
-    const double X0 = s.X[3 * p], X1 = s.X[3 * p + 1], X2 = s.X[3 * p + 2];
-    int lo[3], hi[3];
-    bbox_axis(X0, X0, r, s.nx, s.per_x, lo[0], hi[0]);
-    bbox_axis(X1, X1, r, s.ny, s.per_y, lo[1], hi[1]);
-    bbox_axis(X2, X2, r, s.nz, s.per_z, lo[2], hi[2]);
-    lo[0] -= 1; hi[0] += 1; lo[1] -= 1; hi[1] += 1; lo[2] -= 1; hi[2] += 1;
-    const int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
-    const int tot = ex * ey * ez;
-    float m = 1e30f;
-    for (int k = threadIdx.x; k < tot; k += blockDim.x) {
-        const float a = (float)((lo[0] + k % ex) + 0.5 - X0);
-        const float b = (float)((lo[1] + (k / ex) % ey) + 0.5 - X1);
-        const float c = (float)((lo[2] + k / (ex * ey)) + 0.5 - X2);
-        const float d = fabsf(sqrtf(a * a + b * b + c * c) - (float)r);
-        m = fminf(m, d);
-    }
-    __shared__ float red[256];
-    red[threadIdx.x] = m;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) red[threadIdx.x] = fminf(red[threadIdx.x], red[threadIdx.x + o]);
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        s.margin[p] = 0.5f * red[0] - 1e-4f;
-        s.Xm[3 * p] = X0;
-        s.Xm[3 * p + 1] = X1;
-        s.Xm[3 * p + 2] = X2;
-    }
+// the active particles' map positions move to their current centres
+__global__ void k_map_position(Dev s) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= *s.act_count) return;
+    const int p = s.act[k];
+    s.Xm[3 * p] = s.X[3 * p];
+    s.Xm[3 * p + 1] = s.X[3 * p + 1];
+    s.Xm[3 * p + 2] = s.X[3 * p + 2];
 }
 
 #define FOR_TL(i)                                                                             \
@@ -770,7 +761,7 @@ int launch_particles_step(const Dev& s, int have_prev, int last_parity, cudaStre
     k_active<<<blocks_for(s.np, 128), 128, 0, st>>>(s);
     k_dirty<<<s.np, 256, 0, st>>>(s);
     k_remap_list<<<152 * 8, 128, 0, st>>>(s);
-    k_margin<<<s.np, 256, 0, st>>>(s);
+    k_map_position<<<blocks_for(s.np, 256), 256, 0, st>>>(s);
     k_transitions<<<152 * 4, 128, 0, st>>>(s, last_parity);
     k_apply_transitions<<<152 * 4, 256, 0, st>>>(s);
     k_repair<<<152 * 4, 256, 0, st>>>(s);

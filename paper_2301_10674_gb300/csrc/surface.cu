@@ -317,9 +317,41 @@ int launch_conversion(const Dev& s, int last_parity, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------ work lists
+// Whether any of the 27 cells around a cell is liquid or interface, as a
+// separable OR: along x from the flags, then along y, then along z (cells
+// beyond a wall face count as not fluid).
+__global__ void k_fluid_or_x(Dev s, uint8_t* out) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= s.n) return;
+    int x, y, z;
+    coords(s, c, x, y, z);
+    uint8_t v = 0;
+#pragma unroll
+    for (int d = -1; d <= 1; ++d) {
+        const int a = shift(x, d, s.nx, s.per_x);
+        if (a < 0) continue;
+        const int t = s.flags[c - x + a] & TYPE_MASK;
+        v |= (t == T_LIQ || t == T_IFC) ? 1 : 0;
+    }
+    out[c] = v;
+}
+__global__ void k_fluid_or_y(Dev s, const uint8_t* in, uint8_t* out) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= s.n) return;
+    int x, y, z;
+    coords(s, c, x, y, z);
+    uint8_t v = 0;
+#pragma unroll
+    for (int d = -1; d <= 1; ++d) {
+        const int b = shift(y, d, s.ny, s.per_y);
+        if (b >= 0) v |= in[c + (long long)(b - y) * s.nx];
+    }
+    out[c] = v;
+}
+
 // Lists the interface cells and the solid cells with a liquid or interface
-// neighbour (warp-aggregated appends).
-__global__ void k_classify(Dev s) {
+// neighbour (the OR along z completes the 27-cell neighbourhood).
+__global__ void k_classify(Dev s, const uint8_t* ory) {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool in = c < s.n;
     int t = 0;
@@ -329,19 +361,13 @@ __global__ void k_classify(Dev s) {
         if (t == T_SOL) {
             int x, y, z;
             coords(s, c, x, y, z);
-            const int xs[3] = {shift(x, -1, s.nx, s.per_x), x, shift(x, 1, s.nx, s.per_x)};
-            const int ys[3] = {shift(y, -1, s.ny, s.per_y), y, shift(y, 1, s.ny, s.per_y)};
-            const int zs[3] = {shift(z, -1, s.nz, s.per_z), z, shift(z, 1, s.nz, s.per_z)};
-            unsigned any = 0;
+            uint8_t v = 0;
 #pragma unroll
-            for (int q = 0; q < 27; ++q) {
-                if (q == 13) continue;
-                const int a = xs[1 + cx(q)], b = ys[1 + cy(q)], d = zs[1 + cz(q)];
-                if (a < 0 || b < 0 || d < 0) continue;
-                const int tn = s.flags[a + (long long)s.nx * (b + (long long)s.ny * d)] & TYPE_MASK;
-                any |= (tn == T_LIQ || tn == T_IFC) ? 1u : 0u;
+            for (int d = -1; d <= 1; ++d) {
+                const int e = shift(z, d, s.nz, s.per_z);
+                if (e >= 0) v |= ory[c + (long long)(e - z) * s.nx * s.ny];
             }
-            surf = any != 0;
+            surf = v != 0;
         }
     }
     block_append(s, in && t == T_IFC, (int)c, s.wl, s.wl_count, s.wl_cap);
@@ -376,9 +402,12 @@ __global__ void k_clamp_count(Dev s) {
 int launch_classify(const Dev& s, cudaStream_t st) {
     cudaMemsetAsync(s.wl_count, 0, sizeof(int), st);
     cudaMemsetAsync(s.sl_count, 0, sizeof(int), st);
-    k_classify<<<blocks_for(s.n, 256), 256, 0, st>>>(s);
+    const int bl = blocks_for(s.n, 256);
+    k_fluid_or_x<<<bl, 256, 0, st>>>(s, s.scratch_a);
+    k_fluid_or_y<<<bl, 256, 0, st>>>(s, s.scratch_a, s.scratch_b);
+    k_classify<<<bl, 256, 0, st>>>(s, s.scratch_b);
     k_clamp_count<<<1, 1, 0, st>>>(s);
-    return 2;
+    return 4;
 }
 
 __global__ void k_cell_counts(Dev s, unsigned long long* out) {
