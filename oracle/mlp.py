@@ -1,0 +1,97 @@
+"""FP64 oracle of the learned interface normal: a 27-64-64-4 perceptron
+with ReLU that maps a 3x3x3 fill-level stencil to the interface normal
+(3 components, pointing toward the gas) and the curvature.
+
+TEST INFRASTRUCTURE ONLY (tests, smoke check, CPU baseline). Plain numpy,
+written from the definition: affine layers, ReLU, the loss
+L = mean over the batch of (1 - n_pred.n_true / |n_pred|) + lam (k_pred - k_true)^2,
+its gradient by the chain rule, and the Adam update (Kingma and Ba, with
+bias correction). The tests pin the gradient against central finite
+differences.
+
+Parameter layout (shared convention with the CUDA kernels, which store the
+same matrices): W1 (64, 27), b1 (64), W2 (64, 64), b2 (64), W3 (4, 64), b3 (4).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+SIZES = ((64, 27), (64,), (64, 64), (64,), (4, 64), (4,))
+NPARAM = sum(int(np.prod(s)) for s in SIZES)   # 6212
+
+
+def unpack(theta: np.ndarray):
+    out, k = [], 0
+    for s in SIZES:
+        m = int(np.prod(s))
+        out.append(theta[k:k + m].reshape(s))
+        k += m
+    return out
+
+
+def init(seed: int = 0) -> np.ndarray:
+    """He-uniform weights, zero biases."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for s in SIZES:
+        if len(s) == 2:
+            lim = np.sqrt(6.0 / s[1])
+            parts.append(rng.uniform(-lim, lim, s).ravel())
+        else:
+            parts.append(np.zeros(s))
+    return np.concatenate(parts)
+
+
+def forward(theta: np.ndarray, X: np.ndarray):
+    """X: (B, 27) fill levels. Returns the output (B, 4) and the cache."""
+    W1, b1, W2, b2, W3, b3 = unpack(theta)
+    z1 = X @ W1.T + b1
+    h1 = np.maximum(z1, 0.0)
+    z2 = h1 @ W2.T + b2
+    h2 = np.maximum(z2, 0.0)
+    y = h2 @ W3.T + b3
+    return y, (X, z1, h1, z2, h2)
+
+
+def loss_and_grad(theta: np.ndarray, X: np.ndarray, n_true: np.ndarray, k_true: np.ndarray, lam: float):
+    """Loss and its gradient with respect to every parameter."""
+    W1, b1, W2, b2, W3, b3 = unpack(theta)
+    y, (X, z1, h1, z2, h2) = forward(theta, X)
+    B = X.shape[0]
+    n = y[:, :3]
+    kap = y[:, 3]
+    norm = np.linalg.norm(n, axis=1)
+    cosv = np.sum(n * n_true, axis=1) / norm
+    L = np.mean(1.0 - cosv + lam * (kap - k_true) ** 2)
+    # d(1 - n.t/|n|)/dn = -(t/|n| - (n.t) n/|n|^3)
+    dn = -(n_true / norm[:, None] - (np.sum(n * n_true, axis=1) / norm ** 3)[:, None] * n) / B
+    dk = 2.0 * lam * (kap - k_true) / B
+    dy = np.concatenate([dn, dk[:, None]], axis=1)
+    gW3 = dy.T @ h2
+    gb3 = dy.sum(0)
+    dh2 = dy @ W3
+    dz2 = dh2 * (z2 > 0)
+    gW2 = dz2.T @ h1
+    gb2 = dz2.sum(0)
+    dh1 = dz2 @ W2
+    dz1 = dh1 * (z1 > 0)
+    gW1 = dz1.T @ X
+    gb1 = dz1.sum(0)
+    g = np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2, gW3.ravel(), gb3])
+    return L, g
+
+
+def adam(theta, g, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam step (t counts from 1); returns the new theta, m, v."""
+    m = b1 * m + (1 - b1) * g
+    v = b2 * v + (1 - b2) * g * g
+    mh = m / (1 - b1 ** t)
+    vh = v / (1 - b2 ** t)
+    return theta - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def predict_normal(theta, X):
+    """Unit normal (toward the gas) and curvature predicted for stencils X."""
+    y, _ = forward(theta, X)
+    n = y[:, :3]
+    return n / np.linalg.norm(n, axis=1, keepdims=True), y[:, 3]

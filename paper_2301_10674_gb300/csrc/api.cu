@@ -185,7 +185,12 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     s->elem = p->storage == FSLBM_STORE_FP32 ? 4 : 2;
 
     bool ok = true;
-    d.f = dalloc_bytes(s, (size_t)27 * n * s->elem, ok);
+    // 128 bytes of slack on both sides: the staged sweep's 16-byte-aligned
+    // shifted slices reach one word beyond the first and last element
+    {
+        unsigned char* raw = static_cast<unsigned char*>(dalloc_bytes(s, (size_t)27 * n * s->elem + 256, ok));
+        d.f = raw ? raw + 128 : nullptr;
+    }
     d.fs = dalloc_bytes(s, (size_t)27 * n * s->elem, ok);
     d.flags = dalloc<uint8_t>(s, n + 4, ok);   // word-granular atomics on the last bytes
     d.mass = dalloc<float>(s, n, ok);
@@ -208,8 +213,9 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     d.tl = dalloc<int>(s, tcap, ok);
     d.sl_cap = (int)n;
     d.sl = dalloc<int>(s, n, ok);
+    d.tiles = dalloc<int>(s, n / TILE + 1, ok);
     d.tl_info = dalloc<int>(s, 2 * tcap, ok);
-    int* counts = dalloc<int>(s, 8, ok);
+    int* counts = dalloc<int>(s, 16, ok);
     if (ok) {
         d.wl_count = counts;
         d.nl_count = counts + 1;
@@ -219,6 +225,7 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
         d.act_count = counts + 5;
         d.dl_count = counts + 6;
         d.sl_count = counts + 7;
+        d.tile_count = counts + 8;
     }
     double* dd = dalloc<double>(s, 4, ok);
     if (ok) {
@@ -270,7 +277,7 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     cudaMemsetAsync(d.conv, 0, n, st);
     cudaMemsetAsync(d.exscale, 0, n * sizeof(float), st);
     cudaMemsetAsync(d.nrm1, 0, n * sizeof(float4), st);
-    cudaMemsetAsync(counts, 0, 8 * sizeof(int), st);
+    cudaMemsetAsync(counts, 0, 16 * sizeof(int), st);
     cudaMemsetAsync(dd, 0, 4 * sizeof(double), st);
     cudaMemsetAsync(d.viol, 0, sizeof(unsigned long long), st);
     cudaMemsetAsync(d.dirty, 0, n + 4, st);

@@ -175,6 +175,244 @@ __device__ __forceinline__ PData particle_data(const Dev& s, int p) {
     return d;
 }
 
+// ---------------------------------------------------------------- staged sweep
+// Liquid cells of interior rows, tile by tile: a persistent CTA of TILE
+// threads streams the 27 direction slices of each x-tile into shared memory
+// with bulk asynchronous copies (cp.async.bulk, completion counted on an
+// mbarrier), several tiles ahead, while its threads collide the tile in
+// hand. Even steps copy the slices [c0, c0+TILE) of every direction; odd
+// steps the shifted slices [c0 - off_q, c0 - off_q + TILE) of direction
+// opp(q), rounded down to a 16-byte boundary and widened by one 16-byte
+// word, so every copy starts and ends on 16-byte boundaries. The cells at
+// x = 0 and x = nx-1 (periodic wrap or wall) read global memory directly.
+constexpr int STAGES = 4;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait: false (and the sticky timeout bit) if the phase never completes
+__device__ __forceinline__ bool mbar_wait(const Dev& s, uint64_t* bar, unsigned parity) {
+    for (int it = 0; it < (1 << 22); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    set_error(s, ERR_TIMEOUT);
+    return false;
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+template <typename S>
+struct StagedLayout {
+    static constexpr int PAD = 16 / (int)sizeof(S);          // elements per 16-byte word
+    static constexpr int ROW = TILE + PAD;                    // elements per direction slice
+    static constexpr int STAGE_BYTES = 27 * ROW * (int)sizeof(S);
+};
+
+template <typename S, int PAR>
+__device__ __forceinline__ void staged_issue(const Dev& s, S* buf, uint64_t* full, int tile) {
+    using L = StagedLayout<S>;
+    const S* f = static_cast<const S*>(s.f);
+    const long long n = s.n;
+    const long long c0 = (long long)tile * TILE;
+    const int sxy = s.nx * s.ny;
+    if (PAR == 0) {
+        mbar_expect_tx(full, 27u * TILE * sizeof(S));
+#pragma unroll 1
+        for (int q = 0; q < 27; ++q) bulk_load(buf + q * L::ROW, f + (long long)q * n + c0, TILE * sizeof(S), full);
+    } else {
+        mbar_expect_tx(full, 27u * (TILE + L::PAD) * sizeof(S));
+#pragma unroll 1
+        for (int q = 0; q < 27; ++q) {
+            const long long a = (long long)opp(q) * n + c0 - (cx(q) + (long long)s.nx * cy(q) + (long long)sxy * cz(q));
+            const long long a0 = a & ~(long long)(L::PAD - 1);
+            bulk_load(buf + q * L::ROW, f + a0, (TILE + L::PAD) * sizeof(S), full);
+        }
+    }
+}
+
+template <typename S, int PAR>
+__global__ void __launch_bounds__(TILE) k_liquid_staged(Dev s) {
+    using L = StagedLayout<S>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    S* bufs = reinterpret_cast<S*>(smem_raw);
+    __shared__ __align__(8) uint64_t full[STAGES];
+    __shared__ __align__(8) uint64_t empty[STAGES];
+    __shared__ int abort_flag;
+    const int ntiles = *s.tile_count;
+    const int mine = ntiles > (int)blockIdx.x ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+    if (mine == 0) return;
+    const int tid = threadIdx.x;
+    const int nwarps = TILE / 32;
+    if (tid == 0) {
+        for (int k = 0; k < STAGES; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], nwarps);
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // prologue: the first STAGES tiles of this CTA
+    if (tid == 0)
+        for (int k = 0; k < STAGES && k < mine; ++k)
+            staged_issue<S, PAR>(s, bufs + k * (L::STAGE_BYTES / (int)sizeof(S)), &full[k],
+                                 s.tiles[(int)blockIdx.x + k * (int)gridDim.x]);
+    const S* fg = static_cast<const S*>(s.f);
+    S* f = static_cast<S*>(s.f);
+    const long long n = s.n;
+    const int sxy = s.nx * s.ny;
+    for (int i = 0; i < mine; ++i) {
+        const int st = i % STAGES;
+        const unsigned ph = (unsigned)(i / STAGES) & 1u;
+        const int tile = s.tiles[(int)blockIdx.x + i * (int)gridDim.x];
+        if (!mbar_wait(s, &full[st], ph)) abort_flag = 1;
+        if (abort_flag) break;
+        const S* buf = bufs + st * (L::STAGE_BYTES / (int)sizeof(S));
+        const int cell = tile * TILE + tid;
+        if ((s.flags[cell] & TYPE_MASK) == T_LIQ) {
+            int x, y, z;
+            coords(s, cell, x, y, z);
+            float v[27];
+            const bool edge = (x == 0 || x == s.nx - 1);
+            if (!edge) {
+                if (PAR == 0) {
+#pragma unroll
+                    for (int q = 0; q < 27; ++q) v[q] = Store<S>::ld(buf + q * L::ROW + tid);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 27; ++q) {
+                        // the slice of q starts PAD - rem elements before the first source
+                        const int rem = (cx(q) == 1) ? L::PAD - 1 : (cx(q) == -1 ? 1 : 0);
+                        v[q] = Store<S>::ld(buf + q * L::ROW + tid + rem);
+                    }
+                }
+            } else {
+                const NbrOffsets o = nbr_offsets(s, x, y, z);
+#pragma unroll
+                for (int q = 0; q < 27; ++q) {
+                    long long a;
+                    if (PAR == 0) {
+                        a = (long long)q * n + cell;
+                    } else {
+                        const int src = cell + o.ox[1 - cx(q)] + o.oy[1 - cy(q)] + o.oz[1 - cz(q)];
+                        a = (o.wall & wall_bits(-cx(q), -cy(q), -cz(q))) ? (long long)q * n + cell
+                                                                          : (long long)opp(q) * n + src;
+                    }
+                    v[q] = Store<S>::ld(fg + a);
+                }
+            }
+            float rho, ux, uy, uz;
+            collide(v, s.omega, s.gx, s.gy, s.gz, rho, ux, uy, uz);
+            if (PAR == 0) {
+#pragma unroll
+                for (int q = 0; q < 27; ++q) Store<S>::st(f + (long long)opp(q) * n + cell, v[q]);
+            } else if (!edge) {
+#pragma unroll
+                for (int q = 0; q < 27; ++q)
+                    Store<S>::st(f + (long long)q * n + cell + (cx(q) + s.nx * cy(q) + sxy * cz(q)), v[q]);
+            } else {
+                const NbrOffsets o = nbr_offsets(s, x, y, z);
+#pragma unroll
+                for (int q = 0; q < 27; ++q) {
+                    const int dst = cell + o.ox[1 + cx(q)] + o.oy[1 + cy(q)] + o.oz[1 + cz(q)];
+                    const long long a = (o.wall & wall_bits(cx(q), cy(q), cz(q))) ? (long long)opp(q) * n + cell
+                                                                                   : (long long)q * n + dst;
+                    Store<S>::st(f + a, v[q]);
+                }
+            }
+        }
+        // release the stage, then refill it with the tile STAGES ahead
+        __syncwarp();
+        if ((tid & 31) == 0) mbar_arrive(&empty[st]);
+        if (tid == 0 && i + STAGES < mine) {
+            if (!mbar_wait(s, &empty[st], ph)) {
+                abort_flag = 1;
+            } else {
+                staged_issue<S, PAR>(s, bufs + st * (L::STAGE_BYTES / (int)sizeof(S)), &full[st],
+                                     s.tiles[(int)blockIdx.x + (i + STAGES) * (int)gridDim.x]);
+            }
+        }
+    }
+    // copies still in flight complete before the CTA leaves
+    if (tid == 0) {
+        for (int k = 0; k < STAGES; ++k) {
+            // the last use of stage k was tile index u = largest u < mine with u % STAGES == k
+            if (k >= mine) continue;
+            const int u = k + ((mine - 1 - k) / STAGES) * STAGES;
+            mbar_wait(s, &full[k], (unsigned)(u / STAGES) & 1u);
+        }
+    }
+}
+
+// Per-thread pull-collide for the liquid cells of the rows on the y and z
+// faces (the staged kernel covers the interior rows). Row r < 2 nz: y = 0 or
+// ny-1; then y = 1..ny-2 with z = 0 or nz-1.
+template <typename S, int PAR>
+__global__ void __launch_bounds__(256, 3) k_liquid_rows(Dev s) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nrow = 2LL * s.nz + 2LL * (s.ny > 2 ? s.ny - 2 : 0);
+    if (t >= nrow * s.nx) return;
+    const int r = (int)(t / s.nx), x = (int)(t % s.nx);
+    int y, z;
+    if (r < 2 * s.nz) { z = r >> 1; y = (r & 1) ? s.ny - 1 : 0; }
+    else { const int k = r - 2 * s.nz; y = 1 + (k >> 1); z = (k & 1) ? s.nz - 1 : 0; }
+    const int cell = x + s.nx * (y + s.ny * z);
+    if ((s.flags[cell] & TYPE_MASK) != T_LIQ) return;
+    S* f = static_cast<S*>(s.f);
+    const long long n = s.n;
+    float v[27];
+    const NbrOffsets o = nbr_offsets(s, x, y, z);
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+        long long a;
+        if (PAR == 0) {
+            a = (long long)q * n + cell;
+        } else {
+            const int src = cell + o.ox[1 - cx(q)] + o.oy[1 - cy(q)] + o.oz[1 - cz(q)];
+            a = (o.wall & wall_bits(-cx(q), -cy(q), -cz(q))) ? (long long)q * n + cell : (long long)opp(q) * n + src;
+        }
+        v[q] = Store<S>::ld(f + a);
+    }
+    float rho, ux, uy, uz;
+    collide(v, s.omega, s.gx, s.gy, s.gz, rho, ux, uy, uz);
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+        long long a;
+        if (PAR == 0) {
+            a = (long long)opp(q) * n + cell;
+        } else {
+            const int dst = cell + o.ox[1 + cx(q)] + o.oy[1 + cy(q)] + o.oz[1 + cz(q)];
+            a = (o.wall & wall_bits(cx(q), cy(q), cz(q))) ? (long long)opp(q) * n + cell : (long long)q * n + dst;
+        }
+        Store<S>::st(f + a, v[q]);
+    }
+}
+
 // Moving bounce-back and momentum exchange (Section 2.2), from the solid
 // side: for every surface solid cell s (owner p) and every fluid neighbour
 // x = s + c_q, the PDF x will pull from s in direction q is
@@ -372,17 +610,51 @@ __global__ void __launch_bounds__(128) k_interface(Dev s) {
     }
 }
 
+// CTAs of the staged sweep: as many as fit on the SMs at once (shared
+// memory is the limit), set up once per storage format
+template <typename S>
+static int staged_blocks() {
+    static int blocks = 0;
+    if (blocks == 0) {
+        const int smem = STAGES * StagedLayout<S>::STAGE_BYTES;
+        cudaFuncSetAttribute(k_liquid_staged<S, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_liquid_staged<S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_liquid_staged<S, 1>, TILE, smem);
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        blocks = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+    }
+    return blocks;
+}
+
 template <typename S>
 static void launch_typed(const Dev& s, int parity, cudaStream_t st) {
     const int bl = blocks_for(s.n, 256);
     const int lb = 152 * 8;
+    const bool staged = (s.nx % TILE) == 0 && s.ny >= 3 && s.nz >= 3;
+    const long long nrow = 2LL * s.nz + 2LL * (s.ny - 2);
+    const int rb = (int)((nrow * s.nx + 255) / 256);
+    const size_t smem = (size_t)STAGES * StagedLayout<S>::STAGE_BYTES;
+    const int sb = staged_blocks<S>();
     if (parity == 0) {
         if (s.np > 0) k_solid_links<S, 0><<<lb, 256, 0, st>>>(s);
-        k_liquid<S, 0><<<bl, 256, 0, st>>>(s);
+        if (staged) {
+            k_liquid_staged<S, 0><<<sb, TILE, smem, st>>>(s);
+            k_liquid_rows<S, 0><<<rb, 256, 0, st>>>(s);
+        } else {
+            k_liquid<S, 0><<<bl, 256, 0, st>>>(s);
+        }
         k_interface<S, 0><<<lb, 128, 0, st>>>(s);
     } else {
         if (s.np > 0) k_solid_links<S, 1><<<lb, 256, 0, st>>>(s);
-        k_liquid<S, 1><<<bl, 256, 0, st>>>(s);
+        if (staged) {
+            k_liquid_staged<S, 1><<<sb, TILE, smem, st>>>(s);
+            k_liquid_rows<S, 1><<<rb, 256, 0, st>>>(s);
+        } else {
+            k_liquid<S, 1><<<bl, 256, 0, st>>>(s);
+        }
         k_interface<S, 1><<<lb, 128, 0, st>>>(s);
     }
 }
@@ -391,7 +663,8 @@ int launch_stream_collide(const Dev& s, int parity, cudaStream_t st) {
     if (s.storage == FSLBM_STORE_FP32) launch_typed<float>(s, parity, st);
     else if (s.storage == FSLBM_STORE_FP16) launch_typed<__half>(s, parity, st);
     else launch_typed<__nv_bfloat16>(s, parity, st);
-    return s.np > 0 ? 3 : 2;
+    const bool staged = (s.nx % TILE) == 0 && s.ny >= 3 && s.nz >= 3;
+    return (s.np > 0 ? 1 : 0) + (staged ? 3 : 2);
 }
 
 }  // namespace fsl

@@ -317,41 +317,109 @@ int launch_conversion(const Dev& s, int last_parity, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------ work lists
-// Whether any of the 27 cells around a cell is liquid or interface, as a
-// separable OR: along x from the flags, then along y, then along z (cells
-// beyond a wall face count as not fluid).
-__global__ void k_fluid_or_x(Dev s, uint8_t* out) {
-    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= s.n) return;
-    int x, y, z;
-    coords(s, c, x, y, z);
-    uint8_t v = 0;
+// Block-aggregated append of up to SEG items per thread (one atomic per
+// block). Every thread of the block must call it.
+template <int SEG>
+__device__ __forceinline__ void block_append_multi(const Dev& s, const int (&items)[SEG], int nitems, int* list,
+                                                   int* count, int cap) {
+    __shared__ int warp_tot[32];
+    __shared__ int block_base;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = nitems;
 #pragma unroll
-    for (int d = -1; d <= 1; ++d) {
-        const int a = shift(x, d, s.nx, s.per_x);
-        if (a < 0) continue;
-        const int t = s.flags[c - x + a] & TYPE_MASK;
-        v |= (t == T_LIQ || t == T_IFC) ? 1 : 0;
+    for (int off = 1; off < 32; off <<= 1) {
+        const int t = __shfl_up_sync(full, incl, off);
+        if (lane >= off) incl += t;
     }
-    out[c] = v;
-}
-__global__ void k_fluid_or_y(Dev s, const uint8_t* in, uint8_t* out) {
-    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= s.n) return;
-    int x, y, z;
-    coords(s, c, x, y, z);
-    uint8_t v = 0;
-#pragma unroll
-    for (int d = -1; d <= 1; ++d) {
-        const int b = shift(y, d, s.ny, s.per_y);
-        if (b >= 0) v |= in[c + (long long)(b - y) * s.nx];
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            const int c = warp_tot[w];
+            warp_tot[w] = tot;
+            tot += c;
+        }
+        block_base = tot ? atomicAdd(count, tot) : 0;
     }
-    out[c] = v;
+    __syncthreads();
+    const int start = block_base + warp_tot[wid] + incl - nitems;
+    for (int k = 0; k < nitems; ++k) {
+        if (start + k < cap) list[start + k] = items[k];
+        else set_error(s, ERR_CAPACITY);
+    }
+    __syncthreads();
 }
 
+constexpr int CLS_SEG = 16;
+
 // Lists the interface cells and the solid cells with a liquid or interface
-// neighbour (the OR along z completes the 27-cell neighbourhood).
-__global__ void k_classify(Dev s, const uint8_t* ory) {
+// cell among their 26 neighbours. One thread per 16 consecutive cells of a
+// row (nx a multiple of 16): the 3x3 rows around the segment are read as
+// 16-byte words plus the two halo bytes, the fluid bits ORed along x and
+// over the nine rows.
+__global__ void k_classify_seg(Dev s) {
+    const long long seg = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nseg = s.n / CLS_SEG;
+    int ifc_items[CLS_SEG], sol_items[CLS_SEG];
+    int nifc = 0, nsol = 0;
+    if (seg < nseg) {
+        const long long c0 = seg * CLS_SEG;
+        int x0, y, z;
+        coords(s, c0, x0, y, z);
+        // fluid bits of the segment's own row, then the OR over the 9 rows
+        unsigned own_t[CLS_SEG / 4];
+        unsigned orr = 0;   // bits 0..17 <-> x0-1 .. x0+16
+#pragma unroll
+        for (int dz = -1; dz <= 1; ++dz) {
+            const int zz = shift(z, dz, s.nz, s.per_z);
+            if (zz < 0) continue;
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int yy = shift(y, dy, s.ny, s.per_y);
+                if (yy < 0) continue;
+                const long long row = (long long)s.nx * (yy + (long long)s.ny * zz);
+                const uint4 w = *reinterpret_cast<const uint4*>(s.flags + row + x0);
+                const unsigned wd[4] = {w.x, w.y, w.z, w.w};
+                unsigned bits = 0;
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const unsigned t = (wd[k >> 2] >> (8 * (k & 3))) & TYPE_MASK;
+                    bits |= (t == T_LIQ || t == T_IFC) ? (1u << (k + 1)) : 0u;
+                }
+                const int xl = shift(x0, -1, s.nx, s.per_x), xr = shift(x0 + 15, 1, s.nx, s.per_x);
+                if (xl >= 0) {
+                    const unsigned t = s.flags[row + xl] & TYPE_MASK;
+                    bits |= (t == T_LIQ || t == T_IFC) ? 1u : 0u;
+                }
+                if (xr >= 0) {
+                    const unsigned t = s.flags[row + xr] & TYPE_MASK;
+                    bits |= (t == T_LIQ || t == T_IFC) ? (1u << 17) : 0u;
+                }
+                orr |= bits;
+                if (dz == 0 && dy == 0) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) own_t[k] = wd[k];
+                }
+            }
+        }
+        // x-neighbourhood: bit k+1 of (orr | orr>>1 | orr<<1) covers x0+k-1..x0+k+1
+        const unsigned nb = orr | (orr >> 1) | (orr << 1);
+#pragma unroll
+        for (int k = 0; k < CLS_SEG; ++k) {
+            const unsigned t = (own_t[k >> 2] >> (8 * (k & 3))) & TYPE_MASK;
+            if (t == T_IFC) ifc_items[nifc++] = (int)(c0 + k);
+            else if (t == T_SOL && ((nb >> (k + 1)) & 1u)) sol_items[nsol++] = (int)(c0 + k);
+        }
+    }
+    block_append_multi<CLS_SEG>(s, ifc_items, nifc, s.wl, s.wl_count, s.wl_cap);
+    block_append_multi<CLS_SEG>(s, sol_items, nsol, s.sl, s.sl_count, s.sl_cap);
+}
+
+// Fallback for lattices whose x extent is not a multiple of 16: one thread
+// per cell, 26 neighbour reads for solid cells.
+__global__ void k_classify(Dev s) {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool in = c < s.n;
     int t = 0;
@@ -361,13 +429,19 @@ __global__ void k_classify(Dev s, const uint8_t* ory) {
         if (t == T_SOL) {
             int x, y, z;
             coords(s, c, x, y, z);
-            uint8_t v = 0;
+            const int xs[3] = {shift(x, -1, s.nx, s.per_x), x, shift(x, 1, s.nx, s.per_x)};
+            const int ys[3] = {shift(y, -1, s.ny, s.per_y), y, shift(y, 1, s.ny, s.per_y)};
+            const int zs[3] = {shift(z, -1, s.nz, s.per_z), z, shift(z, 1, s.nz, s.per_z)};
+            unsigned any = 0;
 #pragma unroll
-            for (int d = -1; d <= 1; ++d) {
-                const int e = shift(z, d, s.nz, s.per_z);
-                if (e >= 0) v |= ory[c + (long long)(e - z) * s.nx * s.ny];
+            for (int q = 0; q < 27; ++q) {
+                if (q == 13) continue;
+                const int a = xs[1 + cx(q)], b = ys[1 + cy(q)], d = zs[1 + cz(q)];
+                if (a < 0 || b < 0 || d < 0) continue;
+                const int tn = s.flags[a + (long long)s.nx * (b + (long long)s.ny * d)] & TYPE_MASK;
+                any |= (tn == T_LIQ || tn == T_IFC) ? 1u : 0u;
             }
-            surf = v != 0;
+            surf = any != 0;
         }
     }
     block_append(s, in && t == T_IFC, (int)c, s.wl, s.wl_count, s.wl_cap);
@@ -399,15 +473,52 @@ __global__ void k_clamp_count(Dev s) {
     if (*s.sl_count > s.sl_cap) *s.sl_count = s.sl_cap;
 }
 
+// x-tiles of TILE cells in rows away from the y and z faces that hold at
+// least one liquid cell (these go through the staged stream-collide)
+__global__ void k_tiles(Dev s) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long ntile = s.n / TILE;
+    bool act = false;
+    if (t < ntile) {
+        const long long c0 = t * TILE;
+        int x0, y, z;
+        coords(s, c0, x0, y, z);
+        if (y > 0 && y < s.ny - 1 && z > 0 && z < s.nz - 1) {
+            const uint4* w = reinterpret_cast<const uint4*>(s.flags + c0);
+            unsigned any = 0;
+#pragma unroll
+            for (int k = 0; k < TILE / 16; ++k) {
+                const uint4 v = w[k];
+                const unsigned wd[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    // a byte holds a liquid cell when its type bits are 01
+                    const unsigned lo = wd[j] & 0x03030303u;
+                    any |= (lo ^ 0x01010101u) - 0x01010101u & ~(lo ^ 0x01010101u) & 0x80808080u;
+                }
+            }
+            act = any != 0;
+        }
+    }
+    block_append(s, act, (int)t, s.tiles, s.tile_count, (int)(s.n / TILE));
+}
+
 int launch_classify(const Dev& s, cudaStream_t st) {
     cudaMemsetAsync(s.wl_count, 0, sizeof(int), st);
     cudaMemsetAsync(s.sl_count, 0, sizeof(int), st);
-    const int bl = blocks_for(s.n, 256);
-    k_fluid_or_x<<<bl, 256, 0, st>>>(s, s.scratch_a);
-    k_fluid_or_y<<<bl, 256, 0, st>>>(s, s.scratch_a, s.scratch_b);
-    k_classify<<<bl, 256, 0, st>>>(s, s.scratch_b);
+    if (s.nx % CLS_SEG == 0) {
+        k_classify_seg<<<blocks_for(s.n / CLS_SEG, 128), 128, 0, st>>>(s);
+    } else {
+        k_classify<<<blocks_for(s.n, 256), 256, 0, st>>>(s);
+    }
     k_clamp_count<<<1, 1, 0, st>>>(s);
-    return 4;
+    int k = 2;
+    if (s.nx % TILE == 0) {
+        cudaMemsetAsync(s.tile_count, 0, sizeof(int), st);
+        k_tiles<<<blocks_for(s.n / TILE, 256), 256, 0, st>>>(s);
+        ++k;
+    }
+    return k;
 }
 
 __global__ void k_cell_counts(Dev s, unsigned long long* out) {
