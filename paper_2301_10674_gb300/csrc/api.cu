@@ -163,6 +163,11 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     d.per_y = (p->bc_flags & FSLBM_PERIODIC_Y) ? 1 : 0;
     d.per_z = (p->bc_flags & FSLBM_PERIODIC_Z) ? 1 : 0;
     d.n = n;
+    for (int q = 0; q < 27; ++q) {
+        const long long off = fsl::cx(q) + (long long)p->nx * fsl::cy(q) + (long long)p->nx * p->ny * fsl::cz(q);
+        d.pull_off[q] = (long long)fsl::opp(q) * n - off;
+        d.push_off[q] = (long long)q * n + off;
+    }
     d.omega = (float)p->omega;
     d.gx = (float)p->g[0]; d.gy = (float)p->g[1]; d.gz = (float)p->g[2];
     d.gxd = p->g[0]; d.gyd = p->g[1]; d.gzd = p->g[2];

@@ -59,6 +59,11 @@ struct Dev {
     float rho_gas, eps_conv, eps_normal;
     int recon_normal;
     int storage;
+    // element offsets of an odd step for interior cells: the pull of
+    // direction q reads f[cell + pull_off[q]], the push writes
+    // f[cell + push_off[q]] (constant per launch, held in the parameter bank)
+    long long pull_off[27];
+    long long push_off[27];
     // PDFs (f - w), AA pattern, direction-major [27][n]; side buffer of the
     // interface cells' own post-collision PDFs (same format)
     void* f;

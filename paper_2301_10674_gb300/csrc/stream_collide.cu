@@ -83,8 +83,7 @@ __global__ void __launch_bounds__(256, 3) k_liquid(Dev s) {
     if (interior) {
         S* fc = f + cell;
 #pragma unroll
-        for (int q = 0; q < 27; ++q)
-            v[q] = Store<S>::ld(fc + ((long long)opp(q) * n - (cx(q) + s.nx * cy(q) + sxy * cz(q))));
+        for (int q = 0; q < 27; ++q) v[q] = Store<S>::ld(fc + s.pull_off[q]);
     } else {
         const NbrOffsets o = nbr_offsets(s, x, y, z);
 #pragma unroll
@@ -101,8 +100,7 @@ __global__ void __launch_bounds__(256, 3) k_liquid(Dev s) {
     if (interior) {
         S* fc = f + cell;
 #pragma unroll
-        for (int q = 0; q < 27; ++q)
-            Store<S>::st(fc + ((long long)q * n + (cx(q) + s.nx * cy(q) + sxy * cz(q))), v[q]);
+        for (int q = 0; q < 27; ++q) Store<S>::st(fc + s.push_off[q], v[q]);
     } else {
         const NbrOffsets o = nbr_offsets(s, x, y, z);
 #pragma unroll
@@ -185,7 +183,7 @@ __device__ __forceinline__ PData particle_data(const Dev& s, int p) {
 // opp(q), rounded down to a 16-byte boundary and widened by one 16-byte
 // word, so every copy starts and ends on 16-byte boundaries. The cells at
 // x = 0 and x = nx-1 (periodic wrap or wall) read global memory directly.
-constexpr int STAGES = 4;
+constexpr int STAGES = 3;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
     return static_cast<unsigned>(__cvta_generic_to_shared(p));
@@ -282,7 +280,6 @@ __global__ void __launch_bounds__(TILE) k_liquid_staged(Dev s) {
         for (int k = 0; k < STAGES && k < mine; ++k)
             staged_issue<S, PAR>(s, bufs + k * (L::STAGE_BYTES / (int)sizeof(S)), &full[k],
                                  s.tiles[(int)blockIdx.x + k * (int)gridDim.x]);
-    const S* fg = static_cast<const S*>(s.f);
     S* f = static_cast<S*>(s.f);
     const long long n = s.n;
     const int sxy = s.nx * s.ny;
@@ -294,36 +291,19 @@ __global__ void __launch_bounds__(TILE) k_liquid_staged(Dev s) {
         if (abort_flag) break;
         const S* buf = bufs + st * (L::STAGE_BYTES / (int)sizeof(S));
         const int cell = tile * TILE + tid;
-        if ((s.flags[cell] & TYPE_MASK) == T_LIQ) {
-            int x, y, z;
-            coords(s, cell, x, y, z);
+        const int x = cell % s.nx;
+        // the cells at x = 0 and x = nx-1 belong to the row kernel
+        if (x != 0 && x != s.nx - 1 && (s.flags[cell] & TYPE_MASK) == T_LIQ) {
             float v[27];
-            const bool edge = (x == 0 || x == s.nx - 1);
-            if (!edge) {
-                if (PAR == 0) {
+            if (PAR == 0) {
 #pragma unroll
-                    for (int q = 0; q < 27; ++q) v[q] = Store<S>::ld(buf + q * L::ROW + tid);
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 27; ++q) {
-                        // the slice of q starts PAD - rem elements before the first source
-                        const int rem = (cx(q) == 1) ? L::PAD - 1 : (cx(q) == -1 ? 1 : 0);
-                        v[q] = Store<S>::ld(buf + q * L::ROW + tid + rem);
-                    }
-                }
+                for (int q = 0; q < 27; ++q) v[q] = Store<S>::ld(buf + q * L::ROW + tid);
             } else {
-                const NbrOffsets o = nbr_offsets(s, x, y, z);
 #pragma unroll
                 for (int q = 0; q < 27; ++q) {
-                    long long a;
-                    if (PAR == 0) {
-                        a = (long long)q * n + cell;
-                    } else {
-                        const int src = cell + o.ox[1 - cx(q)] + o.oy[1 - cy(q)] + o.oz[1 - cz(q)];
-                        a = (o.wall & wall_bits(-cx(q), -cy(q), -cz(q))) ? (long long)q * n + cell
-                                                                          : (long long)opp(q) * n + src;
-                    }
-                    v[q] = Store<S>::ld(fg + a);
+                    // the slice of q starts rem elements before the first source
+                    const int rem = (cx(q) == 1) ? L::PAD - 1 : (cx(q) == -1 ? 1 : 0);
+                    v[q] = Store<S>::ld(buf + q * L::ROW + tid + rem);
                 }
             }
             float rho, ux, uy, uz;
@@ -331,19 +311,10 @@ __global__ void __launch_bounds__(TILE) k_liquid_staged(Dev s) {
             if (PAR == 0) {
 #pragma unroll
                 for (int q = 0; q < 27; ++q) Store<S>::st(f + (long long)opp(q) * n + cell, v[q]);
-            } else if (!edge) {
-#pragma unroll
-                for (int q = 0; q < 27; ++q)
-                    Store<S>::st(f + (long long)q * n + cell + (cx(q) + s.nx * cy(q) + sxy * cz(q)), v[q]);
             } else {
-                const NbrOffsets o = nbr_offsets(s, x, y, z);
+                S* fc = f + cell;
 #pragma unroll
-                for (int q = 0; q < 27; ++q) {
-                    const int dst = cell + o.ox[1 + cx(q)] + o.oy[1 + cy(q)] + o.oz[1 + cz(q)];
-                    const long long a = (o.wall & wall_bits(cx(q), cy(q), cz(q))) ? (long long)opp(q) * n + cell
-                                                                                   : (long long)q * n + dst;
-                    Store<S>::st(f + a, v[q]);
-                }
+                for (int q = 0; q < 27; ++q) Store<S>::st(fc + s.push_off[q], v[q]);
             }
         }
         // release the stage, then refill it with the tile STAGES ahead
@@ -370,17 +341,30 @@ __global__ void __launch_bounds__(TILE) k_liquid_staged(Dev s) {
 }
 
 // Per-thread pull-collide for the liquid cells of the rows on the y and z
-// faces (the staged kernel covers the interior rows). Row r < 2 nz: y = 0 or
-// ny-1; then y = 1..ny-2 with z = 0 or nz-1.
+// faces and for the cells at x = 0 and x = nx-1 of the other rows (the
+// staged kernel covers the rest). Row r < 2 nz: y = 0 or ny-1; then
+// y = 1..ny-2 with z = 0 or nz-1; then the two end cells of each interior row.
 template <typename S, int PAR>
 __global__ void __launch_bounds__(256, 3) k_liquid_rows(Dev s) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nrow = 2LL * s.nz + 2LL * (s.ny > 2 ? s.ny - 2 : 0);
-    if (t >= nrow * s.nx) return;
-    const int r = (int)(t / s.nx), x = (int)(t % s.nx);
-    int y, z;
-    if (r < 2 * s.nz) { z = r >> 1; y = (r & 1) ? s.ny - 1 : 0; }
-    else { const int k = r - 2 * s.nz; y = 1 + (k >> 1); z = (k & 1) ? s.nz - 1 : 0; }
+    const long long nedge = 2LL * (s.ny - 2) * (s.nz - 2);
+    int x, y, z;
+    if (t < nrow * s.nx) {
+        const int r = (int)(t / s.nx);
+        x = (int)(t % s.nx);
+        if (r < 2 * s.nz) { z = r >> 1; y = (r & 1) ? s.ny - 1 : 0; }
+        else { const int k = r - 2 * s.nz; y = 1 + (k >> 1); z = (k & 1) ? s.nz - 1 : 0; }
+    } else if (t < nrow * s.nx + nedge) {
+        // x = 0 and x = nx-1 of the interior rows
+        const long long k = t - nrow * s.nx;
+        x = (k & 1) ? s.nx - 1 : 0;
+        const long long r = k >> 1;
+        y = 1 + (int)(r % (s.ny - 2));
+        z = 1 + (int)(r / (s.ny - 2));
+    } else {
+        return;
+    }
     const int cell = x + s.nx * (y + s.ny * z);
     if ((s.flags[cell] & TYPE_MASK) != T_LIQ) return;
     S* f = static_cast<S*>(s.f);
@@ -635,7 +619,7 @@ static void launch_typed(const Dev& s, int parity, cudaStream_t st) {
     const int lb = 152 * 8;
     const bool staged = (s.nx % TILE) == 0 && s.ny >= 3 && s.nz >= 3;
     const long long nrow = 2LL * s.nz + 2LL * (s.ny - 2);
-    const int rb = (int)((nrow * s.nx + 255) / 256);
+    const int rb = (int)((nrow * s.nx + 2LL * (s.ny - 2) * (s.nz - 2) + 255) / 256);
     const size_t smem = (size_t)STAGES * StagedLayout<S>::STAGE_BYTES;
     const int sb = staged_blocks<S>();
     if (parity == 0) {
