@@ -228,7 +228,8 @@ template <typename S>
 struct StagedLayout {
     static constexpr int PAD = 16 / (int)sizeof(S);          // elements per 16-byte word
     static constexpr int ROW = TILE + PAD;                    // elements per direction slice
-    static constexpr int STAGE_BYTES = 27 * ROW * (int)sizeof(S);
+    static constexpr int PDF_BYTES = 27 * ROW * (int)sizeof(S);
+    static constexpr int STAGE_BYTES = PDF_BYTES + TILE;      // + the tile's flag bytes
 };
 
 template <typename S, int PAR>
@@ -238,12 +239,15 @@ __device__ __forceinline__ void staged_issue(const Dev& s, S* buf, uint64_t* ful
     const long long n = s.n;
     const long long c0 = (long long)tile * TILE;
     const int sxy = s.nx * s.ny;
+    unsigned char* fl = reinterpret_cast<unsigned char*>(buf) + L::PDF_BYTES;
     if (PAR == 0) {
-        mbar_expect_tx(full, 27u * TILE * sizeof(S));
+        mbar_expect_tx(full, 27u * TILE * sizeof(S) + TILE);
+        bulk_load(fl, s.flags + c0, TILE, full);
 #pragma unroll 1
         for (int q = 0; q < 27; ++q) bulk_load(buf + q * L::ROW, f + (long long)q * n + c0, TILE * sizeof(S), full);
     } else {
-        mbar_expect_tx(full, 27u * (TILE + L::PAD) * sizeof(S));
+        mbar_expect_tx(full, 27u * (TILE + L::PAD) * sizeof(S) + TILE);
+        bulk_load(fl, s.flags + c0, TILE, full);
 #pragma unroll 1
         for (int q = 0; q < 27; ++q) {
             const long long a = (long long)opp(q) * n + c0 - (cx(q) + (long long)s.nx * cy(q) + (long long)sxy * cz(q));
@@ -260,6 +264,7 @@ __global__ void __launch_bounds__(TILE) k_liquid_staged(Dev s) {
     S* bufs = reinterpret_cast<S*>(smem_raw);
     __shared__ __align__(8) uint64_t full[STAGES];
     __shared__ __align__(8) uint64_t empty[STAGES];
+    __shared__ int stage_tile[STAGES];
     __shared__ int abort_flag;
     const int ntiles = *s.tile_count;
     const int mine = ntiles > (int)blockIdx.x ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
@@ -277,23 +282,26 @@ __global__ void __launch_bounds__(TILE) k_liquid_staged(Dev s) {
     __syncthreads();
     // prologue: the first STAGES tiles of this CTA
     if (tid == 0)
-        for (int k = 0; k < STAGES && k < mine; ++k)
-            staged_issue<S, PAR>(s, bufs + k * (L::STAGE_BYTES / (int)sizeof(S)), &full[k],
-                                 s.tiles[(int)blockIdx.x + k * (int)gridDim.x]);
+        for (int k = 0; k < STAGES && k < mine; ++k) {
+            const int t = s.tiles[(int)blockIdx.x + k * (int)gridDim.x];
+            stage_tile[k] = t;
+            staged_issue<S, PAR>(s, bufs + k * (L::STAGE_BYTES / (int)sizeof(S)), &full[k], t);
+        }
     S* f = static_cast<S*>(s.f);
     const long long n = s.n;
     const int sxy = s.nx * s.ny;
     for (int i = 0; i < mine; ++i) {
         const int st = i % STAGES;
         const unsigned ph = (unsigned)(i / STAGES) & 1u;
-        const int tile = s.tiles[(int)blockIdx.x + i * (int)gridDim.x];
         if (!mbar_wait(s, &full[st], ph)) abort_flag = 1;
         if (abort_flag) break;
         const S* buf = bufs + st * (L::STAGE_BYTES / (int)sizeof(S));
+        const unsigned char* fl = reinterpret_cast<const unsigned char*>(buf) + L::PDF_BYTES;
+        const int tile = stage_tile[st];
         const int cell = tile * TILE + tid;
         const int x = cell % s.nx;
         // the cells at x = 0 and x = nx-1 belong to the row kernel
-        if (x != 0 && x != s.nx - 1 && (s.flags[cell] & TYPE_MASK) == T_LIQ) {
+        if (x != 0 && x != s.nx - 1 && (fl[tid] & TYPE_MASK) == T_LIQ) {
             float v[27];
             if (PAR == 0) {
 #pragma unroll
@@ -324,8 +332,9 @@ __global__ void __launch_bounds__(TILE) k_liquid_staged(Dev s) {
             if (!mbar_wait(s, &empty[st], ph)) {
                 abort_flag = 1;
             } else {
-                staged_issue<S, PAR>(s, bufs + st * (L::STAGE_BYTES / (int)sizeof(S)), &full[st],
-                                     s.tiles[(int)blockIdx.x + (i + STAGES) * (int)gridDim.x]);
+                const int t = s.tiles[(int)blockIdx.x + (i + STAGES) * (int)gridDim.x];
+                stage_tile[st] = t;
+                staged_issue<S, PAR>(s, bufs + st * (L::STAGE_BYTES / (int)sizeof(S)), &full[st], t);
             }
         }
     }
