@@ -232,6 +232,24 @@ __global__ void k_dem_neighbours(Dev s) {
     s.nb_count[p] = cnt;
 }
 
+// FP32 copies of the particle state used by the lattice kernels
+__global__ void k_particle_copies(Dev s) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= s.np) return;
+    const double X = s.X[3 * p], Y = s.X[3 * p + 1], Z = s.X[3 * p + 2];
+    const double r = s.R[p];
+    s.Xr[p] = make_float4((float)X, (float)Y, (float)Z, s.fixed[p] ? -(float)r : (float)r);
+    const double fx = floor(X), fy = floor(Y), fz = floor(Z);
+    s.Xi[p] = make_int4((int)fx, (int)fy, (int)fz, 0);
+    s.Xfr[p] = make_float4((float)(X - fx), (float)(Y - fy), (float)(Z - fz), 0.f);
+    s.Uf[p] = make_float4((float)s.U[3 * p], (float)s.U[3 * p + 1], (float)s.U[3 * p + 2], 0.f);
+    s.Wf[p] = make_float4((float)s.W[3 * p], (float)s.W[3 * p + 1], (float)s.W[3 * p + 2], 0.f);
+}
+
+void launch_particle_copies(const Dev& s, cudaStream_t st) {
+    if (s.np > 0) k_particle_copies<<<blocks_for(s.np, 128), 128, 0, st>>>(s);
+}
+
 // One DEM sub-step with a warp per particle: the lanes take the entries of
 // the neighbour list and the walls (one contact each, so the FP64 chains run
 // side by side), the history slots are shared across the warp and new
