@@ -122,37 +122,6 @@ __global__ void k_force_avg(Dev s, int have_prev) {
     s.Tp[k] = th;
 }
 
-__device__ __forceinline__ void cross3(const double a[3], const double b[3], double c[3]) {
-    c[0] = a[1] * b[2] - a[2] * b[1];
-    c[1] = a[2] * b[0] - a[0] * b[2];
-    c[2] = a[0] * b[1] - a[1] * b[0];
-}
-
-// linear spring-dashpot with tangential history; returns the force on the
-// particle, updates xi; n points from the particle to its partner
-__device__ void contact(const Dev& s, double meff, const double n[3], double delta, const double vrel[3],
-                        double* xi, double dts, double F[3], double Ft[3]) {
-    const double kn = meff * s.kn_coef;
-    const double dn = meff * s.dn_coef;
-    const double kt = kn * s.kt_ratio;
-    const double dt_ = dn;
-    double vn = vrel[0] * n[0] + vrel[1] * n[1] + vrel[2] * n[2];
-    double vt[3] = {vrel[0] - vn * n[0], vrel[1] - vn * n[1], vrel[2] - vn * n[2]};
-    double fn = kn * delta + dn * vn;
-    double xn = xi[0] * n[0] + xi[1] * n[1] + xi[2] * n[2];
-    for (int a = 0; a < 3; ++a) xi[a] = xi[a] - xn * n[a] + vt[a] * dts;
-    for (int a = 0; a < 3; ++a) Ft[a] = -kt * xi[a] - dt_ * vt[a];
-    double ftl = sqrt(Ft[0] * Ft[0] + Ft[1] * Ft[1] + Ft[2] * Ft[2]);
-    double lim = s.friction * fabs(fn);
-    if (ftl > lim && ftl > 0.0) {
-        for (int a = 0; a < 3; ++a) {
-            Ft[a] = lim * Ft[a] / ftl;
-            xi[a] = -(Ft[a] + dt_ * vt[a]) / kt;
-        }
-    }
-    for (int a = 0; a < 3; ++a) F[a] = -fn * n[a] + Ft[a];
-}
-
 __device__ __forceinline__ int hist_slot(const Dev& s, int p, int partner, unsigned& seen) {
     int* hp = s.hist_partner + (long long)p * HIST_SLOTS;
     int freeslot = -1;
@@ -250,158 +219,128 @@ void launch_particle_copies(const Dev& s, cudaStream_t st) {
     if (s.np > 0) k_particle_copies<<<blocks_for(s.np, 128), 128, 0, st>>>(s);
 }
 
-// One DEM sub-step with a warp per particle: the lanes take the entries of
-// the neighbour list and the walls (one contact each, so the FP64 chains run
-// side by side), the history slots are shared across the warp and new
-// contacts get free slots by rank, forces and torques are summed with warp
-// shuffles, and lane 0 integrates.
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    return v;
+// FP32 linear spring-dashpot with tangential history (same law as above);
+// the offsets come in from FP64 differences, forces are summed in FP64
+__device__ void contact_f(const Dev& s, float meff, const float n[3], float delta, const float vrel[3], double* xi,
+                          float dts, float F[3], float Ft[3]) {
+    const float kn = meff * (float)s.kn_coef;
+    const float dn = meff * (float)s.dn_coef;
+    const float kt = kn * (float)s.kt_ratio;
+    const float dt_ = dn;
+    const float vn = vrel[0] * n[0] + vrel[1] * n[1] + vrel[2] * n[2];
+    const float vt[3] = {vrel[0] - vn * n[0], vrel[1] - vn * n[1], vrel[2] - vn * n[2]};
+    const float fn = kn * delta + dn * vn;
+    float x[3] = {(float)xi[0], (float)xi[1], (float)xi[2]};
+    const float xn = x[0] * n[0] + x[1] * n[1] + x[2] * n[2];
+    for (int a = 0; a < 3; ++a) x[a] = x[a] - xn * n[a] + vt[a] * dts;
+    for (int a = 0; a < 3; ++a) Ft[a] = -kt * x[a] - dt_ * vt[a];
+    const float ftl = sqrtf(Ft[0] * Ft[0] + Ft[1] * Ft[1] + Ft[2] * Ft[2]);
+    const float lim = (float)s.friction * fabsf(fn);
+    if (ftl > lim && ftl > 0.f) {
+        const float sc = lim / ftl;
+        for (int a = 0; a < 3; ++a) {
+            Ft[a] *= sc;
+            x[a] = -(Ft[a] + dt_ * vt[a]) / kt;
+        }
+    }
+    for (int a = 0; a < 3; ++a) {
+        xi[a] = x[a];
+        F[a] = -fn * n[a] + Ft[a];
+    }
 }
 
-__global__ void __launch_bounds__(128) k_dem_substep_warp(Dev s, const double* __restrict__ Xa,
-                                                         const double* __restrict__ Ua,
-                                                         const double* __restrict__ Wa, double* Xb, double* Ub,
-                                                         double* Wb, double dts, int last) {
-    const unsigned full = 0xffffffffu;
-    const int p = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (p >= s.np) return;                       // warp-uniform
+// One DEM sub-step, a thread per particle over its neighbour list and the
+// walls: contact law in FP32 on offsets formed in FP64, forces and torques
+// summed in FP64, semi-implicit Euler in FP64.
+__global__ void __launch_bounds__(64) k_dem_substep(Dev s, const double* __restrict__ Xa,
+                                                   const double* __restrict__ Ua, const double* __restrict__ Wa,
+                                                   double* Xb, double* Ub, double* Wb, double dts, int last) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= s.np) return;
     double X[3] = {Xa[3 * p], Xa[3 * p + 1], Xa[3 * p + 2]};
     double U[3] = {Ua[3 * p], Ua[3 * p + 1], Ua[3 * p + 2]};
     double W[3] = {Wa[3 * p], Wa[3 * p + 1], Wa[3 * p + 2]};
     if (s.fixed[p]) {
-        if (lane < 3) { Xb[3 * p + lane] = X[lane]; Ub[3 * p + lane] = U[lane]; Wb[3 * p + lane] = W[lane]; }
+        for (int a = 0; a < 3; ++a) { Xb[3 * p + a] = X[a]; Ub[3 * p + a] = U[a]; Wb[3 * p + a] = W[a]; }
         return;
     }
     const double ri = s.R[p], mi = s.M[p], Ii = s.I[p];
+    const float rif = (float)ri, mif = (float)mi, dtf = (float)dts;
+    const float Uf[3] = {(float)U[0], (float)U[1], (float)U[2]};
+    const float Wf[3] = {(float)W[0], (float)W[1], (float)W[2]};
+    double F[3] = {s.Fa[3 * p] + mi * s.gxd, s.Fa[3 * p + 1] + mi * s.gyd, s.Fa[3 * p + 2] + mi * s.gzd};
+    double T[3] = {s.Ta[3 * p], s.Ta[3 * p + 1], s.Ta[3 * p + 2]};
+    unsigned seen = 0;
+    const int nbc = s.nb_count[p];
+    for (int k = 0; k < nbc; ++k) {
+        const int j = s.nb[(long long)p * NB_SLOTS + k];
+        const float d[3] = {(float)wrapd(Xa[3 * j] - X[0], s.nx, s.per_x),
+                            (float)wrapd(Xa[3 * j + 1] - X[1], s.ny, s.per_y),
+                            (float)wrapd(Xa[3 * j + 2] - X[2], s.nz, s.per_z)};
+        const float rjf = (float)s.R[j];
+        const float dist2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        const float rs = rif + rjf;
+        if (dist2 >= rs * rs) continue;
+        const float dist = sqrtf(dist2);
+        const float inv = 1.f / dist;
+        const float n[3] = {d[0] * inv, d[1] * inv, d[2] * inv};
+        const float delta = rs - dist;
+        float wsum[3];
+        for (int a = 0; a < 3; ++a) wsum[a] = rif * Wf[a] + rjf * (float)Wa[3 * j + a];
+        const float wn[3] = {wsum[1] * n[2] - wsum[2] * n[1], wsum[2] * n[0] - wsum[0] * n[2],
+                             wsum[0] * n[1] - wsum[1] * n[0]};
+        float vrel[3];
+        for (int a = 0; a < 3; ++a) vrel[a] = Uf[a] - (float)Ua[3 * j + a] + wn[a];
+        const float mj = (float)s.M[j];
+        const float meff = mif * mj / (mif + mj);
+        const int slot = hist_slot(s, p, j, seen);
+        if (slot < 0) continue;
+        double* xi = s.hist_xi + ((long long)p * HIST_SLOTS + slot) * 3;
+        float Fc[3], Ft[3];
+        contact_f(s, meff, n, delta, vrel, xi, dtf, Fc, Ft);
+        const float tq[3] = {rif * (n[1] * Ft[2] - n[2] * Ft[1]), rif * (n[2] * Ft[0] - n[0] * Ft[2]),
+                             rif * (n[0] * Ft[1] - n[1] * Ft[0])};
+        for (int a = 0; a < 3; ++a) { F[a] += (double)Fc[a]; T[a] += (double)tq[a]; }
+    }
+    // walls on non-periodic axes
     const int L[3] = {s.nx, s.ny, s.nz};
     const int per[3] = {s.per_x, s.per_y, s.per_z};
-    // history table, one slot per lane 0..15
-    int* hp = s.hist_partner + (long long)p * HIST_SLOTS;
-    const int mine_partner = lane < HIST_SLOTS ? hp[lane] : HIST_EMPTY;
-    unsigned freem = __ballot_sync(full, lane < HIST_SLOTS && mine_partner == HIST_EMPTY);
-    const int nbc = s.nb_count[p];
-    // entries: neighbour-list particles, then the wall faces of non-periodic axes
-    int nwall = 0;
-    int wall_id[6];
-    for (int a = 0; a < 3; ++a)
-        if (!per[a]) { wall_id[nwall++] = 2 * a; wall_id[nwall++] = 2 * a + 1; }
-    const int ntot = nbc + nwall;
-    double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
-    unsigned seen = 0;
-    for (int base = 0; base < ntot; base += 32) {
-        const int k = base + lane;
-        bool contact_now = false;
-        int partner = 0;
-        double n[3] = {0, 0, 0}, delta = 0.0, vrel[3] = {0, 0, 0}, meff = 0.0, rj = 0.0;
-        if (k < nbc) {
-            const int j = s.nb[(long long)p * NB_SLOTS + k];
-            partner = j;
-            double d[3] = {wrapd(Xa[3 * j] - X[0], s.nx, s.per_x), wrapd(Xa[3 * j + 1] - X[1], s.ny, s.per_y),
-                           wrapd(Xa[3 * j + 2] - X[2], s.nz, s.per_z)};
-            const double dist2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-            rj = s.R[j];
-            const double rs = ri + rj;
-            if (dist2 < rs * rs) {
-                contact_now = true;
-                const double dist = sqrt(dist2);
-                for (int a = 0; a < 3; ++a) n[a] = d[a] / dist;
-                delta = rs - dist;
-                double wsum[3], wn[3];
-                for (int a = 0; a < 3; ++a) wsum[a] = ri * W[a] + rj * Wa[3 * j + a];
-                cross3(wsum, n, wn);
-                for (int a = 0; a < 3; ++a) vrel[a] = U[a] - Ua[3 * j + a] + wn[a];
-                const double mj = s.M[j];
-                meff = mi * mj / (mi + mj);
-            }
-        } else if (k < ntot) {
-            const int wid = wall_id[k - nbc];
-            const int a = wid >> 1, side = wid & 1;
-            partner = -1 - wid;
-            const double dist = side == 0 ? X[a] : (L[a] - X[a]);
-            delta = ri - dist;
-            if (delta > 0.0) {
-                contact_now = true;
-                n[a] = side == 0 ? -1.0 : 1.0;
-                double rw[3] = {ri * W[0], ri * W[1], ri * W[2]}, wn[3];
-                cross3(rw, n, wn);
-                for (int b = 0; b < 3; ++b) vrel[b] = U[b] + wn[b];
-                meff = mi;
-            }
-        }
-        // slot of this contact: existing, else a free one by rank
-        int slot = -1;
-#pragma unroll
-        for (int q = 0; q < HIST_SLOTS; ++q) {
-            const int pq = __shfl_sync(full, mine_partner, q);
-            if (contact_now && pq == partner) slot = q;
-        }
-        const unsigned needs = __ballot_sync(full, contact_now && slot < 0);
-        if (contact_now && slot < 0) {
-            const int rank = __popc(needs & ((1u << lane) - 1u));
-            unsigned fm = freem;
-            for (int r = 0; r < rank && fm; ++r) fm &= fm - 1;
-            if (fm) slot = __ffs(fm) - 1;
-            else set_error(s, ERR_HISTORY);
-        }
-        // slots taken by new contacts leave the free set
-        unsigned taken = 0;
-        {
-            const unsigned bit = (contact_now && slot >= 0 && ((freem >> slot) & 1u)) ? (1u << slot) : 0u;
-            taken = __reduce_or_sync(full, bit);
-        }
-        freem &= ~taken;
-        if (contact_now && slot >= 0) {
-            double* xi = s.hist_xi + ((long long)p * HIST_SLOTS + slot) * 3;
-            const bool fresh = (taken >> slot) & 1u;
-            if (fresh) xi[0] = xi[1] = xi[2] = 0.0;
-            double Fc[3], Ft[3];
-            contact(s, meff, n, delta, vrel, xi, dts, Fc, Ft);
-            double rn[3] = {ri * n[0], ri * n[1], ri * n[2]}, tq[3];
-            cross3(rn, Ft, tq);
-            for (int a = 0; a < 3; ++a) { F[a] += Fc[a]; T[a] += tq[a]; }
-            seen |= 1u << slot;
-        }
-        // record the partners of new slots for the next block of entries
-        const unsigned newbit = (contact_now && slot >= 0 && ((taken >> slot) & 1u)) ? 1u : 0u;
-        const unsigned newm = __ballot_sync(full, newbit);
-        for (unsigned m = newm; m; m &= m - 1) {
-            const int src = __ffs(m) - 1;
-            const int sl = __shfl_sync(full, slot, src);
-            const int pa = __shfl_sync(full, partner, src);
-            if (lane == 0) hp[sl] = pa;
-        }
-    }
-    // free the slots no contact touched (new slots were written through)
-    seen = __reduce_or_sync(full, seen);
-    __syncwarp();
-    if (lane < HIST_SLOTS && !((seen >> lane) & 1u)) hp[lane] = HIST_EMPTY;
-#pragma unroll
     for (int a = 0; a < 3; ++a) {
-        F[a] = warp_sum_d(F[a]);
-        T[a] = warp_sum_d(T[a]);
-    }
-    if (lane == 0) {
-        F[0] += s.Fa[3 * p] + mi * s.gxd;
-        F[1] += s.Fa[3 * p + 1] + mi * s.gyd;
-        F[2] += s.Fa[3 * p + 2] + mi * s.gzd;
-        T[0] += s.Ta[3 * p];
-        T[1] += s.Ta[3 * p + 1];
-        T[2] += s.Ta[3 * p + 2];
-        for (int a = 0; a < 3; ++a) {
-            U[a] += dts * F[a] / mi;
-            W[a] += dts * T[a] / Ii;
-            double x = X[a] + dts * U[a];
-            if (per[a]) x -= L[a] * floor(x / L[a]);
-            Xb[3 * p + a] = x;
-            Ub[3 * p + a] = U[a];
-            Wb[3 * p + a] = W[a];
+        if (per[a]) continue;
+        for (int side = 0; side < 2; ++side) {
+            const float dist = (float)(side == 0 ? X[a] : (L[a] - X[a]));
+            const float delta = rif - dist;
+            if (delta <= 0.f) continue;
+            float n[3] = {0.f, 0.f, 0.f};
+            n[a] = side == 0 ? -1.f : 1.f;
+            const float rw[3] = {rif * Wf[0], rif * Wf[1], rif * Wf[2]};
+            const float wn[3] = {rw[1] * n[2] - rw[2] * n[1], rw[2] * n[0] - rw[0] * n[2],
+                                 rw[0] * n[1] - rw[1] * n[0]};
+            const float vrel[3] = {Uf[0] + wn[0], Uf[1] + wn[1], Uf[2] + wn[2]};
+            const int slot = hist_slot(s, p, -1 - (2 * a + side), seen);
+            if (slot < 0) continue;
+            double* xi = s.hist_xi + ((long long)p * HIST_SLOTS + slot) * 3;
+            float Fc[3], Ft[3];
+            contact_f(s, mif, n, delta, vrel, xi, dtf, Fc, Ft);
+            const float tq[3] = {rif * (n[1] * Ft[2] - n[2] * Ft[1]), rif * (n[2] * Ft[0] - n[0] * Ft[2]),
+                                 rif * (n[0] * Ft[1] - n[1] * Ft[0])};
+            for (int b = 0; b < 3; ++b) { F[b] += (double)Fc[b]; T[b] += (double)tq[b]; }
         }
-        if (last) atomicMax(s.zmax_cell, (int)ceil(Xb[3 * p + 2] + ri) + 2);
     }
+    int* hp = s.hist_partner + (long long)p * HIST_SLOTS;
+    for (int k = 0; k < HIST_SLOTS; ++k)
+        if (!(seen & (1u << k))) hp[k] = HIST_EMPTY;
+    const double im = 1.0 / mi, iI = 1.0 / Ii;
+    for (int a = 0; a < 3; ++a) {
+        U[a] += dts * F[a] * im;
+        W[a] += dts * T[a] * iI;
+        double x = X[a] + dts * U[a];
+        if (per[a]) x = x < 0.0 ? x + L[a] : (x >= L[a] ? x - L[a] : x);
+        Xb[3 * p + a] = x;
+        Ub[3 * p + a] = U[a];
+        Wb[3 * p + a] = W[a];
+    }
+    if (last) atomicMax(s.zmax_cell, (int)ceil(X[2] + ri) + 2);
 }
 
 // ------------------------------------------------------------ particle map
@@ -812,9 +751,9 @@ int launch_particles_step(const Dev& s, int have_prev, int last_parity, cudaStre
     const double dts = 1.0 / ns;
     for (int k = 0; k < ns; ++k) {
         const bool ev = (k % 2) == 0;
-        k_dem_substep_warp<<<blocks_for(32LL * s.np, 128), 128, 0, st>>>(
-            s, ev ? s.X : s.X2, ev ? s.U : s.U2, ev ? s.W : s.W2, ev ? s.X2 : s.X, ev ? s.U2 : s.U, ev ? s.W2 : s.W,
-            dts, k == ns - 1);
+        k_dem_substep<<<blocks_for(s.np, 64), 64, 0, st>>>(s, ev ? s.X : s.X2, ev ? s.U : s.U2, ev ? s.W : s.W2,
+                                                          ev ? s.X2 : s.X, ev ? s.U2 : s.U, ev ? s.W2 : s.W, dts,
+                                                          k == ns - 1);
     }
     if (ns % 2 == 1) {
         k_copy3<<<blocks_for(n3, 256), 256, 0, st>>>(s.X2, s.X, n3);

@@ -254,3 +254,45 @@ def test_staged_sweep_fp16():
     dev = np.abs(sim.get(F.FIELD_PDF)[:, fl] - o.get(O.F_PDF)[:, fl]) / weights()[:, None]
     assert dev.max() < 2e-3
     sim.close()
+
+
+def _dry(L=40, **kw):
+    w = W.Workload(name="dry", nx=L, ny=L, nz=L, periodic=(1, 1, 1), g=(0.0, 0.0, 0.0), liquid_height=0.0,
+                   bed="none", **kw).generate()
+    return w
+
+
+@pytest.mark.parametrize("e,r2", [(0.88, 3.0), (0.5, 5.0)])
+def test_dem_restitution_on_gpu(e, r2):
+    """Head-on collision in a gas-filled box: the GPU's DEM returns the
+    restitution coefficient and conserves momentum, like the oracle."""
+    v, r1 = 0.01, 3.0
+    w = _dry(restitution=e, diameter=6.0)
+    w.xyz = np.array([[10.0, 20, 20], [10.0 + r1 + r2 + 1.0, 20, 20]])
+    w.radius = np.array([r1, r2])
+    w.fixed = np.zeros(2, np.uint8)
+    sim = _sim(w)
+    sim.set(F.FIELD_P_U, np.array([[v, 0, 0], [-v, 0, 0]]))
+    sim.step(int(1.0 / v + 3 * w.collision_time + 20))
+    U = sim.get(F.FIELD_P_U)
+    assert abs((U[1, 0] - U[0, 0]) / (2 * v) - e) < 0.01 * e
+    m = np.array([r1 ** 3, r2 ** 3])
+    assert abs(m @ U[:, 0] - (m[0] - m[1]) * v) < 1e-9
+    sim.close()
+
+
+def test_dem_rolling_on_gpu():
+    v0, r = 0.01, 3.0
+    w = W.Workload(name="roll", nx=40, ny=16, nz=16, periodic=(1, 1, 0), g=(0.0, 0.0, -1e-3),
+                   liquid_height=0.0, bed="none", diameter=6.0).generate()
+    w.xyz = np.array([[10.0, 8.0, r]])
+    w.radius = np.array([r])
+    w.fixed = np.zeros(1, np.uint8)
+    sim = _sim(w)
+    sim.set(F.FIELD_P_U, np.array([[v0, 0.0, 0.0]]))
+    sim.step(1500)
+    U = sim.get(F.FIELD_P_U)[0]
+    Wy = sim.get(F.FIELD_P_OMEGA)[0, 1]
+    assert abs(U[0] / v0 - 5 / 7) < 2e-3
+    assert abs(Wy * r / v0 - 5 / 7) < 2e-3
+    sim.close()
