@@ -217,6 +217,36 @@ int fslbm_timing_read(fslbm* s, double* sweep_ms, int64_t* sweeps, int64_t* kern
  * counts[0..3]. Synchronises the stream. */
 int fslbm_cell_counts(fslbm* s, int64_t counts[4]);
 
+/* Allocation-free FP64 reduction of lattice fields the caller already holds
+ * on the device. The paper has no counterpart; this is a service for callers
+ * that cannot call cudaMalloc, such as code running inside a memory pool that
+ * another framework owns, or code allowed to touch only the memory it is
+ * handed. It needs no fslbm handle and allocates nothing: its scratch is a
+ * fixed 128 KiB array in the library's device image, present on every device
+ * that loads the library until the process exits.
+ *   pdf    device, double [27][ncells]: PDFs in the layout of
+ *          FSLBM_FIELD_PDF (what fslbm_get_fields exports)
+ *   type   device, uint8 [ncells]: cell types (FSLBM_FIELD_TYPE)
+ *   mass   device, double [ncells]: interface masses (FSLBM_FIELD_MASS)
+ *   g      host, double [3]: the body acceleration of the run
+ *   out    device, double [4]: written with the liquid mass (sum over liquid
+ *          rho + sum over interface m) and the fluid momentum (x, y, z), the
+ *          quantities of fslbm_reduce out[0] - out[7] and out[1..3]
+ *   cuda_stream  cudaStream_t the work is ordered on (NULL: legacy default)
+ * Returns FSLBM_EINVAL for NULL pointers or ncells <= 0, FSLBM_ECAPACITY for
+ * ncells above 4096 * 65536 (the scratch holds 4096 blocks of partial sums),
+ * FSLBM_EDEVICE if the scratch address cannot be obtained or a launch fails.
+ * The call only enqueues work; read out after synchronising the stream. The
+ * first call on a device looks up the scratch address there (make that call
+ * before any stream capture). Every call shares the one scratch array, which
+ * keeps the last call's partial sums: calls whose kernels overlap on the GPU
+ * (different streams without ordering) race on it. Each call overwrites every
+ * partial sum it reads, so nothing needs clearing between calls, and the sums
+ * are added in a fixed order: two calls on the same fields give identical
+ * results. */
+int fslbm_reduce_fields_noalloc(const double* pdf, const uint8_t* type, const double* mass, int64_t ncells,
+                                const double g[3], double* out, void* cuda_stream);
+
 /* Releases every device buffer of the run. NULL is ignored. */
 void fslbm_destroy(fslbm* s);
 

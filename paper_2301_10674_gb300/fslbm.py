@@ -45,7 +45,7 @@ EXPORTED = (
     "fslbm_default_params", "fslbm_create", "fslbm_add_spheres", "fslbm_init_surface", "fslbm_step",
     "fslbm_get_fields", "fslbm_set_fields", "fslbm_reduce", "fslbm_sync", "fslbm_steps_done",
     "fslbm_num_spheres", "fslbm_invariant_violations", "fslbm_timing", "fslbm_timing_read",
-    "fslbm_cell_counts", "fslbm_destroy", "fslbm_strerror",
+    "fslbm_cell_counts", "fslbm_reduce_fields_noalloc", "fslbm_destroy", "fslbm_strerror",
 )
 
 
@@ -115,6 +115,7 @@ def load():
     L.fslbm_timing_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                     ctypes.POINTER(ctypes.c_int64)]
     L.fslbm_cell_counts.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+    L.fslbm_reduce_fields_noalloc.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), vp, vp]
     L.fslbm_destroy.argtypes = [vp]
     L.fslbm_destroy.restype = None
     L.fslbm_strerror.argtypes = [ctypes.c_int]
@@ -185,6 +186,14 @@ def fslbm_sync(h) -> int:
 
 def fslbm_destroy(h):
     load().fslbm_destroy(h)
+
+
+def fslbm_reduce_fields_noalloc(pdf, types, mass, ncells: int, g, out, stream: int | None = None) -> int:
+    """Allocation-free reduction of caller-held device fields (see the C
+    declaration); pdf, types, mass and out are device buffers."""
+    gg = (ctypes.c_double * 3)(*[float(v) for v in g])
+    return load().fslbm_reduce_fields_noalloc(_ptr(pdf), _ptr(types), _ptr(mass), int(ncells), gg, _ptr(out),
+                                              ctypes.c_void_p(stream or 0))
 
 
 def _ptr(a):
