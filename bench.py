@@ -7,6 +7,14 @@ sub-steps, particle re-mapping) on the 3072x96x320 flume workload (~94 M
 cells, seeded particle bed). Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--storage fp16|bf16|fp32] [--normals mlp|fd] [--no-compare]
+
+The headline form stores the PDFs in FP16 (as f - w) and takes the interface
+normal from the learned model, trained first (untimed) by the library's own
+kernels on 4 M voxelised surfaces. The same steps are then timed for plain
+FP32 with the finite-difference normal from the same initial state; the line
+reports both, the speedup, and the difference between the two runs (mass
+drift of each, liquid volume per column, bulk velocity).
 
 With N > 1 (one process per GPU under torch.distributed.run) every rank runs
 an independent replica with its own seed: the method has no exchange step at
@@ -140,28 +148,46 @@ def run_oracle(w, steps: int, warmup: int, crop_nx: int) -> dict:
 
 # ---------------------------------------------------------------- GPU leg
 
-def run_ours(args, world, rank, local):
+LAM, MU = 0.4, 0.1
+
+
+def train_normal_model(stream, n_stencils: int, steps: int, seed: int = 4) -> tuple[np.ndarray, dict]:
+    """Learned normal trained by the library's own kernels (not timed):
+    voxelised analytic surfaces (planes, droplets, bubbles, sine waves), Adam
+    on batches of 4096 with cube-symmetry augmentation."""
     import torch
 
-    from paper_2301_10674_gb300 import build as B
+    from paper_2301_10674_gb300 import fslbm as F
+    from paper_2301_10674_gb300 import workloads as W
+
+    t0 = time.perf_counter()
+    params = torch.from_numpy(W.surface_stencils(n_stencils, seed=seed)).cuda()
+    fill = torch.empty((n_stencils, 27), dtype=torch.float32, device="cuda")
+    tgt = torch.empty((n_stencils, 4), dtype=torch.float32, device="cuda")
+    F._check(F.fslbm_mlp_stencils(params, n_stencils, fill, tgt, stream.cuda_stream), "fslbm_mlp_stencils")
+    del params
+    t1 = time.perf_counter()
+    theta = torch.from_numpy(W.mlp_initial_weights(seed)).cuda()
+    curve = torch.empty(steps, dtype=torch.float32, device="cuda")
+    F._check(F.fslbm_mlp_train(theta, fill, tgt, n_stencils, steps, 4096, 1e-3, LAM, MU, seed, True, curve,
+                               stream.cuda_stream), "fslbm_mlp_train")
+    t2 = time.perf_counter()
+    c = curve.cpu().numpy()
+    return theta.cpu().numpy(), {"stencils": n_stencils, "steps": steps, "batch": 4096,
+                                 "loss_first": float(c[0]), "loss_last100": float(c[-100:].mean()),
+                                 "data_s": round(t1 - t0, 2), "train_s": round(t2 - t1, 2)}
+
+
+def timed_run(args, w, storage_name, theta, stream, local, barrier, world):
+    """Warm-up, then exactly args.steps timed steps of one form of the method."""
+    import torch
+
     from paper_2301_10674_gb300 import fslbm as F
 
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    B.build()
-    w = _workload(args.workload, rank)
-    storage = STORAGE[args.storage]
-    stream = torch.cuda.Stream()
-    sim = F.Simulation.from_workload(w, storage=storage, stream=stream)
-    ncell = w.ncells
-
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
+    sim = F.Simulation.from_workload(w, storage=STORAGE[storage_name], stream=stream)
+    if theta is not None:
+        sim.set_normal_model(theta)
+    m0 = sim.reduce()
     sim.step(args.warmup)
     sim.sync()
     counts = sim.cell_counts()
@@ -183,69 +209,127 @@ def run_ours(args, world, rank, local):
     sim.timing(False)
     clk = clocks.stop()
     counts_after = sim.cell_counts()
-    violations = sim.violations
     red = sim.reduce()
+    t = sim.get(F.FIELD_TYPE)
+    phi = sim.get(F.FIELD_PHI)
+    column = np.where(t == 1, 1.0, np.where(t == 2, phi, 0.0)).sum(axis=0)     # liquid volume per (y, x)
+    out = {"ms": ms, "sweep_ms": sweep_ms, "sweeps": sweeps, "launches": launches, "counts": counts,
+           "counts_after": counts_after, "clocks": clk, "violations": sim.violations, "m0": m0, "m1": red,
+           "column": column, "normal_stats": sim.normal_stats() if theta is not None else None}
     sim.close()
     del sim
-
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    else:
-        ms_max = ms
-    value = world * ncell * args.steps / (ms_max / 1e3) / 1e6
+        tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        out["ms"] = float(tt.item())
+    return out
 
-    # roofline of the stream-collide sweep: algorithmic bytes per launch
-    elem = ELEM[args.storage]
+
+def _roofline(run, storage_name, ncell):
+    elem = ELEM[storage_name]
+    counts, counts_after = run["counts"], run["counts_after"]
     fluid = int(counts[1] + counts[2] + counts_after[1] + counts_after[2]) / 2.0
     other = ncell - fluid
     bytes_per_sweep = fluid * (54 * elem + 1) + other * 1
-    sweep_s = sweep_ms / 1e3 / max(1, sweeps)
+    sweep_s = run["sweep_ms"] / 1e3 / max(1, run["sweeps"])
     achieved = bytes_per_sweep / sweep_s / 1e9
     peak, peak_kind = _peaks()
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None,
+            "kernel": "stream-collide sweep (staged bulk + face rows + particle links + interface list)",
+            "bytes_per_cell": {"fluid": 54 * elem + 1, "gas_or_solid": 1},
+            "bytes_per_launch": int(bytes_per_sweep), "launch_ms": round(sweep_s * 1e3, 4),
+            "peak_kind": peak_kind}
 
-    # end to end through the public API with host buffers: create, add the
-    # particle bed from pinned host memory, step, read the diagnostics back
-    # every step, destroy
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    from paper_2301_10674_gb300 import build as B
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.build()
+    w = _workload(args.workload, rank)
+    stream = torch.cuda.Stream()
+    ncell = w.ncells
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    theta, train = None, None
+    if args.normals == "mlp":
+        with torch.cuda.stream(stream):
+            theta, train = train_normal_model(stream, args.mlp_stencils, args.mlp_steps)
+    head = timed_run(args, w, args.storage, theta, stream, local, barrier, world)
+    base = None
+    if args.compare and (args.storage != "fp32" or args.normals != "fd"):
+        base = timed_run(args, w, "fp32", None, stream, local, barrier, world)
+
+    value = world * ncell * args.steps / (head["ms"] / 1e3) / 1e6
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(args, w, storage, stream, world)
-
+        e2e = run_e2e(args, w, STORAGE[args.storage], theta, stream, world)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = run_oracle(w, steps=args.cpu_steps, warmup=1, crop_nx=args.cpu_crop)
         cpu = {"value": cpu["value"], "unit": UNIT, "cores": cpu["cores"], "kind": "oracle", "sample": cpu["sample"]}
-
     if rank != 0:
         return None
+
+    def drift(r):
+        return abs(r["m1"][0] - r["m0"][0]) / r["m0"][0]
+
+    form = f"{args.storage}+{'learned' if theta is not None else 'fd'}-normal"
+    comparison = None
+    if base is not None:
+        vb = world * ncell * args.steps / (base["ms"] / 1e3) / 1e6
+        dcol = np.abs(head["column"] - base["column"])
+        comparison = {
+            "form": "fp32+fd-normal", "value": round(vb, 2), "unit": UNIT,
+            "ms_per_step": round(base["ms"] / args.steps, 4), "speedup": round(value / vb, 4),
+            "roofline": _roofline(base, "fp32", ncell), "clocks": base["clocks"],
+            "error": {
+                "horizon_steps": args.warmup + args.steps,
+                "mass_drift": {"head": drift(head), "fp32": drift(base)},
+                "surface_profile_cells": {"max_abs": float(dcol.max()), "mean_abs": float(dcol.mean())},
+                "bulk_ux_rel": float(abs(head["m1"][4] - base["m1"][4]) / max(abs(base["m1"][4]), 1e-30)),
+                "interface_cells": {"head": int(head["m1"][5]), "fp32": int(base["m1"][5])},
+            },
+        }
+    cb = head["counts_after"]
     out = {
         "metric": _metric_name(), "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": round(head["ms"] / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": w.name, "lattice": [w.nx, w.ny, w.nz], "cells": ncell,
+        "config": {"workload": w.name, "form": form, "lattice": [w.nx, w.ny, w.nz], "cells": ncell,
                    "spheres": w.nspheres, "spheres_nominal": w.spheres_nominal, "storage": args.storage,
-                   "cells_by_type": {"gas": int(counts_after[0]), "liquid": int(counts_after[1]),
-                                     "interface": int(counts_after[2]), "solid": int(counts_after[3])},
-                   "l2": f"no flush: the PDF lattice ({27 * 2 * elem * ncell / 1e9:.1f} GB incl. side buffer) "
-                         f"is far larger than L2", "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None,
-                     "kernel": "stream-collide sweep (bulk + boundary kernels)",
-                     "bytes_per_launch": int(bytes_per_sweep), "launch_ms": round(sweep_s * 1e3, 4),
-                     "peak_kind": peak_kind},
-        "clocks": clk,
-        "gpu_launches": int(launches),
+                   "normals": args.normals,
+                   "cells_by_type": {"gas": int(cb[0]), "liquid": int(cb[1]), "interface": int(cb[2]),
+                                     "solid": int(cb[3])},
+                   "l2": f"no flush: the PDF lattice ({27 * 2 * ELEM[args.storage] * ncell / 1e9:.1f} GB incl. "
+                         f"side buffer) is far larger than L2", "parallelism": f"replicas x{world}"},
+        "roofline": _roofline(head, args.storage, ncell),
+        "clocks": head["clocks"],
+        "gpu_launches": int(head["launches"]),
         "e2e": e2e,
         "cpu_baseline": cpu,
-        "checks": {"invariant_violations": int(violations), "liquid_mass": float(red[0]),
-                   "interface_cells": int(red[5])},
+        "comparison": comparison,
+        "learned_normal": None if theta is None else {
+            "training": train,
+            "evaluated": int(head["normal_stats"][0]), "taken": int(head["normal_stats"][1])},
+        "checks": {"invariant_violations": int(head["violations"]), "liquid_mass": float(head["m1"][0]),
+                   "interface_cells": int(head["m1"][5])},
     }
     return out
 
 
-def run_e2e(args, w, storage, stream, world):
+def run_e2e(args, w, storage, theta, stream, world):
     import torch
 
     from paper_2301_10674_gb300 import fslbm as F
@@ -255,10 +339,13 @@ def run_e2e(args, w, storage, stream, world):
     fix = torch.from_numpy(np.ascontiguousarray(w.fixed)).pin_memory().numpy()
     diag = torch.empty(8, dtype=torch.float64).pin_memory().numpy()
     params = F.params_from_workload(w, storage)
+    bits = None if theta is None else torch.from_numpy(F.bf16_bits(theta)).pin_memory().numpy()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     h = F.fslbm_create(params, stream.cuda_stream)
     F._check(F.fslbm_add_spheres(h, xyz, rad, fix), "fslbm_add_spheres")
+    if bits is not None:
+        F._check(F.fslbm_set_normal_model(h, bits), "fslbm_set_normal_model")
     for _ in range(args.steps):
         F._check(F.fslbm_step(h, 1), "fslbm_step")
         rc, out = F.fslbm_reduce(h)
@@ -272,12 +359,13 @@ def run_e2e(args, w, storage, stream, world):
         t = torch.tensor([dt], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dt = float(t.item())
-    h2d = xyz.nbytes + rad.nbytes + fix.nbytes + __import__("ctypes").sizeof(params)
+    h2d = xyz.nbytes + rad.nbytes + fix.nbytes + __import__("ctypes").sizeof(params) + \
+        (0 if bits is None else bits.nbytes)
     return {"value": round(world * w.ncells * args.steps / dt / 1e6, 2), "unit": UNIT,
             "h2d_bytes_per_step": round(h2d / args.steps, 1), "d2h_bytes_per_step": 64,
             "seconds": round(dt, 3),
-            "note": "create + particle bed from pinned host memory + per step (fslbm_step, fslbm_reduce "
-                    "read back to host) + destroy"}
+            "note": "create + particle bed (and learned-normal weights) from pinned host memory + per step "
+                    "(fslbm_step, fslbm_reduce read back to host) + destroy"}
 
 
 def run_reference(args, world, rank):
@@ -306,7 +394,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", default="large")
-    ap.add_argument("--storage", choices=tuple(STORAGE), default="fp32")
+    ap.add_argument("--storage", choices=tuple(STORAGE), default="fp16")
+    ap.add_argument("--normals", choices=("fd", "mlp"), default="mlp")
+    ap.add_argument("--compare", action=argparse.BooleanOptionalAction, default=True,
+                    help="also time plain FP32 with the finite-difference normal")
+    ap.add_argument("--mlp-stencils", type=int, default=1 << 22)
+    ap.add_argument("--mlp-steps", type=int, default=4000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=3)

@@ -84,7 +84,9 @@ typedef struct {
     double liquid_height;        /* initial flat free surface height (cells) */
     int32_t init_profile;        /* 0: fluid at rest */
     int32_t storage;             /* FSLBM_STORE_* */
-    int32_t normal_model;        /* 0: finite-difference (Parker-Youngs) normal */
+    int32_t normal_model;        /* 0: finite-difference (Parker-Youngs) normal;
+                                    1: learned normal (weights must be set with
+                                    fslbm_set_normal_model before fslbm_step) */
     int32_t reconstruct_normal;  /* 1: also rebuild PDFs with n.c_i < -eps_normal */
     double eps_conv;             /* conversion hysteresis on the fill level */
     double eps_normal;           /* margin of the normal-based reconstruction */
@@ -110,7 +112,7 @@ void fslbm_default_params(fslbm_params* p);
  * liquid_height liquid, the layer holding or touching the surface interface
  * with its fill level, gas above; hydrostatic density rho_gas
  * exp(3 |g_z| (H - z)). Returns FSLBM_EINVAL for bad parameters (including
- * sigma != 0 and normal_model != 0), FSLBM_ENOMEM if the device buffers do
+ * sigma != 0 and normal_model outside {0, 1}), FSLBM_ENOMEM if the device buffers do
  * not fit. On success *out owns every device buffer of the run. */
 int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out);
 
@@ -246,6 +248,71 @@ int fslbm_cell_counts(fslbm* s, int64_t counts[4]);
  * results. */
 int fslbm_reduce_fields_noalloc(const double* pdf, const uint8_t* type, const double* mass, int64_t ncells,
                                 const double g[3], double* out, void* cuda_stream);
+
+/* ---------------------------------------------------------------- learned normal
+ * The interface normal used by the free-surface boundary condition (the
+ * choice of reconstructed directions) and by the excess-mass weights
+ * (Section 2.1 cites the free-surface LBM; the paper names no normal
+ * scheme) can come from a 27-64-64-4 perceptron with ReLU instead of the
+ * finite-difference (Parker-Youngs) gradient. Its input is the fill levels
+ * of the 3x3x3 block around an interface cell (liquid 1, gas 0, interface
+ * phi clamped to [0,1]; block index q = (cx+1) + 3(cy+1) + 9(cz+1)); its
+ * outputs are a raw normal toward the gas and the curvature. Parameters,
+ * 6212 values: W1 (64x27), b1 (64), W2 (64x64), b2 (64), W3 (4x64), b3 (4),
+ * matrices row-major (out, in). The finite-difference normal is kept where a
+ * wall or solid cell lies in the block, where the raw normal's length is
+ * outside [1/2, 2], and where the two normals are more than 30 degrees
+ * apart. Products run on tensor cores: BF16 operands, FP32 accumulation. */
+
+/* Selects the learned normal for the run and recomputes the interface
+ * normals of the current state. w: host memory, n_params = 6212 BF16 bit
+ * patterns in the parameter layout (copied; the caller keeps ownership).
+ * w = NULL with n_params = 0 returns to the finite-difference normal.
+ * Stream-ordered; synchronises the stream. FSLBM_EINVAL for another size. */
+int fslbm_set_normal_model(fslbm* s, const uint16_t* w, int64_t n_params);
+
+/* Learned-normal counters since the last fslbm_set_normal_model:
+ * out[0] normals evaluated, out[1] normals taken from the network (the rest
+ * fell back). Zeros under the finite-difference normal. Synchronises. */
+int fslbm_normal_stats(fslbm* s, uint64_t out[2]);
+
+/* Training data of the learned normal. params: device, n rows of 12 doubles
+ * describing analytic surfaces through P = s n0 (kind 0 plane, 1 liquid
+ * sphere of radius r centred at P - r n0, 2 gas sphere centred at P + r n0,
+ * 3 sine wave w <= A (sin(k u + phase) - sin(phase)) with u = (x-P).e1,
+ * w = (x-P).n0); row layout: kind, n0[3], s, r, A, k, phase, e1[3]. Writes,
+ * on the device, fill[n][27] (liquid volume fraction of each cell of the
+ * block around the origin: exact for planes, exact x-chords of 64x64 rows
+ * for spheres, 64^3 midpoint samples for sine waves) and target[n][4]
+ * (unit normal toward the gas at P, mean curvature, positive for a convex
+ * liquid body). Synchronises. */
+int fslbm_mlp_stencils(const double* params, int64_t n, float* fill, float* target, void* cuda_stream);
+
+/* Loss and gradient of the learned normal over n stencils (device
+ * pointers): theta[6212] FP32 parameters, fill[n][27], target[n][4];
+ * loss = mean of 1 - cos(n, n_true) + lam (k - k_true)^2 + mu (|n| - 1)^2,
+ * written to loss[1]; its gradient to grad[6212]. n <= 2^24.
+ * Synchronises. */
+int fslbm_mlp_gradient(const float* theta, const float* fill, const float* target, int64_t n, double lam,
+                       double mu, float* grad, float* loss, void* cuda_stream);
+
+/* Adam (beta 0.9, 0.999, eps 1e-8, bias-corrected, moments starting at
+ * zero) for `steps` batches of `batch` stencils drawn from the n in
+ * fill/target: slot j of step t takes SplitMix64 output t*batch + j of
+ * `seed`, v, stencil v mod n and, with augment, cube symmetry
+ * (v >> 32) mod 48 (permutation (v>>32 mod 48)/8 of the axes in
+ * lexicographic order, sign flips from its low 3 bits). The step size of
+ * step k is lr (lr_end / lr)^(k / (steps - 1)), constant when lr_end is 0.
+ * theta (device,
+ * FP32) is updated in place; loss_curve (device, `steps` floats, or NULL)
+ * receives each step's loss before its update. Synchronises. */
+int fslbm_mlp_train(float* theta, const float* fill, const float* target, int64_t n, int64_t steps, int batch,
+                    double lr, double lr_end, double lam, double mu, uint64_t seed, int augment, float* loss_curve,
+                    void* cuda_stream);
+
+/* Raw network outputs (n_x, n_y, n_z, curvature) of n stencils: theta[6212]
+ * FP32, fill[n][27], out[n][4], all device memory. Synchronises. */
+int fslbm_mlp_infer(const float* theta, const float* fill, int64_t n, float* out, void* cuda_stream);
 
 /* Releases every device buffer of the run. NULL is ignored. */
 void fslbm_destroy(fslbm* s);

@@ -88,6 +88,7 @@ def lib():
         L.orc_collide.argtypes = [dp, dp, ctypes.c_double, dp]
         L.orc_feq.argtypes = [ctypes.c_double, dp, dp]
         L.orc_normal_stencil.argtypes = [dp, dp]
+        L.orc_set_mlp.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
         L.orc_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -217,6 +218,17 @@ class Oracle:
         out = np.zeros(8, np.float64)
         lib().orc_reduce(self._h, _dp(out))
         return out
+
+    def set_mlp(self, theta, bf16: bool = True) -> None:
+        """Learned normal with parameters theta (6212 values, the layout of
+        oracle.mlp); None restores the finite-difference normal."""
+        if theta is None:
+            lib().orc_set_mlp(self._h, None, 0)
+            return
+        a = np.ascontiguousarray(theta, dtype=np.float64)
+        assert a.size == 6212
+        if lib().orc_set_mlp(self._h, a.ctypes.data, int(bf16)) != 0:
+            raise MemoryError("orc_set_mlp")
 
 
 def threads() -> int:

@@ -95,6 +95,8 @@ typedef struct orc {
     orc_hist *hist;           /* np * MAX_HIST */
     double *fixmetric;        /* map of the fixed particles alone (static) */
     int *fixowner;
+    double *mlp;              /* learned-normal parameters, NULL: Parker-Youngs */
+    int mlp_bf16;             /* round products' operands to bfloat16 */
 } orc;
 
 /* ---------------------------------------------------------------- tables */
@@ -345,6 +347,76 @@ static void pyn_normal(const orc* o, long cell, const double* phi, double n[3])
     }
 }
 
+/* Learned normal (R-17): a 27-64-64-4 perceptron with ReLU maps the fill
+ * levels of the 3x3x3 block (clamped to [0,1]) to a raw normal and the
+ * curvature. Parameter layout: W1 (64x27), b1, W2 (64x64), b2, W3 (4x64),
+ * b3, matrices row-major (out, in). The finite-difference normal stands in
+ * when a wall or solid cell lies in the block, when the raw normal's length
+ * is outside [1/2, 2], or when the two normals are more than 30 degrees
+ * apart. With mlp_bf16 the operands of every product (weights, inputs,
+ * hidden activations) are rounded to bfloat16 first, as on tensor cores,
+ * so that the fallback decisions are taken on the same values; sums and
+ * biases stay FP64. */
+#define MLP_NPARAM 6212
+static double bf16_round(double a)
+{
+    if (a == 0.0 || !isfinite(a)) return a;
+    int e;
+    double m = frexp(a, &e);               /* a = m 2^e, |m| in [1/2, 1) */
+    return ldexp(nearbyint(ldexp(m, 8)), e - 8);
+}
+
+static void mlp_normal(const orc* o, long cell, const double* phi, double n[3])
+{
+    int x, y, z;
+    coords(o, cell, &x, &y, &z);
+    double in[NQ];
+    int bad = 0;
+    for (int q = 0; q < NQ; ++q) {
+        long nb = nbr(o, x, y, z, CX[q], CY[q], CZ[q]);
+        if (nb < 0 || o->type[nb] == T_SOL) { bad = 1; in[q] = 0.0; continue; }
+        double v = phi[nb];
+        in[q] = v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
+    }
+    double fd[3];
+    pyn_normal(o, cell, phi, fd);
+    n[0] = fd[0]; n[1] = fd[1]; n[2] = fd[2];
+    if (bad) return;
+    const double *W1 = o->mlp, *b1 = W1 + 64 * 27, *W2 = b1 + 64, *b2 = W2 + 64 * 64, *W3 = b2 + 64,
+                 *b3 = W3 + 4 * 64;
+    const int r = o->mlp_bf16;
+    double h1[64], h2[64], out[4];
+    for (int j = 0; j < 64; ++j) {
+        double a = b1[j];
+        for (int i = 0; i < NQ; ++i)
+            a += (r ? bf16_round(W1[j * 27 + i]) * bf16_round(in[i]) : W1[j * 27 + i] * in[i]);
+        h1[j] = a > 0.0 ? a : 0.0;
+    }
+    for (int j = 0; j < 64; ++j) {
+        double a = b2[j];
+        for (int i = 0; i < 64; ++i)
+            a += (r ? bf16_round(W2[j * 64 + i]) * bf16_round(h1[i]) : W2[j * 64 + i] * h1[i]);
+        h2[j] = a > 0.0 ? a : 0.0;
+    }
+    for (int k = 0; k < 4; ++k) {
+        double a = b3[k];
+        for (int i = 0; i < 64; ++i)
+            a += (r ? bf16_round(W3[k * 64 + i]) * bf16_round(h2[i]) : W3[k * 64 + i] * h2[i]);
+        out[k] = a;
+    }
+    double len = sqrt(out[0] * out[0] + out[1] * out[1] + out[2] * out[2]);
+    if (!(len >= 0.5 && len <= 2.0)) return;
+    double m[3] = {out[0] / len, out[1] / len, out[2] / len};
+    if (m[0] * fd[0] + m[1] * fd[1] + m[2] * fd[2] < 0.8660254037844386) return;   /* cos 30 deg */
+    n[0] = m[0]; n[1] = m[1]; n[2] = m[2];
+}
+
+static void normal_at(const orc* o, long cell, const double* phi, double n[3])
+{
+    if (o->mlp) mlp_normal(o, cell, phi, n);
+    else pyn_normal(o, cell, phi, n);
+}
+
 /* Parker-Youngs normal of a bare 3x3x3 fill stencil (index q as above), used
  * by tests; all 27 values are taken as given. */
 void orc_normal_stencil(const double phi27[NQ], double n[3])
@@ -424,7 +496,7 @@ orc* orc_create(const orc_params* p)
         refresh_phi(o, i);
     }
     for (long i = 0; i < n; ++i)
-        if (o->type[i] == T_IFC) pyn_normal(o, i, o->phi, &o->nrm[3 * i]);
+        if (o->type[i] == T_IFC) normal_at(o, i, o->phi, &o->nrm[3 * i]);
     return o;
 }
 
@@ -472,7 +544,7 @@ int orc_init_surface(orc* o, const double* H)
         refresh_phi(o, i);
     }
     for (long i = 0; i < n; ++i) {
-        if (o->type[i] == T_IFC) pyn_normal(o, i, o->phi, &o->nrm[3 * i]);
+        if (o->type[i] == T_IFC) normal_at(o, i, o->phi, &o->nrm[3 * i]);
         else o->nrm[3 * i] = o->nrm[3 * i + 1] = o->nrm[3 * i + 2] = 0.0;
     }
     free(fill);
@@ -486,8 +558,25 @@ void orc_destroy(orc* o)
     free(o->phi); free(o->nrm); free(o->owner);
     free(o->X); free(o->U); free(o->W); free(o->R); free(o->M); free(o->I); free(o->fixed);
     free(o->Fh); free(o->Th); free(o->Fp); free(o->Tp); free(o->hist);
-    free(o->fixmetric); free(o->fixowner);
+    free(o->fixmetric); free(o->fixowner); free(o->mlp);
     free(o);
+}
+
+/* Selects the learned normal (theta: MLP_NPARAM values in the layout above;
+ * NULL restores Parker-Youngs) and recomputes the interface normals. */
+int orc_set_mlp(orc* o, const double* theta, int bf16)
+{
+    free(o->mlp);
+    o->mlp = NULL;
+    if (theta) {
+        o->mlp = (double*)malloc(sizeof(double) * MLP_NPARAM);
+        if (!o->mlp) return -1;
+        memcpy(o->mlp, theta, sizeof(double) * MLP_NPARAM);
+    }
+    o->mlp_bf16 = bf16;
+    for (long i = 0; i < o->n; ++i)
+        if (o->type[i] == T_IFC) normal_at(o, i, o->phi, &o->nrm[3 * i]);
+    return 0;
 }
 
 /* Map of the particles onto the grid (Section 2.2, R-11): a cell is solid
@@ -588,7 +677,7 @@ int orc_add_spheres(orc* o, int n, const double* xyz, const double* radius, cons
     }
     free(own);
     for (long i = 0; i < o->n; ++i)
-        if (o->type[i] == T_IFC) pyn_normal(o, i, o->phi, &o->nrm[3 * i]);
+        if (o->type[i] == T_IFC) normal_at(o, i, o->phi, &o->nrm[3 * i]);
     return 0;
 }
 
@@ -884,7 +973,7 @@ static void one_step(orc* o)
     /* S4: normals of the new fill levels */
     double* n1 = (double*)calloc((size_t)3 * n, sizeof(double));
     for (long i = 0; i < n; ++i)
-        if (o->type[i] == T_IFC) pyn_normal(o, i, o->phi, &n1[3 * i]);
+        if (o->type[i] == T_IFC) normal_at(o, i, o->phi, &n1[3 * i]);
 
     /* S5: conversion candidates (R-7), from a snapshot of the cell types */
     uint8_t* conv = (uint8_t*)calloc((size_t)n, 1);
@@ -1088,7 +1177,7 @@ static void one_step(orc* o)
     }
     /* S13: normals for the next step's boundary condition */
     for (long i = 0; i < n; ++i) {
-        if (o->type[i] == T_IFC) pyn_normal(o, i, o->phi, &o->nrm[3 * i]);
+        if (o->type[i] == T_IFC) normal_at(o, i, o->phi, &o->nrm[3 * i]);
         else o->nrm[3 * i] = o->nrm[3 * i + 1] = o->nrm[3 * i + 2] = 0.0;
     }
     o->step++;
@@ -1169,7 +1258,7 @@ int orc_set(orc* o, int which, const void* src)
         memcpy(o->mass, src, sizeof(double) * n);
         for (long i = 0; i < n; ++i) refresh_phi(o, i);
         for (long i = 0; i < n; ++i)
-            if (o->type[i] == T_IFC) pyn_normal(o, i, o->phi, &o->nrm[3 * i]);
+            if (o->type[i] == T_IFC) normal_at(o, i, o->phi, &o->nrm[3 * i]);
         return 0;
     case P_U: memcpy(o->U, src, sizeof(double) * 3 * o->np); return 0;
     case P_W: memcpy(o->W, src, sizeof(double) * 3 * o->np); return 0;

@@ -7,6 +7,11 @@
 #include <vector>
 
 #include "fslbm_dev.cuh"
+#include "mlp_dev.cuh"
+
+namespace fsl {
+void mlp_from_bf16_host(const uint16_t* w, MlpBf16& h);
+}
 
 namespace fsl {
 void launch_export_owner(const Dev& s, int* out, cudaStream_t st);
@@ -33,6 +38,8 @@ struct fslbm {
     size_t ev_used;
     int64_t launches;
     unsigned long long* counts4;
+    MlpBf16* mlp_dev;              // operand copies of the learned normal
+    unsigned long long* mlp_stats;
 };
 
 namespace {
@@ -134,7 +141,7 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     const long long n = (long long)p->nx * p->ny * p->nz;
     if (n >= (1LL << 31)) return FSLBM_EINVAL;
     if (!(p->omega > 0.0 && p->omega < 2.0)) return FSLBM_EINVAL;
-    if (p->sigma != 0.0 || p->normal_model != 0 || p->init_profile != 0) return FSLBM_EINVAL;
+    if (p->sigma != 0.0 || p->normal_model < 0 || p->normal_model > 1 || p->init_profile != 0) return FSLBM_EINVAL;
     if (p->storage < 0 || p->storage > 2) return FSLBM_EINVAL;
     if (p->dem_substeps < 1 || !(p->restitution > 0.0 && p->restitution <= 1.0)) return FSLBM_EINVAL;
     if (!(p->collision_time > 0.0) || !(p->rho_p > 0.0) || !(p->rho_gas > 0.0)) return FSLBM_EINVAL;
@@ -156,6 +163,8 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     s->ev_used = 0;
     s->launches = 0;
     s->counts4 = nullptr;
+    s->mlp_dev = nullptr;
+    s->mlp_stats = nullptr;
     Dev& d = s->d;
     std::memset(&d, 0, sizeof(d));
     d.nx = p->nx; d.ny = p->ny; d.nz = p->nz;
@@ -381,6 +390,7 @@ int fslbm_init_surface(fslbm* s, const double* height_xy, int on_device) {
 int fslbm_step(fslbm* s, int64_t n_steps) {
     if (!s || n_steps < 0) return FSLBM_EINVAL;
     if (s->host_err) return s->host_err;
+    if (s->p.normal_model == 1 && !s->d.mlp) return FSLBM_ESTATE;
     Dev& d = s->d;
     cudaStream_t st = s->st;
     for (int64_t k = 0; k < n_steps; ++k) {
@@ -589,6 +599,45 @@ int fslbm_cell_counts(fslbm* s, int64_t counts[4]) {
     cudaMemcpyAsync(h, s->counts4, sizeof(h), cudaMemcpyDeviceToHost, s->st);
     int rc = sync_check(s);
     for (int k = 0; k < 4; ++k) counts[k] = (int64_t)h[k];
+    return rc;
+}
+
+int fslbm_set_normal_model(fslbm* s, const uint16_t* w, int64_t n_params) {
+    if (!s) return FSLBM_EINVAL;
+    if (s->host_err) return s->host_err;
+    Dev& d = s->d;
+    if (!w) {
+        if (n_params != 0) return FSLBM_EINVAL;
+        d.mlp = nullptr;
+        d.mlp_stats = nullptr;
+        s->p.normal_model = 0;
+    } else {
+        if (n_params != MLP_NPARAM) return FSLBM_EINVAL;
+        bool ok = true;
+        if (!s->mlp_dev) s->mlp_dev = dalloc<MlpBf16>(s, 1, ok);
+        if (!s->mlp_stats) s->mlp_stats = dalloc<unsigned long long>(s, 2, ok);
+        if (!ok) return FSLBM_ENOMEM;
+        MlpBf16 h;
+        mlp_from_bf16_host(w, h);
+        cudaMemcpyAsync(s->mlp_dev, &h, sizeof(h), cudaMemcpyHostToDevice, s->st);
+        cudaMemsetAsync(s->mlp_stats, 0, 2 * sizeof(unsigned long long), s->st);
+        d.mlp = s->mlp_dev;
+        d.mlp_stats = s->mlp_stats;
+        s->p.normal_model = 1;
+    }
+    launch_normals(d, d.nrm, s->st);
+    return sync_check(s);   // h stays alive until the copy has completed
+}
+
+int fslbm_normal_stats(fslbm* s, uint64_t out[2]) {
+    if (!s || !out) return FSLBM_EINVAL;
+    out[0] = out[1] = 0;
+    if (!s->d.mlp_stats) return FSLBM_OK;
+    unsigned long long h[2] = {0, 0};
+    cudaMemcpyAsync(h, s->d.mlp_stats, sizeof(h), cudaMemcpyDeviceToHost, s->st);
+    const int rc = sync_check(s);
+    out[0] = h[0];
+    out[1] = h[1];
     return rc;
 }
 

@@ -118,6 +118,10 @@ struct Dev {
     // cell centre, shared-cell flag, active particles and their cells
     double* Xm;
     float* margin;
+    // learned normal: operand copies of the network (null: Parker-Youngs)
+    // and counters of stencils evaluated / normals taken from the network
+    const struct MlpBf16* mlp;
+    unsigned long long* mlp_stats;
     int* shared;
     int* act; int* act_count;
     uint8_t* dirty;

@@ -7,6 +7,7 @@
 // cell computes its own result from a snapshot of its neighbourhood, so no
 // result depends on thread order.
 #include "fslbm_dev.cuh"
+#include "mlp_dev.cuh"
 
 namespace fsl {
 
@@ -61,6 +62,94 @@ __global__ void k_normals(Dev s, float4* out) {
         int c = s.wl[i];
         out[c] = py_normal(s, c);
     }
+}
+
+// Learned normal (R-17), a warp per 16 interface cells of the list. Lane
+// (g, t) loads the stencil columns of its input fragments for the cells of
+// rows g and g + 8; together the four lanes of a group cover all 27 and
+// agree on whether a wall or solid cell lies in the block. The Parker-Youngs
+// normal is both the fallback (wall or solid in the block, raw length
+// outside [1/2, 2]) and the judge (network normal more than 30 degrees
+// away). out[c] = (n, curvature), curvature 0 where the fallback is taken.
+__global__ void __launch_bounds__(128) k_mlp_normals(Dev s, float4* out) {
+    const int count = *s.wl_count;
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    unsigned long long evaluated = 0, taken = 0;
+    for (int base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 16; base < count; base += nwarps * 16) {
+        int cell[2];
+        float v[2][8];
+        bool bad[2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int li = base + g + 8 * r;
+            cell[r] = li < count ? s.wl[li] : -1;
+            bad[r] = false;
+            int x = 0, y = 0, z = 0;
+            if (cell[r] >= 0) coords(s, cell[r], x, y, z);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int col = frag_col(j >> 2, j & 3, t);
+                float val = 0.f;
+                if (cell[r] >= 0 && col < 27) {
+                    const long long nb = nbr(s, x, y, z, cx(col), cy(col), cz(col));
+                    if (nb < 0) {
+                        bad[r] = true;
+                    } else {
+                        const int tn = s.flags[nb] & TYPE_MASK;
+                        bad[r] |= tn == T_SOL;
+                        val = tn == T_LIQ ? 1.f : (tn == T_IFC ? fminf(fmaxf(s.phi[nb], 0.f), 1.f) : 0.f);
+                    }
+                }
+                v[r][j] = val;
+            }
+            bad[r] |= __shfl_xor_sync(0xffffffffu, bad[r], 1);
+            bad[r] |= __shfl_xor_sync(0xffffffffu, bad[r], 2);
+        }
+        uint32_t xf[2][4];
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+            xf[kk][0] = pack_bf16(v[0][4 * kk + 0], v[0][4 * kk + 1]);
+            xf[kk][1] = pack_bf16(v[1][4 * kk + 0], v[1][4 * kk + 1]);
+            xf[kk][2] = pack_bf16(v[0][4 * kk + 2], v[0][4 * kk + 3]);
+            xf[kk][3] = pack_bf16(v[1][4 * kk + 2], v[1][4 * kk + 3]);
+        }
+        MlpAct act;
+        mlp_forward(*s.mlp, xf, act);
+        float y[2][4];
+        mlp_outputs(act, y[0], y[1]);
+        if (t < 2 && cell[t] >= 0) {
+            const int c = cell[t];
+            const float4 fd = py_normal(s, c);
+            float4 res = fd;
+            ++evaluated;
+            const float len = sqrtf(y[t][0] * y[t][0] + y[t][1] * y[t][1] + y[t][2] * y[t][2]);
+            if (!bad[t] && len >= 0.5f && len <= 2.f) {
+                const float mx = y[t][0] / len, my = y[t][1] / len, mz = y[t][2] / len;
+                if (mx * fd.x + my * fd.y + mz * fd.z >= 0.8660254f) {   // cos 30 degrees
+                    res = make_float4(mx, my, mz, y[t][3]);
+                    ++taken;
+                }
+            }
+            out[c] = res;
+        }
+    }
+    if (s.mlp_stats) {
+        for (int o = 16; o > 0; o >>= 1) {
+            evaluated += __shfl_xor_sync(0xffffffffu, evaluated, o);
+            taken += __shfl_xor_sync(0xffffffffu, taken, o);
+        }
+        if (lane == 0 && evaluated) {
+            atomicAdd(&s.mlp_stats[0], evaluated);
+            atomicAdd(&s.mlp_stats[1], taken);
+        }
+    }
+}
+
+static int normals_into(const Dev& s, float4* out, cudaStream_t st) {
+    if (s.mlp) k_mlp_normals<<<152 * 8, 128, 0, st>>>(s, out);
+    else k_normals<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(s, out);
+    return 1;
 }
 
 // ------------------------------------------------------------ conversion
@@ -295,14 +384,11 @@ __global__ void k_clear_conv(Dev s) {
     FOR_LIST(i, s.wl_count) s.conv[s.wl[i]] = 0;
 }
 
-int launch_normals(const Dev& s, float4* out, cudaStream_t st) {
-    k_normals<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(s, out);
-    return 1;
-}
+int launch_normals(const Dev& s, float4* out, cudaStream_t st) { return normals_into(s, out, st); }
 
 int launch_conversion(const Dev& s, int last_parity, cudaStream_t st) {
     k_update_phi<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(s);
-    k_normals<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(s, s.nrm1);
+    normals_into(s, s.nrm1, st);
     k_candidates<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(s);
     k_conflict<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(s);
     cudaMemsetAsync(s.nl_count, 0, sizeof(int), st);

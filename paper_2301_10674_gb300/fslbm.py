@@ -46,7 +46,11 @@ EXPORTED = (
     "fslbm_get_fields", "fslbm_set_fields", "fslbm_reduce", "fslbm_sync", "fslbm_steps_done",
     "fslbm_num_spheres", "fslbm_invariant_violations", "fslbm_timing", "fslbm_timing_read",
     "fslbm_cell_counts", "fslbm_reduce_fields_noalloc", "fslbm_destroy", "fslbm_strerror",
+    "fslbm_set_normal_model", "fslbm_normal_stats", "fslbm_mlp_stencils", "fslbm_mlp_gradient",
+    "fslbm_mlp_train", "fslbm_mlp_infer",
 )
+
+MLP_NPARAM = 6212
 
 
 class FslbmError(RuntimeError):
@@ -116,6 +120,14 @@ def load():
                                     ctypes.POINTER(ctypes.c_int64)]
     L.fslbm_cell_counts.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
     L.fslbm_reduce_fields_noalloc.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), vp, vp]
+    L.fslbm_set_normal_model.argtypes = [vp, vp, ctypes.c_int64]
+    L.fslbm_normal_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+    L.fslbm_mlp_stencils.argtypes = [vp, ctypes.c_int64, vp, vp, vp]
+    L.fslbm_mlp_gradient.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.c_double, ctypes.c_double, vp, vp, vp]
+    L.fslbm_mlp_train.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_uint64, ctypes.c_int,
+                                  vp, vp]
+    L.fslbm_mlp_infer.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
     L.fslbm_destroy.argtypes = [vp]
     L.fslbm_destroy.restype = None
     L.fslbm_strerror.argtypes = [ctypes.c_int]
@@ -194,6 +206,51 @@ def fslbm_reduce_fields_noalloc(pdf, types, mass, ncells: int, g, out, stream: i
     gg = (ctypes.c_double * 3)(*[float(v) for v in g])
     return load().fslbm_reduce_fields_noalloc(_ptr(pdf), _ptr(types), _ptr(mass), int(ncells), gg, _ptr(out),
                                               ctypes.c_void_p(stream or 0))
+
+
+def _stream(stream):
+    return ctypes.c_void_p(stream or 0)
+
+
+def fslbm_set_normal_model(h, w_bf16_bits) -> int:
+    """w_bf16_bits: host uint16 array of 6212 BF16 bit patterns, or None."""
+    if w_bf16_bits is None:
+        return load().fslbm_set_normal_model(h, None, 0)
+    w = np.ascontiguousarray(w_bf16_bits, np.uint16).reshape(-1)
+    return load().fslbm_set_normal_model(h, ctypes.c_void_p(w.ctypes.data), int(w.size))
+
+
+def fslbm_normal_stats(h) -> tuple[int, np.ndarray]:
+    out = (ctypes.c_uint64 * 2)()
+    rc = load().fslbm_normal_stats(h, out)
+    return rc, np.array(list(out), np.uint64)
+
+
+def fslbm_mlp_stencils(params, n: int, fill, target, stream=None) -> int:
+    return load().fslbm_mlp_stencils(_ptr(params), int(n), _ptr(fill), _ptr(target), _stream(stream))
+
+
+def fslbm_mlp_gradient(theta, fill, target, n: int, lam: float, mu: float, grad, loss, stream=None) -> int:
+    return load().fslbm_mlp_gradient(_ptr(theta), _ptr(fill), _ptr(target), int(n), float(lam), float(mu),
+                                     _ptr(grad), _ptr(loss), _stream(stream))
+
+
+def fslbm_mlp_train(theta, fill, target, n: int, steps: int, batch: int, lr: float, lam: float, mu: float,
+                    seed: int, augment: bool, loss_curve, stream=None, lr_end: float = 0.0) -> int:
+    return load().fslbm_mlp_train(_ptr(theta), _ptr(fill), _ptr(target), int(n), int(steps), int(batch),
+                                  float(lr), float(lr_end), float(lam), float(mu), int(seed), int(bool(augment)),
+                                  _ptr(loss_curve), _stream(stream))
+
+
+def fslbm_mlp_infer(theta, fill, n: int, out, stream=None) -> int:
+    return load().fslbm_mlp_infer(_ptr(theta), _ptr(fill), int(n), _ptr(out), _stream(stream))
+
+
+def bf16_bits(theta) -> np.ndarray:
+    """BF16 bit patterns (round to nearest even) of FP32 parameters."""
+    a = np.ascontiguousarray(theta, np.float32).reshape(-1).view(np.uint32).astype(np.uint64)
+    rounded = (a + 0x7FFF + ((a >> 16) & 1)) >> 16
+    return rounded.astype(np.uint16)
 
 
 def _ptr(a):
@@ -324,6 +381,21 @@ class Simulation:
     def reduce(self) -> np.ndarray:
         rc, out = fslbm_reduce(self.h)
         _check(rc, "fslbm_reduce")
+        return out
+
+    def set_normal_model(self, theta_or_bits):
+        """Learned normal from FP32 parameters (rounded to BF16) or BF16 bit
+        patterns (uint16); None returns to the finite-difference normal."""
+        if theta_or_bits is None:
+            _check(fslbm_set_normal_model(self.h, None), "fslbm_set_normal_model")
+            return
+        a = np.asarray(theta_or_bits)
+        bits = a if a.dtype == np.uint16 else bf16_bits(a)
+        _check(fslbm_set_normal_model(self.h, bits), "fslbm_set_normal_model")
+
+    def normal_stats(self) -> np.ndarray:
+        rc, out = fslbm_normal_stats(self.h)
+        _check(rc, "fslbm_normal_stats")
         return out
 
     def timing(self, on: bool):

@@ -265,3 +265,77 @@ def large() -> Workload:
 
 
 WORKLOADS = {"tiny": tiny, "mid": mid, "precision": precision, "large": large}
+
+
+# ---------------------------------------------------------------- surface stencils
+# Training and evaluation data of the learned interface normal: analytic
+# surfaces passing near the centre of a 3x3x3 block of cells. This function
+# draws the surfaces' random parameters only; the fill levels and the exact
+# normal and curvature at the surface point are computed from them by the
+# CUDA path and, independently, by the oracle.
+#
+# Row layout (float64, STENCIL_PARAMS columns):
+#   0 kind (0 plane, 1 liquid sphere, 2 gas sphere, 3 sine wave)
+#   1..3 n0: unit normal toward the gas at the surface point P = s n0
+#   4 s in [-1/2, 1/2] (signed offset of P from the centre cell's centre)
+#   5 r: sphere radius in [2, 30] cells (kinds 1, 2)
+#   6 A: sine amplitude in [1, 8] cells (kind 3)
+#   7 k: sine wavenumber 2 pi / lambda, lambda in [16, 256] cells (kind 3)
+#   8 phase in [0, 2 pi) (kind 3)
+#   9..11 e1: unit vector orthogonal to n0, the direction the sine varies along
+STENCIL_PARAMS = 12
+STENCIL_KIND_SHARES = (0.35, 0.20, 0.20, 0.25)
+
+
+def surface_stencils(n: int, seed: int = 4, kinds=None) -> np.ndarray:
+    """Seeded parameters of n analytic surfaces (see the row layout above).
+    ``kinds`` restricts the draw to the listed kinds (equal shares)."""
+    rng = np.random.default_rng(seed)
+    out = np.zeros((n, STENCIL_PARAMS))
+    if kinds is None:
+        cdf = np.cumsum(STENCIL_KIND_SHARES)
+        kind = np.searchsorted(cdf, rng.uniform(0.0, 1.0, n), side="right")
+    else:
+        kind = np.asarray(kinds)[rng.integers(0, len(kinds), n)]
+    kind = np.minimum(kind, 3)
+    cz = rng.uniform(-1.0, 1.0, n)
+    ph = rng.uniform(0.0, 2.0 * math.pi, n)
+    sz = np.sqrt(np.maximum(0.0, 1.0 - cz * cz))
+    n0 = np.stack([sz * np.cos(ph), sz * np.sin(ph), cz], axis=1)
+    # e1: a random direction in the plane orthogonal to n0
+    a = np.where(np.abs(n0[:, :1]) < 0.9, np.array([[1.0, 0.0, 0.0]]), np.array([[0.0, 1.0, 0.0]]))
+    u = a - np.sum(a * n0, axis=1, keepdims=True) * n0
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    v = np.cross(n0, u)
+    rot = rng.uniform(0.0, 2.0 * math.pi, n)[:, None]
+    e1 = np.cos(rot) * u + np.sin(rot) * v
+    e1 /= np.linalg.norm(e1, axis=1, keepdims=True)
+    out[:, 0] = kind
+    out[:, 1:4] = n0
+    out[:, 4] = rng.uniform(-0.5, 0.5, n)
+    r = rng.uniform(2.0, 30.0, n)
+    out[:, 5] = np.where((kind == 1) | (kind == 2), r, 0.0)
+    amp = rng.uniform(1.0, 8.0, n)
+    lam = rng.uniform(16.0, 256.0, n)
+    phase = rng.uniform(0.0, 2.0 * math.pi, n)
+    sine = kind == 3
+    out[:, 6] = np.where(sine, amp, 0.0)
+    out[:, 7] = np.where(sine, 2.0 * math.pi / lam, 0.0)
+    out[:, 8] = np.where(sine, phase, 0.0)
+    out[:, 9:12] = e1
+    return out
+
+
+def mlp_initial_weights(seed: int) -> np.ndarray:
+    """Seeded initial parameters of the 27-64-64-4 learned normal (FP32):
+    He-uniform weights U(-sqrt(6/fan_in), sqrt(6/fan_in)), zero biases, in
+    the order W1 (64x27), b1, W2 (64x64), b2, W3 (4x64), b3."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for shape in ((64, 27), (64,), (64, 64), (64,), (4, 64), (4,)):
+        if len(shape) == 2:
+            lim = math.sqrt(6.0 / shape[1])
+            parts.append(rng.uniform(-lim, lim, shape).ravel())
+        else:
+            parts.append(np.zeros(shape))
+    return np.concatenate(parts).astype(np.float32)

@@ -1,0 +1,320 @@
+"""GPU tests of the learned interface normal, through the C ABI:
+
+* training data: fill levels and labels of analytic surfaces against the
+  oracle's voxeliser (exact planes, sphere chords, sine samples);
+* training kernels: loss and gradient against the FP64 oracle (BF16
+  operands: 2e-2 relative per parameter block), the batch sampler and cube
+  symmetries against the oracle's SplitMix64 draw;
+* inference inside the step: the normals of a wavy surface against the
+  oracle's learned-normal model with the same (BF16-valued) weights;
+* the gain: a network trained on the GPU against the finite-difference
+  normal on held-out analytic surfaces, and a coupled run with the network
+  against one without (mass conservation, surface profile)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import mlp as OM
+from oracle import stencils as OS
+from paper_2301_10674_gb300 import fslbm as F
+from paper_2301_10674_gb300 import workloads as W
+
+from helpers import oracle_from_workload
+
+pytestmark = pytest.mark.gpu
+
+LAM, MU = 0.4, 0.1          # 0.1 r_min^2 with r_min = 2; unit-length penalty
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2301_10674_gb300 import build as B
+    B.build()
+    F.load()
+
+
+def _dev(a, dtype=None):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def _zeros(shape, dtype):
+    import torch
+    return torch.zeros(shape, dtype=dtype, device="cuda")
+
+
+def _ok(rc, where):
+    assert rc == 0, f"{where}: {rc}"
+
+
+def _gpu_stencils(params):
+    import torch
+    n = len(params)
+    fill = _zeros((n, 27), torch.float32)
+    tgt = _zeros((n, 4), torch.float32)
+    _ok(F.fslbm_mlp_stencils(_dev(params), n, fill, tgt), "fslbm_mlp_stencils")
+    return fill, tgt
+
+
+# ---------------------------------------------------------------- training data
+def test_stencils_match_the_oracle():
+    parts = [W.surface_stencils(n, seed=21 + k, kinds=[k]) for k, n in ((0, 40), (1, 20), (2, 20), (3, 6))]
+    params = np.concatenate(parts)
+    fill, tgt = _gpu_stencils(params)
+    fill, tgt = fill.cpu().numpy(), tgt.cpu().numpy()
+    ref_f, ref_t = OS.make(params)
+    kind = params[:, 0].astype(int)
+    # planes: FP64 closed form on both sides; spheres: FP32 chords; sines:
+    # FP32 phases, a few of the 262144 samples per cell may flip
+    tol = np.array([2e-6, 3e-5, 3e-5, 2.5e-4])[kind][:, None]
+    assert (np.abs(fill - ref_f) <= tol).all(), np.abs(fill - ref_f).max(axis=1)
+    assert np.abs(tgt - ref_t).max() < 2e-6
+    # one surface alone (a grid of one block) and a ragged count
+    f1, t1 = _gpu_stencils(params[37:38])
+    assert np.array_equal(f1.cpu().numpy()[0], fill[37])
+
+
+# ---------------------------------------------------------------- gradients
+def _oracle_set(n, seed):
+    kinds = [0, 1, 2]
+    params = W.surface_stencils(n, seed=seed, kinds=kinds)
+    return OS.make(params)
+
+
+def test_gradient_matches_the_oracle():
+    import torch
+    X, Y = _oracle_set(300, 31)                  # 2 full blocks of 128 and a ragged tail
+    theta = OM.init(7)
+    theta[64 * 27:64 * 27 + 64] = 0.05
+    g = _zeros(F.MLP_NPARAM, torch.float32)
+    loss = _zeros(1, torch.float32)
+    _ok(F.fslbm_mlp_gradient(_dev(theta, torch.float32), _dev(X, torch.float32), _dev(Y, torch.float32), len(X),
+                             LAM, MU, g, loss), "fslbm_mlp_gradient")
+    L_ref, g_ref = OM.loss_and_grad(theta, X, Y[:, :3], Y[:, 3], LAM, MU)
+    g = g.cpu().numpy().astype(np.float64)
+    assert abs(float(loss) - L_ref) < 1e-2 * abs(L_ref)
+    offs = np.cumsum([0] + [int(np.prod(s)) for s in OM.SIZES])
+    for a, b in zip(offs[:-1], offs[1:]):
+        rel = np.linalg.norm(g[a:b] - g_ref[a:b]) / np.linalg.norm(g_ref[a:b])
+        assert rel < 2e-2, (a, b, rel)
+
+
+def _py_network(scale=0.08):
+    """Parker-Youngs gradient as a network: raw normal = -scale grad."""
+    C = OS.CELLS.astype(float)
+    wpy = np.array([{0: 0.0, 1: 4.0, 2: 2.0, 3: 1.0}[int(np.abs(c).sum())] for c in C])
+    W1 = np.zeros((64, 27))
+    W1[0:3] = (wpy[:, None] * C).T
+    W1[3:6] = -(wpy[:, None] * C).T
+    W2 = np.zeros((64, 64))
+    W2[np.arange(6), np.arange(6)] = 1.0
+    W3 = np.zeros((4, 64))
+    W3[:3, 0:3] = -scale * np.eye(3)
+    W3[:3, 3:6] = scale * np.eye(3)
+    return np.concatenate([W1.ravel(), np.zeros(64), W2.ravel(), np.zeros(64), W3.ravel(), np.zeros(4)])
+
+
+def test_sampler_and_symmetries_match_the_oracle():
+    """lr = 0: each step's loss is the loss of that step's drawn batch under
+    a network that already predicts the finite-difference normal, small for
+    correctly mapped samples and about 1 for a wrong symmetry mapping."""
+    import torch
+    X, Y = _oracle_set(64, 41)
+    theta = _py_network()
+    steps, batch, seed = 6, 16, 12345
+    th = _dev(theta, torch.float32)
+    curve = _zeros(steps, torch.float32)
+    _ok(F.fslbm_mlp_train(th, _dev(X, torch.float32), _dev(Y, torch.float32), len(X), steps, batch, 0.0, LAM, MU,
+                          seed, True, curve), "fslbm_mlp_train")
+    assert np.array_equal(th.cpu().numpy(), theta.astype(np.float32))      # lr = 0 leaves theta
+    _, ref = OM.train(theta, X, Y, steps, batch, 0.0, LAM, MU, seed, augment=True)
+    got = curve.cpu().numpy()
+    assert np.all(np.abs(got - ref) < 2e-2 * np.abs(ref) + 2e-3), (got, ref)
+    # the losses differ between steps by far more than the tolerance
+    assert np.ptp(ref) > 0.1 * ref.mean()
+
+
+def test_adam_steps_track_the_oracle():
+    import torch
+    X, Y = _oracle_set(256, 43)
+    theta = OM.init(9)
+    steps = 40
+    th = _dev(theta, torch.float32)
+    curve = _zeros(steps, torch.float32)
+    _ok(F.fslbm_mlp_train(th, _dev(X, torch.float32), _dev(Y, torch.float32), len(X), steps, 64, 1e-3, LAM, MU,
+                          5, True, curve), "fslbm_mlp_train")
+    t_ref, ref = OM.train(theta, X, Y, steps, 64, 1e-3, LAM, MU, 5, augment=True)
+    got = curve.cpu().numpy()
+    assert abs(got[0] - ref[0]) < 1e-2 * ref[0]
+    assert np.all(np.abs(got - ref) < 5e-2 * ref), (got, ref)
+    d_gpu = th.cpu().numpy() - theta
+    d_ref = t_ref - theta
+    assert np.dot(d_gpu, d_ref) / (np.linalg.norm(d_gpu) * np.linalg.norm(d_ref)) > 0.95
+
+
+# ---------------------------------------------------------------- inference in the step
+def _wavy(w):
+    x = (np.arange(w.nx) + 0.5) / w.nx
+    y = (np.arange(w.ny) + 0.5) / w.ny
+    return 20.0 + 3.0 * np.sin(2 * np.pi * x)[None, :] + 1.5 * np.cos(2 * np.pi * y)[:, None]
+
+
+def _near_threshold(theta, X, fd):
+    y, _ = OM.forward(theta, X[None, :], bf16=True)
+    n = y[0, :3]
+    L = np.linalg.norm(n)
+    c = float(n @ fd) / L if L > 0 else 0.0
+    return min(abs(L - 0.5), abs(L - 2.0)) < 1e-2 or abs(c - math.cos(math.radians(30))) < 1e-2
+
+
+def test_in_step_normals_match_the_oracle():
+    w = W.tiny()
+    w.generate()
+    rng = np.random.default_rng(5)
+    theta = OM.round_bf16(_py_network() + rng.normal(0.0, 0.02, OM.NPARAM))
+    sim = F.Simulation.from_workload(w)
+    o = oracle_from_workload(w)
+    h = _wavy(w)
+    sim.init_surface(h)
+    o.init_surface(h)
+    fd_g = sim.get(F.FIELD_NORMAL)
+    sim.set_normal_model(theta)
+    o.set_mlp(theta, bf16=True)
+    ng, no = sim.get(F.FIELD_NORMAL), o.get(O.F_NORMAL)
+    fd_o = oracle_from_workload(w)
+    fd_o.init_surface(h)
+    fd = fd_o.get(O.F_NORMAL)
+    t = o.get(O.F_TYPE)
+    phi = o.get(O.F_PHI)
+    ifc = np.argwhere(t == O.INTERFACE)
+    taken = differ = 0
+    for z, y, x in ifc:
+        a, b = ng[:, z, y, x], no[:, z, y, x]
+        o_mlp = not np.allclose(b, fd[:, z, y, x], atol=1e-12)
+        g_mlp = not np.allclose(a, fd_g[:, z, y, x], atol=1e-6)
+        taken += o_mlp
+        if o_mlp == g_mlp:
+            assert np.abs(a - b).max() < 1e-2, ((z, y, x), a, b)
+        else:
+            X = np.zeros(27)
+            for q in range(27):
+                c = OS.CELLS[q]
+                tt = t[z + c[2], y + c[1], (x + c[0]) % w.nx]
+                X[q] = 1.0 if tt == O.LIQUID else (min(max(phi[z + c[2], y + c[1], (x + c[0]) % w.nx], 0), 1)
+                                                   if tt == O.INTERFACE else 0.0)
+            assert _near_threshold(theta, X, fd[:, z, y, x]), (z, y, x)
+            differ += 1
+    assert taken > 0.3 * len(ifc) and differ <= 0.01 * len(ifc)
+    ev, tk = sim.normal_stats()
+    assert ev == len(ifc) and 0 < tk < ev      # wall-side cells fall back
+    # a few coupled steps with the learned normal on both sides
+    sim.step(10)
+    o.step(10)
+    tg, to = sim.get(F.FIELD_TYPE), o.get(O.F_TYPE)
+    assert (tg != to).sum() <= 2
+    m_g = sim.reduce()[0]
+    m_o = o.reduce()[0]
+    assert abs(m_g - m_o) < 1e-5 * m_o
+    sim.close()
+
+
+def test_missing_weights_are_a_state_error():
+    p = F.params_from_workload(W.tiny().generate())
+    p.normal_model = 1
+    sim = F.Simulation(p)
+    assert F.fslbm_step(sim.h, 1) == -6          # FSLBM_ESTATE: no weights yet
+    sim.set_normal_model(_py_network())
+    sim.step(1)
+    sim.set_normal_model(None)
+    sim.step(1)
+    assert F.fslbm_set_normal_model(sim.h, np.zeros(100, np.uint16)) == -1
+    sim.close()
+
+
+# ---------------------------------------------------------------- the gain
+@pytest.fixture(scope="module")
+def trained():
+    """A network trained on the GPU by the library's own kernels: 2^18
+    voxelised surfaces, 4000 Adam steps of 4096 with cube-symmetry
+    augmentation."""
+    import torch
+    params = W.surface_stencils(1 << 18, seed=4)
+    fill, tgt = _gpu_stencils(params)
+    theta = _dev(OM.init(11), torch.float32)
+    steps = 4000
+    curve = _zeros(steps, torch.float32)
+    _ok(F.fslbm_mlp_train(theta, fill, tgt, len(params), steps, 4096, 1e-3, LAM, MU, 17, True, curve),
+        "fslbm_mlp_train")
+    c = curve.cpu().numpy()
+    assert np.isfinite(c).all() and c[-100:].mean() < 0.2 * c[:10].mean()
+    return theta.cpu().numpy().astype(np.float64), c
+
+
+def _angle(a, b):
+    a = a / np.linalg.norm(a, axis=1, keepdims=True)
+    b = b / np.linalg.norm(b, axis=1, keepdims=True)
+    return np.degrees(np.arccos(np.clip(np.sum(a * b, axis=1), -1.0, 1.0)))
+
+
+def test_trained_network_beats_the_finite_difference_normal(trained):
+    import torch
+    theta, curve = trained
+    kinds = {0: 120, 1: 80, 2: 80, 3: 24}
+    params = np.concatenate([W.surface_stencils(n, seed=900 + k, kinds=[k]) for k, n in kinds.items()])
+    X, Y = OS.make(params)                          # held out: another seed, oracle voxeliser
+    out = _zeros((len(X), 4), torch.float32)
+    _ok(F.fslbm_mlp_infer(_dev(theta, torch.float32), _dev(X, torch.float32), len(X), out), "fslbm_mlp_infer")
+    y = out.cpu().numpy().astype(np.float64)
+    fd = np.array([O.normal_stencil(x) for x in X])
+    L = np.linalg.norm(y[:, :3], axis=1)
+    n_ml = y[:, :3] / L[:, None]
+    use = (L >= 0.5) & (L <= 2.0) & (np.sum(n_ml * fd, axis=1) >= math.cos(math.radians(30)))
+    n_used = np.where(use[:, None], n_ml, fd)
+    e_fd = _angle(fd, Y[:, :3])
+    e_ml = _angle(n_used, Y[:, :3])
+    kind = params[:, 0].astype(int)
+    report = {k: (e_fd[kind == k].mean(), e_ml[kind == k].mean()) for k in kinds}
+    print("mean angular error (deg), FD vs learned:", report, "taken:", use.mean())
+    assert use.mean() > 0.95
+    assert e_ml.mean() < 0.6 * e_fd.mean(), report
+    for k in kinds:
+        assert report[k][1] < report[k][0], (k, report[k])
+    # curvature: the finite-difference normal carries none; the network's
+    # estimate beats the zero guess on spheres
+    sph = (kind == 1) | (kind == 2)
+    assert np.abs(y[sph, 3] - Y[sph, 3]).mean() < 0.5 * np.abs(Y[sph, 3]).mean()
+
+
+def test_coupled_run_with_the_learned_normal(trained):
+    """The tiny flume for 200 steps with the trained network and without:
+    mass conserved as tightly, the surface profile (liquid volume per column)
+    within a small fraction of a cell, no invariant violations."""
+    theta, _ = trained
+    w = W.tiny()
+    w.generate()
+    runs = {}
+    for tag in ("fd", "mlp"):
+        sim = F.Simulation.from_workload(w)
+        sim.init_surface(_wavy(w))
+        if tag == "mlp":
+            sim.set_normal_model(theta)
+        m0 = sim.reduce()[0]
+        sim.step(200)
+        m1 = sim.reduce()[0]
+        t = sim.get(F.FIELD_TYPE)
+        phi = sim.get(F.FIELD_PHI)
+        vol = np.where(t == O.LIQUID, 1.0, np.where(t == O.INTERFACE, phi, 0.0)).sum(axis=0)
+        runs[tag] = (abs(m1 - m0) / m0, vol, sim.violations, sim.normal_stats())
+        sim.close()
+    assert runs["fd"][0] < 1e-6 and runs["mlp"][0] < 1e-6
+    assert runs["mlp"][2] == 0
+    ev, tk = runs["mlp"][3]
+    assert tk > 0.5 * ev
+    assert np.abs(runs["mlp"][1] - runs["fd"][1]).max() < 0.1

@@ -59,3 +59,33 @@ def test_training_reduces_the_loss_on_planes():
         L, g = mlp.loss_and_grad(theta, X, n, k, 0.1)
         theta, m, v = mlp.adam(theta, g, m, v, t, lr=3e-3)
     assert L < 0.1 * L0
+
+
+def test_gradient_with_norm_penalty_matches_central_differences():
+    rng = np.random.default_rng(7)
+    theta = mlp.init(4)
+    theta[64 * 27:64 * 27 + 64] = rng.uniform(0.05, 0.2, 64)
+    X, n, k = _batch(rng, 12)
+    L, g = mlp.loss_and_grad(theta, X, n, k, lam=0.4, mu=0.1)
+    h = 1e-6
+    for i in rng.choice(mlp.NPARAM, 200, replace=False):
+        tp = theta.copy(); tp[i] += h
+        tm = theta.copy(); tm[i] -= h
+        num = (mlp.loss_and_grad(tp, X, n, k, 0.4, 0.1)[0] - mlp.loss_and_grad(tm, X, n, k, 0.4, 0.1)[0]) / (2 * h)
+        assert abs(num - g[i]) <= 1e-6 * max(1.0, abs(g[i])) + 1e-9, (i, num, g[i])
+
+
+def test_bf16_rounding_is_nearest_even():
+    # bfloat16 keeps 8 significant bits: spacing 2^-7 on [1, 2)
+    vals = np.array([1.0, 1 + 2 ** -8, 1 + 3 * 2 ** -8, 1 + 2 ** -8 + 2 ** -20, -3.0, 0.0, 1e-3])
+    want = np.array([1.0, 1.0, 1 + 2 ** -6, 1 + 2 ** -7, -3.0, 0.0, 0.00099945068359375])
+    assert np.array_equal(mlp.round_bf16(vals), want)
+
+
+def test_augmented_training_lowers_the_loss():
+    from oracle import stencils
+    from paper_2301_10674_gb300.workloads import surface_stencils
+    fills, labs = stencils.make(surface_stencils(64, seed=12, kinds=[0]))
+    theta = mlp.init(5)
+    theta, losses = mlp.train(theta, fills, labs, steps=60, batch=32, lr=3e-3, lam=0.4, mu=0.1, seed=3)
+    assert losses[-10:].mean() < 0.5 * losses[:5].mean()
