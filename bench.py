@@ -125,8 +125,10 @@ def _workload(name: str, rank: int):
 
 # ---------------------------------------------------------------- oracle leg
 
-def run_oracle(w, steps: int, warmup: int, crop_nx: int) -> dict:
-    """The FP64 oracle on an x-crop of the same workload (host cores)."""
+def run_oracle(w, steps: int, warmup: int, crop_nx: int, theta=None) -> dict:
+    """The FP64 oracle on an x-crop of the same workload (host cores), with
+    the learned normal when weights are given (rounded to BF16 as the GPU
+    holds them)."""
     import oracle as O
     c = w.crop_x(crop_nx)
     o = O.Oracle(O.OracleParams(
@@ -136,6 +138,10 @@ def run_oracle(w, steps: int, warmup: int, crop_nx: int) -> dict:
         poisson=c.poisson, collision_time=c.collision_time, dem_substeps=c.dem_substeps))
     if c.nspheres:
         o.add_spheres(c.xyz, c.radius, c.fixed)
+    if theta is not None:
+        from paper_2301_10674_gb300 import fslbm as F
+        bits = F.bf16_bits(theta).astype(np.uint32) << 16
+        o.set_mlp(bits.view(np.float32).astype(np.float64), bf16=True)
     o.step(warmup)
     t0 = time.perf_counter()
     o.step(steps)
@@ -143,7 +149,8 @@ def run_oracle(w, steps: int, warmup: int, crop_nx: int) -> dict:
     cells = c.nx * c.ny * c.nz
     return {"value": cells * steps / dt / 1e6, "cores": O.threads(), "seconds": dt,
             "sample": f"{c.nx}x{c.ny}x{c.nz} x-crop of {w.name} ({c.nspheres} spheres), {steps} steps "
-                      f"after {warmup} warm-up steps"}
+                      f"after {warmup} warm-up steps"
+                      + (", learned normal" if theta is not None else ", finite-difference normal")}
 
 
 # ---------------------------------------------------------------- GPU leg
@@ -154,7 +161,8 @@ LAM, MU = 0.4, 0.1
 def train_normal_model(stream, n_stencils: int, steps: int, seed: int = 4) -> tuple[np.ndarray, dict]:
     """Learned normal trained by the library's own kernels (not timed):
     voxelised analytic surfaces (planes, droplets, bubbles, sine waves), Adam
-    on batches of 4096 with cube-symmetry augmentation."""
+    on batches of 4096 with cube-symmetry augmentation, step size decaying
+    geometrically from 2e-3 to 1e-5."""
     import torch
 
     from paper_2301_10674_gb300 import fslbm as F
@@ -169,11 +177,11 @@ def train_normal_model(stream, n_stencils: int, steps: int, seed: int = 4) -> tu
     t1 = time.perf_counter()
     theta = torch.from_numpy(W.mlp_initial_weights(seed)).cuda()
     curve = torch.empty(steps, dtype=torch.float32, device="cuda")
-    F._check(F.fslbm_mlp_train(theta, fill, tgt, n_stencils, steps, 4096, 1e-3, LAM, MU, seed, True, curve,
-                               stream.cuda_stream), "fslbm_mlp_train")
+    F._check(F.fslbm_mlp_train(theta, fill, tgt, n_stencils, steps, 4096, 2e-3, LAM, MU, seed, True, curve,
+                               stream.cuda_stream, lr_end=1e-5), "fslbm_mlp_train")
     t2 = time.perf_counter()
     c = curve.cpu().numpy()
-    return theta.cpu().numpy(), {"stencils": n_stencils, "steps": steps, "batch": 4096,
+    return theta.cpu().numpy(), {"stencils": n_stencils, "steps": steps, "batch": 4096, "lr": [2e-3, 1e-5],
                                  "loss_first": float(c[0]), "loss_last100": float(c[-100:].mean()),
                                  "data_s": round(t1 - t0, 2), "train_s": round(t2 - t1, 2)}
 
@@ -277,7 +285,7 @@ def run_ours(args, world, rank, local):
         e2e = run_e2e(args, w, STORAGE[args.storage], theta, stream, world)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = run_oracle(w, steps=args.cpu_steps, warmup=1, crop_nx=args.cpu_crop)
+        cpu = run_oracle(w, steps=args.cpu_steps, warmup=1, crop_nx=args.cpu_crop, theta=theta)
         cpu = {"value": cpu["value"], "unit": UNIT, "cores": cpu["cores"], "kind": "oracle", "sample": cpu["sample"]}
     if rank != 0:
         return None
@@ -399,7 +407,7 @@ def main():
     ap.add_argument("--compare", action=argparse.BooleanOptionalAction, default=True,
                     help="also time plain FP32 with the finite-difference normal")
     ap.add_argument("--mlp-stencils", type=int, default=1 << 22)
-    ap.add_argument("--mlp-steps", type=int, default=4000)
+    ap.add_argument("--mlp-steps", type=int, default=40000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=3)

@@ -59,7 +59,10 @@ extern "C" {
 #define FSLBM_PERIODIC_Y 2u
 #define FSLBM_PERIODIC_Z 4u
 
-/* PDF storage (all arithmetic is FP32; the stored value is f_i - w_i) */
+/* PDF storage (all arithmetic is FP32; the stored value is f_i - w_i, in
+ * FP16 multiplied by the exact factor 2^12 so that small deviations stay in
+ * FP16's normal range; |f_i - w_i| above 16 overflows and is reported as
+ * FSLBM_ENAN) */
 #define FSLBM_STORE_FP32 0
 #define FSLBM_STORE_FP16 1
 #define FSLBM_STORE_BF16 2
@@ -96,7 +99,8 @@ typedef struct {
     double poisson;              /* Poisson ratio of the particle material */
     double collision_time;       /* DEM collision time T_c (time steps) */
     int32_t dem_substeps;        /* DEM sub-steps per LBM step, >= 1 */
-    int32_t reserved0;
+    int32_t link_mass_correction; /* 1: the net mass the moving bounce-back injects
+                                    into liquid cells is taken from the mass pool */
     int64_t capacity_particles;  /* maximum number of spheres (0: 65536) */
     int64_t capacity_interface;  /* maximum interface cells (0: ncells/4 + 4096) */
 } fslbm_params;

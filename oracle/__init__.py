@@ -60,6 +60,7 @@ class _Params(ctypes.Structure):
         ("poisson", ctypes.c_double),
         ("collision_time", ctypes.c_double),
         ("dem_substeps", ctypes.c_int),
+        ("link_mass_correction", ctypes.c_int),
     ]
 
 
@@ -117,6 +118,7 @@ class OracleParams:
     poisson: float = 0.22
     collision_time: float = 24.0
     dem_substeps: int = 10
+    link_mass_correction: int = 1
 
     def _c(self) -> _Params:
         p = _Params()
@@ -135,6 +137,7 @@ class OracleParams:
         p.poisson = self.poisson
         p.collision_time = self.collision_time
         p.dem_substeps = self.dem_substeps
+        p.link_mass_correction = self.link_mass_correction
         return p
 
 

@@ -66,6 +66,8 @@ typedef struct {
     double poisson;           /* Poisson ratio nu_p */
     double collision_time;    /* DEM collision time T_c */
     int dem_substeps;         /* DEM sub-steps per LBM step */
+    int link_mass_correction; /* 1: net moving-bounce-back injection into liquid
+                                 cells is taken from the pool (R-12a) */
 } orc_params;
 
 typedef struct {
@@ -382,26 +384,27 @@ static void mlp_normal(const orc* o, long cell, const double* phi, double n[3])
     pyn_normal(o, cell, phi, fd);
     n[0] = fd[0]; n[1] = fd[1]; n[2] = fd[2];
     if (bad) return;
+    /* o->mlp already holds the operand values (weights rounded at set-up
+     * when mlp_bf16); inputs and hidden activations are rounded here */
     const double *W1 = o->mlp, *b1 = W1 + 64 * 27, *W2 = b1 + 64, *b2 = W2 + 64 * 64, *W3 = b2 + 64,
                  *b3 = W3 + 4 * 64;
     const int r = o->mlp_bf16;
     double h1[64], h2[64], out[4];
+    if (r)
+        for (int i = 0; i < NQ; ++i) in[i] = bf16_round(in[i]);
     for (int j = 0; j < 64; ++j) {
         double a = b1[j];
-        for (int i = 0; i < NQ; ++i)
-            a += (r ? bf16_round(W1[j * 27 + i]) * bf16_round(in[i]) : W1[j * 27 + i] * in[i]);
-        h1[j] = a > 0.0 ? a : 0.0;
+        for (int i = 0; i < NQ; ++i) a += W1[j * 27 + i] * in[i];
+        h1[j] = a > 0.0 ? (r ? bf16_round(a) : a) : 0.0;
     }
     for (int j = 0; j < 64; ++j) {
         double a = b2[j];
-        for (int i = 0; i < 64; ++i)
-            a += (r ? bf16_round(W2[j * 64 + i]) * bf16_round(h1[i]) : W2[j * 64 + i] * h1[i]);
-        h2[j] = a > 0.0 ? a : 0.0;
+        for (int i = 0; i < 64; ++i) a += W2[j * 64 + i] * h1[i];
+        h2[j] = a > 0.0 ? (r ? bf16_round(a) : a) : 0.0;
     }
     for (int k = 0; k < 4; ++k) {
         double a = b3[k];
-        for (int i = 0; i < 64; ++i)
-            a += (r ? bf16_round(W3[k * 64 + i]) * bf16_round(h2[i]) : W3[k * 64 + i] * h2[i]);
+        for (int i = 0; i < 64; ++i) a += W3[k * 64 + i] * h2[i];
         out[k] = a;
     }
     double len = sqrt(out[0] * out[0] + out[1] * out[1] + out[2] * out[2]);
@@ -572,6 +575,13 @@ int orc_set_mlp(orc* o, const double* theta, int bf16)
         o->mlp = (double*)malloc(sizeof(double) * MLP_NPARAM);
         if (!o->mlp) return -1;
         memcpy(o->mlp, theta, sizeof(double) * MLP_NPARAM);
+        if (bf16) {   /* weight matrices to their operand values; biases stay */
+            for (int i = 0; i < MLP_NPARAM; ++i) {
+                int is_bias = (i >= 64 * 27 && i < 64 * 27 + 64) ||
+                              (i >= 64 * 27 + 64 + 64 * 64 && i < 64 * 27 + 64 + 64 * 64 + 64) || i >= 6208;
+                if (!is_bias) o->mlp[i] = bf16_round(o->mlp[i]);
+            }
+        }
     }
     o->mlp_bf16 = bf16;
     for (long i = 0; i < o->n; ++i)
@@ -936,6 +946,7 @@ static void one_step(orc* o)
      * force. Torque (x_b - X_p) x F. */
     for (int p = 0; p < o->np; ++p)
         for (int a = 0; a < 3; ++a) o->Fh[3 * p + a] = o->Th[3 * p + a] = 0.0;
+    double injected = 0.0;   /* mass the moving bounce-back added to liquid cells */
     for (long i = 0; i < n; ++i) {
         if (!is_fluid(o->type[i])) continue;
         int x, y, z;
@@ -952,6 +963,7 @@ static void one_step(orc* o)
             double cu = CX[q] * ub[0] + CY[q] * ub[1] + CZ[q] * ub[2];
             double fout = fs[qb] - WQ[qb];                       /* f*_ibar - w */
             double fback = fs[qb] + 6.0 * WQ[q] * rho0 * cu - WQ[q];  /* f_i - w */
+            if (o->type[i] == T_LIQ) injected += 6.0 * WQ[q] * rho0 * cu;
             double c[3] = {CX[q], CY[q], CZ[q]};
             double Fl[3];
             for (int a = 0; a < 3; ++a) Fl[a] = -c[a] * (fout + fback) - ub[a] * (fout - fback);
@@ -962,6 +974,11 @@ static void one_step(orc* o)
             for (int a = 0; a < 3; ++a) { o->Fh[3 * p + a] += Fl[a]; o->Th[3 * p + a] += tq[a]; }
         }
     }
+
+    /* R-12a: over a closed voxel surface the injections cancel; where a
+     * moving sphere touches a wall or another solid they do not, and the
+     * remainder is taken from the pool so that the liquid mass is kept */
+    if (P->link_mass_correction) o->pool -= injected;
 
     /* commit S1-S3 */
     double* tmp = o->f; o->f = o->ft; o->ft = tmp;

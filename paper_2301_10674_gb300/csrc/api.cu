@@ -117,6 +117,7 @@ void fslbm_default_params(fslbm_params* p) {
     p->poisson = 0.22;
     p->collision_time = 24.0;
     p->dem_substeps = 10;
+    p->link_mass_correction = 1;
 }
 
 const char* fslbm_strerror(int code) {
@@ -143,6 +144,7 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     if (!(p->omega > 0.0 && p->omega < 2.0)) return FSLBM_EINVAL;
     if (p->sigma != 0.0 || p->normal_model < 0 || p->normal_model > 1 || p->init_profile != 0) return FSLBM_EINVAL;
     if (p->storage < 0 || p->storage > 2) return FSLBM_EINVAL;
+    if (p->link_mass_correction < 0 || p->link_mass_correction > 1) return FSLBM_EINVAL;
     if (p->dem_substeps < 1 || !(p->restitution > 0.0 && p->restitution <= 1.0)) return FSLBM_EINVAL;
     if (!(p->collision_time > 0.0) || !(p->rho_p > 0.0) || !(p->rho_gas > 0.0)) return FSLBM_EINVAL;
     if (!(p->poisson >= 0.0 && p->poisson < 1.0) || !(p->friction >= 0.0)) return FSLBM_EINVAL;
@@ -184,6 +186,7 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     d.eps_conv = (float)p->eps_conv;
     d.eps_normal = (float)p->eps_normal;
     d.recon_normal = p->reconstruct_normal;
+    d.link_corr = p->link_mass_correction;
     d.storage = p->storage;
     d.rho_p = p->rho_p;
     d.restitution = p->restitution;

@@ -59,6 +59,7 @@ struct Dev {
     float rho_gas, eps_conv, eps_normal;
     int recon_normal;
     int storage;
+    int link_corr;     // net moving-bounce-back injection into liquid cells taken from the pool
     // element offsets of an odd step for interior cells: the pull of
     // direction q reads f[cell + pull_off[q]], the push writes
     // f[cell + push_off[q]] (constant per launch, held in the parameter bank)
@@ -138,9 +139,14 @@ template <> struct Store<float> {
     __device__ static __forceinline__ float ld(const float* p) { return *p; }
     __device__ static __forceinline__ void st(float* p, float v) { *p = v; }
 };
+// FP16 holds (f - w) 2^12: the scale is exact, so rounding is FP16's own
+// (11 significant bits), but the normal range starts at 1.5e-8 instead of
+// 6.1e-5 and deviations of slow flows do not fall into subnormals; the
+// largest deviation held is 16.
+constexpr float FP16_SCALE = 4096.f, FP16_UNSCALE = 1.f / 4096.f;
 template <> struct Store<__half> {
-    __device__ static __forceinline__ float ld(const __half* p) { return __half2float(*p); }
-    __device__ static __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+    __device__ static __forceinline__ float ld(const __half* p) { return __half2float(*p) * FP16_UNSCALE; }
+    __device__ static __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v * FP16_SCALE); }
 };
 template <> struct Store<__nv_bfloat16> {
     __device__ static __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
@@ -149,12 +155,12 @@ template <> struct Store<__nv_bfloat16> {
 
 __device__ __forceinline__ float ld_any(const Dev& s, const void* base, long long i) {
     if (s.storage == FSLBM_STORE_FP32) return static_cast<const float*>(base)[i];
-    if (s.storage == FSLBM_STORE_FP16) return __half2float(static_cast<const __half*>(base)[i]);
+    if (s.storage == FSLBM_STORE_FP16) return Store<__half>::ld(static_cast<const __half*>(base) + i);
     return __bfloat162float(static_cast<const __nv_bfloat16*>(base)[i]);
 }
 __device__ __forceinline__ void st_any(const Dev& s, void* base, long long i, float v) {
     if (s.storage == FSLBM_STORE_FP32) static_cast<float*>(base)[i] = v;
-    else if (s.storage == FSLBM_STORE_FP16) static_cast<__half*>(base)[i] = __float2half_rn(v);
+    else if (s.storage == FSLBM_STORE_FP16) Store<__half>::st(static_cast<__half*>(base) + i, v);
     else static_cast<__nv_bfloat16*>(base)[i] = __float2bfloat16_rn(v);
 }
 

@@ -420,6 +420,7 @@ template <typename S, int PAR>
 __global__ void __launch_bounds__(256) k_solid_links(Dev s) {
     const int count = min(*s.sl_count, s.sl_cap);
     const int stride = gridDim.x * blockDim.x;
+    float injected = 0.f;   // mass the moving bounce-back adds to liquid cells
     for (int base = blockIdx.x * blockDim.x; base < count; base += stride) {
         const int i = base + threadIdx.x;
         int key = -1;
@@ -433,13 +434,14 @@ __global__ void __launch_bounds__(256) k_solid_links(Dev s) {
             const long long n = s.n;
             const NbrOffsets o = nbr_offsets(s, x, y, z);
             // phase 1: which neighbours are fluid (wall faces excluded)
-            unsigned fluidm = 0;
+            unsigned fluidm = 0, liqm = 0;
 #pragma unroll
             for (int q = 0; q < 27; ++q) {
                 if (q == 13 || (o.wall & wall_bits(cx(q), cy(q), cz(q)))) continue;
                 const int xn = cell + o.ox[1 + cx(q)] + o.oy[1 + cy(q)] + o.oz[1 + cz(q)];
                 const int tn = s.flags[xn] & TYPE_MASK;
                 fluidm |= (tn == T_LIQ || tn == T_IFC) ? (1u << q) : 0u;
+                liqm |= tn == T_LIQ ? (1u << q) : 0u;
             }
             if (p < 0 || p >= s.np) {
                 if (fluidm) set_error(s, ERR_INVARIANT);
@@ -471,6 +473,7 @@ __global__ void __launch_bounds__(256) k_solid_links(Dev s) {
                     const float ubz = P.u.z + (P.w.x * dy - P.w.y * dx);
                     const float cu = cx(q) * ubx + cy(q) * uby + cz(q) * ubz;
                     const float val = fo[q] + 6.f * wq(q) * cu;
+                    if ((liqm >> q) & 1u) injected += 6.f * wq(q) * cu;
                     const long long dst = PAR == 0 ? (long long)q * n + xn : (long long)opp(q) * n + cell;
                     Store<S>::st(f + dst, val);
                     const float sum = fo[q] + val, dif = fo[q] - val;
@@ -485,6 +488,18 @@ __global__ void __launch_bounds__(256) k_solid_links(Dev s) {
             }
         }
         flush_mem(s, key, F, T);
+    }
+    // R-12a: the net injection leaves the pool (one FP64 atomic per block)
+    if (s.link_corr) {
+        __shared__ float red[8];
+        for (int off = 16; off > 0; off >>= 1) injected += __shfl_xor_sync(0xffffffffu, injected, off);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = injected;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t = 0.f;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+            if (t != 0.f) atomicAdd(s.pool, -(double)t);
+        }
     }
 }
 

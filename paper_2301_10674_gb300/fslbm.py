@@ -81,7 +81,7 @@ class FslbmParams(ctypes.Structure):
         ("poisson", ctypes.c_double),
         ("collision_time", ctypes.c_double),
         ("dem_substeps", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("link_mass_correction", ctypes.c_int32),
         ("capacity_particles", ctypes.c_int64),
         ("capacity_interface", ctypes.c_int64),
     ]

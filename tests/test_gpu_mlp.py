@@ -241,17 +241,17 @@ def test_missing_weights_are_a_state_error():
 # ---------------------------------------------------------------- the gain
 @pytest.fixture(scope="module")
 def trained():
-    """A network trained on the GPU by the library's own kernels: 2^18
-    voxelised surfaces, 4000 Adam steps of 4096 with cube-symmetry
-    augmentation."""
+    """A network trained on the GPU by the library's own kernels: 2^20
+    voxelised surfaces, 20000 Adam steps of 4096 with cube-symmetry
+    augmentation, step size decaying geometrically from 2e-3 to 1e-5."""
     import torch
-    params = W.surface_stencils(1 << 18, seed=4)
+    params = W.surface_stencils(1 << 20, seed=4)
     fill, tgt = _gpu_stencils(params)
-    theta = _dev(OM.init(11), torch.float32)
-    steps = 4000
+    theta = _dev(W.mlp_initial_weights(11))
+    steps = 20000
     curve = _zeros(steps, torch.float32)
-    _ok(F.fslbm_mlp_train(theta, fill, tgt, len(params), steps, 4096, 1e-3, LAM, MU, 17, True, curve),
-        "fslbm_mlp_train")
+    _ok(F.fslbm_mlp_train(theta, fill, tgt, len(params), steps, 4096, 2e-3, LAM, MU, 17, True, curve,
+                          lr_end=1e-5), "fslbm_mlp_train")
     c = curve.cpu().numpy()
     assert np.isfinite(c).all() and c[-100:].mean() < 0.2 * c[:10].mean()
     return theta.cpu().numpy().astype(np.float64), c
