@@ -187,6 +187,7 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     d.eps_normal = (float)p->eps_normal;
     d.recon_normal = p->reconstruct_normal;
     d.link_corr = p->link_mass_correction;
+    d.idx32 = 27LL * n < (1LL << 32) ? 1 : 0;
     d.storage = p->storage;
     d.rho_p = p->rho_p;
     d.restitution = p->restitution;

@@ -60,6 +60,7 @@ struct Dev {
     int recon_normal;
     int storage;
     int link_corr;     // net moving-bounce-back injection into liquid cells taken from the pool
+    int idx32;         // 27 n < 2^32: PDF element indices fit 32 bits
     // element offsets of an odd step for interior cells: the pull of
     // direction q reads f[cell + pull_off[q]], the push writes
     // f[cell + push_off[q]] (constant per launch, held in the parameter bank)
@@ -135,9 +136,15 @@ struct Dev {
 
 // ---------------------------------------------------------------- storage
 template <typename S> struct Store;
+// ld/st convert to and from the deviation f - w; ld_raw/st_raw move the
+// stored value times `scale` (exact power of two), for kernels that fold the
+// scale into the collision
 template <> struct Store<float> {
+    static constexpr float scale = 1.f;
     __device__ static __forceinline__ float ld(const float* p) { return *p; }
     __device__ static __forceinline__ void st(float* p, float v) { *p = v; }
+    __device__ static __forceinline__ float ld_raw(const float* p) { return *p; }
+    __device__ static __forceinline__ void st_raw(float* p, float v) { *p = v; }
 };
 // FP16 holds (f - w) 2^12: the scale is exact, so rounding is FP16's own
 // (11 significant bits), but the normal range starts at 1.5e-8 instead of
@@ -145,12 +152,18 @@ template <> struct Store<float> {
 // largest deviation held is 16.
 constexpr float FP16_SCALE = 4096.f, FP16_UNSCALE = 1.f / 4096.f;
 template <> struct Store<__half> {
+    static constexpr float scale = FP16_SCALE;
     __device__ static __forceinline__ float ld(const __half* p) { return __half2float(*p) * FP16_UNSCALE; }
     __device__ static __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v * FP16_SCALE); }
+    __device__ static __forceinline__ float ld_raw(const __half* p) { return __half2float(*p); }
+    __device__ static __forceinline__ void st_raw(__half* p, float v) { *p = __float2half_rn(v); }
 };
 template <> struct Store<__nv_bfloat16> {
+    static constexpr float scale = 1.f;
     __device__ static __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
     __device__ static __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+    __device__ static __forceinline__ float ld_raw(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+    __device__ static __forceinline__ void st_raw(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
 __device__ __forceinline__ float ld_any(const Dev& s, const void* base, long long i) {
@@ -202,26 +215,32 @@ __device__ __forceinline__ long long fstar_slot(const Dev& s, int q, int x, int 
 }
 
 // ---------------------------------------------------------------- collision
-// Central moments per axis on deviations from the rest state. A column of
-// three values (c = -1, 0, +1) whose rest part is R (1/6, 2/3, 1/6) maps to
-// moments (k0, k1, k2) about u whose rest part is (R, 0, R/3); only the
-// deviations are carried, so FP32 resolves them to their own precision.
-__device__ __forceinline__ void fwd_axis(float& a, float& b, float& c, float u, float R) {
-    float k0 = a + b + c;
-    float d = c - a;
-    float sm = c + a;
-    float K = R + k0;
-    a = k0;
-    b = d - u * K;
-    c = sm - 2.f * u * d + u * u * K;
+// Per-axis (chimera) transforms on deviations from the rest state: a column
+// of three values (c = -1, 0, +1) with rest part (1/6, 2/3, 1/6) R has
+// moments (k0, k1, k2) about u with rest part (R, 0, R/3); only deviations
+// are carried, so FP32 resolves them to their own precision.
+// Backward per-axis transform of one line: (k0, k1, k2) are the zeroth,
+// first and second moments about u of the deviations, R the rest value of
+// the zeroth moment (K = R + k0 the full one). With the per-axis
+// coefficients A = (u^2 - u)/2, B = u - 1/2, C = (u^2 + u)/2, D = u + 1/2:
+// f_-1 = A K + B k1 + k2/2, f_+1 = C K + D k1 + k2/2, and, since the three
+// values sum to the zeroth moment of the deviations, f_0 = k0 - f_-1 - f_+1.
+struct AxisCoef {
+    float A, B, C, D;
+};
+__device__ __forceinline__ AxisCoef axis_coef(float u) {
+    const float uu = u * u;
+    return {0.5f * (uu - u), u - 0.5f, 0.5f * (uu + u), u + 0.5f};
 }
-__device__ __forceinline__ void bwd_axis(float& a, float& b, float& c, float u, float R) {
-    float k0 = a, k1 = b, k2 = c;
-    float K = R + k0;
-    float uu = u * u;
-    b = k0 - uu * K - 2.f * u * k1 - k2;
-    a = 0.5f * ((uu - u) * K + (2.f * u - 1.f) * k1 + k2);
-    c = 0.5f * ((uu + u) * K + (2.f * u + 1.f) * k1 + k2);
+__device__ __forceinline__ void bwd_axis(float& a, float& b, float& c, const AxisCoef& w, float R) {
+    const float k0 = a, k1 = b, k2 = c;
+    const float K = R + k0;
+    const float h = 0.5f * k2;
+    const float lo = fmaf(w.A, K, fmaf(w.B, k1, h));
+    const float hi = fmaf(w.C, K, fmaf(w.D, k1, h));
+    a = lo;
+    c = hi;
+    b = k0 - lo - hi;
 }
 
 __device__ __forceinline__ float w1(int i) { return i == 1 ? 2.f / 3.f : 1.f / 6.f; }
@@ -235,25 +254,55 @@ __device__ __forceinline__ float mrest(int i) { return i == 0 ? 1.f : (i == 1 ? 
 // rho and u (the collision velocity).
 //
 // Only rho, the momentum and the six second-order central moments survive
-// the collision, so they are formed directly from raw sums of the
-// deviations (kappa_ab = Pi_ab - u_a j_b - u_b j_a + rho u_a u_b, diagonal
-// taken relative to its rest value 1/3); the post-collision central moments
-// go back through the per-axis (chimera) transform.
-__device__ __forceinline__ void collide(float (&f)[27], float omega, float gx, float gy, float gz,
-                                        float& rho_out, float& ux_out, float& uy_out, float& uz_out) {
-    float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-    float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
+// the collision. Their raw sums (of the deviations) come from the per-axis
+// (chimera) forward transform pruned to orders <= 2; the central moments
+// follow as kappa_ab = Pi_ab - u_a j_b - u_b j_a + rho u_a u_b (diagonal
+// relative to its rest value 1/3). The post-collision central moments go
+// back through the per-axis backward transform.
+//
+// f may hold the deviations times an exact power of two `scale` (the FP16
+// storage scale): the forward sums are unscaled once, and the backward
+// transform, which is linear in the moments and the rest values, produces
+// scaled values again.
+__device__ __forceinline__ void collide_scaled(float (&f)[27], float scale, float omega, float gx, float gy,
+                                               float gz, float& rho_out, float& ux_out, float& uy_out,
+                                               float& uz_out) {
+    // x: per (b, c) line the sum, first and second raw moments
+    float X0[9], X1[9], X2[9];
 #pragma unroll
-    for (int q = 0; q < 27; ++q) {
-        const float v = f[q];
-        drho += v;
-        if (cx(q)) { jx += cx(q) * v; pxx += v; }
-        if (cy(q)) { jy += cy(q) * v; pyy += v; }
-        if (cz(q)) { jz += cz(q) * v; pzz += v; }
-        if (cx(q) && cy(q)) pxy += cx(q) * cy(q) * v;
-        if (cx(q) && cz(q)) pxz += cx(q) * cz(q) * v;
-        if (cy(q) && cz(q)) pyz += cy(q) * cz(q) * v;
+    for (int l = 0; l < 9; ++l) {
+        const float a = f[3 * l], b = f[3 * l + 1], c = f[3 * l + 2];
+        const float t = a + c;
+        X0[l] = t + b;
+        X1[l] = c - a;
+        X2[l] = t;
     }
+    // y (line index l = b + 3c): only the combinations of total order <= 2
+    float Y00[3], Y01[3], Y02[3], Y10[3], Y11[3], Y20[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float t0 = X0[3 * c] + X0[3 * c + 2];
+        Y00[c] = t0 + X0[3 * c + 1];
+        Y01[c] = X0[3 * c + 2] - X0[3 * c];
+        Y02[c] = t0;
+        Y10[c] = X1[3 * c] + X1[3 * c + 1] + X1[3 * c + 2];
+        Y11[c] = X1[3 * c + 2] - X1[3 * c];
+        Y20[c] = X2[3 * c] + X2[3 * c + 1] + X2[3 * c + 2];
+    }
+    // z
+    const float inv_scale = 1.f / scale;
+    const float tz = Y00[0] + Y00[2];
+    const float drho = (tz + Y00[1]) * inv_scale;
+    const float jz = (Y00[2] - Y00[0]) * inv_scale;
+    const float pzz = tz * inv_scale;
+    const float jy = (Y01[0] + Y01[1] + Y01[2]) * inv_scale;
+    const float pyz = (Y01[2] - Y01[0]) * inv_scale;
+    const float jx = (Y10[0] + Y10[1] + Y10[2]) * inv_scale;
+    const float pxz = (Y10[2] - Y10[0]) * inv_scale;
+    const float pyy = (Y02[0] + Y02[1] + Y02[2]) * inv_scale;
+    const float pxy = (Y11[0] + Y11[1] + Y11[2]) * inv_scale;
+    const float pxx = (Y20[0] + Y20[1] + Y20[2]) * inv_scale;
+
     const float rho = 1.f + drho;
     const float inv = 1.f / rho;
     const float Fx = rho * gx, Fy = rho * gy, Fz = rho * gz;
@@ -282,45 +331,53 @@ __device__ __forceinline__ void collide(float (&f)[27], float omega, float gx, f
     const float szz = (k002 - drho * (1.f / 3.f)) * inv;
     const float Sxy = k110 * inv, Sxz = k101 * inv, Syz = k011 * inv;
     const float third = 1.f / 3.f;
-    f[0] = drho;
-    f[1] = 0.5f * Fx;
-    f[3] = 0.5f * Fy;
-    f[9] = 0.5f * Fz;
-    f[2] = k200; f[6] = k020; f[18] = k002;
-    f[4] = k110; f[10] = k101; f[12] = k011;
+    const float rs = rho * scale;
+    f[0] = drho * scale;
+    f[1] = 0.5f * Fx * scale;
+    f[3] = 0.5f * Fy * scale;
+    f[9] = 0.5f * Fz * scale;
+    f[2] = k200 * scale; f[6] = k020 * scale; f[18] = k002 * scale;
+    f[4] = k110 * scale; f[10] = k101 * scale; f[12] = k011 * scale;
     f[5] = f[11] = f[7] = f[15] = f[19] = f[21] = f[13] = 0.f;
-    f[8] = drho * (1.f / 9.f) + rho * ((sxx + syy) * third + sxx * syy + 2.f * Sxy * Sxy);
-    f[20] = drho * (1.f / 9.f) + rho * ((sxx + szz) * third + sxx * szz + 2.f * Sxz * Sxz);
-    f[24] = drho * (1.f / 9.f) + rho * ((syy + szz) * third + syy * szz + 2.f * Syz * Syz);
-    f[14] = rho * ((third + sxx) * Syz + 2.f * Sxy * Sxz);
-    f[16] = rho * ((third + syy) * Sxz + 2.f * Sxy * Syz);
-    f[22] = rho * ((third + szz) * Sxy + 2.f * Sxz * Syz);
+    f[8] = drho * (scale / 9.f) + rs * ((sxx + syy) * third + sxx * syy + 2.f * Sxy * Sxy);
+    f[20] = drho * (scale / 9.f) + rs * ((sxx + szz) * third + sxx * szz + 2.f * Sxz * Sxz);
+    f[24] = drho * (scale / 9.f) + rs * ((syy + szz) * third + syy * szz + 2.f * Syz * Syz);
+    f[14] = rs * ((third + sxx) * Syz + 2.f * Sxy * Sxz);
+    f[16] = rs * ((third + syy) * Sxz + 2.f * Sxy * Syz);
+    f[22] = rs * ((third + szz) * Sxy + 2.f * Sxz * Syz);
     f[17] = f[23] = f[25] = 0.f;
-    f[26] = drho * (1.f / 27.f)
-            + rho * ((sxx + syy + szz) * (1.f / 9.f) + (sxx * syy + sxx * szz + syy * szz) * third
-                     + sxx * syy * szz
-                     + 2.f * ((third + sxx) * Syz * Syz + (third + syy) * Sxz * Sxz + (third + szz) * Sxy * Sxy)
-                     + 8.f * Sxy * Sxz * Syz);
-    // backward: x, then y, then z
+    f[26] = drho * (scale / 27.f)
+            + rs * ((sxx + syy + szz) * (1.f / 9.f) + (sxx * syy + sxx * szz + syy * szz) * third
+                    + sxx * syy * szz
+                    + 2.f * ((third + sxx) * Syz * Syz + (third + syy) * Sxz * Sxz + (third + szz) * Sxy * Sxy)
+                    + 8.f * Sxy * Sxz * Syz);
+    // backward: x, then y, then z (rest values scaled with the moments)
+    const AxisCoef wx = axis_coef(ux), wy = axis_coef(uy), wz = axis_coef(uz);
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int b = 0; b < 3; ++b)
-            bwd_axis(f[3 * b + 9 * c], f[1 + 3 * b + 9 * c], f[2 + 3 * b + 9 * c], ux, mrest(b) * mrest(c));
+            bwd_axis(f[3 * b + 9 * c], f[1 + 3 * b + 9 * c], f[2 + 3 * b + 9 * c], wx,
+                     scale * mrest(b) * mrest(c));
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int a = 0; a < 3; ++a)
-            bwd_axis(f[a + 9 * c], f[a + 3 + 9 * c], f[a + 6 + 9 * c], uy, w1(a) * mrest(c));
+            bwd_axis(f[a + 9 * c], f[a + 3 + 9 * c], f[a + 6 + 9 * c], wy, scale * w1(a) * mrest(c));
 #pragma unroll
     for (int b = 0; b < 3; ++b)
 #pragma unroll
         for (int a = 0; a < 3; ++a)
-            bwd_axis(f[a + 3 * b], f[a + 3 * b + 9], f[a + 3 * b + 18], uz, w1(a) * w1(b));
+            bwd_axis(f[a + 3 * b], f[a + 3 * b + 9], f[a + 3 * b + 18], wz, scale * w1(a) * w1(b));
     rho_out = rho;
     ux_out = ux;
     uy_out = uy;
     uz_out = uz;
+}
+
+__device__ __forceinline__ void collide(float (&f)[27], float omega, float gx, float gy, float gz,
+                                        float& rho_out, float& ux_out, float& uy_out, float& uz_out) {
+    collide_scaled(f, 1.f, omega, gx, gy, gz, rho_out, ux_out, uy_out, uz_out);
 }
 
 // second-order equilibrium minus the weight: w_q [(rho - 1) + rho (3 cu +

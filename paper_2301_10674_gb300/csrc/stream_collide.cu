@@ -183,7 +183,10 @@ __device__ __forceinline__ PData particle_data(const Dev& s, int p) {
 // opp(q), rounded down to a 16-byte boundary and widened by one 16-byte
 // word, so every copy starts and ends on 16-byte boundaries. The cells at
 // x = 0 and x = nx-1 (periodic wrap or wall) read global memory directly.
-constexpr int STAGES = 3;
+#ifndef FSLBM_STAGED_DEPTH
+#define FSLBM_STAGED_DEPTH 3
+#endif
+constexpr int STAGES = FSLBM_STAGED_DEPTH;   // tiles in flight per CTA
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
     return static_cast<unsigned>(__cvta_generic_to_shared(p));
@@ -265,6 +268,7 @@ __global__ void __launch_bounds__(TILE) k_liquid_staged(Dev s) {
     __shared__ __align__(8) uint64_t full[STAGES];
     __shared__ __align__(8) uint64_t empty[STAGES];
     __shared__ int stage_tile[STAGES];
+    __shared__ int stage_edge[STAGES];   // bit 0: tile starts at x = 0; bit 1: ends at x = nx - 1
     __shared__ int abort_flag;
     const int ntiles = *s.tile_count;
     const int mine = ntiles > (int)blockIdx.x ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
@@ -285,6 +289,8 @@ __global__ void __launch_bounds__(TILE) k_liquid_staged(Dev s) {
         for (int k = 0; k < STAGES && k < mine; ++k) {
             const int t = s.tiles[(int)blockIdx.x + k * (int)gridDim.x];
             stage_tile[k] = t;
+            const int x0 = (int)(((long long)t * TILE) % s.nx);
+            stage_edge[k] = (x0 == 0 ? 1 : 0) | (x0 + TILE == s.nx ? 2 : 0);
             staged_issue<S, PAR>(s, bufs + k * (L::STAGE_BYTES / (int)sizeof(S)), &full[k], t);
         }
     S* f = static_cast<S*>(s.f);
@@ -299,30 +305,47 @@ __global__ void __launch_bounds__(TILE) k_liquid_staged(Dev s) {
         const unsigned char* fl = reinterpret_cast<const unsigned char*>(buf) + L::PDF_BYTES;
         const int tile = stage_tile[st];
         const int cell = tile * TILE + tid;
-        const int x = cell % s.nx;
+        const int edge = stage_edge[st];
         // the cells at x = 0 and x = nx-1 belong to the row kernel
-        if (x != 0 && x != s.nx - 1 && (fl[tid] & TYPE_MASK) == T_LIQ) {
+        const bool x_edge = (tid == 0 && (edge & 1)) || (tid == TILE - 1 && (edge & 2));
+        if (!x_edge && (fl[tid] & TYPE_MASK) == T_LIQ) {
+            // stored values (times the storage scale) in and out; the
+            // collision folds the scale into its moments
             float v[27];
             if (PAR == 0) {
 #pragma unroll
-                for (int q = 0; q < 27; ++q) v[q] = Store<S>::ld(buf + q * L::ROW + tid);
+                for (int q = 0; q < 27; ++q) v[q] = Store<S>::ld_raw(buf + q * L::ROW + tid);
             } else {
 #pragma unroll
                 for (int q = 0; q < 27; ++q) {
                     // the slice of q starts rem elements before the first source
                     const int rem = (cx(q) == 1) ? L::PAD - 1 : (cx(q) == -1 ? 1 : 0);
-                    v[q] = Store<S>::ld(buf + q * L::ROW + tid + rem);
+                    v[q] = Store<S>::ld_raw(buf + q * L::ROW + tid + rem);
                 }
             }
             float rho, ux, uy, uz;
-            collide(v, s.omega, s.gx, s.gy, s.gz, rho, ux, uy, uz);
-            if (PAR == 0) {
+            collide_scaled(v, Store<S>::scale, s.omega, s.gx, s.gy, s.gz, rho, ux, uy, uz);
+            if (s.idx32) {
+                // element indices in 32 bits: one wide multiply-add per address
+                const unsigned un = (unsigned)n;
+                if (PAR == 0) {
 #pragma unroll
-                for (int q = 0; q < 27; ++q) Store<S>::st(f + (long long)opp(q) * n + cell, v[q]);
+                    for (int q = 0; q < 27; ++q) Store<S>::st_raw(f + ((unsigned)opp(q) * un + (unsigned)cell), v[q]);
+                } else {
+                    const int nx = s.nx;
+#pragma unroll
+                    for (int q = 0; q < 27; ++q) {
+                        const int d = cx(q) + nx * cy(q) + sxy * cz(q);
+                        Store<S>::st_raw(f + ((unsigned)q * un + (unsigned)(cell + d)), v[q]);
+                    }
+                }
+            } else if (PAR == 0) {
+#pragma unroll
+                for (int q = 0; q < 27; ++q) Store<S>::st_raw(f + (long long)opp(q) * n + cell, v[q]);
             } else {
                 S* fc = f + cell;
 #pragma unroll
-                for (int q = 0; q < 27; ++q) Store<S>::st(fc + s.push_off[q], v[q]);
+                for (int q = 0; q < 27; ++q) Store<S>::st_raw(fc + s.push_off[q], v[q]);
             }
         }
         // release the stage, then refill it with the tile STAGES ahead
@@ -334,6 +357,8 @@ __global__ void __launch_bounds__(TILE) k_liquid_staged(Dev s) {
             } else {
                 const int t = s.tiles[(int)blockIdx.x + (i + STAGES) * (int)gridDim.x];
                 stage_tile[st] = t;
+                const int x0 = (int)(((long long)t * TILE) % s.nx);
+                stage_edge[st] = (x0 == 0 ? 1 : 0) | (x0 + TILE == s.nx ? 2 : 0);
                 staged_issue<S, PAR>(s, bufs + st * (L::STAGE_BYTES / (int)sizeof(S)), &full[st], t);
             }
         }
