@@ -401,8 +401,8 @@ __device__ __forceinline__ uint8_t flag_or(uint8_t* flags, long long i, uint8_t 
 
 // Block-aggregated append to a device list: one atomic per block. Every
 // thread of the block must call it (it synchronises the block); blockDim.x
-// must be a multiple of 32 and at most 1024.
-__device__ __forceinline__ void block_append(const Dev& s, bool pred, int v, int* list, int* count, int cap) {
+// must be a multiple of 32 and at most 1024. Returns the slot written, or -1.
+__device__ __forceinline__ int block_append(const Dev& s, bool pred, int v, int* list, int* count, int cap) {
     __shared__ int warp_n[32];
     __shared__ int block_base;
     const unsigned full = 0xffffffffu;
@@ -420,12 +420,36 @@ __device__ __forceinline__ void block_append(const Dev& s, bool pred, int v, int
         block_base = tot ? atomicAdd(count, tot) : 0;
     }
     __syncthreads();
+    int slot = -1;
     if (pred) {
         const int k = block_base + warp_n[wid] + __popc(m & ((1u << lane) - 1u));
+        if (k < cap) {
+            list[k] = v;
+            slot = k;
+        } else {
+            set_error(s, ERR_CAPACITY);
+        }
+    }
+    __syncthreads();
+    return slot;
+}
+
+// Warp-aggregated append: one atomic per warp. Every lane of the warp must
+// call it.
+__device__ __forceinline__ void warp_append(const Dev& s, bool pred, int v, int* list, int* count, int cap) {
+    const unsigned full = 0xffffffffu;
+    const unsigned m = __ballot_sync(full, pred);
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(count, __popc(m));
+    base = __shfl_sync(full, base, leader);
+    if (pred) {
+        const int k = base + __popc(m & ((1u << lane) - 1u));
         if (k < cap) list[k] = v;
         else set_error(s, ERR_CAPACITY);
     }
-    __syncthreads();
 }
 
 // post-collision PDFs of a cell read from the AA layout (outside the

@@ -124,47 +124,99 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-__global__ void k_reduce_cells(Dev s, int last_parity, double* out) {
-    __shared__ double sh[6][8];
-    double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < s.n;
-         c += (long long)gridDim.x * blockDim.x) {
-        const uint8_t fl = s.flags[c];
-        if (!fluid(fl)) continue;
-        const int t = fl & TYPE_MASK;
-        float f[27];
-        load_fstar(s, c, last_parity, f);
-        // per-cell sums of the deviations in FP32, accumulation in FP64
-        float d = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-        for (int q = 0; q < 27; ++q) {
-            d += f[q];
-            jx += cx(q) * f[q];
-            jy += cy(q) * f[q];
-            jz += cz(q) * f[q];
-        }
-        if (!isfinite(d) || !isfinite(jx) || !isfinite(jy) || !isfinite(jz)) set_error(s, ERR_NAN);
-        const double rho = 1.0 + (double)d;
-        const double mx = (double)jx - 0.5 * rho * s.gxd;   // rho u
-        const double phi = t == T_LIQ ? 1.0 : (double)s.phi[c];
-        acc[0] += t == T_LIQ ? rho : (double)s.mass[c];
-        acc[1] += mx;
-        acc[2] += (double)jy - 0.5 * rho * s.gyd;
-        acc[3] += (double)jz - 0.5 * rho * s.gzd;
-        acc[4] += phi * mx;
-        acc[5] += phi * rho;
-        if (t == T_IFC && !isfinite(s.mass[c])) set_error(s, ERR_NAN);
+// compensated FP32 sum (Kahan): per-thread partial sums keep about twice
+// FP32's precision before they enter the FP64 block reduction
+struct KSum {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
     }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// Fluid-cell sums: liquid mass (liquid rho + interface m), momentum, and the
+// phi-weighted sums of the bulk velocity. Threads run along x, blocks over
+// rows (grid-stride over rows). Each cell's 27 post-collision PDFs come from
+// the slots the last step wrote: (opp q, x) after an even step, (q, x + c_q)
+// after an odd one (constant offsets inside the lattice, the general lookup
+// at the faces). The liquid density enters as a count plus the sum of
+// deviations, so no rounding of 1 + d is accumulated.
+template <typename S, int LP>
+__global__ void __launch_bounds__(256) k_reduce_cells(Dev s, double* out) {
+    __shared__ double sh[7][8];
+    KSum acc[6];
+    long long nfluid = 0;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const S* f = static_cast<const S*>(s.f);
+    const long long n = s.n;
+    const int nrows = s.ny * s.nz, sxy = s.nx * s.ny;
+    const float gx = s.gx, gy = s.gy, gz = s.gz;
+    if (x < s.nx) {
+        for (int row = blockIdx.y; row < nrows; row += gridDim.y) {
+            const int cell = x + s.nx * row;
+            const uint8_t fl = s.flags[cell];
+            if (!fluid(fl)) continue;
+            const int t = fl & TYPE_MASK;
+            const int y = row % s.ny, z = row / s.ny;
+            float fv[27];
+            if (LP == 0) {
+#pragma unroll
+                for (int q = 0; q < 27; ++q) fv[q] = Store<S>::ld(f + (long long)opp(q) * n + cell);
+            } else if (x > 0 && x < s.nx - 1 && y > 0 && y < s.ny - 1 && z > 0 && z < s.nz - 1) {
+#pragma unroll
+                for (int q = 0; q < 27; ++q)
+                    fv[q] = Store<S>::ld(f + (long long)q * n + (cell + cx(q) + s.nx * cy(q) + sxy * cz(q)));
+            } else {
+#pragma unroll
+                for (int q = 0; q < 27; ++q) fv[q] = Store<S>::ld(f + fstar_slot(s, q, x, y, z, cell, 1));
+            }
+            float d = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+            for (int q = 0; q < 27; ++q) {
+                d += fv[q];
+                jx += cx(q) * fv[q];
+                jy += cy(q) * fv[q];
+                jz += cz(q) * fv[q];
+            }
+            if (!isfinite(d) || !isfinite(jx) || !isfinite(jy) || !isfinite(jz)) set_error(s, ERR_NAN);
+            const float rho = 1.f + d;
+            const float mx = jx - 0.5f * rho * gx;   // rho u
+            // sums over fluid cells, the 1 of every cell counted apart:
+            // mass - 1 (liquid d, interface m - 1), momentum, phi rho - 1,
+            // phi rho u_x
+            ++nfluid;
+            acc[1].add(mx);
+            acc[2].add(jy - 0.5f * rho * gy);
+            acc[3].add(jz - 0.5f * rho * gz);
+            if (t == T_LIQ) {
+                acc[0].add(d);
+                acc[4].add(d);
+                acc[5].add(mx);
+            } else {
+                const float m = s.mass[cell], phi = s.phi[cell];
+                if (!isfinite(m)) set_error(s, ERR_NAN);
+                acc[0].add(m - 1.f);
+                acc[4].add(phi * rho - 1.f);
+                acc[5].add(phi * mx);
+            }
+        }
+    }
+    // out[0..5]: mass, momentum x, y, z, sum phi rho u_x, sum phi rho
+    double v[7] = {acc[0].value(), acc[1].value(), acc[2].value(), acc[3].value(), acc[5].value(),
+                   acc[4].value(), (double)nfluid};
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int k = 0; k < 6; ++k) {
-        double v = warp_sum(acc[k]);
-        if (lane == 0) sh[k][wid] = v;
+    for (int k = 0; k < 7; ++k) {
+        const double w = warp_sum(v[k]);
+        if (lane == 0) sh[k][wid] = w;
     }
     __syncthreads();
-    if (threadIdx.x < 6) {
-        double v = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[threadIdx.x][w];
-        atomicAdd(&out[threadIdx.x], v);
+    if (threadIdx.x < 7) {
+        double w = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) w += sh[threadIdx.x][i];
+        atomicAdd(&out[threadIdx.x == 6 ? 7 : threadIdx.x], w);
     }
 }
 
@@ -188,8 +240,12 @@ __global__ void k_reduce_particles(Dev s, double* out) {
 }
 
 __global__ void k_reduce_final(Dev s, double* out) {
-    // out[0..5] hold: mass, mom x, y, z, sum phi rho u_x, sum phi rho
+    // out[0..5] hold: mass and sum phi rho without the fluid-cell count
+    // (out[7]), mom x, y, z, sum phi rho u_x; out[6] the bedload sum
     const double qb = out[6];
+    const double count = out[7];
+    out[0] += count;
+    out[5] += count;
     double num = out[4], den = out[5];
     out[0] += *s.pool;
     out[4] = den > 0 ? num / den : 0.0;
@@ -201,7 +257,22 @@ __global__ void k_reduce_final(Dev s, double* out) {
 
 void launch_reduce(const Dev& s, int last_parity, double* out, cudaStream_t st) {
     cudaMemsetAsync(out, 0, 8 * sizeof(double), st);
-    k_reduce_cells<<<152 * 8, 256, 0, st>>>(s, last_parity, out);
+    const unsigned bx = (unsigned)((s.nx + 255) / 256);
+    const int rows = s.ny * s.nz;
+    // about 32 blocks of 256 threads per SM, each thread a column of rows
+    const int want = (int)(152 * 32 / bx) > 0 ? (int)(152 * 32 / bx) : 1;
+    const unsigned by = (unsigned)(rows < want ? rows : want);
+    const dim3 grid(bx, by);
+    if (s.storage == FSLBM_STORE_FP32) {
+        if (last_parity == 0) k_reduce_cells<float, 0><<<grid, 256, 0, st>>>(s, out);
+        else k_reduce_cells<float, 1><<<grid, 256, 0, st>>>(s, out);
+    } else if (s.storage == FSLBM_STORE_FP16) {
+        if (last_parity == 0) k_reduce_cells<__half, 0><<<grid, 256, 0, st>>>(s, out);
+        else k_reduce_cells<__half, 1><<<grid, 256, 0, st>>>(s, out);
+    } else {
+        if (last_parity == 0) k_reduce_cells<__nv_bfloat16, 0><<<grid, 256, 0, st>>>(s, out);
+        else k_reduce_cells<__nv_bfloat16, 1><<<grid, 256, 0, st>>>(s, out);
+    }
     k_reduce_particles<<<1, 1024, 0, st>>>(s, out);
     k_reduce_final<<<1, 1, 0, st>>>(s, out);
 }

@@ -555,8 +555,12 @@ __device__ __forceinline__ void bbox_axis(double a, double b, double r, int L, i
     }
 }
 
-// cells of the shell (or of the old and new boxes) of every active particle
-// join the dirty list, each once
+// Cells of the shell (or of the old and new boxes) of every active particle
+// join the dirty list, each once. A block per particle, a thread per (y, z)
+// row of its box: the row meets the shell | |x_c - X| - r | <= band in at
+// most two x-intervals, found from the row's distance to the centre; the
+// radii are widened by 1e-3 cells so that rounding can only add cells (a
+// cell re-mapped without need keeps its owner).
 __global__ void k_dirty(Dev s) {
     if ((int)blockIdx.x >= *s.act_count) return;
     const int p = s.act[blockIdx.x];
@@ -570,28 +574,53 @@ __global__ void k_dirty(Dev s) {
     const int4 xi = s.Xi[p];
     const float4 xf = s.Xfr[p];
     const float rf = (float)r, band = w + 1e-3f;
+    const float ro = rf + band + 1e-3f, ri = fmaxf(rf - band - 1e-3f, 0.f);
     const int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
-    const int tot = ex * ey * ez;
-    for (int k0 = 0; k0 < tot; k0 += blockDim.x) {
-        const int k = k0 + threadIdx.x;
-        bool first = false;
-        long long cell = 0;
-        if (k < tot) {
-            const int ua = lo[0] + k % ex, ub = lo[1] + (k / ex) % ey, uc = lo[2] + k / (ex * ey);
-            bool mark = whole;
-            if (!whole) {
-                const float a = (float)(ua - xi.x) + 0.5f - xf.x;
-                const float b = (float)(ub - xi.y) + 0.5f - xf.y;
-                const float c = (float)(uc - xi.z) + 0.5f - xf.z;
-                mark = fabsf(sqrtf(a * a + b * b + c * c) - rf) <= band;
-            }
-            if (mark) {
-                const int a = (ua % s.nx + s.nx) % s.nx, b = (ub % s.ny + s.ny) % s.ny, c = (uc % s.nz + s.nz) % s.nz;
-                cell = a + (long long)s.nx * (b + (long long)s.ny * c);
-                first = !(flag_or(s.dirty, cell, 1) & 1);
+    const int rows = ey * ez;
+    // relative x index of a cell = a + xoff, with a its x offset from the centre
+    const float xoff = (float)(xi.x - lo[0]) - 0.5f + xf.x;
+    for (int r0 = 0; r0 < rows; r0 += blockDim.x) {
+        const int rr = r0 + threadIdx.x;
+        int a0 = 0, a1 = -1, b0 = 0, b1 = -1;    // relative x ranges of the row
+        int ub = 0, uc = 0;
+        if (rr < rows) {
+            ub = lo[1] + rr % ey;
+            uc = lo[2] + rr / ey;
+            if (whole) {
+                a1 = ex - 1;
+            } else {
+                const float bb = (float)(ub - xi.y) + 0.5f - xf.y;
+                const float cc = (float)(uc - xi.z) + 0.5f - xf.z;
+                const float rho2 = bb * bb + cc * cc;
+                if (rho2 <= ro * ro) {
+                    const float ho = sqrtf(ro * ro - rho2);
+                    const float hin = rho2 < ri * ri ? sqrtf(ri * ri - rho2) : 0.f;
+                    if (hin == 0.f) {
+                        a0 = (int)ceilf(xoff - ho);
+                        a1 = (int)floorf(xoff + ho);
+                    } else {
+                        a0 = (int)ceilf(xoff - ho);
+                        a1 = (int)floorf(xoff - hin);
+                        b0 = (int)ceilf(xoff + hin);
+                        b1 = (int)floorf(xoff + ho);
+                    }
+                    a0 = max(a0, 0); a1 = min(a1, ex - 1);
+                    b0 = max(b0, 0); b1 = min(b1, ex - 1);
+                }
             }
         }
-        block_append(s, first, (int)cell, s.dl, s.dl_count, s.dl_cap);
+        const int n1 = max(0, a1 - a0 + 1), n2 = max(0, b1 - b0 + 1), nc = n1 + n2;
+        for (int k = 0; __any_sync(0xffffffffu, k < nc); ++k) {
+            bool first = false;
+            int cell = 0;
+            if (k < nc) {
+                const int ua = lo[0] + (k < n1 ? a0 + k : b0 + k - n1);
+                const int a = (ua % s.nx + s.nx) % s.nx, b = (ub % s.ny + s.ny) % s.ny, c = (uc % s.nz + s.nz) % s.nz;
+                cell = a + s.nx * (b + s.ny * c);
+                first = !(flag_or(s.dirty, cell, 1) & 1);
+            }
+            warp_append(s, first, cell, s.dl, s.dl_count, s.dl_cap);
+        }
     }
 }
 
@@ -624,6 +653,7 @@ enum : int { NT_UNCOVERED_LIQ = 0x100 };
 // (interface next to gas, gas without fluid neighbours) with f_eq(mean rho,
 // u_b) and take their mass from the pool (snapshot of the cell types)
 __global__ void k_transitions(Dev s, int last_parity) {
+    double dpool = 0.0;   // this thread's change of the pool (one atomic per block)
     FOR_TL(i) {
         const int c = s.tl[i];
         const int o1 = s.tl_info[2 * i];
@@ -635,9 +665,9 @@ __global__ void k_transitions(Dev s, int last_parity) {
                 load_fstar(s, c, last_parity, f);
                 float d = 0.f;
                 for (int q = 0; q < 27; ++q) d += f[q];
-                atomicAdd(s.pool, (double)(1.f + d));
+                dpool += (double)(1.f + d);
             } else if (t0 == T_IFC) {
-                atomicAdd(s.pool, (double)s.mass[c]);
+                dpool += (double)s.mass[c];
             }
             nt = T_SOL;
         } else {
@@ -689,11 +719,20 @@ __global__ void k_transitions(Dev s, int last_parity) {
                 } else {
                     nt = T_LIQ | NT_UNCOVERED_LIQ;
                     s.mass[c] = rb;
-                    atomicAdd(s.pool, -(double)rb);
+                    dpool -= (double)rb;
                 }
             }
         }
         s.tl_info[2 * i + 1] = nt;
+    }
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) dpool += __shfl_xor_sync(0xffffffffu, dpool, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dpool;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        if (t != 0.0) atomicAdd(s.pool, t);
     }
 }
 
@@ -767,7 +806,7 @@ int launch_particles_step(const Dev& s, int have_prev, int last_parity, cudaStre
     cudaMemsetAsync(s.act_count, 0, sizeof(int), st);
     cudaMemsetAsync(s.dl_count, 0, sizeof(int), st);
     k_active<<<blocks_for(s.np, 128), 128, 0, st>>>(s);
-    k_dirty<<<s.np, 256, 0, st>>>(s);
+    k_dirty<<<s.np, 128, 0, st>>>(s);
     k_remap_list<<<152 * 8, 128, 0, st>>>(s);
     k_map_position<<<blocks_for(s.np, 256), 256, 0, st>>>(s);
     k_transitions<<<152 * 4, 128, 0, st>>>(s, last_parity);

@@ -11,20 +11,16 @@
 // reconstruction also replaces PDFs pulled from fluid neighbours, whose slots
 // are being rewritten.
 //
-// Three kernels share the work: the particle links from the solid side
-// (they place the moving bounce-back values in the pull slots and gather the
-// momentum exchange), one lean pull-collide kernel for every liquid cell,
-// and one for the interface cells of the interface list.
+// The work per step: the particle links from the solid side (they place the
+// moving bounce-back values in the pull slots and gather the momentum
+// exchange); the liquid cells (even steps: interior rows staged tile by tile
+// through shared memory by bulk copies, plus a row kernel for the faces;
+// odd steps: one lean pull-collide kernel); and the interface cells of the
+// interface list.
 #include "fslbm_dev.cuh"
 
 namespace fsl {
 
-// All liquid cells. Every PDF is a plain pull: PDFs from fluid cells, and
-// from solid cells the bounce-back values k_solid_links placed in the pull
-// slots. Only wall faces need handling here, and they follow from the
-// coordinates: an even step reads its own slots (a wall-bound PDF came back
-// into (q, x) in the previous odd step), an odd step reads (q, x) across a
-// wall face and writes (opp(q), x) toward one.
 // offsets of the x, y, z neighbours (-1, 0, +1) of a cell with the wall
 // faces it touches as bits (x-, x+, y-, y+, z-, z+)
 struct NbrOffsets {
@@ -58,58 +54,74 @@ __host__ __device__ constexpr unsigned wall_bits(int dx, int dy, int dz) {
 // coordinates: an even step reads its own slots (a wall-bound PDF came back
 // into (q, x) in the previous odd step), an odd step reads (q, x) across a
 // wall face and writes (opp(q), x) toward one. Interior cells of an odd step
-// use offsets that are the same for every thread.
+// use offsets that are the same for every thread. Threads run along x,
+// blocks over rows (y, z), so the coordinates need no division per cell.
+// Stored values move raw (times the storage scale); the collision folds the
+// scale into its moments.
 template <typename S, int PAR>
 __global__ void __launch_bounds__(256, 3) k_liquid(Dev s) {
-    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= s.n) return;
-    if ((s.flags[cell] & TYPE_MASK) != T_LIQ) return;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= s.nx) return;
     S* f = static_cast<S*>(s.f);
     const long long n = s.n;
-    float v[27];
-    if (PAR == 0) {
-#pragma unroll
-        for (int q = 0; q < 27; ++q) v[q] = Store<S>::ld(f + (long long)q * n + cell);
-        float rho, ux, uy, uz;
-        collide(v, s.omega, s.gx, s.gy, s.gz, rho, ux, uy, uz);
-#pragma unroll
-        for (int q = 0; q < 27; ++q) Store<S>::st(f + (long long)opp(q) * n + cell, v[q]);
-        return;
-    }
-    int x, y, z;
-    coords(s, cell, x, y, z);
+    const int nrows = s.ny * s.nz;
     const int sxy = s.nx * s.ny;
-    const bool interior = x > 0 && x < s.nx - 1 && y > 0 && y < s.ny - 1 && z > 0 && z < s.nz - 1;
-    if (interior) {
-        S* fc = f + cell;
+    for (int row = blockIdx.y; row < nrows; row += gridDim.y) {
+        const int cell = x + s.nx * row;
+        if ((s.flags[cell] & TYPE_MASK) != T_LIQ) continue;
+        const int y = row % s.ny, z = row / s.ny;
+        const bool interior =
+            PAR == 0 || (x > 0 && x < s.nx - 1 && y > 0 && y < s.ny - 1 && z > 0 && z < s.nz - 1);
+        float v[27];
+        if (interior && s.idx32) {
+            const unsigned un = (unsigned)n;
 #pragma unroll
-        for (int q = 0; q < 27; ++q) v[q] = Store<S>::ld(fc + s.pull_off[q]);
-    } else {
-        const NbrOffsets o = nbr_offsets(s, x, y, z);
+            for (int q = 0; q < 27; ++q) {
+                const unsigned a = PAR == 0 ? (unsigned)q * un + (unsigned)cell
+                                            : (unsigned)opp(q) * un +
+                                                  (unsigned)(cell - (cx(q) + s.nx * cy(q) + sxy * cz(q)));
+                v[q] = Store<S>::ld_raw(f + a);
+            }
+        } else if (interior) {
 #pragma unroll
-        for (int q = 0; q < 27; ++q) {
-            // source x - c_q beyond a wall face?
-            const int src = cell + o.ox[1 - cx(q)] + o.oy[1 - cy(q)] + o.oz[1 - cz(q)];
-            const long long a = (o.wall & wall_bits(-cx(q), -cy(q), -cz(q))) ? (long long)q * n + cell
-                                                                               : (long long)opp(q) * n + src;
-            v[q] = Store<S>::ld(f + a);
+            for (int q = 0; q < 27; ++q)
+                v[q] = Store<S>::ld_raw(PAR == 0 ? f + (long long)q * n + cell : f + cell + s.pull_off[q]);
+        } else {
+            const NbrOffsets o = nbr_offsets(s, x, y, z);
+#pragma unroll
+            for (int q = 0; q < 27; ++q) {
+                // source x - c_q beyond a wall face?
+                const int src = cell + o.ox[1 - cx(q)] + o.oy[1 - cy(q)] + o.oz[1 - cz(q)];
+                const long long a = (o.wall & wall_bits(-cx(q), -cy(q), -cz(q))) ? (long long)q * n + cell
+                                                                                   : (long long)opp(q) * n + src;
+                v[q] = Store<S>::ld_raw(f + a);
+            }
         }
-    }
-    float rho, ux, uy, uz;
-    collide(v, s.omega, s.gx, s.gy, s.gz, rho, ux, uy, uz);
-    if (interior) {
-        S* fc = f + cell;
+        float rho, ux, uy, uz;
+        collide_scaled(v, Store<S>::scale, s.omega, s.gx, s.gy, s.gz, rho, ux, uy, uz);
+        if (interior && s.idx32) {
+            const unsigned un = (unsigned)n;
 #pragma unroll
-        for (int q = 0; q < 27; ++q) Store<S>::st(fc + s.push_off[q], v[q]);
-    } else {
-        const NbrOffsets o = nbr_offsets(s, x, y, z);
+            for (int q = 0; q < 27; ++q) {
+                const unsigned a = PAR == 0 ? (unsigned)opp(q) * un + (unsigned)cell
+                                            : (unsigned)q * un +
+                                                  (unsigned)(cell + cx(q) + s.nx * cy(q) + sxy * cz(q));
+                Store<S>::st_raw(f + a, v[q]);
+            }
+        } else if (interior) {
 #pragma unroll
-        for (int q = 0; q < 27; ++q) {
-            // target x + c_q beyond a wall face?
-            const int dst = cell + o.ox[1 + cx(q)] + o.oy[1 + cy(q)] + o.oz[1 + cz(q)];
-            const long long a = (o.wall & wall_bits(cx(q), cy(q), cz(q))) ? (long long)opp(q) * n + cell
-                                                                           : (long long)q * n + dst;
-            Store<S>::st(f + a, v[q]);
+            for (int q = 0; q < 27; ++q)
+                Store<S>::st_raw(PAR == 0 ? f + (long long)opp(q) * n + cell : f + cell + s.push_off[q], v[q]);
+        } else {
+            const NbrOffsets o = nbr_offsets(s, x, y, z);
+#pragma unroll
+            for (int q = 0; q < 27; ++q) {
+                // target x + c_q beyond a wall face?
+                const int dst = cell + o.ox[1 + cx(q)] + o.oy[1 + cy(q)] + o.oz[1 + cz(q)];
+                const long long a = (o.wall & wall_bits(cx(q), cy(q), cz(q))) ? (long long)opp(q) * n + cell
+                                                                               : (long long)q * n + dst;
+                Store<S>::st_raw(f + a, v[q]);
+            }
         }
     }
 }
@@ -174,15 +186,14 @@ __device__ __forceinline__ PData particle_data(const Dev& s, int p) {
 }
 
 // ---------------------------------------------------------------- staged sweep
-// Liquid cells of interior rows, tile by tile: a persistent CTA of TILE
-// threads streams the 27 direction slices of each x-tile into shared memory
-// with bulk asynchronous copies (cp.async.bulk, completion counted on an
-// mbarrier), several tiles ahead, while its threads collide the tile in
-// hand. Even steps copy the slices [c0, c0+TILE) of every direction; odd
-// steps the shifted slices [c0 - off_q, c0 - off_q + TILE) of direction
-// opp(q), rounded down to a 16-byte boundary and widened by one 16-byte
-// word, so every copy starts and ends on 16-byte boundaries. The cells at
-// x = 0 and x = nx-1 (periodic wrap or wall) read global memory directly.
+// Even steps, liquid cells of interior rows, tile by tile: a persistent CTA
+// of TILE threads streams the 27 direction slices [c0, c0 + TILE) of each
+// x-tile into shared memory with bulk asynchronous copies (cp.async.bulk,
+// completion counted on an mbarrier), several tiles ahead, while its threads
+// collide the tile in hand. Every copy starts and ends on a 16-byte boundary
+// (nx is a multiple of TILE). The cells at x = 0 and x = nx-1 belong to the
+// row kernel. Odd steps run k_liquid: their slices are shifted by one
+// element along x, and staging them measured slower than direct loads.
 #ifndef FSLBM_STAGED_DEPTH
 #define FSLBM_STAGED_DEPTH 3
 #endif
@@ -229,38 +240,25 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
 
 template <typename S>
 struct StagedLayout {
-    static constexpr int PAD = 16 / (int)sizeof(S);          // elements per 16-byte word
-    static constexpr int ROW = TILE + PAD;                    // elements per direction slice
+    static constexpr int ROW = TILE;                            // elements per direction slice
     static constexpr int PDF_BYTES = 27 * ROW * (int)sizeof(S);
-    static constexpr int STAGE_BYTES = PDF_BYTES + TILE;      // + the tile's flag bytes
+    static constexpr int STAGE_BYTES = PDF_BYTES + TILE;        // + the tile's flag bytes
 };
 
-template <typename S, int PAR>
+template <typename S>
 __device__ __forceinline__ void staged_issue(const Dev& s, S* buf, uint64_t* full, int tile) {
     using L = StagedLayout<S>;
     const S* f = static_cast<const S*>(s.f);
     const long long n = s.n;
     const long long c0 = (long long)tile * TILE;
-    const int sxy = s.nx * s.ny;
     unsigned char* fl = reinterpret_cast<unsigned char*>(buf) + L::PDF_BYTES;
-    if (PAR == 0) {
-        mbar_expect_tx(full, 27u * TILE * sizeof(S) + TILE);
-        bulk_load(fl, s.flags + c0, TILE, full);
+    mbar_expect_tx(full, 27u * TILE * sizeof(S) + TILE);
+    bulk_load(fl, s.flags + c0, TILE, full);
 #pragma unroll 1
-        for (int q = 0; q < 27; ++q) bulk_load(buf + q * L::ROW, f + (long long)q * n + c0, TILE * sizeof(S), full);
-    } else {
-        mbar_expect_tx(full, 27u * (TILE + L::PAD) * sizeof(S) + TILE);
-        bulk_load(fl, s.flags + c0, TILE, full);
-#pragma unroll 1
-        for (int q = 0; q < 27; ++q) {
-            const long long a = (long long)opp(q) * n + c0 - (cx(q) + (long long)s.nx * cy(q) + (long long)sxy * cz(q));
-            const long long a0 = a & ~(long long)(L::PAD - 1);
-            bulk_load(buf + q * L::ROW, f + a0, (TILE + L::PAD) * sizeof(S), full);
-        }
-    }
+    for (int q = 0; q < 27; ++q) bulk_load(buf + q * L::ROW, f + (long long)q * n + c0, TILE * sizeof(S), full);
 }
 
-template <typename S, int PAR>
+template <typename S>
 __global__ void __launch_bounds__(TILE) k_liquid_staged(Dev s) {
     using L = StagedLayout<S>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -275,6 +273,14 @@ __global__ void __launch_bounds__(TILE) k_liquid_staged(Dev s) {
     if (mine == 0) return;
     const int tid = threadIdx.x;
     const int nwarps = TILE / 32;
+    constexpr int SE = L::STAGE_BYTES / (int)sizeof(S);   // stage stride in elements
+    auto issue = [&](int k, int i) {
+        const int t = s.tiles[(int)blockIdx.x + i * (int)gridDim.x];
+        stage_tile[k] = t;
+        const int x0 = (int)(((long long)t * TILE) % s.nx);
+        stage_edge[k] = (x0 == 0 ? 1 : 0) | (x0 + TILE == s.nx ? 2 : 0);
+        staged_issue<S>(s, bufs + k * SE, &full[k], t);
+    };
     if (tid == 0) {
         for (int k = 0; k < STAGES; ++k) {
             mbar_init(&full[k], 1);
@@ -286,81 +292,43 @@ __global__ void __launch_bounds__(TILE) k_liquid_staged(Dev s) {
     __syncthreads();
     // prologue: the first STAGES tiles of this CTA
     if (tid == 0)
-        for (int k = 0; k < STAGES && k < mine; ++k) {
-            const int t = s.tiles[(int)blockIdx.x + k * (int)gridDim.x];
-            stage_tile[k] = t;
-            const int x0 = (int)(((long long)t * TILE) % s.nx);
-            stage_edge[k] = (x0 == 0 ? 1 : 0) | (x0 + TILE == s.nx ? 2 : 0);
-            staged_issue<S, PAR>(s, bufs + k * (L::STAGE_BYTES / (int)sizeof(S)), &full[k], t);
-        }
+        for (int k = 0; k < STAGES && k < mine; ++k) issue(k, k);
     S* f = static_cast<S*>(s.f);
     const long long n = s.n;
-    const int sxy = s.nx * s.ny;
     for (int i = 0; i < mine; ++i) {
         const int st = i % STAGES;
         const unsigned ph = (unsigned)(i / STAGES) & 1u;
         if (!mbar_wait(s, &full[st], ph)) abort_flag = 1;
         if (abort_flag) break;
-        const S* buf = bufs + st * (L::STAGE_BYTES / (int)sizeof(S));
+        const S* buf = bufs + st * SE;
         const unsigned char* fl = reinterpret_cast<const unsigned char*>(buf) + L::PDF_BYTES;
-        const int tile = stage_tile[st];
-        const int cell = tile * TILE + tid;
+        const int cell = stage_tile[st] * TILE + tid;
         const int edge = stage_edge[st];
-        // the cells at x = 0 and x = nx-1 belong to the row kernel
         const bool x_edge = (tid == 0 && (edge & 1)) || (tid == TILE - 1 && (edge & 2));
         if (!x_edge && (fl[tid] & TYPE_MASK) == T_LIQ) {
             // stored values (times the storage scale) in and out; the
             // collision folds the scale into its moments
             float v[27];
-            if (PAR == 0) {
 #pragma unroll
-                for (int q = 0; q < 27; ++q) v[q] = Store<S>::ld_raw(buf + q * L::ROW + tid);
-            } else {
-#pragma unroll
-                for (int q = 0; q < 27; ++q) {
-                    // the slice of q starts rem elements before the first source
-                    const int rem = (cx(q) == 1) ? L::PAD - 1 : (cx(q) == -1 ? 1 : 0);
-                    v[q] = Store<S>::ld_raw(buf + q * L::ROW + tid + rem);
-                }
-            }
+            for (int q = 0; q < 27; ++q) v[q] = Store<S>::ld_raw(buf + q * L::ROW + tid);
             float rho, ux, uy, uz;
             collide_scaled(v, Store<S>::scale, s.omega, s.gx, s.gy, s.gz, rho, ux, uy, uz);
             if (s.idx32) {
                 // element indices in 32 bits: one wide multiply-add per address
                 const unsigned un = (unsigned)n;
-                if (PAR == 0) {
 #pragma unroll
-                    for (int q = 0; q < 27; ++q) Store<S>::st_raw(f + ((unsigned)opp(q) * un + (unsigned)cell), v[q]);
-                } else {
-                    const int nx = s.nx;
-#pragma unroll
-                    for (int q = 0; q < 27; ++q) {
-                        const int d = cx(q) + nx * cy(q) + sxy * cz(q);
-                        Store<S>::st_raw(f + ((unsigned)q * un + (unsigned)(cell + d)), v[q]);
-                    }
-                }
-            } else if (PAR == 0) {
+                for (int q = 0; q < 27; ++q) Store<S>::st_raw(f + ((unsigned)opp(q) * un + (unsigned)cell), v[q]);
+            } else {
 #pragma unroll
                 for (int q = 0; q < 27; ++q) Store<S>::st_raw(f + (long long)opp(q) * n + cell, v[q]);
-            } else {
-                S* fc = f + cell;
-#pragma unroll
-                for (int q = 0; q < 27; ++q) Store<S>::st_raw(fc + s.push_off[q], v[q]);
             }
         }
         // release the stage, then refill it with the tile STAGES ahead
         __syncwarp();
         if ((tid & 31) == 0) mbar_arrive(&empty[st]);
         if (tid == 0 && i + STAGES < mine) {
-            if (!mbar_wait(s, &empty[st], ph)) {
-                abort_flag = 1;
-            } else {
-                const int t = s.tiles[(int)blockIdx.x + (i + STAGES) * (int)gridDim.x];
-                stage_tile[st] = t;
-                const int x0 = (int)(((long long)t * TILE) % s.nx);
-                stage_edge[st] = (x0 == 0 ? 1 : 0) | (x0 + TILE == s.nx ? 2 : 0);
-                staged_issue<S, PAR>(s, bufs + st * (L::STAGE_BYTES / (int)sizeof(S)), &full[st], t);
-            }
+            if (!mbar_wait(s, &empty[st], ph)) abort_flag = 1;
+            else issue(st, i + STAGES);
         }
     }
     // copies still in flight complete before the CTA leaves
@@ -650,10 +618,9 @@ static int staged_blocks() {
     static int blocks = 0;
     if (blocks == 0) {
         const int smem = STAGES * StagedLayout<S>::STAGE_BYTES;
-        cudaFuncSetAttribute(k_liquid_staged<S, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaFuncSetAttribute(k_liquid_staged<S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_liquid_staged<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_liquid_staged<S, 1>, TILE, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_liquid_staged<S>, TILE, smem);
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -662,32 +629,28 @@ static int staged_blocks() {
     return blocks;
 }
 
+static bool use_staged(const Dev& s) { return (s.nx % TILE) == 0 && s.ny >= 3 && s.nz >= 3; }
+
 template <typename S>
 static void launch_typed(const Dev& s, int parity, cudaStream_t st) {
-    const int bl = blocks_for(s.n, 256);
     const int lb = 152 * 8;
-    const bool staged = (s.nx % TILE) == 0 && s.ny >= 3 && s.nz >= 3;
-    const long long nrow = 2LL * s.nz + 2LL * (s.ny - 2);
-    const int rb = (int)((nrow * s.nx + 2LL * (s.ny - 2) * (s.nz - 2) + 255) / 256);
-    const size_t smem = (size_t)STAGES * StagedLayout<S>::STAGE_BYTES;
-    const int sb = staged_blocks<S>();
+    // k_liquid: threads along x, blocks over the rows (y, z)
+    const dim3 lgrid((unsigned)((s.nx + 255) / 256), (unsigned)(s.ny * s.nz < 65535 ? s.ny * s.nz : 65535));
     if (parity == 0) {
         if (s.np > 0) k_solid_links<S, 0><<<lb, 256, 0, st>>>(s);
-        if (staged) {
-            k_liquid_staged<S, 0><<<sb, TILE, smem, st>>>(s);
+        if (use_staged(s)) {
+            const long long nrow = 2LL * s.nz + 2LL * (s.ny - 2);
+            const int rb = (int)((nrow * s.nx + 2LL * (s.ny - 2) * (s.nz - 2) + 255) / 256);
+            const size_t smem = (size_t)STAGES * StagedLayout<S>::STAGE_BYTES;
+            k_liquid_staged<S><<<staged_blocks<S>(), TILE, smem, st>>>(s);
             k_liquid_rows<S, 0><<<rb, 256, 0, st>>>(s);
         } else {
-            k_liquid<S, 0><<<bl, 256, 0, st>>>(s);
+            k_liquid<S, 0><<<lgrid, 256, 0, st>>>(s);
         }
         k_interface<S, 0><<<lb, 128, 0, st>>>(s);
     } else {
         if (s.np > 0) k_solid_links<S, 1><<<lb, 256, 0, st>>>(s);
-        if (staged) {
-            k_liquid_staged<S, 1><<<sb, TILE, smem, st>>>(s);
-            k_liquid_rows<S, 1><<<rb, 256, 0, st>>>(s);
-        } else {
-            k_liquid<S, 1><<<bl, 256, 0, st>>>(s);
-        }
+        k_liquid<S, 1><<<lgrid, 256, 0, st>>>(s);
         k_interface<S, 1><<<lb, 128, 0, st>>>(s);
     }
 }
@@ -696,8 +659,7 @@ int launch_stream_collide(const Dev& s, int parity, cudaStream_t st) {
     if (s.storage == FSLBM_STORE_FP32) launch_typed<float>(s, parity, st);
     else if (s.storage == FSLBM_STORE_FP16) launch_typed<__half>(s, parity, st);
     else launch_typed<__nv_bfloat16>(s, parity, st);
-    const bool staged = (s.nx % TILE) == 0 && s.ny >= 3 && s.nz >= 3;
-    return (s.np > 0 ? 1 : 0) + (staged ? 3 : 2);
+    return (s.np > 0 ? 1 : 0) + (parity == 0 && use_staged(s) ? 3 : 2);
 }
 
 }  // namespace fsl

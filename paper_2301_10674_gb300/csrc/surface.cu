@@ -66,45 +66,69 @@ __global__ void k_normals(Dev s, float4* out) {
 
 // Learned normal (R-17), a warp per 16 interface cells of the list. Lane
 // (g, t) loads the stencil columns of its input fragments for the cells of
-// rows g and g + 8; together the four lanes of a group cover all 27 and
-// agree on whether a wall or solid cell lies in the block. The Parker-Youngs
-// normal is both the fallback (wall or solid in the block, raw length
-// outside [1/2, 2]) and the judge (network normal more than 30 degrees
-// away). out[c] = (n, curvature), curvature 0 where the fallback is taken.
+// rows g and g + 8; together the four lanes of a group cover all 27, agree on
+// whether a wall or solid cell lies in the block, and sum the Parker-Youngs
+// gradient from the same values (walls and solids taking the centre value).
+// The Parker-Youngs normal is both the fallback (wall or solid in the block,
+// raw length outside [1/2, 2]) and the judge (network normal more than 30
+// degrees away). out[c] = (n, curvature), curvature 0 where the fallback is
+// taken.
 __global__ void __launch_bounds__(128) k_mlp_normals(Dev s, float4* out) {
     const int count = *s.wl_count;
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const unsigned full = 0xffffffffu;
     unsigned long long evaluated = 0, taken = 0;
     for (int base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 16; base < count; base += nwarps * 16) {
         int cell[2];
         float v[2][8];
         bool bad[2];
+        float gr[2][3];
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             const int li = base + g + 8 * r;
             cell[r] = li < count ? s.wl[li] : -1;
             bad[r] = false;
+            gr[r][0] = gr[r][1] = gr[r][2] = 0.f;
             int x = 0, y = 0, z = 0;
-            if (cell[r] >= 0) coords(s, cell[r], x, y, z);
+            float p0 = 0.f;
+            if (cell[r] >= 0) {
+                coords(s, cell[r], x, y, z);
+                p0 = s.phi[cell[r]];
+            }
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int col = frag_col(j >> 2, j & 3, t);
-                float val = 0.f;
+                float in = 0.f, raw = p0;
                 if (cell[r] >= 0 && col < 27) {
                     const long long nb = nbr(s, x, y, z, cx(col), cy(col), cz(col));
                     if (nb < 0) {
                         bad[r] = true;
                     } else {
                         const int tn = s.flags[nb] & TYPE_MASK;
-                        bad[r] |= tn == T_SOL;
-                        val = tn == T_LIQ ? 1.f : (tn == T_IFC ? fminf(fmaxf(s.phi[nb], 0.f), 1.f) : 0.f);
+                        if (tn == T_SOL) {
+                            bad[r] = true;
+                        } else {
+                            raw = tn == T_LIQ ? 1.f : (tn == T_IFC ? s.phi[nb] : 0.f);
+                            in = fminf(fmaxf(raw, 0.f), 1.f);
+                        }
+                    }
+                    if (col != 13) {
+                        const float w = nnz(col) == 1 ? 4.f : (nnz(col) == 2 ? 2.f : 1.f);
+                        gr[r][0] += w * cx(col) * raw;
+                        gr[r][1] += w * cy(col) * raw;
+                        gr[r][2] += w * cz(col) * raw;
                     }
                 }
-                v[r][j] = val;
+                v[r][j] = in;
             }
-            bad[r] |= __shfl_xor_sync(0xffffffffu, bad[r], 1);
-            bad[r] |= __shfl_xor_sync(0xffffffffu, bad[r], 2);
+            bad[r] |= __shfl_xor_sync(full, bad[r], 1);
+            bad[r] |= __shfl_xor_sync(full, bad[r], 2);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                gr[r][k] += __shfl_xor_sync(full, gr[r][k], 1);
+                gr[r][k] += __shfl_xor_sync(full, gr[r][k], 2);
+            }
         }
         uint32_t xf[2][4];
 #pragma unroll
@@ -120,7 +144,9 @@ __global__ void __launch_bounds__(128) k_mlp_normals(Dev s, float4* out) {
         mlp_outputs(act, y[0], y[1]);
         if (t < 2 && cell[t] >= 0) {
             const int c = cell[t];
-            const float4 fd = py_normal(s, c);
+            const float gl = sqrtf(gr[t][0] * gr[t][0] + gr[t][1] * gr[t][1] + gr[t][2] * gr[t][2]);
+            const float4 fd = gl > 0.f ? make_float4(-gr[t][0] / gl, -gr[t][1] / gl, -gr[t][2] / gl, 0.f)
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
             float4 res = fd;
             ++evaluated;
             const float len = sqrtf(y[t][0] * y[t][0] + y[t][1] * y[t][1] + y[t][2] * y[t][2]);
@@ -136,8 +162,8 @@ __global__ void __launch_bounds__(128) k_mlp_normals(Dev s, float4* out) {
     }
     if (s.mlp_stats) {
         for (int o = 16; o > 0; o >>= 1) {
-            evaluated += __shfl_xor_sync(0xffffffffu, evaluated, o);
-            taken += __shfl_xor_sync(0xffffffffu, taken, o);
+            evaluated += __shfl_xor_sync(full, evaluated, o);
+            taken += __shfl_xor_sync(full, taken, o);
         }
         if (lane == 0 && evaluated) {
             atomicAdd(&s.mlp_stats[0], evaluated);
@@ -403,15 +429,16 @@ int launch_conversion(const Dev& s, int last_parity, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------ work lists
-// Block-aggregated append of up to SEG items per thread (one atomic per
-// block). Every thread of the block must call it.
-template <int SEG>
-__device__ __forceinline__ void block_append_multi(const Dev& s, const int (&items)[SEG], int nitems, int* list,
-                                                   int* count, int cap) {
+// Block-aggregated append of the cells c0 + k for the set bits k of a
+// thread's 32-bit mask (one atomic per block). Every thread of the block must
+// call it.
+__device__ __forceinline__ void block_append_mask(const Dev& s, unsigned mask, int c0, int* list, int* count,
+                                                  int cap) {
     __shared__ int warp_tot[32];
     __shared__ int block_base;
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nitems = __popc(mask);
     int incl = nitems;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -430,9 +457,9 @@ __device__ __forceinline__ void block_append_multi(const Dev& s, const int (&ite
         block_base = tot ? atomicAdd(count, tot) : 0;
     }
     __syncthreads();
-    const int start = block_base + warp_tot[wid] + incl - nitems;
-    for (int k = 0; k < nitems; ++k) {
-        if (start + k < cap) list[start + k] = items[k];
+    int k = block_base + warp_tot[wid] + incl - nitems;
+    for (unsigned m = mask; m; m &= m - 1, ++k) {
+        if (k < cap) list[k] = c0 + __ffs(m) - 1;
         else set_error(s, ERR_CAPACITY);
     }
     __syncthreads();
@@ -448,13 +475,12 @@ constexpr int CLS_SEG = 16;
 __global__ void k_classify_seg(Dev s) {
     const long long seg = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nseg = s.n / CLS_SEG;
-    int ifc_items[CLS_SEG], sol_items[CLS_SEG];
-    int nifc = 0, nsol = 0;
+    unsigned ifc_mask = 0, sol_mask = 0;     // bit k: cell c0 + k
+    const long long c0 = seg * CLS_SEG;
     if (seg < nseg) {
-        const long long c0 = seg * CLS_SEG;
         int x0, y, z;
         coords(s, c0, x0, y, z);
-        // fluid bits of the segment's own row, then the OR over the 9 rows
+        // fluid bits of the 9 rows, ORed
         unsigned own_t[CLS_SEG / 4];
         unsigned orr = 0;   // bits 0..17 <-> x0-1 .. x0+16
 #pragma unroll
@@ -495,12 +521,12 @@ __global__ void k_classify_seg(Dev s) {
 #pragma unroll
         for (int k = 0; k < CLS_SEG; ++k) {
             const unsigned t = (own_t[k >> 2] >> (8 * (k & 3))) & TYPE_MASK;
-            if (t == T_IFC) ifc_items[nifc++] = (int)(c0 + k);
-            else if (t == T_SOL && ((nb >> (k + 1)) & 1u)) sol_items[nsol++] = (int)(c0 + k);
+            ifc_mask |= (t == T_IFC) ? (1u << k) : 0u;
+            sol_mask |= (t == T_SOL && ((nb >> (k + 1)) & 1u)) ? (1u << k) : 0u;
         }
     }
-    block_append_multi<CLS_SEG>(s, ifc_items, nifc, s.wl, s.wl_count, s.wl_cap);
-    block_append_multi<CLS_SEG>(s, sol_items, nsol, s.sl, s.sl_count, s.sl_cap);
+    block_append_mask(s, ifc_mask, (int)c0, s.wl, s.wl_count, s.wl_cap);
+    block_append_mask(s, sol_mask, (int)c0, s.sl, s.sl_count, s.sl_cap);
 }
 
 // Fallback for lattices whose x extent is not a multiple of 16: one thread
