@@ -58,8 +58,13 @@ __host__ __device__ constexpr unsigned wall_bits(int dx, int dy, int dz) {
 // blocks over rows (y, z), so the coordinates need no division per cell.
 // Stored values move raw (times the storage scale); the collision folds the
 // scale into its moments.
+// resident blocks per SM asked of the compiler: 64 registers for FP32 storage,
+// 48 for 16-bit storage (a few spilled words cost less than the lost warps)
+template <typename S>
+constexpr int liquid_min_blocks() { return sizeof(S) == 2 ? 5 : 4; }
+
 template <typename S, int PAR>
-__global__ void __launch_bounds__(256, 3) k_liquid(Dev s) {
+__global__ void __launch_bounds__(256, liquid_min_blocks<S>()) k_liquid(Dev s) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= s.nx) return;
     S* f = static_cast<S*>(s.f);
@@ -194,11 +199,6 @@ __device__ __forceinline__ PData particle_data(const Dev& s, int p) {
 // (nx is a multiple of TILE). The cells at x = 0 and x = nx-1 belong to the
 // row kernel. Odd steps run k_liquid: their slices are shifted by one
 // element along x, and staging them measured slower than direct loads.
-#ifndef FSLBM_STAGED_DEPTH
-#define FSLBM_STAGED_DEPTH 3
-#endif
-constexpr int STAGES = FSLBM_STAGED_DEPTH;   // tiles in flight per CTA
-
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
     return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }
@@ -240,6 +240,9 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
 
 template <typename S>
 struct StagedLayout {
+    // tiles in flight per CTA: with 16-bit elements two stages leave room for
+    // more CTAs per SM, which measured faster; 32-bit elements keep three
+    static constexpr int STAGES = sizeof(S) == 2 ? 2 : 3;
     static constexpr int ROW = TILE;                            // elements per direction slice
     static constexpr int PDF_BYTES = 27 * ROW * (int)sizeof(S);
     static constexpr int STAGE_BYTES = PDF_BYTES + TILE;        // + the tile's flag bytes
@@ -261,6 +264,7 @@ __device__ __forceinline__ void staged_issue(const Dev& s, S* buf, uint64_t* ful
 template <typename S>
 __global__ void __launch_bounds__(TILE) k_liquid_staged(Dev s) {
     using L = StagedLayout<S>;
+    constexpr int STAGES = L::STAGES;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     S* bufs = reinterpret_cast<S*>(smem_raw);
     __shared__ __align__(8) uint64_t full[STAGES];
@@ -617,7 +621,7 @@ template <typename S>
 static int staged_blocks() {
     static int blocks = 0;
     if (blocks == 0) {
-        const int smem = STAGES * StagedLayout<S>::STAGE_BYTES;
+        const int smem = StagedLayout<S>::STAGES * StagedLayout<S>::STAGE_BYTES;
         cudaFuncSetAttribute(k_liquid_staged<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_liquid_staged<S>, TILE, smem);
@@ -641,7 +645,7 @@ static void launch_typed(const Dev& s, int parity, cudaStream_t st) {
         if (use_staged(s)) {
             const long long nrow = 2LL * s.nz + 2LL * (s.ny - 2);
             const int rb = (int)((nrow * s.nx + 2LL * (s.ny - 2) * (s.nz - 2) + 255) / 256);
-            const size_t smem = (size_t)STAGES * StagedLayout<S>::STAGE_BYTES;
+            const size_t smem = (size_t)StagedLayout<S>::STAGES * StagedLayout<S>::STAGE_BYTES;
             k_liquid_staged<S><<<staged_blocks<S>(), TILE, smem, st>>>(s);
             k_liquid_rows<S, 0><<<rb, 256, 0, st>>>(s);
         } else {
