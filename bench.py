@@ -157,6 +157,28 @@ def run_oracle(w, steps: int, warmup: int, crop_nx: int, theta=None) -> dict:
 
 LAM, MU = 0.4, 0.1
 
+# DRAM traffic of the stream-collide sweep per fluid cell: dram__bytes_read.sum +
+# dram__bytes_write.sum of every sweep kernel (links, liquid, rows, interface),
+# even and odd steps averaged, from one ncu capture on the 1024x64x128 flume.
+# It is valid while the sweep's sources hash to `sources`, and is scaled to a
+# run by its fluid cells.
+SWEEP_TRAFFIC = {"sources": "b17cf9cac7074204", "workload": "precision-1024x64x128",
+                 "per_fluid_cell": {"fp16": 193.0, "fp32": 379.9, "bf16": None}}
+SWEEP_SOURCES = ("paper_2301_10674_gb300/csrc/stream_collide.cu", "paper_2301_10674_gb300/csrc/fslbm_dev.cuh")
+
+
+def _sweep_traffic(storage_name: str, fluid: float):
+    import hashlib
+    h = hashlib.sha256()
+    for rel in SWEEP_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    per = SWEEP_TRAFFIC["per_fluid_cell"].get(storage_name)
+    if per is None or h.hexdigest()[:16] != SWEEP_TRAFFIC["sources"]:
+        return None, "no ncu capture of the current sweep for this storage"
+    return int(per * fluid), (f"{per} B per fluid cell from an ncu capture on {SWEEP_TRAFFIC['workload']}, "
+                              f"scaled by fluid cells")
+
 
 def train_normal_model(stream, n_stencils: int, steps: int, seed: int = 4) -> tuple[np.ndarray, dict]:
     """Learned normal trained by the library's own kernels (not timed):
@@ -243,8 +265,9 @@ def _roofline(run, storage_name, ncell):
     sweep_s = run["sweep_ms"] / 1e3 / max(1, run["sweeps"])
     achieved = bytes_per_sweep / sweep_s / 1e9
     peak, peak_kind = _peaks()
+    traffic, traffic_note = _sweep_traffic(storage_name, fluid)
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": None,
+            "frac": round(achieved / peak, 4), "traffic": traffic, "traffic_note": traffic_note,
             "kernel": "stream-collide sweep (staged bulk + face rows + particle links + interface list)",
             "bytes_per_cell": {"fluid": 54 * elem + 1, "gas_or_solid": 1},
             "bytes_per_launch": int(bytes_per_sweep), "launch_ms": round(sweep_s * 1e3, 4),

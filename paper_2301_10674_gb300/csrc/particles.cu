@@ -676,6 +676,9 @@ __global__ void k_transitions(Dev s, int last_parity) {
             float rs = 0.f;
             int cnt = 0;
             bool gas = false;
+            // rolled: unrolled with its 27 loads per neighbour the loop is
+            // tens of kilobytes of code run once, bound by instruction fetch
+#pragma unroll 1
             for (int q = 0; q < 27; ++q) {
                 if (q == 13) continue;
                 long long nb = nbr(s, x, y, z, cx(q), cy(q), cz(q));

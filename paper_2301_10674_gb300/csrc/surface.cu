@@ -267,6 +267,9 @@ __global__ void k_init_new(Dev s, int last_parity) {
             coords(s, c, x, y, z);
             float rs = 0.f, us = 0.f, vs = 0.f, ws = 0.f;
             int cnt = 0;
+            // rolled: the 27 loads per liquid neighbour make an unrolled loop
+            // bound by instruction fetch
+#pragma unroll 1
             for (int q = 0; q < 27; ++q) {
                 if (q == 13) continue;
                 long long nb = nbr(s, x, y, z, cx(q), cy(q), cz(q));
