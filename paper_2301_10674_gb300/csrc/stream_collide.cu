@@ -54,8 +54,9 @@ __host__ __device__ constexpr unsigned wall_bits(int dx, int dy, int dz) {
 // coordinates: an even step reads its own slots (a wall-bound PDF came back
 // into (q, x) in the previous odd step), an odd step reads (q, x) across a
 // wall face and writes (opp(q), x) toward one. Interior cells of an odd step
-// use offsets that are the same for every thread. Threads run along x,
-// blocks over rows (y, z), so the coordinates need no division per cell.
+// use offsets that are the same for every thread. Blocks run over a
+// 256-cell segment of a row (y, z), so the coordinates need no division per
+// cell; the segment's liquid cells are compacted onto the first threads.
 // Stored values move raw (times the storage scale); the collision folds the
 // scale into its moments.
 // resident blocks per SM asked of the compiler: 64 registers for FP32 storage,
@@ -65,15 +66,33 @@ constexpr int liquid_min_blocks() { return sizeof(S) == 2 ? 5 : 4; }
 
 template <typename S, int PAR>
 __global__ void __launch_bounds__(256, liquid_min_blocks<S>()) k_liquid(Dev s) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= s.nx) return;
+    __shared__ int xs[256];      // x of the liquid cells of this block's row segment, compacted
+    __shared__ int wn[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     S* f = static_cast<S*>(s.f);
     const long long n = s.n;
     const int nrows = s.ny * s.nz;
     const int sxy = s.nx * s.ny;
     for (int row = blockIdx.y; row < nrows; row += gridDim.y) {
+        // compaction: thread t collides the t-th liquid cell of the segment,
+        // so only the last busy warp has idle lanes
+        const int xt = blockIdx.x * blockDim.x + threadIdx.x;
+        const bool liq = xt < s.nx && (s.flags[xt + s.nx * row] & TYPE_MASK) == T_LIQ;
+        const unsigned m = __ballot_sync(0xffffffffu, liq);
+        if (lane == 0) wn[warp] = __popc(m);
+        __syncthreads();
+        int off = 0, tot = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            off += w < warp ? wn[w] : 0;
+            tot += wn[w];
+        }
+        if (liq) xs[off + __popc(m & ((1u << lane) - 1u))] = xt;
+        __syncthreads();
+        const int x = (int)threadIdx.x < tot ? xs[threadIdx.x] : -1;
+        __syncthreads();             // xs and wn are rewritten by the next row
+        if (x < 0) continue;
         const int cell = x + s.nx * row;
-        if ((s.flags[cell] & TYPE_MASK) != T_LIQ) continue;
         const int y = row % s.ny, z = row / s.ny;
         const bool interior =
             PAR == 0 || (x > 0 && x < s.nx - 1 && y > 0 && y < s.ny - 1 && z > 0 && z < s.nz - 1);
@@ -271,7 +290,8 @@ __global__ void __launch_bounds__(TILE) k_liquid_staged(Dev s) {
     __shared__ __align__(8) uint64_t empty[STAGES];
     __shared__ int stage_tile[STAGES];
     __shared__ int stage_edge[STAGES];   // bit 0: tile starts at x = 0; bit 1: ends at x = nx - 1
-    __shared__ int abort_flag;
+    __shared__ int pos[TILE];            // tile positions of the liquid cells, compacted
+    __shared__ int wn[TILE / 32];
     const int ntiles = *s.tile_count;
     const int mine = ntiles > (int)blockIdx.x ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
     if (mine == 0) return;
@@ -290,7 +310,6 @@ __global__ void __launch_bounds__(TILE) k_liquid_staged(Dev s) {
             mbar_init(&full[k], 1);
             mbar_init(&empty[k], nwarps);
         }
-        abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -299,22 +318,44 @@ __global__ void __launch_bounds__(TILE) k_liquid_staged(Dev s) {
         for (int k = 0; k < STAGES && k < mine; ++k) issue(k, k);
     S* f = static_cast<S*>(s.f);
     const long long n = s.n;
+    // thread 0: the last tile index issued into each stage (-1: none), and
+    // whether a refill gave up waiting for its stage to be released
+    int last_issued[STAGES];
+    bool refill_failed = false;
+    for (int k = 0; k < STAGES; ++k) last_issued[k] = k < mine ? k : -1;
     for (int i = 0; i < mine; ++i) {
         const int st = i % STAGES;
         const unsigned ph = (unsigned)(i / STAGES) & 1u;
-        if (!mbar_wait(s, &full[st], ph)) abort_flag = 1;
-        if (abort_flag) break;
+        const bool ok = mbar_wait(s, &full[st], ph);
         const S* buf = bufs + st * SE;
         const unsigned char* fl = reinterpret_cast<const unsigned char*>(buf) + L::PDF_BYTES;
-        const int cell = stage_tile[st] * TILE + tid;
-        const int edge = stage_edge[st];
+        const int edge = ok ? stage_edge[st] : 0;
         const bool x_edge = (tid == 0 && (edge & 1)) || (tid == TILE - 1 && (edge & 2));
-        if (!x_edge && (fl[tid] & TYPE_MASK) == T_LIQ) {
+        // compaction: thread t collides the t-th liquid cell of the tile, so
+        // only the last busy warp has idle lanes
+        const bool liq = ok && !x_edge && (fl[tid] & TYPE_MASK) == T_LIQ;
+        const int lane = tid & 31, warp = tid >> 5;
+        const unsigned m = __ballot_sync(0xffffffffu, liq);
+        if (lane == 0) wn[warp] = __popc(m);
+        // a bounded wait that gave up ends the loop for every thread at once
+        if (__syncthreads_or(!ok || refill_failed)) break;
+        int off = 0, tot = 0;
+#pragma unroll
+        for (int w = 0; w < TILE / 32; ++w) {
+            off += w < warp ? wn[w] : 0;
+            tot += wn[w];
+        }
+        if (liq) pos[off + __popc(m & ((1u << lane) - 1u))] = tid;
+        __syncthreads();
+        const int p = tid < tot ? pos[tid] : -1;
+        const int cell = stage_tile[st] * TILE + p;
+        __syncthreads();             // pos and wn are rewritten by the next tile
+        if (p >= 0) {
             // stored values (times the storage scale) in and out; the
             // collision folds the scale into its moments
             float v[27];
 #pragma unroll
-            for (int q = 0; q < 27; ++q) v[q] = Store<S>::ld_raw(buf + q * L::ROW + tid);
+            for (int q = 0; q < 27; ++q) v[q] = Store<S>::ld_raw(buf + q * L::ROW + p);
             float rho, ux, uy, uz;
             collide_scaled(v, Store<S>::scale, s.omega, s.gx, s.gy, s.gz, rho, ux, uy, uz);
             if (s.idx32) {
@@ -331,19 +372,18 @@ __global__ void __launch_bounds__(TILE) k_liquid_staged(Dev s) {
         __syncwarp();
         if ((tid & 31) == 0) mbar_arrive(&empty[st]);
         if (tid == 0 && i + STAGES < mine) {
-            if (!mbar_wait(s, &empty[st], ph)) abort_flag = 1;
-            else issue(st, i + STAGES);
+            if (!mbar_wait(s, &empty[st], ph)) {
+                refill_failed = true;
+            } else {
+                issue(st, i + STAGES);
+                last_issued[st] = i + STAGES;
+            }
         }
     }
     // copies still in flight complete before the CTA leaves
-    if (tid == 0) {
-        for (int k = 0; k < STAGES; ++k) {
-            // the last use of stage k was tile index u = largest u < mine with u % STAGES == k
-            if (k >= mine) continue;
-            const int u = k + ((mine - 1 - k) / STAGES) * STAGES;
-            mbar_wait(s, &full[k], (unsigned)(u / STAGES) & 1u);
-        }
-    }
+    if (tid == 0)
+        for (int k = 0; k < STAGES; ++k)
+            if (last_issued[k] >= 0) mbar_wait(s, &full[k], (unsigned)(last_issued[k] / STAGES) & 1u);
 }
 
 // Per-thread pull-collide for the liquid cells of the rows on the y and z
