@@ -231,6 +231,9 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     d.tl = dalloc<int>(s, tcap, ok);
     d.sl_cap = (int)n;
     d.sl = dalloc<int>(s, n, ok);
+    d.fbits = dalloc<unsigned>(s, n / 32 + 1, ok);
+    d.ibits = dalloc<unsigned>(s, n / 32 + 1, ok);
+    d.sbits = dalloc<unsigned>(s, n / 32 + 1, ok);
     d.tiles = dalloc<int>(s, n / TILE + 1, ok);
     d.tl_info = dalloc<int>(s, 2 * tcap, ok);
     int* counts = dalloc<int>(s, 16, ok);

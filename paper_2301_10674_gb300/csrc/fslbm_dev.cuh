@@ -85,6 +85,7 @@ struct Dev {
     int* tl; int* tl_count; int tl_cap;        // particle map transitions
     int* sl; int* sl_count; int sl_cap;        // solid cells with a fluid neighbour
     int* tiles; int* tile_count;               // 128-cell x-tiles of interior rows holding liquid
+    unsigned* fbits; unsigned* ibits; unsigned* sbits;   // per 32 cells of a row: fluid / interface / solid bits
     int* tl_info;                               // per transition: new owner / new type
     double* pool;
     double* pool_share;

@@ -454,7 +454,7 @@ __global__ void __launch_bounds__(256, 3) k_liquid_rows(Dev s) {
 // PDFs, the torque (x_b - X_p) x F; one owner per thread, so a warp
 // segmented reduction gathers them.
 template <typename S, int PAR>
-__global__ void __launch_bounds__(256) k_solid_links(Dev s) {
+__global__ void __launch_bounds__(256, 3) k_solid_links(Dev s) {
     const int count = min(*s.sl_count, s.sl_cap);
     const int stride = gridDim.x * blockDim.x;
     float injected = 0.f;   // mass the moving bounce-back adds to liquid cells

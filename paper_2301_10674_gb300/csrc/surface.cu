@@ -468,24 +468,58 @@ __device__ __forceinline__ void block_append_mask(const Dev& s, unsigned mask, i
     __syncthreads();
 }
 
-constexpr int CLS_SEG = 16;
-
 // Lists the interface cells and the solid cells with a liquid or interface
-// cell among their 26 neighbours. One thread per 16 consecutive cells of a
-// row (nx a multiple of 16): the 3x3 rows around the segment are read as
-// 16-byte words plus the two halo bytes, the fluid bits ORed along x and
-// over the nine rows.
-__global__ void k_classify_seg(Dev s) {
-    const long long seg = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long nseg = s.n / CLS_SEG;
-    unsigned ifc_mask = 0, sol_mask = 0;     // bit k: cell c0 + k
-    const long long c0 = seg * CLS_SEG;
-    if (seg < nseg) {
-        int x0, y, z;
-        coords(s, c0, x0, y, z);
-        // fluid bits of the 9 rows, ORed
-        unsigned own_t[CLS_SEG / 4];
-        unsigned orr = 0;   // bits 0..17 <-> x0-1 .. x0+16
+// cell among their 26 neighbours, for lattices whose x extent is a multiple of
+// 32. First pass, a thread per 32 consecutive cells of a row: their fluid,
+// interface and solid bits from two 16-byte loads. Second pass, a thread per
+// 32-cell word:
+// the fluid words of the 3x3 rows around it, each widened by the halo bits of
+// its x-neighbour words, are ORed, then ORed along x.
+// four type bytes (gas 0, liquid 1, interface 2, solid 3 in the low two
+// bits) to three 4-bit masks: fluid (1 or 2), interface, solid; the multiply
+// gathers the bits at positions 0, 8, 16, 24 into bits 21..24
+__device__ __forceinline__ void type_nibbles(unsigned v, unsigned& f, unsigned& i, unsigned& sl) {
+    const unsigned a = v & 0x03030303u;
+    const unsigned hi = a >> 1;
+    auto pack = [](unsigned x) { return ((x * 0x00204081u) >> 21) & 0xFu; };
+    f = pack((a ^ hi) & 0x01010101u);
+    i = pack(hi & ~a & 0x01010101u);
+    sl = pack(hi & a & 0x01010101u);
+}
+
+__global__ void k_type_bits(Dev s) {
+    const long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= (s.n >> 5)) return;
+    const uint4* src = reinterpret_cast<const uint4*>(s.flags + (w << 5));
+    const uint4 a = src[0], b = src[1];
+    const unsigned words[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    unsigned fm = 0, im = 0, sm = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        unsigned f, i, sl;
+        type_nibbles(words[k], f, i, sl);
+        fm |= f << (4 * k);
+        im |= i << (4 * k);
+        sm |= sl << (4 * k);
+    }
+    s.fbits[w] = fm;
+    s.ibits[w] = im;
+    s.sbits[w] = sm;
+}
+
+__global__ void k_classify_bits(Dev s) {
+    const long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nxw = s.nx >> 5;                      // words per row
+    const long long nw = s.n >> 5;
+    unsigned ifc_mask = 0, sol_mask = 0;
+    if (w < nw) {
+        const int xw = (int)(w % nxw);
+        const long long row = w / nxw;
+        const int y = (int)(row % s.ny), z = (int)(row / s.ny);
+        // x-neighbour words (periodic wrap, or none beyond a wall face)
+        const int xl = xw > 0 ? xw - 1 : (s.per_x ? nxw - 1 : -1);
+        const int xr = xw < nxw - 1 ? xw + 1 : (s.per_x ? 0 : -1);
+        unsigned long long orr = 0;   // bit 1 + k <-> x0 + k, bit 0 <-> x0 - 1, bit 33 <-> x0 + 32
 #pragma unroll
         for (int dz = -1; dz <= 1; ++dz) {
             const int zz = shift(z, dz, s.nz, s.per_z);
@@ -494,45 +528,24 @@ __global__ void k_classify_seg(Dev s) {
             for (int dy = -1; dy <= 1; ++dy) {
                 const int yy = shift(y, dy, s.ny, s.per_y);
                 if (yy < 0) continue;
-                const long long row = (long long)s.nx * (yy + (long long)s.ny * zz);
-                const uint4 w = *reinterpret_cast<const uint4*>(s.flags + row + x0);
-                const unsigned wd[4] = {w.x, w.y, w.z, w.w};
-                unsigned bits = 0;
-#pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    const unsigned t = (wd[k >> 2] >> (8 * (k & 3))) & TYPE_MASK;
-                    bits |= (t == T_LIQ || t == T_IFC) ? (1u << (k + 1)) : 0u;
-                }
-                const int xl = shift(x0, -1, s.nx, s.per_x), xr = shift(x0 + 15, 1, s.nx, s.per_x);
-                if (xl >= 0) {
-                    const unsigned t = s.flags[row + xl] & TYPE_MASK;
-                    bits |= (t == T_LIQ || t == T_IFC) ? 1u : 0u;
-                }
-                if (xr >= 0) {
-                    const unsigned t = s.flags[row + xr] & TYPE_MASK;
-                    bits |= (t == T_LIQ || t == T_IFC) ? (1u << 17) : 0u;
-                }
-                orr |= bits;
-                if (dz == 0 && dy == 0) {
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) own_t[k] = wd[k];
-                }
+                const long long rbase = ((long long)zz * s.ny + yy) * nxw;
+                const unsigned cw = s.fbits[rbase + xw];
+                const unsigned lw = xl >= 0 ? s.fbits[rbase + xl] : 0u;
+                const unsigned rw = xr >= 0 ? s.fbits[rbase + xr] : 0u;
+                orr |= ((unsigned long long)cw << 1) | (unsigned long long)(lw >> 31) |
+                       ((unsigned long long)(rw & 1u) << 33);
             }
         }
-        // x-neighbourhood: bit k+1 of (orr | orr>>1 | orr<<1) covers x0+k-1..x0+k+1
-        const unsigned nb = orr | (orr >> 1) | (orr << 1);
-#pragma unroll
-        for (int k = 0; k < CLS_SEG; ++k) {
-            const unsigned t = (own_t[k >> 2] >> (8 * (k & 3))) & TYPE_MASK;
-            ifc_mask |= (t == T_IFC) ? (1u << k) : 0u;
-            sol_mask |= (t == T_SOL && ((nb >> (k + 1)) & 1u)) ? (1u << k) : 0u;
-        }
+        const unsigned long long nb = orr | (orr >> 1) | (orr << 1);   // bit 1 + k: fluid in the 3x3x3 block
+        sol_mask = s.sbits[w] & (unsigned)(nb >> 1);
+        ifc_mask = s.ibits[w];
     }
-    block_append_mask(s, ifc_mask, (int)c0, s.wl, s.wl_count, s.wl_cap);
-    block_append_mask(s, sol_mask, (int)c0, s.sl, s.sl_count, s.sl_cap);
+    const int c0 = (int)(w << 5);
+    block_append_mask(s, ifc_mask, c0, s.wl, s.wl_count, s.wl_cap);
+    block_append_mask(s, sol_mask, c0, s.sl, s.sl_count, s.sl_cap);
 }
 
-// Fallback for lattices whose x extent is not a multiple of 16: one thread
+// Fallback for lattices whose x extent is not a multiple of 32: one thread
 // per cell, 26 neighbour reads for solid cells.
 __global__ void k_classify(Dev s) {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -621,13 +634,15 @@ __global__ void k_tiles(Dev s) {
 int launch_classify(const Dev& s, cudaStream_t st) {
     cudaMemsetAsync(s.wl_count, 0, sizeof(int), st);
     cudaMemsetAsync(s.sl_count, 0, sizeof(int), st);
-    if (s.nx % CLS_SEG == 0) {
-        k_classify_seg<<<blocks_for(s.n / CLS_SEG, 128), 128, 0, st>>>(s);
+    int k = 2;
+    if (s.nx % 32 == 0) {
+        k_type_bits<<<blocks_for(s.n / 32, 256), 256, 0, st>>>(s);
+        k_classify_bits<<<blocks_for(s.n / 32, 128), 128, 0, st>>>(s);
+        ++k;
     } else {
         k_classify<<<blocks_for(s.n, 256), 256, 0, st>>>(s);
     }
     k_clamp_count<<<1, 1, 0, st>>>(s);
-    int k = 2;
     if (s.nx % TILE == 0) {
         cudaMemsetAsync(s.tile_count, 0, sizeof(int), st);
         k_tiles<<<blocks_for(s.n / TILE, 256), 256, 0, st>>>(s);
