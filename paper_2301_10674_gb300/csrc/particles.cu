@@ -31,27 +31,47 @@ __global__ void k_grid_count(Dev s) {
     atomicAdd(&s.g_count[g], 1);
 }
 
-// exclusive scan of the grid counts by one block
-__global__ void k_grid_scan(Dev s, int G) {
-    __shared__ int part[1024];
-    const int t = threadIdx.x;
-    const int chunk = (G + blockDim.x - 1) / blockDim.x;
-    const int lo = t * chunk, hi = min(G, lo + chunk);
+// exclusive scan of the grid counts by one block of 32 warps: warp w owns a
+// contiguous chunk, read 32 counts at a time (coalesced); its total joins a
+// scan of the 32 warp totals, then the warp scans its chunk from that offset
+__global__ void __launch_bounds__(1024) k_grid_scan(Dev s, int G) {
+    __shared__ int wtot[32];
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int rows = (G + 31) / 32;                    // rows of 32 counts
+    const int per = (rows + 31) / 32;                  // rows per warp
+    const int r0 = warp * per, r1 = min(rows, r0 + per);
     int sum = 0;
-    for (int i = lo; i < hi; ++i) sum += s.g_count[i];
-    part[t] = sum;
-    __syncthreads();
-    for (int off = 1; off < blockDim.x; off <<= 1) {
-        int v = t >= off ? part[t - off] : 0;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
+    for (int r = r0; r < r1; ++r) {
+        const int i = 32 * r + lane;
+        sum += i < G ? s.g_count[i] : 0;
     }
-    int run = part[t] - sum;
-    for (int i = lo; i < hi; ++i) {
-        s.g_start[i] = run;
-        s.g_cursor[i] = run;
-        run += s.g_count[i];
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(full, sum, o);
+    if (lane == 0) wtot[warp] = sum;
+    __syncthreads();
+    if (warp == 0) {
+        int v = wtot[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(full, v, o);
+            if (lane >= o) v += u;
+        }
+        wtot[lane] = v - wtot[lane];                   // exclusive
+    }
+    __syncthreads();
+    int run = wtot[warp];
+    for (int r = r0; r < r1; ++r) {
+        const int i = 32 * r + lane;
+        const int c = i < G ? s.g_count[i] : 0;
+        int v = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(full, v, o);
+            if (lane >= o) v += u;
+        }
+        if (i < G) {
+            s.g_start[i] = run + v - c;
+            s.g_cursor[i] = run + v - c;
+        }
+        run += __shfl_sync(full, v, 31);
     }
 }
 
@@ -653,84 +673,94 @@ enum : int { NT_UNCOVERED_LIQ = 0x100 };
 // (interface next to gas, gas without fluid neighbours) with f_eq(mean rho,
 // u_b) and take their mass from the pool (snapshot of the cell types)
 __global__ void k_transitions(Dev s, int last_parity) {
-    double dpool = 0.0;   // this thread's change of the pool (one atomic per block)
-    FOR_TL(i) {
+    // a warp per transition: the 27 PDFs of a covered cell, the 26
+    // neighbours of an uncovered one and its 27 new PDFs are spread over the
+    // lanes, so no thread walks a long chain of dependent loads
+    double dpool = 0.0;   // lane 0's change of the pool (one atomic per block)
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int count = min(*s.tl_count, s.tl_cap);
+    for (int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); i < count; i += nwarps) {
         const int c = s.tl[i];
         const int o1 = s.tl_info[2 * i];
         const int t0 = s.flags[c] & TYPE_MASK;
+        int x, y, z;
+        coords(s, c, x, y, z);
         int nt;
         if (o1 >= 0) {
-            if (t0 == T_LIQ) {
-                float f[27];
-                load_fstar(s, c, last_parity, f);
-                float d = 0.f;
-                for (int q = 0; q < 27; ++q) d += f[q];
-                dpool += (double)(1.f + d);
-            } else if (t0 == T_IFC) {
-                dpool += (double)s.mass[c];
+            // covered: its liquid mass goes to the pool
+            float v = (t0 == T_LIQ && lane < 27) ? ld_any(s, s.f, fstar_slot(s, lane, x, y, z, c, last_parity)) : 0.f;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(full, v, o);
+            if (lane == 0) {
+                if (t0 == T_LIQ) dpool += (double)(1.f + v);
+                else if (t0 == T_IFC) dpool += (double)s.mass[c];
             }
             nt = T_SOL;
         } else {
-            int x, y, z;
-            coords(s, c, x, y, z);
+            // uncovered: lane k takes neighbour q = k (k < 13) or k + 1
             float rs = 0.f;
             int cnt = 0;
             bool gas = false;
-            // rolled: unrolled with its 27 loads per neighbour the loop is
-            // tens of kilobytes of code run once, bound by instruction fetch
-#pragma unroll 1
-            for (int q = 0; q < 27; ++q) {
-                if (q == 13) continue;
-                long long nb = nbr(s, x, y, z, cx(q), cy(q), cz(q));
-                if (nb < 0) continue;
-                int tn = s.flags[nb] & TYPE_MASK;
-                if (tn == T_IFC) { rs += s.ru[nb].x; cnt++; }
-                else if (tn == T_LIQ) {
-                    float g[27];
-                    load_fstar(s, nb, last_parity, g);
-                    float d = 0.f;
-                    for (int k = 0; k < 27; ++k) d += g[k];
-                    rs += 1.f + d;
-                    cnt++;
+            if (lane < 26) {
+                const int q = lane < 13 ? lane : lane + 1;
+                const long long nb = nbr(s, x, y, z, cx(q), cy(q), cz(q));
+                if (nb >= 0) {
+                    const int tn = s.flags[nb] & TYPE_MASK;
+                    if (tn == T_IFC) {
+                        rs = s.ru[nb].x;
+                        cnt = 1;
+                    } else if (tn == T_LIQ) {
+                        float g[27];
+                        load_fstar(s, nb, last_parity, g);
+                        float d = 0.f;
+                        for (int k = 0; k < 27; ++k) d += g[k];
+                        rs = 1.f + d;
+                        cnt = 1;
+                    }
+                    gas = tn == T_GAS;
                 }
-                if (tn == T_GAS) gas = true;
             }
+            for (int o = 16; o > 0; o >>= 1) {
+                rs += __shfl_xor_sync(full, rs, o);
+                cnt += __shfl_xor_sync(full, cnt, o);
+            }
+            gas = __any_sync(full, gas);
             if (cnt == 0) {
                 nt = T_GAS;
             } else {
                 const float rb = rs / cnt;
                 int po = s.owner[c];
                 if (po < 0 || po >= s.np) {
-                    set_error(s, ERR_INVARIANT);
+                    if (lane == 0) set_error(s, ERR_INVARIANT);
                     po = 0;
                 }
                 const double* Xp = s.X + 3 * po;
-                double d[3] = {wrapd(x + 0.5 - Xp[0], s.nx, s.per_x), wrapd(y + 0.5 - Xp[1], s.ny, s.per_y),
-                               wrapd(z + 0.5 - Xp[2], s.nz, s.per_z)};
+                const double d[3] = {wrapd(x + 0.5 - Xp[0], s.nx, s.per_x), wrapd(y + 0.5 - Xp[1], s.ny, s.per_y),
+                                     wrapd(z + 0.5 - Xp[2], s.nz, s.per_z)};
                 const double* Up = s.U + 3 * po;
                 const double* Wp = s.W + 3 * po;
-                double ub[3] = {Up[0] + (Wp[1] * d[2] - Wp[2] * d[1]), Up[1] + (Wp[2] * d[0] - Wp[0] * d[2]),
-                                Up[2] + (Wp[0] * d[1] - Wp[1] * d[0])};
-                float f[27];
-                for (int q = 0; q < 27; ++q) f[q] = feq_dev(q, rb, (float)ub[0], (float)ub[1], (float)ub[2]);
-                store_fstar(s, c, last_parity, f);
-                for (int q = 0; q < 27; ++q) st_any(s, s.fs, (long long)q * s.n + c, f[q]);
-                s.ru[c] = make_float4(rb, (float)ub[0], (float)ub[1], (float)ub[2]);
-                if (gas) {
-                    nt = T_IFC;
-                    s.mass[c] = 0.f;
-                } else {
-                    nt = T_LIQ | NT_UNCOVERED_LIQ;
-                    s.mass[c] = rb;
-                    dpool -= (double)rb;
+                const float ub[3] = {(float)(Up[0] + (Wp[1] * d[2] - Wp[2] * d[1])),
+                                     (float)(Up[1] + (Wp[2] * d[0] - Wp[0] * d[2])),
+                                     (float)(Up[2] + (Wp[0] * d[1] - Wp[1] * d[0]))};
+                if (lane < 27) {
+                    const float fq = feq_dev(lane, rb, ub[0], ub[1], ub[2]);
+                    st_any(s, s.f, fstar_slot(s, lane, x, y, z, c, last_parity), fq);
+                    st_any(s, s.fs, (long long)lane * s.n + c, fq);
                 }
+                if (lane == 0) {
+                    s.ru[c] = make_float4(rb, ub[0], ub[1], ub[2]);
+                    s.mass[c] = gas ? 0.f : rb;
+                    if (!gas) dpool -= (double)rb;
+                }
+                nt = gas ? T_IFC : (T_LIQ | NT_UNCOVERED_LIQ);
             }
         }
-        s.tl_info[2 * i + 1] = nt;
+        if (lane == 0) s.tl_info[2 * i + 1] = nt;
     }
     __shared__ double red[32];
-    for (int o = 16; o > 0; o >>= 1) dpool += __shfl_xor_sync(0xffffffffu, dpool, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dpool;
+    for (int o = 16; o > 0; o >>= 1) dpool += __shfl_xor_sync(full, dpool, o);
+    if (lane == 0) red[threadIdx.x >> 5] = dpool;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
