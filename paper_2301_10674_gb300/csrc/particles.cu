@@ -142,26 +142,31 @@ __global__ void k_force_avg(Dev s, int have_prev) {
     s.Tp[k] = th;
 }
 
-__device__ __forceinline__ int hist_slot(const Dev& s, int p, int partner, unsigned& seen) {
-    int* hp = s.hist_partner + (long long)p * HIST_SLOTS;
-    int freeslot = -1;
+// The history slot of a partner among the particle's slots held in
+// registers: its own, else the first empty one, whose spring starts at zero;
+// -1 (and the sticky history bit) when none is left.
+__device__ __forceinline__ int hist_slot(const Dev& s, int p, int partner, int (&hpart)[HIST_SLOTS],
+                                         unsigned& seen) {
+    int found = -1, freeslot = -1;
+#pragma unroll
     for (int k = 0; k < HIST_SLOTS; ++k) {
-        int v = hp[k];
-        if (v == partner) {
-            seen |= 1u << k;
-            return k;
+        if (hpart[k] == partner && found < 0) found = k;
+        if (hpart[k] == HIST_EMPTY && freeslot < 0) freeslot = k;
+    }
+    if (found < 0) {
+        if (freeslot < 0) {
+            set_error(s, ERR_HISTORY);
+            return -1;
         }
-        if (v == HIST_EMPTY && freeslot < 0) freeslot = k;
+        found = freeslot;
+#pragma unroll
+        for (int k = 0; k < HIST_SLOTS; ++k)
+            if (k == found) hpart[k] = partner;
+        double* xi = s.hist_xi + ((long long)p * HIST_SLOTS + found) * 3;
+        xi[0] = xi[1] = xi[2] = 0.0;
     }
-    if (freeslot < 0) {
-        set_error(s, ERR_HISTORY);
-        return -1;
-    }
-    hp[freeslot] = partner;
-    double* xi = s.hist_xi + ((long long)p * HIST_SLOTS + freeslot) * 3;
-    xi[0] = xi[1] = xi[2] = 0.0;
-    seen |= 1u << freeslot;
-    return freeslot;
+    seen |= 1u << found;
+    return found;
 }
 
 // minimal image of a displacement along a periodic axis (|d| < 1.5 L)
@@ -291,36 +296,61 @@ __global__ void __launch_bounds__(64) k_dem_substep(Dev s, const double* __restr
     double F[3] = {s.Fa[3 * p] + mi * s.gxd, s.Fa[3 * p + 1] + mi * s.gyd, s.Fa[3 * p + 2] + mi * s.gzd};
     double T[3] = {s.Ta[3 * p], s.Ta[3 * p + 1], s.Ta[3 * p + 2]};
     unsigned seen = 0;
+    // the particle's tangential-history partners, held in registers for the
+    // sub-step (slot k: partner index, a wall code, or HIST_EMPTY)
+    int hpart[HIST_SLOTS];
+    {
+        const int4* hp4 = reinterpret_cast<const int4*>(s.hist_partner + (long long)p * HIST_SLOTS);
+#pragma unroll
+        for (int k = 0; k < HIST_SLOTS / 4; ++k) {
+            const int4 v = hp4[k];
+            hpart[4 * k] = v.x; hpart[4 * k + 1] = v.y; hpart[4 * k + 2] = v.z; hpart[4 * k + 3] = v.w;
+        }
+    }
     const int nbc = s.nb_count[p];
-    for (int k = 0; k < nbc; ++k) {
-        const int j = s.nb[(long long)p * NB_SLOTS + k];
-        const float d[3] = {(float)wrapd(Xa[3 * j] - X[0], s.nx, s.per_x),
-                            (float)wrapd(Xa[3 * j + 1] - X[1], s.ny, s.per_y),
-                            (float)wrapd(Xa[3 * j + 2] - X[2], s.nz, s.per_z)};
-        const float rjf = (float)s.R[j];
-        const float dist2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-        const float rs = rif + rjf;
-        if (dist2 >= rs * rs) continue;
-        const float dist = sqrtf(dist2);
-        const float inv = 1.f / dist;
-        const float n[3] = {d[0] * inv, d[1] * inv, d[2] * inv};
-        const float delta = rs - dist;
-        float wsum[3];
-        for (int a = 0; a < 3; ++a) wsum[a] = rif * Wf[a] + rjf * (float)Wa[3 * j + a];
-        const float wn[3] = {wsum[1] * n[2] - wsum[2] * n[1], wsum[2] * n[0] - wsum[0] * n[2],
-                             wsum[0] * n[1] - wsum[1] * n[0]};
-        float vrel[3];
-        for (int a = 0; a < 3; ++a) vrel[a] = Uf[a] - (float)Ua[3 * j + a] + wn[a];
-        const float mj = (float)s.M[j];
-        const float meff = mif * mj / (mif + mj);
-        const int slot = hist_slot(s, p, j, seen);
-        if (slot < 0) continue;
-        double* xi = s.hist_xi + ((long long)p * HIST_SLOTS + slot) * 3;
-        float Fc[3], Ft[3];
-        contact_f(s, meff, n, delta, vrel, xi, dtf, Fc, Ft);
-        const float tq[3] = {rif * (n[1] * Ft[2] - n[2] * Ft[1]), rif * (n[2] * Ft[0] - n[0] * Ft[2]),
-                             rif * (n[0] * Ft[1] - n[1] * Ft[0])};
-        for (int a = 0; a < 3; ++a) { F[a] += (double)Fc[a]; T[a] += (double)tq[a]; }
+    const int* nbl = s.nb + (long long)p * NB_SLOTS;
+    // neighbours four at a time: their indices and positions load together
+    for (int k0 = 0; k0 < nbc; k0 += 4) {
+        int jj[4];
+        double xj[4][3];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) jj[u] = k0 + u < nbc ? nbl[k0 + u] : -1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) xj[u][a] = jj[u] >= 0 ? Xa[3 * jj[u] + a] : 0.0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = jj[u];
+            if (j < 0) continue;
+            const float d[3] = {(float)wrapd(xj[u][0] - X[0], s.nx, s.per_x),
+                                (float)wrapd(xj[u][1] - X[1], s.ny, s.per_y),
+                                (float)wrapd(xj[u][2] - X[2], s.nz, s.per_z)};
+            const float rjf = (float)s.R[j];
+            const float dist2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            const float rs = rif + rjf;
+            if (dist2 >= rs * rs) continue;
+            const float dist = sqrtf(dist2);
+            const float inv = 1.f / dist;
+            const float n[3] = {d[0] * inv, d[1] * inv, d[2] * inv};
+            const float delta = rs - dist;
+            float wsum[3];
+            for (int a = 0; a < 3; ++a) wsum[a] = rif * Wf[a] + rjf * (float)Wa[3 * j + a];
+            const float wn[3] = {wsum[1] * n[2] - wsum[2] * n[1], wsum[2] * n[0] - wsum[0] * n[2],
+                                 wsum[0] * n[1] - wsum[1] * n[0]};
+            float vrel[3];
+            for (int a = 0; a < 3; ++a) vrel[a] = Uf[a] - (float)Ua[3 * j + a] + wn[a];
+            const float mj = (float)s.M[j];
+            const float meff = mif * mj / (mif + mj);
+            const int slot = hist_slot(s, p, j, hpart, seen);
+            if (slot < 0) continue;
+            double* xi = s.hist_xi + ((long long)p * HIST_SLOTS + slot) * 3;
+            float Fc[3], Ft[3];
+            contact_f(s, meff, n, delta, vrel, xi, dtf, Fc, Ft);
+            const float tq[3] = {rif * (n[1] * Ft[2] - n[2] * Ft[1]), rif * (n[2] * Ft[0] - n[0] * Ft[2]),
+                                 rif * (n[0] * Ft[1] - n[1] * Ft[0])};
+            for (int a = 0; a < 3; ++a) { F[a] += (double)Fc[a]; T[a] += (double)tq[a]; }
+        }
     }
     // walls on non-periodic axes
     const int L[3] = {s.nx, s.ny, s.nz};
@@ -337,7 +367,7 @@ __global__ void __launch_bounds__(64) k_dem_substep(Dev s, const double* __restr
             const float wn[3] = {rw[1] * n[2] - rw[2] * n[1], rw[2] * n[0] - rw[0] * n[2],
                                  rw[0] * n[1] - rw[1] * n[0]};
             const float vrel[3] = {Uf[0] + wn[0], Uf[1] + wn[1], Uf[2] + wn[2]};
-            const int slot = hist_slot(s, p, -1 - (2 * a + side), seen);
+            const int slot = hist_slot(s, p, -1 - (2 * a + side), hpart, seen);
             if (slot < 0) continue;
             double* xi = s.hist_xi + ((long long)p * HIST_SLOTS + slot) * 3;
             float Fc[3], Ft[3];
@@ -347,9 +377,19 @@ __global__ void __launch_bounds__(64) k_dem_substep(Dev s, const double* __restr
             for (int b = 0; b < 3; ++b) { F[b] += (double)Fc[b]; T[b] += (double)tq[b]; }
         }
     }
-    int* hp = s.hist_partner + (long long)p * HIST_SLOTS;
-    for (int k = 0; k < HIST_SLOTS; ++k)
-        if (!(seen & (1u << k))) hp[k] = HIST_EMPTY;
+    // partners not met in this sub-step lose their springs
+    {
+        int4* hp4 = reinterpret_cast<int4*>(s.hist_partner + (long long)p * HIST_SLOTS);
+#pragma unroll
+        for (int k = 0; k < HIST_SLOTS / 4; ++k) {
+            int4 v;
+            v.x = (seen >> (4 * k)) & 1u ? hpart[4 * k] : HIST_EMPTY;
+            v.y = (seen >> (4 * k + 1)) & 1u ? hpart[4 * k + 1] : HIST_EMPTY;
+            v.z = (seen >> (4 * k + 2)) & 1u ? hpart[4 * k + 2] : HIST_EMPTY;
+            v.w = (seen >> (4 * k + 3)) & 1u ? hpart[4 * k + 3] : HIST_EMPTY;
+            hp4[k] = v;
+        }
+    }
     const double im = 1.0 / mi, iI = 1.0 / Ii;
     for (int a = 0; a < 3; ++a) {
         U[a] += dts * F[a] * im;
