@@ -161,6 +161,35 @@ def test_moving_particles_cover_and_uncover_cells():
     sim.close()
 
 
+def test_overlapping_moving_spheres_share_cells():
+    """Mobile spheres that overlap each other and a fixed sphere: cells
+    covered by two of them change owner as they move (the tie goes to the
+    smaller |x - X|^2 - r^2). The re-map of sharing particles must find every
+    such cell; owners and types are compared with the oracle exactly."""
+    w = W.Workload(name="cluster", nx=32, ny=16, nz=24, tau=0.6, g=(0.0, 0.0, -2e-4), liquid_height=20.0,
+                   diameter=6.0, bed="none", seed=9).generate()
+    w.xyz = np.array([[10.2, 8.1, 10.3], [14.9, 7.7, 11.1], [12.4, 9.3, 14.6], [22.0, 8.0, 5.2],
+                      [24.8, 8.4, 9.6]])
+    w.radius = np.array([3.0, 2.8, 2.7, 3.1, 2.6])
+    w.fixed = np.array([0, 0, 0, 1, 0], np.uint8)
+    sim = _sim(w)
+    o = oracle_from_workload(w)
+    u0 = np.array([[0.015, 0.0, -0.01], [-0.012, 0.004, 0.006], [0.0, -0.01, -0.012], [0.0, 0.0, 0.0],
+                   [-0.01, 0.0, -0.015]])
+    sim.set(F.FIELD_P_U, u0)
+    o.set(O.P_U, u0)
+    owners0 = o.get(O.F_OWNER)
+    for _ in range(15):
+        sim.step(10)
+        o.step(10)
+        _compare(sim, o, 1e-4, check_particles=False)
+        # overlaps of up to a cell make contact forces far above the other
+        # tests'; the FP32 contact law then leaves positions ~1e-6 apart
+        assert np.abs(sim.get(F.FIELD_P_X) - o.get(O.P_X)).max() < 1e-5
+    assert (o.get(O.F_OWNER) != owners0).sum() > 20
+    sim.close()
+
+
 @pytest.mark.parametrize("storage,tol", [(F.STORE_FP16, 2e-3), (F.STORE_BF16, 2e-2)])
 def test_reduced_precision_storage(storage, tol):
     """PDFs stored as f - w in FP16 / BF16 with FP32 arithmetic: one step of
