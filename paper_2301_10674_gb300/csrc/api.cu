@@ -203,12 +203,7 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     s->elem = p->storage == FSLBM_STORE_FP32 ? 4 : 2;
 
     bool ok = true;
-    // 128 bytes of slack on both sides: the staged sweep's 16-byte-aligned
-    // shifted slices reach one word beyond the first and last element
-    {
-        unsigned char* raw = static_cast<unsigned char*>(dalloc_bytes(s, (size_t)27 * n * s->elem + 256, ok));
-        d.f = raw ? raw + 128 : nullptr;
-    }
+    d.f = dalloc_bytes(s, (size_t)27 * n * s->elem, ok);
     d.fs = dalloc_bytes(s, (size_t)27 * n * s->elem, ok);
     d.flags = dalloc<uint8_t>(s, n + 4, ok);   // word-granular atomics on the last bytes
     d.mass = dalloc<float>(s, n, ok);
@@ -234,7 +229,6 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     d.fbits = dalloc<unsigned>(s, n / 32 + 1, ok);
     d.ibits = dalloc<unsigned>(s, n / 32 + 1, ok);
     d.sbits = dalloc<unsigned>(s, n / 32 + 1, ok);
-    d.tiles = dalloc<int>(s, n / TILE + 1, ok);
     d.tl_info = dalloc<int>(s, 2 * tcap, ok);
     int* counts = dalloc<int>(s, 16, ok);
     if (ok) {
@@ -246,7 +240,6 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
         d.act_count = counts + 5;
         d.dl_count = counts + 6;
         d.sl_count = counts + 7;
-        d.tile_count = counts + 8;
     }
     double* dd = dalloc<double>(s, 4, ok);
     if (ok) {

@@ -1,5 +1,5 @@
 // Fused stream + boundary conditions + mass exchange + cumulant collision
-// (Sections 2.1 and 2.2), in place with the AA pattern. One thread per cell.
+// (Sections 2.1 and 2.2), in place with the AA pattern.
 //
 // Even step: each cell reads its own slots (q, x), writes (opp(q), x).
 // Odd step: each cell reads (opp(q), x - c_q), writes (q, x + c_q).
@@ -13,10 +13,10 @@
 //
 // The work per step: the particle links from the solid side (they place the
 // moving bounce-back values in the pull slots and gather the momentum
-// exchange); the liquid cells (even steps: interior rows staged tile by tile
-// through shared memory by bulk copies, plus a row kernel for the faces;
-// odd steps: one lean pull-collide kernel); and the interface cells of the
-// interface list.
+// exchange); the liquid cells (x-adjacent pairs per thread on packed FP32
+// arithmetic; one cell per thread where nx is odd or the lattice needs
+// 64-bit element indices); and the interface cells of the interface list.
+#include "collide_pair.cuh"
 #include "fslbm_dev.cuh"
 
 namespace fsl {
@@ -150,6 +150,128 @@ __global__ void __launch_bounds__(256, liquid_min_blocks<S>()) k_liquid(Dev s) {
     }
 }
 
+// The liquid cells as x-adjacent pairs (x even, x + 1), one pair per
+// thread: the collision runs on packed FP32 pairs, a direction whose source
+// or target keeps the pair's alignment (every direction in an even step,
+// c_x = 0 in an odd one) moves both values with one aligned access, and the
+// others with two accesses from one address. Blocks run over a 256-cell
+// segment of a row; the segment's pairs that hold a liquid cell are
+// compacted onto the first threads. A pair with one liquid cell collides
+// both and stores only the liquid one (the other cell's pull slots are
+// written by no thread of the sweep, so reading them races with nothing).
+// Needs nx even and 32-bit element indices.
+// Resident blocks per SM asked of the compiler, measured per parity: an
+// even step (all accesses aligned pairs) runs fastest without spills (4
+// blocks, up to 128 registers), an odd step with more warps (6 blocks for
+// 16-bit storage, 5 for FP32).
+template <typename S, int PAR>
+constexpr int liquid_pair_min_blocks() { return PAR == 0 ? 4 : (sizeof(S) == 2 ? 6 : 5); }
+
+template <typename S, int PAR>
+__global__ void __launch_bounds__(128, liquid_pair_min_blocks<S, PAR>()) k_liquid_pair(Dev s) {
+    __shared__ int ps[128];      // (x << 2 | liquid bits) of the compacted pairs
+    __shared__ int wn[4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    S* f = static_cast<S*>(s.f);
+    const unsigned un = (unsigned)s.n;
+    const int nrows = s.ny * s.nz;
+    const int sxy = s.nx * s.ny;
+    for (int row = blockIdx.y; row < nrows; row += gridDim.y) {
+        const int x0 = blockIdx.x * 256 + 2 * (int)threadIdx.x;
+        unsigned lm = 0;
+        if (x0 < s.nx) {
+            const uchar2 fl = *reinterpret_cast<const uchar2*>(s.flags + x0 + (long long)s.nx * row);
+            lm = ((fl.x & TYPE_MASK) == T_LIQ ? 1u : 0u) | ((fl.y & TYPE_MASK) == T_LIQ ? 2u : 0u);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, lm != 0);
+        if (lane == 0) wn[warp] = __popc(m);
+        __syncthreads();
+        int off = 0, tot = 0;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            off += w < warp ? wn[w] : 0;
+            tot += wn[w];
+        }
+        if (lm) ps[off + __popc(m & ((1u << lane) - 1u))] = (x0 << 2) | (int)lm;
+        __syncthreads();
+        const int e = (int)threadIdx.x < tot ? ps[threadIdx.x] : -1;
+        __syncthreads();             // ps and wn are rewritten by the next row
+        if (e < 0) continue;
+        const int x = e >> 2;
+        const unsigned liq = (unsigned)e & 3u;
+        const int cell = x + s.nx * row;
+        const int y = row % s.ny, z = row / s.ny;
+        const bool interior =
+            PAR == 0 || (x > 0 && x + 1 < s.nx - 1 && y > 0 && y < s.ny - 1 && z > 0 && z < s.nz - 1);
+        float2 v[27];
+        if (interior) {
+#pragma unroll
+            for (int q = 0; q < 27; ++q) {
+                const unsigned a = PAR == 0 ? (unsigned)q * un + (unsigned)cell
+                                            : (unsigned)opp(q) * un +
+                                                  (unsigned)(cell - (cx(q) + s.nx * cy(q) + sxy * cz(q)));
+                if (PAR == 0 || cx(q) == 0) v[q] = Pair<S>::ld2(f + a);
+                else v[q] = make_float2(Store<S>::ld_raw(f + a), Store<S>::ld_raw(f + a + 1));
+            }
+        } else {
+            const NbrOffsets o0 = nbr_offsets(s, x, y, z), o1 = nbr_offsets(s, x + 1, y, z);
+#pragma unroll
+            for (int q = 0; q < 27; ++q) {
+                // source x - c_q beyond a wall face: the cell's own slot (q, x)
+                const unsigned wb = wall_bits(-cx(q), -cy(q), -cz(q));
+                const int src0 = cell + o0.ox[1 - cx(q)] + o0.oy[1 - cy(q)] + o0.oz[1 - cz(q)];
+                const int src1 = cell + 1 + o1.ox[1 - cx(q)] + o1.oy[1 - cy(q)] + o1.oz[1 - cz(q)];
+                const long long a0 = (o0.wall & wb) ? (long long)q * s.n + cell : (long long)opp(q) * s.n + src0;
+                const long long a1 =
+                    (o1.wall & wb) ? (long long)q * s.n + cell + 1 : (long long)opp(q) * s.n + src1;
+                v[q] = make_float2((liq & 1u) ? Store<S>::ld_raw(f + a0) : 0.f,
+                                   (liq & 2u) ? Store<S>::ld_raw(f + a1) : 0.f);
+            }
+        }
+        collide_pair<Pair<S>::SCALE_LOG2>(v, s.omega, s.gx, s.gy, s.gz);
+        if (interior && liq == 3u) {
+#pragma unroll
+            for (int q = 0; q < 27; ++q) {
+                const unsigned a = PAR == 0 ? (unsigned)opp(q) * un + (unsigned)cell
+                                            : (unsigned)q * un +
+                                                  (unsigned)(cell + cx(q) + s.nx * cy(q) + sxy * cz(q));
+                if (PAR == 0 || cx(q) == 0) {
+                    Pair<S>::st2(f + a, v[q]);
+                } else {
+                    Store<S>::st_raw(f + a, v[q].x);
+                    Store<S>::st_raw(f + a + 1, v[q].y);
+                }
+            }
+        } else if (interior) {
+            // one liquid cell: liq is 1 (x) or 2 (x + 1)
+            const unsigned k = liq >> 1;
+#pragma unroll
+            for (int q = 0; q < 27; ++q) {
+                const unsigned a = PAR == 0 ? (unsigned)opp(q) * un + (unsigned)cell
+                                            : (unsigned)q * un +
+                                                  (unsigned)(cell + cx(q) + s.nx * cy(q) + sxy * cz(q));
+                Store<S>::st_raw(f + a + k, k ? v[q].y : v[q].x);
+            }
+        } else {
+            const NbrOffsets o0 = nbr_offsets(s, x, y, z), o1 = nbr_offsets(s, x + 1, y, z);
+#pragma unroll
+            for (int q = 0; q < 27; ++q) {
+                // target x + c_q beyond a wall face: the cell's own slot (opp(q), x)
+                const unsigned wb = wall_bits(cx(q), cy(q), cz(q));
+                const int dst0 = cell + o0.ox[1 + cx(q)] + o0.oy[1 + cy(q)] + o0.oz[1 + cz(q)];
+                const int dst1 = cell + 1 + o1.ox[1 + cx(q)] + o1.oy[1 + cy(q)] + o1.oz[1 + cz(q)];
+                if (liq & 1u)
+                    Store<S>::st_raw(
+                        f + ((o0.wall & wb) ? (long long)opp(q) * s.n + cell : (long long)q * s.n + dst0), v[q].x);
+                if (liq & 2u)
+                    Store<S>::st_raw(
+                        f + ((o1.wall & wb) ? (long long)opp(q) * s.n + cell + 1 : (long long)q * s.n + dst1),
+                        v[q].y);
+            }
+        }
+    }
+}
+
 // Warp segmented reduction of per-lane (key, F, T) for runs of equal keys,
 // then one FP64 atomic per run and component.
 __device__ __forceinline__ void flush_mem(const Dev& s, int key, const float (&F)[3], const float (&T)[3]) {
@@ -207,240 +329,6 @@ __device__ __forceinline__ PData particle_data(const Dev& s, int p) {
     d.u = s.Uf[p];
     d.w = s.Wf[p];
     return d;
-}
-
-// ---------------------------------------------------------------- staged sweep
-// Even steps, liquid cells of interior rows, tile by tile: a persistent CTA
-// of TILE threads streams the 27 direction slices [c0, c0 + TILE) of each
-// x-tile into shared memory with bulk asynchronous copies (cp.async.bulk,
-// completion counted on an mbarrier), several tiles ahead, while its threads
-// collide the tile in hand. Every copy starts and ends on a 16-byte boundary
-// (nx is a multiple of TILE). The cells at x = 0 and x = nx-1 belong to the
-// row kernel. Odd steps run k_liquid: their slices are shifted by one
-// element along x, and staging them measured slower than direct loads.
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-    return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// bounded wait: false (and the sticky timeout bit) if the phase never completes
-__device__ __forceinline__ bool mbar_wait(const Dev& s, uint64_t* bar, unsigned parity) {
-    for (int it = 0; it < (1 << 22); ++it)
-        if (mbar_try_wait(bar, parity)) return true;
-    set_error(s, ERR_TIMEOUT);
-    return false;
-}
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
-template <typename S>
-struct StagedLayout {
-    // tiles in flight per CTA: with 16-bit elements two stages leave room for
-    // more CTAs per SM, which measured faster; 32-bit elements keep three
-    static constexpr int STAGES = sizeof(S) == 2 ? 2 : 3;
-    static constexpr int ROW = TILE;                            // elements per direction slice
-    static constexpr int PDF_BYTES = 27 * ROW * (int)sizeof(S);
-    static constexpr int STAGE_BYTES = PDF_BYTES + TILE;        // + the tile's flag bytes
-};
-
-template <typename S>
-__device__ __forceinline__ void staged_issue(const Dev& s, S* buf, uint64_t* full, int tile) {
-    using L = StagedLayout<S>;
-    const S* f = static_cast<const S*>(s.f);
-    const long long n = s.n;
-    const long long c0 = (long long)tile * TILE;
-    unsigned char* fl = reinterpret_cast<unsigned char*>(buf) + L::PDF_BYTES;
-    mbar_expect_tx(full, 27u * TILE * sizeof(S) + TILE);
-    bulk_load(fl, s.flags + c0, TILE, full);
-#pragma unroll 1
-    for (int q = 0; q < 27; ++q) bulk_load(buf + q * L::ROW, f + (long long)q * n + c0, TILE * sizeof(S), full);
-}
-
-template <typename S>
-__global__ void __launch_bounds__(TILE) k_liquid_staged(Dev s) {
-    using L = StagedLayout<S>;
-    constexpr int STAGES = L::STAGES;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    S* bufs = reinterpret_cast<S*>(smem_raw);
-    __shared__ __align__(8) uint64_t full[STAGES];
-    __shared__ __align__(8) uint64_t empty[STAGES];
-    __shared__ int stage_tile[STAGES];
-    __shared__ int stage_edge[STAGES];   // bit 0: tile starts at x = 0; bit 1: ends at x = nx - 1
-    __shared__ int pos[TILE];            // tile positions of the liquid cells, compacted
-    __shared__ int wn[TILE / 32];
-    const int ntiles = *s.tile_count;
-    const int mine = ntiles > (int)blockIdx.x ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
-    if (mine == 0) return;
-    const int tid = threadIdx.x;
-    const int nwarps = TILE / 32;
-    constexpr int SE = L::STAGE_BYTES / (int)sizeof(S);   // stage stride in elements
-    auto issue = [&](int k, int i) {
-        const int t = s.tiles[(int)blockIdx.x + i * (int)gridDim.x];
-        stage_tile[k] = t;
-        const int x0 = (int)(((long long)t * TILE) % s.nx);
-        stage_edge[k] = (x0 == 0 ? 1 : 0) | (x0 + TILE == s.nx ? 2 : 0);
-        staged_issue<S>(s, bufs + k * SE, &full[k], t);
-    };
-    if (tid == 0) {
-        for (int k = 0; k < STAGES; ++k) {
-            mbar_init(&full[k], 1);
-            mbar_init(&empty[k], nwarps);
-        }
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    // prologue: the first STAGES tiles of this CTA
-    if (tid == 0)
-        for (int k = 0; k < STAGES && k < mine; ++k) issue(k, k);
-    S* f = static_cast<S*>(s.f);
-    const long long n = s.n;
-    // thread 0: the last tile index issued into each stage (-1: none), and
-    // whether a refill gave up waiting for its stage to be released
-    int last_issued[STAGES];
-    bool refill_failed = false;
-    for (int k = 0; k < STAGES; ++k) last_issued[k] = k < mine ? k : -1;
-    for (int i = 0; i < mine; ++i) {
-        const int st = i % STAGES;
-        const unsigned ph = (unsigned)(i / STAGES) & 1u;
-        const bool ok = mbar_wait(s, &full[st], ph);
-        const S* buf = bufs + st * SE;
-        const unsigned char* fl = reinterpret_cast<const unsigned char*>(buf) + L::PDF_BYTES;
-        const int edge = ok ? stage_edge[st] : 0;
-        const bool x_edge = (tid == 0 && (edge & 1)) || (tid == TILE - 1 && (edge & 2));
-        // compaction: thread t collides the t-th liquid cell of the tile, so
-        // only the last busy warp has idle lanes
-        const bool liq = ok && !x_edge && (fl[tid] & TYPE_MASK) == T_LIQ;
-        const int lane = tid & 31, warp = tid >> 5;
-        const unsigned m = __ballot_sync(0xffffffffu, liq);
-        if (lane == 0) wn[warp] = __popc(m);
-        // a bounded wait that gave up ends the loop for every thread at once
-        if (__syncthreads_or(!ok || refill_failed)) break;
-        int off = 0, tot = 0;
-#pragma unroll
-        for (int w = 0; w < TILE / 32; ++w) {
-            off += w < warp ? wn[w] : 0;
-            tot += wn[w];
-        }
-        if (liq) pos[off + __popc(m & ((1u << lane) - 1u))] = tid;
-        __syncthreads();
-        const int p = tid < tot ? pos[tid] : -1;
-        const int cell = stage_tile[st] * TILE + p;
-        __syncthreads();             // pos and wn are rewritten by the next tile
-        if (p >= 0) {
-            // stored values (times the storage scale) in and out; the
-            // collision folds the scale into its moments
-            float v[27];
-#pragma unroll
-            for (int q = 0; q < 27; ++q) v[q] = Store<S>::ld_raw(buf + q * L::ROW + p);
-            float rho, ux, uy, uz;
-            collide_scaled(v, Store<S>::scale, s.omega, s.gx, s.gy, s.gz, rho, ux, uy, uz);
-            if (s.idx32) {
-                // element indices in 32 bits: one wide multiply-add per address
-                const unsigned un = (unsigned)n;
-#pragma unroll
-                for (int q = 0; q < 27; ++q) Store<S>::st_raw(f + ((unsigned)opp(q) * un + (unsigned)cell), v[q]);
-            } else {
-#pragma unroll
-                for (int q = 0; q < 27; ++q) Store<S>::st_raw(f + (long long)opp(q) * n + cell, v[q]);
-            }
-        }
-        // release the stage, then refill it with the tile STAGES ahead
-        __syncwarp();
-        if ((tid & 31) == 0) mbar_arrive(&empty[st]);
-        if (tid == 0 && i + STAGES < mine) {
-            if (!mbar_wait(s, &empty[st], ph)) {
-                refill_failed = true;
-            } else {
-                issue(st, i + STAGES);
-                last_issued[st] = i + STAGES;
-            }
-        }
-    }
-    // copies still in flight complete before the CTA leaves
-    if (tid == 0)
-        for (int k = 0; k < STAGES; ++k)
-            if (last_issued[k] >= 0) mbar_wait(s, &full[k], (unsigned)(last_issued[k] / STAGES) & 1u);
-}
-
-// Per-thread pull-collide for the liquid cells of the rows on the y and z
-// faces and for the cells at x = 0 and x = nx-1 of the other rows (the
-// staged kernel covers the rest). Row r < 2 nz: y = 0 or ny-1; then
-// y = 1..ny-2 with z = 0 or nz-1; then the two end cells of each interior row.
-template <typename S, int PAR>
-__global__ void __launch_bounds__(256, 3) k_liquid_rows(Dev s) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long nrow = 2LL * s.nz + 2LL * (s.ny > 2 ? s.ny - 2 : 0);
-    const long long nedge = 2LL * (s.ny - 2) * (s.nz - 2);
-    int x, y, z;
-    if (t < nrow * s.nx) {
-        const int r = (int)(t / s.nx);
-        x = (int)(t % s.nx);
-        if (r < 2 * s.nz) { z = r >> 1; y = (r & 1) ? s.ny - 1 : 0; }
-        else { const int k = r - 2 * s.nz; y = 1 + (k >> 1); z = (k & 1) ? s.nz - 1 : 0; }
-    } else if (t < nrow * s.nx + nedge) {
-        // x = 0 and x = nx-1 of the interior rows
-        const long long k = t - nrow * s.nx;
-        x = (k & 1) ? s.nx - 1 : 0;
-        const long long r = k >> 1;
-        y = 1 + (int)(r % (s.ny - 2));
-        z = 1 + (int)(r / (s.ny - 2));
-    } else {
-        return;
-    }
-    const int cell = x + s.nx * (y + s.ny * z);
-    if ((s.flags[cell] & TYPE_MASK) != T_LIQ) return;
-    S* f = static_cast<S*>(s.f);
-    const long long n = s.n;
-    float v[27];
-    const NbrOffsets o = nbr_offsets(s, x, y, z);
-#pragma unroll
-    for (int q = 0; q < 27; ++q) {
-        long long a;
-        if (PAR == 0) {
-            a = (long long)q * n + cell;
-        } else {
-            const int src = cell + o.ox[1 - cx(q)] + o.oy[1 - cy(q)] + o.oz[1 - cz(q)];
-            a = (o.wall & wall_bits(-cx(q), -cy(q), -cz(q))) ? (long long)q * n + cell : (long long)opp(q) * n + src;
-        }
-        v[q] = Store<S>::ld(f + a);
-    }
-    float rho, ux, uy, uz;
-    collide(v, s.omega, s.gx, s.gy, s.gz, rho, ux, uy, uz);
-#pragma unroll
-    for (int q = 0; q < 27; ++q) {
-        long long a;
-        if (PAR == 0) {
-            a = (long long)opp(q) * n + cell;
-        } else {
-            const int dst = cell + o.ox[1 + cx(q)] + o.oy[1 + cy(q)] + o.oz[1 + cz(q)];
-            a = (o.wall & wall_bits(cx(q), cy(q), cz(q))) ? (long long)opp(q) * n + cell : (long long)q * n + dst;
-        }
-        Store<S>::st(f + a, v[q]);
-    }
 }
 
 // Moving bounce-back and momentum exchange (Section 2.2), from the solid
@@ -655,46 +543,22 @@ __global__ void __launch_bounds__(128) k_interface(Dev s) {
     }
 }
 
-// CTAs of the staged sweep: as many as fit on the SMs at once (shared
-// memory is the limit), set up once per storage format
-template <typename S>
-static int staged_blocks() {
-    static int blocks = 0;
-    if (blocks == 0) {
-        const int smem = StagedLayout<S>::STAGES * StagedLayout<S>::STAGE_BYTES;
-        cudaFuncSetAttribute(k_liquid_staged<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_liquid_staged<S>, TILE, smem);
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        blocks = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
-    }
-    return blocks;
-}
-
-static bool use_staged(const Dev& s) { return (s.nx % TILE) == 0 && s.ny >= 3 && s.nz >= 3; }
+static bool use_pairs(const Dev& s) { return s.idx32 && (s.nx % 2) == 0; }
 
 template <typename S>
 static void launch_typed(const Dev& s, int parity, cudaStream_t st) {
     const int lb = 152 * 8;
-    // k_liquid: threads along x, blocks over the rows (y, z)
+    // liquid kernels: threads along x, blocks over the rows (y, z)
     const dim3 lgrid((unsigned)((s.nx + 255) / 256), (unsigned)(s.ny * s.nz < 65535 ? s.ny * s.nz : 65535));
     if (parity == 0) {
         if (s.np > 0) k_solid_links<S, 0><<<lb, 256, 0, st>>>(s);
-        if (use_staged(s)) {
-            const long long nrow = 2LL * s.nz + 2LL * (s.ny - 2);
-            const int rb = (int)((nrow * s.nx + 2LL * (s.ny - 2) * (s.nz - 2) + 255) / 256);
-            const size_t smem = (size_t)StagedLayout<S>::STAGES * StagedLayout<S>::STAGE_BYTES;
-            k_liquid_staged<S><<<staged_blocks<S>(), TILE, smem, st>>>(s);
-            k_liquid_rows<S, 0><<<rb, 256, 0, st>>>(s);
-        } else {
-            k_liquid<S, 0><<<lgrid, 256, 0, st>>>(s);
-        }
+        if (use_pairs(s)) k_liquid_pair<S, 0><<<lgrid, 128, 0, st>>>(s);
+        else k_liquid<S, 0><<<lgrid, 256, 0, st>>>(s);
         k_interface<S, 0><<<lb, 128, 0, st>>>(s);
     } else {
         if (s.np > 0) k_solid_links<S, 1><<<lb, 256, 0, st>>>(s);
-        k_liquid<S, 1><<<lgrid, 256, 0, st>>>(s);
+        if (use_pairs(s)) k_liquid_pair<S, 1><<<lgrid, 128, 0, st>>>(s);
+        else k_liquid<S, 1><<<lgrid, 256, 0, st>>>(s);
         k_interface<S, 1><<<lb, 128, 0, st>>>(s);
     }
 }
@@ -703,7 +567,8 @@ int launch_stream_collide(const Dev& s, int parity, cudaStream_t st) {
     if (s.storage == FSLBM_STORE_FP32) launch_typed<float>(s, parity, st);
     else if (s.storage == FSLBM_STORE_FP16) launch_typed<__half>(s, parity, st);
     else launch_typed<__nv_bfloat16>(s, parity, st);
-    return (s.np > 0 ? 1 : 0) + (parity == 0 && use_staged(s) ? 3 : 2);
+    (void)parity;
+    return (s.np > 0 ? 1 : 0) + 2;
 }
 
 }  // namespace fsl

@@ -601,36 +601,6 @@ __global__ void k_clamp_count(Dev s) {
     if (*s.sl_count > s.sl_cap) *s.sl_count = s.sl_cap;
 }
 
-// x-tiles of TILE cells in rows away from the y and z faces that hold at
-// least one liquid cell (these go through the staged stream-collide)
-__global__ void k_tiles(Dev s) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long ntile = s.n / TILE;
-    bool act = false;
-    if (t < ntile) {
-        const long long c0 = t * TILE;
-        int x0, y, z;
-        coords(s, c0, x0, y, z);
-        if (y > 0 && y < s.ny - 1 && z > 0 && z < s.nz - 1) {
-            const uint4* w = reinterpret_cast<const uint4*>(s.flags + c0);
-            unsigned any = 0;
-#pragma unroll
-            for (int k = 0; k < TILE / 16; ++k) {
-                const uint4 v = w[k];
-                const unsigned wd[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    // a byte holds a liquid cell when its type bits are 01
-                    const unsigned lo = wd[j] & 0x03030303u;
-                    any |= (lo ^ 0x01010101u) - 0x01010101u & ~(lo ^ 0x01010101u) & 0x80808080u;
-                }
-            }
-            act = any != 0;
-        }
-    }
-    block_append(s, act, (int)t, s.tiles, s.tile_count, (int)(s.n / TILE));
-}
-
 int launch_classify(const Dev& s, cudaStream_t st) {
     cudaMemsetAsync(s.wl_count, 0, sizeof(int), st);
     cudaMemsetAsync(s.sl_count, 0, sizeof(int), st);
@@ -643,11 +613,6 @@ int launch_classify(const Dev& s, cudaStream_t st) {
         k_classify<<<blocks_for(s.n, 256), 256, 0, st>>>(s);
     }
     k_clamp_count<<<1, 1, 0, st>>>(s);
-    if (s.nx % TILE == 0) {
-        cudaMemsetAsync(s.tile_count, 0, sizeof(int), st);
-        k_tiles<<<blocks_for(s.n / TILE, 256), 256, 0, st>>>(s);
-        ++k;
-    }
     return k;
 }
 
