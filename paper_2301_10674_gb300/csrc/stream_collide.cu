@@ -545,18 +545,33 @@ __global__ void __launch_bounds__(128) k_interface(Dev s) {
 
 static bool use_pairs(const Dev& s) { return s.idx32 && (s.nx % 2) == 0; }
 
+// blocks of the link pass: one resident wave (the kernel strides over the
+// list), found once per storage format and parity
+template <typename S, int PAR>
+static int link_blocks() {
+    static int blocks = 0;
+    if (blocks == 0) {
+        int per_sm = 0, dev = 0, sms = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solid_links<S, PAR>, 256, 0);
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        blocks = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+    }
+    return blocks;
+}
+
 template <typename S>
 static void launch_typed(const Dev& s, int parity, cudaStream_t st) {
     const int lb = 152 * 8;
     // liquid kernels: threads along x, blocks over the rows (y, z)
     const dim3 lgrid((unsigned)((s.nx + 255) / 256), (unsigned)(s.ny * s.nz < 65535 ? s.ny * s.nz : 65535));
     if (parity == 0) {
-        if (s.np > 0) k_solid_links<S, 0><<<lb, 256, 0, st>>>(s);
+        if (s.np > 0) k_solid_links<S, 0><<<link_blocks<S, 0>(), 256, 0, st>>>(s);
         if (use_pairs(s)) k_liquid_pair<S, 0><<<lgrid, 128, 0, st>>>(s);
         else k_liquid<S, 0><<<lgrid, 256, 0, st>>>(s);
         k_interface<S, 0><<<lb, 128, 0, st>>>(s);
     } else {
-        if (s.np > 0) k_solid_links<S, 1><<<lb, 256, 0, st>>>(s);
+        if (s.np > 0) k_solid_links<S, 1><<<link_blocks<S, 1>(), 256, 0, st>>>(s);
         if (use_pairs(s)) k_liquid_pair<S, 1><<<lgrid, 128, 0, st>>>(s);
         else k_liquid<S, 1><<<lgrid, 256, 0, st>>>(s);
         k_interface<S, 1><<<lb, 128, 0, st>>>(s);
