@@ -162,9 +162,10 @@ LAM, MU = 0.4, 0.1
 # even and odd steps averaged, from one ncu capture on the 1024x64x128 flume.
 # It is valid while the sweep's sources hash to `sources`, and is scaled to a
 # run by its fluid cells.
-SWEEP_TRAFFIC = {"sources": "b17cf9cac7074204", "workload": "precision-1024x64x128",
-                 "per_fluid_cell": {"fp16": 193.0, "fp32": 379.9, "bf16": None}}
-SWEEP_SOURCES = ("paper_2301_10674_gb300/csrc/stream_collide.cu", "paper_2301_10674_gb300/csrc/fslbm_dev.cuh")
+SWEEP_TRAFFIC = {"sources": "65656f288440a34f", "workload": "precision-1024x64x128",
+                 "per_fluid_cell": {"fp16": 192.2, "fp32": 382.0, "bf16": None}}
+SWEEP_SOURCES = ("paper_2301_10674_gb300/csrc/stream_collide.cu", "paper_2301_10674_gb300/csrc/fslbm_dev.cuh",
+                 "paper_2301_10674_gb300/csrc/collide_pair.cuh")
 
 
 def _sweep_traffic(storage_name: str, fluid: float):
@@ -268,7 +269,7 @@ def _roofline(run, storage_name, ncell):
     traffic, traffic_note = _sweep_traffic(storage_name, fluid)
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic, "traffic_note": traffic_note,
-            "kernel": "stream-collide sweep (staged bulk + face rows + particle links + interface list)",
+            "kernel": "stream-collide sweep (particle links + liquid cell pairs + interface list)",
             "bytes_per_cell": {"fluid": 54 * elem + 1, "gas_or_solid": 1},
             "bytes_per_launch": int(bytes_per_sweep), "launch_ms": round(sweep_s * 1e3, 4),
             "peak_kind": peak_kind}
