@@ -229,6 +229,7 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     d.fbits = dalloc<unsigned>(s, n / 32 + 1, ok);
     d.ibits = dalloc<unsigned>(s, n / 32 + 1, ok);
     d.sbits = dalloc<unsigned>(s, n / 32 + 1, ok);
+    d.tiles = dalloc<int>(s, n / fsl::SP_TILE + 1, ok);
     d.tl_info = dalloc<int>(s, 2 * tcap, ok);
     int* counts = dalloc<int>(s, 16, ok);
     if (ok) {
@@ -240,6 +241,7 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
         d.act_count = counts + 5;
         d.dl_count = counts + 6;
         d.sl_count = counts + 7;
+        d.tile_count = counts + 8;
     }
     double* dd = dalloc<double>(s, 4, ok);
     if (ok) {

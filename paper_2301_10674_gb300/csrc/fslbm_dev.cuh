@@ -44,6 +44,8 @@ enum : uint8_t { CV_TO_LIQ = 1, CV_TO_GAS = 2, CV_EVEN = 4 };
 // error bits of the sticky device word (mapped to FSLBM_E* on the host)
 enum : int { ERR_CAPACITY = 1, ERR_NAN = 2, ERR_INVARIANT = 4, ERR_HISTORY = 8, ERR_DISPLACEMENT = 16, ERR_TIMEOUT = 32 };
 
+constexpr int SP_TILE = 256;     // cells per x-tile of the staged even step
+
 constexpr int HIST_SLOTS = 16;   // tangential-spring history slots per particle
 constexpr int NB_SLOTS = 32;     // DEM neighbour-list slots per particle
 
@@ -82,6 +84,7 @@ struct Dev {
     int* nl; int* nl_count; int nl_cap;        // cells becoming interface this step
     int* tl; int* tl_count; int tl_cap;        // particle map transitions
     int* sl; int* sl_count; int sl_cap;        // solid cells with a fluid neighbour
+    int* tiles; int* tile_count;               // SP_TILE-cell x-tiles holding a liquid cell
     unsigned* fbits; unsigned* ibits; unsigned* sbits;   // per 32 cells of a row: fluid / interface / solid bits
     int* tl_info;                               // per transition: new owner / new type
     double* pool;

@@ -272,6 +272,208 @@ __global__ void __launch_bounds__(128, liquid_pair_min_blocks<S, PAR>()) k_liqui
     }
 }
 
+// ---------------------------------------------------------------- staged even step
+// Even steps at 16-bit storage, tile by tile: a persistent CTA of SP_TILE/2
+// threads streams the 27 direction slices [c0, c0 + SP_TILE) of each
+// SP_TILE-cell x-tile that holds a liquid cell (and its flag bytes) into
+// shared memory with bulk asynchronous copies (cp.async.bulk, completion
+// counted on an mbarrier), STAGES tiles ahead, while its threads collide the
+// tile in hand as x-adjacent pairs and write the results back with aligned
+// pair stores. An even step reads and writes only a cell's own slots, so
+// cells on the faces of the lattice need nothing else. Every copy starts and
+// ends on a 16-byte boundary (nx is a multiple of SP_TILE). Every wait is
+// bounded: one that gives up sets the timeout bit, the block leaves its loop
+// on a block-wide vote, and the copies in flight are waited for before the
+// block exits.
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait: false (and the sticky timeout bit) if the phase never completes
+__device__ __forceinline__ bool mbar_wait(const Dev& s, uint64_t* bar, unsigned parity) {
+    for (int it = 0; it < (1 << 22); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    set_error(s, ERR_TIMEOUT);
+    return false;
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// the x-tiles of SP_TILE cells that hold at least one liquid cell, in the
+// order of their first cell within each block
+__global__ void k_sp_tiles(Dev s) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long ntile = s.n / SP_TILE;
+    bool act = false;
+    if (t < ntile) {
+        const uint4* w = reinterpret_cast<const uint4*>(s.flags + t * SP_TILE);
+        unsigned any = 0;
+#pragma unroll 4
+        for (int k = 0; k < SP_TILE / 16; ++k) {
+            const uint4 v = w[k];
+            const unsigned wd[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                // a byte holds a liquid cell when its type bits are 01
+                const unsigned lo = (wd[j] & 0x03030303u) ^ 0x01010101u;
+                any |= (lo - 0x01010101u) & ~lo & 0x80808080u;
+            }
+        }
+        act = any != 0;
+    }
+    block_append(s, act, (int)t, s.tiles, s.tile_count, (int)ntile);
+}
+
+template <typename S>
+struct StagedPairLayout {
+    static constexpr int STAGES = 2;
+    static constexpr int ROW = SP_TILE;                          // elements per direction slice
+    static constexpr int PDF_BYTES = 27 * ROW * (int)sizeof(S);
+    static constexpr int STAGE_BYTES = PDF_BYTES + SP_TILE;      // + the tile's flag bytes
+    static constexpr int SMEM = STAGES * STAGE_BYTES;
+};
+
+template <typename S>
+__device__ __forceinline__ void staged_pair_issue(const Dev& s, unsigned char* stage, uint64_t* full, int tile) {
+    using L = StagedPairLayout<S>;
+    const S* f = static_cast<const S*>(s.f);
+    const long long n = s.n;
+    const long long c0 = (long long)tile * SP_TILE;
+    S* buf = reinterpret_cast<S*>(stage);
+    mbar_expect_tx(full, (unsigned)L::STAGE_BYTES);
+    bulk_load(stage + L::PDF_BYTES, s.flags + c0, SP_TILE, full);
+#pragma unroll 1
+    for (int q = 0; q < 27; ++q)
+        bulk_load(buf + q * L::ROW, f + (long long)q * n + c0, SP_TILE * (unsigned)sizeof(S), full);
+}
+
+template <typename S>
+__global__ void __launch_bounds__(SP_TILE / 2, 6) k_liquid_staged_pair(Dev s) {
+    using L = StagedPairLayout<S>;
+    constexpr int STAGES = L::STAGES;
+    constexpr int NT = SP_TILE / 2;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[STAGES];
+    __shared__ __align__(8) uint64_t empty[STAGES];
+    __shared__ int stage_tile[STAGES];
+    __shared__ int pos[NT];              // (pair << 2 | liquid bits) of the compacted pairs
+    __shared__ int wn[NT / 32];
+    const int ntiles = *s.tile_count;
+    const int mine = ntiles > (int)blockIdx.x ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+    if (mine == 0) return;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    auto issue = [&](int k, int i) {
+        const int t = s.tiles[(int)blockIdx.x + i * (int)gridDim.x];
+        stage_tile[k] = t;
+        staged_pair_issue<S>(s, smem_raw + k * L::STAGE_BYTES, &full[k], t);
+    };
+    if (tid == 0) {
+        for (int k = 0; k < STAGES; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], NT / 32);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int k = 0; k < STAGES && k < mine; ++k) issue(k, k);
+    S* f = static_cast<S*>(s.f);
+    const unsigned un = (unsigned)s.n;
+    // thread 0: the last tile index issued into each stage (-1: none), and
+    // whether a refill gave up waiting for its stage to be released
+    int last_issued[STAGES];
+    bool refill_failed = false;
+    for (int k = 0; k < STAGES; ++k) last_issued[k] = k < mine ? k : -1;
+    for (int i = 0; i < mine; ++i) {
+        const int st = i % STAGES;
+        const unsigned ph = (unsigned)(i / STAGES) & 1u;
+        const bool ok = mbar_wait(s, &full[st], ph);
+        const unsigned char* stage = smem_raw + st * L::STAGE_BYTES;
+        const S* buf = reinterpret_cast<const S*>(stage);
+        const unsigned char* fl = stage + L::PDF_BYTES;
+        // compaction: thread t collides the t-th pair of the tile that holds
+        // a liquid cell
+        unsigned lm = 0;
+        if (ok) {
+            const uchar2 b = *reinterpret_cast<const uchar2*>(fl + 2 * tid);
+            lm = ((b.x & TYPE_MASK) == T_LIQ ? 1u : 0u) | ((b.y & TYPE_MASK) == T_LIQ ? 2u : 0u);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, lm != 0);
+        if (lane == 0) wn[warp] = __popc(m);
+        // a bounded wait that gave up ends the loop for every thread at once
+        if (__syncthreads_or(!ok || refill_failed)) break;
+        int off = 0, tot = 0;
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) {
+            off += w < warp ? wn[w] : 0;
+            tot += wn[w];
+        }
+        if (lm) pos[off + __popc(m & ((1u << lane) - 1u))] = (tid << 2) | (int)lm;
+        __syncthreads();
+        const int e = tid < tot ? pos[tid] : -1;
+        const int cell = stage_tile[st] * SP_TILE + 2 * (e >> 2);
+        __syncthreads();             // pos and wn are rewritten by the next tile
+        if (e >= 0) {
+            const int p = 2 * (e >> 2);
+            const unsigned liq = (unsigned)e & 3u;
+            float2 v[27];
+#pragma unroll
+            for (int q = 0; q < 27; ++q) v[q] = Pair<S>::ld2(buf + q * L::ROW + p);
+            collide_pair<Pair<S>::SCALE_LOG2>(v, s.omega, s.gx, s.gy, s.gz);
+            if (liq == 3u) {
+#pragma unroll
+                for (int q = 0; q < 27; ++q) Pair<S>::st2(f + ((unsigned)opp(q) * un + (unsigned)cell), v[q]);
+            } else {
+                const unsigned k = liq >> 1;
+#pragma unroll
+                for (int q = 0; q < 27; ++q)
+                    Store<S>::st_raw(f + ((unsigned)opp(q) * un + (unsigned)cell + k), k ? v[q].y : v[q].x);
+            }
+        }
+        // release the stage, then refill it with the tile STAGES ahead
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[st]);
+        if (tid == 0 && i + STAGES < mine) {
+            if (!mbar_wait(s, &empty[st], ph)) {
+                refill_failed = true;
+            } else {
+                issue(st, i + STAGES);
+                last_issued[st] = i + STAGES;
+            }
+        }
+    }
+    // copies still in flight complete before the CTA leaves
+    if (tid == 0)
+        for (int k = 0; k < STAGES; ++k)
+            if (last_issued[k] >= 0) mbar_wait(s, &full[k], (unsigned)(last_issued[k] / STAGES) & 1u);
+}
+
 // Warp segmented reduction of per-lane (key, F, T) for runs of equal keys,
 // then one FP64 atomic per run and component.
 __device__ __forceinline__ void flush_mem(const Dev& s, int key, const float (&F)[3], const float (&T)[3]) {
@@ -544,6 +746,27 @@ __global__ void __launch_bounds__(128) k_interface(Dev s) {
 }
 
 static bool use_pairs(const Dev& s) { return s.idx32 && (s.nx % 2) == 0; }
+// the staged even step: 16-bit storage, nx a multiple of the tile
+static bool use_staged_pairs(const Dev& s) {
+    return s.idx32 && s.storage != FSLBM_STORE_FP32 && (s.nx % SP_TILE) == 0;
+}
+
+// CTAs of the staged even step: as many as fit on the SMs at once, found
+// once per storage format
+template <typename S>
+static int staged_pair_blocks() {
+    static int blocks = 0;
+    if (blocks == 0) {
+        const int smem = StagedPairLayout<S>::SMEM;
+        cudaFuncSetAttribute(k_liquid_staged_pair<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        int per_sm = 0, dev = 0, sms = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_liquid_staged_pair<S>, SP_TILE / 2, smem);
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        blocks = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+    }
+    return blocks;
+}
 
 // blocks of the link pass: one resident wave (the kernel strides over the
 // list), found once per storage format and parity
@@ -567,8 +790,17 @@ static void launch_typed(const Dev& s, int parity, cudaStream_t st) {
     const dim3 lgrid((unsigned)((s.nx + 255) / 256), (unsigned)(s.ny * s.nz < 65535 ? s.ny * s.nz : 65535));
     if (parity == 0) {
         if (s.np > 0) k_solid_links<S, 0><<<link_blocks<S, 0>(), 256, 0, st>>>(s);
-        if (use_pairs(s)) k_liquid_pair<S, 0><<<lgrid, 128, 0, st>>>(s);
-        else k_liquid<S, 0><<<lgrid, 256, 0, st>>>(s);
+        if (use_staged_pairs(s)) {
+            if constexpr (sizeof(S) == 2) {
+                cudaMemsetAsync(s.tile_count, 0, sizeof(int), st);
+                k_sp_tiles<<<(unsigned)((s.n / SP_TILE + 255) / 256), 256, 0, st>>>(s);
+                k_liquid_staged_pair<S><<<staged_pair_blocks<S>(), SP_TILE / 2, StagedPairLayout<S>::SMEM, st>>>(s);
+            }
+        } else if (use_pairs(s)) {
+            k_liquid_pair<S, 0><<<lgrid, 128, 0, st>>>(s);
+        } else {
+            k_liquid<S, 0><<<lgrid, 256, 0, st>>>(s);
+        }
         k_interface<S, 0><<<lb, 128, 0, st>>>(s);
     } else {
         if (s.np > 0) k_solid_links<S, 1><<<link_blocks<S, 1>(), 256, 0, st>>>(s);
@@ -582,8 +814,8 @@ int launch_stream_collide(const Dev& s, int parity, cudaStream_t st) {
     if (s.storage == FSLBM_STORE_FP32) launch_typed<float>(s, parity, st);
     else if (s.storage == FSLBM_STORE_FP16) launch_typed<__half>(s, parity, st);
     else launch_typed<__nv_bfloat16>(s, parity, st);
-    (void)parity;
-    return (s.np > 0 ? 1 : 0) + 2;
+    const bool staged = parity == 0 && use_staged_pairs(s);
+    return (s.np > 0 ? 1 : 0) + 2 + (staged ? 1 : 0);
 }
 
 }  // namespace fsl

@@ -246,13 +246,16 @@ def test_non_finite_state_is_reported():
 
 
 def _staged_workload():
-    """x extent 128 (a multiple of the 128-cell tile): the staged sweep runs
-    the interior rows, the row kernel the rows on the y and z faces."""
-    w = W.Workload(name="staged", nx=128, ny=10, nz=20, tau=0.55, g=(5e-6, 0.0, -5e-5), liquid_height=14.0,
+    """x extent 256 (a multiple of the 256-cell tile): with 16-bit storage the
+    even steps run the staged pair kernel on every tile that holds liquid,
+    face rows and x-edges included; the odd steps and FP32 run the pair
+    kernel. Spheres sit on the periodic x seam and across tile borders."""
+    w = W.Workload(name="staged", nx=256, ny=10, nz=20, tau=0.55, g=(5e-6, 0.0, -5e-5), liquid_height=14.0,
                    diameter=5.0, bed="none", seed=11).generate()
-    w.xyz = np.array([[20.3, 5.1, 4.2], [60.7, 4.4, 6.1], [100.2, 5.5, 3.1], [127.5, 5.0, 5.0]])
-    w.radius = np.array([2.6, 2.2, 2.9, 2.4])
-    w.fixed = np.array([0, 0, 1, 0], np.uint8)
+    w.xyz = np.array([[20.3, 5.1, 4.2], [60.7, 4.4, 6.1], [128.2, 5.5, 3.1], [255.5, 5.0, 5.0],
+                      [190.4, 4.6, 12.8]])
+    w.radius = np.array([2.6, 2.2, 2.9, 2.4, 2.5])
+    w.fixed = np.array([0, 0, 1, 0, 0], np.uint8)
     return w
 
 
@@ -271,17 +274,22 @@ def test_staged_sweep_matches_oracle():
     sim.close()
 
 
-def test_staged_sweep_fp16():
+@pytest.mark.parametrize("storage,tol", [(F.STORE_FP16, 2e-3), (F.STORE_BF16, 2e-2)])
+def test_staged_sweep_16bit(storage, tol):
+    """16-bit storage through the staged even step and the pair odd step:
+    types exact, PDFs of fluid cells within the storage's rounding after one
+    and after four steps (two of each parity)."""
     w = _staged_workload()
-    sim = _sim(w, storage=F.STORE_FP16)
+    sim = _sim(w, storage=storage)
     o = oracle_from_workload(w)
-    sim.step(2)
-    o.step(2)
-    to = o.get(O.F_TYPE)
-    assert (sim.get(F.FIELD_TYPE) == to).all()
-    fl = (to == 1) | (to == 2)
-    dev = np.abs(sim.get(F.FIELD_PDF)[:, fl] - o.get(O.F_PDF)[:, fl]) / weights()[:, None]
-    assert dev.max() < 2e-3
+    for k in (1, 3):
+        sim.step(k)
+        o.step(k)
+        to = o.get(O.F_TYPE)
+        assert (sim.get(F.FIELD_TYPE) == to).all()
+        fl = (to == 1) | (to == 2)
+        dev = np.abs(sim.get(F.FIELD_PDF)[:, fl] - o.get(O.F_PDF)[:, fl]) / weights()[:, None]
+        assert dev.max() < tol, (k, dev.max())
     sim.close()
 
 
