@@ -167,21 +167,106 @@ __global__ void __launch_bounds__(256, liquid_min_blocks<S>()) k_liquid(Dev s) {
 template <typename S, int PAR>
 constexpr int liquid_pair_min_blocks() { return PAR == 0 ? 4 : (sizeof(S) == 2 ? 6 : 5); }
 
+// Stream and collide one pair (x even, x + 1) of row `row`; liq: bit 0 cell
+// x liquid, bit 1 cell x + 1 liquid. `interior`: every neighbour of both
+// cells inside the lattice without wrap (always true in an even step, which
+// touches only a cell's own slots).
 template <typename S, int PAR>
+__device__ __forceinline__ void pair_update(const Dev& s, S* f, int x, int row, unsigned liq, bool interior) {
+    const unsigned un = (unsigned)s.n;
+    const int sxy = s.nx * s.ny;
+    const int cell = x + s.nx * row;
+    const int y = row % s.ny, z = row / s.ny;
+    float2 v[27];
+    if (interior) {
+#pragma unroll
+        for (int q = 0; q < 27; ++q) {
+            const unsigned a = PAR == 0 ? (unsigned)q * un + (unsigned)cell
+                                        : (unsigned)opp(q) * un +
+                                              (unsigned)(cell - (cx(q) + s.nx * cy(q) + sxy * cz(q)));
+            if (PAR == 0 || cx(q) == 0) v[q] = Pair<S>::ld2(f + a);
+            else v[q] = make_float2(Store<S>::ld_raw(f + a), Store<S>::ld_raw(f + a + 1));
+        }
+    } else {
+        const NbrOffsets o0 = nbr_offsets(s, x, y, z), o1 = nbr_offsets(s, x + 1, y, z);
+#pragma unroll
+        for (int q = 0; q < 27; ++q) {
+            // source x - c_q beyond a wall face: the cell's own slot (q, x)
+            const unsigned wb = wall_bits(-cx(q), -cy(q), -cz(q));
+            const int src0 = cell + o0.ox[1 - cx(q)] + o0.oy[1 - cy(q)] + o0.oz[1 - cz(q)];
+            const int src1 = cell + 1 + o1.ox[1 - cx(q)] + o1.oy[1 - cy(q)] + o1.oz[1 - cz(q)];
+            const long long a0 = (o0.wall & wb) ? (long long)q * s.n + cell : (long long)opp(q) * s.n + src0;
+            const long long a1 =
+                (o1.wall & wb) ? (long long)q * s.n + cell + 1 : (long long)opp(q) * s.n + src1;
+            v[q] = make_float2((liq & 1u) ? Store<S>::ld_raw(f + a0) : 0.f,
+                               (liq & 2u) ? Store<S>::ld_raw(f + a1) : 0.f);
+        }
+    }
+    collide_pair<Pair<S>::SCALE_LOG2>(v, s.omega, s.gx, s.gy, s.gz);
+    if (interior && liq == 3u) {
+#pragma unroll
+        for (int q = 0; q < 27; ++q) {
+            const unsigned a = PAR == 0 ? (unsigned)opp(q) * un + (unsigned)cell
+                                        : (unsigned)q * un +
+                                              (unsigned)(cell + cx(q) + s.nx * cy(q) + sxy * cz(q));
+            if (PAR == 0 || cx(q) == 0) {
+                Pair<S>::st2(f + a, v[q]);
+            } else {
+                Store<S>::st_raw(f + a, v[q].x);
+                Store<S>::st_raw(f + a + 1, v[q].y);
+            }
+        }
+    } else if (interior) {
+        // one liquid cell: liq is 1 (x) or 2 (x + 1)
+        const unsigned k = liq >> 1;
+#pragma unroll
+        for (int q = 0; q < 27; ++q) {
+            const unsigned a = PAR == 0 ? (unsigned)opp(q) * un + (unsigned)cell
+                                        : (unsigned)q * un +
+                                              (unsigned)(cell + cx(q) + s.nx * cy(q) + sxy * cz(q));
+            Store<S>::st_raw(f + a + k, k ? v[q].y : v[q].x);
+        }
+    } else {
+        const NbrOffsets o0 = nbr_offsets(s, x, y, z), o1 = nbr_offsets(s, x + 1, y, z);
+#pragma unroll
+        for (int q = 0; q < 27; ++q) {
+            // target x + c_q beyond a wall face: the cell's own slot (opp(q), x)
+            const unsigned wb = wall_bits(cx(q), cy(q), cz(q));
+            const int dst0 = cell + o0.ox[1 + cx(q)] + o0.oy[1 + cy(q)] + o0.oz[1 + cz(q)];
+            const int dst1 = cell + 1 + o1.ox[1 + cx(q)] + o1.oy[1 + cy(q)] + o1.oz[1 + cz(q)];
+            if (liq & 1u)
+                Store<S>::st_raw(
+                    f + ((o0.wall & wb) ? (long long)opp(q) * s.n + cell : (long long)q * s.n + dst0), v[q].x);
+            if (liq & 2u)
+                Store<S>::st_raw(
+                    f + ((o1.wall & wb) ? (long long)opp(q) * s.n + cell + 1 : (long long)q * s.n + dst1),
+                    v[q].y);
+        }
+    }
+}
+
+// PART 1 keeps to the interior pairs of an odd step (all 26 neighbours of
+// both cells inside the lattice, no wrap), so that the kernel of the bulk
+// carries no boundary code; k_liquid_pair_edges takes the others. PART 0:
+// every pair (even steps).
+template <typename S, int PAR, int PART>
 __global__ void __launch_bounds__(128, liquid_pair_min_blocks<S, PAR>()) k_liquid_pair(Dev s) {
     __shared__ int ps[128];      // (x << 2 | liquid bits) of the compacted pairs
     __shared__ int wn[4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     S* f = static_cast<S*>(s.f);
-    const unsigned un = (unsigned)s.n;
     const int nrows = s.ny * s.nz;
-    const int sxy = s.nx * s.ny;
     for (int row = blockIdx.y; row < nrows; row += gridDim.y) {
+        const int yr = row % s.ny, zr = row / s.ny;
+        const bool face_row = yr == 0 || yr == s.ny - 1 || zr == 0 || zr == s.nz - 1;
         const int x0 = blockIdx.x * 256 + 2 * (int)threadIdx.x;
         unsigned lm = 0;
         if (x0 < s.nx) {
-            const uchar2 fl = *reinterpret_cast<const uchar2*>(s.flags + x0 + (long long)s.nx * row);
-            lm = ((fl.x & TYPE_MASK) == T_LIQ ? 1u : 0u) | ((fl.y & TYPE_MASK) == T_LIQ ? 2u : 0u);
+            const bool inner_pair = !face_row && x0 > 0 && x0 + 1 < s.nx - 1;
+            if (PART == 0 || inner_pair) {
+                const uchar2 fl = *reinterpret_cast<const uchar2*>(s.flags + x0 + (long long)s.nx * row);
+                lm = ((fl.x & TYPE_MASK) == T_LIQ ? 1u : 0u) | ((fl.y & TYPE_MASK) == T_LIQ ? 2u : 0u);
+            }
         }
         const unsigned m = __ballot_sync(0xffffffffu, lm != 0);
         if (lane == 0) wn[warp] = __popc(m);
@@ -198,78 +283,41 @@ __global__ void __launch_bounds__(128, liquid_pair_min_blocks<S, PAR>()) k_liqui
         __syncthreads();             // ps and wn are rewritten by the next row
         if (e < 0) continue;
         const int x = e >> 2;
-        const unsigned liq = (unsigned)e & 3u;
-        const int cell = x + s.nx * row;
-        const int y = row % s.ny, z = row / s.ny;
         const bool interior =
-            PAR == 0 || (x > 0 && x + 1 < s.nx - 1 && y > 0 && y < s.ny - 1 && z > 0 && z < s.nz - 1);
-        float2 v[27];
-        if (interior) {
-#pragma unroll
-            for (int q = 0; q < 27; ++q) {
-                const unsigned a = PAR == 0 ? (unsigned)q * un + (unsigned)cell
-                                            : (unsigned)opp(q) * un +
-                                                  (unsigned)(cell - (cx(q) + s.nx * cy(q) + sxy * cz(q)));
-                if (PAR == 0 || cx(q) == 0) v[q] = Pair<S>::ld2(f + a);
-                else v[q] = make_float2(Store<S>::ld_raw(f + a), Store<S>::ld_raw(f + a + 1));
-            }
-        } else {
-            const NbrOffsets o0 = nbr_offsets(s, x, y, z), o1 = nbr_offsets(s, x + 1, y, z);
-#pragma unroll
-            for (int q = 0; q < 27; ++q) {
-                // source x - c_q beyond a wall face: the cell's own slot (q, x)
-                const unsigned wb = wall_bits(-cx(q), -cy(q), -cz(q));
-                const int src0 = cell + o0.ox[1 - cx(q)] + o0.oy[1 - cy(q)] + o0.oz[1 - cz(q)];
-                const int src1 = cell + 1 + o1.ox[1 - cx(q)] + o1.oy[1 - cy(q)] + o1.oz[1 - cz(q)];
-                const long long a0 = (o0.wall & wb) ? (long long)q * s.n + cell : (long long)opp(q) * s.n + src0;
-                const long long a1 =
-                    (o1.wall & wb) ? (long long)q * s.n + cell + 1 : (long long)opp(q) * s.n + src1;
-                v[q] = make_float2((liq & 1u) ? Store<S>::ld_raw(f + a0) : 0.f,
-                                   (liq & 2u) ? Store<S>::ld_raw(f + a1) : 0.f);
-            }
-        }
-        collide_pair<Pair<S>::SCALE_LOG2>(v, s.omega, s.gx, s.gy, s.gz);
-        if (interior && liq == 3u) {
-#pragma unroll
-            for (int q = 0; q < 27; ++q) {
-                const unsigned a = PAR == 0 ? (unsigned)opp(q) * un + (unsigned)cell
-                                            : (unsigned)q * un +
-                                                  (unsigned)(cell + cx(q) + s.nx * cy(q) + sxy * cz(q));
-                if (PAR == 0 || cx(q) == 0) {
-                    Pair<S>::st2(f + a, v[q]);
-                } else {
-                    Store<S>::st_raw(f + a, v[q].x);
-                    Store<S>::st_raw(f + a + 1, v[q].y);
-                }
-            }
-        } else if (interior) {
-            // one liquid cell: liq is 1 (x) or 2 (x + 1)
-            const unsigned k = liq >> 1;
-#pragma unroll
-            for (int q = 0; q < 27; ++q) {
-                const unsigned a = PAR == 0 ? (unsigned)opp(q) * un + (unsigned)cell
-                                            : (unsigned)q * un +
-                                                  (unsigned)(cell + cx(q) + s.nx * cy(q) + sxy * cz(q));
-                Store<S>::st_raw(f + a + k, k ? v[q].y : v[q].x);
-            }
-        } else {
-            const NbrOffsets o0 = nbr_offsets(s, x, y, z), o1 = nbr_offsets(s, x + 1, y, z);
-#pragma unroll
-            for (int q = 0; q < 27; ++q) {
-                // target x + c_q beyond a wall face: the cell's own slot (opp(q), x)
-                const unsigned wb = wall_bits(cx(q), cy(q), cz(q));
-                const int dst0 = cell + o0.ox[1 + cx(q)] + o0.oy[1 + cy(q)] + o0.oz[1 + cz(q)];
-                const int dst1 = cell + 1 + o1.ox[1 + cx(q)] + o1.oy[1 + cy(q)] + o1.oz[1 + cz(q)];
-                if (liq & 1u)
-                    Store<S>::st_raw(
-                        f + ((o0.wall & wb) ? (long long)opp(q) * s.n + cell : (long long)q * s.n + dst0), v[q].x);
-                if (liq & 2u)
-                    Store<S>::st_raw(
-                        f + ((o1.wall & wb) ? (long long)opp(q) * s.n + cell + 1 : (long long)q * s.n + dst1),
-                        v[q].y);
-            }
-        }
+            PAR == 0 || PART == 1 || (x > 0 && x + 1 < s.nx - 1 && !face_row);
+        pair_update<S, PAR>(s, f, x, row, (unsigned)e & 3u, interior);
     }
+}
+
+// The pairs of an odd step that k_liquid_pair<S, 1, 1> leaves out, one per
+// thread: every pair of the rows on the y and z faces, then the pairs at
+// x = 0 and x = nx - 2 of the other rows (ny, nz >= 3 and nx >= 4, so that
+// no pair is listed twice).
+template <typename S>
+__global__ void __launch_bounds__(128) k_liquid_pair_edges(Dev s) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int hp = s.nx / 2;                                   // pairs per row
+    const long long nface = 2LL * s.nz + 2LL * (s.ny > 2 ? s.ny - 2 : 0);
+    int y, z, x;
+    if (t < nface * hp) {
+        const int r = (int)(t / hp);
+        x = 2 * (int)(t % hp);
+        if (r < 2 * s.nz) { z = r >> 1; y = (r & 1) ? s.ny - 1 : 0; }
+        else { const int k = r - 2 * s.nz; y = 1 + (k >> 1); z = (k & 1) ? s.nz - 1 : 0; }
+    } else if (t < nface * hp + 2LL * (s.ny - 2) * (s.nz - 2)) {
+        const long long k = t - nface * hp;
+        x = (k & 1) ? s.nx - 2 : 0;
+        const long long r = k >> 1;
+        y = 1 + (int)(r % (s.ny - 2));
+        z = 1 + (int)(r / (s.ny - 2));
+    } else {
+        return;
+    }
+    const int row = y + s.ny * z;
+    const uchar2 fl = *reinterpret_cast<const uchar2*>(s.flags + x + (long long)s.nx * row);
+    const unsigned lm = ((fl.x & TYPE_MASK) == T_LIQ ? 1u : 0u) | ((fl.y & TYPE_MASK) == T_LIQ ? 2u : 0u);
+    if (!lm) return;
+    pair_update<S, 1>(s, static_cast<S*>(s.f), x, row, lm, false);
 }
 
 // ---------------------------------------------------------------- staged even step
@@ -746,6 +794,11 @@ __global__ void __launch_bounds__(128) k_interface(Dev s) {
 }
 
 static bool use_pairs(const Dev& s) { return s.idx32 && (s.nx % 2) == 0; }
+// odd steps at 16-bit storage: interior pairs and the boundary pairs in two
+// launches (at FP32 the odd step is bound by HBM, and one launch is faster)
+static bool use_split(const Dev& s) {
+    return use_pairs(s) && s.storage != FSLBM_STORE_FP32 && s.nx >= 4 && s.ny >= 3 && s.nz >= 3;
+}
 // the staged even step: 16-bit storage, nx a multiple of the tile
 static bool use_staged_pairs(const Dev& s) {
     return s.idx32 && s.storage != FSLBM_STORE_FP32 && (s.nx % SP_TILE) == 0;
@@ -797,15 +850,23 @@ static void launch_typed(const Dev& s, int parity, cudaStream_t st) {
                 k_liquid_staged_pair<S><<<staged_pair_blocks<S>(), SP_TILE / 2, StagedPairLayout<S>::SMEM, st>>>(s);
             }
         } else if (use_pairs(s)) {
-            k_liquid_pair<S, 0><<<lgrid, 128, 0, st>>>(s);
+            k_liquid_pair<S, 0, 0><<<lgrid, 128, 0, st>>>(s);
         } else {
             k_liquid<S, 0><<<lgrid, 256, 0, st>>>(s);
         }
         k_interface<S, 0><<<lb, 128, 0, st>>>(s);
     } else {
         if (s.np > 0) k_solid_links<S, 1><<<link_blocks<S, 1>(), 256, 0, st>>>(s);
-        if (use_pairs(s)) k_liquid_pair<S, 1><<<lgrid, 128, 0, st>>>(s);
-        else k_liquid<S, 1><<<lgrid, 256, 0, st>>>(s);
+        if (use_split(s)) {
+            k_liquid_pair<S, 1, 1><<<lgrid, 128, 0, st>>>(s);
+            const long long ne = (2LL * s.nz + 2LL * (s.ny > 2 ? s.ny - 2 : 0)) * (s.nx / 2) +
+                                 2LL * (s.ny > 2 ? s.ny - 2 : 0) * (s.nz > 2 ? s.nz - 2 : 0);
+            k_liquid_pair_edges<S><<<blocks_for(ne, 128), 128, 0, st>>>(s);
+        } else if (use_pairs(s)) {
+            k_liquid_pair<S, 1, 0><<<lgrid, 128, 0, st>>>(s);
+        } else {
+            k_liquid<S, 1><<<lgrid, 256, 0, st>>>(s);
+        }
         k_interface<S, 1><<<lb, 128, 0, st>>>(s);
     }
 }
@@ -815,7 +876,8 @@ int launch_stream_collide(const Dev& s, int parity, cudaStream_t st) {
     else if (s.storage == FSLBM_STORE_FP16) launch_typed<__half>(s, parity, st);
     else launch_typed<__nv_bfloat16>(s, parity, st);
     const bool staged = parity == 0 && use_staged_pairs(s);
-    return (s.np > 0 ? 1 : 0) + 2 + (staged ? 1 : 0);
+    const bool split = parity == 1 && use_split(s);
+    return (s.np > 0 ? 1 : 0) + 2 + (staged ? 1 : 0) + (split ? 1 : 0);
 }
 
 }  // namespace fsl
