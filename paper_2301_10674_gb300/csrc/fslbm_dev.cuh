@@ -186,6 +186,15 @@ __host__ __device__ __forceinline__ void coords(const Dev& s, long long c, int& 
     z = (int)(r / s.ny);
 }
 
+// the same for a cell index below 2^31 (list entries), in 32-bit arithmetic
+__device__ __forceinline__ void coords32(const Dev& s, int c, int& x, int& y, int& z) {
+    const unsigned u = (unsigned)c, nx = (unsigned)s.nx, ny = (unsigned)s.ny;
+    const unsigned r = u / nx;
+    x = (int)(u - r * nx);
+    z = (int)(r / ny);
+    y = (int)(r - (unsigned)z * ny);
+}
+
 // coordinate of x + d along an axis of length L: wrapped if periodic, -1 if
 // it lies beyond a wall face
 __device__ __forceinline__ int shift(int x, int d, int L, int periodic) {

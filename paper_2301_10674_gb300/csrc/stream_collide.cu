@@ -373,14 +373,17 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
 }
 
 // the x-tiles of SP_TILE cells that hold at least one liquid cell, in the
-// order of their first cell within each block
+// order of their first cell within each block; SP_FULL marks a tile whose
+// cells are all liquid
+constexpr int SP_FULL = 1 << 30;
 __global__ void k_sp_tiles(Dev s) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long ntile = s.n / SP_TILE;
     bool act = false;
+    int val = (int)t;
     if (t < ntile) {
         const uint4* w = reinterpret_cast<const uint4*>(s.flags + t * SP_TILE);
-        unsigned any = 0;
+        unsigned any = 0, other = 0;
 #pragma unroll 4
         for (int k = 0; k < SP_TILE / 16; ++k) {
             const uint4 v = w[k];
@@ -390,11 +393,13 @@ __global__ void k_sp_tiles(Dev s) {
                 // a byte holds a liquid cell when its type bits are 01
                 const unsigned lo = (wd[j] & 0x03030303u) ^ 0x01010101u;
                 any |= (lo - 0x01010101u) & ~lo & 0x80808080u;
+                other |= lo;
             }
         }
         act = any != 0;
+        if (other == 0) val |= SP_FULL;
     }
-    block_append(s, act, (int)t, s.tiles, s.tile_count, (int)ntile);
+    block_append(s, act, val, s.tiles, s.tile_count, (int)ntile);
 }
 
 template <typename S>
@@ -411,7 +416,7 @@ __device__ __forceinline__ void staged_pair_issue(const Dev& s, unsigned char* s
     using L = StagedPairLayout<S>;
     const S* f = static_cast<const S*>(s.f);
     const long long n = s.n;
-    const long long c0 = (long long)tile * SP_TILE;
+    const long long c0 = (long long)(tile & ~SP_FULL) * SP_TILE;
     S* buf = reinterpret_cast<S*>(stage);
     mbar_expect_tx(full, (unsigned)L::STAGE_BYTES);
     bulk_load(stage + L::PDF_BYTES, s.flags + c0, SP_TILE, full);
@@ -465,28 +470,31 @@ __global__ void __launch_bounds__(SP_TILE / 2, 6) k_liquid_staged_pair(Dev s) {
         const unsigned char* stage = smem_raw + st * L::STAGE_BYTES;
         const S* buf = reinterpret_cast<const S*>(stage);
         const unsigned char* fl = stage + L::PDF_BYTES;
-        // compaction: thread t collides the t-th pair of the tile that holds
-        // a liquid cell
-        unsigned lm = 0;
-        if (ok) {
-            const uchar2 b = *reinterpret_cast<const uchar2*>(fl + 2 * tid);
-            lm = ((b.x & TYPE_MASK) == T_LIQ ? 1u : 0u) | ((b.y & TYPE_MASK) == T_LIQ ? 2u : 0u);
-        }
-        const unsigned m = __ballot_sync(0xffffffffu, lm != 0);
-        if (lane == 0) wn[warp] = __popc(m);
-        // a bounded wait that gave up ends the loop for every thread at once
+        // a bounded wait that gave up ends the loop for every thread at once;
+        // the vote also keeps the next tile's compaction off pos and wn
+        // until every thread has read them
         if (__syncthreads_or(!ok || refill_failed)) break;
-        int off = 0, tot = 0;
+        const int traw = stage_tile[st];
+        int e = (tid << 2) | 3;
+        if (!(traw & SP_FULL)) {
+            // compaction: thread t collides the t-th pair of the tile that
+            // holds a liquid cell
+            const uchar2 b = *reinterpret_cast<const uchar2*>(fl + 2 * tid);
+            const unsigned lm = ((b.x & TYPE_MASK) == T_LIQ ? 1u : 0u) | ((b.y & TYPE_MASK) == T_LIQ ? 2u : 0u);
+            const unsigned m = __ballot_sync(0xffffffffu, lm != 0);
+            if (lane == 0) wn[warp] = __popc(m);
+            __syncthreads();
+            int off = 0, tot = 0;
 #pragma unroll
-        for (int w = 0; w < NT / 32; ++w) {
-            off += w < warp ? wn[w] : 0;
-            tot += wn[w];
+            for (int w = 0; w < NT / 32; ++w) {
+                off += w < warp ? wn[w] : 0;
+                tot += wn[w];
+            }
+            if (lm) pos[off + __popc(m & ((1u << lane) - 1u))] = (tid << 2) | (int)lm;
+            __syncthreads();
+            e = tid < tot ? pos[tid] : -1;
         }
-        if (lm) pos[off + __popc(m & ((1u << lane) - 1u))] = (tid << 2) | (int)lm;
-        __syncthreads();
-        const int e = tid < tot ? pos[tid] : -1;
-        const int cell = stage_tile[st] * SP_TILE + 2 * (e >> 2);
-        __syncthreads();             // pos and wn are rewritten by the next tile
+        const int cell = (traw & ~SP_FULL) * SP_TILE + 2 * (e >> 2);
         if (e >= 0) {
             const int p = 2 * (e >> 2);
             const unsigned liq = (unsigned)e & 3u;
@@ -603,7 +611,7 @@ __global__ void __launch_bounds__(256, 3) k_solid_links(Dev s) {
         if (i < count) {
             const int cell = s.sl[i];
             int x, y, z;
-            coords(s, cell, x, y, z);
+            coords32(s, cell, x, y, z);
             const int p = s.owner[cell];
             S* f = static_cast<S*>(s.f);
             const long long n = s.n;
@@ -691,7 +699,7 @@ __global__ void __launch_bounds__(128) k_interface(Dev s) {
         if (work) {
             const long long cell = s.wl[i];
             int x, y, z;
-            coords(s, cell, x, y, z);
+            coords32(s, (int)cell, x, y, z);
             S* f = static_cast<S*>(s.f);
             S* fs = static_cast<S*>(s.fs);
             const long long n = s.n;
