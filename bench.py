@@ -241,12 +241,21 @@ def timed_run(args, w, storage_name, theta, stream, local, barrier, world):
     clk = clocks.stop()
     counts_after = sim.cell_counts()
     red = sim.reduce()
+    # bed topography of Section 3.2 on the final state, and its cost per call
+    # through the C ABI (two kernels, a copy to the host, a synchronisation)
+    bed_h = sim.bed_height()
+    t0 = time.perf_counter()
+    for _ in range(5):
+        sim.bed_height()
+    bed_ms = (time.perf_counter() - t0) / 5 * 1e3
     t = sim.get(F.FIELD_TYPE)
     phi = sim.get(F.FIELD_PHI)
     column = np.where(t == 1, 1.0, np.where(t == 2, phi, 0.0)).sum(axis=0)     # liquid volume per (y, x)
     out = {"ms": ms, "sweep_ms": sweep_ms, "sweeps": sweeps, "launches": launches, "counts": counts,
            "counts_after": counts_after, "clocks": clk, "violations": sim.violations, "m0": m0, "m1": red,
-           "column": column, "normal_stats": sim.normal_stats() if theta is not None else None}
+           "column": column, "normal_stats": sim.normal_stats() if theta is not None else None,
+           "bed": {"level": 0.3, "mean": round(float(bed_h.mean()), 4), "min": round(float(bed_h.min()), 4),
+                   "max": round(float(bed_h.max()), 4), "ms_per_call": round(bed_ms, 3)}}
     sim.close()
     del sim
     if world > 1:
@@ -357,6 +366,7 @@ def run_ours(args, world, rank, local):
             "evaluated": int(head["normal_stats"][0]), "taken": int(head["normal_stats"][1])},
         "checks": {"invariant_violations": int(head["violations"]), "liquid_mass": float(head["m1"][0]),
                    "interface_cells": int(head["m1"][5])},
+        "bed_height": head["bed"],
     }
     return out
 

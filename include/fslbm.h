@@ -196,6 +196,21 @@ int fslbm_set_fields(fslbm* s, uint32_t field_mask, const void* const* src, int 
  * out[7] mass pool. Synchronises the stream. */
 int fslbm_reduce(fslbm* s, double out[8]);
 
+/* Bed topography (Section 3.2): phi_b(x, z), the fraction of the cells of
+ * the column (x, ., z) covered by a particle (y-averaged solid fraction), and
+ * the bed height h_b(x), the z at which phi_b crosses phi_b_level (the paper
+ * uses 0.3), linearly interpolated between cell centres (cell k at
+ * z = k + 1/2). The topmost crossing counts; above the lattice phi_b is 0,
+ * and below it the bottom wall counts as solid (phi_b = 1 at z = -1/2). A
+ * bed whose top solid layer is H - 1 therefore gives H - 1/2 + (1 - level).
+ *   phi_b_level  threshold in (0, 1]; other values: FSLBM_EINVAL
+ *   h            double [nx] out, x-fastest (device if on_device, else host)
+ *   phi          optional double [nz][nx] out (NULL: not copied), same memory
+ *                kind as h
+ * The first call allocates (nz + 1) nx doubles of device scratch, kept until
+ * fslbm_destroy. Synchronises the stream; returns the sticky error word. */
+int fslbm_bed_height(fslbm* s, double phi_b_level, double* h, double* phi, int on_device);
+
 /* Waits for the stream; returns the sticky error word. */
 int fslbm_sync(fslbm* s);
 

@@ -38,6 +38,7 @@ struct fslbm {
     size_t ev_used;
     int64_t launches;
     unsigned long long* counts4;
+    double* bed;                   // nx * nz + nx doubles: phi_b(x, z), then h_b(x)
     MlpBf16* mlp_dev;              // operand copies of the learned normal
     unsigned long long* mlp_stats;
 };
@@ -165,6 +166,7 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     s->ev_used = 0;
     s->launches = 0;
     s->counts4 = nullptr;
+    s->bed = nullptr;
     s->mlp_dev = nullptr;
     s->mlp_stats = nullptr;
     Dev& d = s->d;
@@ -602,6 +604,24 @@ int fslbm_cell_counts(fslbm* s, int64_t counts[4]) {
     int rc = sync_check(s);
     for (int k = 0; k < 4; ++k) counts[k] = (int64_t)h[k];
     return rc;
+}
+
+int fslbm_bed_height(fslbm* s, double phi_b, double* h, double* phi, int on_device) {
+    if (!s || !h || !(phi_b > 0.0 && phi_b <= 1.0)) return FSLBM_EINVAL;
+    if (s->host_err) return s->host_err;
+    const Dev& d = s->d;
+    const size_t nxz = (size_t)d.nx * d.nz;
+    if (!s->bed) {
+        bool ok = true;
+        s->bed = dalloc<double>(s, nxz + d.nx, ok);
+        if (!ok) return FSLBM_ENOMEM;
+    }
+    launch_bed_height(d, phi_b, s->bed, s->bed + nxz, s->st);
+    const cudaMemcpyKind kind = kind_to(on_device);
+    cudaMemcpyAsync(h, s->bed + nxz, d.nx * sizeof(double), kind, s->st);
+    if (phi) cudaMemcpyAsync(phi, s->bed, nxz * sizeof(double), kind, s->st);
+    launch_check(s);
+    return sync_check(s);
 }
 
 int fslbm_set_normal_model(fslbm* s, const uint16_t* w, int64_t n_params) {

@@ -277,4 +277,41 @@ void launch_reduce(const Dev& s, int last_parity, double* out, cudaStream_t st) 
     k_reduce_final<<<1, 1, 0, st>>>(s, out);
 }
 
+// ------------------------------------------------------------ bed height
+// Bed topography of Section 3.2: phi_b(x, z), the fraction of the cells of
+// the column (x, ., z) that a particle covers, then h_b(x), the z at which
+// phi_b crosses the threshold, linearly interpolated between cell centres
+// (cell k at z = k + 1/2). The topmost crossing counts; above the lattice
+// phi_b is 0, and below it the bottom wall counts as solid (phi_b = 1 at
+// z = -1/2).
+__global__ void k_bed_fraction(Dev s, double* phi) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)s.nx * s.nz) return;
+    const int x = (int)(t % s.nx), z = (int)(t / s.nx);
+    const uint8_t* fl = s.flags + x + (long long)s.nx * s.ny * z;
+    int c = 0;
+    for (int y = 0; y < s.ny; ++y) c += (fl[(long long)s.nx * y] & TYPE_MASK) == T_SOL;
+    phi[t] = (double)c / (double)s.ny;
+}
+__global__ void k_bed_height(Dev s, const double* phi, double phi_b, double* h) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= s.nx) return;
+    int k = s.nz - 1;
+    while (k >= 0 && !(phi[x + (long long)s.nx * k] >= phi_b)) --k;
+    double pk, pn;
+    if (k < 0) {
+        pk = 1.0;
+        pn = phi[x];
+    } else {
+        pk = phi[x + (long long)s.nx * k];
+        pn = k + 1 < s.nz ? phi[x + (long long)s.nx * (k + 1)] : 0.0;
+    }
+    h[x] = __dadd_rn((double)k + 0.5, __ddiv_rn(pk - phi_b, pk - pn));
+}
+
+void launch_bed_height(const Dev& s, double phi_b, double* phi, double* h, cudaStream_t st) {
+    k_bed_fraction<<<blocks_for((long long)s.nx * s.nz, 256), 256, 0, st>>>(s, phi);
+    k_bed_height<<<blocks_for(s.nx, 128), 128, 0, st>>>(s, phi, phi_b, h);
+}
+
 }  // namespace fsl

@@ -47,7 +47,7 @@ EXPORTED = (
     "fslbm_num_spheres", "fslbm_invariant_violations", "fslbm_timing", "fslbm_timing_read",
     "fslbm_cell_counts", "fslbm_reduce_fields_noalloc", "fslbm_destroy", "fslbm_strerror",
     "fslbm_set_normal_model", "fslbm_normal_stats", "fslbm_mlp_stencils", "fslbm_mlp_gradient",
-    "fslbm_mlp_train", "fslbm_mlp_infer",
+    "fslbm_mlp_train", "fslbm_mlp_infer", "fslbm_bed_height",
 )
 
 MLP_NPARAM = 6212
@@ -119,6 +119,7 @@ def load():
     L.fslbm_timing_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                     ctypes.POINTER(ctypes.c_int64)]
     L.fslbm_cell_counts.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+    L.fslbm_bed_height.argtypes = [vp, ctypes.c_double, vp, vp, ctypes.c_int]
     L.fslbm_reduce_fields_noalloc.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), vp, vp]
     L.fslbm_set_normal_model.argtypes = [vp, vp, ctypes.c_int64]
     L.fslbm_normal_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
@@ -408,6 +409,15 @@ class Simulation:
         _check(load().fslbm_timing_read(self.h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(k)),
                "fslbm_timing_read")
         return ms.value, n.value, k.value
+
+    def bed_height(self, level: float = 0.3, with_fraction: bool = False):
+        """Bed height h_b(x) (nx,) of Section 3.2 at solid fraction `level`;
+        with_fraction also returns phi_b(x, z) as (nz, nx)."""
+        h = np.zeros(self.shape[2])
+        phi = np.zeros((self.shape[0], self.shape[2])) if with_fraction else None
+        _check(load().fslbm_bed_height(self.h, float(level), h.ctypes.data,
+                                       phi.ctypes.data if phi is not None else None, 0), "fslbm_bed_height")
+        return (h, phi) if with_fraction else h
 
     def cell_counts(self) -> np.ndarray:
         out = np.zeros(4, np.int64)

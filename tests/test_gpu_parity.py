@@ -349,3 +349,24 @@ def test_mass_conservation_with_moving_bed(storage):
     assert np.abs(sim.get(F.FIELD_P_X) - w.xyz).max() > 1e-3
     assert sim.violations == 0
     sim.close()
+
+
+def test_bed_height_matches_oracle():
+    """Bed topography (Section 3.2) of a bed that has moved for a few steps:
+    the library's phi_b(x, z) equals the oracle's definition applied to the
+    same cell types exactly, and h_b(x) to rounding, at two thresholds."""
+    from oracle import diagnostics as D
+    w = W.tiny().generate()
+    sim = _sim(w)
+    sim.step(3)
+    t = sim.get(F.FIELD_TYPE)
+    for level in (0.3, 0.55):
+        h, phi = sim.bed_height(level, with_fraction=True)
+        assert np.array_equal(phi, D.solid_fraction(t))
+        assert np.allclose(h, D.bed_height(t, level), rtol=0.0, atol=1e-12)
+        # the sparse hexagonal bed: some columns reach the threshold near
+        # the bed top, the others only at the wall
+        assert h.max() > 5.0 and h.min() >= -0.5 and h.max() <= w.nz + 0.5
+    with pytest.raises(F.FslbmError):
+        sim.bed_height(0.0)
+    sim.close()
