@@ -15,6 +15,7 @@ void mlp_from_bf16_host(const uint16_t* w, MlpBf16& h);
 
 namespace fsl {
 void launch_export_owner(const Dev& s, int* out, cudaStream_t st);
+void launch_bed_height(const Dev& s, double phi_b, double* phi, double* h, cudaStream_t st);
 }
 
 using namespace fsl;

@@ -505,7 +505,6 @@ int launch_normals(const Dev& s, float4* out, cudaStream_t st);
 int launch_conversion(const Dev& s, int last_parity, cudaStream_t st);
 int launch_pool_spread(const Dev& s, cudaStream_t st);
 void launch_cell_counts(const Dev& s, unsigned long long* out, cudaStream_t st);
-void launch_bed_height(const Dev& s, double phi_b, double* phi, double* h, cudaStream_t st);
 void launch_init_flat(const Dev& s, double H, cudaStream_t st);
 void launch_init_surface(const Dev& s, const double* H, cudaStream_t st);
 int launch_particles_step(const Dev& s, int have_prev, int last_parity, cudaStream_t st);
