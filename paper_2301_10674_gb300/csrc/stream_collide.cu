@@ -604,12 +604,15 @@ __global__ void __launch_bounds__(256, 3) k_solid_links(Dev s) {
     const int count = min(*s.sl_count, s.sl_cap);
     const int stride = gridDim.x * blockDim.x;
     float injected = 0.f;   // mass the moving bounce-back adds to liquid cells
+    // the list entry of the next pass is loaded one pass ahead
+    int next = blockIdx.x * blockDim.x + threadIdx.x < count ? s.sl[blockIdx.x * blockDim.x + threadIdx.x] : 0;
     for (int base = blockIdx.x * blockDim.x; base < count; base += stride) {
         const int i = base + threadIdx.x;
+        const int cell = next;
+        next = i + stride < count ? s.sl[i + stride] : 0;
         int key = -1;
         float F[3] = {0.f, 0.f, 0.f}, T[3] = {0.f, 0.f, 0.f};
         if (i < count) {
-            const int cell = s.sl[i];
             int x, y, z;
             coords32(s, cell, x, y, z);
             const int p = s.owner[cell];
