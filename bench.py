@@ -162,8 +162,8 @@ LAM, MU = 0.4, 0.1
 # even and odd steps averaged, from one ncu capture on the 1024x64x128 flume.
 # It is valid while the sweep's sources hash to `sources`, and is scaled to a
 # run by its fluid cells.
-SWEEP_TRAFFIC = {"sources": "d12bed33ec0a96e7", "workload": "precision-1024x64x128",
-                 "per_fluid_cell": {"fp16": 195.0, "fp32": 381.4, "bf16": None}}
+SWEEP_TRAFFIC = {"sources": "04486a592246c3d3", "workload": "precision-1024x64x128",
+                 "per_fluid_cell": {"fp16": 195.4, "fp32": 382.6, "bf16": None}}
 SWEEP_SOURCES = ("paper_2301_10674_gb300/csrc/stream_collide.cu", "paper_2301_10674_gb300/csrc/fslbm_dev.cuh",
                  "paper_2301_10674_gb300/csrc/collide_pair.cuh")
 

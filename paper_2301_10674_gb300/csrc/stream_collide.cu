@@ -162,10 +162,10 @@ __global__ void __launch_bounds__(256, liquid_min_blocks<S>()) k_liquid(Dev s) {
 // Needs nx even and 32-bit element indices.
 // Resident blocks per SM asked of the compiler, measured per parity: an
 // even step (all accesses aligned pairs) runs fastest without spills (4
-// blocks, up to 128 registers), an odd step with more warps (6 blocks for
+// blocks, up to 128 registers), an odd step with more warps (7 blocks for
 // 16-bit storage, 5 for FP32).
 template <typename S, int PAR>
-constexpr int liquid_pair_min_blocks() { return PAR == 0 ? 4 : (sizeof(S) == 2 ? 6 : 5); }
+constexpr int liquid_pair_min_blocks() { return PAR == 0 ? 4 : (sizeof(S) == 2 ? 7 : 5); }
 
 // Stream and collide one pair (x even, x + 1) of row `row`; liq: bit 0 cell
 // x liquid, bit 1 cell x + 1 liquid. `interior`: every neighbour of both
