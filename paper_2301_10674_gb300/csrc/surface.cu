@@ -70,8 +70,8 @@ __global__ void k_normals(Dev s, float4* out) {
 // whether a wall or solid cell lies in the block, and sum the Parker-Youngs
 // gradient from the same values (walls and solids taking the centre value).
 // The Parker-Youngs normal is both the fallback (wall or solid in the block,
-// raw length outside [1/2, 2]) and the judge (network normal more than 30
-// degrees away). out[c] = (n, curvature), curvature 0 where the fallback is
+// raw length outside [1/2, 2]) and the check on the network (its normal more
+// than 30 degrees away falls back too). out[c] = (n, curvature), curvature 0 where the fallback is
 // taken.
 __global__ void __launch_bounds__(128) k_mlp_normals(Dev s, float4* out) {
     const int count = *s.wl_count;
