@@ -111,6 +111,23 @@ def _dist():
     return world, rank, local
 
 
+def _max_over_ranks(x: float, device: str) -> float:
+    """The largest value over the ranks of the process group (x alone
+    without one): the timing of a multi-rank run is its slowest rank's."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _throughput(world: int, ncell: int, steps: int, seconds: float) -> float:
+    """Whole-job MLUPS: every rank updates its own lattice of ncell cells."""
+    return world * ncell * steps / seconds / 1e6
+
+
 def _workload(name: str, rank: int):
     from paper_2301_10674_gb300 import workloads as W
     w = W.WORKLOADS[name]()
@@ -253,11 +270,7 @@ def timed_run(args, w, storage_name, theta, stream, local, barrier, world):
                    "max": round(float(bed_h.max()), 4), "ms_per_call": round(bed_ms, 3)}}
     sim.close()
     del sim
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        out["ms"] = float(tt.item())
+    out["ms"] = _max_over_ranks(ms, "cuda")
     return out
 
 
@@ -307,7 +320,7 @@ def run_ours(args, world, rank, local):
     if args.compare and (args.storage != "fp32" or args.normals != "fd"):
         base = timed_run(args, w, "fp32", None, stream, local, barrier, world)
 
-    value = world * ncell * args.steps / (head["ms"] / 1e3) / 1e6
+    value = _throughput(world, ncell, args.steps, head["ms"] / 1e3)
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, w, STORAGE[args.storage], theta, stream, world)
@@ -324,7 +337,7 @@ def run_ours(args, world, rank, local):
     form = f"{args.storage}+{'learned' if theta is not None else 'fd'}-normal"
     comparison = None
     if base is not None:
-        vb = world * ncell * args.steps / (base["ms"] / 1e3) / 1e6
+        vb = _throughput(world, ncell, args.steps, base["ms"] / 1e3)
         dcol = np.abs(head["column"] - base["column"])
         comparison = {
             "form": "fp32+fd-normal", "value": round(vb, 2), "unit": UNIT,
@@ -390,15 +403,10 @@ def run_e2e(args, w, storage, theta, stream, world):
         diag[:] = out
     F.fslbm_destroy(h)
     torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([dt], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dt = float(t.item())
+    dt = _max_over_ranks(time.perf_counter() - t0, "cuda")
     h2d = xyz.nbytes + rad.nbytes + fix.nbytes + __import__("ctypes").sizeof(params) + \
         (0 if bits is None else bits.nbytes)
-    return {"value": round(world * w.ncells * args.steps / dt / 1e6, 2), "unit": UNIT,
+    return {"value": round(_throughput(world, w.ncells, args.steps, dt), 2), "unit": UNIT,
             "h2d_bytes_per_step": round(h2d / args.steps, 1), "d2h_bytes_per_step": 64,
             "seconds": round(dt, 3),
             "note": "create + particle bed (and learned-normal weights) from pinned host memory + per step "
