@@ -86,6 +86,7 @@ def lib():
         L.orc_pool.restype = ctypes.c_double
         L.orc_pool.argtypes = [ctypes.c_void_p]
         L.orc_reduce.argtypes = [ctypes.c_void_p, dp]
+        L.orc_set_gravity.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_double]
         L.orc_collide.argtypes = [dp, dp, ctypes.c_double, dp]
         L.orc_feq.argtypes = [ctypes.c_double, dp, dp]
         L.orc_normal_stencil.argtypes = [dp, dp]
@@ -216,6 +217,11 @@ class Oracle:
     @property
     def pool(self) -> float:
         return lib().orc_pool(self._h)
+
+    def set_gravity(self, g) -> None:
+        """Body-force acceleration for the following steps (fluid and particles)."""
+        self.params.g = tuple(float(v) for v in g)
+        lib().orc_set_gravity(self._h, *self.params.g)
 
     def reduce(self) -> np.ndarray:
         out = np.zeros(8, np.float64)

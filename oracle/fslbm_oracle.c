@@ -1302,6 +1302,15 @@ int orc_nparticles(const orc* o) { return o->np; }
 long orc_violations(const orc* o) { return o->invariant_violations; }
 double orc_pool(const orc* o) { return o->pool; }
 
+/* Body-force acceleration (gravity) for the following steps: the fluid's
+ * forcing and the particles' weight both read it. */
+void orc_set_gravity(orc* o, double gx, double gy, double gz)
+{
+    o->p.g[0] = gx;
+    o->p.g[1] = gy;
+    o->p.g[2] = gz;
+}
+
 /* Diagnostics: [0] liquid mass sum_L rho + sum_I m + pool, [1..3] fluid
  * momentum sum rho u over liquid and interface cells, [4] fill-weighted bulk
  * velocity sum phi rho u_x / sum phi rho, [5] interface cell count,

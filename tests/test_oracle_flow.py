@@ -126,3 +126,23 @@ def test_standing_gravity_wave_dispersion():
     r64 = _wave_period_ratio(64)
     assert abs(r64 - 1) < 0.1
     assert abs(r64 - 1) < 0.5 * abs(r32 - 1)
+
+
+def test_flow_rate_controller_settles_on_the_film_force():
+    """The body-force controller (Section 3.1; law of the flow_control module)
+    on a gravity-free start: it must reach the bulk velocity asked for, with
+    g_x at the value the half-Poiseuille film needs for it, 3 nu U / H^2."""
+    from oracle import flow_control as FC
+    om, nz = 1.0, 24
+    o = O.Oracle(O.OracleParams(nx=1, ny=1, nz=nz, periodic=(1, 1, 0), omega=om, g=(0.0, 0, 0),
+                                liquid_height=16.0))
+    nu = (1 / om - 0.5) / 3
+    H = o.get(O.F_PHI)[:, 0, 0].sum()
+    target = 2e-4
+    gain = 0.15 * 3 * nu / H ** 2
+    hist = FC.run_controlled(o, 12000, target, gain, 100)
+    assert hist[0, 2] == 0.0 and hist[0, 1] == pytest.approx(gain * target, rel=1e-12)   # from rest
+    g_film = 3 * nu * target / H ** 2
+    assert abs(hist[-1, 1] / g_film - 1) < 5e-3
+    assert abs(hist[-1, 2] / target - 1) < 1e-3
+    assert np.all(np.abs(hist[-10:, 2] / target - 1) < 2e-3)
