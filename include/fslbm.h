@@ -196,6 +196,25 @@ int fslbm_set_fields(fslbm* s, uint32_t field_mask, const void* const* src, int 
  * out[7] mass pool. Synchronises the stream. */
 int fslbm_reduce(fslbm* s, double out[8]);
 
+/* Body-force acceleration g (lattice units): drives the fluid (Section 2.1
+ * forcing) and weighs the particles, from the next step on. Each component
+ * must be finite and within [-1, 1]; else FSLBM_EINVAL. No synchronisation. */
+int fslbm_set_body_force(fslbm* s, const double g[3]);
+int fslbm_get_body_force(const fslbm* s, double g[3]);
+
+/* Flow-rate control (Section 3.1: the streamwise body force is adjusted
+ * during the run to hold the bulk flow rate). The paper gives no control
+ * law; this one is an integral controller: after every `interval` completed
+ * steps of fslbm_step, with U the fill-weighted bulk velocity of the state
+ * reached (fslbm_reduce out[4]), g_x <- g_x + gain (target_u - U). Each
+ * update costs one reduction over the lattice and a synchronisation of the
+ * stream. In a steady laminar film of depth H it settles at
+ * g_x = 3 nu target_u / H^2.
+ *   interval  steps between updates; 0 switches the control off
+ *   gain      >= 0, in acceleration per unit of velocity error
+ * Invalid arguments: FSLBM_EINVAL. */
+int fslbm_set_flow_control(fslbm* s, double target_u, double gain, int64_t interval);
+
 /* Bed topography (Section 3.2): phi_b(x, z), the fraction of the cells of
  * the column (x, ., z) covered by a particle (y-averaged solid fraction), and
  * the bed height h_b(x), the z at which phi_b crosses phi_b_level (the paper

@@ -40,6 +40,9 @@ struct fslbm {
     int64_t launches;
     unsigned long long* counts4;
     double* bed;                   // nx * nz + nx doubles: phi_b(x, z), then h_b(x)
+    // flow-rate control: target bulk velocity, gain, steps between updates (0: off)
+    double ctrl_target, ctrl_gain;
+    int64_t ctrl_interval;
     MlpBf16* mlp_dev;              // operand copies of the learned normal
     unsigned long long* mlp_stats;
 };
@@ -168,6 +171,8 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     s->launches = 0;
     s->counts4 = nullptr;
     s->bed = nullptr;
+    s->ctrl_target = s->ctrl_gain = 0.0;
+    s->ctrl_interval = 0;
     s->mlp_dev = nullptr;
     s->mlp_stats = nullptr;
     Dev& d = s->d;
@@ -425,10 +430,22 @@ int fslbm_step(fslbm* s, int64_t n_steps) {
         nl += launch_classify(d, st);
         nl += launch_pool_spread(d, st);
         nl += launch_normals(d, d.nrm, st);
-        if (s->timing) s->launches += nl;
         s->last_parity = parity;
         s->have_prev = 1;
         s->steps++;
+        if (s->ctrl_interval > 0 && s->steps % s->ctrl_interval == 0) {
+            // flow-rate control: g_x += gain (U_target - U), U the fill-weighted
+            // bulk velocity of the state just reached
+            double r[8];
+            launch_reduce(d, s->last_parity, s->red, st);
+            nl += 2;
+            cudaMemcpyAsync(r, s->red, sizeof(r), cudaMemcpyDeviceToHost, st);
+            launch_check(s);
+            if (sync_check(s)) return s->host_err;
+            d.gxd = d.gxd + s->ctrl_gain * (s->ctrl_target - r[4]);
+            d.gx = (float)d.gxd;
+        }
+        if (s->timing) s->launches += nl;
     }
     return launch_check(s);
 }
@@ -605,6 +622,30 @@ int fslbm_cell_counts(fslbm* s, int64_t counts[4]) {
     int rc = sync_check(s);
     for (int k = 0; k < 4; ++k) counts[k] = (int64_t)h[k];
     return rc;
+}
+
+int fslbm_set_body_force(fslbm* s, const double g[3]) {
+    if (!s || !g) return FSLBM_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (!(g[a] == g[a]) || g[a] > 1.0 || g[a] < -1.0) return FSLBM_EINVAL;
+    Dev& d = s->d;
+    d.gxd = g[0]; d.gyd = g[1]; d.gzd = g[2];
+    d.gx = (float)g[0]; d.gy = (float)g[1]; d.gz = (float)g[2];
+    return FSLBM_OK;
+}
+
+int fslbm_get_body_force(const fslbm* s, double g[3]) {
+    if (!s || !g) return FSLBM_EINVAL;
+    g[0] = s->d.gxd; g[1] = s->d.gyd; g[2] = s->d.gzd;
+    return FSLBM_OK;
+}
+
+int fslbm_set_flow_control(fslbm* s, double target_u, double gain, int64_t interval) {
+    if (!s || interval < 0 || !(target_u == target_u) || !(gain == gain) || gain < 0.0) return FSLBM_EINVAL;
+    s->ctrl_target = target_u;
+    s->ctrl_gain = gain;
+    s->ctrl_interval = interval;
+    return FSLBM_OK;
 }
 
 int fslbm_bed_height(fslbm* s, double phi_b, double* h, double* phi, int on_device) {

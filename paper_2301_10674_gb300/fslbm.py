@@ -47,7 +47,8 @@ EXPORTED = (
     "fslbm_num_spheres", "fslbm_invariant_violations", "fslbm_timing", "fslbm_timing_read",
     "fslbm_cell_counts", "fslbm_reduce_fields_noalloc", "fslbm_destroy", "fslbm_strerror",
     "fslbm_set_normal_model", "fslbm_normal_stats", "fslbm_mlp_stencils", "fslbm_mlp_gradient",
-    "fslbm_mlp_train", "fslbm_mlp_infer", "fslbm_bed_height",
+    "fslbm_mlp_train", "fslbm_mlp_infer", "fslbm_bed_height", "fslbm_set_body_force",
+    "fslbm_get_body_force", "fslbm_set_flow_control",
 )
 
 MLP_NPARAM = 6212
@@ -120,6 +121,9 @@ def load():
                                     ctypes.POINTER(ctypes.c_int64)]
     L.fslbm_cell_counts.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
     L.fslbm_bed_height.argtypes = [vp, ctypes.c_double, vp, vp, ctypes.c_int]
+    L.fslbm_set_body_force.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    L.fslbm_get_body_force.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    L.fslbm_set_flow_control.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int64]
     L.fslbm_reduce_fields_noalloc.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), vp, vp]
     L.fslbm_set_normal_model.argtypes = [vp, vp, ctypes.c_int64]
     L.fslbm_normal_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
@@ -409,6 +413,21 @@ class Simulation:
         _check(load().fslbm_timing_read(self.h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(k)),
                "fslbm_timing_read")
         return ms.value, n.value, k.value
+
+    def body_force(self) -> np.ndarray:
+        g = np.zeros(3)
+        _check(load().fslbm_get_body_force(self.h, g.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "fslbm_get_body_force")
+        return g
+
+    def set_body_force(self, g) -> None:
+        a = np.ascontiguousarray(g, dtype=np.float64)
+        _check(load().fslbm_set_body_force(self.h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "fslbm_set_body_force")
+
+    def set_flow_control(self, target_u: float, gain: float, interval: int) -> None:
+        _check(load().fslbm_set_flow_control(self.h, float(target_u), float(gain), int(interval)),
+               "fslbm_set_flow_control")
 
     def bed_height(self, level: float = 0.3, with_fraction: bool = False):
         """Bed height h_b(x) (nx,) of Section 3.2 at solid fraction `level`;

@@ -370,3 +370,30 @@ def test_bed_height_matches_oracle():
     with pytest.raises(F.FslbmError):
         sim.bed_height(0.0)
     sim.close()
+
+
+def test_flow_rate_control_matches_oracle():
+    """Flow-rate control (Section 3.1) of a laminar film started from rest:
+    after every 500 steps the library's body force equals the oracle
+    controller's on the same film (same law, same update points), and the
+    bulk velocities agree."""
+    from oracle import flow_control as FC
+    w = W.Workload(name="film", nx=8, ny=4, nz=24, periodic=(1, 1, 0), tau=1.0, g=(0.0, 0.0, 0.0),
+                   liquid_height=16.0, bed="none", seed=1).generate()
+    sim = _sim(w, spheres=False)
+    o = oracle_from_workload(w, spheres=False)
+    nu = (1.0 - 0.5) / 3
+    target, gain, interval = 2e-4, 0.15 * 3 * nu / 16.0 ** 2, 100
+    sim.set_flow_control(target, gain, interval)
+    for _ in range(6):
+        sim.step(500)
+        hist = FC.run_controlled(o, 500, target, gain, interval)
+        assert sim.body_force()[0] == pytest.approx(hist[-1, 1], rel=2e-3)
+    assert sim.reduce()[4] == pytest.approx(o.reduce()[4], rel=2e-3)
+    with pytest.raises(F.FslbmError):
+        sim.set_flow_control(target, -1.0, interval)
+    sim.set_flow_control(0.0, 0.0, 0)
+    g = sim.body_force()
+    sim.step(100)
+    assert np.array_equal(sim.body_force(), g)          # control off: the force stays
+    sim.close()
