@@ -25,7 +25,7 @@ _lock = threading.Lock()
 _lib = None
 
 # field identifiers of orc_get / orc_set
-F_PDF, F_TYPE, F_MASS, F_PHI, F_RHO, F_U, F_NORMAL, F_OWNER = range(8)
+F_PDF, F_TYPE, F_MASS, F_PHI, F_RHO, F_U, F_NORMAL, F_OWNER, F_CURV = range(9)
 P_X, P_U, P_W, P_F, P_T, P_R = 16, 17, 18, 19, 20, 21
 
 GAS, LIQUID, INTERFACE, SOLID = 0, 1, 2, 3
@@ -61,6 +61,7 @@ class _Params(ctypes.Structure):
         ("collision_time", ctypes.c_double),
         ("dem_substeps", ctypes.c_int),
         ("link_mass_correction", ctypes.c_int),
+        ("sigma", ctypes.c_double),
     ]
 
 
@@ -120,6 +121,7 @@ class OracleParams:
     collision_time: float = 24.0
     dem_substeps: int = 10
     link_mass_correction: int = 1
+    sigma: float = 0.0
 
     def _c(self) -> _Params:
         p = _Params()
@@ -139,6 +141,7 @@ class OracleParams:
         p.collision_time = self.collision_time
         p.dem_substeps = self.dem_substeps
         p.link_mass_correction = self.link_mass_correction
+        p.sigma = self.sigma
         return p
 
 

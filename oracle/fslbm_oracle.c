@@ -68,6 +68,8 @@ typedef struct {
     int dem_substeps;         /* DEM sub-steps per LBM step */
     int link_mass_correction; /* 1: net moving-bounce-back injection into liquid
                                  cells is taken from the pool (R-12a) */
+    double sigma;             /* surface tension: the gas-side reconstruction
+                                 density is rho_gas + 6 sigma kappa (R-21) */
 } orc_params;
 
 typedef struct {
@@ -84,6 +86,7 @@ typedef struct orc {
     double *f, *ft;           /* post-collision state, scratch */
     uint8_t *type;
     double *mass, *rho, *u, *phi, *nrm;
+    double *curv;             /* interface curvature of the learned model, 0 elsewhere */
     int *owner;
     double pool;
     long step;
@@ -368,7 +371,7 @@ static double bf16_round(double a)
     return ldexp(nearbyint(ldexp(m, 8)), e - 8);
 }
 
-static void mlp_normal(const orc* o, long cell, const double* phi, double n[3])
+static void mlp_normal(const orc* o, long cell, const double* phi, double n[3], double* kappa)
 {
     int x, y, z;
     coords(o, cell, &x, &y, &z);
@@ -412,11 +415,15 @@ static void mlp_normal(const orc* o, long cell, const double* phi, double n[3])
     double m[3] = {out[0] / len, out[1] / len, out[2] / len};
     if (m[0] * fd[0] + m[1] * fd[1] + m[2] * fd[2] < 0.8660254037844386) return;   /* cos 30 deg */
     n[0] = m[0]; n[1] = m[1]; n[2] = m[2];
+    if (kappa) *kappa = out[3];
 }
 
-static void normal_at(const orc* o, long cell, const double* phi, double n[3])
+/* Interface normal, and (kappa not NULL) the curvature: the learned model's
+ * where its normal is taken, 0 where the finite-difference normal stands */
+static void normal_at(const orc* o, long cell, const double* phi, double n[3], double* kappa)
 {
-    if (o->mlp) mlp_normal(o, cell, phi, n);
+    if (kappa) *kappa = 0.0;
+    if (o->mlp) mlp_normal(o, cell, phi, n, kappa);
     else pyn_normal(o, cell, phi, n);
 }
 
@@ -465,6 +472,7 @@ orc* orc_create(const orc_params* p)
     o->u = (double*)calloc((size_t)n * 3, sizeof(double));
     o->phi = (double*)calloc((size_t)n, sizeof(double));
     o->nrm = (double*)calloc((size_t)n * 3, sizeof(double));
+    o->curv = (double*)calloc((size_t)n, sizeof(double));
     o->owner = (int*)malloc((size_t)n * sizeof(int));
     for (long i = 0; i < n; ++i) o->owner[i] = -1;
 
@@ -499,7 +507,7 @@ orc* orc_create(const orc_params* p)
         refresh_phi(o, i);
     }
     for (long i = 0; i < n; ++i)
-        if (o->type[i] == T_IFC) normal_at(o, i, o->phi, &o->nrm[3 * i]);
+        if (o->type[i] == T_IFC) normal_at(o, i, o->phi, &o->nrm[3 * i], &o->curv[i]);
     return o;
 }
 
@@ -547,8 +555,8 @@ int orc_init_surface(orc* o, const double* H)
         refresh_phi(o, i);
     }
     for (long i = 0; i < n; ++i) {
-        if (o->type[i] == T_IFC) normal_at(o, i, o->phi, &o->nrm[3 * i]);
-        else o->nrm[3 * i] = o->nrm[3 * i + 1] = o->nrm[3 * i + 2] = 0.0;
+        if (o->type[i] == T_IFC) normal_at(o, i, o->phi, &o->nrm[3 * i], &o->curv[i]);
+        else o->nrm[3 * i] = o->nrm[3 * i + 1] = o->nrm[3 * i + 2] = o->curv[i] = 0.0;
     }
     free(fill);
     return 0;
@@ -558,7 +566,7 @@ void orc_destroy(orc* o)
 {
     if (!o) return;
     free(o->f); free(o->ft); free(o->type); free(o->mass); free(o->rho); free(o->u);
-    free(o->phi); free(o->nrm); free(o->owner);
+    free(o->phi); free(o->nrm); free(o->curv); free(o->owner);
     free(o->X); free(o->U); free(o->W); free(o->R); free(o->M); free(o->I); free(o->fixed);
     free(o->Fh); free(o->Th); free(o->Fp); free(o->Tp); free(o->hist);
     free(o->fixmetric); free(o->fixowner); free(o->mlp);
@@ -585,7 +593,7 @@ int orc_set_mlp(orc* o, const double* theta, int bf16)
     }
     o->mlp_bf16 = bf16;
     for (long i = 0; i < o->n; ++i)
-        if (o->type[i] == T_IFC) normal_at(o, i, o->phi, &o->nrm[3 * i]);
+        if (o->type[i] == T_IFC) normal_at(o, i, o->phi, &o->nrm[3 * i], &o->curv[i]);
     return 0;
 }
 
@@ -687,7 +695,7 @@ int orc_add_spheres(orc* o, int n, const double* xyz, const double* radius, cons
     }
     free(own);
     for (long i = 0; i < o->n; ++i)
-        if (o->type[i] == T_IFC) normal_at(o, i, o->phi, &o->nrm[3 * i]);
+        if (o->type[i] == T_IFC) normal_at(o, i, o->phi, &o->nrm[3 * i], &o->curv[i]);
     return 0;
 }
 
@@ -898,7 +906,8 @@ static void one_step(orc* o)
                 if (t != T_IFC) viol++;
                 if (!have_rec) {
                     post_velocity(o, fs, &rr, ur);
-                    orc_feq(P->rho_gas, ur, feqG);
+                    /* gas pressure plus the Laplace pressure 2 sigma kappa (Section 2.1) */
+                    orc_feq(P->rho_gas + 6.0 * P->sigma * o->curv[i], ur, feqG);
                     have_rec = 1;
                 }
                 fin[q] = feqG[q] + feqG[qb] - fs[qb];
@@ -990,7 +999,7 @@ static void one_step(orc* o)
     /* S4: normals of the new fill levels */
     double* n1 = (double*)calloc((size_t)3 * n, sizeof(double));
     for (long i = 0; i < n; ++i)
-        if (o->type[i] == T_IFC) normal_at(o, i, o->phi, &n1[3 * i]);
+        if (o->type[i] == T_IFC) normal_at(o, i, o->phi, &n1[3 * i], NULL);
 
     /* S5: conversion candidates (R-7), from a snapshot of the cell types */
     uint8_t* conv = (uint8_t*)calloc((size_t)n, 1);
@@ -1194,8 +1203,8 @@ static void one_step(orc* o)
     }
     /* S13: normals for the next step's boundary condition */
     for (long i = 0; i < n; ++i) {
-        if (o->type[i] == T_IFC) normal_at(o, i, o->phi, &o->nrm[3 * i]);
-        else o->nrm[3 * i] = o->nrm[3 * i + 1] = o->nrm[3 * i + 2] = 0.0;
+        if (o->type[i] == T_IFC) normal_at(o, i, o->phi, &o->nrm[3 * i], &o->curv[i]);
+        else o->nrm[3 * i] = o->nrm[3 * i + 1] = o->nrm[3 * i + 2] = o->curv[i] = 0.0;
     }
     o->step++;
 }
@@ -1208,7 +1217,7 @@ void orc_step(orc* o, int nsteps)
 /* --------------------------------------------------------- accessors */
 
 enum {
-    F_PDF = 0, F_TYPE = 1, F_MASS = 2, F_PHI = 3, F_RHO = 4, F_U = 5, F_NORMAL = 6, F_OWNER = 7,
+    F_PDF = 0, F_TYPE = 1, F_MASS = 2, F_PHI = 3, F_RHO = 4, F_U = 5, F_NORMAL = 6, F_OWNER = 7, F_CURV = 8,
     P_X = 16, P_U = 17, P_W = 18, P_F = 19, P_T = 20, P_R = 21
 };
 
@@ -1240,6 +1249,7 @@ int orc_get(const orc* o, int which, void* dst)
         return 0;
     }
     case F_OWNER: memcpy(dst, o->owner, sizeof(int) * n); return 0;
+    case F_CURV: memcpy(dst, o->curv, sizeof(double) * n); return 0;
     case P_X: memcpy(dst, o->X, sizeof(double) * 3 * o->np); return 0;
     case P_U: memcpy(dst, o->U, sizeof(double) * 3 * o->np); return 0;
     case P_W: memcpy(dst, o->W, sizeof(double) * 3 * o->np); return 0;
@@ -1275,7 +1285,7 @@ int orc_set(orc* o, int which, const void* src)
         memcpy(o->mass, src, sizeof(double) * n);
         for (long i = 0; i < n; ++i) refresh_phi(o, i);
         for (long i = 0; i < n; ++i)
-            if (o->type[i] == T_IFC) normal_at(o, i, o->phi, &o->nrm[3 * i]);
+            if (o->type[i] == T_IFC) normal_at(o, i, o->phi, &o->nrm[3 * i], &o->curv[i]);
         return 0;
     case P_U: memcpy(o->U, src, sizeof(double) * 3 * o->np); return 0;
     case P_W: memcpy(o->W, src, sizeof(double) * 3 * o->np); return 0;
