@@ -88,11 +88,15 @@ def test_walls_in_every_axis():
     sim.close()
 
 
-def test_free_surface_without_particles():
+@pytest.mark.parametrize("recon", [1, 0])
+def test_free_surface_without_particles(recon):
     """Wavy free surface over a no-slip floor: reconstruction, mass exchange,
-    conversions and excess mass, with exact cell types every 10 steps."""
+    conversions and excess mass, with exact cell types every 10 steps; with
+    recon = 0 the variant that rebuilds only the PDFs streaming in from gas
+    cells (no normal-based rebuild)."""
     w = W.tiny()
     w.bed = "none"
+    w.reconstruct_normal = recon
     w.generate()
     sim = _sim(w)
     o = oracle_from_workload(w)
