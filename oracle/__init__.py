@@ -62,6 +62,7 @@ class _Params(ctypes.Structure):
         ("dem_substeps", ctypes.c_int),
         ("link_mass_correction", ctypes.c_int),
         ("sigma", ctypes.c_double),
+        ("excess_even", ctypes.c_int),
     ]
 
 
@@ -122,6 +123,7 @@ class OracleParams:
     dem_substeps: int = 10
     link_mass_correction: int = 1
     sigma: float = 0.0
+    excess_even: int = 0
 
     def _c(self) -> _Params:
         p = _Params()
@@ -142,6 +144,7 @@ class OracleParams:
         p.dem_substeps = self.dem_substeps
         p.link_mass_correction = self.link_mass_correction
         p.sigma = self.sigma
+        p.excess_even = self.excess_even
         return p
 
 

@@ -70,6 +70,8 @@ typedef struct {
                                  cells is taken from the pool (R-12a) */
     double sigma;             /* surface tension: the gas-side reconstruction
                                  density is rho_gas + 6 sigma kappa (R-21) */
+    int excess_even;          /* 1: excess mass split evenly over the receivers
+                                 instead of by the normal weights (R-8 variant) */
 } orc_params;
 
 typedef struct {
@@ -1100,7 +1102,7 @@ static void one_step(orc* o)
         }
         if (nrec == 0) { o->pool += ex; continue; }
         for (int k = 0; k < nrec; ++k) {
-            double share = wsum > 0.0 ? ex * wts[k] / wsum : ex / nrec;
+            double share = (wsum > 0.0 && !P->excess_even) ? ex * wts[k] / wsum : ex / nrec;
             o->mass[recv[k]] += share;
         }
     }

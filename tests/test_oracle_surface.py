@@ -173,3 +173,30 @@ def test_liquid_mass_conserved_with_moving_bed():
     o.step(60)
     assert abs(o.reduce()[0] - m0) < 1e-11 * m0
     assert np.abs(o.get(O.P_X) - w.xyz).max() > 1e-3      # the bed did move
+
+
+def test_even_excess_mass_variant():
+    """The R-8 variant that splits the excess mass of a converting cell evenly
+    over its receivers: the liquid mass is still kept to round-off and the
+    liquid/gas separation holds, while the interface masses differ from the
+    normal-weighted rule once cells have converted."""
+    w = W.tiny()
+    w.bed = "none"
+    w.generate()
+    w.g = (2e-5, 0.0, -1e-5)
+    h = 20.0 + 3.0 * np.cos(2 * np.pi * (np.arange(w.nx) + 0.5) / w.nx) \
+        + 1.0 * np.sin(2 * np.pi * (np.arange(w.ny)[:, None] + 0.5) / w.ny)
+    masses = {}
+    for even in (0, 1):
+        o = O.Oracle(O.OracleParams(nx=w.nx, ny=w.ny, nz=w.nz, periodic=w.periodic, omega=w.omega, g=w.g,
+                                    rho_gas=w.rho_gas, liquid_height=w.liquid_height, excess_even=even))
+        o.init_surface(h)
+        m0 = o.reduce()[0]
+        types0 = o.get(O.F_TYPE)
+        o.step(120)
+        assert abs(o.reduce()[0] - m0) / m0 < 1e-12
+        t = o.get(O.F_TYPE)
+        assert (t != types0).sum() > 0
+        assert o.violations == 0 and _liquid_touches_gas(t, w.periodic) == 0
+        masses[even] = o.get(O.F_MASS)
+    assert np.abs(masses[0] - masses[1]).max() > 1e-6
