@@ -55,3 +55,12 @@ def test_invalid_parameters_are_rejected_before_any_device_work(lib):
     h = ctypes.c_void_p()
     assert lib.fslbm_create(ctypes.byref(p), None, ctypes.byref(h)) == -1
     assert lib.fslbm_strerror(-3).decode() == "device list capacity exceeded"
+
+
+def test_new_entry_points_reject_a_missing_handle(lib):
+    g = (ctypes.c_double * 3)(0.0, 0.0, 0.0)
+    h = (ctypes.c_double * 4)()
+    assert lib.fslbm_bed_height(None, 0.3, ctypes.cast(h, ctypes.c_void_p), None, 0) == -1
+    assert lib.fslbm_set_body_force(None, g) == -1
+    assert lib.fslbm_get_body_force(None, g) == -1
+    assert lib.fslbm_set_flow_control(None, 1e-3, 1e-4, 100) == -1
