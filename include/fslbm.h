@@ -52,6 +52,7 @@ extern "C" {
 #define FSLBM_EDEVICE (-5)     /* CUDA runtime error */
 #define FSLBM_ESTATE (-6)      /* call not valid in the current state */
 #define FSLBM_EINVARIANT (-7)  /* a liquid cell touched a gas cell */
+#define FSLBM_ETIMEOUT (-8)    /* a bounded device wait gave up */
 
 /* boundary flags: a set bit makes the axis periodic, a clear bit puts no-slip
  * walls (halfway bounce-back, Section 2.1) on both of its faces */
@@ -209,9 +210,11 @@ int fslbm_get_body_force(const fslbm* s, double g[3]);
  * reached (fslbm_reduce out[4]), g_x <- g_x + gain (target_u - U). Each
  * update costs one reduction over the lattice and a synchronisation of the
  * stream. In a steady laminar film of depth H it settles at
- * g_x = 3 nu target_u / H^2.
+ * g_x = 3 nu target_u / H^2. The updated g_x is clamped to [-1, 1], the range
+ * fslbm_set_body_force accepts; a non-finite update sets FSLBM_ENAN.
+ *   target_u  finite
  *   interval  steps between updates; 0 switches the control off
- *   gain      >= 0, in acceleration per unit of velocity error
+ *   gain      finite, >= 0, in acceleration per unit of velocity error
  * Invalid arguments: FSLBM_EINVAL. */
 int fslbm_set_flow_control(fslbm* s, double target_u, double gain, int64_t interval);
 
@@ -253,6 +256,18 @@ int64_t fslbm_invariant_violations(fslbm* s);
 int fslbm_timing(fslbm* s, int on);
 int fslbm_timing_read(fslbm* s, double* sweep_ms, int64_t* sweeps, int64_t* kernel_launches);
 
+/* Test hook of the device error path. Every wait of a kernel on an
+ * asynchronous copy (the bulk copies of the staged stream-collide sweep) is
+ * bounded: after `polls` unsuccessful polls it gives up, sets the sticky
+ * error FSLBM_ETIMEOUT, and its kernel returns early (still waiting, with the
+ * default bound, for the copies it has issued, so that none lands after the
+ * block has left). The default, and the maximum, is 4194304 polls; 0 makes
+ * every such wait give up at once, which lets a test check that a wait that
+ * runs out reaches the caller as FSLBM_ETIMEOUT with the context still
+ * usable. Takes effect from the next fslbm_step. FSLBM_EINVAL outside
+ * [0, 4194304]. */
+int fslbm_set_wait_limit(fslbm* s, int64_t polls);
+
 /* Number of cells of each type (gas, liquid, interface, solid) in
  * counts[0..3]. Synchronises the stream. */
 int fslbm_cell_counts(fslbm* s, int64_t counts[4]);
@@ -277,8 +292,12 @@ int fslbm_cell_counts(fslbm* s, int64_t counts[4]);
  * ncells above 4096 * 65536 (the scratch holds 4096 blocks of partial sums),
  * FSLBM_EDEVICE if the scratch address cannot be obtained or a launch fails.
  * The call only enqueues work; read out after synchronising the stream. The
- * first call on a device looks up the scratch address there (make that call
- * before any stream capture). Every call shares the one scratch array, which
+ * first call on a device loads the library's device code there, if nothing
+ * has yet, to find the scratch array's address (make that first call before
+ * any stream capture); every call looks the address up again, which is a
+ * host-side query, so a device reset between calls does no harm. Pending
+ * launch errors of earlier, unrelated work are cleared at entry and not
+ * reported by this call. Every call shares the one scratch array, which
  * keeps the last call's partial sums: calls whose kernels overlap on the GPU
  * (different streams without ordering) race on it. Each call overwrites every
  * partial sum it reads, so nothing needs clearing between calls, and the sums

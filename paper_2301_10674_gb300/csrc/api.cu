@@ -70,6 +70,7 @@ int map_device_error(int bits) {
     if (bits & ERR_NAN) return FSLBM_ENAN;
     if (bits & (ERR_CAPACITY | ERR_HISTORY | ERR_DISPLACEMENT)) return FSLBM_ECAPACITY;
     if (bits & ERR_INVARIANT) return FSLBM_EINVARIANT;
+    if (bits & ERR_TIMEOUT) return FSLBM_ETIMEOUT;
     return FSLBM_OK;
 }
 
@@ -135,6 +136,7 @@ const char* fslbm_strerror(int code) {
     case FSLBM_EDEVICE: return "CUDA runtime error";
     case FSLBM_ESTATE: return "call not valid in the current state";
     case FSLBM_EINVARIANT: return "liquid cell next to a gas cell";
+    case FSLBM_ETIMEOUT: return "a bounded device wait gave up";
     default: return "unknown error";
     }
 }
@@ -196,6 +198,7 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     d.recon_normal = p->reconstruct_normal;
     d.link_corr = p->link_mass_correction;
     d.idx32 = 27LL * n < (1LL << 32) ? 1 : 0;
+    d.wait_limit = WAIT_LIMIT_DEFAULT;
     d.storage = p->storage;
     d.rho_p = p->rho_p;
     d.restitution = p->restitution;
@@ -442,8 +445,15 @@ int fslbm_step(fslbm* s, int64_t n_steps) {
             cudaMemcpyAsync(r, s->red, sizeof(r), cudaMemcpyDeviceToHost, st);
             launch_check(s);
             if (sync_check(s)) return s->host_err;
-            d.gxd = d.gxd + s->ctrl_gain * (s->ctrl_target - r[4]);
-            d.gx = (float)d.gxd;
+            // kept within the range fslbm_set_body_force accepts
+            double gx = d.gxd + s->ctrl_gain * (s->ctrl_target - r[4]);
+            if (!std::isfinite(gx)) {
+                s->host_err = FSLBM_ENAN;
+                return s->host_err;
+            }
+            gx = gx > 1.0 ? 1.0 : (gx < -1.0 ? -1.0 : gx);
+            d.gxd = gx;
+            d.gx = (float)gx;
         }
         if (s->timing) s->launches += nl;
     }
@@ -641,7 +651,7 @@ int fslbm_get_body_force(const fslbm* s, double g[3]) {
 }
 
 int fslbm_set_flow_control(fslbm* s, double target_u, double gain, int64_t interval) {
-    if (!s || interval < 0 || !(target_u == target_u) || !(gain == gain) || gain < 0.0) return FSLBM_EINVAL;
+    if (!s || interval < 0 || !std::isfinite(target_u) || !std::isfinite(gain) || gain < 0.0) return FSLBM_EINVAL;
     s->ctrl_target = target_u;
     s->ctrl_gain = gain;
     s->ctrl_interval = interval;
@@ -664,6 +674,12 @@ int fslbm_bed_height(fslbm* s, double phi_b, double* h, double* phi, int on_devi
     if (phi) cudaMemcpyAsync(phi, s->bed, nxz * sizeof(double), kind, s->st);
     launch_check(s);
     return sync_check(s);
+}
+
+int fslbm_set_wait_limit(fslbm* s, int64_t polls) {
+    if (!s || polls < 0 || polls > WAIT_LIMIT_DEFAULT) return FSLBM_EINVAL;
+    s->d.wait_limit = (int)polls;
+    return FSLBM_OK;
 }
 
 int fslbm_set_normal_model(fslbm* s, const uint16_t* w, int64_t n_params) {

@@ -45,6 +45,7 @@ enum : uint8_t { CV_TO_LIQ = 1, CV_TO_GAS = 2, CV_EVEN = 4 };
 enum : int { ERR_CAPACITY = 1, ERR_NAN = 2, ERR_INVARIANT = 4, ERR_HISTORY = 8, ERR_DISPLACEMENT = 16, ERR_TIMEOUT = 32 };
 
 constexpr int SP_TILE = 256;     // cells per x-tile of the staged even step
+constexpr int WAIT_LIMIT_DEFAULT = 1 << 22;   // polls of a bounded device wait
 
 constexpr int HIST_SLOTS = 16;   // tangential-spring history slots per particle
 constexpr int NB_SLOTS = 32;     // DEM neighbour-list slots per particle
@@ -61,6 +62,7 @@ struct Dev {
     int storage;
     int link_corr;     // net moving-bounce-back injection into liquid cells taken from the pool
     int idx32;         // 27 n < 2^32: PDF element indices fit 32 bits
+    int wait_limit;    // polls before a bounded device wait gives up
     // element offsets of an odd step for interior cells: the pull of
     // direction q reads f[cell + pull_off[q]], the push writes
     // f[cell + push_off[q]] (constant per launch, held in the parameter bank)

@@ -16,13 +16,10 @@ namespace {
 constexpr int NA_CHUNK = 65536;    // cells per block of the reduction
 constexpr int NA_PARTIALS = 4096;  // blocks of partial sums the scratch holds
 constexpr int NA_THREADS = 256;
-constexpr int NA_MAX_DEVICES = 64;
 
 // Scratch: one row of 4 partial sums per block. It lives as long as the
 // library is loaded on each device that uses it, and every call shares it.
 static __device__ __align__(256) double na_scratch[NA_PARTIALS * 4];
-
-double* na_ptr[NA_MAX_DEVICES] = {nullptr};
 
 // Each block reduces its own chunk of cells in a fixed order and stores one
 // row of partials; the final pass adds the rows in block order, so the result
@@ -73,26 +70,25 @@ extern "C" int fslbm_reduce_fields_noalloc(const double* pdf, const uint8_t* typ
                                            int64_t ncells, const double g[3], double* out, void* cuda_stream) {
     if (!pdf || !type || !mass || !g || !out || ncells <= 0) return FSLBM_EINVAL;
     if (ncells > (int64_t)NA_CHUNK * NA_PARTIALS) return FSLBM_ECAPACITY;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) {
+    // Device address of the scratch array on the current device. In host code
+    // na_scratch names a host-side stand-in, not device memory, so the address
+    // is looked up (a host-side table query once the device image is loaded;
+    // the first call on a device loads it). Looking it up on every call keeps
+    // no host state between calls, so a device reset in between does no harm
+    // and concurrent host threads share nothing.
+    double* scratch = nullptr;
+    if (cudaGetSymbolAddress(reinterpret_cast<void**>(&scratch), na_scratch) != cudaSuccess || !scratch) {
         cudaGetLastError();
         return FSLBM_EDEVICE;
     }
-    if (!na_ptr[dev]) {
-        // first call on this device: the address of the scratch array in its
-        // copy of the device image
-        double* p = nullptr;
-        if (cudaGetSymbolAddress(reinterpret_cast<void**>(&p), na_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return FSLBM_EDEVICE;
-        }
-        na_ptr[dev] = p;
-    }
+    // a launch error pending from earlier, unrelated work is not this call's
+    cudaGetLastError();
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const int blocks = (int)((ncells + NA_CHUNK - 1) / NA_CHUNK);
     // every block writes its own row, so nothing has to be cleared first
-    k_na_partials<<<blocks, NA_THREADS, 0, st>>>(pdf, type, mass, (long long)ncells, g[0], g[1], g[2], na_ptr[dev]);
-    k_na_final<<<1, 32, 0, st>>>(na_ptr[dev], blocks, out);
+    k_na_partials<<<blocks, NA_THREADS, 0, st>>>(pdf, type, mass, (long long)ncells, g[0], g[1], g[2], scratch);
+    if (cudaGetLastError() != cudaSuccess) return FSLBM_EDEVICE;
+    k_na_final<<<1, 32, 0, st>>>(scratch, blocks, out);
     if (cudaGetLastError() != cudaSuccess) return FSLBM_EDEVICE;
     return FSLBM_OK;
 }

@@ -357,9 +357,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
         : "memory");
     return ok != 0;
 }
-// bounded wait: false (and the sticky timeout bit) if the phase never completes
-__device__ __forceinline__ bool mbar_wait(const Dev& s, uint64_t* bar, unsigned parity) {
-    for (int it = 0; it < (1 << 22); ++it)
+// bounded wait: false (and the sticky timeout bit) if the phase has not
+// completed after `limit` polls
+__device__ __forceinline__ bool mbar_wait(const Dev& s, uint64_t* bar, unsigned parity, int limit) {
+    for (int it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     set_error(s, ERR_TIMEOUT);
     return false;
@@ -466,7 +467,7 @@ __global__ void __launch_bounds__(SP_TILE / 2, 6) k_liquid_staged_pair(Dev s) {
     for (int i = 0; i < mine; ++i) {
         const int st = i % STAGES;
         const unsigned ph = (unsigned)(i / STAGES) & 1u;
-        const bool ok = mbar_wait(s, &full[st], ph);
+        const bool ok = mbar_wait(s, &full[st], ph, s.wait_limit);
         const unsigned char* stage = smem_raw + st * L::STAGE_BYTES;
         const S* buf = reinterpret_cast<const S*>(stage);
         const unsigned char* fl = stage + L::PDF_BYTES;
@@ -516,7 +517,7 @@ __global__ void __launch_bounds__(SP_TILE / 2, 6) k_liquid_staged_pair(Dev s) {
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[st]);
         if (tid == 0 && i + STAGES < mine) {
-            if (!mbar_wait(s, &empty[st], ph)) {
+            if (!mbar_wait(s, &empty[st], ph, s.wait_limit)) {
                 refill_failed = true;
             } else {
                 issue(st, i + STAGES);
@@ -524,10 +525,13 @@ __global__ void __launch_bounds__(SP_TILE / 2, 6) k_liquid_staged_pair(Dev s) {
             }
         }
     }
-    // copies still in flight complete before the CTA leaves
+    // copies still in flight complete before the CTA leaves (with the default
+    // limit whatever the stage waits were given: these copies were issued
+    // and land in this CTA's shared memory)
     if (tid == 0)
         for (int k = 0; k < STAGES; ++k)
-            if (last_issued[k] >= 0) mbar_wait(s, &full[k], (unsigned)(last_issued[k] / STAGES) & 1u);
+            if (last_issued[k] >= 0)
+                mbar_wait(s, &full[k], (unsigned)(last_issued[k] / STAGES) & 1u, WAIT_LIMIT_DEFAULT);
 }
 
 // Warp segmented reduction of per-lane (key, F, T) for runs of equal keys,

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libfslbm.so")
 FSLBM_OK = 0
 ERRORS = {
     -1: "EINVAL", -2: "ENOMEM", -3: "ECAPACITY", -4: "ENAN", -5: "EDEVICE", -6: "ESTATE", -7: "EINVARIANT",
+    -8: "ETIMEOUT",
 }
 PERIODIC_X, PERIODIC_Y, PERIODIC_Z = 1, 2, 4
 STORE_FP32, STORE_FP16, STORE_BF16 = 0, 1, 2
@@ -48,7 +49,7 @@ EXPORTED = (
     "fslbm_cell_counts", "fslbm_reduce_fields_noalloc", "fslbm_destroy", "fslbm_strerror",
     "fslbm_set_normal_model", "fslbm_normal_stats", "fslbm_mlp_stencils", "fslbm_mlp_gradient",
     "fslbm_mlp_train", "fslbm_mlp_infer", "fslbm_bed_height", "fslbm_set_body_force",
-    "fslbm_get_body_force", "fslbm_set_flow_control",
+    "fslbm_get_body_force", "fslbm_set_flow_control", "fslbm_set_wait_limit",
 )
 
 MLP_NPARAM = 6212
@@ -124,6 +125,7 @@ def load():
     L.fslbm_set_body_force.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     L.fslbm_get_body_force.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     L.fslbm_set_flow_control.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int64]
+    L.fslbm_set_wait_limit.argtypes = [vp, ctypes.c_int64]
     L.fslbm_reduce_fields_noalloc.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), vp, vp]
     L.fslbm_set_normal_model.argtypes = [vp, vp, ctypes.c_int64]
     L.fslbm_normal_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
@@ -437,6 +439,11 @@ class Simulation:
         _check(load().fslbm_bed_height(self.h, float(level), h.ctypes.data,
                                        phi.ctypes.data if phi is not None else None, 0), "fslbm_bed_height")
         return (h, phi) if with_fraction else h
+
+    def set_wait_limit(self, polls: int) -> None:
+        """Polls before a bounded device wait gives up (test hook of the
+        error path; see fslbm_set_wait_limit)."""
+        _check(load().fslbm_set_wait_limit(self.h, int(polls)), "fslbm_set_wait_limit")
 
     def cell_counts(self) -> np.ndarray:
         out = np.zeros(4, np.int64)

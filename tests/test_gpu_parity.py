@@ -249,6 +249,35 @@ def test_non_finite_state_is_reported():
     sim.close()
 
 
+def test_bounded_wait_that_runs_out_is_reported():
+    """A wait of the staged sweep on its bulk copies that gives up (here after
+    zero polls, set by the test hook) sets FSLBM_ETIMEOUT; the kernel still
+    waits for the copies it issued before it leaves, so the context stays
+    usable: a fresh simulation on the same device then runs normally and
+    matches the oracle."""
+    w = _staged_workload()
+    sim = _sim(w, storage=F.STORE_FP16)
+    sim.set_wait_limit(0)
+    with pytest.raises(F.FslbmError) as e:
+        sim.step(1)                # an even step: the staged kernel's first wait gives up
+        sim.sync()
+    assert e.value.code == -8
+    with pytest.raises(F.FslbmError) as e:
+        sim.step(1)                # the error word is sticky
+    assert e.value.code == -8
+    sim.close()
+    sim = _sim(w, storage=F.STORE_FP16)
+    o = oracle_from_workload(w)
+    sim.step(2)
+    o.step(2)
+    to = o.get(O.F_TYPE)
+    assert (sim.get(F.FIELD_TYPE) == to).all()
+    fl = (to == 1) | (to == 2)
+    dev = np.abs(sim.get(F.FIELD_PDF)[:, fl] - o.get(O.F_PDF)[:, fl]) / weights()[:, None]
+    assert dev.max() < 2e-3
+    sim.close()
+
+
 def _staged_workload():
     """x extent 256 (a multiple of the 256-cell tile): with 16-bit storage the
     even steps run the staged pair kernel on every tile that holds liquid,

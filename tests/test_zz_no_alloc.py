@@ -41,3 +41,52 @@ def test_noalloc_reduction_matches_fslbm_reduce():
     # sizes beyond the scratch are refused before any work
     assert F.fslbm_reduce_fields_noalloc(pdf, typ, mass, 4096 * 65536 + 1, w.g, out, stream) == -3
     sim.close()
+
+
+def test_noalloc_reduction_spans_many_blocks_and_keeps_no_stale_rows():
+    """Synthetic FP64 fields of 3 * 65536 + 17 cells (four blocks of partial
+    sums, the last one ragged) against numpy's FP64 sums; then a call on the
+    first 1000 cells after the large one: the rows the large call left in the
+    shared scratch must not leak into it, and it must repeat bit for bit."""
+    import torch
+    from paper_2301_10674_gb300 import build as B
+    B.build()
+    dev = torch.device("cuda")
+    n = 3 * 65536 + 17
+    rng = np.random.default_rng(7)
+    pdf = rng.uniform(0.0, 0.2, (27, n))
+    typ = rng.integers(0, 4, n).astype(np.uint8)
+    mass = rng.uniform(0.0, 1.0, n)
+    g = (1e-5, -2e-5, 3e-5)
+    C = np.array([[q % 3 - 1, (q // 3) % 3 - 1, q // 9 - 1] for q in range(27)], np.float64)
+
+    def expected(k):
+        f, t, m = pdf[:, :k], typ[:k], mass[:k]
+        fluid = (t == F.LIQUID) | (t == F.INTERFACE)
+        rho = f.sum(axis=0)
+        j = C.T @ f
+        tot = np.where(t == F.LIQUID, rho, 0.0).sum() + np.where(t == F.INTERFACE, m, 0.0).sum()
+        mom = [(j[a] - 0.5 * rho * g[a])[fluid].sum() for a in range(3)]
+        return np.array([tot] + mom)
+
+    d_pdf = torch.from_numpy(pdf).to(dev)
+    d_typ = torch.from_numpy(typ).to(dev)
+    d_mass = torch.from_numpy(mass).to(dev)
+    stream = torch.cuda.current_stream().cuda_stream
+
+    def call(k, pdf_view):
+        out = torch.full((4,), float("nan"), dtype=torch.float64, device=dev)
+        assert F.fslbm_reduce_fields_noalloc(pdf_view, d_typ, d_mass, k, g, out, stream) == 0
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+    small = 1000
+    d_small = d_pdf[:, :small].contiguous()
+    first_small = call(small, d_small)
+    big = call(n, d_pdf)
+    after_small = call(small, d_small)
+    for got, k in ((big, n), (first_small, small)):
+        ref = expected(k)
+        assert np.all(np.abs(got - ref) <= 1e-12 * np.abs(ref).max()), (got, ref)
+    assert np.array_equal(first_small, after_small)
+    assert np.array_equal(big, call(n, d_pdf))
