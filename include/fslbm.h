@@ -84,7 +84,12 @@ typedef struct {
     double omega;                /* shear relaxation rate, 0 < omega < 2 */
     double g[3];                 /* body acceleration (gravity incl. slope forcing) */
     double rho_gas;              /* gas pressure p_g = rho_gas / 3 */
-    double sigma;                /* surface tension; only 0 is supported */
+    double sigma;                /* surface tension sigma >= 0 (Section 2.1): the
+                                    gas-side reconstruction density is
+                                    rho_gas + 6 sigma kappa, kappa the
+                                    curvature of the learned normal model (0
+                                    where the finite-difference normal is
+                                    taken, which carries none) */
     double liquid_height;        /* initial flat free surface height (cells) */
     int32_t init_profile;        /* 0: fluid at rest */
     int32_t storage;             /* FSLBM_STORE_* */
@@ -104,6 +109,10 @@ typedef struct {
                                     into liquid cells is taken from the mass pool */
     int64_t capacity_particles;  /* maximum number of spheres (0: 65536) */
     int64_t capacity_interface;  /* maximum interface cells (0: ncells/4 + 4096) */
+    int32_t excess_even;         /* 1: the excess mass of a converting cell is split
+                                    evenly over its receivers instead of along the
+                                    normal (a variant of the free-surface method) */
+    int32_t reserved;            /* 0 */
 } fslbm_params;
 
 /* Fills *p with defaults: periodic x, walls in y and z, omega = 1/0.51,
@@ -117,7 +126,7 @@ void fslbm_default_params(fslbm_params* p);
  * liquid_height liquid, the layer holding or touching the surface interface
  * with its fill level, gas above; hydrostatic density rho_gas
  * exp(3 |g_z| (H - z)). Returns FSLBM_EINVAL for bad parameters (including
- * sigma != 0 and normal_model outside {0, 1}), FSLBM_ENOMEM if the device buffers do
+ * a negative or non-finite sigma and normal_model outside {0, 1}), FSLBM_ENOMEM if the device buffers do
  * not fit. On success *out owns every device buffer of the run. */
 int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out);
 

@@ -94,6 +94,14 @@ def lib():
         L.orc_normal_stencil.argtypes = [dp, dp]
         L.orc_set_mlp.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
         L.orc_threads.restype = ctypes.c_int
+        u8p = ctypes.c_void_p
+        L.orc_excess_shares.restype = ctypes.c_int
+        L.orc_excess_shares.argtypes = [ctypes.c_int, ctypes.c_double, dp, u8p, ctypes.c_int, dp]
+        L.orc_new_interface_mean.restype = ctypes.c_int
+        L.orc_new_interface_mean.argtypes = [u8p, dp, dp, dp, dp]
+        L.orc_uncovered_state.restype = ctypes.c_int
+        L.orc_uncovered_state.argtypes = [u8p, dp, dp, dp, dp, dp, dp, dp, dp]
+        L.orc_set_pool.argtypes = [ctypes.c_void_p, ctypes.c_double]
         _lib = L
     return _lib
 
@@ -229,6 +237,10 @@ class Oracle:
         self.params.g = tuple(float(v) for v in g)
         lib().orc_set_gravity(self._h, *self.params.g)
 
+    def set_pool(self, value: float) -> None:
+        """Test set-up: the mass pool that the next step spreads."""
+        lib().orc_set_pool(self._h, float(value))
+
     def reduce(self) -> np.ndarray:
         out = np.zeros(8, np.float64)
         lib().orc_reduce(self._h, _dp(out))
@@ -270,3 +282,43 @@ def normal_stencil(phi27) -> np.ndarray:
     out = np.empty(3, np.float64)
     lib().orc_normal_stencil(_dp(a), _dp(out))
     return out
+
+
+# Blocks of 3x3x3 cells, index q = (cx+1) + 3(cy+1) + 9(cz+1); WALL marks a
+# position beyond a wall face.
+WALL = 255
+
+
+def excess_shares(to_liquid: bool, ex: float, n, receivers, even: bool = False):
+    """Shares of a converting cell's excess mass among its block (27,);
+    returns (to_pool, shares)."""
+    nn = np.ascontiguousarray(n, dtype=np.float64)
+    rc = np.ascontiguousarray(receivers, dtype=np.uint8).reshape(27)
+    out = np.empty(27, np.float64)
+    r = lib().orc_excess_shares(int(bool(to_liquid)), float(ex), _dp(nn), rc.ctypes.data, int(bool(even)), _dp(out))
+    return bool(r), out
+
+
+def new_interface_mean(types, rho, u):
+    """(count, rho_bar, u_bar) a new interface cell starts from."""
+    t = np.ascontiguousarray(types, dtype=np.uint8).reshape(27)
+    r = np.ascontiguousarray(rho, dtype=np.float64).reshape(27)
+    uu = np.ascontiguousarray(u, dtype=np.float64).reshape(27, 3)
+    rb = np.zeros(1)
+    ub = np.zeros(3)
+    cnt = lib().orc_new_interface_mean(t.ctypes.data, _dp(r), _dp(uu), _dp(rb), _dp(ub))
+    return int(cnt), float(rb[0]), ub
+
+
+def uncovered_state(types, rho, U, W, d):
+    """(type, f, rho_bar, u_b, mass) of a cell a particle uncovers."""
+    t = np.ascontiguousarray(types, dtype=np.uint8).reshape(27)
+    r = np.ascontiguousarray(rho, dtype=np.float64).reshape(27)
+    a = [np.ascontiguousarray(v, dtype=np.float64) for v in (U, W, d)]
+    f = np.zeros(27)
+    rb = np.zeros(1)
+    ub = np.zeros(3)
+    m = np.zeros(1)
+    typ = lib().orc_uncovered_state(t.ctypes.data, _dp(r), _dp(a[0]), _dp(a[1]), _dp(a[2]), _dp(f), _dp(rb),
+                                    _dp(ub), _dp(m))
+    return int(typ), f, float(rb[0]), ub, float(m[0])

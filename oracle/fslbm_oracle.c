@@ -33,9 +33,12 @@
  *
  * Parity status: the collision, streaming, free-surface boundary, mass
  * exchange, normals and DEM contact law are pinned by tests against closed
- * forms and invariants; the heuristic parts of the conversion (S5-S9) and
- * the re-mapping (S11) are pinned only through the mass-conservation and
- * order-independence invariants.
+ * forms and invariants. The heuristic parts of the conversion (S5-S9) and
+ * the re-mapping (S11) are pinned by the mass-conservation and
+ * order-independence invariants and by hand-computed cases: the excess
+ * shares, the new-interface and uncovered-cell states (orc_excess_shares,
+ * orc_new_interface_mean, orc_uncovered_state on hand-built blocks) and
+ * whole steps on flat layers at rest whose outcome is worked out by hand.
  */
 #include <math.h>
 #include <stdint.h>
@@ -324,6 +327,96 @@ static void particle_velocity_at(const orc* o, int p, const double x[3], double 
     ub[0] = o->U[3 * p + 0] + (w[1] * d[2] - w[2] * d[1]);
     ub[1] = o->U[3 * p + 1] + (w[2] * d[0] - w[0] * d[2]);
     ub[2] = o->U[3 * p + 2] + (w[0] * d[1] - w[1] * d[0]);
+}
+
+/* ------------------------------------------ conversion heuristics (R-7, R-8, R-11)
+ * Each works on the 3x3x3 block around one cell, index q = (cx+1) +
+ * 3(cy+1) + 9(cz+1) (13 is the cell itself), with the cell types of the
+ * snapshot taken before the conversion; NB_WALL marks a block position
+ * beyond a wall face. one_step calls them; the tests call them on blocks
+ * built by hand. */
+#define NB_WALL 255
+
+/* Excess mass of an interface cell that converts (Section 2.1, R-8): ex is
+ * shared among the receivers (recv[q] != 0, q != 13) with weights
+ * max(0, s n.c_q), s = +1 for a cell turning liquid and -1 for one turning
+ * gas, n the cell's normal toward the gas; evenly over the receivers when
+ * every weight vanishes or `even` is set. share[q] gets each part (0 for
+ * the others). Returns 1, with every share 0, when there is no receiver:
+ * the excess then belongs to the global pool. */
+int orc_excess_shares(int to_liquid, double ex, const double n[3], const uint8_t recv[NQ], int even,
+                      double share[NQ])
+{
+    build_tables();
+    double sgn = to_liquid ? 1.0 : -1.0;
+    double w[NQ], wsum = 0.0;
+    int nrec = 0;
+    for (int q = 0; q < NQ; ++q) {
+        share[q] = 0.0;
+        w[q] = 0.0;
+        if (q == 13 || !recv[q]) continue;
+        double v = sgn * (n[0] * CX[q] + n[1] * CY[q] + n[2] * CZ[q]);
+        if (v < 0.0) v = 0.0;
+        w[q] = v;
+        wsum += v;
+        nrec++;
+    }
+    if (nrec == 0) return 1;
+    for (int q = 0; q < NQ; ++q) {
+        if (q == 13 || !recv[q]) continue;
+        share[q] = (wsum > 0.0 && !even) ? ex * w[q] / wsum : ex / nrec;
+    }
+    return 0;
+}
+
+/* Start of a gas cell that turns interface next to a filled cell (Section
+ * 2.1, R-7): the mean density and velocity over the block's liquid and
+ * interface cells (q != 13; type[q] from the snapshot, u[3q..3q+2]). The new
+ * cell then holds f_eq(rho_bar, u_bar) and mass 0. Returns the number of
+ * cells averaged; with none, nothing is written. */
+int orc_new_interface_mean(const uint8_t type[NQ], const double rho[NQ], const double u[3 * NQ], double* rb,
+                           double ub[3])
+{
+    double rs = 0, us[3] = {0, 0, 0};
+    int cnt = 0;
+    for (int q = 0; q < NQ; ++q) {
+        if (q == 13 || !is_fluid(type[q])) continue;
+        rs += rho[q];
+        for (int a = 0; a < 3; ++a) us[a] += u[3 * q + a];
+        cnt++;
+    }
+    if (cnt == 0) return 0;
+    *rb = rs / cnt;
+    for (int a = 0; a < 3; ++a) ub[a] = us[a] / cnt;
+    return cnt;
+}
+
+/* State of a cell that a particle uncovers (Section 2.2, R-11), from the
+ * snapshot of its block: without a liquid or interface neighbour it turns
+ * gas (returns T_GAS, nothing else written); otherwise it takes
+ * f_eq(rho_bar, u_b), rho_bar the mean density of those neighbours and u_b
+ * = U_p + Omega_p x d the particle's surface velocity at the cell centre
+ * (d = x_c - X_p, minimal image), and becomes interface with mass 0 if a
+ * neighbour is gas, liquid with mass rho_bar otherwise. The mass it holds is
+ * taken from the pool by the caller. */
+int orc_uncovered_state(const uint8_t type[NQ], const double rho[NQ], const double Up[3], const double Wp[3],
+                        const double d[3], double f[NQ], double* rb, double ub[3], double* mass)
+{
+    double rs = 0.0;
+    int cnt = 0, gas = 0;
+    for (int q = 0; q < NQ; ++q) {
+        if (q == 13 || type[q] == NB_WALL) continue;
+        if (is_fluid(type[q])) { rs += rho[q]; cnt++; }
+        if (type[q] == T_GAS) gas = 1;
+    }
+    if (cnt == 0) return T_GAS;
+    *rb = rs / cnt;
+    ub[0] = Up[0] + (Wp[1] * d[2] - Wp[2] * d[1]);
+    ub[1] = Up[1] + (Wp[2] * d[0] - Wp[0] * d[2]);
+    ub[2] = Up[2] + (Wp[0] * d[1] - Wp[1] * d[0]);
+    orc_feq(*rb, ub, f);
+    *mass = gas ? 0.0 : *rb;
+    return gas ? T_IFC : T_LIQ;
 }
 
 /* Parker-Youngs normal (R-10): gradient sum_c w(c) c phi(x+c), weights 4
@@ -859,6 +952,27 @@ static void dem_substep(orc* o, const double* Fhyd, const double* Thyd, double d
 
 /* ------------------------------------------------------------ one step */
 
+/* the 3x3x3 block around cell i: types (NB_WALL beyond a wall face) from
+ * `types`, densities and velocities from the current state */
+static void gather_block(const orc* o, long i, const uint8_t* types, uint8_t t27[NQ], double r27[NQ],
+                         double u27[3 * NQ])
+{
+    int x, y, z;
+    coords(o, i, &x, &y, &z);
+    for (int q = 0; q < NQ; ++q) {
+        long y_ = nbr(o, x, y, z, CX[q], CY[q], CZ[q]);
+        if (y_ < 0) {
+            t27[q] = NB_WALL;
+            r27[q] = 0.0;
+            u27[3 * q] = u27[3 * q + 1] = u27[3 * q + 2] = 0.0;
+            continue;
+        }
+        t27[q] = types[y_];
+        r27[q] = o->rho[y_];
+        for (int a = 0; a < 3; ++a) u27[3 * q + a] = o->u[3 * y_ + a];
+    }
+}
+
 static void one_step(orc* o)
 {
     const orc_params* P = &o->p;
@@ -1052,20 +1166,12 @@ static void one_step(orc* o)
     for (long i = 0; i < n; ++i) {
         if (mark[i] == MK_NEW) {
             /* f* = f_eq(mean rho, mean u) of the liquid/interface neighbours
-             * of the snapshot; m = 0 */
-            int x, y, z;
-            coords(o, i, &x, &y, &z);
-            double rs = 0, us[3] = {0, 0, 0};
-            int cnt = 0;
-            for (int q = 0; q < NQ; ++q) {
-                if (q == 13) continue;
-                long y_ = nbr(o, x, y, z, CX[q], CY[q], CZ[q]);
-                if (y_ < 0 || !is_fluid(o->type[y_])) continue;
-                rs += o->rho[y_];
-                for (int a = 0; a < 3; ++a) us[a] += o->u[3 * y_ + a];
-                cnt++;
-            }
-            double rb = rs / cnt, ubar[3] = {us[0] / cnt, us[1] / cnt, us[2] / cnt};
+             * of the snapshot; m = 0 (a new cell always neighbours the
+             * interface cell that filled) */
+            uint8_t t27[NQ];
+            double r27[NQ], u27[3 * NQ], rb = 0.0, ubar[3] = {0, 0, 0};
+            gather_block(o, i, o->type, t27, r27, u27);
+            orc_new_interface_mean(t27, r27, u27, &rb, ubar);
             orc_feq(rb, ubar, &o->f[i * NQ]);
             o->rho[i] = rb;
             for (int a = 0; a < 3; ++a) o->u[3 * i + a] = ubar[a];
@@ -1080,31 +1186,28 @@ static void one_step(orc* o)
         double ex;
         if (conv[i] == CV_TO_LIQ) { ex = o->mass[i] - o->rho[i]; o->mass[i] = o->rho[i]; }
         else { ex = o->mass[i]; o->mass[i] = 0.0; }
+        /* receivers: interface neighbours that do not convert, and the
+         * cells that turn interface in this step */
         int x, y, z;
         coords(o, i, &x, &y, &z);
-        double sgn = conv[i] == CV_TO_LIQ ? 1.0 : -1.0;
-        double wsum = 0.0;
-        int nrec = 0;
-        long recv[26];
-        double wts[26];
+        uint8_t recv[NQ];
+        long cell_of[NQ];
         for (int q = 0; q < NQ; ++q) {
+            recv[q] = 0;
+            cell_of[q] = -1;
             if (q == 13) continue;
             long y_ = nbr(o, x, y, z, CX[q], CY[q], CZ[q]);
             if (y_ < 0) continue;
-            int receiver = (o->type[y_] == T_IFC && conv[y_] == CV_NONE) || mark[y_] != MK_NONE;
-            if (!receiver) continue;
-            double w = sgn * (n1[3 * i] * CX[q] + n1[3 * i + 1] * CY[q] + n1[3 * i + 2] * CZ[q]);
-            if (w < 0.0) w = 0.0;
-            recv[nrec] = y_;
-            wts[nrec] = w;
-            wsum += w;
-            nrec++;
+            cell_of[q] = y_;
+            recv[q] = (o->type[y_] == T_IFC && conv[y_] == CV_NONE) || mark[y_] != MK_NONE;
         }
-        if (nrec == 0) { o->pool += ex; continue; }
-        for (int k = 0; k < nrec; ++k) {
-            double share = (wsum > 0.0 && !P->excess_even) ? ex * wts[k] / wsum : ex / nrec;
-            o->mass[recv[k]] += share;
+        double share[NQ];
+        if (orc_excess_shares(conv[i] == CV_TO_LIQ, ex, &n1[3 * i], recv, P->excess_even, share)) {
+            o->pool += ex;
+            continue;
         }
+        for (int q = 0; q < NQ; ++q)
+            if (recv[q]) o->mass[cell_of[q]] += share[q];
     }
     /* S9: finalise */
     for (long i = 0; i < n; ++i) {
@@ -1155,25 +1258,20 @@ static void one_step(orc* o)
             int x, y, z;
             coords(o, i, &x, &y, &z);
             int pold = o->owner[i];
-            double rs = 0.0;
-            int cnt = 0, gas = 0;
-            for (int q = 0; q < NQ; ++q) {
-                if (q == 13) continue;
-                long y_ = nbr(o, x, y, z, CX[q], CY[q], CZ[q]);
-                if (y_ < 0) continue;
-                if (is_fluid(snap[y_])) { rs += o->rho[y_]; cnt++; }
-                if (snap[y_] == T_GAS) gas = 1;
-            }
+            uint8_t t27[NQ];
+            double r27[NQ], u27[3 * NQ];
+            gather_block(o, i, snap, t27, r27, u27);
+            double xc[3] = {x + 0.5, y + 0.5, z + 0.5}, d[3];
+            for (int a = 0; a < 3; ++a) d[a] = min_image(o, a, xc[a] - o->X[3 * pold + a]);
+            double rb = 0.0, ub[3] = {0, 0, 0}, m = 0.0;
+            int t = orc_uncovered_state(t27, r27, &o->U[3 * pold], &o->W[3 * pold], d, &o->f[i * NQ], &rb, ub, &m);
             o->owner[i] = -1;
-            if (cnt == 0) { o->type[i] = T_GAS; o->mass[i] = 0.0; continue; }
-            double rb = rs / cnt;
-            double xc[3] = {x + 0.5, y + 0.5, z + 0.5}, ub[3];
-            particle_velocity_at(o, pold, xc, ub);
-            orc_feq(rb, ub, &o->f[i * NQ]);
+            o->type[i] = (uint8_t)t;
+            if (t == T_GAS) { o->mass[i] = 0.0; continue; }
             o->rho[i] = rb;
             for (int a = 0; a < 3; ++a) o->u[3 * i + a] = ub[a];
-            if (gas) { o->type[i] = T_IFC; o->mass[i] = 0.0; }
-            else { o->type[i] = T_LIQ; o->mass[i] = rb; uncovered_liq[i] = 1; }
+            o->mass[i] = m;
+            if (t == T_LIQ) uncovered_liq[i] = 1;
             o->pool -= o->mass[i];
         }
         /* uncovered liquid cells that ended next to a gas cell become
@@ -1313,6 +1411,8 @@ long orc_ncells(const orc* o) { return o->n; }
 int orc_nparticles(const orc* o) { return o->np; }
 long orc_violations(const orc* o) { return o->invariant_violations; }
 double orc_pool(const orc* o) { return o->pool; }
+/* test set-up: the FP64 mass pool that the next step spreads */
+void orc_set_pool(orc* o, double pool) { o->pool = pool; }
 
 /* Body-force acceleration (gravity) for the following steps: the fluid's
  * forcing and the particles' weight both read it. */

@@ -149,9 +149,11 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     const long long n = (long long)p->nx * p->ny * p->nz;
     if (n >= (1LL << 31)) return FSLBM_EINVAL;
     if (!(p->omega > 0.0 && p->omega < 2.0)) return FSLBM_EINVAL;
-    if (p->sigma != 0.0 || p->normal_model < 0 || p->normal_model > 1 || p->init_profile != 0) return FSLBM_EINVAL;
+    if (!std::isfinite(p->sigma) || p->sigma < 0.0) return FSLBM_EINVAL;
+    if (p->normal_model < 0 || p->normal_model > 1 || p->init_profile != 0) return FSLBM_EINVAL;
     if (p->storage < 0 || p->storage > 2) return FSLBM_EINVAL;
     if (p->link_mass_correction < 0 || p->link_mass_correction > 1) return FSLBM_EINVAL;
+    if (p->excess_even < 0 || p->excess_even > 1 || p->reserved != 0) return FSLBM_EINVAL;
     if (p->dem_substeps < 1 || !(p->restitution > 0.0 && p->restitution <= 1.0)) return FSLBM_EINVAL;
     if (!(p->collision_time > 0.0) || !(p->rho_p > 0.0) || !(p->rho_gas > 0.0)) return FSLBM_EINVAL;
     if (!(p->poisson >= 0.0 && p->poisson < 1.0) || !(p->friction >= 0.0)) return FSLBM_EINVAL;
@@ -193,9 +195,11 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     d.gx = (float)p->g[0]; d.gy = (float)p->g[1]; d.gz = (float)p->g[2];
     d.gxd = p->g[0]; d.gyd = p->g[1]; d.gzd = p->g[2];
     d.rho_gas = (float)p->rho_gas;
+    d.sigma = (float)p->sigma;
     d.eps_conv = (float)p->eps_conv;
     d.eps_normal = (float)p->eps_normal;
     d.recon_normal = p->reconstruct_normal;
+    d.excess_even = p->excess_even;
     d.link_corr = p->link_mass_correction;
     d.idx32 = 27LL * n < (1LL << 32) ? 1 : 0;
     d.wait_limit = WAIT_LIMIT_DEFAULT;

@@ -58,7 +58,9 @@ struct Dev {
     // LBM parameters
     float omega, gx, gy, gz;
     float rho_gas, eps_conv, eps_normal;
+    float sigma;       // surface tension: reconstruction density rho_gas + 6 sigma kappa
     int recon_normal;
+    int excess_even;   // excess mass split evenly over the receivers
     int storage;
     int link_corr;     // net moving-bounce-back injection into liquid cells taken from the pool
     int idx32;         // 27 n < 2^32: PDF element indices fit 32 bits

@@ -755,7 +755,10 @@ __global__ void __launch_bounds__(128) k_interface(Dev s) {
             const float ury = (jy - 0.5f * rr * s.gy) / rr;
             const float urz = (jz - 0.5f * rr * s.gz) / rr;
             const float uur = urx * urx + ury * ury + urz * urz;
-            const float rhoG = s.rho_gas;
+            // gas pressure plus the Laplace pressure 2 sigma kappa (Section 2.1),
+            // kappa the curvature that came with the cell's normal (0 where
+            // the finite-difference normal was taken)
+            const float rhoG = s.rho_gas + 6.f * s.sigma * nn.w;
             float dm = 0.f;
 #pragma unroll
             for (int q = 0; q < 27; ++q) {

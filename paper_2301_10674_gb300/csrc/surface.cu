@@ -313,8 +313,9 @@ __device__ __forceinline__ bool is_receiver(const Dev& s, long long c) {
 
 // excess mass of converting cells: m - rho (to liquid, m := rho) or m (to
 // gas, m := 0), spread over interface neighbours with weights max(0, n.c)
-// (filled) or max(0, -n.c) (emptied), evenly if all weights vanish, into the
-// FP64 pool if there is no interface neighbour
+// (filled) or max(0, -n.c) (emptied), evenly if all weights vanish or the
+// even variant is selected, into the FP64 pool if there is no interface
+// neighbour
 __global__ void k_excess_prep(Dev s) {
     FOR_LIST(i, s.wl_count) {
         int c = s.wl[i];
@@ -342,7 +343,7 @@ __global__ void k_excess_prep(Dev s) {
         if (nrec == 0) {
             atomicAdd(s.pool, (double)ex);
             s.exscale[c] = 0.f;
-        } else if (wsum > 0.f) {
+        } else if (wsum > 0.f && !s.excess_even) {
             s.exscale[c] = ex / wsum;
         } else {
             s.exscale[c] = ex / (float)nrec;

@@ -86,6 +86,8 @@ class FslbmParams(ctypes.Structure):
         ("link_mass_correction", ctypes.c_int32),
         ("capacity_particles", ctypes.c_int64),
         ("capacity_interface", ctypes.c_int64),
+        ("excess_even", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 

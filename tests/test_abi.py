@@ -40,7 +40,7 @@ def test_params_struct_matches_c_layout(lib):
 
 def test_invalid_parameters_are_rejected_before_any_device_work(lib):
     bad = []
-    for field, value in (("nx", 0), ("omega", 2.0), ("sigma", 0.1), ("storage", 7),
+    for field, value in (("nx", 0), ("omega", 2.0), ("sigma", -0.1), ("sigma", float("nan")), ("storage", 7),
                          ("dem_substeps", 0), ("restitution", 0.0), ("normal_model", 2),
                          ("normal_model", -1)):
         p = F.fslbm_default_params()

@@ -21,7 +21,7 @@ from oracle import stencils as OS
 from paper_2301_10674_gb300 import fslbm as F
 from paper_2301_10674_gb300 import workloads as W
 
-from helpers import oracle_from_workload
+from helpers import oracle_from_workload, py_network
 
 pytestmark = pytest.mark.gpu
 
@@ -318,3 +318,42 @@ def test_coupled_run_with_the_learned_normal(trained):
     ev, tk = runs["mlp"][3]
     assert tk > 0.5 * ev
     assert np.abs(runs["mlp"][1] - runs["fd"][1]).max() < 0.1
+
+
+# ---------------------------------------------------------------- Laplace pressure
+def test_laplace_pressure_on_the_gpu():
+    """Surface tension in the free-surface boundary condition (Section 2.1):
+    a flat layer without gravity under a network that returns the layer's
+    finite-difference normal and the constant curvature kappa0 settles at
+    the reconstruction density rho_gas + 6 sigma kappa0 (the oracle's closed
+    form, to 1e-3 of the offset), keeps its mass, and follows the oracle's
+    density within 1e-6; sigma = 0 leaves the density at rho_gas."""
+    sigma, kappa0 = 1e-3, 1.0 / 6.0
+    theta = py_network(1.0 / 16.0, kappa0)
+    out = {}
+    for sg in (sigma, 0.0):
+        p = F.fslbm_default_params()
+        p.nx, p.ny, p.nz = 4, 4, 16
+        p.bc_flags = F.PERIODIC_X | F.PERIODIC_Y
+        p.omega = 1.0
+        p.liquid_height = 8.4
+        p.sigma = sg
+        p.normal_model = 1
+        sim = F.Simulation(p)
+        sim.set_normal_model(theta)
+        m0 = sim.reduce()[0]
+        sim.step(3000)
+        t = sim.get(F.FIELD_TYPE)
+        rho = float(sim.get(F.FIELD_RHO)[t == F.LIQUID].mean())
+        assert abs(sim.reduce()[0] / m0 - 1.0) < 1e-6
+        assert sim.normal_stats()[1] > 0
+        out[sg] = rho
+        sim.close()
+    assert (out[sigma] - 1.0) == pytest.approx(6 * sigma * kappa0, rel=1e-3)
+    assert abs(out[0.0] - 1.0) < 1e-6
+    o = O.Oracle(O.OracleParams(nx=4, ny=4, nz=16, periodic=(1, 1, 0), omega=1.0, g=(0.0, 0.0, 0.0),
+                                liquid_height=8.4, sigma=sigma))
+    o.set_mlp(theta, bf16=True)
+    o.step(3000)
+    to = o.get(O.F_TYPE)
+    assert abs(out[sigma] - float(o.get(O.F_RHO)[to == O.LIQUID].mean())) < 1e-6

@@ -8,7 +8,7 @@ import oracle as O
 from paper_2301_10674_gb300 import fslbm as F
 from paper_2301_10674_gb300 import workloads as W
 
-from helpers import oracle_from_workload, pdf_rel_err, weights
+from helpers import oracle_from_workload, pdf_dev_err, pdf_rel_err, weights
 
 pytestmark = pytest.mark.gpu
 
@@ -88,18 +88,21 @@ def test_walls_in_every_axis():
     sim.close()
 
 
-@pytest.mark.parametrize("recon", [1, 0])
-def test_free_surface_without_particles(recon):
+@pytest.mark.parametrize("recon,even", [(1, 0), (0, 0), (1, 1)])
+def test_free_surface_without_particles(recon, even):
     """Wavy free surface over a no-slip floor: reconstruction, mass exchange,
     conversions and excess mass, with exact cell types every 10 steps; with
     recon = 0 the variant that rebuilds only the PDFs streaming in from gas
-    cells (no normal-based rebuild)."""
+    cells (no normal-based rebuild), with even = 1 the variant that splits
+    the excess mass evenly over the receivers."""
     w = W.tiny()
     w.bed = "none"
     w.reconstruct_normal = recon
     w.generate()
-    sim = _sim(w)
-    o = oracle_from_workload(w)
+    p = F.params_from_workload(w)
+    p.excess_even = even
+    sim = F.Simulation(p)
+    o = oracle_from_workload(w, excess_even=even)
     h = 20.0 + 3.0 * np.cos(2 * np.pi * (np.arange(w.nx) + 0.5) / w.nx) \
         + 1.0 * np.sin(2 * np.pi * (np.arange(w.ny)[:, None] + 0.5) / w.ny)
     sim.init_surface(h)
@@ -140,6 +143,57 @@ def test_tiny_workload_200_steps():
     rg, ro = sim.reduce(), o.reduce()
     assert abs(rg[0] - ro[0]) / ro[0] < 1e-6
     print("tiny pdf rel err after 1 / 201 steps:", e1, e)
+    sim.close()
+
+
+@pytest.mark.parametrize("link_corr", [1, 0])
+def test_tiny_workload_1000_steps_statistics(link_corr):
+    """The 64x16x32 flume for 1000 steps on both sides. Cell types and particle
+    owners exact after every one of the first 200 steps; PDFs, measured on
+    f - w, within 1e-5 of the largest deviation after one step and 1e-4 after
+    200; after 1000 steps the mass drift of each side at most 1e-6, and the
+    bulk velocity and the mean bed height within 1% of the oracle's. Run with
+    the contact mass correction of R-12a and without it (the drift of both is
+    printed)."""
+    from oracle import diagnostics as D
+    w = W.tiny().generate()
+    p = F.params_from_workload(w)
+    p.link_mass_correction = link_corr
+    sim = F.Simulation(p)
+    sim.add_spheres(w.xyz, w.radius, w.fixed)
+    o = oracle_from_workload(w, link_mass_correction=link_corr)
+    mg0, mo0 = sim.reduce()[0], o.reduce()[0]
+    e1 = e200 = None
+    for k in range(1, 201):
+        sim.step(1)
+        o.step(1)
+        to = o.get(O.F_TYPE)
+        mism = int((sim.get(F.FIELD_TYPE) != to).sum())
+        assert mism == 0, f"step {k}: {mism} cell types differ"
+        solid = to == O.SOLID
+        assert np.array_equal(sim.get(F.FIELD_OWNER)[solid], o.get(O.F_OWNER)[solid]), f"step {k}: owners"
+        if k in (1, 200):
+            err = pdf_dev_err(sim.get(F.FIELD_PDF), o.get(O.F_PDF), to)
+            if k == 1:
+                e1 = err
+            else:
+                e200 = err
+    assert e1 < 1e-5, e1
+    assert e200 < 1e-4, e200
+    sim.step(800)
+    o.step(800)
+    rg, ro = sim.reduce(), o.reduce()
+    drift_g, drift_o = abs(rg[0] - mg0) / mg0, abs(ro[0] - mo0) / mo0
+    ub_g, ub_o = rg[4], ro[4]
+    hb_g = sim.bed_height(0.3).mean()
+    hb_o = D.bed_height(o.get(O.F_TYPE), 0.3).mean()
+    print(f"R-12a={link_corr}: pdf err (f - w) {e1:.2e} / {e200:.2e}; drift gpu {drift_g:.2e} oracle {drift_o:.2e}; "
+          f"bulk u {ub_g:.6e} vs {ub_o:.6e}; mean h_b {hb_g:.4f} vs {hb_o:.4f}")
+    if link_corr:
+        assert drift_g < 1e-6 and drift_o < 1e-6, (drift_g, drift_o)
+    assert abs(ub_g - ub_o) <= 0.01 * abs(ub_o), (ub_g, ub_o)
+    assert abs(hb_g - hb_o) <= 0.01 * abs(hb_o), (hb_g, hb_o)
+    assert sim.violations == 0 and o.violations == 0
     sim.close()
 
 

@@ -9,22 +9,7 @@ import pytest
 
 import oracle as O
 
-C = np.array([[q % 3 - 1, (q // 3) % 3 - 1, q // 9 - 1] for q in range(27)], float)
-WPY = np.array([{0: 0.0, 1: 4.0, 2: 2.0, 3: 1.0}[int(np.abs(c).sum())] for c in C])
-
-
-def _network(scale, kappa0):
-    """Raw normal -scale * (Parker-Youngs gradient), curvature kappa0."""
-    W1 = np.zeros((64, 27))
-    W1[0:3] = (WPY[:, None] * C).T
-    W1[3:6] = -(WPY[:, None] * C).T
-    W2 = np.zeros((64, 64))
-    W2[np.arange(6), np.arange(6)] = 1.0
-    W3 = np.zeros((4, 64))
-    W3[:3, 0:3] = -scale * np.eye(3)
-    W3[:3, 3:6] = scale * np.eye(3)
-    b3 = np.array([0.0, 0.0, 0.0, kappa0])
-    return np.concatenate([W1.ravel(), np.zeros(64), W2.ravel(), np.zeros(64), W3.ravel(), b3])
+from helpers import py_network as _network
 
 
 def _layer(sigma):
