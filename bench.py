@@ -169,6 +169,10 @@ def run_oracle(w, steps: int, warmup: int, crop_nx: int, theta=None) -> dict:
 
 LAM, MU = 0.4, 0.1
 
+# forms timed beside the headline one (storage, normal): plain FP32 with the
+# finite-difference normal is the reference form of the comparison
+COMPARE_FORMS = (("fp32", "fd"), ("fp16", "fd"), ("bf16", "fd"), ("fp32", "mlp"), ("fp16", "mlp"))
+
 # DRAM traffic of the stream-collide sweep per fluid cell: dram__bytes_read.sum +
 # dram__bytes_write.sum of every sweep kernel (links, liquid, rows, interface),
 # even and odd steps averaged, from one ncu capture on the 1024x64x128 flume.
@@ -221,8 +225,10 @@ def train_normal_model(stream, n_stencils: int, steps: int, seed: int = 4) -> tu
                                  "data_s": round(t1 - t0, 2), "train_s": round(t2 - t1, 2)}
 
 
-def timed_run(args, w, storage_name, theta, stream, local, barrier, world):
-    """Warm-up, then exactly args.steps timed steps of one form of the method."""
+def timed_run(args, w, storage_name, theta, stream, local, barrier, world, horizon=0):
+    """Warm-up, then exactly args.steps timed steps of one form of the method;
+    then, untimed, on to `horizon` steps in all, where the state is recorded
+    for the comparison between the forms."""
     import torch
 
     from paper_2301_10674_gb300 import fslbm as F
@@ -260,11 +266,32 @@ def timed_run(args, w, storage_name, theta, stream, local, barrier, world):
     for _ in range(5):
         sim.bed_height()
     bed_ms = (time.perf_counter() - t0) / 5 * 1e3
+    # the comparison horizon (untimed): the bed height h_b(x) is logged every
+    # 10 steps on the way for its spectrum (Section 4.1)
+    done = args.warmup + args.steps
+    series = [sim.bed_height()]
+    while done < horizon:
+        k = min(10, horizon - done)
+        sim.step(k)
+        done += k
+        series.append(sim.bed_height())
+    hred = sim.reduce()
+    series = np.array(series)
+    spectrum = None
+    if len(series) >= 2:
+        dh = torch.from_numpy(series).cuda()
+        psd = torch.empty_like(dh)
+        rc, peak = F.fslbm_bed_spectrum(dh, len(series), w.nx, 1.0, 10.0, psd, stream.cuda_stream)
+        if rc == 0:
+            spectrum = {"samples": len(series), "every_steps": 10, "wavelength": float(peak[0]),
+                        "period_steps": float(peak[1]), "celerity": float(peak[2]), "amplitude": float(peak[3])}
+    transport = sim.transport_numbers(w.diameter)
     t = sim.get(F.FIELD_TYPE)
     phi = sim.get(F.FIELD_PHI)
     column = np.where(t == 1, 1.0, np.where(t == 2, phi, 0.0)).sum(axis=0)     # liquid volume per (y, x)
     out = {"ms": ms, "sweep_ms": sweep_ms, "sweeps": sweeps, "launches": launches, "counts": counts,
            "counts_after": counts_after, "clocks": clk, "violations": sim.violations, "m0": m0, "m1": red,
+           "mh": hred, "horizon": done, "hb_end": series[-1], "spectrum": spectrum, "transport": transport,
            "column": column, "normal_stats": sim.normal_stats() if theta is not None else None,
            "bed": {"level": 0.3, "mean": round(float(bed_h.mean()), 4), "min": round(float(bed_h.min()), 4),
                    "max": round(float(bed_h.max()), 4), "ms_per_call": round(bed_ms, 3)}}
@@ -315,10 +342,19 @@ def run_ours(args, world, rank, local):
     if args.normals == "mlp":
         with torch.cuda.stream(stream):
             theta, train = train_normal_model(stream, args.mlp_stencils, args.mlp_steps)
-    head = timed_run(args, w, args.storage, theta, stream, local, barrier, world)
-    base = None
-    if args.compare and (args.storage != "fp32" or args.normals != "fd"):
-        base = timed_run(args, w, "fp32", None, stream, local, barrier, world)
+    horizon = args.error_horizon if args.compare else 0
+    head = timed_run(args, w, args.storage, theta, stream, local, barrier, world, horizon)
+    # the other forms, timed the same way from the same initial state: plain
+    # FP32 with the finite-difference normal (the reference form), and each
+    # change on its own (16-bit storage, the learned normal)
+    others = {}
+    if args.compare:
+        for st_name, nm in COMPARE_FORMS:
+            if (st_name, nm) == (args.storage, args.normals) or (nm == "mlp" and theta is None):
+                continue
+            others[(st_name, nm)] = timed_run(args, w, st_name, theta if nm == "mlp" else None, stream, local,
+                                              barrier, world, horizon)
+    base = others.get(("fp32", "fd"))
 
     value = _throughput(world, ncell, args.steps, head["ms"] / 1e3)
     e2e = None
@@ -331,25 +367,45 @@ def run_ours(args, world, rank, local):
     if rank != 0:
         return None
 
-    def drift(r):
-        return abs(r["m1"][0] - r["m0"][0]) / r["m0"][0]
+    def hdrift(r):
+        return abs(r["mh"][0] - r["m0"][0]) / r["m0"][0]
 
     form = f"{args.storage}+{'learned' if theta is not None else 'fd'}-normal"
     comparison = None
     if base is not None:
         vb = _throughput(world, ncell, args.steps, base["ms"] / 1e3)
-        dcol = np.abs(head["column"] - base["column"])
+
+        def error_vs_base(r):
+            dcol = np.abs(r["column"] - base["column"])
+            return {"mass_drift": hdrift(r),
+                    "bed_height_rms_cells": float(np.sqrt(np.mean((r["hb_end"] - base["hb_end"]) ** 2))),
+                    "bulk_ux_rel": float(abs(r["mh"][4] - base["mh"][4]) / max(abs(base["mh"][4]), 1e-30)),
+                    "surface_profile_cells": {"max_abs": float(dcol.max()), "mean_abs": float(dcol.mean())},
+                    "interface_cells": int(r["mh"][5])}
+
+        forms = []
+        for key, r in [((args.storage, args.normals), head)] + list(others.items()):
+            v = _throughput(world, ncell, args.steps, r["ms"] / 1e3)
+            forms.append({"form": f"{key[0]}+{'learned' if key[1] == 'mlp' else 'fd'}-normal", "value": round(v, 2),
+                          "ms_per_step": round(r["ms"] / args.steps, 4), "speedup_vs_fp32_fd": round(v / vb, 4),
+                          "sweep_roofline_frac": _roofline(r, key[0], ncell)["frac"],
+                          "bed_spectrum": r["spectrum"],
+                          "transport": {k: round(v, 8) for k, v in r["transport"].items()},
+                          "error_vs_fp32_fd": None if r is base else error_vs_base(r)})
+        herr = error_vs_base(head)
         comparison = {
             "form": "fp32+fd-normal", "value": round(vb, 2), "unit": UNIT,
             "ms_per_step": round(base["ms"] / args.steps, 4), "speedup": round(value / vb, 4),
             "roofline": _roofline(base, "fp32", ncell), "clocks": base["clocks"],
             "error": {
-                "horizon_steps": args.warmup + args.steps,
-                "mass_drift": {"head": drift(head), "fp32": drift(base)},
-                "surface_profile_cells": {"max_abs": float(dcol.max()), "mean_abs": float(dcol.mean())},
-                "bulk_ux_rel": float(abs(head["m1"][4] - base["m1"][4]) / max(abs(base["m1"][4]), 1e-30)),
-                "interface_cells": {"head": int(head["m1"][5]), "fp32": int(base["m1"][5])},
+                "horizon_steps": head["horizon"],
+                "mass_drift": {"head": herr["mass_drift"], "fp32": hdrift(base)},
+                "surface_profile_cells": herr["surface_profile_cells"],
+                "bulk_ux_rel": herr["bulk_ux_rel"],
+                "bulk_ux": {"head": float(head["mh"][4]), "fp32": float(base["mh"][4])},
+                "interface_cells": {"head": herr["interface_cells"], "fp32": int(base["mh"][5])},
             },
+            "forms": forms,
         }
     cb = head["counts_after"]
     out = {
@@ -375,6 +431,8 @@ def run_ours(args, world, rank, local):
         "checks": {"invariant_violations": int(head["violations"]), "liquid_mass": float(head["m1"][0]),
                    "interface_cells": int(head["m1"][5])},
         "bed_height": head["bed"],
+        "transport": {k: round(v, 8) for k, v in head["transport"].items()},
+        "bed_spectrum": head["spectrum"],
     }
     return out
 
@@ -393,24 +451,112 @@ def run_e2e(args, w, storage, theta, stream, world):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     h = F.fslbm_create(params, stream.cuda_stream)
+    t1 = time.perf_counter()
     F._check(F.fslbm_add_spheres(h, xyz, rad, fix), "fslbm_add_spheres")
     if bits is not None:
         F._check(F.fslbm_set_normal_model(h, bits), "fslbm_set_normal_model")
+    t2 = time.perf_counter()
     for _ in range(args.steps):
         F._check(F.fslbm_step(h, 1), "fslbm_step")
         rc, out = F.fslbm_reduce(h)
         F._check(rc, "fslbm_reduce")
         diag[:] = out
+    t3 = time.perf_counter()
     F.fslbm_destroy(h)
     torch.cuda.synchronize()
-    dt = _max_over_ranks(time.perf_counter() - t0, "cuda")
+    t4 = time.perf_counter()
+    dt = _max_over_ranks(t4 - t0, "cuda")
+    phases = {"create_s": round(t1 - t0, 4), "spheres_and_weights_s": round(t2 - t1, 4),
+              "steps_s": round(t3 - t2, 4), "destroy_s": round(t4 - t3, 4)}
     h2d = xyz.nbytes + rad.nbytes + fix.nbytes + __import__("ctypes").sizeof(params) + \
         (0 if bits is None else bits.nbytes)
     return {"value": round(_throughput(world, w.ncells, args.steps, dt), 2), "unit": UNIT,
             "h2d_bytes_per_step": round(h2d / args.steps, 1), "d2h_bytes_per_step": 64,
-            "seconds": round(dt, 3),
+            "seconds": round(dt, 3), "phases": phases,
             "note": "create + particle bed (and learned-normal weights) from pinned host memory + per step "
                     "(fslbm_step, fslbm_reduce read back to host) + destroy"}
+
+
+def _state(types, phi, red, u):
+    """Liquid volume per (y, x) column, bulk velocity, mass, interface count and
+    the velocity of the liquid cells of one state."""
+    column = np.where(types == 1, 1.0, np.where(types == 2, phi, 0.0)).sum(axis=0)
+    return {"column": column, "bulk_ux": float(red[4]), "mass": float(red[0]), "nifc": int(red[5]),
+            "types": types, "u": u}
+
+
+def run_precision_study(args):
+    """Every storage / normal form of the method against the FP64 oracle on
+    the 128x64x128 x-crop of the 1024x64x128 flume (the precision workload),
+    after args.study_steps steps from the same initial state: mass drift,
+    bulk velocity, liquid volume per column, cell types and the liquid
+    velocity field. The learned-normal forms are compared with the oracle
+    running the same BF16 network. Prints one JSON line."""
+    import torch
+
+    import oracle as O
+    from paper_2301_10674_gb300 import build as B
+    from paper_2301_10674_gb300 import fslbm as F
+    from paper_2301_10674_gb300 import workloads as W
+
+    B.build()
+    torch.cuda.set_device(0)
+    w = W.precision().generate().crop_x(args.study_crop)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        theta, train = train_normal_model(stream, args.mlp_stencils, args.mlp_steps)
+    steps = args.study_steps
+    gpu = {}
+    for st_name, nm in COMPARE_FORMS:
+        sim = F.Simulation.from_workload(w, storage=STORAGE[st_name], stream=stream)
+        if nm == "mlp":
+            sim.set_normal_model(theta)
+        m0 = sim.reduce()[0]
+        sim.step(steps)
+        st = _state(sim.get(F.FIELD_TYPE), sim.get(F.FIELD_PHI), sim.reduce(), sim.get(F.FIELD_U)[0])
+        st["drift"] = abs(st["mass"] - m0) / m0
+        gpu[(st_name, nm)] = st
+        sim.close()
+    orc = {}
+    for nm in ("fd", "mlp"):
+        o = O.Oracle(O.OracleParams(
+            nx=w.nx, ny=w.ny, nz=w.nz, periodic=tuple(w.periodic), omega=w.omega, g=tuple(w.g), rho_gas=w.rho_gas,
+            liquid_height=w.liquid_height, eps_conv=w.eps_conv, eps_normal=w.eps_normal,
+            reconstruct_normal=w.reconstruct_normal, rho_p=w.rho_p, restitution=w.restitution, friction=w.friction,
+            poisson=w.poisson, collision_time=w.collision_time, dem_substeps=w.dem_substeps))
+        o.add_spheres(w.xyz, w.radius, w.fixed)
+        if nm == "mlp":
+            bits = F.bf16_bits(theta).astype(np.uint32) << 16
+            o.set_mlp(bits.view(np.float32).astype(np.float64), bf16=True)
+        m0 = o.reduce()[0]
+        t0 = time.perf_counter()
+        o.step(steps)
+        dt = time.perf_counter() - t0
+        st = _state(o.get(O.F_TYPE), o.get(O.F_PHI), o.reduce(), o.get(O.F_U)[0])
+        st["drift"] = abs(st["mass"] - m0) / m0
+        st["seconds"] = dt
+        orc[nm] = st
+        o.close()
+    forms = []
+    for (st_name, nm), g in gpu.items():
+        r = orc[nm]
+        both = (g["types"] == 1) & (r["types"] == 1)
+        du = g["u"][both] - r["u"][both]
+        dcol = np.abs(g["column"] - r["column"])
+        forms.append({
+            "form": f"{st_name}+{'learned' if nm == 'mlp' else 'fd'}-normal",
+            "mass_drift": g["drift"], "oracle_mass_drift": r["drift"],
+            "bulk_ux": g["bulk_ux"], "oracle_bulk_ux": r["bulk_ux"],
+            "bulk_ux_rel": abs(g["bulk_ux"] - r["bulk_ux"]) / max(abs(r["bulk_ux"]), 1e-30),
+            "u_liquid_rel_l2": float(np.sqrt((du ** 2).sum() / max((r["u"][both] ** 2).sum(), 1e-300))),
+            "column_cells": {"max_abs": float(dcol.max()), "mean_abs": float(dcol.mean())},
+            "cell_types_differing": int((g["types"] != r["types"]).sum()),
+            "interface_cells": {"gpu": g["nifc"], "oracle": r["nifc"]},
+        })
+    return {"study": "precision forms against the FP64 oracle", "workload": w.name,
+            "lattice": [w.nx, w.ny, w.nz], "spheres": w.nspheres, "steps": steps,
+            "oracle_cores": O.threads(), "oracle_seconds": {k: round(v["seconds"], 1) for k, v in orc.items()},
+            "learned_normal_training": train, "forms": forms}
 
 
 def run_reference(args, world, rank):
@@ -442,7 +588,9 @@ def main():
     ap.add_argument("--storage", choices=tuple(STORAGE), default="fp16")
     ap.add_argument("--normals", choices=("fd", "mlp"), default="mlp")
     ap.add_argument("--compare", action=argparse.BooleanOptionalAction, default=True,
-                    help="also time plain FP32 with the finite-difference normal")
+                    help="also time plain FP32 with the finite-difference normal and the other forms")
+    ap.add_argument("--error-horizon", type=int, default=300,
+                    help="steps after which the forms' states are compared (untimed beyond the timed steps)")
     ap.add_argument("--mlp-stencils", type=int, default=1 << 22)
     ap.add_argument("--mlp-steps", type=int, default=40000)
     ap.add_argument("--no-e2e", action="store_true")
@@ -450,10 +598,18 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--cpu-crop", type=int, default=64)
     ap.add_argument("--ref-crop", type=int, default=4)
+    ap.add_argument("--precision-study", action="store_true",
+                    help="instead of the benchmark: every form against the FP64 oracle on a crop of the "
+                         "1024x64x128 flume")
+    ap.add_argument("--study-steps", type=int, default=500)
+    ap.add_argument("--study-crop", type=int, default=128)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     world, rank, local = _dist()
+    if args.precision_study:
+        print(json.dumps(run_precision_study(args)), flush=True)
+        return
     if args.impl == "reference":
         line = run_reference(args, world, rank)
     else:

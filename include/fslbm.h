@@ -242,6 +242,42 @@ int fslbm_set_flow_control(fslbm* s, double target_u, double gain, int64_t inter
  * fslbm_destroy. Synchronises the stream; returns the sticky error word. */
 int fslbm_bed_height(fslbm* s, double phi_b_level, double* h, double* phi, int on_device);
 
+/* Transport and flow numbers of the current state (Section 4.2, Table 2):
+ *   out[0] mean water depth h_bar: the free-surface elevation of each column
+ *          (its liquid and solid volume: 1 per liquid or solid cell, the fill
+ *          level per interface cell), averaged over y, less the bed height
+ *          h_b(x) at phi_b = 0.3 (fslbm_bed_height), averaged over x
+ *   out[1] tan(psi) = g_x / |g_z|, the slope of the imposed body force
+ *   out[2] Shields number h_bar tan(psi) / (d50 (rho_p - 1)), with the
+ *          hydraulic radius taken as h_bar (periodic spanwise boundaries)
+ *   out[3] bedload rate q_b of Eq. (1) (fslbm_reduce out[6])
+ *   out[4] Einstein number q_b / sqrt((rho_p - 1) |g| d50^3), |g| the
+ *          magnitude of the body acceleration
+ *   out[5] mean bed height
+ * rho_p is the particle density of the run (liquid reference density 1);
+ * out[2] and out[4] are 0 where rho_p = 1 or g = 0. d50 > 0 (lattice units).
+ * The first call allocates nx (nz + ny + 1) + 2 doubles of device scratch,
+ * kept until fslbm_destroy. Synchronises the stream. */
+int fslbm_transport_numbers(fslbm* s, double d50, double out[6]);
+
+/* Power spectral density of a bed-height series (Section 4.1) and its
+ * dominant bedform. h: device, double [nt][nx], h_b(x) sampled every dt
+ * steps on cells of size dx (for example rows of fslbm_bed_height results);
+ * psd: device, double [nt][nx], written with |H(l, j)|^2 / (nt nx), H the
+ * two-dimensional discrete Fourier transform over t and x (kernel
+ * exp(-2 pi i (j x / nx + l t / nt))) of h less its mean. peak: host,
+ * double [4], the largest value at wavenumbers 1 <= j <= nx / 2 (ties: the
+ * lowest l, then j) as wavelength nx dx / j, period nt dt / |l| (l taken in
+ * (-nt/2, nt/2]; infinity for l = 0), celerity wavelength / period, positive
+ * toward +x, and amplitude 2 sqrt(psd / (nt nx)) (exact for a single
+ * travelling sine on the grid's frequencies). 2 <= nt <= 65535,
+ * 2 <= nx <= 2^20, dx, dt > 0, else FSLBM_EINVAL. Needs no handle;
+ * allocates 16 (nx + nt + nt nx) + 32 bytes of device scratch for the call
+ * (FSLBM_ENOMEM if that fails) and synchronises cuda_stream (NULL: the
+ * legacy default stream). FSLBM_EDEVICE on a CUDA error. */
+int fslbm_bed_spectrum(const double* h, int64_t nt, int64_t nx, double dx, double dt, double* psd, double peak[4],
+                       void* cuda_stream);
+
 /* Waits for the stream; returns the sticky error word. */
 int fslbm_sync(fslbm* s);
 

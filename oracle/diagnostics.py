@@ -49,3 +49,66 @@ def bed_height(types: np.ndarray, phi_b: float = 0.3) -> np.ndarray:
             pn = col[k + 1] if k + 1 < nz else 0.0
         h[x] = (k + 0.5) + (pk - phi_b) / (pk - pn)
     return h
+
+
+# ---------------------------------------------------------------- Section 4
+# Evaluation quantities of the results (Sections 4.1 and 4.2), written from
+# their definitions. Readings (the paper names each quantity in a sentence):
+#
+# * Free-surface elevation of a column (x, y): its liquid and solid volume,
+#   sum over z of 1 (liquid, solid), phi (interface), 0 (gas); the mean water
+#   depth h_bar is its y-average above the bed height h_b(x), averaged over x.
+# * Power spectral density of h_b(x, t): the squared modulus of the
+#   two-dimensional discrete Fourier transform over x and t of the series with
+#   its mean removed, divided by the number of samples nx * nt. The dominant
+#   bedform is the largest value at a positive wavenumber; for the transform
+#   kernel exp(-2 pi i (j x / nx + l t / nt)) a pattern travelling toward +x
+#   at positive wavenumber j has a negative frequency index l, so its celerity
+#   lambda / T carries the sign of -l.
+# * Shields number Theta = R_b tan(psi) / (d50 (rho_p / rho_l - 1)) with the
+#   hydraulic radius R_b taken as the mean water depth (periodic spanwise
+#   boundaries) and tan(psi) the slope of the imposed body force,
+#   g_x / |g_z|.
+# * Einstein bedload number q_b* = q_b / ((rho_p / rho_l - 1) g d50^3)^(1/2),
+#   g the magnitude of the body acceleration.
+
+
+def surface_elevation(types: np.ndarray, phi: np.ndarray) -> np.ndarray:
+    """(ny, nx) liquid plus solid volume of every column, from cell types and
+    fill levels of shape (nz, ny, nx)."""
+    t = np.asarray(types)
+    vol = np.where((t == 1) | (t == SOLID), 1.0, np.where(t == 2, np.asarray(phi), 0.0))
+    return vol.sum(axis=0)
+
+
+def mean_water_depth(types: np.ndarray, phi: np.ndarray, phi_b: float = 0.3) -> float:
+    """h_bar: mean over x of (y-mean surface elevation - h_b(x))."""
+    eta = surface_elevation(types, phi).mean(axis=0)
+    return float(np.mean(eta - bed_height(types, phi_b)))
+
+
+def shields(depth: float, tan_psi: float, density_ratio: float, d50: float) -> float:
+    return depth * tan_psi / (d50 * (density_ratio - 1.0))
+
+
+def einstein(q_b: float, density_ratio: float, g: float, d50: float) -> float:
+    return q_b / np.sqrt((density_ratio - 1.0) * g * d50 ** 3)
+
+
+def bed_spectrum(h_xt: np.ndarray, dx: float = 1.0, dt: float = 1.0):
+    """PSD of h_b(x, t) given as (nt, nx), and the dominant bedform
+    (wavelength, period, signed celerity, amplitude) at the largest value
+    with wavenumber index 1 <= j <= nx / 2."""
+    h = np.asarray(h_xt, dtype=np.float64)
+    nt, nx = h.shape
+    X = np.fft.fft2(h - h.mean())
+    psd = np.abs(X) ** 2 / (nt * nx)
+    half = psd[:, 1:nx // 2 + 1]
+    l, j = np.unravel_index(int(np.argmax(half)), half.shape)
+    j += 1
+    lsig = l if l <= nt // 2 else l - nt
+    lam = nx * dx / j
+    T = np.inf if lsig == 0 else nt * dt / abs(lsig)
+    c = 0.0 if lsig == 0 else -np.sign(lsig) * lam / T
+    amp = 2.0 * np.sqrt(psd[l, j] / (nt * nx))
+    return psd, (lam, T, c, amp)

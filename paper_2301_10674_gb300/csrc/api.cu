@@ -1,5 +1,6 @@
 // C ABI of the free-surface LBM / DEM step (declared in include/fslbm.h):
 // parameter checks, device buffers, and the per-step kernel sequence.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -16,6 +17,8 @@ void mlp_from_bf16_host(const uint16_t* w, MlpBf16& h);
 namespace fsl {
 void launch_export_owner(const Dev& s, int* out, cudaStream_t st);
 void launch_bed_height(const Dev& s, double phi_b, double* phi, double* h, cudaStream_t st);
+void launch_water_depth(const Dev& s, double* bed, double* eta, double* out, cudaStream_t st);
+int launch_bed_spectrum(const double* h, int nt, int nx, double* psd, double* work, double* peak3, cudaStream_t st);
 }
 
 using namespace fsl;
@@ -40,11 +43,16 @@ struct fslbm {
     int64_t launches;
     unsigned long long* counts4;
     double* bed;                   // nx * nz + nx doubles: phi_b(x, z), then h_b(x)
+    double* eta;                   // nx * ny + 2 doubles: surface elevation, then depth and mean h_b
     // flow-rate control: target bulk velocity, gain, steps between updates (0: off)
     double ctrl_target, ctrl_gain;
     int64_t ctrl_interval;
     MlpBf16* mlp_dev;              // operand copies of the learned normal
     unsigned long long* mlp_stats;
+    // side stream of the DEM half of a step (overlapped with the free-surface
+    // conversion), and the events that fork it from and join it to st
+    cudaStream_t side;
+    cudaEvent_t ev_fork, ev_join;
 };
 
 namespace {
@@ -175,10 +183,13 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     s->launches = 0;
     s->counts4 = nullptr;
     s->bed = nullptr;
+    s->eta = nullptr;
     s->ctrl_target = s->ctrl_gain = 0.0;
     s->ctrl_interval = 0;
     s->mlp_dev = nullptr;
     s->mlp_stats = nullptr;
+    s->side = nullptr;
+    s->ev_fork = s->ev_join = nullptr;
     Dev& d = s->d;
     std::memset(&d, 0, sizeof(d));
     d.nx = p->nx; d.ny = p->ny; d.nz = p->nz;
@@ -298,11 +309,32 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     d.g_list = dalloc<int>(s, pc, ok);
     s->stage = dalloc<double>(s, n > 8 ? n : 8, ok);
     s->red = dalloc<double>(s, 8, ok);
+    float* href = p->storage != FSLBM_STORE_FP32 ? dalloc<float>(s, p->nz, ok) : nullptr;
+    if (ok && (cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess ||
+               cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+               cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess)) {
+        cudaGetLastError();
+        ok = false;
+    }
     if (!ok) {
         fslbm_destroy(s);
         return FSLBM_ENOMEM;
     }
     cudaStream_t st = s->st;
+    std::vector<float> href_h;
+    if (href) {
+        // reference of the 16-bit stored values: the hydrostatic density of
+        // the flat initial surface, delta(z) = rho_gas exp(3 |g_z| (H - z_c)) - 1
+        // (H clamped to the lattice), so that a stored value holds the
+        // deviation from the liquid at rest and FP16/BF16 rounding acts on
+        // the flow, not on the hydrostatic head
+        const double H = std::min(std::max(p->liquid_height, 0.0), (double)p->nz);
+        href_h.resize(p->nz);
+        for (int z = 0; z < p->nz; ++z)
+            href_h[z] = (float)(p->rho_gas * std::exp(3.0 * std::fabs(p->g[2]) * (H - (z + 0.5))) - 1.0);
+        cudaMemcpyAsync(href, href_h.data(), sizeof(float) * p->nz, cudaMemcpyHostToDevice, st);
+        d.href = href;
+    }
     cudaMemsetAsync(d.f, 0, (size_t)27 * n * s->elem, st);
     cudaMemsetAsync(d.fs, 0, (size_t)27 * n * s->elem, st);
     cudaMemsetAsync(d.conv, 0, n, st);
@@ -432,8 +464,18 @@ int fslbm_step(fslbm* s, int64_t n_steps) {
         }
         nl += launch_stream_collide(d, parity, st);
         if (s->timing) cudaEventRecord(e1, st);
+        if (d.np > 0) {
+            // the DEM half on the side stream, beside the conversion
+            cudaEventRecord(s->ev_fork, st);
+            cudaStreamWaitEvent(s->side, s->ev_fork, 0);
+            nl += launch_dem(d, s->have_prev, s->side);
+            cudaEventRecord(s->ev_join, s->side);
+        }
         nl += launch_conversion(d, parity, st);
-        if (d.np > 0) nl += launch_particles_step(d, s->have_prev, parity, st);
+        if (d.np > 0) {
+            cudaStreamWaitEvent(st, s->ev_join, 0);
+            nl += launch_remap(d, parity, st);
+        }
         nl += launch_classify(d, st);
         nl += launch_pool_spread(d, st);
         nl += launch_normals(d, d.nrm, st);
@@ -680,6 +722,75 @@ int fslbm_bed_height(fslbm* s, double phi_b, double* h, double* phi, int on_devi
     return sync_check(s);
 }
 
+int fslbm_transport_numbers(fslbm* s, double d50, double out[6]) {
+    if (!s || !out || !(d50 > 0.0) || !std::isfinite(d50)) return FSLBM_EINVAL;
+    if (s->host_err) return s->host_err;
+    const Dev& d = s->d;
+    const size_t nxz = (size_t)d.nx * d.nz, nxy = (size_t)d.nx * d.ny;
+    bool ok = true;
+    if (!s->bed) s->bed = dalloc<double>(s, nxz + d.nx, ok);
+    if (!s->eta) s->eta = dalloc<double>(s, nxy + 2, ok);
+    if (!ok) return FSLBM_ENOMEM;
+    launch_water_depth(d, s->bed, s->eta, s->eta + nxy, s->st);
+    launch_reduce(d, s->last_parity, s->red, s->st);
+    double dep[2] = {0.0, 0.0}, red[8];
+    cudaMemcpyAsync(dep, s->eta + nxy, sizeof(dep), cudaMemcpyDeviceToHost, s->st);
+    cudaMemcpyAsync(red, s->red, sizeof(red), cudaMemcpyDeviceToHost, s->st);
+    launch_check(s);
+    const int rc = sync_check(s);
+    if (rc) return rc;
+    // slope of the imposed body force in the x-z plane, density ratio of
+    // the particles to the liquid (reference density 1), |g| the magnitude
+    // of the body acceleration (Section 4.2, Table 2)
+    const double tanpsi = d.gzd != 0.0 ? d.gxd / std::fabs(d.gzd) : 0.0;
+    const double s1 = s->p.rho_p - 1.0;
+    const double gm = std::sqrt(d.gxd * d.gxd + d.gyd * d.gyd + d.gzd * d.gzd);
+    out[0] = dep[0];
+    out[1] = tanpsi;
+    out[2] = s1 != 0.0 ? dep[0] * tanpsi / (d50 * s1) : 0.0;
+    out[3] = red[6];
+    out[4] = (s1 > 0.0 && gm > 0.0) ? red[6] / std::sqrt(s1 * gm * d50 * d50 * d50) : 0.0;
+    out[5] = dep[1];
+    return FSLBM_OK;
+}
+
+int fslbm_bed_spectrum(const double* h, int64_t nt, int64_t nx, double dx, double dt, double* psd, double peak[4],
+                       void* cuda_stream) {
+    if (!h || !psd || !peak || nt < 2 || nx < 2 || nt > 65535 || nx > (1 << 20)) return FSLBM_EINVAL;
+    if (!(dx > 0.0) || !(dt > 0.0) || !std::isfinite(dx) || !std::isfinite(dt)) return FSLBM_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    // scratch: twiddles (nx + nt complex), the x-transformed series (nt nx
+    // complex), the mean, and the peak (value, l, j)
+    const size_t work_doubles = 2 * ((size_t)nx + nt + (size_t)nt * nx) + 4;
+    double* work = nullptr;
+    if (cudaMalloc(&work, work_doubles * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return FSLBM_ENOMEM;
+    }
+    double* peak3 = work + work_doubles - 3;
+    cudaGetLastError();
+    launch_bed_spectrum(h, (int)nt, (int)nx, psd, work, peak3, st);
+    double pk[3] = {0.0, 0.0, 0.0};
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(pk, peak3, sizeof(pk), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(work);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return FSLBM_EDEVICE;
+    }
+    // the transform kernel is exp(-2 pi i (j x / nx + l t / nt)): a bedform
+    // moving toward +x at wavenumber j > 0 has frequency index l < 0
+    const long long l = (long long)pk[1], j = (long long)pk[2];
+    const long long ls = l <= nt / 2 ? l : l - nt;
+    const double lam = (double)nx * dx / (double)j;
+    peak[0] = lam;
+    peak[1] = ls == 0 ? INFINITY : (double)nt * dt / (double)(ls < 0 ? -ls : ls);
+    peak[2] = ls == 0 ? 0.0 : (ls < 0 ? 1.0 : -1.0) * lam / peak[1];
+    peak[3] = 2.0 * std::sqrt(pk[0] / ((double)nt * (double)nx));
+    return FSLBM_OK;
+}
+
 int fslbm_set_wait_limit(fslbm* s, int64_t polls) {
     if (!s || polls < 0 || polls > WAIT_LIMIT_DEFAULT) return FSLBM_EINVAL;
     s->d.wait_limit = (int)polls;
@@ -728,6 +839,12 @@ int fslbm_normal_stats(fslbm* s, uint64_t out[2]) {
 void fslbm_destroy(fslbm* s) {
     if (!s) return;
     cudaStreamSynchronize(s->st);
+    if (s->side) {
+        cudaStreamSynchronize(s->side);
+        cudaStreamDestroy(s->side);
+    }
+    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+    if (s->ev_join) cudaEventDestroy(s->ev_join);
     for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
     for (void* p : s->allocs) cudaFree(p);
     delete s;

@@ -83,6 +83,10 @@ struct Dev {
     int* owner;        // owning particle of solid cells
     uint8_t* conv;     // conversion code of interface cells (0 outside a step)
     float* exscale;    // excess mass per unit weight of converting cells
+    // 16-bit storage: reference deviation delta(z) of the stored values, one
+    // per z (null at FP32); a stored value is (f - w_q (1 + delta(z))) scale,
+    // z that of the cell whose index the slot carries
+    const float* href;
     // work lists (device counts)
     int* wl; int* wl_count; int wl_cap;        // interface cells
     int* nl; int* nl_count; int nl_cap;        // cells becoming interface this step
@@ -146,6 +150,7 @@ template <typename S> struct Store;
 // scale into the collision
 template <> struct Store<float> {
     static constexpr float scale = 1.f;
+    static constexpr bool HREF = false;    // no reference: the stored value is f - w
     __device__ static __forceinline__ float ld(const float* p) { return *p; }
     __device__ static __forceinline__ void st(float* p, float v) { *p = v; }
     __device__ static __forceinline__ float ld_raw(const float* p) { return *p; }
@@ -158,6 +163,7 @@ template <> struct Store<float> {
 constexpr float FP16_SCALE = 4096.f, FP16_UNSCALE = 1.f / 4096.f;
 template <> struct Store<__half> {
     static constexpr float scale = FP16_SCALE;
+    static constexpr bool HREF = true;     // relative to w (1 + delta(z)), see Dev::href
     __device__ static __forceinline__ float ld(const __half* p) { return __half2float(*p) * FP16_UNSCALE; }
     __device__ static __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v * FP16_SCALE); }
     __device__ static __forceinline__ float ld_raw(const __half* p) { return __half2float(*p); }
@@ -165,22 +171,35 @@ template <> struct Store<__half> {
 };
 template <> struct Store<__nv_bfloat16> {
     static constexpr float scale = 1.f;
+    static constexpr bool HREF = true;
     __device__ static __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
     __device__ static __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
     __device__ static __forceinline__ float ld_raw(const __nv_bfloat16* p) { return __bfloat162float(*p); }
     __device__ static __forceinline__ void st_raw(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
+// w_q delta(z) of slot i = q n + cell (16-bit storage): the part of f - w
+// that the stored value leaves to the reference
+__device__ __forceinline__ float slot_ref(const Dev& s, long long i) {
+    const int q = (int)(i / s.n);
+    const long long c = i - (long long)q * s.n;
+    return wq(q) * s.href[(int)(c / ((long long)s.nx * s.ny))];
+}
+// f - w at PDF slot i, in any storage format
 __device__ __forceinline__ float ld_any(const Dev& s, const void* base, long long i) {
     if (s.storage == FSLBM_STORE_FP32) return static_cast<const float*>(base)[i];
-    if (s.storage == FSLBM_STORE_FP16) return Store<__half>::ld(static_cast<const __half*>(base) + i);
-    return __bfloat162float(static_cast<const __nv_bfloat16*>(base)[i]);
+    if (s.storage == FSLBM_STORE_FP16) return Store<__half>::ld(static_cast<const __half*>(base) + i) + slot_ref(s, i);
+    return __bfloat162float(static_cast<const __nv_bfloat16*>(base)[i]) + slot_ref(s, i);
 }
 __device__ __forceinline__ void st_any(const Dev& s, void* base, long long i, float v) {
     if (s.storage == FSLBM_STORE_FP32) static_cast<float*>(base)[i] = v;
-    else if (s.storage == FSLBM_STORE_FP16) Store<__half>::st(static_cast<__half*>(base) + i, v);
-    else static_cast<__nv_bfloat16*>(base)[i] = __float2bfloat16_rn(v);
+    else if (s.storage == FSLBM_STORE_FP16) Store<__half>::st(static_cast<__half*>(base) + i, v - slot_ref(s, i));
+    else static_cast<__nv_bfloat16*>(base)[i] = __float2bfloat16_rn(v - slot_ref(s, i));
 }
+// z of the slot a PDF moving in direction (.., .., dz) from a cell at z
+// lands in: z + dz, wrapped on a periodic z axis (the caller has excluded
+// wall faces)
+__device__ __forceinline__ int wrap_z(const Dev& s, int z) { return z < 0 ? z + s.nz : (z >= s.nz ? z - s.nz : z); }
 
 // ---------------------------------------------------------------- geometry
 __host__ __device__ __forceinline__ void coords(const Dev& s, long long c, int& x, int& y, int& z) {
@@ -511,7 +530,8 @@ int launch_pool_spread(const Dev& s, cudaStream_t st);
 void launch_cell_counts(const Dev& s, unsigned long long* out, cudaStream_t st);
 void launch_init_flat(const Dev& s, double H, cudaStream_t st);
 void launch_init_surface(const Dev& s, const double* H, cudaStream_t st);
-int launch_particles_step(const Dev& s, int have_prev, int last_parity, cudaStream_t st);
+int launch_dem(const Dev& s, int have_prev, cudaStream_t st);
+int launch_remap(const Dev& s, int last_parity, cudaStream_t st);
 void launch_particles_add(const Dev& s, int first, int count, cudaStream_t st);
 void launch_particle_copies(const Dev& s, cudaStream_t st);
 int launch_grid_build(const Dev& s, cudaStream_t st);

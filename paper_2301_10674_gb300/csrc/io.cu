@@ -161,17 +161,28 @@ __global__ void __launch_bounds__(256) k_reduce_cells(Dev s, double* out) {
             if (!fluid(fl)) continue;
             const int t = fl & TYPE_MASK;
             const int y = row % s.ny, z = row / s.ny;
+            // f - w of the cell's post-collision PDFs (16-bit storage: the
+            // reference of each slot's z added back)
             float fv[27];
             if (LP == 0) {
 #pragma unroll
-                for (int q = 0; q < 27; ++q) fv[q] = Store<S>::ld(f + (long long)opp(q) * n + cell);
+                for (int q = 0; q < 27; ++q) {
+                    fv[q] = Store<S>::ld(f + (long long)opp(q) * n + cell);
+                    if (Store<S>::HREF) fv[q] += wq(q) * s.href[z];
+                }
             } else if (x > 0 && x < s.nx - 1 && y > 0 && y < s.ny - 1 && z > 0 && z < s.nz - 1) {
 #pragma unroll
-                for (int q = 0; q < 27; ++q)
+                for (int q = 0; q < 27; ++q) {
                     fv[q] = Store<S>::ld(f + (long long)q * n + (cell + cx(q) + s.nx * cy(q) + sxy * cz(q)));
+                    if (Store<S>::HREF) fv[q] += wq(q) * s.href[z + cz(q)];
+                }
             } else {
 #pragma unroll
-                for (int q = 0; q < 27; ++q) fv[q] = Store<S>::ld(f + fstar_slot(s, q, x, y, z, cell, 1));
+                for (int q = 0; q < 27; ++q) {
+                    const long long i = fstar_slot(s, q, x, y, z, cell, 1);
+                    fv[q] = Store<S>::ld(f + i);
+                    if (Store<S>::HREF) fv[q] += slot_ref(s, i);
+                }
             }
             float d = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
@@ -312,6 +323,174 @@ __global__ void k_bed_height(Dev s, const double* phi, double phi_b, double* h) 
 void launch_bed_height(const Dev& s, double phi_b, double* phi, double* h, cudaStream_t st) {
     k_bed_fraction<<<blocks_for((long long)s.nx * s.nz, 256), 256, 0, st>>>(s, phi);
     k_bed_height<<<blocks_for(s.nx, 128), 128, 0, st>>>(s, phi, phi_b, h);
+}
+
+// ------------------------------------------------------------ water depth
+// Free-surface elevation of every column (x, y): its liquid and solid
+// volume, 1 per liquid or solid cell and the fill level per interface cell
+// (Section 4.2 mean water depth, with the bed height h_b of Section 3.2).
+__global__ void k_surface_elevation(Dev s, double* eta) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)s.nx * s.ny) return;
+    const long long sxy = (long long)s.nx * s.ny;
+    double v = 0.0;
+    for (int z = 0; z < s.nz; ++z) {
+        const long long c = t + sxy * z;
+        const int ty = s.flags[c] & TYPE_MASK;
+        v += (ty == T_LIQ || ty == T_SOL) ? 1.0 : (ty == T_IFC ? (double)s.phi[c] : 0.0);
+    }
+    eta[t] = v;
+}
+// out[0]: mean over x of (y-mean elevation - h_b(x)); out[1]: mean h_b. One
+// block; the sums run in a fixed order.
+__global__ void k_water_depth(Dev s, const double* eta, const double* hb, double* out) {
+    __shared__ double sh[2][256];
+    double d = 0.0, b = 0.0;
+    for (int x = threadIdx.x; x < s.nx; x += blockDim.x) {
+        double e = 0.0;
+        for (int y = 0; y < s.ny; ++y) e += eta[x + (long long)s.nx * y];
+        d += e / s.ny - hb[x];
+        b += hb[x];
+    }
+    sh[0][threadIdx.x] = d;
+    sh[1][threadIdx.x] = b;
+    __syncthreads();
+    for (int off = 128; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + off];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + off];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = sh[0][0] / s.nx;
+        out[1] = sh[1][0] / s.nx;
+    }
+}
+
+void launch_water_depth(const Dev& s, double* bed, double* eta, double* out, cudaStream_t st) {
+    const size_t nxz = (size_t)s.nx * s.nz;
+    launch_bed_height(s, 0.3, bed, bed + nxz, st);
+    k_surface_elevation<<<blocks_for((long long)s.nx * s.ny, 256), 256, 0, st>>>(s, eta);
+    k_water_depth<<<1, 256, 0, st>>>(s, eta, bed + nxz, out);
+}
+
+// ------------------------------------------------------------ bed spectrum
+// Power spectral density of a bed-height series h(t, x) (Section 4.1): the
+// squared modulus of its two-dimensional discrete Fourier transform, mean
+// removed, over the number of samples; the transforms along x and then t are
+// direct sums in FP64 with tabulated twiddles exp(-2 pi i k / N).
+__global__ void k_twiddle(double2* tw, int N) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    double sn, cs;
+    sincospi(2.0 * (double)k / (double)N, &sn, &cs);
+    tw[k] = make_double2(cs, -sn);
+}
+// mean of n values by one block in a fixed order
+__global__ void k_series_mean(const double* h, long long n, double* mean) {
+    __shared__ double sh[1024];
+    double v = 0.0;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) v += h[i];
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = 512; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *mean = sh[0] / (double)n;
+}
+// X1[t][j] = sum_x (h[t][x] - mean) exp(-2 pi i j x / nx); a block per
+// (t, 256 wavenumbers), the row staged through shared memory in chunks
+constexpr int SPEC_CHUNK = 2048;
+__global__ void k_dft_x(const double* h, const double* mean, const double2* tw, int nx, double2* X1) {
+    __shared__ double row[SPEC_CHUNK];
+    const int t = blockIdx.y;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const double m = *mean;
+    double re = 0.0, im = 0.0;
+    int k = 0;                       // (j x) mod nx
+    for (int x0 = 0; x0 < nx; x0 += SPEC_CHUNK) {
+        const int len = min(SPEC_CHUNK, nx - x0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < len; i += blockDim.x) row[i] = h[(long long)t * nx + x0 + i] - m;
+        __syncthreads();
+        if (j < nx) {
+            for (int i = 0; i < len; ++i) {
+                const double2 w = tw[k];
+                re = fma(row[i], w.x, re);
+                im = fma(row[i], w.y, im);
+                k += j;
+                if (k >= nx) k -= nx;
+            }
+        }
+    }
+    if (j < nx) X1[(long long)t * nx + j] = make_double2(re, im);
+}
+// psd[l][j] = |sum_t X1[t][j] exp(-2 pi i l t / nt)|^2 / (nt nx)
+__global__ void k_dft_t(const double2* X1, const double2* tw, int nt, int nx, double* psd) {
+    const int l = blockIdx.y;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nx) return;
+    double re = 0.0, im = 0.0;
+    int k = 0;                       // (l t) mod nt
+    for (int t = 0; t < nt; ++t) {
+        const double2 a = X1[(long long)t * nx + j];
+        const double2 w = tw[k];
+        re += a.x * w.x - a.y * w.y;
+        im += a.x * w.y + a.y * w.x;
+        k += l;
+        if (k >= nt) k -= nt;
+    }
+    psd[(long long)l * nx + j] = (re * re + im * im) / ((double)nt * (double)nx);
+}
+// largest PSD value at wavenumbers 1 <= j <= nx / 2 (ties: lowest l, then j);
+// out[0] value, out[1] l, out[2] j
+__global__ void k_psd_peak(const double* psd, int nt, int nx, double* out) {
+    __shared__ double sv[1024];
+    __shared__ long long si[1024];
+    const int jm = nx / 2;
+    double best = -1.0;
+    long long bi = -1;
+    for (long long i = threadIdx.x; i < (long long)nt * jm; i += blockDim.x) {
+        const int l = (int)(i / jm), j = 1 + (int)(i % jm);
+        const double v = psd[(long long)l * nx + j];
+        if (v > best) { best = v; bi = i; }
+    }
+    sv[threadIdx.x] = best;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int off = 512; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off) {
+            const double v = sv[threadIdx.x + off];
+            const long long i = si[threadIdx.x + off];
+            if (v > sv[threadIdx.x] || (v == sv[threadIdx.x] && i >= 0 && (si[threadIdx.x] < 0 || i < si[threadIdx.x]))) {
+                sv[threadIdx.x] = v;
+                si[threadIdx.x] = i;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = sv[0];
+        out[1] = (double)(si[0] / jm);
+        out[2] = (double)(1 + si[0] % jm);
+    }
+}
+
+int launch_bed_spectrum(const double* h, int nt, int nx, double* psd, double* work, double* peak3, cudaStream_t st) {
+    // work: nx + nt twiddles, nt * nx transformed values (complex), the mean
+    double2* twx = reinterpret_cast<double2*>(work);
+    double2* twt = twx + nx;
+    double2* X1 = twt + nt;
+    double* mean = reinterpret_cast<double*>(X1 + (size_t)nt * nx);
+    k_twiddle<<<blocks_for(nx, 256), 256, 0, st>>>(twx, nx);
+    k_twiddle<<<blocks_for(nt, 256), 256, 0, st>>>(twt, nt);
+    k_series_mean<<<1, 1024, 0, st>>>(h, (long long)nt * nx, mean);
+    k_dft_x<<<dim3((unsigned)blocks_for(nx, 256), (unsigned)nt), 256, 0, st>>>(h, mean, twx, nx, X1);
+    k_dft_t<<<dim3((unsigned)blocks_for(nx, 256), (unsigned)nt), 256, 0, st>>>(X1, twt, nt, nx, psd);
+    k_psd_peak<<<1, 1024, 0, st>>>(psd, nt, nx, peak3);
+    return 6;
 }
 
 }  // namespace fsl

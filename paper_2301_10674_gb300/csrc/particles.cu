@@ -851,7 +851,11 @@ __global__ void k_copy3(const double* a, double* b, int n3) {
     if (k < n3) b[k] = a[k];
 }
 
-int launch_particles_step(const Dev& s, int have_prev, int last_parity, cudaStream_t st) {
+// The particle part of a step in two halves. The DEM half (force average,
+// neighbour list, sub-steps, FP32 copies, particle grid) reads and writes
+// particle state only, so it can run beside the free-surface conversion,
+// which reads and writes cell state only; the re-map half needs both.
+int launch_dem(const Dev& s, int have_prev, cudaStream_t st) {
     if (s.np == 0) return 0;
     int launches = 0;
     const int n3 = 3 * s.np;
@@ -875,6 +879,11 @@ int launch_particles_step(const Dev& s, int have_prev, int last_parity, cudaStre
     }
     k_particle_copies<<<blocks_for(s.np, 128), 128, 0, st>>>(s);
     launches += 1 + launch_grid_build(s, st);
+    return launches;
+}
+
+int launch_remap(const Dev& s, int last_parity, cudaStream_t st) {
+    if (s.np == 0) return 0;
     cudaMemsetAsync(s.tl_count, 0, sizeof(int), st);
     cudaMemsetAsync(s.act_count, 0, sizeof(int), st);
     cudaMemsetAsync(s.dl_count, 0, sizeof(int), st);
@@ -885,7 +894,7 @@ int launch_particles_step(const Dev& s, int have_prev, int last_parity, cudaStre
     k_transitions<<<152 * 4, 128, 0, st>>>(s, last_parity);
     k_apply_transitions<<<152 * 4, 256, 0, st>>>(s);
     k_repair<<<152 * 4, 256, 0, st>>>(s);
-    return launches + 7;
+    return 7;
 }
 
 __global__ void k_init_particles(Dev s, int first, int count, double rho_p) {

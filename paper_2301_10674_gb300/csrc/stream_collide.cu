@@ -121,8 +121,27 @@ __global__ void __launch_bounds__(256, liquid_min_blocks<S>()) k_liquid(Dev s) {
                 v[q] = Store<S>::ld_raw(f + a);
             }
         }
+        if (Store<S>::HREF) {
+            // deviations from w: each slot's reference added (the slot read is
+            // the cell's own in an even step or across a wall face, else the
+            // one at z - c_z)
+            const NbrOffsets o = nbr_offsets(s, x, y, z);
+#pragma unroll
+            for (int q = 0; q < 27; ++q) {
+                const bool own = PAR == 0 || (o.wall & wall_bits(-cx(q), -cy(q), -cz(q)));
+                v[q] += Store<S>::scale * wq(q) * s.href[own ? z : wrap_z(s, z - cz(q))];
+            }
+        }
         float rho, ux, uy, uz;
         collide_scaled(v, Store<S>::scale, s.omega, s.gx, s.gy, s.gz, rho, ux, uy, uz);
+        if (Store<S>::HREF) {
+            const NbrOffsets o = nbr_offsets(s, x, y, z);
+#pragma unroll
+            for (int q = 0; q < 27; ++q) {
+                const bool own = PAR == 0 || (o.wall & wall_bits(cx(q), cy(q), cz(q)));
+                v[q] -= Store<S>::scale * wq(q) * s.href[own ? z : wrap_z(s, z + cz(q))];
+            }
+        }
         if (interior && s.idx32) {
             const unsigned un = (unsigned)n;
 #pragma unroll
@@ -178,6 +197,14 @@ __device__ __forceinline__ void pair_update(const Dev& s, S* f, int x, int row, 
     const int cell = x + s.nx * row;
     const int y = row % s.ny, z = row / s.ny;
     float2 v[27];
+    constexpr float SC = Store<S>::scale;
+    // storage references (16-bit storage): interior pairs fold them into the
+    // collision (even step: every slot at z; odd step: direction c_z read
+    // from z - c_z, written to z + c_z); the others add and remove them value
+    // by value and collide with zero references
+    PairRef ref;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) ref.rd[k] = ref.wt[k] = 0.f;
     if (interior) {
 #pragma unroll
         for (int q = 0; q < 27; ++q) {
@@ -186,6 +213,16 @@ __device__ __forceinline__ void pair_update(const Dev& s, S* f, int x, int row, 
                                               (unsigned)(cell - (cx(q) + s.nx * cy(q) + sxy * cz(q)));
             if (PAR == 0 || cx(q) == 0) v[q] = Pair<S>::ld2(f + a);
             else v[q] = make_float2(Store<S>::ld_raw(f + a), Store<S>::ld_raw(f + a + 1));
+        }
+        if (Store<S>::HREF) {
+            const float h0 = s.href[z];
+            if (PAR == 0) {
+                ref.rd[0] = ref.rd[1] = ref.rd[2] = ref.wt[0] = ref.wt[1] = ref.wt[2] = h0;
+            } else {
+                const float hm = s.href[z - 1], hp = s.href[z + 1];
+                ref.rd[0] = hp; ref.rd[1] = h0; ref.rd[2] = hm;
+                ref.wt[0] = hm; ref.wt[1] = h0; ref.wt[2] = hp;
+            }
         }
     } else {
         const NbrOffsets o0 = nbr_offsets(s, x, y, z), o1 = nbr_offsets(s, x + 1, y, z);
@@ -200,9 +237,14 @@ __device__ __forceinline__ void pair_update(const Dev& s, S* f, int x, int row, 
                 (o1.wall & wb) ? (long long)q * s.n + cell + 1 : (long long)opp(q) * s.n + src1;
             v[q] = make_float2((liq & 1u) ? Store<S>::ld_raw(f + a0) : 0.f,
                                (liq & 2u) ? Store<S>::ld_raw(f + a1) : 0.f);
+            if (Store<S>::HREF) {
+                const float hs = SC * wq(q) * s.href[wrap_z(s, z - cz(q))], ho = SC * wq(q) * s.href[z];
+                v[q].x += (o0.wall & wb) ? ho : hs;
+                v[q].y += (o1.wall & wb) ? ho : hs;
+            }
         }
     }
-    collide_pair<Pair<S>::SCALE_LOG2>(v, s.omega, s.gx, s.gy, s.gz);
+    collide_pair<Pair<S>::SCALE_LOG2, Store<S>::HREF>(v, s.omega, s.gx, s.gy, s.gz, ref);
     if (interior && liq == 3u) {
 #pragma unroll
         for (int q = 0; q < 27; ++q) {
@@ -234,13 +276,19 @@ __device__ __forceinline__ void pair_update(const Dev& s, S* f, int x, int row, 
             const unsigned wb = wall_bits(cx(q), cy(q), cz(q));
             const int dst0 = cell + o0.ox[1 + cx(q)] + o0.oy[1 + cy(q)] + o0.oz[1 + cz(q)];
             const int dst1 = cell + 1 + o1.ox[1 + cx(q)] + o1.oy[1 + cy(q)] + o1.oz[1 + cz(q)];
+            float2 e = v[q];
+            if (Store<S>::HREF) {
+                const float ht = SC * wq(q) * s.href[wrap_z(s, z + cz(q))], ho = SC * wq(q) * s.href[z];
+                e.x -= (o0.wall & wb) ? ho : ht;
+                e.y -= (o1.wall & wb) ? ho : ht;
+            }
             if (liq & 1u)
                 Store<S>::st_raw(
-                    f + ((o0.wall & wb) ? (long long)opp(q) * s.n + cell : (long long)q * s.n + dst0), v[q].x);
+                    f + ((o0.wall & wb) ? (long long)opp(q) * s.n + cell : (long long)q * s.n + dst0), e.x);
             if (liq & 2u)
                 Store<S>::st_raw(
                     f + ((o1.wall & wb) ? (long long)opp(q) * s.n + cell + 1 : (long long)q * s.n + dst1),
-                    v[q].y);
+                    e.y);
         }
     }
 }
@@ -502,7 +550,12 @@ __global__ void __launch_bounds__(SP_TILE / 2, 6) k_liquid_staged_pair(Dev s) {
             float2 v[27];
 #pragma unroll
             for (int q = 0; q < 27; ++q) v[q] = Pair<S>::ld2(buf + q * L::ROW + p);
-            collide_pair<Pair<S>::SCALE_LOG2>(v, s.omega, s.gx, s.gy, s.gz);
+            // an even step reads and writes the cells' own slots: one reference
+            PairRef ref;
+            const float h0 = s.href[(unsigned)cell / ((unsigned)s.nx * (unsigned)s.ny)];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) ref.rd[k] = ref.wt[k] = h0;
+            collide_pair<Pair<S>::SCALE_LOG2, true>(v, s.omega, s.gx, s.gy, s.gz, ref);
             if (liq == 3u) {
 #pragma unroll
                 for (int q = 0; q < 27; ++q) Pair<S>::st2(f + ((unsigned)opp(q) * un + (unsigned)cell), v[q]);
@@ -640,12 +693,24 @@ __global__ void __launch_bounds__(256, 3) k_solid_links(Dev s) {
                 key = p;
             }
             // phase 2: the post-collision PDFs the fluid neighbours send here
+            // (16-bit storage: references of the solid cell's z and of the
+            // neighbour's; an even step reads at the solid cell and writes at
+            // the neighbour, an odd step the other way round)
+            float hz = 0.f, hn[3] = {0.f, 0.f, 0.f};
+            if (Store<S>::HREF) {
+                hz = s.href[z];
+                hn[0] = (o.wall & 16u) ? hz : s.href[wrap_z(s, z - 1)];
+                hn[1] = hz;
+                hn[2] = (o.wall & 32u) ? hz : s.href[wrap_z(s, z + 1)];
+            }
             float fo[27];
 #pragma unroll
             for (int q = 0; q < 27; ++q) {
                 const int xn = cell + o.ox[1 + cx(q)] + o.oy[1 + cy(q)] + o.oz[1 + cz(q)];
                 const long long a = PAR == 0 ? (long long)opp(q) * n + cell : (long long)q * n + xn;
-                fo[q] = ((fluidm >> q) & 1u) ? Store<S>::ld(f + a) : 0.f;
+                float v = ((fluidm >> q) & 1u) ? Store<S>::ld(f + a) : 0.f;
+                if (Store<S>::HREF) v += wq(q) * (PAR == 0 ? hz : hn[1 + cz(q)]);
+                fo[q] = v;
             }
             // phase 3: bounce-back values and momentum exchange
             if (fluidm) {
@@ -665,7 +730,7 @@ __global__ void __launch_bounds__(256, 3) k_solid_links(Dev s) {
                     const float val = fo[q] + 6.f * wq(q) * cu;
                     if ((liqm >> q) & 1u) injected += 6.f * wq(q) * cu;
                     const long long dst = PAR == 0 ? (long long)q * n + xn : (long long)opp(q) * n + cell;
-                    Store<S>::st(f + dst, val);
+                    Store<S>::st(f + dst, Store<S>::HREF ? val - wq(q) * (PAR == 0 ? hn[1 + cz(q)] : hz) : val);
                     const float sum = fo[q] + val, dif = fo[q] - val;
                     const float Fx = -cx(q) * sum - ubx * dif;
                     const float Fy = -cy(q) * sum - uby * dif;
@@ -729,9 +794,15 @@ __global__ void __launch_bounds__(128) k_interface(Dev s) {
             const float phix = s.phi[cell];
             const float mx = s.mass[cell];
             const float4 nn = s.nrm[cell];
+            // 16-bit storage: references of the slots (the cell's own z, the
+            // pull source's z - c_z in an odd step, the target's z + c_z)
+            const float hz = Store<S>::HREF ? s.href[z] : 0.f;
             float fo[27];
 #pragma unroll
-            for (int q = 0; q < 27; ++q) fo[q] = Store<S>::ld(fs + (long long)q * n + cell);
+            for (int q = 0; q < 27; ++q) {
+                fo[q] = Store<S>::ld(fs + (long long)q * n + cell);
+                if (Store<S>::HREF) fo[q] += wq(q) * hz;
+            }
             float v[27];
 #pragma unroll
             for (int q = 0; q < 27; ++q) {
@@ -740,6 +811,7 @@ __global__ void __launch_bounds__(128) k_interface(Dev s) {
                 const long long src = pull ? sx + (long long)s.nx * (sy + (long long)s.ny * sz) : cell;
                 const long long a = PAR == 0 ? (long long)q * n + cell : (long long)opp(q) * n + src;
                 v[q] = pull ? Store<S>::ld(f + a) : 0.f;
+                if (Store<S>::HREF && pull) v[q] += wq(q) * (PAR == 0 ? hz : s.href[sz]);
             }
             // own collision velocity from the post-collision PDFs
             float d = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
@@ -790,7 +862,8 @@ __global__ void __launch_bounds__(128) k_interface(Dev s) {
             collide(v, s.omega, s.gx, s.gy, s.gz, rho, ux, uy, uz);
             if (PAR == 0) {
 #pragma unroll
-                for (int q = 0; q < 27; ++q) Store<S>::st(f + (long long)opp(q) * n + cell, v[q]);
+                for (int q = 0; q < 27; ++q)
+                    Store<S>::st(f + (long long)opp(q) * n + cell, Store<S>::HREF ? v[q] - wq(q) * hz : v[q]);
             } else {
 #pragma unroll
                 for (int q = 0; q < 27; ++q) {
@@ -798,11 +871,12 @@ __global__ void __launch_bounds__(128) k_interface(Dev s) {
                     const bool out = tx < 0 || ty < 0 || tz < 0;
                     const long long a = out ? (long long)opp(q) * n + cell
                                             : (long long)q * n + tx + (long long)s.nx * (ty + (long long)s.ny * tz);
-                    Store<S>::st(f + a, v[q]);
+                    Store<S>::st(f + a, Store<S>::HREF ? v[q] - wq(q) * (out ? hz : s.href[tz]) : v[q]);
                 }
             }
 #pragma unroll
-            for (int q = 0; q < 27; ++q) Store<S>::st(fs + (long long)q * n + cell, v[q]);
+            for (int q = 0; q < 27; ++q)
+                Store<S>::st(fs + (long long)q * n + cell, Store<S>::HREF ? v[q] - wq(q) * hz : v[q]);
             // phi = m / rho is refreshed after the sweep: neighbours read the
             // old phi in their mass exchange
             s.mass[cell] = mx + dm;

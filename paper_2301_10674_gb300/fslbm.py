@@ -49,7 +49,8 @@ EXPORTED = (
     "fslbm_cell_counts", "fslbm_reduce_fields_noalloc", "fslbm_destroy", "fslbm_strerror",
     "fslbm_set_normal_model", "fslbm_normal_stats", "fslbm_mlp_stencils", "fslbm_mlp_gradient",
     "fslbm_mlp_train", "fslbm_mlp_infer", "fslbm_bed_height", "fslbm_set_body_force",
-    "fslbm_get_body_force", "fslbm_set_flow_control", "fslbm_set_wait_limit",
+    "fslbm_get_body_force", "fslbm_set_flow_control", "fslbm_set_wait_limit", "fslbm_transport_numbers",
+    "fslbm_bed_spectrum",
 )
 
 MLP_NPARAM = 6212
@@ -128,6 +129,9 @@ def load():
     L.fslbm_get_body_force.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     L.fslbm_set_flow_control.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int64]
     L.fslbm_set_wait_limit.argtypes = [vp, ctypes.c_int64]
+    L.fslbm_transport_numbers.argtypes = [vp, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    L.fslbm_bed_spectrum.argtypes = [vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_double, ctypes.c_double, vp,
+                                     ctypes.POINTER(ctypes.c_double), vp]
     L.fslbm_reduce_fields_noalloc.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), vp, vp]
     L.fslbm_set_normal_model.argtypes = [vp, vp, ctypes.c_int64]
     L.fslbm_normal_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
@@ -219,6 +223,15 @@ def fslbm_reduce_fields_noalloc(pdf, types, mass, ncells: int, g, out, stream: i
 
 def _stream(stream):
     return ctypes.c_void_p(stream or 0)
+
+
+def fslbm_bed_spectrum(h, nt: int, nx: int, dx: float, dt: float, psd, stream=None) -> tuple[int, np.ndarray]:
+    """PSD of a device bed-height series h (nt, nx) into the device buffer
+    psd; returns (code, [wavelength, period, celerity, amplitude])."""
+    peak = np.zeros(4, np.float64)
+    rc = load().fslbm_bed_spectrum(_ptr(h), int(nt), int(nx), float(dx), float(dt), _ptr(psd),
+                                   peak.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream(stream))
+    return rc, peak
 
 
 def fslbm_set_normal_model(h, w_bf16_bits) -> int:
@@ -446,6 +459,15 @@ class Simulation:
         """Polls before a bounded device wait gives up (test hook of the
         error path; see fslbm_set_wait_limit)."""
         _check(load().fslbm_set_wait_limit(self.h, int(polls)), "fslbm_set_wait_limit")
+
+    def transport_numbers(self, d50: float) -> dict:
+        """Mean water depth, slope, Shields and Einstein numbers, bedload rate
+        and mean bed height of the current state (fslbm_transport_numbers)."""
+        out = np.zeros(6, np.float64)
+        _check(load().fslbm_transport_numbers(self.h, float(d50), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "fslbm_transport_numbers")
+        keys = ("water_depth", "tan_psi", "shields", "q_b", "einstein", "bed_height")
+        return dict(zip(keys, (float(v) for v in out)))
 
     def cell_counts(self) -> np.ndarray:
         out = np.zeros(4, np.int64)

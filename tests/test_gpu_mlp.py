@@ -327,8 +327,11 @@ def test_laplace_pressure_on_the_gpu():
     finite-difference normal and the constant curvature kappa0 settles at
     the reconstruction density rho_gas + 6 sigma kappa0 (the oracle's closed
     form, to 1e-3 of the offset), keeps its mass, and follows the oracle's
-    density within 1e-6; sigma = 0 leaves the density at rho_gas."""
-    sigma, kappa0 = 1e-3, 1.0 / 6.0
+    density within 1e-6; sigma = 0 leaves the density at rho_gas. The
+    network's parameters, biases included, reach the library as BF16, so
+    kappa0 = 1/8 is chosen exactly representable (1/6 would arrive as
+    0.16699)."""
+    sigma, kappa0 = 1e-3 / 0.75, 0.125
     theta = py_network(1.0 / 16.0, kappa0)
     out = {}
     for sg in (sigma, 0.0):

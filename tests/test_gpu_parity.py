@@ -380,6 +380,31 @@ def test_staged_sweep_16bit(storage, tol):
     sim.close()
 
 
+@pytest.mark.parametrize("storage,tol", [(F.STORE_FP16, 1e-2), (F.STORE_BF16, 2e-2)])
+def test_16bit_storage_keeps_a_slow_flow_under_a_deep_head(storage, tol):
+    """A 110-cell deep liquid at rest starts to flow under a slope force of
+    3e-8 (the laminar force of the large flume's Froude target): after 300
+    steps its bulk velocity is about 1e-5, a PDF signal 3 w u of 3e-5 w
+    beside the hydrostatic head 3 |g_z| h = 3.3e-3 w. The 16-bit stores hold
+    deviations from the hydrostatic reference of the flat surface, so the
+    rounding acts on the flow: bulk velocity within 1% (FP16) / 2% (BF16) of
+    FP32, and the liquid mass kept to 1e-6."""
+    w = W.Workload(name="deep", nx=64, ny=16, nz=128, g=(3e-8, 0.0, -1e-5), liquid_height=110.0,
+                   bed="none").generate()
+    out = {}
+    for st in (F.STORE_FP32, storage):
+        sim = _sim(w, storage=st, spheres=False)
+        m0 = sim.reduce()[0]
+        sim.step(300)
+        r = sim.reduce()
+        assert abs(r[0] / m0 - 1) < 1e-6
+        out[st] = r[4]
+        sim.close()
+    u32, u16 = out[F.STORE_FP32], out[storage]
+    assert 5e-6 < u32 < 2e-5, u32
+    assert abs(u16 - u32) <= tol * abs(u32), (u16, u32)
+
+
 def _dry(L=40, **kw):
     w = W.Workload(name="dry", nx=L, ny=L, nz=L, periodic=(1, 1, 1), g=(0.0, 0.0, 0.0), liquid_height=0.0,
                    bed="none", **kw).generate()
@@ -483,4 +508,54 @@ def test_flow_rate_control_matches_oracle():
     g = sim.body_force()
     sim.step(100)
     assert np.array_equal(sim.body_force(), g)          # control off: the force stays
+    sim.close()
+
+
+def test_bed_spectrum_matches_the_oracle():
+    """PSD of a bed-height series (Section 4.1) on the GPU against the
+    oracle's numpy transform: two travelling sines and noise on a 40 x 96
+    grid, PSD within 1e-9 of its largest value, and the same dominant bedform
+    (wavelength, period, celerity, amplitude)."""
+    import torch
+    from oracle import diagnostics as D
+    nt, nx, dx, dt = 40, 96, 1.0, 25.0
+    rng = np.random.default_rng(5)
+    x = np.arange(nx)
+    t = np.arange(nt)[:, None]
+    h = 140.0 + 1.3 * np.sin(2 * np.pi * (4 * x / nx - 3 * t / nt)) + 0.4 * np.cos(2 * np.pi * (9 * x / nx + 2 * t / nt)) \
+        + 0.05 * rng.standard_normal((nt, nx))
+    dh = torch.from_numpy(h).cuda()
+    psd = torch.empty((nt, nx), dtype=torch.float64, device="cuda")
+    rc, peak = F.fslbm_bed_spectrum(dh, nt, nx, dx, dt, psd)
+    assert rc == 0
+    ref, (lam, T, c, amp) = D.bed_spectrum(h, dx, dt)
+    got = psd.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-9 * ref.max()
+    assert np.allclose(peak, [lam, T, c, amp], rtol=1e-9, atol=0)
+    assert peak[0] == pytest.approx(24.0) and peak[2] > 0
+    assert F.fslbm_bed_spectrum(dh, 1, nx, dx, dt, psd)[0] == -1
+
+
+def test_transport_numbers_match_their_definitions():
+    """Mean water depth, slope, Shields and Einstein numbers (Section 4.2,
+    Table 2) of the tiny flume after a few steps: the library's values equal
+    the oracle's definitions applied to the same cell types and fill levels,
+    and the bedload rate of Eq. (1) that fslbm_reduce returns."""
+    from oracle import diagnostics as D
+    w = W.tiny().generate()
+    sim = _sim(w)
+    sim.step(12)
+    tn = sim.transport_numbers(w.diameter)
+    t, phi = sim.get(F.FIELD_TYPE), sim.get(F.FIELD_PHI)
+    depth = D.mean_water_depth(t, phi)
+    assert tn["water_depth"] == pytest.approx(depth, rel=0, abs=1e-9)
+    assert tn["bed_height"] == pytest.approx(D.bed_height(t, 0.3).mean(), rel=0, abs=1e-9)
+    tp = w.g[0] / abs(w.g[2])
+    assert tn["tan_psi"] == pytest.approx(tp, rel=1e-15)
+    assert tn["shields"] == pytest.approx(D.shields(depth, tp, w.rho_p, w.diameter), rel=1e-9)
+    qb = sim.reduce()[6]
+    assert tn["q_b"] == pytest.approx(qb, rel=1e-12, abs=1e-300)
+    assert tn["einstein"] == pytest.approx(D.einstein(qb, w.rho_p, float(np.linalg.norm(w.g)), w.diameter),
+                                           rel=1e-9, abs=1e-300)
+    assert 10.0 < tn["water_depth"] < 26.0
     sim.close()
