@@ -424,6 +424,7 @@ def run_ours(args, world, rank, local):
         "gpu_launches": int(head["launches"]),
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "oracle_table": ORACLE_TABLE,
         "comparison": comparison,
         "learned_normal": None if theta is None else {
             "training": train,
@@ -456,18 +457,24 @@ def run_e2e(args, w, storage, theta, stream, world):
     if bits is not None:
         F._check(F.fslbm_set_normal_model(h, bits), "fslbm_set_normal_model")
     t2 = time.perf_counter()
+    t_step = t_red = 0.0
     for _ in range(args.steps):
+        ta = time.perf_counter()
         F._check(F.fslbm_step(h, 1), "fslbm_step")
+        tb = time.perf_counter()
         rc, out = F.fslbm_reduce(h)
         F._check(rc, "fslbm_reduce")
         diag[:] = out
+        t_step += tb - ta
+        t_red += time.perf_counter() - tb
     t3 = time.perf_counter()
     F.fslbm_destroy(h)
     torch.cuda.synchronize()
     t4 = time.perf_counter()
     dt = _max_over_ranks(t4 - t0, "cuda")
     phases = {"create_s": round(t1 - t0, 4), "spheres_and_weights_s": round(t2 - t1, 4),
-              "steps_s": round(t3 - t2, 4), "destroy_s": round(t4 - t3, 4)}
+              "steps_s": round(t3 - t2, 4), "destroy_s": round(t4 - t3, 4),
+              "step_calls_s": round(t_step, 4), "reduce_calls_s": round(t_red, 4)}
     h2d = xyz.nbytes + rad.nbytes + fix.nbytes + __import__("ctypes").sizeof(params) + \
         (0 if bits is None else bits.nbytes)
     return {"value": round(_throughput(world, w.ncells, args.steps, dt), 2), "unit": UNIT,
@@ -559,6 +566,26 @@ def run_precision_study(args):
             "learned_normal_training": train, "forms": forms}
 
 
+# The oracle timed on the host cores of the GB300 machine (16 Grace cores) by
+# `python bench.py --oracle-table`: the tiny flume in full, the mid flume
+# and a 128-wide x-crop of the precision flume for 200 steps each. The line
+# quotes it beside the live cpu_baseline.
+ORACLE_TABLE = None
+
+
+def run_oracle_table() -> dict:
+    """Oracle MLUPS of the smaller workloads, each with its particle bed and
+    the finite-difference normal."""
+    from paper_2301_10674_gb300 import workloads as W
+    rows = []
+    for name, crop, steps in (("tiny", None, 1000), ("mid", None, 200), ("precision", 128, 200)):
+        w = W.WORKLOADS[name]().generate()
+        r = run_oracle(w, steps=steps, warmup=1, crop_nx=crop or w.nx)
+        rows.append({"workload": w.name, "sample": r["sample"], "mlups": round(r["value"], 3), "cores": r["cores"],
+                     "mlups_per_core": round(r["value"] / r["cores"], 4), "seconds": round(r["seconds"], 1)})
+    return {"oracle_table": rows}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return None
@@ -595,9 +622,12 @@ def main():
     ap.add_argument("--mlp-steps", type=int, default=40000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--cpu-steps", type=int, default=5)
     ap.add_argument("--cpu-crop", type=int, default=64)
-    ap.add_argument("--ref-crop", type=int, default=4)
+    ap.add_argument("--ref-crop", type=int, default=64)
+    ap.add_argument("--oracle-table", action="store_true",
+                    help="instead of the benchmark: time the oracle on the tiny flume, the mid flume and a "
+                         "128-wide crop of the precision flume (host cores)")
     ap.add_argument("--precision-study", action="store_true",
                     help="instead of the benchmark: every form against the FP64 oracle on a crop of the "
                          "1024x64x128 flume")
@@ -609,6 +639,9 @@ def main():
     world, rank, local = _dist()
     if args.precision_study:
         print(json.dumps(run_precision_study(args)), flush=True)
+        return
+    if args.oracle_table:
+        print(json.dumps(run_oracle_table()), flush=True)
         return
     if args.impl == "reference":
         line = run_reference(args, world, rank)

@@ -112,12 +112,18 @@ typedef struct {
     int32_t excess_even;         /* 1: the excess mass of a converting cell is split
                                     evenly over its receivers instead of along the
                                     normal (a variant of the free-surface method) */
-    int32_t reserved;            /* 0 */
+    int32_t lubrication;         /* 1: lubrication corrections of the DEM where a gap
+                                    between two particles, or a particle and a wall,
+                                    is below the 2/3 cell the lattice resolves
+                                    (Section 2.2): normal 6 pi mu R^2 (1/h - 1/h_c),
+                                    tangential 6 pi mu R (8/15) ln(h_c / h), R the
+                                    effective radius, h clamped at 1e-2 */
 } fslbm_params;
 
 /* Fills *p with defaults: periodic x, walls in y and z, omega = 1/0.51,
  * g = 0, rho_gas = 1, eps_conv = eps_normal = 1e-2, reconstruct_normal = 1,
- * rho_p = 2.55, e = 0.88, mu = 0.5, nu_p = 0.22, T_c = 24, 10 sub-steps. */
+ * rho_p = 2.55, e = 0.88, mu = 0.5, nu_p = 0.22, T_c = 24, 10 sub-steps,
+ * lubrication on. */
 void fslbm_default_params(fslbm_params* p);
 
 /* Creates a simulation on the current CUDA device. `cuda_stream` is a

@@ -63,6 +63,7 @@ class _Params(ctypes.Structure):
         ("link_mass_correction", ctypes.c_int),
         ("sigma", ctypes.c_double),
         ("excess_even", ctypes.c_int),
+        ("lubrication", ctypes.c_int),
     ]
 
 
@@ -132,6 +133,7 @@ class OracleParams:
     link_mass_correction: int = 1
     sigma: float = 0.0
     excess_even: int = 0
+    lubrication: int = 1
 
     def _c(self) -> _Params:
         p = _Params()
@@ -153,6 +155,7 @@ class OracleParams:
         p.link_mass_correction = self.link_mass_correction
         p.sigma = self.sigma
         p.excess_even = self.excess_even
+        p.lubrication = self.lubrication
         return p
 
 

@@ -75,6 +75,7 @@ typedef struct {
                                  density is rho_gas + 6 sigma kappa (R-21) */
     int excess_even;          /* 1: excess mass split evenly over the receivers
                                  instead of by the normal weights (R-8 variant) */
+    int lubrication;          /* 1: lubrication corrections below the resolved gap (R-23) */
 } orc_params;
 
 typedef struct {
@@ -850,6 +851,35 @@ static void contact_force(const orc* o, double meff, const double n[3], double d
     for (int a = 0; a < 3; ++a) F[a] = -fn * n[a] + Ft[a];
 }
 
+/* Lubrication correction (Section 2.2, reading R-23): the paper adds normal
+ * and tangential lubrication forces where a gap between two surfaces is too
+ * small for the lattice to resolve, and gives no formula. Reading: the
+ * asymptotic resistances of two nearly touching spheres with effective
+ * radius R_eff = r_i r_j / (r_i + r_j) (a sphere at a wall: R_eff = r),
+ *   normal      6 pi mu R_eff^2 / h
+ *   tangential  6 pi mu R_eff (8/15) ln(1 / h)   (relative sliding)
+ * each less its value at the gap h_c = 2/3 cell that the lattice still
+ * resolves, so both vanish at h_c; the gap is clamped below at h_min = 1e-2
+ * cell. mu = rho nu with the reference density 1. n points from the
+ * particle to its partner (or the wall), vrel is the relative velocity of
+ * the surfaces at the contact point; returns the force on the particle. */
+#define LUB_HC (2.0 / 3.0)
+#define LUB_HMIN 1e-2
+static void lubrication_force(const orc* o, double Reff, const double n[3], double h, const double vrel[3],
+                              double Fl[3], double Ft[3])
+{
+    double hh = h < LUB_HMIN ? LUB_HMIN : h;
+    double mu = (1.0 / o->p.omega - 0.5) / 3.0;
+    double vn = vrel[0] * n[0] + vrel[1] * n[1] + vrel[2] * n[2];
+    double cn = 6.0 * M_PI * mu * Reff * Reff * (1.0 / hh - 1.0 / LUB_HC);
+    double ct = 6.0 * M_PI * mu * Reff * (8.0 / 15.0) * log(LUB_HC / hh);
+    for (int a = 0; a < 3; ++a) {
+        double vt = vrel[a] - vn * n[a];
+        Ft[a] = -ct * vt;
+        Fl[a] = -cn * vn * n[a] + Ft[a];
+    }
+}
+
 static void dem_substep(orc* o, const double* Fhyd, const double* Thyd, double dts)
 {
     int np = o->np;
@@ -869,6 +899,25 @@ static void dem_substep(orc* o, const double* Fhyd, const double* Thyd, double d
             for (int a = 0; a < 3; ++a) d[a] = min_image(o, a, o->X[3 * j + a] - o->X[3 * i + a]);
             double dist2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
             double rs = o->R[i] + o->R[j];
+            if (o->p.lubrication && dist2 < (rs + LUB_HC) * (rs + LUB_HC)) {
+                double dist = sqrt(dist2);
+                double n[3] = {d[0] / dist, d[1] / dist, d[2] / dist};
+                double wsum[3], wn[3], vrel[3], Fl[3], Ft[3], ti[3], tj[3];
+                for (int a = 0; a < 3; ++a) wsum[a] = o->R[i] * o->W[3 * i + a] + o->R[j] * o->W[3 * j + a];
+                cross(wsum, n, wn);
+                for (int a = 0; a < 3; ++a) vrel[a] = o->U[3 * i + a] - o->U[3 * j + a] + wn[a];
+                lubrication_force(o, o->R[i] * o->R[j] / rs, n, dist - rs, vrel, Fl, Ft);
+                double ri_n[3] = {o->R[i] * n[0], o->R[i] * n[1], o->R[i] * n[2]};
+                double rj_n[3] = {o->R[j] * n[0], o->R[j] * n[1], o->R[j] * n[2]};
+                cross(ri_n, Ft, ti);
+                cross(rj_n, Ft, tj);
+                for (int a = 0; a < 3; ++a) {
+                    F[3 * i + a] += Fl[a];
+                    F[3 * j + a] -= Fl[a];
+                    T[3 * i + a] += ti[a];
+                    T[3 * j + a] += tj[a];
+                }
+            }
             if (dist2 >= rs * rs) {
                 orc_hist* h = hist_find(o, i, j, 0);
                 if (h) h->used = 0;
@@ -911,6 +960,18 @@ static void dem_substep(orc* o, const double* Fhyd, const double* Thyd, double d
                 int wid = -1 - (2 * a + side);
                 double dist = side == 0 ? o->X[3 * i + a] : (L[a] - o->X[3 * i + a]);
                 double delta = o->R[i] - dist;
+                if (o->p.lubrication && -delta < LUB_HC) {
+                    double n[3] = {0, 0, 0};
+                    n[a] = side == 0 ? -1.0 : 1.0;
+                    double rw[3] = {o->R[i] * o->W[3 * i + 0], o->R[i] * o->W[3 * i + 1], o->R[i] * o->W[3 * i + 2]};
+                    double wn[3], vrel[3], Fl[3], Ft[3], ti[3];
+                    cross(rw, n, wn);
+                    for (int b = 0; b < 3; ++b) vrel[b] = o->U[3 * i + b] + wn[b];
+                    lubrication_force(o, o->R[i], n, -delta, vrel, Fl, Ft);
+                    double ri_n[3] = {o->R[i] * n[0], o->R[i] * n[1], o->R[i] * n[2]};
+                    cross(ri_n, Ft, ti);
+                    for (int b = 0; b < 3; ++b) { F[3 * i + b] += Fl[b]; T[3 * i + b] += ti[b]; }
+                }
                 if (delta <= 0.0) {
                     orc_hist* h = hist_find(o, i, wid, 0);
                     if (h) h->used = 0;

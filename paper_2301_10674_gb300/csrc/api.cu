@@ -132,6 +132,7 @@ void fslbm_default_params(fslbm_params* p) {
     p->collision_time = 24.0;
     p->dem_substeps = 10;
     p->link_mass_correction = 1;
+    p->lubrication = 1;
 }
 
 const char* fslbm_strerror(int code) {
@@ -161,7 +162,7 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     if (p->normal_model < 0 || p->normal_model > 1 || p->init_profile != 0) return FSLBM_EINVAL;
     if (p->storage < 0 || p->storage > 2) return FSLBM_EINVAL;
     if (p->link_mass_correction < 0 || p->link_mass_correction > 1) return FSLBM_EINVAL;
-    if (p->excess_even < 0 || p->excess_even > 1 || p->reserved != 0) return FSLBM_EINVAL;
+    if (p->excess_even < 0 || p->excess_even > 1 || p->lubrication < 0 || p->lubrication > 1) return FSLBM_EINVAL;
     if (p->dem_substeps < 1 || !(p->restitution > 0.0 && p->restitution <= 1.0)) return FSLBM_EINVAL;
     if (!(p->collision_time > 0.0) || !(p->rho_p > 0.0) || !(p->rho_gas > 0.0)) return FSLBM_EINVAL;
     if (!(p->poisson >= 0.0 && p->poisson < 1.0) || !(p->friction >= 0.0)) return FSLBM_EINVAL;
@@ -226,6 +227,8 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     d.dn_coef = -2.0 * le / p->collision_time;
     d.kt_ratio = 2.0 * (1.0 - p->poisson) / (2.0 - p->poisson);
     d.dem_substeps = p->dem_substeps;
+    d.lub = p->lubrication;
+    d.lub_mu = (1.0 / p->omega - 0.5) / 3.0;
     s->elem = p->storage == FSLBM_STORE_FP32 ? 4 : 2;
 
     bool ok = true;

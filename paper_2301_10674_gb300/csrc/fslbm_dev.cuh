@@ -119,6 +119,8 @@ struct Dev {
     double kn_coef, dn_coef, kt_ratio;          // contact law constants (host-computed)
     double gxd, gyd, gzd;
     int dem_substeps;
+    int lub;                                    // lubrication corrections on
+    double lub_mu;                              // dynamic viscosity rho nu of the liquid
     // particle grid (DEM neighbours and the particle-to-cell map)
     int gnx, gny, gnz;
     double ghx, ghy, ghz;

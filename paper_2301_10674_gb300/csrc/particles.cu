@@ -187,9 +187,31 @@ __device__ __forceinline__ float wrapf(float d, int L, int periodic) {
     return d;
 }
 
+// Lubrication corrections (Section 2.2): the paper augments the DEM with
+// normal and tangential lubrication forces where a gap is too small for the
+// lattice to resolve and gives no formula. These are the asymptotic
+// resistances of two nearly touching spheres with effective radius R,
+// normal 6 pi mu R^2 / h and tangential 6 pi mu R (8/15) ln(1 / h), each less
+// its value at the resolved gap h_c = 2/3 cell, with h clamped at 1e-2.
+constexpr float LUB_HC = 2.f / 3.f, LUB_HMIN = 1e-2f;
+// force on the particle (n toward the partner or wall, vrel the relative
+// velocity of the surfaces at the contact point) and its tangential part
+__device__ __forceinline__ void lub_f(const Dev& s, float R, const float n[3], float h, const float vrel[3],
+                                      float Fl[3], float Ft[3]) {
+    const float hh = fmaxf(h, LUB_HMIN);
+    const float vn = vrel[0] * n[0] + vrel[1] * n[1] + vrel[2] * n[2];
+    const float k = 6.f * 3.14159265f * (float)s.lub_mu * R;
+    const float cn = k * R * (1.f / hh - 1.f / LUB_HC);
+    const float ct = k * (8.f / 15.f) * logf(LUB_HC / hh);
+    for (int a = 0; a < 3; ++a) {
+        Ft[a] = -ct * (vrel[a] - vn * n[a]);
+        Fl[a] = -cn * vn * n[a] + Ft[a];
+    }
+}
+
 // Neighbour list of every mobile particle for the sub-steps of one LBM
-// step: particles whose surfaces are within half a cell (the motion within a
-// step is far below that).
+// step: particles whose surfaces are within 3/4 cell (beyond the
+// lubrication range; the motion within a step is far below the margin).
 __global__ void k_dem_neighbours(Dev s) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= s.np) return;
@@ -212,7 +234,7 @@ __global__ void k_dem_neighbours(Dev s) {
                         const float4 xrj = s.Xr[j];
                         const float ex = wrapf(xrj.x - xri.x, s.nx, s.per_x), ey = wrapf(xrj.y - xri.y, s.ny, s.per_y),
                                     ez = wrapf(xrj.z - xri.z, s.nz, s.per_z);
-                        const float reach = fabsf(xri.w) + fabsf(xrj.w) + 0.5f;
+                        const float reach = fabsf(xri.w) + fabsf(xrj.w) + 0.75f;
                         if (ex * ex + ey * ey + ez * ez > reach * reach) continue;
                         if (cnt < NB_SLOTS) s.nb[(long long)p * NB_SLOTS + cnt] = j;
                         cnt++;
@@ -329,7 +351,9 @@ __global__ void __launch_bounds__(64) k_dem_substep(Dev s, const double* __restr
             const float rjf = (float)s.R[j];
             const float dist2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
             const float rs = rif + rjf;
-            if (dist2 >= rs * rs) continue;
+            const bool touch = dist2 < rs * rs;
+            const bool lub = s.lub && dist2 < (rs + LUB_HC) * (rs + LUB_HC);
+            if (!touch && !lub) continue;
             const float dist = sqrtf(dist2);
             const float inv = 1.f / dist;
             const float n[3] = {d[0] * inv, d[1] * inv, d[2] * inv};
@@ -340,6 +364,14 @@ __global__ void __launch_bounds__(64) k_dem_substep(Dev s, const double* __restr
                                  wsum[0] * n[1] - wsum[1] * n[0]};
             float vrel[3];
             for (int a = 0; a < 3; ++a) vrel[a] = Uf[a] - (float)Ua[3 * j + a] + wn[a];
+            if (lub) {
+                float Fl[3], Ftl[3];
+                lub_f(s, rif * rjf / rs, n, -delta, vrel, Fl, Ftl);
+                const float tq[3] = {rif * (n[1] * Ftl[2] - n[2] * Ftl[1]), rif * (n[2] * Ftl[0] - n[0] * Ftl[2]),
+                                     rif * (n[0] * Ftl[1] - n[1] * Ftl[0])};
+                for (int a = 0; a < 3; ++a) { F[a] += (double)Fl[a]; T[a] += (double)tq[a]; }
+            }
+            if (!touch) continue;
             const float mj = (float)s.M[j];
             const float meff = mif * mj / (mif + mj);
             const int slot = hist_slot(s, p, j, hpart, seen);
@@ -360,13 +392,22 @@ __global__ void __launch_bounds__(64) k_dem_substep(Dev s, const double* __restr
         for (int side = 0; side < 2; ++side) {
             const float dist = (float)(side == 0 ? X[a] : (L[a] - X[a]));
             const float delta = rif - dist;
-            if (delta <= 0.f) continue;
+            const bool lub = s.lub && -delta < LUB_HC;
+            if (delta <= 0.f && !lub) continue;
             float n[3] = {0.f, 0.f, 0.f};
             n[a] = side == 0 ? -1.f : 1.f;
             const float rw[3] = {rif * Wf[0], rif * Wf[1], rif * Wf[2]};
             const float wn[3] = {rw[1] * n[2] - rw[2] * n[1], rw[2] * n[0] - rw[0] * n[2],
                                  rw[0] * n[1] - rw[1] * n[0]};
             const float vrel[3] = {Uf[0] + wn[0], Uf[1] + wn[1], Uf[2] + wn[2]};
+            if (lub) {
+                float Fl[3], Ftl[3];
+                lub_f(s, rif, n, -delta, vrel, Fl, Ftl);
+                const float tq[3] = {rif * (n[1] * Ftl[2] - n[2] * Ftl[1]), rif * (n[2] * Ftl[0] - n[0] * Ftl[2]),
+                                     rif * (n[0] * Ftl[1] - n[1] * Ftl[0])};
+                for (int b = 0; b < 3; ++b) { F[b] += (double)Fl[b]; T[b] += (double)tq[b]; }
+            }
+            if (delta <= 0.f) continue;
             const int slot = hist_slot(s, p, -1 - (2 * a + side), hpart, seen);
             if (slot < 0) continue;
             double* xi = s.hist_xi + ((long long)p * HIST_SLOTS + slot) * 3;

@@ -88,7 +88,7 @@ class FslbmParams(ctypes.Structure):
         ("capacity_particles", ctypes.c_int64),
         ("capacity_interface", ctypes.c_int64),
         ("excess_even", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("lubrication", ctypes.c_int32),
     ]
 
 
@@ -312,6 +312,7 @@ def params_from_workload(w, storage: int = STORE_FP32) -> FslbmParams:
     p.poisson = w.poisson
     p.collision_time = w.collision_time
     p.dem_substeps = w.dem_substeps
+    p.lubrication = w.lubrication
     p.capacity_particles = max(1024, 2 * (w.nspheres or 0))
     return p
 

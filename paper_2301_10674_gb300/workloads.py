@@ -44,6 +44,7 @@ class Workload:
     eps_conv: float = 1e-2
     eps_normal: float = 1e-2
     reconstruct_normal: int = 1
+    lubrication: int = 1                   # DEM lubrication corrections (Section 2.2)
     steps: int = 1000
     seed: int = 1
     spheres_nominal: int = 0

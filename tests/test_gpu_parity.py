@@ -406,6 +406,8 @@ def test_16bit_storage_keeps_a_slow_flow_under_a_deep_head(storage, tol):
 
 
 def _dry(L=40, **kw):
+    # the dry contact law alone (no lubrication correction)
+    kw.setdefault("lubrication", 0)
     w = W.Workload(name="dry", nx=L, ny=L, nz=L, periodic=(1, 1, 1), g=(0.0, 0.0, 0.0), liquid_height=0.0,
                    bed="none", **kw).generate()
     return w
@@ -433,7 +435,7 @@ def test_dem_restitution_on_gpu(e, r2):
 def test_dem_rolling_on_gpu():
     v0, r = 0.01, 3.0
     w = W.Workload(name="roll", nx=40, ny=16, nz=16, periodic=(1, 1, 0), g=(0.0, 0.0, -1e-3),
-                   liquid_height=0.0, bed="none", diameter=6.0).generate()
+                   liquid_height=0.0, bed="none", diameter=6.0, lubrication=0).generate()
     w.xyz = np.array([[10.0, 8.0, r]])
     w.radius = np.array([r])
     w.fixed = np.zeros(1, np.uint8)
@@ -444,6 +446,41 @@ def test_dem_rolling_on_gpu():
     Wy = sim.get(F.FIELD_P_OMEGA)[0, 1]
     assert abs(U[0] / v0 - 5 / 7) < 2e-3
     assert abs(Wy * r / v0 - 5 / 7) < 2e-3
+    sim.close()
+
+
+@pytest.mark.parametrize("motion", ["approach", "slide"])
+def test_dem_lubrication_matches_the_oracle(motion):
+    """Lubrication corrections (Section 2.2, reading R-23) near the floor of
+    a gas-filled box (omega 1.9): a sphere entering the lubrication range at
+    0.01 toward the wall, and a sphere sliding at 0.01 at a fixed gap of
+    0.2. The GPU's FP32 contact and lubrication terms summed in FP64 follow
+    the FP64 oracle's trajectory: position within 1e-6, velocities within
+    1e-3 of the initial speed, after every 20 steps."""
+    r, v0 = 3.0, 0.01
+    w = W.Workload(name="lub", nx=16, ny=16, nz=16, periodic=(1, 1, 0), tau=1 / 1.9, g=(0.0, 0.0, 0.0),
+                   liquid_height=0.0, bed="none", diameter=6.0).generate()
+    h0 = 2.0 / 3.0 if motion == "approach" else 0.2
+    w.xyz = np.array([[8.0, 8.0, r + h0]])
+    w.radius = np.array([r])
+    w.fixed = np.zeros(1, np.uint8)
+    u0 = np.array([[0.0, 0.0, -v0]]) if motion == "approach" else np.array([[v0, 0.0, 0.0]])
+    sim = _sim(w)
+    o = oracle_from_workload(w)
+    sim.set(F.FIELD_P_U, u0)
+    o.set(O.P_U, u0)
+    for _ in range(5):
+        sim.step(20)
+        o.step(20)
+        assert np.abs(sim.get(F.FIELD_P_X) - o.get(O.P_X)).max() < 1e-6
+        assert np.abs(sim.get(F.FIELD_P_U) - o.get(O.P_U)).max() < 1e-3 * v0
+        assert np.abs(sim.get(F.FIELD_P_OMEGA) - o.get(O.P_W)).max() * r < 1e-3 * v0
+    # the lubrication acted: the approach slowed, the sliding turned into rolling
+    U, Wo = sim.get(F.FIELD_P_U)[0], sim.get(F.FIELD_P_OMEGA)[0]
+    if motion == "approach":
+        assert -U[2] < 0.9 * v0
+    else:
+        assert U[0] - r * Wo[1] < 0.8 * v0
     sim.close()
 
 
