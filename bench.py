@@ -266,6 +266,10 @@ def timed_run(args, w, storage_name, theta, stream, local, barrier, world, horiz
     for _ in range(5):
         sim.bed_height()
     bed_ms = (time.perf_counter() - t0) / 5 * 1e3
+    t0 = time.perf_counter()
+    for _ in range(5):
+        sim.reduce()
+    red_ms = (time.perf_counter() - t0) / 5 * 1e3
     # the comparison horizon (untimed): the bed height h_b(x) is logged every
     # 10 steps on the way for its spectrum (Section 4.1)
     done = args.warmup + args.steps
@@ -294,7 +298,8 @@ def timed_run(args, w, storage_name, theta, stream, local, barrier, world, horiz
            "mh": hred, "horizon": done, "hb_end": series[-1], "spectrum": spectrum, "transport": transport,
            "column": column, "normal_stats": sim.normal_stats() if theta is not None else None,
            "bed": {"level": 0.3, "mean": round(float(bed_h.mean()), 4), "min": round(float(bed_h.min()), 4),
-                   "max": round(float(bed_h.max()), 4), "ms_per_call": round(bed_ms, 3)}}
+                   "max": round(float(bed_h.max()), 4), "ms_per_call": round(bed_ms, 3)},
+           "reduce_ms_per_call": round(red_ms, 3)}
     sim.close()
     del sim
     out["ms"] = _max_over_ranks(ms, "cuda")
@@ -430,7 +435,7 @@ def run_ours(args, world, rank, local):
             "training": train,
             "evaluated": int(head["normal_stats"][0]), "taken": int(head["normal_stats"][1])},
         "checks": {"invariant_violations": int(head["violations"]), "liquid_mass": float(head["m1"][0]),
-                   "interface_cells": int(head["m1"][5])},
+                   "interface_cells": int(head["m1"][5]), "reduce_ms_per_call": head["reduce_ms_per_call"]},
         "bed_height": head["bed"],
         "transport": {k: round(v, 8) for k, v in head["transport"].items()},
         "bed_spectrum": head["spectrum"],

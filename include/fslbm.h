@@ -118,12 +118,19 @@ typedef struct {
                                     (Section 2.2): normal 6 pi mu R^2 (1/h - 1/h_c),
                                     tangential 6 pi mu R (8/15) ln(h_c / h), R the
                                     effective radius, h clamped at 1e-2 */
+    int32_t galilean_correction; /* 1: Galilean-invariance correction of the second-
+                                    order relaxation (Geier et al. 2015): the normal-
+                                    stress differences and the trace lose their terms
+                                    of third order in u; the liquid cells then run in
+                                    the one-cell kernel. Default 0 (the paper's runs,
+                                    read as without it) */
+    int32_t reserved;            /* 0 */
 } fslbm_params;
 
 /* Fills *p with defaults: periodic x, walls in y and z, omega = 1/0.51,
  * g = 0, rho_gas = 1, eps_conv = eps_normal = 1e-2, reconstruct_normal = 1,
  * rho_p = 2.55, e = 0.88, mu = 0.5, nu_p = 0.22, T_c = 24, 10 sub-steps,
- * lubrication on. */
+ * lubrication on, Galilean correction off. */
 void fslbm_default_params(fslbm_params* p);
 
 /* Creates a simulation on the current CUDA device. `cuda_stream` is a

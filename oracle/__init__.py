@@ -64,6 +64,7 @@ class _Params(ctypes.Structure):
         ("sigma", ctypes.c_double),
         ("excess_even", ctypes.c_int),
         ("lubrication", ctypes.c_int),
+        ("galilean_correction", ctypes.c_int),
     ]
 
 
@@ -134,6 +135,7 @@ class OracleParams:
     sigma: float = 0.0
     excess_even: int = 0
     lubrication: int = 1
+    galilean_correction: int = 0
 
     def _c(self) -> _Params:
         p = _Params()
@@ -156,6 +158,7 @@ class OracleParams:
         p.sigma = self.sigma
         p.excess_even = self.excess_even
         p.lubrication = self.lubrication
+        p.galilean_correction = self.galilean_correction
         return p
 
 

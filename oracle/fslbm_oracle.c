@@ -76,6 +76,8 @@ typedef struct {
     int excess_even;          /* 1: excess mass split evenly over the receivers
                                  instead of by the normal weights (R-8 variant) */
     int lubrication;          /* 1: lubrication corrections below the resolved gap (R-23) */
+    int galilean_correction;  /* 1: Galilean-invariance correction of the second-order
+                                 rates (R-3 variant) */
 } orc_params;
 
 typedef struct {
@@ -188,8 +190,20 @@ static const double BINOM[3][3] = {{1, 0, 0}, {1, 1, 0}, {1, 2, 1}};
  * cumulants of order >= 3 relax with rate 1 to zero, so the post-collision
  * central moments of orders 3..6 are those of rho * N(0, S), S = k2* / rho.
  * Moments are formed by direct summation and inverted through the raw-moment
- * matrix, without any per-axis (chimera) factorisation. */
-void orc_collide(const double f[NQ], const double g[3], double omega, double out[NQ])
+ * matrix, without any per-axis (chimera) factorisation.
+ *
+ * With gal set, the Galilean-invariance correction of Geier et al. (2015) for
+ * the second-order relaxation (reading R-3, off by default): the velocity
+ * gradients follow from the non-equilibrium second-order moments,
+ *   d_x u_x = -omega/(2 rho) (2 k_xx - k_yy - k_zz) - 1/(2 rho) (k_xx + k_yy + k_zz - rho),
+ *   d_y u_y = d_x u_x + 3 omega/(2 rho) (k_xx - k_yy),
+ *   d_z u_z = d_x u_x + 3 omega/(2 rho) (k_xx - k_zz),
+ * (bulk rate 1), and the relaxed normal-stress differences and trace lose
+ * 3 rho (1 - omega/2) (u_x^2 d_x u_x - u_y^2 d_y u_y), the same with z, and
+ * 3 rho (1 - 1/2) (u_x^2 d_x u_x + u_y^2 d_y u_y + u_z^2 d_z u_z): the terms
+ * of third order in u that the D3Q27 lattice (c^3 = c) puts into the
+ * viscous stress. */
+void orc_collide_gal(const double f[NQ], const double g[3], double omega, int gal, double out[NQ])
 {
     build_tables();
     double rho = 0.0, j[3] = {0, 0, 0};
@@ -225,6 +239,16 @@ void orc_collide(const double f[NQ], const double g[3], double omega, double out
     double Dxy_s = (1.0 - omega) * Dxy;
     double Dxz_s = (1.0 - omega) * Dxz;
     double T_s = rho;
+    if (gal) {
+        double kxx = k[2][0][0], kyy = k[0][2][0], kzz = k[0][0][2];
+        double dxu = -omega / (2.0 * rho) * (2.0 * kxx - kyy - kzz) - 1.0 / (2.0 * rho) * (kxx + kyy + kzz - rho);
+        double dyv = dxu + 3.0 * omega / (2.0 * rho) * (kxx - kyy);
+        double dzw = dxu + 3.0 * omega / (2.0 * rho) * (kxx - kzz);
+        double ax = u[0] * u[0] * dxu, ay = u[1] * u[1] * dyv, az = u[2] * u[2] * dzw;
+        Dxy_s -= 3.0 * rho * (1.0 - 0.5 * omega) * (ax - ay);
+        Dxz_s -= 3.0 * rho * (1.0 - 0.5 * omega) * (ax - az);
+        T_s -= 3.0 * rho * 0.5 * (ax + ay + az);
+    }
     kp[2][0][0] = (Dxy_s + Dxz_s + T_s) / 3.0;
     kp[0][2][0] = (Dxz_s - 2.0 * Dxy_s + T_s) / 3.0;
     kp[0][0][2] = (Dxy_s - 2.0 * Dxz_s + T_s) / 3.0;
@@ -263,6 +287,11 @@ void orc_collide(const double f[NQ], const double g[3], double omega, double out
         for (int r = 0; r < NQ; ++r) s += MINV[q][r] * m[r];
         out[q] = s;
     }
+}
+
+void orc_collide(const double f[NQ], const double g[3], double omega, double out[NQ])
+{
+    orc_collide_gal(f, g, omega, 0, out);
 }
 
 /* ------------------------------------------------------------ geometry */
@@ -1120,7 +1149,7 @@ static void one_step(orc* o)
         }
         rnew[i] = rho;
         for (int a = 0; a < 3; ++a) unew[3 * i + a] = (j[a] + 0.5 * rho * P->g[a]) / rho;
-        orc_collide(fin, P->g, P->omega, &o->ft[i * NQ]);
+        orc_collide_gal(fin, P->g, P->omega, P->galilean_correction, &o->ft[i * NQ]);
         if (t == T_LIQ) mnew[i] = rho;
     }
     o->invariant_violations += viol;

@@ -163,6 +163,7 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     if (p->storage < 0 || p->storage > 2) return FSLBM_EINVAL;
     if (p->link_mass_correction < 0 || p->link_mass_correction > 1) return FSLBM_EINVAL;
     if (p->excess_even < 0 || p->excess_even > 1 || p->lubrication < 0 || p->lubrication > 1) return FSLBM_EINVAL;
+    if (p->galilean_correction < 0 || p->galilean_correction > 1 || p->reserved != 0) return FSLBM_EINVAL;
     if (p->dem_substeps < 1 || !(p->restitution > 0.0 && p->restitution <= 1.0)) return FSLBM_EINVAL;
     if (!(p->collision_time > 0.0) || !(p->rho_p > 0.0) || !(p->rho_gas > 0.0)) return FSLBM_EINVAL;
     if (!(p->poisson >= 0.0 && p->poisson < 1.0) || !(p->friction >= 0.0)) return FSLBM_EINVAL;
@@ -212,6 +213,7 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     d.eps_normal = (float)p->eps_normal;
     d.recon_normal = p->reconstruct_normal;
     d.excess_even = p->excess_even;
+    d.galilean = p->galilean_correction;
     d.link_corr = p->link_mass_correction;
     d.idx32 = 27LL * n < (1LL << 32) ? 1 : 0;
     d.wait_limit = WAIT_LIMIT_DEFAULT;
@@ -312,6 +314,7 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     d.g_list = dalloc<int>(s, pc, ok);
     s->stage = dalloc<double>(s, n > 8 ? n : 8, ok);
     s->red = dalloc<double>(s, 8, ok);
+    d.rpart = dalloc<double>(s, 8 * (size_t)reduce_blocks(d), ok);
     float* href = p->storage != FSLBM_STORE_FP32 ? dalloc<float>(s, p->nz, ok) : nullptr;
     if (ok && (cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess ||
                cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||

@@ -56,33 +56,18 @@ __device__ __forceinline__ void bwd_line2(float2& a, float2& b, float2& c, const
     b = K0 ? p_sub(p_sub(k0, lo), hi) : p_sub(p_mul(lo, p_set(-1.f)), hi);
 }
 
-// The last backward line (z) with the storage reference taken out of its
-// outputs: s_lo, s_mid, s_hi are subtracted from the outputs with
-// c_z = -1, 0, +1. Since the middle output is the zeroth moment less the two
-// others, the zeroth moment drops by the sum of the three.
-__device__ __forceinline__ void bwd_line2_ref(float2& a, float2& b, float2& c, const AxisCoef2& w, float R,
-                                              float s_lo, float s_mid, float s_hi) {
-    const float2 k0 = a, k1 = b, k2 = c;
-    const float2 K = p_add(p_set(R), k0);
-    const float2 half = p_set(0.5f);
-    const float2 lo = p_fma(w.A, K, p_fma(w.B, k1, p_fma(half, k2, p_set(-s_lo))));
-    const float2 hi = p_fma(w.C, K, p_fma(w.D, k1, p_fma(half, k2, p_set(-s_hi))));
-    a = lo;
-    c = hi;
-    b = p_sub(p_sub(p_add(k0, p_set(-(s_lo + s_mid + s_hi))), lo), hi);
-}
-
 // Reference of the 16-bit stored values (Section 2.1 hydrostatic start of the
 // liquid): a stored value is (f - w_q (1 + r)) 2^SCALE_LOG2, r the reference
 // deviation delta(z) of the z of the slot it sits in. rd[c_z + 1] is r of the
-// slots the pair's directions with c_z = -1, 0, +1 were read from; wt[c_z + 1]
-// that of the slots they are written to. The collision works on deviations
-// from w: the read reference enters the moments (its zeroth, z and second
-// diagonal moments; the D3Q27 weights factor into per-axis weights 1/6, 2/3,
-// 1/6, so nothing else), the write reference leaves through the last
-// backward line.
+// slots the pair's directions with c_z = -1, 0, +1 were read from. The
+// collision works on deviations from w: the read reference enters the
+// moments (its zeroth, z and second diagonal moments; the D3Q27 weights
+// factor into per-axis weights 1/6, 2/3, 1/6, so nothing else). The outputs
+// come out relative to w; the caller takes the reference of the slot each
+// one is written to off at its store (keeping the rest values of the
+// backward transform compile-time constants keeps the registers free).
 struct PairRef {
-    float rd[3], wt[3];
+    float rd[3];
 };
 
 // f: the stored values (deviations times 2^SCALE_LOG2) of two cells, in place;
@@ -93,6 +78,7 @@ __device__ __forceinline__ void collide_pair(float2 (&f)[27], float omega, float
                                              const PairRef& ref) {
     constexpr float scale = (float)(1u << SCALE_LOG2);
     constexpr bool scaled = SCALE_LOG2 != 0;
+
     // forward, x: per (b, c) line the sum, first and second raw moments
     float2 X0[9], X1[9], X2[9];
 #pragma unroll
@@ -231,26 +217,12 @@ __device__ __forceinline__ void collide_pair(float2 (&f)[27], float omega, float
         for (int a = 0; a < 3; ++a)
             bwd_line2<true, true, true>(f[a + 9 * c], f[a + 3 + 9 * c], f[a + 6 + 9 * c], wy,
                                         scale * w1(a) * mrest(c));
-    if (HREF) {
-        // output (a, b, c) loses scale w_q wt[c], w_q = w1(a) w1(b) w1(c)
-        const float wl = scale * (1.f / 6.f) * ref.wt[0], wm = scale * (2.f / 3.f) * ref.wt[1],
-                    wh = scale * (1.f / 6.f) * ref.wt[2];
 #pragma unroll
-        for (int b = 0; b < 3; ++b)
+    for (int b = 0; b < 3; ++b)
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const float W = w1(a) * w1(b);
-                bwd_line2_ref(f[a + 3 * b], f[a + 3 * b + 9], f[a + 3 * b + 18], wz, scale * W, W * wl, W * wm,
-                              W * wh);
-            }
-    } else {
-#pragma unroll
-        for (int b = 0; b < 3; ++b)
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-                bwd_line2<true, true, true>(f[a + 3 * b], f[a + 3 * b + 9], f[a + 3 * b + 18], wz,
-                                            scale * w1(a) * w1(b));
-    }
+        for (int a = 0; a < 3; ++a)
+            bwd_line2<true, true, true>(f[a + 3 * b], f[a + 3 * b + 9], f[a + 3 * b + 18], wz,
+                                        scale * w1(a) * w1(b));
 }
 
 // loads and stores of two x-adjacent stored values; the pair starts on an

@@ -47,6 +47,7 @@ enum : int { ERR_CAPACITY = 1, ERR_NAN = 2, ERR_INVARIANT = 4, ERR_HISTORY = 8, 
 constexpr int SP_TILE = 256;     // cells per x-tile of the staged even step
 constexpr int WAIT_LIMIT_DEFAULT = 1 << 22;   // polls of a bounded device wait
 
+constexpr int REDUCE_MAX_BY = 8192;   // row blocks of the lattice reduction (a few rows per thread)
 constexpr int HIST_SLOTS = 16;   // tangential-spring history slots per particle
 constexpr int NB_SLOTS = 32;     // DEM neighbour-list slots per particle
 
@@ -61,6 +62,7 @@ struct Dev {
     float sigma;       // surface tension: reconstruction density rho_gas + 6 sigma kappa
     int recon_normal;
     int excess_even;   // excess mass split evenly over the receivers
+    int galilean;      // Galilean-invariance correction of the second-order relaxation
     int storage;
     int link_corr;     // net moving-bounce-back injection into liquid cells taken from the pool
     int idx32;         // 27 n < 2^32: PDF element indices fit 32 bits
@@ -97,6 +99,7 @@ struct Dev {
     int* tl_info;                               // per transition: new owner / new type
     double* pool;
     double* pool_share;
+    double* rpart;     // partial sums of the lattice reduction, 8 per block
     int* err;
     unsigned long long* viol;
     // particles (FP64 state)
@@ -299,9 +302,18 @@ __device__ __forceinline__ float mrest(int i) { return i == 0 ? 1.f : (i == 1 ? 
 // storage scale): the forward sums are unscaled once, and the backward
 // transform, which is linear in the moments and the rest values, produces
 // scaled values again.
+//
+// With gal, the Galilean-invariance correction of Geier et al. (2015): the
+// diagonal velocity gradients follow from the non-equilibrium second-order
+// moments (shear rate omega, bulk rate 1), d_x u_x = -omega/(2 rho)
+// (2 k_xx - k_yy - k_zz) - (k_xx + k_yy + k_zz - (rho - 1))/(2 rho) in the
+// deviation variables, d_y u_y = d_x u_x + 3 omega/(2 rho) (k_xx - k_yy),
+// likewise z; the relaxed normal-stress differences lose 3 rho (1 - omega/2)
+// (u_x^2 d_x u_x - u_y^2 d_y u_y) (and z), the trace 3 rho / 2 (u_x^2 d_x u_x
+// + u_y^2 d_y u_y + u_z^2 d_z u_z).
 __device__ __forceinline__ void collide_scaled(float (&f)[27], float scale, float omega, float gx, float gy,
                                                float gz, float& rho_out, float& ux_out, float& uy_out,
-                                               float& uz_out) {
+                                               float& uz_out, bool gal = false) {
     // x: per (b, c) line the sum, first and second raw moments
     float X0[9], X1[9], X2[9];
 #pragma unroll
@@ -353,11 +365,22 @@ __device__ __forceinline__ void collide_scaled(float (&f)[27], float scale, floa
     const float kyz = pyz - uy * jz - uz * jy + rho * uy * uz;
     // m[a + 3b + 9c]: post-collision central-moment deviation of orders (a, b, c)
     const float om1 = 1.f - omega;
-    const float Dxy = om1 * (kxx - kyy);
-    const float Dxz = om1 * (kxx - kzz);
-    const float k200 = (Dxy + Dxz + drho) * (1.f / 3.f);
-    const float k020 = (Dxz - 2.f * Dxy + drho) * (1.f / 3.f);
-    const float k002 = (Dxy - 2.f * Dxz + drho) * (1.f / 3.f);
+    float Dxy = om1 * (kxx - kyy);
+    float Dxz = om1 * (kxx - kzz);
+    float trace = drho;   // relaxed trace less 1 (rate 1: rho - 1)
+    if (gal) {
+        const float dxu = -omega * 0.5f * inv * (2.f * kxx - kyy - kzz) - 0.5f * inv * (kxx + kyy + kzz - drho);
+        const float dyv = dxu + 1.5f * omega * inv * (kxx - kyy);
+        const float dzw = dxu + 1.5f * omega * inv * (kxx - kzz);
+        const float ax = ux * ux * dxu, ay = uy * uy * dyv, az = uz * uz * dzw;
+        const float c1 = 3.f * rho * (1.f - 0.5f * omega);
+        Dxy -= c1 * (ax - ay);
+        Dxz -= c1 * (ax - az);
+        trace -= 1.5f * rho * (ax + ay + az);
+    }
+    const float k200 = (Dxy + Dxz + trace) * (1.f / 3.f);
+    const float k020 = (Dxz - 2.f * Dxy + trace) * (1.f / 3.f);
+    const float k002 = (Dxy - 2.f * Dxz + trace) * (1.f / 3.f);
     const float k110 = om1 * kxy;
     const float k101 = om1 * kxz;
     const float k011 = om1 * kyz;
@@ -542,6 +565,7 @@ void launch_export_type(const Dev& s, uint8_t* out, cudaStream_t st);
 void launch_import_pdf(const Dev& s, int last_parity, const double* in, cudaStream_t st);
 void launch_import_mass(const Dev& s, const double* in, cudaStream_t st);
 void launch_reduce(const Dev& s, int last_parity, double* out, cudaStream_t st);
+int reduce_blocks(const Dev& s);
 
 inline int blocks_for(long long n, int threads) { return (int)((n + threads - 1) / threads); }
 

@@ -139,13 +139,15 @@ struct KSum {
 
 // Fluid-cell sums: liquid mass (liquid rho + interface m), momentum, and the
 // phi-weighted sums of the bulk velocity. Threads run along x, blocks over
-// rows (grid-stride over rows). Each cell's 27 post-collision PDFs come from
+// rows (a few rows per thread, so that many cells are in flight); every
+// block writes its partial sums to its own row of `part`, and k_reduce_sum
+// adds the rows in a fixed order. Each cell's 27 post-collision PDFs come from
 // the slots the last step wrote: (opp q, x) after an even step, (q, x + c_q)
 // after an odd one (constant offsets inside the lattice, the general lookup
 // at the faces). The liquid density enters as a count plus the sum of
 // deviations, so no rounding of 1 + d is accumulated.
 template <typename S, int LP>
-__global__ void __launch_bounds__(256) k_reduce_cells(Dev s, double* out) {
+__global__ void __launch_bounds__(256, 3) k_reduce_cells(Dev s, double* part) {
     __shared__ double sh[7][8];
     KSum acc[6];
     long long nfluid = 0;
@@ -227,8 +229,28 @@ __global__ void __launch_bounds__(256) k_reduce_cells(Dev s, double* out) {
     if (threadIdx.x < 7) {
         double w = 0;
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) w += sh[threadIdx.x][i];
-        atomicAdd(&out[threadIdx.x == 6 ? 7 : threadIdx.x], w);
+        part[8 * ((long long)blockIdx.y * gridDim.x + blockIdx.x) + threadIdx.x] = w;
     }
+}
+
+// out[0..5], out[7] from the blocks' partial rows (fixed order: thread t
+// takes rows t, t + 1024, ..., then a tree over the threads)
+__global__ void __launch_bounds__(1024) k_reduce_sum(const double* part, int blocks, double* out) {
+    __shared__ double sh[7][1024];
+    double v[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < blocks; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < 7; ++k) v[k] += part[8 * (long long)b + k];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) sh[k][threadIdx.x] = v[k];
+    __syncthreads();
+    for (int off = 512; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off)
+#pragma unroll
+            for (int k = 0; k < 7; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x < 7) out[threadIdx.x == 6 ? 7 : threadIdx.x] = sh[threadIdx.x][0];
 }
 
 // bedload of Eq. (1): sum u_x,p V_p, one block
@@ -266,24 +288,29 @@ __global__ void k_reduce_final(Dev s, double* out) {
     if (!isfinite(*s.pool)) set_error(s, ERR_NAN);
 }
 
+int reduce_blocks(const Dev& s) {
+    const int bx = (s.nx + 255) / 256;
+    const int rows = s.ny * s.nz;
+    return bx * (rows < REDUCE_MAX_BY ? rows : REDUCE_MAX_BY);
+}
+
 void launch_reduce(const Dev& s, int last_parity, double* out, cudaStream_t st) {
-    cudaMemsetAsync(out, 0, 8 * sizeof(double), st);
     const unsigned bx = (unsigned)((s.nx + 255) / 256);
     const int rows = s.ny * s.nz;
-    // about 32 blocks of 256 threads per SM, each thread a column of rows
-    const int want = (int)(152 * 32 / bx) > 0 ? (int)(152 * 32 / bx) : 1;
-    const unsigned by = (unsigned)(rows < want ? rows : want);
+    const unsigned by = (unsigned)(rows < REDUCE_MAX_BY ? rows : REDUCE_MAX_BY);
     const dim3 grid(bx, by);
+    double* part = s.rpart;
     if (s.storage == FSLBM_STORE_FP32) {
-        if (last_parity == 0) k_reduce_cells<float, 0><<<grid, 256, 0, st>>>(s, out);
-        else k_reduce_cells<float, 1><<<grid, 256, 0, st>>>(s, out);
+        if (last_parity == 0) k_reduce_cells<float, 0><<<grid, 256, 0, st>>>(s, part);
+        else k_reduce_cells<float, 1><<<grid, 256, 0, st>>>(s, part);
     } else if (s.storage == FSLBM_STORE_FP16) {
-        if (last_parity == 0) k_reduce_cells<__half, 0><<<grid, 256, 0, st>>>(s, out);
-        else k_reduce_cells<__half, 1><<<grid, 256, 0, st>>>(s, out);
+        if (last_parity == 0) k_reduce_cells<__half, 0><<<grid, 256, 0, st>>>(s, part);
+        else k_reduce_cells<__half, 1><<<grid, 256, 0, st>>>(s, part);
     } else {
-        if (last_parity == 0) k_reduce_cells<__nv_bfloat16, 0><<<grid, 256, 0, st>>>(s, out);
-        else k_reduce_cells<__nv_bfloat16, 1><<<grid, 256, 0, st>>>(s, out);
+        if (last_parity == 0) k_reduce_cells<__nv_bfloat16, 0><<<grid, 256, 0, st>>>(s, part);
+        else k_reduce_cells<__nv_bfloat16, 1><<<grid, 256, 0, st>>>(s, part);
     }
+    k_reduce_sum<<<1, 1024, 0, st>>>(part, (int)(bx * by), out);
     k_reduce_particles<<<1, 1024, 0, st>>>(s, out);
     k_reduce_final<<<1, 1, 0, st>>>(s, out);
 }

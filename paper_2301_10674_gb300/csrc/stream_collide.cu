@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(256, liquid_min_blocks<S>()) k_liquid(Dev s) {
             }
         }
         float rho, ux, uy, uz;
-        collide_scaled(v, Store<S>::scale, s.omega, s.gx, s.gy, s.gz, rho, ux, uy, uz);
+        collide_scaled(v, Store<S>::scale, s.omega, s.gx, s.gy, s.gz, rho, ux, uy, uz, s.galilean != 0);
         if (Store<S>::HREF) {
             const NbrOffsets o = nbr_offsets(s, x, y, z);
 #pragma unroll
@@ -204,7 +204,8 @@ __device__ __forceinline__ void pair_update(const Dev& s, S* f, int x, int row, 
     // by value and collide with zero references
     PairRef ref;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) ref.rd[k] = ref.wt[k] = 0.f;
+    for (int k = 0; k < 3; ++k) ref.rd[k] = 0.f;
+    float wt[3] = {0.f, 0.f, 0.f};   // reference of the slots written along c_z = -1, 0, +1
     if (interior) {
 #pragma unroll
         for (int q = 0; q < 27; ++q) {
@@ -217,11 +218,11 @@ __device__ __forceinline__ void pair_update(const Dev& s, S* f, int x, int row, 
         if (Store<S>::HREF) {
             const float h0 = s.href[z];
             if (PAR == 0) {
-                ref.rd[0] = ref.rd[1] = ref.rd[2] = ref.wt[0] = ref.wt[1] = ref.wt[2] = h0;
+                ref.rd[0] = ref.rd[1] = ref.rd[2] = wt[0] = wt[1] = wt[2] = h0;
             } else {
                 const float hm = s.href[z - 1], hp = s.href[z + 1];
                 ref.rd[0] = hp; ref.rd[1] = h0; ref.rd[2] = hm;
-                ref.wt[0] = hm; ref.wt[1] = h0; ref.wt[2] = hp;
+                wt[0] = hm; wt[1] = h0; wt[2] = hp;
             }
         }
     } else {
@@ -245,6 +246,11 @@ __device__ __forceinline__ void pair_update(const Dev& s, S* f, int x, int row, 
         }
     }
     collide_pair<Pair<S>::SCALE_LOG2, Store<S>::HREF>(v, s.omega, s.gx, s.gy, s.gz, ref);
+    if (Store<S>::HREF && interior) {
+        // each output loses the reference of the slot it is written to
+#pragma unroll
+        for (int q = 0; q < 27; ++q) v[q] = p_fma(p_set(-SC * wq(q)), p_set(wt[1 + cz(q)]), v[q]);
+    }
     if (interior && liq == 3u) {
 #pragma unroll
         for (int q = 0; q < 27; ++q) {
@@ -554,8 +560,11 @@ __global__ void __launch_bounds__(SP_TILE / 2, 6) k_liquid_staged_pair(Dev s) {
             PairRef ref;
             const float h0 = s.href[(unsigned)cell / ((unsigned)s.nx * (unsigned)s.ny)];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) ref.rd[k] = ref.wt[k] = h0;
+            for (int k = 0; k < 3; ++k) ref.rd[k] = h0;
             collide_pair<Pair<S>::SCALE_LOG2, true>(v, s.omega, s.gx, s.gy, s.gz, ref);
+            // outputs relative to w (1 + delta(z)) for the cells' own slots
+#pragma unroll
+            for (int q = 0; q < 27; ++q) v[q] = p_fma(p_set(-Store<S>::scale * wq(q)), p_set(h0), v[q]);
             if (liq == 3u) {
 #pragma unroll
                 for (int q = 0; q < 27; ++q) Pair<S>::st2(f + ((unsigned)opp(q) * un + (unsigned)cell), v[q]);
@@ -693,24 +702,12 @@ __global__ void __launch_bounds__(256, 3) k_solid_links(Dev s) {
                 key = p;
             }
             // phase 2: the post-collision PDFs the fluid neighbours send here
-            // (16-bit storage: references of the solid cell's z and of the
-            // neighbour's; an even step reads at the solid cell and writes at
-            // the neighbour, an odd step the other way round)
-            float hz = 0.f, hn[3] = {0.f, 0.f, 0.f};
-            if (Store<S>::HREF) {
-                hz = s.href[z];
-                hn[0] = (o.wall & 16u) ? hz : s.href[wrap_z(s, z - 1)];
-                hn[1] = hz;
-                hn[2] = (o.wall & 32u) ? hz : s.href[wrap_z(s, z + 1)];
-            }
             float fo[27];
 #pragma unroll
             for (int q = 0; q < 27; ++q) {
                 const int xn = cell + o.ox[1 + cx(q)] + o.oy[1 + cy(q)] + o.oz[1 + cz(q)];
                 const long long a = PAR == 0 ? (long long)opp(q) * n + cell : (long long)q * n + xn;
-                float v = ((fluidm >> q) & 1u) ? Store<S>::ld(f + a) : 0.f;
-                if (Store<S>::HREF) v += wq(q) * (PAR == 0 ? hz : hn[1 + cz(q)]);
-                fo[q] = v;
+                fo[q] = ((fluidm >> q) & 1u) ? Store<S>::ld(f + a) : 0.f;
             }
             // phase 3: bounce-back values and momentum exchange
             if (fluidm) {
@@ -719,8 +716,19 @@ __global__ void __launch_bounds__(256, 3) k_solid_links(Dev s) {
                 const float ddy = (float)wrap_int(y - P.xi.y, s.ny, s.per_y) + 0.5f - P.xf.y;
                 const float ddz = (float)wrap_int(z - P.xi.z, s.nz, s.per_z) + 0.5f - P.xf.z;
 #pragma unroll
+                // 16-bit storage: references of the solid cell's z and of the
+                // neighbour's (an even step reads at the solid cell and writes
+                // at the neighbour, an odd step the other way round)
+                const float hz = Store<S>::HREF ? s.href[z] : 0.f;
+                const int zm = wrap_z(s, z - 1), zp = wrap_z(s, z + 1);
+#pragma unroll
                 for (int q = 0; q < 27; ++q) {
                     if (!((fluidm >> q) & 1u)) continue;
+                    float hn = 0.f;
+                    if (Store<S>::HREF) {
+                        hn = cz(q) == 0 ? hz : s.href[cz(q) < 0 ? zm : zp];
+                        fo[q] += wq(q) * (PAR == 0 ? hz : hn);
+                    }
                     const int xn = cell + o.ox[1 + cx(q)] + o.oy[1 + cy(q)] + o.oz[1 + cz(q)];
                     const float dx = ddx + 0.5f * cx(q), dy = ddy + 0.5f * cy(q), dz = ddz + 0.5f * cz(q);
                     const float ubx = P.u.x + (P.w.y * dz - P.w.z * dy);
@@ -730,7 +738,7 @@ __global__ void __launch_bounds__(256, 3) k_solid_links(Dev s) {
                     const float val = fo[q] + 6.f * wq(q) * cu;
                     if ((liqm >> q) & 1u) injected += 6.f * wq(q) * cu;
                     const long long dst = PAR == 0 ? (long long)q * n + xn : (long long)opp(q) * n + cell;
-                    Store<S>::st(f + dst, Store<S>::HREF ? val - wq(q) * (PAR == 0 ? hn[1 + cz(q)] : hz) : val);
+                    Store<S>::st(f + dst, Store<S>::HREF ? val - wq(q) * (PAR == 0 ? hn : hz) : val);
                     const float sum = fo[q] + val, dif = fo[q] - val;
                     const float Fx = -cx(q) * sum - ubx * dif;
                     const float Fy = -cy(q) * sum - uby * dif;
@@ -795,8 +803,14 @@ __global__ void __launch_bounds__(128) k_interface(Dev s) {
             const float mx = s.mass[cell];
             const float4 nn = s.nrm[cell];
             // 16-bit storage: references of the slots (the cell's own z, the
-            // pull source's z - c_z in an odd step, the target's z + c_z)
+            // pull source's z - c_z in an odd step, the target's z + c_z); h3[k]
+            // that of z + k - 1 (the cell's own beyond a wall face, never used)
             const float hz = Store<S>::HREF ? s.href[z] : 0.f;
+            float h3[3] = {hz, hz, hz};
+            if (Store<S>::HREF && PAR == 1) {
+                if (zs[0] >= 0) h3[0] = s.href[zs[0]];
+                if (zs[2] >= 0) h3[2] = s.href[zs[2]];
+            }
             float fo[27];
 #pragma unroll
             for (int q = 0; q < 27; ++q) {
@@ -811,7 +825,7 @@ __global__ void __launch_bounds__(128) k_interface(Dev s) {
                 const long long src = pull ? sx + (long long)s.nx * (sy + (long long)s.ny * sz) : cell;
                 const long long a = PAR == 0 ? (long long)q * n + cell : (long long)opp(q) * n + src;
                 v[q] = pull ? Store<S>::ld(f + a) : 0.f;
-                if (Store<S>::HREF && pull) v[q] += wq(q) * (PAR == 0 ? hz : s.href[sz]);
+                if (Store<S>::HREF && pull) v[q] += wq(q) * (PAR == 0 ? hz : h3[1 - cz(q)]);
             }
             // own collision velocity from the post-collision PDFs
             float d = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
@@ -859,7 +873,7 @@ __global__ void __launch_bounds__(128) k_interface(Dev s) {
                 }
             }
             float rho, ux, uy, uz;
-            collide(v, s.omega, s.gx, s.gy, s.gz, rho, ux, uy, uz);
+            collide_scaled(v, 1.f, s.omega, s.gx, s.gy, s.gz, rho, ux, uy, uz, s.galilean != 0);
             if (PAR == 0) {
 #pragma unroll
                 for (int q = 0; q < 27; ++q)
@@ -871,7 +885,7 @@ __global__ void __launch_bounds__(128) k_interface(Dev s) {
                     const bool out = tx < 0 || ty < 0 || tz < 0;
                     const long long a = out ? (long long)opp(q) * n + cell
                                             : (long long)q * n + tx + (long long)s.nx * (ty + (long long)s.ny * tz);
-                    Store<S>::st(f + a, Store<S>::HREF ? v[q] - wq(q) * (out ? hz : s.href[tz]) : v[q]);
+                    Store<S>::st(f + a, Store<S>::HREF ? v[q] - wq(q) * (out ? hz : h3[1 + cz(q)]) : v[q]);
                 }
             }
 #pragma unroll
@@ -885,7 +899,9 @@ __global__ void __launch_bounds__(128) k_interface(Dev s) {
     }
 }
 
-static bool use_pairs(const Dev& s) { return s.idx32 && (s.nx % 2) == 0; }
+// the pair collision carries no Galilean correction: with it every liquid
+// cell runs in the one-cell kernel
+static bool use_pairs(const Dev& s) { return s.idx32 && (s.nx % 2) == 0 && !s.galilean; }
 // odd steps at 16-bit storage: interior pairs and the boundary pairs in two
 // launches (at FP32 the odd step is bound by HBM, and one launch is faster)
 static bool use_split(const Dev& s) {
@@ -893,7 +909,7 @@ static bool use_split(const Dev& s) {
 }
 // the staged even step: 16-bit storage, nx a multiple of the tile
 static bool use_staged_pairs(const Dev& s) {
-    return s.idx32 && s.storage != FSLBM_STORE_FP32 && (s.nx % SP_TILE) == 0;
+    return s.idx32 && s.storage != FSLBM_STORE_FP32 && (s.nx % SP_TILE) == 0 && !s.galilean;
 }
 
 // CTAs of the staged even step: as many as fit on the SMs at once, found

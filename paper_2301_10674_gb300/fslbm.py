@@ -89,6 +89,8 @@ class FslbmParams(ctypes.Structure):
         ("capacity_interface", ctypes.c_int64),
         ("excess_even", ctypes.c_int32),
         ("lubrication", ctypes.c_int32),
+        ("galilean_correction", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -313,6 +315,7 @@ def params_from_workload(w, storage: int = STORE_FP32) -> FslbmParams:
     p.collision_time = w.collision_time
     p.dem_substeps = w.dem_substeps
     p.lubrication = w.lubrication
+    p.galilean_correction = w.galilean_correction
     p.capacity_particles = max(1024, 2 * (w.nspheres or 0))
     return p
 

@@ -45,6 +45,7 @@ class Workload:
     eps_normal: float = 1e-2
     reconstruct_normal: int = 1
     lubrication: int = 1                   # DEM lubrication corrections (Section 2.2)
+    galilean_correction: int = 0           # Galilean correction of the collision (off: the paper's runs)
     steps: int = 1000
     seed: int = 1
     spheres_nominal: int = 0

@@ -11,7 +11,7 @@ def oracle_from_workload(w, spheres=True, **overrides):
         rho_gas=w.rho_gas, liquid_height=w.liquid_height, eps_conv=w.eps_conv, eps_normal=w.eps_normal,
         reconstruct_normal=w.reconstruct_normal, rho_p=w.rho_p, restitution=w.restitution,
         friction=w.friction, poisson=w.poisson, collision_time=w.collision_time,
-        dem_substeps=w.dem_substeps, lubrication=w.lubrication)
+        dem_substeps=w.dem_substeps, lubrication=w.lubrication, galilean_correction=w.galilean_correction)
     kw.update(overrides)
     o = O.Oracle(O.OracleParams(**kw))
     if spheres and w.nspheres:
