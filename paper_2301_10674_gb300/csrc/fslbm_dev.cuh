@@ -47,7 +47,7 @@ enum : int { ERR_CAPACITY = 1, ERR_NAN = 2, ERR_INVARIANT = 4, ERR_HISTORY = 8, 
 constexpr int SP_TILE = 256;     // cells per x-tile of the staged even step
 constexpr int WAIT_LIMIT_DEFAULT = 1 << 22;   // polls of a bounded device wait
 
-constexpr int REDUCE_MAX_BY = 8192;   // row blocks of the lattice reduction (a few rows per thread)
+constexpr int REDUCE_MAX_BY = 2048;   // row blocks of the lattice reduction (several rows per thread)
 constexpr int HIST_SLOTS = 16;   // tangential-spring history slots per particle
 constexpr int NB_SLOTS = 32;     // DEM neighbour-list slots per particle
 
@@ -186,6 +186,11 @@ template <> struct Store<__nv_bfloat16> {
 // w_q delta(z) of slot i = q n + cell (16-bit storage): the part of f - w
 // that the stored value leaves to the reference
 __device__ __forceinline__ float slot_ref(const Dev& s, long long i) {
+    if (s.idx32) {   // 32-bit division where the indices fit
+        const unsigned u = (unsigned)i, un = (unsigned)s.n;
+        const unsigned q = u / un;
+        return wq((int)q) * s.href[(u - q * un) / ((unsigned)s.nx * (unsigned)s.ny)];
+    }
     const int q = (int)(i / s.n);
     const long long c = i - (long long)q * s.n;
     return wq(q) * s.href[(int)(c / ((long long)s.nx * s.ny))];

@@ -163,30 +163,41 @@ __global__ void __launch_bounds__(256, 3) k_reduce_cells(Dev s, double* part) {
             if (!fluid(fl)) continue;
             const int t = fl & TYPE_MASK;
             const int y = row % s.ny, z = row / s.ny;
-            // f - w of the cell's post-collision PDFs (16-bit storage: the
-            // reference of each slot's z added back)
+            // f - w of the cell's post-collision PDFs. With 16-bit storage
+            // each slot's reference w_q delta(z_slot) is added back: in closed
+            // form where every slot of direction c_z sits at the same z (after
+            // an even step all at z; after an odd step, inside the lattice, at
+            // z + c_z: per-axis weights 1/6, 2/3, 1/6), value by value at the
+            // faces
             float fv[27];
+            float rd = 0.f, rz = 0.f;   // reference part of sum f and sum c_z f
             if (LP == 0) {
 #pragma unroll
-                for (int q = 0; q < 27; ++q) {
-                    fv[q] = Store<S>::ld(f + (long long)opp(q) * n + cell);
-                    if (Store<S>::HREF) fv[q] += wq(q) * s.href[z];
-                }
+                for (int q = 0; q < 27; ++q) fv[q] = Store<S>::ld(f + (long long)opp(q) * n + cell);
+                if (Store<S>::HREF) rd = s.href[z];
             } else if (x > 0 && x < s.nx - 1 && y > 0 && y < s.ny - 1 && z > 0 && z < s.nz - 1) {
 #pragma unroll
-                for (int q = 0; q < 27; ++q) {
+                for (int q = 0; q < 27; ++q)
                     fv[q] = Store<S>::ld(f + (long long)q * n + (cell + cx(q) + s.nx * cy(q) + sxy * cz(q)));
-                    if (Store<S>::HREF) fv[q] += wq(q) * s.href[z + cz(q)];
+                if (Store<S>::HREF) {
+                    const float hm = s.href[z - 1], h0 = s.href[z], hp = s.href[z + 1];
+                    rd = (hm + hp) * (1.f / 6.f) + h0 * (2.f / 3.f);
+                    rz = (hp - hm) * (1.f / 6.f);
                 }
             } else {
 #pragma unroll
                 for (int q = 0; q < 27; ++q) {
-                    const long long i = fstar_slot(s, q, x, y, z, cell, 1);
+                    // slot (q, x + c_q), or (opp q, x) beyond a wall face
+                    const int tx = shift(x, cx(q), s.nx, s.per_x), ty = shift(y, cy(q), s.ny, s.per_y),
+                              tz = shift(z, cz(q), s.nz, s.per_z);
+                    const bool wall = tx < 0 || ty < 0 || tz < 0;
+                    const long long i = wall ? (long long)opp(q) * n + cell
+                                             : (long long)q * n + tx + (long long)s.nx * (ty + (long long)s.ny * tz);
                     fv[q] = Store<S>::ld(f + i);
-                    if (Store<S>::HREF) fv[q] += slot_ref(s, i);
+                    if (Store<S>::HREF) fv[q] += wq(q) * s.href[wall ? z : tz];
                 }
             }
-            float d = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+            float d = rd, jx = 0.f, jy = 0.f, jz = rz;
 #pragma unroll
             for (int q = 0; q < 27; ++q) {
                 d += fv[q];

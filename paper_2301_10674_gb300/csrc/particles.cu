@@ -657,14 +657,16 @@ __device__ __forceinline__ void bbox_axis(double a, double b, double r, int L, i
 }
 
 // Cells of the shell (or of the old and new boxes) of every active particle
-// join the dirty list, each once. A block per particle, a thread per (y, z)
+// join the dirty list, each once. A warp per particle, a lane per (y, z)
 // row of its box: the row meets the shell | |x_c - X| - r | <= band in at
 // most two x-intervals, found from the row's distance to the centre; the
 // radii are widened by 1e-3 cells so that rounding can only add cells (a
 // cell re-mapped without need keeps its owner).
 __global__ void k_dirty(Dev s) {
-    if ((int)blockIdx.x >= *s.act_count) return;
-    const int p = s.act[blockIdx.x];
+    const int wid = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (wid >= *s.act_count) return;   // whole warps leave together
+    const int p = s.act[wid];
     const double r = s.R[p];
     const float w = s.margin[p];
     const bool whole = w < 0.f;
@@ -680,8 +682,8 @@ __global__ void k_dirty(Dev s) {
     const int rows = ey * ez;
     // relative x index of a cell = a + xoff, with a its x offset from the centre
     const float xoff = (float)(xi.x - lo[0]) - 0.5f + xf.x;
-    for (int r0 = 0; r0 < rows; r0 += blockDim.x) {
-        const int rr = r0 + threadIdx.x;
+    for (int r0 = 0; r0 < rows; r0 += 32) {
+        const int rr = r0 + lane;
         int a0 = 0, a1 = -1, b0 = 0, b1 = -1;    // relative x ranges of the row
         int ub = 0, uc = 0;
         if (rr < rows) {
@@ -929,7 +931,7 @@ int launch_remap(const Dev& s, int last_parity, cudaStream_t st) {
     cudaMemsetAsync(s.act_count, 0, sizeof(int), st);
     cudaMemsetAsync(s.dl_count, 0, sizeof(int), st);
     k_active<<<blocks_for(s.np, 128), 128, 0, st>>>(s);
-    k_dirty<<<s.np, 128, 0, st>>>(s);
+    k_dirty<<<blocks_for(32LL * s.np, 128), 128, 0, st>>>(s);
     k_remap_list<<<152 * 8, 128, 0, st>>>(s);
     k_map_position<<<blocks_for(s.np, 256), 256, 0, st>>>(s);
     k_transitions<<<152 * 4, 128, 0, st>>>(s, last_parity);
