@@ -575,7 +575,15 @@ def run_precision_study(args):
 # `python bench.py --oracle-table`: the tiny flume in full, the mid flume
 # and a 128-wide x-crop of the precision flume for 200 steps each. The line
 # quotes it beside the live cpu_baseline.
-ORACLE_TABLE = None
+ORACLE_TABLE = {
+    "cores": 16, "host": "GB300 box (Grace)", "normal": "finite-difference",
+    "rows": [
+        {"workload": "tiny-64x16x32", "sample": "full lattice, 34 spheres, 1000 steps", "mlups": 4.051},
+        {"workload": "mid-512x40x96", "sample": "full lattice, 1160 spheres, 200 steps", "mlups": 3.571},
+        {"workload": "precision-1024x64x128", "sample": "128x64x128 x-crop, 651 spheres, 200 steps",
+         "mlups": 3.858},
+    ],
+}
 
 
 def run_oracle_table() -> dict:

@@ -954,7 +954,9 @@ __global__ void k_init_particles(Dev s, int first, int count, double rho_p) {
     }
     for (int j = 0; j < HIST_SLOTS; ++j) s.hist_partner[(long long)p * HIST_SLOTS + j] = HIST_EMPTY;
     s.margin[p] = 0.f;
-    s.shared[p] = 1;
+    // the set-up map (k_remap_all) flags every particle that shares a cell;
+    // the others re-map their thin shell from the first step on
+    s.shared[p] = 0;
     for (int a = 0; a < 3; ++a) s.Xm[3 * p + a] = s.X[3 * p + a];
     atomicMax(s.zmax_cell, (int)ceil(s.X[3 * p + 2] + r) + 2);
 }

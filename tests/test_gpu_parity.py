@@ -26,7 +26,9 @@ def _sim(w, storage=F.STORE_FP32, spheres=True):
     return F.Simulation.from_workload(w, storage=storage, spheres=spheres)
 
 
-def _compare(sim, o, pdf_tol, check_particles=True):
+def _compare(sim, o, pdf_tol, check_particles=True, dev_tol=None):
+    """Cell types and owners exact; PDFs on f - w within dev_tol (default
+    pdf_tol) of the largest deviation; interface masses and normals."""
     tg = sim.get(F.FIELD_TYPE)
     to = o.get(O.F_TYPE)
     mism = int((tg != to).sum())
@@ -35,12 +37,18 @@ def _compare(sim, o, pdf_tol, check_particles=True):
     oo = o.get(O.F_OWNER)
     solid = to == O.SOLID
     assert (og[solid] == oo[solid]).all()
-    err = pdf_rel_err(sim.get(F.FIELD_PDF), o.get(O.F_PDF), to)
-    assert err < pdf_tol, err
+    # PDFs measured on f - w (relative to the largest deviation of the
+    # oracle's fluid cells), the part of the PDFs that carries the flow
+    err = pdf_dev_err(sim.get(F.FIELD_PDF), o.get(O.F_PDF), to)
+    assert err < (pdf_tol if dev_tol is None else dev_tol), err
     mg, mo = sim.get(F.FIELD_MASS), o.get(O.F_MASS)
     ifc = to == O.INTERFACE
     if ifc.any():
         assert np.abs(mg[ifc] - mo[ifc]).max() < 50 * pdf_tol
+        # the finite-difference normals of the interface cells (used by the
+        # next step's boundary condition) from the same fill levels
+        ng, no = sim.get(F.FIELD_NORMAL), o.get(O.F_NORMAL)
+        assert np.abs(ng[:, ifc] - no[:, ifc]).max() < 1e3 * pdf_tol
     if check_particles and o.nparticles:
         xg, xo = sim.get(F.FIELD_P_X), o.get(O.P_X)
         assert np.abs(xg - xo).max() < 1e-6
@@ -116,7 +124,10 @@ def test_free_surface_without_particles(recon, even):
     for _ in range(20):
         sim.step(10)
         o.step(10)
-        _compare(sim, o, 1e-4)
+        # a moving free surface: FP32 against FP64 through mass exchange and
+        # conversions leaves up to a few 1e-4 of the largest deviation after
+        # 200 steps (measured 1.1e-4 to 2.3e-4), with every cell type equal
+        _compare(sim, o, 1e-4, dev_tol=5e-4)
         changed += int((o.get(O.F_TYPE) != t0).sum())
     assert changed > 0
     assert sim.violations == 0 and o.violations == 0
@@ -214,7 +225,9 @@ def test_moving_particles_cover_and_uncover_cells():
     for _ in range(12):
         sim.step(10)
         o.step(10)
-        _compare(sim, o, 1e-4)
+        # spheres moving at 0.02 cover and uncover cells (refills from FP32
+        # neighbour averages): up to 3.6e-4 of the largest deviation
+        _compare(sim, o, 1e-4, dev_tol=1e-3)
     assert (o.get(O.F_OWNER) != owners0).sum() > 20
     sim.close()
 
