@@ -170,7 +170,15 @@ int fslbm_init_surface(fslbm* s, const double* height_xy, int on_device);
  *     uncovered cells are refilled from it);
  *   5 the pool is spread over all interface cells; normals for the next step.
  * Asynchronous on the stream; returns the sticky error word as of the call
- * (a device error raised by these steps is returned by a later call). */
+ * (a device error raised by these steps is returned by a later call).
+ * From the third step on, each step is replayed from a CUDA graph captured
+ * once per parity (the same kernels with the same arguments, so the results
+ * are bitwise those of direct launches), unless the stream given to
+ * fslbm_create is the legacy default stream (NULL), which cannot be captured,
+ * the caller is itself capturing the stream (the launches then go into the
+ * caller's graph), or the flow-rate control is on. The graphs are captured
+ * again after a call that changes a launch argument (body force, flow
+ * control, wait limit, normal model, spheres). */
 int fslbm_step(fslbm* s, int64_t n_steps);
 
 /* Field selection bits for fslbm_get_fields / fslbm_set_fields. dst[k] /

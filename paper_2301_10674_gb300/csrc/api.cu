@@ -53,6 +53,16 @@ struct fslbm {
     // conversion), and the events that fork it from and join it to st
     cudaStream_t side;
     cudaEvent_t ev_fork, ev_join;
+    // CUDA graphs of one step per parity (replayed once the step's launch
+    // sequence and parameters are settled; captured again when a parameter
+    // the kernels receive changes)
+    cudaGraph_t graph[2];
+    cudaGraphExec_t gexec[2];
+    cudaGraphNode_t gev[2][2];   // the sweep's two event-record nodes per graph
+    cudaEvent_t ev_cap[2];       // the events they record when no timing is on
+    int graph_launches[2];
+    bool graph_dirty;
+    bool graphs_on;
 };
 
 namespace {
@@ -192,6 +202,16 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     s->mlp_stats = nullptr;
     s->side = nullptr;
     s->ev_fork = s->ev_join = nullptr;
+    for (int k = 0; k < 2; ++k) {
+        s->graph[k] = nullptr;
+        s->gexec[k] = nullptr;
+        s->gev[k][0] = s->gev[k][1] = nullptr;
+        s->ev_cap[k] = nullptr;
+        s->graph_launches[k] = 0;
+    }
+    s->graph_dirty = false;
+    // a stream can be captured unless it is the legacy default stream
+    s->graphs_on = cuda_stream != nullptr && static_cast<cudaStream_t>(cuda_stream) != cudaStreamLegacy;
     Dev& d = s->d;
     std::memset(&d, 0, sizeof(d));
     d.nx = p->nx; d.ny = p->ny; d.nz = p->nz;
@@ -425,6 +445,7 @@ int fslbm_add_spheres(fslbm* s, int64_t n, const double* xyz, const double* radi
         launch_normals(d, d.nrm, st);
     }
     s->spheres_added = true;
+    s->graph_dirty = true;
     launch_check(s);
     return sync_check(s);
 }
@@ -442,49 +463,164 @@ int fslbm_init_surface(fslbm* s, const double* height_xy, int on_device) {
     return sync_check(s);
 }
 
+// Enqueues the launches of one step of the given parity on s->st (and the
+// DEM half on the side stream); returns the number of kernels. Under graph
+// capture the sweep's two timing events are recorded as external
+// event-record nodes of the placeholder events, retargeted at each replay.
+static int enqueue_step(fslbm* s, int parity, bool capturing) {
+    Dev& d = s->d;
+    cudaStream_t st = s->st;
+    if (d.np > 0) {
+        cudaMemsetAsync(d.Fh, 0, sizeof(double) * 3 * d.np, st);
+        cudaMemsetAsync(d.Th, 0, sizeof(double) * 3 * d.np, st);
+    }
+    int nl = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (capturing) {
+        e0 = s->ev_cap[0];
+        e1 = s->ev_cap[1];
+        cudaEventRecordWithFlags(e0, st, cudaEventRecordExternal);
+    } else if (s->timing) {
+        if (s->ev_used + 2 > s->ev.size()) {
+            for (int j = 0; j < 64; ++j) {
+                cudaEvent_t e;
+                cudaEventCreate(&e);
+                s->ev.push_back(e);
+            }
+        }
+        e0 = s->ev[s->ev_used++];
+        e1 = s->ev[s->ev_used++];
+        cudaEventRecord(e0, st);
+    }
+    nl += launch_stream_collide(d, parity, st);
+    if (capturing)
+        cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal);
+    else if (s->timing)
+        cudaEventRecord(e1, st);
+    if (d.np > 0) {
+        // the DEM half on the side stream, beside the conversion
+        cudaEventRecord(s->ev_fork, st);
+        cudaStreamWaitEvent(s->side, s->ev_fork, 0);
+        nl += launch_dem(d, s->have_prev, s->side);
+        cudaEventRecord(s->ev_join, s->side);
+    }
+    nl += launch_conversion(d, parity, st);
+    if (d.np > 0) {
+        cudaStreamWaitEvent(st, s->ev_join, 0);
+        nl += launch_remap(d, parity, st);
+    }
+    nl += launch_classify(d, st);
+    nl += launch_pool_spread(d, st);
+    nl += launch_normals(d, d.nrm, st);
+    return nl;
+}
+
+static void drop_graph(fslbm* s, int parity) {
+    if (s->gexec[parity]) cudaGraphExecDestroy(s->gexec[parity]);
+    if (s->graph[parity]) cudaGraphDestroy(s->graph[parity]);
+    s->gexec[parity] = nullptr;
+    s->graph[parity] = nullptr;
+    s->gev[parity][0] = s->gev[parity][1] = nullptr;
+}
+
+// Captures the step of one parity into a graph; false if it cannot be (the
+// stream is already being captured by the caller, or capture fails: graphs
+// then stay off for this simulation).
+static bool capture_step(fslbm* s, int parity) {
+    drop_graph(s, parity);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s->st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return false;
+    }
+    for (int k = 0; k < 2; ++k)
+        if (!s->ev_cap[k] && cudaEventCreate(&s->ev_cap[k]) != cudaSuccess) {
+            cudaGetLastError();
+            s->graphs_on = false;
+            return false;
+        }
+    if (cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        s->graphs_on = false;
+        return false;
+    }
+    const int nl = enqueue_step(s, parity, true);
+    cudaGraph_t g = nullptr;
+    if (cudaStreamEndCapture(s->st, &g) != cudaSuccess || !g) {
+        cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        s->graphs_on = false;
+        return false;
+    }
+    // the two event-record nodes, told apart by their placeholder event
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
+    for (size_t k = 0; k < nn; ++k) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[k], &t) != cudaSuccess || t != cudaGraphNodeTypeEventRecord) continue;
+        cudaEvent_t e = nullptr;
+        cudaGraphEventRecordNodeGetEvent(nodes[k], &e);
+        if (e == s->ev_cap[0]) s->gev[parity][0] = nodes[k];
+        if (e == s->ev_cap[1]) s->gev[parity][1] = nodes[k];
+    }
+    s->graph[parity] = g;
+    if (!s->gev[parity][0] || !s->gev[parity][1] ||
+        cudaGraphInstantiate(&s->gexec[parity], g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        drop_graph(s, parity);
+        s->graphs_on = false;
+        return false;
+    }
+    s->graph_launches[parity] = nl;
+    return true;
+}
+
+// Replays the graph of one parity; the sweep's events are retargeted at a
+// fresh pair when timing is on.
+static int replay_step(fslbm* s, int parity) {
+    if (s->timing) {
+        if (s->ev_used + 2 > s->ev.size()) {
+            for (int j = 0; j < 64; ++j) {
+                cudaEvent_t e;
+                cudaEventCreate(&e);
+                s->ev.push_back(e);
+            }
+        }
+        cudaGraphExecEventRecordNodeSetEvent(s->gexec[parity], s->gev[parity][0], s->ev[s->ev_used++]);
+        cudaGraphExecEventRecordNodeSetEvent(s->gexec[parity], s->gev[parity][1], s->ev[s->ev_used++]);
+    } else {
+        cudaGraphExecEventRecordNodeSetEvent(s->gexec[parity], s->gev[parity][0], s->ev_cap[0]);
+        cudaGraphExecEventRecordNodeSetEvent(s->gexec[parity], s->gev[parity][1], s->ev_cap[1]);
+    }
+    cudaGraphLaunch(s->gexec[parity], s->st);
+    return s->graph_launches[parity];
+}
+
 int fslbm_step(fslbm* s, int64_t n_steps) {
     if (!s || n_steps < 0) return FSLBM_EINVAL;
     if (s->host_err) return s->host_err;
     if (s->p.normal_model == 1 && !s->d.mlp) return FSLBM_ESTATE;
     Dev& d = s->d;
     cudaStream_t st = s->st;
+    if (s->graph_dirty) {
+        drop_graph(s, 0);
+        drop_graph(s, 1);
+        s->graph_dirty = false;
+    }
     for (int64_t k = 0; k < n_steps; ++k) {
         const int parity = (int)(s->steps & 1);
-        if (d.np > 0) {
-            cudaMemsetAsync(d.Fh, 0, sizeof(double) * 3 * d.np, st);
-            cudaMemsetAsync(d.Th, 0, sizeof(double) * 3 * d.np, st);
-        }
         int nl = 0;
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (s->timing) {
-            if (s->ev_used + 2 > s->ev.size()) {
-                for (int j = 0; j < 64; ++j) {
-                    cudaEvent_t e;
-                    cudaEventCreate(&e);
-                    s->ev.push_back(e);
-                }
-            }
-            e0 = s->ev[s->ev_used++];
-            e1 = s->ev[s->ev_used++];
-            cudaEventRecord(e0, st);
-        }
-        nl += launch_stream_collide(d, parity, st);
-        if (s->timing) cudaEventRecord(e1, st);
-        if (d.np > 0) {
-            // the DEM half on the side stream, beside the conversion
-            cudaEventRecord(s->ev_fork, st);
-            cudaStreamWaitEvent(s->side, s->ev_fork, 0);
-            nl += launch_dem(d, s->have_prev, s->side);
-            cudaEventRecord(s->ev_join, s->side);
-        }
-        nl += launch_conversion(d, parity, st);
-        if (d.np > 0) {
-            cudaStreamWaitEvent(st, s->ev_join, 0);
-            nl += launch_remap(d, parity, st);
-        }
-        nl += launch_classify(d, st);
-        nl += launch_pool_spread(d, st);
-        nl += launch_normals(d, d.nrm, st);
+        // replay a graph of the step once its launch sequence is settled
+        // (from the third step on: the first differs, and both parities have
+        // then run once), unless the flow control changes the body force
+        // between steps
+        const bool graph = s->graphs_on && s->ctrl_interval == 0 && s->steps >= 2;
+        if (graph && (s->gexec[parity] || capture_step(s, parity)))
+            nl = replay_step(s, parity);
+        else
+            nl = enqueue_step(s, parity, false);
         s->last_parity = parity;
         s->have_prev = 1;
         s->steps++;
@@ -693,6 +829,7 @@ int fslbm_set_body_force(fslbm* s, const double g[3]) {
     Dev& d = s->d;
     d.gxd = g[0]; d.gyd = g[1]; d.gzd = g[2];
     d.gx = (float)g[0]; d.gy = (float)g[1]; d.gz = (float)g[2];
+    s->graph_dirty = true;
     return FSLBM_OK;
 }
 
@@ -707,6 +844,7 @@ int fslbm_set_flow_control(fslbm* s, double target_u, double gain, int64_t inter
     s->ctrl_target = target_u;
     s->ctrl_gain = gain;
     s->ctrl_interval = interval;
+    s->graph_dirty = true;
     return FSLBM_OK;
 }
 
@@ -800,6 +938,7 @@ int fslbm_bed_spectrum(const double* h, int64_t nt, int64_t nx, double dx, doubl
 int fslbm_set_wait_limit(fslbm* s, int64_t polls) {
     if (!s || polls < 0 || polls > WAIT_LIMIT_DEFAULT) return FSLBM_EINVAL;
     s->d.wait_limit = (int)polls;
+    s->graph_dirty = true;
     return FSLBM_OK;
 }
 
@@ -826,6 +965,7 @@ int fslbm_set_normal_model(fslbm* s, const uint16_t* w, int64_t n_params) {
         d.mlp_stats = s->mlp_stats;
         s->p.normal_model = 1;
     }
+    s->graph_dirty = true;
     launch_normals(d, d.nrm, s->st);
     return sync_check(s);   // h stays alive until the copy has completed
 }
@@ -851,6 +991,10 @@ void fslbm_destroy(fslbm* s) {
     }
     if (s->ev_fork) cudaEventDestroy(s->ev_fork);
     if (s->ev_join) cudaEventDestroy(s->ev_join);
+    for (int k = 0; k < 2; ++k) {
+        drop_graph(s, k);
+        if (s->ev_cap[k]) cudaEventDestroy(s->ev_cap[k]);
+    }
     for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
     for (void* p : s->allocs) cudaFree(p);
     delete s;
