@@ -39,6 +39,7 @@ import numpy as np  # noqa: E402
 
 UNIT = "MLUPS"
 STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
+LINK_MODE = 0   # where the particle links are taken (--links: 0 the library's choice, 1 solid side, 2 fluid side)
 ELEM = {"fp32": 4, "fp16": 2, "bf16": 2}
 
 
@@ -233,7 +234,8 @@ def timed_run(args, w, storage_name, theta, stream, local, barrier, world, horiz
 
     from paper_2301_10674_gb300 import fslbm as F
 
-    sim = F.Simulation.from_workload(w, storage=STORAGE[storage_name], stream=stream)
+    sim = F.Simulation.from_workload(w, storage=STORAGE[storage_name], stream=stream,
+                                     link_mode=LINK_MODE)
     if theta is not None:
         sim.set_normal_model(theta)
     m0 = sim.reduce()
@@ -420,6 +422,7 @@ def run_ours(args, world, rank, local):
         "config": {"workload": w.name, "form": form, "lattice": [w.nx, w.ny, w.nz], "cells": ncell,
                    "spheres": w.nspheres, "spheres_nominal": w.spheres_nominal, "storage": args.storage,
                    "normals": args.normals,
+                   "particle_links": {0: "library default", 1: "solid-side pass", 2: "fluid side (bed kernel)"}[LINK_MODE],
                    "cells_by_type": {"gas": int(cb[0]), "liquid": int(cb[1]), "interface": int(cb[2]),
                                      "solid": int(cb[3])},
                    "l2": f"no flush: the PDF lattice ({27 * 2 * ELEM[args.storage] * ncell / 1e9:.1f} GB incl. "
@@ -452,7 +455,7 @@ def run_e2e(args, w, storage, theta, stream, world):
     rad = torch.from_numpy(np.ascontiguousarray(w.radius)).pin_memory().numpy()
     fix = torch.from_numpy(np.ascontiguousarray(w.fixed)).pin_memory().numpy()
     diag = torch.empty(8, dtype=torch.float64).pin_memory().numpy()
-    params = F.params_from_workload(w, storage)
+    params = F.params_from_workload(w, storage, LINK_MODE)
     bits = None if theta is None else torch.from_numpy(F.bf16_bits(theta)).pin_memory().numpy()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -520,7 +523,8 @@ def run_precision_study(args):
     steps = args.study_steps
     gpu = {}
     for st_name, nm in COMPARE_FORMS:
-        sim = F.Simulation.from_workload(w, storage=STORAGE[st_name], stream=stream)
+        sim = F.Simulation.from_workload(w, storage=STORAGE[st_name], stream=stream,
+                                         link_mode=LINK_MODE)
         if nm == "mlp":
             sim.set_normal_model(theta)
         m0 = sim.reduce()[0]
@@ -633,6 +637,8 @@ def main():
                     help="steps after which the forms' states are compared (untimed beyond the timed steps)")
     ap.add_argument("--mlp-stencils", type=int, default=1 << 22)
     ap.add_argument("--mlp-steps", type=int, default=40000)
+    ap.add_argument("--links", type=int, choices=(0, 1, 2), default=0,
+                    help="particle links: 0 the library's choice, 1 pass over the solid cells, 2 fluid side")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=5)
@@ -649,6 +655,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    global LINK_MODE
+    LINK_MODE = args.links
     world, rank, local = _dist()
     if args.precision_study:
         print(json.dumps(run_precision_study(args)), flush=True)

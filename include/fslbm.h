@@ -124,7 +124,15 @@ typedef struct {
                                     of third order in u; the liquid cells then run in
                                     the one-cell kernel. Default 0 (the paper's runs,
                                     read as without it) */
-    int32_t reserved;            /* 0 */
+    int32_t link_mode;           /* where the moving bounce-back and the momentum
+                                    exchange at particle links (Section 2.2) are taken:
+                                    0 (default) the library's choice, at present 1;
+                                    1 a separate pass over the solid cells before the
+                                    liquid cells; 2 the fluid side, inside the kernels
+                                    of the liquid and interface cells, where the lattice
+                                    allows it (x extent a multiple of 32, 32-bit element
+                                    indices, no Galilean correction; else 1). Both give
+                                    the same values up to rounding */
 } fslbm_params;
 
 /* Fills *p with defaults: periodic x, walls in y and z, omega = 1/0.51,

@@ -173,7 +173,8 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     if (p->storage < 0 || p->storage > 2) return FSLBM_EINVAL;
     if (p->link_mass_correction < 0 || p->link_mass_correction > 1) return FSLBM_EINVAL;
     if (p->excess_even < 0 || p->excess_even > 1 || p->lubrication < 0 || p->lubrication > 1) return FSLBM_EINVAL;
-    if (p->galilean_correction < 0 || p->galilean_correction > 1 || p->reserved != 0) return FSLBM_EINVAL;
+    if (p->galilean_correction < 0 || p->galilean_correction > 1 || p->link_mode < 0 || p->link_mode > 2)
+        return FSLBM_EINVAL;
     if (p->dem_substeps < 1 || !(p->restitution > 0.0 && p->restitution <= 1.0)) return FSLBM_EINVAL;
     if (!(p->collision_time > 0.0) || !(p->rho_p > 0.0) || !(p->rho_gas > 0.0)) return FSLBM_EINVAL;
     if (!(p->poisson >= 0.0 && p->poisson < 1.0) || !(p->friction >= 0.0)) return FSLBM_EINVAL;
@@ -236,6 +237,10 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     d.galilean = p->galilean_correction;
     d.link_corr = p->link_mass_correction;
     d.idx32 = 27LL * n < (1LL << 32) ? 1 : 0;
+    // fluid-side particle links need the pair kernels (nx even, 32-bit
+    // indices, no Galilean correction) and the 32-cell type bit words
+    d.links_fused = (p->link_mode == 2 && d.idx32 && p->nx % 32 == 0 && !p->galilean_correction) ? 1 : 0;
+    d.nsegx = (p->nx + fsl::BED_SEG - 1) / fsl::BED_SEG;
     d.wait_limit = WAIT_LIMIT_DEFAULT;
     d.storage = p->storage;
     d.rho_p = p->rho_p;
@@ -281,6 +286,11 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     d.ibits = dalloc<unsigned>(s, n / 32 + 1, ok);
     d.sbits = dalloc<unsigned>(s, n / 32 + 1, ok);
     d.tiles = dalloc<int>(s, n / fsl::SP_TILE + 1, ok);
+    {
+        const long long nseg = (long long)d.nsegx * p->ny * p->nz;
+        d.segflag = dalloc<uint8_t>(s, nseg + 4, ok);
+        d.bseg = dalloc<int>(s, nseg + 1, ok);
+    }
     d.tl_info = dalloc<int>(s, 2 * tcap, ok);
     int* counts = dalloc<int>(s, 16, ok);
     if (ok) {
@@ -293,6 +303,7 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
         d.dl_count = counts + 6;
         d.sl_count = counts + 7;
         d.tile_count = counts + 8;
+        d.bseg_count = counts + 9;
     }
     double* dd = dalloc<double>(s, 4, ok);
     if (ok) {
@@ -371,6 +382,7 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     cudaMemsetAsync(d.viol, 0, sizeof(unsigned long long), st);
     cudaMemsetAsync(d.dirty, 0, n + 4, st);
     cudaMemsetAsync(d.fixowner, 0xff, n * sizeof(int), st);
+    cudaMemsetAsync(d.segflag, 0, (size_t)d.nsegx * p->ny * p->nz + 4, st);
     launch_init_flat(d, p->liquid_height, st);
     launch_classify(d, st);
     launch_normals(d, d.nrm, st);

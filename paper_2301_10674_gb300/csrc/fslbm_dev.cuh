@@ -45,6 +45,7 @@ enum : uint8_t { CV_TO_LIQ = 1, CV_TO_GAS = 2, CV_EVEN = 4 };
 enum : int { ERR_CAPACITY = 1, ERR_NAN = 2, ERR_INVARIANT = 4, ERR_HISTORY = 8, ERR_DISPLACEMENT = 16, ERR_TIMEOUT = 32 };
 
 constexpr int SP_TILE = 256;     // cells per x-tile of the staged even step
+constexpr int BED_SEG = 256;     // cells per x-segment of the bed kernel (one block of 128 pairs)
 constexpr int WAIT_LIMIT_DEFAULT = 1 << 22;   // polls of a bounded device wait
 
 constexpr int REDUCE_MAX_BY = 2048;   // row blocks of the lattice reduction (several rows per thread)
@@ -95,6 +96,13 @@ struct Dev {
     int* tl; int* tl_count; int tl_cap;        // particle map transitions
     int* sl; int* sl_count; int sl_cap;        // solid cells with a fluid neighbour
     int* tiles; int* tile_count;               // SP_TILE-cell x-tiles holding a liquid cell
+    // particle links taken from the fluid side: the bed segments (BED_SEG-cell
+    // x-ranges of a row holding a liquid cell with a solid neighbour) are
+    // flagged per segment and listed for the bed kernel
+    int links_fused;
+    int nsegx;                                  // segments per row, ceil(nx / BED_SEG)
+    uint8_t* segflag;                           // [nz][ny][nsegx]
+    int* bseg; int* bseg_count;
     unsigned* fbits; unsigned* ibits; unsigned* sbits;   // per 32 cells of a row: fluid / interface / solid bits
     int* tl_info;                               // per transition: new owner / new type
     double* pool;

@@ -309,6 +309,8 @@ __global__ void __launch_bounds__(64) k_dem_substep(Dev s, const double* __restr
     double W[3] = {Wa[3 * p], Wa[3 * p + 1], Wa[3 * p + 2]};
     if (s.fixed[p]) {
         for (int a = 0; a < 3; ++a) { Xb[3 * p + a] = X[a]; Ub[3 * p + a] = U[a]; Wb[3 * p + a] = W[a]; }
+        // the top of the particle cells counts the fixed particles too
+        if (last) atomicMax(s.zmax_cell, (int)ceil(X[2] + s.R[p]) + 2);
         return;
     }
     const double ri = s.R[p], mi = s.M[p], Ii = s.I[p];

@@ -189,23 +189,27 @@ constexpr int liquid_pair_min_blocks() { return PAR == 0 ? 4 : (sizeof(S) == 2 ?
 // Stream and collide one pair (x even, x + 1) of row `row`; liq: bit 0 cell
 // x liquid, bit 1 cell x + 1 liquid. `interior`: every neighbour of both
 // cells inside the lattice without wrap (always true in an even step, which
-// touches only a cell's own slots).
+// touches only a cell's own slots). In two halves, so that the bed kernel can
+// replace the values pulled from particle cells in between: pair_load pulls
+// the PDFs (v, with the references ref of the slots read and wt of the slots
+// written), pair_finish collides and stores them.
 template <typename S, int PAR>
-__device__ __forceinline__ void pair_update(const Dev& s, S* f, int x, int row, unsigned liq, bool interior) {
+__device__ __forceinline__ void pair_load(const Dev& s, const S* f, int x, int row, unsigned liq, bool interior,
+                                          float2 (&v)[27], PairRef& ref, float (&wt)[3]) {
     const unsigned un = (unsigned)s.n;
     const int sxy = s.nx * s.ny;
     const int cell = x + s.nx * row;
     const int y = row % s.ny, z = row / s.ny;
-    float2 v[27];
     constexpr float SC = Store<S>::scale;
     // storage references (16-bit storage): interior pairs fold them into the
     // collision (even step: every slot at z; odd step: direction c_z read
     // from z - c_z, written to z + c_z); the others add and remove them value
     // by value and collide with zero references
-    PairRef ref;
 #pragma unroll
     for (int k = 0; k < 3; ++k) ref.rd[k] = 0.f;
-    float wt[3] = {0.f, 0.f, 0.f};   // reference of the slots written along c_z = -1, 0, +1
+    // wt: reference of the slots written along c_z = -1, 0, +1
+#pragma unroll
+    for (int k = 0; k < 3; ++k) wt[k] = 0.f;
     if (interior) {
 #pragma unroll
         for (int q = 0; q < 27; ++q) {
@@ -245,6 +249,16 @@ __device__ __forceinline__ void pair_update(const Dev& s, S* f, int x, int row, 
             }
         }
     }
+}
+
+template <typename S, int PAR>
+__device__ __forceinline__ void pair_finish(const Dev& s, S* f, int x, int row, unsigned liq, bool interior,
+                                            float2 (&v)[27], const PairRef& ref, const float (&wt)[3]) {
+    const unsigned un = (unsigned)s.n;
+    const int sxy = s.nx * s.ny;
+    const int cell = x + s.nx * row;
+    const int y = row % s.ny, z = row / s.ny;
+    constexpr float SC = Store<S>::scale;
     collide_pair<Pair<S>::SCALE_LOG2, Store<S>::HREF>(v, s.omega, s.gx, s.gy, s.gz, ref);
     if (Store<S>::HREF && interior) {
         // each output loses the reference of the slot it is written to
@@ -299,6 +313,15 @@ __device__ __forceinline__ void pair_update(const Dev& s, S* f, int x, int row, 
     }
 }
 
+template <typename S, int PAR>
+__device__ __forceinline__ void pair_update(const Dev& s, S* f, int x, int row, unsigned liq, bool interior) {
+    float2 v[27];
+    PairRef ref;
+    float wt[3];
+    pair_load<S, PAR>(s, f, x, row, liq, interior, v, ref, wt);
+    pair_finish<S, PAR>(s, f, x, row, liq, interior, v, ref, wt);
+}
+
 // PART 1 keeps to the interior pairs of an odd step (all 26 neighbours of
 // both cells inside the lattice, no wrap), so that the kernel of the bulk
 // carries no boundary code; k_liquid_pair_edges takes the others. PART 0:
@@ -311,6 +334,9 @@ __global__ void __launch_bounds__(128, liquid_pair_min_blocks<S, PAR>()) k_liqui
     S* f = static_cast<S*>(s.f);
     const int nrows = s.ny * s.nz;
     for (int row = blockIdx.y; row < nrows; row += gridDim.y) {
+        // the bed kernel takes the segments with particle links (the whole
+        // block skips the row together)
+        if (s.links_fused && s.segflag[row * s.nsegx + blockIdx.x]) continue;
         const int yr = row % s.ny, zr = row / s.ny;
         const bool face_row = yr == 0 || yr == s.ny - 1 || zr == 0 || zr == s.nz - 1;
         const int x0 = blockIdx.x * 256 + 2 * (int)threadIdx.x;
@@ -368,6 +394,7 @@ __global__ void __launch_bounds__(128) k_liquid_pair_edges(Dev s) {
         return;
     }
     const int row = y + s.ny * z;
+    if (s.links_fused && s.segflag[row * s.nsegx + x / BED_SEG]) return;   // a bed segment
     const uchar2 fl = *reinterpret_cast<const uchar2*>(s.flags + x + (long long)s.nx * row);
     const unsigned lm = ((fl.x & TYPE_MASK) == T_LIQ ? 1u : 0u) | ((fl.y & TYPE_MASK) == T_LIQ ? 2u : 0u);
     if (!lm) return;
@@ -451,7 +478,9 @@ __global__ void k_sp_tiles(Dev s) {
                 other |= lo;
             }
         }
-        act = any != 0;
+        // bed tiles (the same 256-cell x-ranges as the bed segments) are the
+        // bed kernel's
+        act = any != 0 && !(s.links_fused && s.segflag[t]);
         if (other == 0) val |= SP_FULL;
     }
     block_append(s, act, val, s.tiles, s.tile_count, (int)ntile);
@@ -628,6 +657,15 @@ __device__ __forceinline__ void flush_mem(const Dev& s, int key, const float (&F
     }
 }
 
+// one run's force and torque straight to the particle's FP64 sums
+__device__ __forceinline__ void flush_direct(const Dev& s, int key, const float (&F)[3], const float (&T)[3]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        atomicAdd(&s.Fh[3 * key + c], (double)F[c]);
+        atomicAdd(&s.Th[3 * key + c], (double)T[c]);
+    }
+}
+
 // particle surface velocity at a link midpoint and the link force
 // (Section 2.2): f_q = f*_opp + 6 w_q c_q.u_b, force on the particle
 // -c_q (f*_opp + f_q) - u_b (f*_opp - f_q) with zero-centred PDFs; torque
@@ -766,6 +804,314 @@ __global__ void __launch_bounds__(256, 3) k_solid_links(Dev s) {
     }
 }
 
+// ---------------------------------------------------------------- bed segments
+// Particle links from the fluid side (Section 2.2). A liquid cell x pulls f_q
+// from a particle cell s = x - c_q as the moving bounce-back value
+// f_q(x) = f*_opp(q)(x) + 6 w_q c_q.u_b, u_b the particle's surface velocity
+// at the link midpoint x - c_q/2. The cell's own post-collision PDF
+// f*_opp(q)(x) sits in a slot no running cell touches: (opp(q), s) before an
+// even step (the odd step before pushed it there), (q, x) before an odd one.
+// The force on the particle is -c_q (f*_opp + f_q) - u_b (f*_opp - f_q) with
+// zero-centred PDFs, the torque (x_b - X_p) x F. These are the values and
+// sums of the pass over the solid cells (k_solid_links), taken where the
+// liquid cell is updated, so that the bed's PDFs cross HBM once per step.
+//
+// k_liquid_pair_bed updates every liquid pair of the bed segments listed by
+// the classification (the bulk kernels skip them), a warp per 256-cell
+// segment and no block-wide barrier. The warp stages the solid bit words of
+// the 3x3 rows around its segment, compacts the segment's liquid pairs
+// (interior pairs first, then those on the faces of the lattice), and takes
+// them 32 at a time. Each pair reads its solid-neighbour masks from the
+// words; the warp spreads the round's links evenly over its lanes (a
+// contiguous run of links per lane, in the order pair, cell, direction),
+// which compute the bounce-back values into shared memory and sum the
+// momentum exchange per run of equal owner; the runs ending the lanes' shares
+// merge across the warp (a segmented scan) into one FP64 atomic per run and
+// component. The pair then pulls its PDFs as in the bulk kernels, takes the
+// link values in place of those pulled from particle cells, collides and
+// stores.
+constexpr int BED_LINKS = 50;   // links of a pair at most (25 per liquid cell of a liquid pair)
+static_assert(BED_SEG == 256 && SP_TILE == BED_SEG, "bed segments are the 256-cell blocks and tiles");
+
+struct BedWarp {
+    unsigned sw[9][10];              // solid words of rows (y + dy, z + dz), r = dy + 1 + 3 (dz + 1); halo words 0, 9
+    int pairs[BED_SEG / 2];          // the segment's liquid pairs (x << 2 | liquid bits), interior ones first
+    int lbase[33];                   // first link of each lane's pair in the round, and the round's total
+    unsigned lm[2][32];              // solid masks of each lane's two cells
+    int lx[32];                      // x of each lane's pair, bit 30 set for an interior pair
+    float sval[32 * BED_LINKS];      // the round's link values, in link order
+};
+
+// The links of the round, lane `lane`'s share: links [lane C, lane C + C)
+// of `total`, C = ceil(total / 32), four at a time (their owner and PDF loads
+// issued together). Every lane of the warp calls it.
+template <typename S, int PAR>
+__device__ __forceinline__ void bed_links(BedWarp& sh, const Dev& s, const S* f, int lane, int row, int y, int z,
+                                          int total, float& injected) {
+    const int C = (total + 31) >> 5;
+    const int t0 = min(lane * C, total), t1 = min(t0 + C, total);
+    const unsigned un = (unsigned)s.n;
+    int key = -1;
+    float F[3] = {0.f, 0.f, 0.f}, T[3] = {0.f, 0.f, 0.f};
+    PData P;
+    P.xi = make_int4(0, 0, 0, 0);
+    P.xf = P.u = P.w = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (t0 < t1) {
+        int l = 0;
+        while (sh.lbase[l + 1] <= t0) ++l;
+        unsigned r0 = sh.lm[0][l], r1 = sh.lm[1][l];
+        for (int r = t0 - sh.lbase[l]; r > 0; --r) {
+            if (r0) r0 &= r0 - 1u;
+            else r1 &= r1 - 1u;
+        }
+        for (int tb = t0; tb < t1; tb += 4) {
+            int qq[4], xq[4], own[4];
+            float fo[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                own[u] = -2;   // no link (beyond the share)
+                qq[u] = 0;
+                xq[u] = 0;
+                fo[u] = 0.f;
+                if (tb + u < t1) {
+                    while (!(r0 | r1) && l < 31) {   // lanes without links hold none
+                        ++l;
+                        r0 = sh.lm[0][l];
+                        r1 = sh.lm[1][l];
+                    }
+                    int q, kc;
+                    if (r0) { q = __ffs(r0) - 1; r0 &= r0 - 1u; kc = 0; }
+                    else if (r1) { q = __ffs(r1) - 1; r1 &= r1 - 1u; kc = 1; }
+                    else { q = -1; kc = 0; }   // (the counts and masks disagree: cannot happen)
+                    own[u] = -1;
+                    if (q >= 0) {
+                        const int lx = sh.lx[l];
+                        const int xl = (lx & 0x3fffffff) + kc;
+                        qq[u] = q;
+                        xq[u] = xl | (lx & (1 << 30));
+                        const int qx = q % 3 - 1, qy = (q / 3) % 3 - 1, qz = q / 9 - 1;
+                        // the source x - c_q: inside the lattice (the masks
+                        // hold no source beyond a wall face)
+                        const int sx = shift(xl, -qx, s.nx, s.per_x), sy = shift(y, -qy, s.ny, s.per_y),
+                                  sz = shift(z, -qz, s.nz, s.per_z);
+                        if (sx >= 0 && sy >= 0 && sz >= 0) {
+                            const int src = sx + s.nx * (sy + s.ny * sz);
+                            own[u] = s.owner[src];
+                            const unsigned a = PAR == 0 ? (unsigned)(26 - q) * un + (unsigned)src
+                                                        : (unsigned)q * un + (unsigned)(xl + s.nx * row);
+                            fo[u] = Store<S>::ld(f + a);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (own[u] == -2) continue;
+                const int t = tb + u;
+                const int p = own[u];
+                if (p < 0 || p >= s.np) {
+                    set_error(s, ERR_INVARIANT);
+                    sh.sval[t] = 0.f;
+                    continue;
+                }
+                if (p != key) {
+                    if (key >= 0) flush_direct(s, key, F, T);
+                    key = p;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) F[c] = T[c] = 0.f;
+                    P = particle_data(s, p);
+                }
+                const int q = qq[u];
+                const int xl = xq[u] & 0x3fffffff;
+                const bool interior = (xq[u] >> 30) & 1;
+                const int qx = q % 3 - 1, qy = (q / 3) % 3 - 1, qz = q / 9 - 1;
+                const int nzc = (qx != 0) + (qy != 0) + (qz != 0);
+                const float w = nzc == 1 ? 2.f / 27.f : (nzc == 2 ? 1.f / 54.f : 1.f / 216.f);
+                float fov = fo[u];
+                if (Store<S>::HREF) fov += w * s.href[PAR == 0 ? wrap_z(s, z - qz) : z];
+                const float dx = (float)wrap_int(xl - P.xi.x, s.nx, s.per_x) + 0.5f - P.xf.x - 0.5f * (float)qx;
+                const float dy = (float)wrap_int(y - P.xi.y, s.ny, s.per_y) + 0.5f - P.xf.y - 0.5f * (float)qy;
+                const float dz = (float)wrap_int(z - P.xi.z, s.nz, s.per_z) + 0.5f - P.xf.z - 0.5f * (float)qz;
+                const float ubx = P.u.x + (P.w.y * dz - P.w.z * dy);
+                const float uby = P.u.y + (P.w.z * dx - P.w.x * dz);
+                const float ubz = P.u.z + (P.w.x * dy - P.w.y * dx);
+                const float cu = (float)qx * ubx + (float)qy * uby + (float)qz * ubz;
+                const float corr = 6.f * w * cu;
+                const float val = fov + corr;
+                injected += corr;
+                // in the convention of the pair's pull: scaled, and relative
+                // to the reference the collision assumes for the slot
+                // (interior pairs: that of z in an even step, of z - c_z in
+                // an odd one)
+                float rexp = 0.f;
+                if (Store<S>::HREF && interior) rexp = s.href[PAR == 0 ? z : z - qz];
+                sh.sval[t] = Store<S>::scale * (val - w * rexp);
+                const float sum = fov + val;
+                const float Fx = -(float)qx * sum + ubx * corr;
+                const float Fy = -(float)qy * sum + uby * corr;
+                const float Fz = -(float)qz * sum + ubz * corr;
+                F[0] += Fx; F[1] += Fy; F[2] += Fz;
+                T[0] += dy * Fz - dz * Fy;
+                T[1] += dz * Fx - dx * Fz;
+                T[2] += dx * Fy - dy * Fx;
+            }
+        }
+    }
+    // the lanes' last runs, merged where adjacent lanes share the owner
+    flush_mem(s, key, F, T);
+}
+
+// resident blocks per SM asked of the compiler: 6 for the even step (no
+// spills), 5 for the odd one, whose pairs on the faces of the lattice take
+// the boundary code
+template <int PAR>
+constexpr int bed_min_blocks() { return PAR == 0 ? 6 : 5; }
+
+template <typename S, int PAR>
+__global__ void __launch_bounds__(128, bed_min_blocks<PAR>()) k_liquid_pair_bed(Dev s) {
+    __shared__ BedWarp shw[4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    BedWarp& sh = shw[warp];
+    const unsigned full = 0xffffffffu;
+    S* f = static_cast<S*>(s.f);
+    const int count = min(*s.bseg_count, s.nsegx * s.ny * s.nz);
+    const int nxw = s.nx >> 5;
+    float injected = 0.f;
+    for (int i = blockIdx.x * 4 + warp; i < count; i += gridDim.x * 4) {
+        const int seg = s.bseg[i];
+        const int row = seg / s.nsegx, xs = seg - row * s.nsegx;
+        const int y = row % s.ny, z = row / s.ny;
+        const bool face_row = y == 0 || y == s.ny - 1 || z == 0 || z == s.nz - 1;
+        for (int k = lane; k < 90; k += 32) {
+            const int r = k / 10, j = k - 10 * r;
+            const int yy = shift(y, r % 3 - 1, s.ny, s.per_y), zz = shift(z, r / 3 - 1, s.nz, s.per_z);
+            int xw = xs * (BED_SEG / 32) + j - 1;
+            if (xw < 0) xw = s.per_x ? nxw - 1 : -1;
+            else if (xw == nxw) xw = s.per_x ? 0 : -1;
+            else if (xw > nxw) xw = -1;
+            sh.sw[r][j] = (yy >= 0 && zz >= 0 && xw >= 0) ? s.sbits[((long long)zz * s.ny + yy) * nxw + xw] : 0u;
+        }
+        // the segment's liquid pairs: lane l looks at cells xb + 8l .. + 7
+        // (pairs 4l .. 4l + 3; nx is a multiple of 32, so a segment holds
+        // whole groups of eight)
+        const int xb = xs * BED_SEG;
+        const int xg = xb + 8 * lane;
+        unsigned codes = 0;   // 4 bits per pair: liquid bits, and bit 2 for an interior pair
+        if (xg < s.nx) {
+            const uint2 fl = *reinterpret_cast<const uint2*>(s.flags + xg + (long long)s.nx * row);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const unsigned b = ((k < 2 ? fl.x : fl.y) >> (16 * (k & 1))) & 0xffffu;
+                const unsigned lq = ((b & TYPE_MASK) == T_LIQ ? 1u : 0u) | (((b >> 8) & TYPE_MASK) == T_LIQ ? 2u : 0u);
+                const int x = xg + 2 * k;
+                const bool in = PAR == 0 || (x > 0 && x + 1 < s.nx - 1 && !face_row);
+                codes |= (lq | (lq && in ? 4u : 0u)) << (4 * k);
+            }
+        }
+        int ni = 0, nb = 0;   // interior and face pairs of this lane
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const unsigned c = (codes >> (4 * k)) & 0xFu;
+            ni += (c & 4u) ? 1 : 0;
+            nb += ((c & 3u) && !(c & 4u)) ? 1 : 0;
+        }
+        int ii = ni, ib = nb;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int a = __shfl_up_sync(full, ii, o), b = __shfl_up_sync(full, ib, o);
+            if (lane >= o) { ii += a; ib += b; }
+        }
+        const int n_int = __shfl_sync(full, ii, 31), n_all = n_int + __shfl_sync(full, ib, 31);
+        {
+            int pi = ii - ni, pb = n_int + ib - nb;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const unsigned c = (codes >> (4 * k)) & 0xFu;
+                const int v = ((xg + 2 * k) << 2) | (int)(c & 3u);
+                if (c & 4u) sh.pairs[pi++] = v;
+                else if (c & 3u) sh.pairs[pb++] = v;
+            }
+        }
+        __syncwarp();
+        // rounds of 32 pairs: the interior ones, then those on the faces
+        const int nr_int = (n_int + 31) >> 5, nr_all = nr_int + ((n_all - n_int + 31) >> 5);
+        for (int rnd = 0; rnd < nr_all; ++rnd) {
+            const bool in_phase = rnd < nr_int;
+            const int lo = in_phase ? 32 * rnd : n_int + 32 * (rnd - nr_int);
+            const int e = lo + lane < (in_phase ? n_int : n_all) ? sh.pairs[lo + lane] : -1;
+            const bool act = e >= 0;
+            const bool interior = PAR == 0 || in_phase;   // (every pair of an even step)
+            const int x = act ? e >> 2 : 0;
+            const unsigned liq = act ? (unsigned)e & 3u : 0u;
+            // solid masks: bit q where the source x - c_q (x + 1 - c_q) of
+            // the pair's liquid cell x (x + 1) is a particle cell
+            unsigned qm0 = 0u, qm1 = 0u;
+            if (act) {
+                const int k = x - xb;   // even
+                const int jw = 1 + (k >> 5), kb = k & 31;
+                unsigned n0 = 0u, n1 = 0u;
+#pragma unroll
+                for (int r = 0; r < 9; ++r) {
+                    // bit 1 + j: cell (x & ~31) + j of row r, j = -1 .. 32
+                    const unsigned long long v64 = ((unsigned long long)sh.sw[r][jw] << 1) |
+                                                   (sh.sw[r][jw - 1] >> 31) |
+                                                   ((unsigned long long)(sh.sw[r][jw + 1] & 1u) << 33);
+                    const unsigned b4 = (unsigned)(v64 >> kb) & 0xFu;   // cells x - 1 .. x + 2
+                    n0 |= (b4 & 7u) << (3 * r);
+                    n1 |= ((b4 >> 1) & 7u) << (3 * r);
+                }
+                // neighbour (dx, dy, dz) has index (dx+1) + 3(dy+1) + 9(dz+1),
+                // which is 26 - q for the source of direction q
+                qm0 = (liq & 1u) ? __brev(n0) >> 5 : 0u;
+                qm1 = (liq & 2u) ? __brev(n1) >> 5 : 0u;
+            }
+            const int cnt = __popc(qm0) + __popc(qm1);
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(full, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int total = __shfl_sync(full, incl, 31);
+            if (total) {
+                sh.lbase[lane] = incl - cnt;
+                if (lane == 31) sh.lbase[32] = total;
+                sh.lm[0][lane] = qm0;
+                sh.lm[1][lane] = qm1;
+                sh.lx[lane] = x | (interior ? 1 << 30 : 0);
+                __syncwarp();
+                bed_links<S, PAR>(sh, s, f, lane, row, y, z, total, injected);
+                __syncwarp();
+            }
+            if (act) {
+                float2 v[27];
+                PairRef ref;
+                float wt[3];
+                pair_load<S, PAR>(s, f, x, row, liq, interior, v, ref, wt);
+                if (cnt) {
+                    int pos = incl - cnt;
+#pragma unroll
+                    for (int q = 0; q < 27; ++q)
+                        if ((qm0 >> q) & 1u) v[q].x = sh.sval[pos++];
+#pragma unroll
+                    for (int q = 0; q < 27; ++q)
+                        if ((qm1 >> q) & 1u) v[q].y = sh.sval[pos++];
+                }
+                pair_finish<S, PAR>(s, f, x, row, liq, interior, v, ref, wt);
+            }
+            __syncwarp();   // lbase, lm, lx, sval free for the next round
+        }
+        __syncwarp();       // sw and pairs free for the next segment
+    }
+    // R-12a: the net injection into liquid cells leaves the pool (one FP64
+    // atomic per warp)
+    if (s.link_corr) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) injected += __shfl_xor_sync(full, injected, o);
+        if (lane == 0 && injected != 0.f) atomicAdd(s.pool, -(double)injected);
+    }
+}
+
 // Interface cells, from the interface list: gas-pressure reconstruction
 // (Section 2.1), mass exchange, particle links, collision; the cell's own
 // post-collision PDFs come from and go to the side buffer.
@@ -776,6 +1122,9 @@ __global__ void __launch_bounds__(128) k_interface(Dev s) {
     for (int base = blockIdx.x * blockDim.x; base < count; base += stride) {
         const int i = base + threadIdx.x;
         const bool work = i < count;
+        // momentum exchange of the fluid-side particle links
+        int lkey = -1;
+        float LF[3] = {0.f, 0.f, 0.f}, LT[3] = {0.f, 0.f, 0.f};
         if (work) {
             const long long cell = s.wl[i];
             int x, y, z;
@@ -855,9 +1204,43 @@ __global__ void __launch_bounds__(128) k_interface(Dev s) {
                 }
                 const int sx = xs[1 - cx(q)], sy = ys[1 - cy(q)], sz = zs[1 - cz(q)];
                 const long long src = sx + (long long)s.nx * (sy + (long long)s.ny * sz);
-                // solid source: the pulled value is the bounce-back value
-                // placed by the link pass
-                if ((solidm >> q) & 1u) continue;
+                // solid source: the pulled value is the bounce-back value,
+                // placed by the link pass, or formed here from the cell's own
+                // f*_opp(q) (its side-buffer copy) with the momentum exchange
+                // summed per run of equal owner
+                if ((solidm >> q) & 1u) {
+                    if (s.links_fused) {
+                        const int p = s.owner[src];
+                        if (p < 0 || p >= s.np) {
+                            set_error(s, ERR_INVARIANT);
+                            continue;
+                        }
+                        if (p != lkey) {
+                            if (lkey >= 0) flush_direct(s, lkey, LF, LT);
+                            lkey = p;
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) LF[c] = LT[c] = 0.f;
+                        }
+                        const PData P = particle_data(s, p);
+                        const float dx = (float)wrap_int(x - P.xi.x, s.nx, s.per_x) + 0.5f - P.xf.x - 0.5f * cx(q);
+                        const float dy = (float)wrap_int(y - P.xi.y, s.ny, s.per_y) + 0.5f - P.xf.y - 0.5f * cy(q);
+                        const float dz = (float)wrap_int(z - P.xi.z, s.nz, s.per_z) + 0.5f - P.xf.z - 0.5f * cz(q);
+                        const float ubx = P.u.x + (P.w.y * dz - P.w.z * dy);
+                        const float uby = P.u.y + (P.w.z * dx - P.w.x * dz);
+                        const float ubz = P.u.z + (P.w.x * dy - P.w.y * dx);
+                        const float corr = 6.f * wq(q) * (cx(q) * ubx + cy(q) * uby + cz(q) * ubz);
+                        v[q] = fob + corr;
+                        const float sum = fob + v[q];
+                        const float Fx = -cx(q) * sum + ubx * corr;
+                        const float Fy = -cy(q) * sum + uby * corr;
+                        const float Fz = -cz(q) * sum + ubz * corr;
+                        LF[0] += Fx; LF[1] += Fy; LF[2] += Fz;
+                        LT[0] += dy * Fz - dz * Fy;
+                        LT[1] += dz * Fx - dx * Fz;
+                        LT[2] += dx * Fy - dy * Fx;
+                    }
+                    continue;
+                }
                 const bool gas = (gasm >> q) & 1u;
                 if (!gas) {
                     // fluid source: mass exchange with the pulled post-collision PDF
@@ -896,6 +1279,7 @@ __global__ void __launch_bounds__(128) k_interface(Dev s) {
             s.mass[cell] = mx + dm;
             s.ru[cell] = make_float4(rho, ux, uy, uz);
         }
+        flush_mem(s, lkey, LF, LT);
     }
 }
 
@@ -944,13 +1328,28 @@ static int link_blocks() {
     return blocks;
 }
 
+// blocks of the bed kernel: one resident wave (the kernel strides over the
+// list of bed segments)
+template <typename S, int PAR>
+static int bed_blocks() {
+    static int blocks = 0;
+    if (blocks == 0) {
+        int per_sm = 0, dev = 0, sms = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_liquid_pair_bed<S, PAR>, 128, 0);
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        blocks = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+    }
+    return blocks;
+}
+
 template <typename S>
 static void launch_typed(const Dev& s, int parity, cudaStream_t st) {
     const int lb = 152 * 8;
     // liquid kernels: threads along x, blocks over the rows (y, z)
     const dim3 lgrid((unsigned)((s.nx + 255) / 256), (unsigned)(s.ny * s.nz < 65535 ? s.ny * s.nz : 65535));
     if (parity == 0) {
-        if (s.np > 0) k_solid_links<S, 0><<<link_blocks<S, 0>(), 256, 0, st>>>(s);
+        if (s.np > 0 && !s.links_fused) k_solid_links<S, 0><<<link_blocks<S, 0>(), 256, 0, st>>>(s);
         if (use_staged_pairs(s)) {
             if constexpr (sizeof(S) == 2) {
                 cudaMemsetAsync(s.tile_count, 0, sizeof(int), st);
@@ -962,9 +1361,10 @@ static void launch_typed(const Dev& s, int parity, cudaStream_t st) {
         } else {
             k_liquid<S, 0><<<lgrid, 256, 0, st>>>(s);
         }
+        if (s.np > 0 && s.links_fused) k_liquid_pair_bed<S, 0><<<bed_blocks<S, 0>(), 128, 0, st>>>(s);
         k_interface<S, 0><<<lb, 128, 0, st>>>(s);
     } else {
-        if (s.np > 0) k_solid_links<S, 1><<<link_blocks<S, 1>(), 256, 0, st>>>(s);
+        if (s.np > 0 && !s.links_fused) k_solid_links<S, 1><<<link_blocks<S, 1>(), 256, 0, st>>>(s);
         if (use_split(s)) {
             k_liquid_pair<S, 1, 1><<<lgrid, 128, 0, st>>>(s);
             const long long ne = (2LL * s.nz + 2LL * (s.ny > 2 ? s.ny - 2 : 0)) * (s.nx / 2) +
@@ -975,6 +1375,7 @@ static void launch_typed(const Dev& s, int parity, cudaStream_t st) {
         } else {
             k_liquid<S, 1><<<lgrid, 256, 0, st>>>(s);
         }
+        if (s.np > 0 && s.links_fused) k_liquid_pair_bed<S, 1><<<bed_blocks<S, 1>(), 128, 0, st>>>(s);
         k_interface<S, 1><<<lb, 128, 0, st>>>(s);
     }
 }

@@ -546,6 +546,65 @@ __global__ void k_classify_bits(Dev s) {
     block_append_mask(s, sol_mask, c0, s.sl, s.sl_count, s.sl_cap);
 }
 
+// Bed segments, for particle links taken from the fluid side: a thread per
+// BED_SEG-cell x-segment of a row flags it when one of its liquid cells has a
+// solid cell among its 26 neighbours (the solid words of the 3x3 rows around
+// it, dilated by one cell along x, ANDed with its liquid words) and lists it.
+// Rows at or above zmax_cell hold no such cell (no particle reaches them).
+__global__ void k_bed_segments(Dev s) {
+    constexpr int WPS = BED_SEG / 32;                // words per segment
+    const long long sg = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nxw = s.nx >> 5;
+    const long long nseg = (long long)s.nsegx * s.ny * s.nz;
+    bool bed = false;
+    if (sg < nseg) {
+        const long long row = sg / s.nsegx;
+        const int xs = (int)(sg - row * s.nsegx);
+        const int y = (int)(row % s.ny), z = (int)(row / s.ny);
+        const int w0 = xs * WPS;
+        const int nw = min(WPS, nxw - w0);
+        unsigned liq[WPS];
+        unsigned any = 0;
+#pragma unroll
+        for (int k = 0; k < WPS; ++k) {
+            liq[k] = k < nw ? s.fbits[row * nxw + w0 + k] & ~s.ibits[row * nxw + w0 + k] : 0u;
+            any |= liq[k];
+        }
+        if (any && (s.per_z || z < *s.zmax_cell)) {
+            unsigned dil[WPS];
+#pragma unroll
+            for (int k = 0; k < WPS; ++k) dil[k] = 0u;
+            for (int dz = -1; dz <= 1; ++dz) {
+                const int zz = shift(z, dz, s.nz, s.per_z);
+                if (zz < 0) continue;
+                for (int dy = -1; dy <= 1; ++dy) {
+                    const int yy = shift(y, dy, s.ny, s.per_y);
+                    if (yy < 0) continue;
+                    const long long rb = ((long long)zz * s.ny + yy) * nxw;
+                    // word w0 + k for k in [-1, nw]: the x-halo wraps on a
+                    // periodic x axis and is empty beyond a wall face
+                    unsigned wv[WPS + 2];
+#pragma unroll
+                    for (int k = -1; k <= WPS; ++k) {
+                        int xw = w0 + k;
+                        if (k > nw) { wv[k + 1] = 0u; continue; }
+                        if (xw < 0) xw = s.per_x ? nxw - 1 : -1;
+                        else if (xw >= nxw) xw = s.per_x ? 0 : -1;
+                        wv[k + 1] = xw >= 0 ? s.sbits[rb + xw] : 0u;
+                    }
+#pragma unroll
+                    for (int k = 0; k < WPS; ++k)
+                        dil[k] |= wv[k + 1] | (wv[k + 1] << 1) | (wv[k + 1] >> 1) | (wv[k] >> 31) | (wv[k + 2] << 31);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < WPS; ++k) bed |= (liq[k] & dil[k]) != 0u;
+        }
+        s.segflag[sg] = bed ? 1 : 0;
+    }
+    block_append(s, bed, (int)sg, s.bseg, s.bseg_count, (int)nseg);
+}
+
 // Fallback for lattices whose x extent is not a multiple of 32: one thread
 // per cell, 26 neighbour reads for solid cells.
 __global__ void k_classify(Dev s) {
@@ -610,6 +669,11 @@ int launch_classify(const Dev& s, cudaStream_t st) {
         k_type_bits<<<blocks_for(s.n / 32, 256), 256, 0, st>>>(s);
         k_classify_bits<<<blocks_for(s.n / 32, 128), 128, 0, st>>>(s);
         ++k;
+        if (s.links_fused) {
+            cudaMemsetAsync(s.bseg_count, 0, sizeof(int), st);
+            k_bed_segments<<<blocks_for((long long)s.nsegx * s.ny * s.nz, 128), 128, 0, st>>>(s);
+            ++k;
+        }
     } else {
         k_classify<<<blocks_for(s.n, 256), 256, 0, st>>>(s);
     }

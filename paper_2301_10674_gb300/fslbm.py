@@ -90,7 +90,7 @@ class FslbmParams(ctypes.Structure):
         ("excess_even", ctypes.c_int32),
         ("lubrication", ctypes.c_int32),
         ("galilean_correction", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("link_mode", ctypes.c_int32),
     ]
 
 
@@ -295,7 +295,7 @@ def _ptr(a):
 
 # ------------------------------------------------------------------ wrapper
 
-def params_from_workload(w, storage: int = STORE_FP32) -> FslbmParams:
+def params_from_workload(w, storage: int = STORE_FP32, link_mode: int = 0) -> FslbmParams:
     p = fslbm_default_params()
     p.nx, p.ny, p.nz = w.nx, w.ny, w.nz
     p.bc_flags = (PERIODIC_X if w.periodic[0] else 0) | (PERIODIC_Y if w.periodic[1] else 0) | \
@@ -317,6 +317,7 @@ def params_from_workload(w, storage: int = STORE_FP32) -> FslbmParams:
     p.lubrication = w.lubrication
     p.galilean_correction = w.galilean_correction
     p.capacity_particles = max(1024, 2 * (w.nspheres or 0))
+    p.link_mode = int(link_mode)
     return p
 
 
@@ -334,8 +335,8 @@ class Simulation:
         self.h = fslbm_create(params, stream.cuda_stream)
 
     @classmethod
-    def from_workload(cls, w, storage: int = STORE_FP32, stream=None, spheres: bool = True):
-        sim = cls(params_from_workload(w, storage), stream)
+    def from_workload(cls, w, storage: int = STORE_FP32, stream=None, spheres: bool = True, link_mode: int = 0):
+        sim = cls(params_from_workload(w, storage, link_mode), stream)
         if spheres and w.nspheres:
             sim.add_spheres(w.xyz, w.radius, w.fixed)
         return sim

@@ -261,6 +261,76 @@ def test_overlapping_moving_spheres_share_cells():
     sim.close()
 
 
+def _links_workload():
+    """x extent 288: a full 256-cell bed segment and a partial one of 32
+    cells; mobile spheres across the segment border at x = 256, across the
+    periodic x seam and near the walls, one fixed sphere."""
+    w = W.Workload(name="links", nx=288, ny=12, nz=24, tau=0.6, g=(1e-5, 0.0, -2e-4), liquid_height=20.0,
+                   diameter=6.0, bed="none", seed=13).generate()
+    w.xyz = np.array([[255.4, 6.2, 9.3], [286.9, 5.7, 8.1], [100.3, 2.9, 4.2], [140.0, 6.0, 3.05],
+                      [30.6, 9.2, 12.4]])
+    w.radius = np.array([3.0, 2.7, 2.6, 3.0, 2.8])
+    w.fixed = np.array([0, 0, 0, 1, 0], np.uint8)
+    u0 = np.array([[0.015, -0.004, -0.01], [-0.012, 0.006, 0.004], [0.01, 0.0, -0.006], [0.0, 0.0, 0.0],
+                   [0.0, -0.012, -0.014]])
+    return w, u0
+
+
+@pytest.mark.parametrize("storage", [F.STORE_FP32, F.STORE_FP16])
+def test_fluid_side_links_match_the_solid_side_pass(storage):
+    """Particle links taken inside the liquid and interface kernels (the
+    default) against the separate pass over the solid cells: moving spheres
+    cover and uncover cells across a bed-segment border, a partial segment
+    and the periodic seam. Types and owners exact against the oracle at FP32
+    (and between the two forms at every storage); PDFs and hydrodynamic
+    forces of the two forms within rounding of each other, and both within
+    the oracle tolerance at FP32."""
+    w, u0 = _links_workload()
+    sims = []
+    for mode in (2, 1):
+        p = F.params_from_workload(w, storage)
+        p.link_mode = mode
+        sim = F.Simulation(p)
+        sim.add_spheres(w.xyz, w.radius, w.fixed)
+        sim.set(F.FIELD_P_U, u0)
+        sims.append(sim)
+    o = None
+    if storage == F.STORE_FP32:
+        o = oracle_from_workload(w)
+        o.set(O.P_U, u0)
+    fmax = 0.0
+    for _ in range(4):
+        for sim in sims:
+            sim.step(15)
+        if o is not None:
+            o.step(15)
+            for sim in sims:
+                _compare(sim, o, 1e-4, check_particles=False, dev_tol=1e-3)
+        a, b = sims
+        assert np.array_equal(a.get(F.FIELD_TYPE), b.get(F.FIELD_TYPE))
+        assert np.array_equal(a.get(F.FIELD_OWNER), b.get(F.FIELD_OWNER))
+        fa, fb = a.get(F.FIELD_P_F), b.get(F.FIELD_P_F)
+        ta, tb = a.get(F.FIELD_P_T), b.get(F.FIELD_P_T)
+        fmax = max(fmax, np.abs(fb).max())
+        # FP32: rounding only; 16-bit storage: the pass over the solid cells
+        # rounds its bounce-back values to 16 bits once more
+        tol = 1e-5 if storage == F.STORE_FP32 else 1e-2
+        assert np.abs(fa - fb).max() < tol * np.abs(fb).max(), np.abs(fa - fb).max()
+        assert np.abs(ta - tb).max() < tol * np.abs(tb).max(), np.abs(ta - tb).max()
+        to = a.get(F.FIELD_TYPE)
+        if storage == F.STORE_FP32:
+            err = pdf_dev_err(a.get(F.FIELD_PDF), b.get(F.FIELD_PDF), to)
+            assert err < 1e-5, err
+        else:
+            fl = (to == 1) | (to == 2)
+            dev = np.abs(a.get(F.FIELD_PDF)[:, fl] - b.get(F.FIELD_PDF)[:, fl]) / weights()[:, None]
+            assert dev.max() < 2e-3, dev.max()
+    assert fmax > 0.0
+    for sim in sims:
+        assert sim.violations == 0
+        sim.close()
+
+
 @pytest.mark.parametrize("storage,tol", [(F.STORE_FP16, 2e-3), (F.STORE_BF16, 2e-2)])
 def test_reduced_precision_storage(storage, tol):
     """PDFs stored as f - w in FP16 / BF16 with FP32 arithmetic: one step of
