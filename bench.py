@@ -55,6 +55,14 @@ def _peaks() -> tuple[float, str]:
         return 6800.0, "fallback"
 
 
+def _bf16_peak() -> tuple[float, str]:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
@@ -221,9 +229,23 @@ def train_normal_model(stream, n_stencils: int, steps: int, seed: int = 4) -> tu
                                stream.cuda_stream, lr_end=1e-5), "fslbm_mlp_train")
     t2 = time.perf_counter()
     c = curve.cpu().numpy()
+    # FLOPs of one sample and step of the 27-64-64-4 network: forward 2 x 6080
+    # multiply-adds; backward the weight gradients of every layer and the
+    # activation gradients of the two upper ones
+    macs = 27 * 64 + 64 * 64 + 64 * 4
+    flops = 2 * (3 * macs - 27 * 64)
+    tflops = flops * 4096 * steps / max(t2 - t1, 1e-9) / 1e12
+    peak, kind = _bf16_peak()
     return theta.cpu().numpy(), {"stencils": n_stencils, "steps": steps, "batch": 4096, "lr": [2e-3, 1e-5],
                                  "loss_first": float(c[0]), "loss_last100": float(c[-100:].mean()),
-                                 "data_s": round(t1 - t0, 2), "train_s": round(t2 - t1, 2)}
+                                 "data_s": round(t1 - t0, 2), "train_s": round(t2 - t1, 2),
+                                 "roofline": {"bound": "latency", "flops_per_sample": flops,
+                                              "achieved_tflops": round(tflops, 2), "peak_tflops": peak,
+                                              "peak_kind": kind, "frac": round(tflops / peak, 5),
+                                              "us_per_step": round(1e6 * (t2 - t1) / max(steps, 1), 1),
+                                              "limiter": "each Adam step is two dependent launches over 32 "
+                                                         "blocks of 128 samples (a 4096 batch fills a fifth "
+                                                         "of the SMs); the tensor cores wait on the chain"}}
 
 
 def timed_run(args, w, storage_name, theta, stream, local, barrier, world, horizon=0):

@@ -701,8 +701,9 @@ __device__ __forceinline__ PData particle_data(const Dev& s, int p) {
 // (q, x) before an even step, (opp(q), s) before an odd one; f*_opp(q)(x)
 // is read from (opp(q), s) or (q, x) respectively. The force on the
 // particle is -c_q (f*_opp + f_q) - u_b (f*_opp - f_q) with zero-centred
-// PDFs, the torque (x_b - X_p) x F; one owner per thread, so a warp
-// segmented reduction gathers them.
+// PDFs, the torque (x_b - X_p) x F, both summed over the cell's links in
+// closed form (phase 3); one owner per thread, so a warp segmented reduction
+// gathers them.
 template <typename S, int PAR>
 __global__ void __launch_bounds__(256, 3) k_solid_links(Dev s) {
     const int count = min(*s.sl_count, s.sl_cap);
@@ -747,45 +748,73 @@ __global__ void __launch_bounds__(256, 3) k_solid_links(Dev s) {
                 const long long a = PAR == 0 ? (long long)opp(q) * n + cell : (long long)q * n + xn;
                 fo[q] = ((fluidm >> q) & 1u) ? Store<S>::ld(f + a) : 0.f;
             }
-            // phase 3: bounce-back values and momentum exchange
+            // phase 3: bounce-back values and momentum exchange. With u_s the
+            // particle velocity at the solid cell's centre (offset d_s from
+            // the particle centre), the link midpoint lies at d_s + c_q/2, so
+            // u_b = u_s + W x c_q/2 and c_q.u_b = c_q.u_s. With
+            // corr_q = 6 w_q c_q.u_s and t_q = 2 f*_opp + corr_q the link force
+            // is -c_q t_q + u_b corr_q, and the sums over the cell's links are
+            //   F = -sum c t + u_s sum corr + W x (sum c corr) / 2,
+            //   T = d_s x F + [(sum c corr) x u_s + (W sum |c|^2 corr - M W) / 2] / 2,
+            // M = sum corr c c^T: per link only sums with the signs of c_q.
             if (fluidm) {
                 const PData P = particle_data(s, p);
                 const float ddx = (float)wrap_int(x - P.xi.x, s.nx, s.per_x) + 0.5f - P.xf.x;
                 const float ddy = (float)wrap_int(y - P.xi.y, s.ny, s.per_y) + 0.5f - P.xf.y;
                 const float ddz = (float)wrap_int(z - P.xi.z, s.nz, s.per_z) + 0.5f - P.xf.z;
-#pragma unroll
+                const float usx = P.u.x + (P.w.y * ddz - P.w.z * ddy);
+                const float usy = P.u.y + (P.w.z * ddx - P.w.x * ddz);
+                const float usz = P.u.z + (P.w.x * ddy - P.w.y * ddx);
                 // 16-bit storage: references of the solid cell's z and of the
                 // neighbour's (an even step reads at the solid cell and writes
                 // at the neighbour, an odd step the other way round)
                 const float hz = Store<S>::HREF ? s.href[z] : 0.f;
                 const int zm = wrap_z(s, z - 1), zp = wrap_z(s, z + 1);
+                const float hm = Store<S>::HREF ? s.href[zm] : 0.f, hp = Store<S>::HREF ? s.href[zp] : 0.f;
+                float Ax = 0.f, Ay = 0.f, Az = 0.f, B = 0.f, Cx = 0.f, Cy = 0.f, Cz = 0.f, D = 0.f;
+                float Mxx = 0.f, Myy = 0.f, Mzz = 0.f, Mxy = 0.f, Mxz = 0.f, Myz = 0.f;
 #pragma unroll
                 for (int q = 0; q < 27; ++q) {
                     if (!((fluidm >> q) & 1u)) continue;
-                    float hn = 0.f;
-                    if (Store<S>::HREF) {
-                        hn = cz(q) == 0 ? hz : s.href[cz(q) < 0 ? zm : zp];
-                        fo[q] += wq(q) * (PAR == 0 ? hz : hn);
-                    }
+                    const float hn = cz(q) == 0 ? hz : (cz(q) < 0 ? hm : hp);
+                    if (Store<S>::HREF) fo[q] += wq(q) * (PAR == 0 ? hz : hn);
                     const int xn = cell + o.ox[1 + cx(q)] + o.oy[1 + cy(q)] + o.oz[1 + cz(q)];
-                    const float dx = ddx + 0.5f * cx(q), dy = ddy + 0.5f * cy(q), dz = ddz + 0.5f * cz(q);
-                    const float ubx = P.u.x + (P.w.y * dz - P.w.z * dy);
-                    const float uby = P.u.y + (P.w.z * dx - P.w.x * dz);
-                    const float ubz = P.u.z + (P.w.x * dy - P.w.y * dx);
-                    const float cu = cx(q) * ubx + cy(q) * uby + cz(q) * ubz;
-                    const float val = fo[q] + 6.f * wq(q) * cu;
-                    if ((liqm >> q) & 1u) injected += 6.f * wq(q) * cu;
+                    // c_q.u_s with the signs of c_q
+                    float cu = 0.f;
+                    if (cx(q)) cu = cx(q) > 0 ? cu + usx : cu - usx;
+                    if (cy(q)) cu = cy(q) > 0 ? cu + usy : cu - usy;
+                    if (cz(q)) cu = cz(q) > 0 ? cu + usz : cu - usz;
+                    const float corr = (6.f * wq(q)) * cu;
+                    const float val = fo[q] + corr;
+                    if ((liqm >> q) & 1u) injected += corr;
                     const long long dst = PAR == 0 ? (long long)q * n + xn : (long long)opp(q) * n + cell;
                     Store<S>::st(f + dst, Store<S>::HREF ? val - wq(q) * (PAR == 0 ? hn : hz) : val);
-                    const float sum = fo[q] + val, dif = fo[q] - val;
-                    const float Fx = -cx(q) * sum - ubx * dif;
-                    const float Fy = -cy(q) * sum - uby * dif;
-                    const float Fz = -cz(q) * sum - ubz * dif;
-                    F[0] += Fx; F[1] += Fy; F[2] += Fz;
-                    T[0] += dy * Fz - dz * Fy;
-                    T[1] += dz * Fx - dx * Fz;
-                    T[2] += dx * Fy - dy * Fx;
+                    const float t = fmaf(2.f, fo[q], corr);
+                    if (cx(q)) { Ax = cx(q) > 0 ? Ax + t : Ax - t; Cx = cx(q) > 0 ? Cx + corr : Cx - corr; Mxx += corr; }
+                    if (cy(q)) { Ay = cy(q) > 0 ? Ay + t : Ay - t; Cy = cy(q) > 0 ? Cy + corr : Cy - corr; Myy += corr; }
+                    if (cz(q)) { Az = cz(q) > 0 ? Az + t : Az - t; Cz = cz(q) > 0 ? Cz + corr : Cz - corr; Mzz += corr; }
+                    if (cx(q) && cy(q)) Mxy = cx(q) * cy(q) > 0 ? Mxy + corr : Mxy - corr;
+                    if (cx(q) && cz(q)) Mxz = cx(q) * cz(q) > 0 ? Mxz + corr : Mxz - corr;
+                    if (cy(q) && cz(q)) Myz = cy(q) * cz(q) > 0 ? Myz + corr : Myz - corr;
+                    B += corr;
+                    D += (float)nnz(q) * corr;
                 }
+                const float hx = 0.5f * (P.w.y * Cz - P.w.z * Cy);
+                const float hy = 0.5f * (P.w.z * Cx - P.w.x * Cz);
+                const float hzz = 0.5f * (P.w.x * Cy - P.w.y * Cx);
+                F[0] = fmaf(usx, B, hx) - Ax;
+                F[1] = fmaf(usy, B, hy) - Ay;
+                F[2] = fmaf(usz, B, hzz) - Az;
+                // M W
+                const float mwx = Mxx * P.w.x + Mxy * P.w.y + Mxz * P.w.z;
+                const float mwy = Mxy * P.w.x + Myy * P.w.y + Myz * P.w.z;
+                const float mwz = Mxz * P.w.x + Myz * P.w.y + Mzz * P.w.z;
+                const float gx = (Cy * usz - Cz * usy) + 0.5f * (P.w.x * D - mwx);
+                const float gy = (Cz * usx - Cx * usz) + 0.5f * (P.w.y * D - mwy);
+                const float gz = (Cx * usy - Cy * usx) + 0.5f * (P.w.z * D - mwz);
+                T[0] = (ddy * F[2] - ddz * F[1]) + 0.5f * gx;
+                T[1] = (ddz * F[0] - ddx * F[2]) + 0.5f * gy;
+                T[2] = (ddx * F[1] - ddy * F[0]) + 0.5f * gz;
             }
         }
         flush_mem(s, key, F, T);
