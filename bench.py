@@ -206,11 +206,52 @@ def _sweep_traffic(storage_name: str, fluid: float):
                               f"scaled by fluid cells")
 
 
+def log_flume_stencils(stream, steps: int = 300, every: int = 50):
+    """Interface stencils logged from a run of the mid flume (512x40x96, its
+    particle bed, FP32, finite-difference normal) whose free surface starts
+    with a seeded perturbation (amplitude 3 cells, x-wavelength 128, a
+    y-modulation), labelled by the library's height function: every `every`
+    steps, the snapshots alternating between training and held-out sets."""
+    import torch
+
+    from paper_2301_10674_gb300 import fslbm as F
+    from paper_2301_10674_gb300 import workloads as W
+
+    w = W.mid().generate()
+    sim = F.Simulation.from_workload(w, storage=F.STORE_FP32, stream=stream)
+    x = np.arange(w.nx) + 0.5
+    y = np.arange(w.ny) + 0.5
+    h = (w.liquid_height + 3.0 * np.sin(2 * np.pi * x / 128.0)[None, :] *
+         (1.0 + 0.3 * np.cos(2 * np.pi * y / w.ny))[:, None])
+    sim.init_surface(h)
+    parts = ([], [])
+    k = 0
+    while k < steps:
+        sim.step(every)
+        k += every
+        fill, target, fd, _ = sim.log_stencils()
+        parts[(k // every) % 2].append((fill, target, fd))
+    sim.close()
+    cat = lambda ps, i: torch.cat([p[i] for p in ps]) if ps else None  # noqa: E731
+    train = (cat(parts[0], 0), cat(parts[0], 1))
+    held = (cat(parts[1], 0), cat(parts[1], 1), cat(parts[1], 2))
+    return w.name, train, held
+
+
+def _angles(a, b):
+    a = a / np.linalg.norm(a, axis=1, keepdims=True)
+    b = b / np.linalg.norm(b, axis=1, keepdims=True)
+    return np.degrees(np.arccos(np.clip(np.sum(a * b, axis=1), -1.0, 1.0)))
+
+
 def train_normal_model(stream, n_stencils: int, steps: int, seed: int = 4) -> tuple[np.ndarray, dict]:
     """Learned normal trained by the library's own kernels (not timed):
-    voxelised analytic surfaces (planes, droplets, bubbles, sine waves), Adam
-    on batches of 4096 with cube-symmetry augmentation, step size decaying
-    geometrically from 2e-3 to 1e-5."""
+    voxelised analytic surfaces (planes, droplets, bubbles, sine waves) and
+    the stencils logged from a mid-flume run with their height-function
+    labels, Adam on batches of 4096 with cube-symmetry augmentation, step
+    size decaying geometrically from 2e-3 to 1e-5. The held-out logged
+    stencils measure the network against the finite-difference normal on the
+    method's own surfaces."""
     import torch
 
     from paper_2301_10674_gb300 import fslbm as F
@@ -222,6 +263,11 @@ def train_normal_model(stream, n_stencils: int, steps: int, seed: int = 4) -> tu
     tgt = torch.empty((n_stencils, 4), dtype=torch.float32, device="cuda")
     F._check(F.fslbm_mlp_stencils(params, n_stencils, fill, tgt, stream.cuda_stream), "fslbm_mlp_stencils")
     del params
+    log_name, (lf, lt), (hf, ht, hfd) = log_flume_stencils(stream)
+    n_logged = len(lf)
+    fill = torch.cat([fill, lf])
+    tgt = torch.cat([tgt, lt])
+    n_stencils = len(fill)
     t1 = time.perf_counter()
     theta = torch.from_numpy(W.mlp_initial_weights(seed)).cuda()
     curve = torch.empty(steps, dtype=torch.float32, device="cuda")
@@ -229,6 +275,26 @@ def train_normal_model(stream, n_stencils: int, steps: int, seed: int = 4) -> tu
                                stream.cuda_stream, lr_end=1e-5), "fslbm_mlp_train")
     t2 = time.perf_counter()
     c = curve.cpu().numpy()
+    # the held-out logged stencils: the network with the step's fallback
+    # rules (raw length in [1/2, 2], within 30 degrees of the
+    # finite-difference normal) and the finite-difference normal, both
+    # against the height-function labels
+    out = torch.empty((len(hf), 4), dtype=torch.float32, device="cuda")
+    F._check(F.fslbm_mlp_infer(theta, hf, len(hf), out, stream.cuda_stream), "fslbm_mlp_infer")
+    yv = out.cpu().numpy().astype(np.float64)
+    lab = ht.cpu().numpy().astype(np.float64)
+    fdn = hfd.cpu().numpy().astype(np.float64)[:, :3]
+    L = np.linalg.norm(yv[:, :3], axis=1)
+    nml = yv[:, :3] / np.maximum(L, 1e-30)[:, None]
+    use = (L >= 0.5) & (L <= 2.0) & (np.sum(nml * fdn, axis=1) >= np.cos(np.radians(30.0)))
+    e_fd = _angles(fdn, lab[:, :3])
+    e_ml = _angles(np.where(use[:, None], nml, fdn), lab[:, :3])
+    logged = {"workload": log_name, "train": n_logged, "held_out": int(len(hf)),
+              "label": "height function (3x3 columns of 7 cells)",
+              "fd_deg": round(float(e_fd.mean()), 4), "learned_deg": round(float(e_ml.mean()), 4),
+              "taken": round(float(use.mean()), 4),
+              "kappa_mae": round(float(np.abs(np.where(use, yv[:, 3], 0.0) - lab[:, 3]).mean()), 6),
+              "kappa_label_mean_abs": round(float(np.abs(lab[:, 3]).mean()), 6)}
     # FLOPs of one sample and step of the 27-64-64-4 network: forward 2 x 6080
     # multiply-adds; backward the weight gradients of every layer and the
     # activation gradients of the two upper ones
@@ -236,7 +302,8 @@ def train_normal_model(stream, n_stencils: int, steps: int, seed: int = 4) -> tu
     flops = 2 * (3 * macs - 27 * 64)
     tflops = flops * 4096 * steps / max(t2 - t1, 1e-9) / 1e12
     peak, kind = _bf16_peak()
-    return theta.cpu().numpy(), {"stencils": n_stencils, "steps": steps, "batch": 4096, "lr": [2e-3, 1e-5],
+    return theta.cpu().numpy(), {"stencils": n_stencils, "logged_stencils": logged, "steps": steps,
+                                 "batch": 4096, "lr": [2e-3, 1e-5],
                                  "loss_first": float(c[0]), "loss_last100": float(c[-100:].mean()),
                                  "data_s": round(t1 - t0, 2), "train_s": round(t2 - t1, 2),
                                  "roofline": {"bound": "latency", "flops_per_sample": flops,

@@ -407,6 +407,32 @@ int fslbm_set_normal_model(fslbm* s, const uint16_t* w, int64_t n_params);
  * fell back). Zeros under the finite-difference normal. Synchronises. */
 int fslbm_normal_stats(fslbm* s, uint64_t out[2]);
 
+/* Interface stencils of the current state, labelled by the height-function
+ * method: training and test data of the learned normal taken from the
+ * method's own runs (the survey's logged stencils; the paper has no learned
+ * normal). For every interface cell whose 3x3x3 block holds no wall or
+ * solid cell: the network's input (fill levels of the block, liquid 1,
+ * interface phi clamped to [0, 1], gas 0, stencil index
+ * (dx+1) + 3(dy+1) + 9(dz+1)) and, where the height function is defined, a
+ * label. The height function takes the axis a of the largest component of
+ * the Parker-Youngs normal, sums the fill levels of the 3x3 columns of seven
+ * cells along a centred on the cell's row (a column counts only if its end
+ * cell on the liquid side is liquid and on the gas side gas), and forms the
+ * normal toward the gas and the mean curvature (positive for a convex liquid
+ * body) from the central differences of the heights.
+ *   capacity  stencils the buffers hold; the first `capacity` found are
+ *             written, in no fixed order
+ *   fill      device float [capacity][27] out
+ *   target    device float [capacity][4] out: label (n_x, n_y, n_z, kappa)
+ *   fd        optional (NULL) device float [capacity][4] out: the
+ *             Parker-Youngs normal of the same block, 0
+ *   cells     optional (NULL) device int32 [capacity] out: cell index
+ *   found     host out: the number of labelled stencils (may exceed capacity)
+ * Stream-ordered; synchronises the stream. FSLBM_EINVAL for a NULL handle or
+ * found, capacity < 0, or capacity > 0 with fill or target NULL. */
+int fslbm_log_stencils(fslbm* s, int64_t capacity, float* fill, float* target, float* fd, int32_t* cells,
+                       int64_t* found);
+
 /* Training data of the learned normal. params: device, n rows of 12 doubles
  * describing analytic surfaces through P = s n0 (kind 0 plane, 1 liquid
  * sphere of radius r centred at P - r n0, 2 gas sphere centred at P + r n0,

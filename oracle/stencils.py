@@ -211,3 +211,108 @@ def draw(seed: int, step: int, batch: int, n: int, augment: bool = True):
         idx[j] = v % n
         sym[j] = (v >> 32) % 48 if augment else 0
     return idx, sym
+
+
+# ---------------------------------------------------------------- height function
+# Labels of interface stencils taken from a run's own state (the logged
+# stencils of the learned normal). The height-function method: along the
+# axis a of the largest component of the Parker-Youngs normal (gas toward the
+# sign sg of that component), the fill levels of the 3 x 3 columns of seven
+# cells centred on the cell's row, summed, give the surface's height above
+# each column's centre plane, eta = sum - 7/2, measured toward the gas; the
+# normal toward the gas and the mean curvature follow from the central
+# differences of eta (the surface is t = eta(u, v), liquid below).
+LIQ, IFC, GAS, SOL, WALL = 1, 2, 0, 3, -1
+
+
+def block7(phi, types, cell, periodic):
+    """Fill levels (raw phi for interface cells, liquid 1, gas 0) and types
+    of the 7 x 7 x 7 block around `cell` of (nz, ny, nx) fields, indexed
+    [dz + 3, dy + 3, dx + 3]; cells beyond a wall face get type WALL."""
+    nz, ny, nx = types.shape
+    z, rem = divmod(int(cell), nx * ny)
+    y, x = divmod(rem, nx)
+    f = np.zeros((7, 7, 7))
+    t = np.full((7, 7, 7), WALL, dtype=np.int64)
+    for k in range(7):
+        for j in range(7):
+            for i in range(7):
+                c = [x + i - 3, y + j - 3, z + k - 3]
+                ok = True
+                for a, L in enumerate((nx, ny, nz)):
+                    if c[a] < 0 or c[a] >= L:
+                        if periodic[a]:
+                            c[a] %= L
+                        else:
+                            ok = False
+                if ok:
+                    ty = int(types[c[2], c[1], c[0]])
+                    t[k, j, i] = ty
+                    f[k, j, i] = 1.0 if ty == LIQ else (float(phi[c[2], c[1], c[0]]) if ty == IFC else 0.0)
+    return f, t
+
+
+def parker_youngs32(f27):
+    """The Parker-Youngs gradient of a 27-stencil of raw fill levels in FP32,
+    summed in stencil order (the precision and order in which the logging
+    kernel forms it; every product is exact, weight and offset being small
+    powers of two), and the normal -g/|g|; None for a zero gradient."""
+    g = np.zeros(3, dtype=np.float32)
+    for q in range(27):
+        if q == 13:
+            continue
+        c = CELLS[q]
+        w = np.float32({1: 4.0, 2: 2.0, 3: 1.0}[int(np.abs(c).sum())])
+        for a in range(3):
+            g[a] = np.float32(g[a] + np.float32(w * np.float32(c[a])) * np.float32(f27[q]))
+    L = math.sqrt(float(g[0]) ** 2 + float(g[1]) ** 2 + float(g[2]) ** 2)
+    if not L > 0:
+        return None
+    return g, -g.astype(np.float64) / L
+
+
+def height_function_label(f7, t7):
+    """(input27, label4, fd3) of the centre cell of a 7 x 7 x 7 block, or
+    None where the stencil is not logged (a wall or solid cell in the 3x3x3
+    block, or a column without a liquid end on the liquid side and a gas end
+    on the gas side). input27: fill levels clamped to [0, 1]; label4: normal
+    toward the gas and mean curvature (positive for a convex liquid body),
+    FP64; fd3: the Parker-Youngs normal."""
+    inner_t = t7[2:5, 2:5, 2:5]
+    if np.any((inner_t == WALL) | (inner_t == SOL)):
+        return None
+    f27 = np.array([f7[c[2] + 3, c[1] + 3, c[0] + 3] for c in CELLS])
+    py = parker_youngs32(f27)
+    if py is None:
+        return None
+    g, n = py
+    ag = np.abs(g)
+    a = 0 if (ag[0] >= ag[1] and ag[0] >= ag[2]) else (1 if ag[1] >= ag[2] else 2)
+    u, v = [b for b in range(3) if b != a]
+    sg = 1 if g[a] < 0 else -1
+    eta = np.zeros((3, 3))
+    for iu in (-1, 0, 1):
+        for iv in (-1, 0, 1):
+            total = 0.0
+            for tt in range(-3, 4):
+                d = [0, 0, 0]
+                d[u], d[v], d[a] = iu, iv, sg * tt
+                ty = t7[d[2] + 3, d[1] + 3, d[0] + 3]
+                if ty in (WALL, SOL):
+                    return None
+                if (tt == -3 and ty != LIQ) or (tt == 3 and ty != GAS):
+                    return None
+                total += min(max(f7[d[2] + 3, d[1] + 3, d[0] + 3], 0.0), 1.0)
+            eta[iu + 1, iv + 1] = total - 3.5
+    eu = 0.5 * (eta[2, 1] - eta[0, 1])
+    ev = 0.5 * (eta[1, 2] - eta[1, 0])
+    euu = eta[2, 1] - 2.0 * eta[1, 1] + eta[0, 1]
+    evv = eta[1, 2] - 2.0 * eta[1, 1] + eta[1, 0]
+    euv = 0.25 * (eta[2, 2] - eta[2, 0] - eta[0, 2] + eta[0, 0])
+    g2 = 1.0 + eu * eu + ev * ev
+    m = np.zeros(3)
+    m[a] = sg / math.sqrt(g2)
+    m[u] = -eu / math.sqrt(g2)
+    m[v] = -ev / math.sqrt(g2)
+    kappa = -(euu * (1.0 + ev * ev) + evv * (1.0 + eu * eu) - 2.0 * eu * ev * euv) / (2.0 * g2 ** 1.5)
+    return np.clip(f27, 0.0, 1.0), np.array([m[0], m[1], m[2], kappa]), n

@@ -994,6 +994,23 @@ int fslbm_normal_stats(fslbm* s, uint64_t out[2]) {
     return rc;
 }
 
+int fslbm_log_stencils(fslbm* s, int64_t capacity, float* fill, float* target, float* fd, int32_t* cells,
+                       int64_t* found) {
+    if (!s || !found || capacity < 0 || (capacity > 0 && (!fill || !target))) return FSLBM_EINVAL;
+    *found = 0;
+    if (s->host_err) return s->host_err;
+    // the counter lives in the reduction's output block (8 doubles), whose
+    // values no caller reads across this call
+    unsigned long long* dfound = reinterpret_cast<unsigned long long*>(s->red);
+    launch_log_stencils(s->d, capacity, fill, target, fd, cells, dfound, s->st);
+    unsigned long long h = 0;
+    cudaMemcpyAsync(&h, dfound, sizeof(h), cudaMemcpyDeviceToHost, s->st);
+    const int rc = sync_check(s);
+    if (rc) return rc;
+    *found = (int64_t)h;
+    return launch_check(s);
+}
+
 void fslbm_destroy(fslbm* s) {
     if (!s) return;
     cudaStreamSynchronize(s->st);

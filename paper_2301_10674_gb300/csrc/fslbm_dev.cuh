@@ -563,6 +563,8 @@ int launch_stream_collide(const Dev& s, int parity, cudaStream_t st);
 int launch_classify(const Dev& s, cudaStream_t st);
 void launch_check_invariant(const Dev& s, cudaStream_t st);
 int launch_normals(const Dev& s, float4* out, cudaStream_t st);
+void launch_log_stencils(const Dev& s, long long cap, float* fill, float* target, float* fd, int* cells,
+                         unsigned long long* found, cudaStream_t st);
 int launch_conversion(const Dev& s, int last_parity, cudaStream_t st);
 int launch_pool_spread(const Dev& s, cudaStream_t st);
 void launch_cell_counts(const Dev& s, unsigned long long* out, cudaStream_t st);

@@ -414,6 +414,140 @@ __global__ void k_clear_conv(Dev s) {
     FOR_LIST(i, s.wl_count) s.conv[s.wl[i]] = 0;
 }
 
+// Interface stencils of the current state with height-function labels (R-17e):
+// a thread per interface cell. The input is the learned normal's: the fill
+// levels of the 3x3x3 block (liquid 1, interface phi clamped to [0, 1], gas
+// 0), stencil index (dx+1) + 3(dy+1) + 9(dz+1); a block with a wall or solid
+// cell is not logged. The label follows the height-function method: along
+// the axis a where the Parker-Youngs normal is largest (gas toward sign
+// sg), the fill levels of the 3x3 columns of 7 cells centred on the cell's
+// row sum to the heights eta(i, j) = sum - 7/2 of the surface above the
+// column's centre plane, measured toward the gas; a column counts only if
+// its liquid end cell is liquid and its gas end cell gas. With eta_u, eta_v
+// the central differences and eta_uu, eta_vv, eta_uv the second ones, the
+// normal toward the gas is (sg e_a - eta_u e_u - eta_v e_v) / |.| and the
+// mean curvature, positive for a convex liquid body,
+//   kappa = -(eta_uu (1 + eta_v^2) + eta_vv (1 + eta_u^2) - 2 eta_u eta_v eta_uv)
+//           / (2 (1 + eta_u^2 + eta_v^2)^(3/2)).
+// Written per logged cell: fill[27], target = (n, kappa), fd = (Parker-Youngs
+// normal, 0) and the cell index, at slots taken in no fixed order; `found`
+// counts every valid cell, the first `cap` of them are written.
+// fill level (clamped, and raw in `raw`) and type of a neighbour; false
+// beyond a wall face or at a solid cell
+__device__ __forceinline__ bool fill_at(const Dev& s, int x, int y, int z, int dx, int dy, int dz, float& v, int& t,
+                                        float& raw) {
+    const long long nb = nbr(s, x, y, z, dx, dy, dz);
+    if (nb < 0) return false;
+    t = s.flags[nb] & TYPE_MASK;
+    if (t == T_SOL) return false;
+    raw = t == T_LIQ ? 1.f : (t == T_IFC ? s.phi[nb] : 0.f);
+    v = fminf(fmaxf(raw, 0.f), 1.f);
+    return true;
+}
+
+__global__ void k_log_stencils(Dev s, long long cap, float* fill, float4* target, float4* fd, int* cells,
+                               unsigned long long* found) {
+    const int count = min(*s.wl_count, s.wl_cap);
+    const int stride = gridDim.x * blockDim.x;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    for (int base = blockIdx.x * blockDim.x; base < count; base += stride) {
+        const int i = base + threadIdx.x;
+        bool ok = false;
+        float in[27];
+        float4 lab = make_float4(0.f, 0.f, 0.f, 0.f), pyn = lab;
+        int c = -1;
+        if (i < count) {
+            c = s.wl[i];
+            int x, y, z;
+            coords(s, c, x, y, z);
+            ok = true;
+            float gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+            for (int q = 0; q < 27; ++q) {
+                float v = 0.f, raw = 0.f;
+                int t = 0;
+                if (!fill_at(s, x, y, z, cx(q), cy(q), cz(q), v, t, raw)) ok = false;
+                in[q] = v;
+                // the Parker-Youngs gradient of the raw fill levels
+                if (q != 13) {
+                    const float w = nnz(q) == 1 ? 4.f : (nnz(q) == 2 ? 2.f : 1.f);
+                    gx += w * cx(q) * raw;
+                    gy += w * cy(q) * raw;
+                    gz += w * cz(q) * raw;
+                }
+            }
+            const float gl = sqrtf(gx * gx + gy * gy + gz * gz);
+            if (!(gl > 0.f)) ok = false;
+            if (ok) {
+                pyn = make_float4(-gx / gl, -gy / gl, -gz / gl, 0.f);
+                // the dominant axis from the gradient itself (ties: the lower axis)
+                const float g[3] = {gx, gy, gz};
+                const int a = (fabsf(gx) >= fabsf(gy) && fabsf(gx) >= fabsf(gz)) ? 0 : (fabsf(gy) >= fabsf(gz) ? 1 : 2);
+                const int u = a == 0 ? 1 : 0, v = a == 2 ? 1 : 2;
+                const int sg = g[a] < 0.f ? 1 : -1;   // the normal -grad points to the gas
+                float eta[3][3];
+                for (int iu = -1; iu <= 1 && ok; ++iu)
+                    for (int iv = -1; iv <= 1 && ok; ++iv) {
+                        float sum = 0.f;
+                        for (int t = -3; t <= 3 && ok; ++t) {
+                            int d[3] = {0, 0, 0};
+                            d[u] = iu;
+                            d[v] = iv;
+                            d[a] = sg * t;
+                            float f = 0.f, fr = 0.f;
+                            int ty = 0;
+                            if (!fill_at(s, x, y, z, d[0], d[1], d[2], f, ty, fr)) ok = false;
+                            else if ((t == -3 && ty != T_LIQ) || (t == 3 && ty != T_GAS)) ok = false;
+                            sum += f;
+                        }
+                        eta[iu + 1][iv + 1] = sum - 3.5f;
+                    }
+                if (ok) {
+                    const float eu = 0.5f * (eta[2][1] - eta[0][1]), ev = 0.5f * (eta[1][2] - eta[1][0]);
+                    const float euu = eta[2][1] - 2.f * eta[1][1] + eta[0][1];
+                    const float evv = eta[1][2] - 2.f * eta[1][1] + eta[1][0];
+                    const float euv = 0.25f * (eta[2][2] - eta[2][0] - eta[0][2] + eta[0][0]);
+                    const float g2 = 1.f + eu * eu + ev * ev;
+                    const float inv = rsqrtf(g2);
+                    float m[3];
+                    m[a] = sg * inv;
+                    m[u] = -eu * inv;
+                    m[v] = -ev * inv;
+                    const float kap = -(euu * (1.f + ev * ev) + evv * (1.f + eu * eu) - 2.f * eu * ev * euv) /
+                                      (2.f * g2 * sqrtf(g2));
+                    lab = make_float4(m[0], m[1], m[2], kap);
+                }
+            }
+        }
+        // warp-aggregated slots
+        const unsigned bal = __ballot_sync(full, ok);
+        unsigned long long slot0 = 0;
+        if (bal) {
+            const int leader = __ffs(bal) - 1;
+            if (lane == leader) slot0 = atomicAdd(found, (unsigned long long)__popc(bal));
+            slot0 = __shfl_sync(full, slot0, leader);
+        }
+        if (ok) {
+            const unsigned long long k = slot0 + __popc(bal & ((1u << lane) - 1u));
+            if ((long long)k < cap) {
+#pragma unroll
+                for (int q = 0; q < 27; ++q) fill[k * 27 + q] = in[q];
+                target[k] = lab;
+                if (fd) fd[k] = pyn;
+                if (cells) cells[k] = c;
+            }
+        }
+    }
+}
+
+void launch_log_stencils(const Dev& s, long long cap, float* fill, float* target, float* fd, int* cells,
+                         unsigned long long* found, cudaStream_t st) {
+    cudaMemsetAsync(found, 0, sizeof(unsigned long long), st);
+    k_log_stencils<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(s, cap, fill, reinterpret_cast<float4*>(target),
+                                                          reinterpret_cast<float4*>(fd), cells, found);
+}
+
 int launch_normals(const Dev& s, float4* out, cudaStream_t st) { return normals_into(s, out, st); }
 
 int launch_conversion(const Dev& s, int last_parity, cudaStream_t st) {

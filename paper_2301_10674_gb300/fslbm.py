@@ -50,7 +50,7 @@ EXPORTED = (
     "fslbm_set_normal_model", "fslbm_normal_stats", "fslbm_mlp_stencils", "fslbm_mlp_gradient",
     "fslbm_mlp_train", "fslbm_mlp_infer", "fslbm_bed_height", "fslbm_set_body_force",
     "fslbm_get_body_force", "fslbm_set_flow_control", "fslbm_set_wait_limit", "fslbm_transport_numbers",
-    "fslbm_bed_spectrum",
+    "fslbm_bed_spectrum", "fslbm_log_stencils",
 )
 
 MLP_NPARAM = 6212
@@ -143,6 +143,7 @@ def load():
                                   ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_uint64, ctypes.c_int,
                                   vp, vp]
     L.fslbm_mlp_infer.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
+    L.fslbm_log_stencils.argtypes = [vp, ctypes.c_int64, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int64)]
     L.fslbm_destroy.argtypes = [vp]
     L.fslbm_destroy.restype = None
     L.fslbm_strerror.argtypes = [ctypes.c_int]
@@ -459,6 +460,28 @@ class Simulation:
         _check(load().fslbm_bed_height(self.h, float(level), h.ctypes.data,
                                        phi.ctypes.data if phi is not None else None, 0), "fslbm_bed_height")
         return (h, phi) if with_fraction else h
+
+    def log_stencils(self, capacity: int | None = None):
+        """Interface stencils of the current state with height-function labels
+        (see fslbm_log_stencils): device tensors fill (n, 27), target (n, 4),
+        fd (n, 4) and cells (n,) int32, n the number found (all of them when
+        capacity is None)."""
+        import torch
+        found = ctypes.c_int64()
+        if capacity is None:
+            _check(load().fslbm_log_stencils(self.h, 0, None, None, None, None, ctypes.byref(found)),
+                   "fslbm_log_stencils")
+            capacity = int(found.value)
+        cap = max(int(capacity), 1)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        fill = torch.empty((cap, 27), dtype=torch.float32, device=dev)
+        target = torch.empty((cap, 4), dtype=torch.float32, device=dev)
+        fd = torch.empty((cap, 4), dtype=torch.float32, device=dev)
+        cells = torch.empty(cap, dtype=torch.int32, device=dev)
+        _check(load().fslbm_log_stencils(self.h, cap, _ptr(fill), _ptr(target), _ptr(fd), _ptr(cells),
+                                         ctypes.byref(found)), "fslbm_log_stencils")
+        n = min(int(found.value), cap)
+        return fill[:n], target[:n], fd[:n], cells[:n]
 
     def set_wait_limit(self, polls: int) -> None:
         """Polls before a bounded device wait gives up (test hook of the

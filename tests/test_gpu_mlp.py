@@ -364,3 +364,94 @@ def test_laplace_pressure_on_the_gpu():
     o.step(3000)
     to = o.get(O.F_TYPE)
     assert abs(out[sigma] - float(o.get(O.F_RHO)[to == O.LIQUID].mean())) < 1e-6
+
+
+# ---------------------------------------------------------------- logged stencils
+def _wavy_flume():
+    """The tiny flume (with its particle bed) under a wavy free surface,
+    stepped a little so that the fill levels are the method's own."""
+    w = W.tiny().generate()
+    sim = F.Simulation.from_workload(w)
+    x = np.arange(w.nx) + 0.5
+    y = np.arange(w.ny) + 0.5
+    h = 23.0 + 2.5 * np.sin(2 * np.pi * x / 32 + 0.3)[None, :] + 1.2 * np.cos(2 * np.pi * y / 16)[:, None]
+    sim.init_surface(h)
+    sim.step(12)
+    return w, sim
+
+
+def test_logged_stencils_match_the_oracle_height_function():
+    """fslbm_log_stencils on a wavy flume state against the oracle's height
+    function applied to the same exported fill levels and types: the same
+    cells logged, the input fill levels exact, labels within FP32 rounding
+    (normal 1e-5, curvature 1e-4), the Parker-Youngs normal within 1e-6."""
+    w, sim = _wavy_flume()
+    fill, target, fd, cells = sim.log_stencils()
+    fill, target, fd, cells = (a.cpu().numpy() for a in (fill, target, fd, cells))
+    types = sim.get(F.FIELD_TYPE).reshape(w.nz, w.ny, w.nx)
+    phi = sim.get(F.FIELD_PHI).reshape(w.nz, w.ny, w.nx)
+    ifc = np.nonzero(types.ravel() == OS.IFC)[0]
+    want = {}
+    for c in ifc:
+        out = OS.height_function_label(*OS.block7(phi, types, c, w.periodic))
+        if out is not None:
+            want[int(c)] = out
+    assert len(want) > 300, len(want)
+    assert sorted(cells.tolist()) == sorted(want), (len(cells), len(want))
+    for k, c in enumerate(cells.tolist()):
+        f27, lab, n_fd = want[c]
+        assert np.array_equal(fill[k], f27.astype(np.float32)), c
+        assert np.abs(target[k, :3] - lab[:3]).max() < 1e-5, (c, target[k], lab)
+        assert abs(target[k, 3] - lab[3]) < 1e-4, (c, target[k], lab)
+        assert np.abs(fd[k, :3] - n_fd).max() < 1e-6, (c, fd[k], n_fd)
+    # labels are unit normals toward the gas: the gas side of a rising
+    # surface is up
+    assert (np.abs(np.linalg.norm(target[:, :3], axis=1) - 1.0) < 1e-5).all()
+    assert (target[:, 2] > 0).mean() > 0.95
+    sim.close()
+
+
+def test_logged_stencils_train_the_network():
+    """Stencils logged from the method's own run (a wavy free surface in a
+    128x32x48 box, every 20 steps; even snapshots for training, odd ones held
+    out) join 2^19 analytic surfaces in the training set. On the held-out
+    stencils the trained network, with the step's fallback rules, is closer
+    to the height-function labels than the finite-difference normal."""
+    import torch
+    w = W.Workload(name="waves", nx=128, ny=32, nz=48, periodic=(1, 1, 0), tau=0.55, g=(0.0, 0.0, -1e-4),
+                   liquid_height=30.0, bed="none", seed=21).generate()
+    sim = F.Simulation.from_workload(w, spheres=False)
+    x = np.arange(w.nx) + 0.5
+    y = np.arange(w.ny) + 0.5
+    h = 30.0 + 3.0 * np.sin(2 * np.pi * x / 64)[None, :] * np.cos(2 * np.pi * y / 32)[:, None]
+    sim.init_surface(h)
+    parts = ([], [])
+    for k in range(10):
+        sim.step(20)
+        parts[k % 2].append(sim.log_stencils())
+    sim.close()
+    lf = torch.cat([p[0] for p in parts[0]])
+    lt = torch.cat([p[1] for p in parts[0]])
+    hf, ht, hfd = (torch.cat([p[i] for p in parts[1]]) for i in range(3))
+    assert len(lf) > 5000 and len(hf) > 5000, (len(lf), len(hf))
+    fill, tgt = _gpu_stencils(W.surface_stencils(1 << 19, seed=5))
+    fill = torch.cat([fill, lf])
+    tgt = torch.cat([tgt, lt])
+    theta = _dev(W.mlp_initial_weights(12))
+    steps = 12000
+    curve = _zeros(steps, torch.float32)
+    _ok(F.fslbm_mlp_train(theta, fill, tgt, len(fill), steps, 4096, 2e-3, LAM, MU, 19, True, curve,
+                          lr_end=1e-5), "fslbm_mlp_train")
+    out = _zeros((len(hf), 4), torch.float32)
+    _ok(F.fslbm_mlp_infer(theta, hf, len(hf), out), "fslbm_mlp_infer")
+    y = out.cpu().numpy().astype(np.float64)
+    lab = ht.cpu().numpy().astype(np.float64)
+    fd = hfd.cpu().numpy().astype(np.float64)[:, :3]
+    L = np.linalg.norm(y[:, :3], axis=1)
+    n_ml = y[:, :3] / L[:, None]
+    use = (L >= 0.5) & (L <= 2.0) & (np.sum(n_ml * fd, axis=1) >= math.cos(math.radians(30)))
+    e_fd = _angle(fd, lab[:, :3]).mean()
+    e_ml = _angle(np.where(use[:, None], n_ml, fd), lab[:, :3]).mean()
+    print(f"held-out logged stencils: {len(hf)}, FD {e_fd:.3f} deg, learned {e_ml:.3f} deg, taken {use.mean():.3f}")
+    assert use.mean() > 0.9
+    assert e_ml < e_fd, (e_ml, e_fd)

@@ -203,3 +203,109 @@ def test_draw_covers_indices_and_symmetries():
     assert sym.min() >= 0 and sym.max() == 47
     idx2, sym2 = S.draw(11, 3, 4096, 1000, augment=False)
     assert np.array_equal(idx, idx2) and not sym2.any()
+
+
+# ---------------------------------------------------------------- height function
+def _block(fillfun):
+    """7 x 7 x 7 block of fill levels fillfun(c) and their types."""
+    f = np.zeros((7, 7, 7))
+    for k in range(7):
+        for j in range(7):
+            for i in range(7):
+                f[k, j, i] = fillfun((i - 3, j - 3, k - 3))
+    t = np.where(f >= 1.0, S.LIQ, np.where(f <= 0.0, S.GAS, S.IFC))
+    return f, t
+
+
+@pytest.mark.parametrize("n0,s", [((0.1, -0.2, 1.0), 0.2), ((-1.0, 0.3, 0.25), -0.1), ((0.4, 1.0, -0.35), 0.4),
+                                  ((0.0, 0.0, -1.0), 0.0)])
+def test_height_function_is_exact_on_planes(n0, s):
+    """A column's fill levels integrate the plane's height over its cross
+    section, whose mean is the height at the column's centre: the heights are
+    exact, so the normal is n0 and the curvature 0 to rounding."""
+    n0 = np.asarray(n0) / np.linalg.norm(n0)
+    P = s * n0
+    f, t = _block(lambda c: S.plane_fill(n0, P, c))
+    out = S.height_function_label(f, t)
+    assert out is not None
+    fill27, lab, fd = out
+    assert np.allclose(lab[:3], n0, atol=1e-12, rtol=0), (lab, n0)
+    assert abs(lab[3]) < 1e-12
+    # the input is the 3x3x3 block of clamped fill levels, stencil order
+    for q in range(27):
+        c = S.CELLS[q]
+        assert fill27[q] == f[c[2] + 3, c[1] + 3, c[0] + 3]
+    assert np.dot(fd, n0) > 0.99
+
+
+def _sphere_fill_fine(C, r, c, inside, sub=512):
+    """Fraction of cell c inside (or outside) the sphere from the exact
+    x-chords of sub x sub rows (finer than the training data's 64 x 64, so
+    that the reference fills resolve a large sphere's curvature)."""
+    t = (np.arange(sub) + 0.5) / sub - 0.5
+    Y, Z = np.meshgrid(t, t, indexing="ij")
+    dy = c[1] + Y.ravel() - C[1]
+    dz = c[2] + Z.ravel() - C[2]
+    h2 = r * r - dy * dy - dz * dz
+    h = np.sqrt(np.maximum(h2, 0.0))
+    lo = np.maximum(C[0] - h, c[0] - 0.5)
+    hi = np.minimum(C[0] + h, c[0] + 0.5)
+    frac = float(np.where(h2 > 0.0, np.maximum(hi - lo, 0.0), 0.0).sum()) / (sub * sub)
+    return frac if inside else 1.0 - frac
+
+
+@pytest.mark.parametrize("R,inside,tol", [(8.0, True, 0.015), (16.0, True, 0.005), (12.0, False, 0.01)])
+def test_height_function_on_spheres(R, inside, tol):
+    """A droplet (liquid inside) and a bubble (liquid outside) of radius R
+    above or below the cell: the mean curvature is +1/R and -1/R within the
+    method's second-order error (0.7% at R = 8, 0.2% at R = 16), the normal
+    within half a degree of the sphere's normal at the surface point above
+    the cell centre."""
+    off = np.array([0.3, -0.2, 0.1])
+    C = np.array([off[0], off[1], (off[2] - R) if inside else (off[2] + R)])
+    f, t = _block(lambda c: _sphere_fill_fine(C, R, c, inside))
+    out = S.height_function_label(f, t)
+    assert out is not None
+    _, lab, _ = out
+    zs = C[2] + (1 if inside else -1) * math.sqrt(R * R - C[0] ** 2 - C[1] ** 2)
+    nx = (np.array([0.0, 0.0, zs]) - C) / R
+    n_true = nx if inside else -nx
+    ang = math.degrees(math.acos(min(1.0, float(np.dot(lab[:3], n_true)))))
+    assert ang < 0.5, ang
+    k_true = (1.0 if inside else -1.0) / R
+    assert abs(lab[3] - k_true) < tol * abs(k_true), (lab[3], k_true)
+
+
+def test_height_function_rejects_incomplete_blocks():
+    # a droplet of radius 2: the columns beside it have no liquid end
+    f, t = _block(lambda c: S.sphere_fill((0.0, 0.0, -1.8), 2.0, c, inside=True))
+    assert S.height_function_label(f, t) is None
+    # a plane with a solid cell, and with a wall, in the 3x3x3 block
+    n0 = np.array([0.0, 0.0, 1.0])
+    f, t = _block(lambda c: S.plane_fill(n0, 0.1 * n0, c))
+    assert S.height_function_label(f, t) is not None
+    t2 = t.copy()
+    t2[3, 3, 4] = S.SOL
+    assert S.height_function_label(f, t2) is None
+    t3 = t.copy()
+    t3[2, :, :] = S.WALL
+    assert S.height_function_label(f, t3) is None
+    # a solid cell in a column (outside the 3x3x3 block) drops the label too
+    t4 = t.copy()
+    t4[0, 3, 3] = S.SOL
+    assert S.height_function_label(f, t4) is None
+
+
+def test_height_function_block_from_fields_wraps_periodic_axes():
+    """block7 reads the fields around a cell with the periodic x wrap and
+    walls beyond non-periodic faces."""
+    nz, ny, nx = 8, 5, 6
+    types = np.full((nz, ny, nx), S.GAS)
+    types[:4] = S.LIQ
+    phi = np.zeros((nz, ny, nx))
+    phi[:4] = 1.0
+    cell = 4 * nx * ny + 2 * nx + 0          # x = 0, y = 2, z = 4
+    f, t = S.block7(phi, types, cell, (1, 0, 0))
+    assert t[3, 3, 0] == types[4, 2, nx - 3]  # x = -3 wraps to nx - 3
+    assert (t[:, 0, :] == S.WALL).all()       # y = -1 lies beyond the wall
+    assert f[2, 3, 3] == 1.0 and f[3, 3, 3] == 0.0
