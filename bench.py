@@ -244,7 +244,8 @@ def _angles(a, b):
     return np.degrees(np.arccos(np.clip(np.sum(a * b, axis=1), -1.0, 1.0)))
 
 
-def train_normal_model(stream, n_stencils: int, steps: int, seed: int = 4) -> tuple[np.ndarray, dict]:
+def train_normal_model(stream, n_stencils: int, steps: int, seed: int = 4,
+                       log_steps: int = 300) -> tuple[np.ndarray, dict]:
     """Learned normal trained by the library's own kernels (not timed):
     voxelised analytic surfaces (planes, droplets, bubbles, sine waves) and
     the stencils logged from a mid-flume run with their height-function
@@ -263,11 +264,13 @@ def train_normal_model(stream, n_stencils: int, steps: int, seed: int = 4) -> tu
     tgt = torch.empty((n_stencils, 4), dtype=torch.float32, device="cuda")
     F._check(F.fslbm_mlp_stencils(params, n_stencils, fill, tgt, stream.cuda_stream), "fslbm_mlp_stencils")
     del params
-    log_name, (lf, lt), (hf, ht, hfd) = log_flume_stencils(stream)
-    n_logged = len(lf)
-    fill = torch.cat([fill, lf])
-    tgt = torch.cat([tgt, lt])
-    n_stencils = len(fill)
+    logged = None
+    if log_steps > 0:
+        log_name, (lf, lt), (hf, ht, hfd) = log_flume_stencils(stream, steps=log_steps)
+        n_logged = len(lf)
+        fill = torch.cat([fill, lf])
+        tgt = torch.cat([tgt, lt])
+        n_stencils = len(fill)
     t1 = time.perf_counter()
     theta = torch.from_numpy(W.mlp_initial_weights(seed)).cuda()
     curve = torch.empty(steps, dtype=torch.float32, device="cuda")
@@ -279,22 +282,23 @@ def train_normal_model(stream, n_stencils: int, steps: int, seed: int = 4) -> tu
     # rules (raw length in [1/2, 2], within 30 degrees of the
     # finite-difference normal) and the finite-difference normal, both
     # against the height-function labels
-    out = torch.empty((len(hf), 4), dtype=torch.float32, device="cuda")
-    F._check(F.fslbm_mlp_infer(theta, hf, len(hf), out, stream.cuda_stream), "fslbm_mlp_infer")
-    yv = out.cpu().numpy().astype(np.float64)
-    lab = ht.cpu().numpy().astype(np.float64)
-    fdn = hfd.cpu().numpy().astype(np.float64)[:, :3]
-    L = np.linalg.norm(yv[:, :3], axis=1)
-    nml = yv[:, :3] / np.maximum(L, 1e-30)[:, None]
-    use = (L >= 0.5) & (L <= 2.0) & (np.sum(nml * fdn, axis=1) >= np.cos(np.radians(30.0)))
-    e_fd = _angles(fdn, lab[:, :3])
-    e_ml = _angles(np.where(use[:, None], nml, fdn), lab[:, :3])
-    logged = {"workload": log_name, "train": n_logged, "held_out": int(len(hf)),
-              "label": "height function (3x3 columns of 7 cells)",
-              "fd_deg": round(float(e_fd.mean()), 4), "learned_deg": round(float(e_ml.mean()), 4),
-              "taken": round(float(use.mean()), 4),
-              "kappa_mae": round(float(np.abs(np.where(use, yv[:, 3], 0.0) - lab[:, 3]).mean()), 6),
-              "kappa_label_mean_abs": round(float(np.abs(lab[:, 3]).mean()), 6)}
+    if log_steps > 0:
+        out = torch.empty((len(hf), 4), dtype=torch.float32, device="cuda")
+        F._check(F.fslbm_mlp_infer(theta, hf, len(hf), out, stream.cuda_stream), "fslbm_mlp_infer")
+        yv = out.cpu().numpy().astype(np.float64)
+        lab = ht.cpu().numpy().astype(np.float64)
+        fdn = hfd.cpu().numpy().astype(np.float64)[:, :3]
+        L = np.linalg.norm(yv[:, :3], axis=1)
+        nml = yv[:, :3] / np.maximum(L, 1e-30)[:, None]
+        use = (L >= 0.5) & (L <= 2.0) & (np.sum(nml * fdn, axis=1) >= np.cos(np.radians(30.0)))
+        e_fd = _angles(fdn, lab[:, :3])
+        e_ml = _angles(np.where(use[:, None], nml, fdn), lab[:, :3])
+        logged = {"workload": log_name, "steps": log_steps, "train": n_logged, "held_out": int(len(hf)),
+                  "label": "height function (3x3 columns of 7 cells)",
+                  "fd_deg": round(float(e_fd.mean()), 4), "learned_deg": round(float(e_ml.mean()), 4),
+                  "taken": round(float(use.mean()), 4),
+                  "kappa_mae": round(float(np.abs(np.where(use, yv[:, 3], 0.0) - lab[:, 3]).mean()), 6),
+                  "kappa_label_mean_abs": round(float(np.abs(lab[:, 3]).mean()), 6)}
     # FLOPs of one sample and step of the 27-64-64-4 network: forward 2 x 6080
     # multiply-adds; backward the weight gradients of every layer and the
     # activation gradients of the two upper ones
@@ -437,7 +441,8 @@ def run_ours(args, world, rank, local):
     theta, train = None, None
     if args.normals == "mlp":
         with torch.cuda.stream(stream):
-            theta, train = train_normal_model(stream, args.mlp_stencils, args.mlp_steps)
+            theta, train = train_normal_model(stream, args.mlp_stencils, args.mlp_steps,
+                                               log_steps=args.mlp_log_steps)
     horizon = args.error_horizon if args.compare else 0
     head = timed_run(args, w, args.storage, theta, stream, local, barrier, world, horizon)
     # the other forms, timed the same way from the same initial state: plain
@@ -608,7 +613,8 @@ def run_precision_study(args):
     w = W.precision().generate().crop_x(args.study_crop)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        theta, train = train_normal_model(stream, args.mlp_stencils, args.mlp_steps)
+        theta, train = train_normal_model(stream, args.mlp_stencils, args.mlp_steps,
+                                               log_steps=args.mlp_log_steps)
     steps = args.study_steps
     gpu = {}
     for st_name, nm in COMPARE_FORMS:
@@ -726,6 +732,8 @@ def main():
                     help="steps after which the forms' states are compared (untimed beyond the timed steps)")
     ap.add_argument("--mlp-stencils", type=int, default=1 << 22)
     ap.add_argument("--mlp-steps", type=int, default=40000)
+    ap.add_argument("--mlp-log-steps", type=int, default=300,
+                    help="steps of the mid-flume run whose logged stencils join the training (0: none)")
     ap.add_argument("--links", type=int, choices=(0, 1, 2), default=0,
                     help="particle links: 0 the library's choice, 1 pass over the solid cells, 2 fluid side")
     ap.add_argument("--no-e2e", action="store_true")

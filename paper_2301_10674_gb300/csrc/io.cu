@@ -2,6 +2,7 @@
 // post-collision PDFs, FP64 scalars) and the FP64 diagnostic reductions of
 // Section 3.2 (liquid mass, momentum, bulk velocity, interface count,
 // bedload rate of Eq. (1)).
+#include "collide_pair.cuh"
 #include "fslbm_dev.cuh"
 
 namespace fsl {
@@ -244,6 +245,187 @@ __global__ void __launch_bounds__(256, 3) k_reduce_cells(Dev s, double* part) {
     }
 }
 
+// A block's seven partial sums (mass, momentum x, y, z, sum phi rho u_x, sum
+// phi rho, fluid cells) into its row `row` of the partial array (blockDim.x
+// a multiple of 32, at most 128 threads).
+__device__ __forceinline__ void block_partials(const KSum (&acc)[6], long long nfluid, double* row,
+                                               double (&sh)[7][4]) {
+    double v[7] = {acc[0].value(), acc[1].value(), acc[2].value(), acc[3].value(), acc[5].value(),
+                   acc[4].value(), (double)nfluid};
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int k = 0; k < 7; ++k) {
+        const double w = warp_sum(v[k]);
+        if (lane == 0) sh[k][wid] = w;
+    }
+    __syncthreads();
+    if (threadIdx.x < 7) {
+        double w = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) w += sh[threadIdx.x][i];
+        row[threadIdx.x] = w;
+    }
+}
+
+// One fluid cell's contribution: d = sum (f - w), j = sum c (f - w).
+__device__ __forceinline__ void reduce_cell(const Dev& s, KSum (&acc)[6], long long& nfluid, int cell, int t,
+                                            float d, float jx, float jy, float jz) {
+    if (!isfinite(d) || !isfinite(jx) || !isfinite(jy) || !isfinite(jz)) set_error(s, ERR_NAN);
+    const float rho = 1.f + d;
+    const float mx = jx - 0.5f * rho * s.gx;   // rho u
+    ++nfluid;
+    acc[1].add(mx);
+    acc[2].add(jy - 0.5f * rho * s.gy);
+    acc[3].add(jz - 0.5f * rho * s.gz);
+    if (t == T_LIQ) {
+        acc[0].add(d);
+        acc[4].add(d);
+        acc[5].add(mx);
+    } else {
+        const float m = s.mass[cell], phi = s.phi[cell];
+        if (!isfinite(m)) set_error(s, ERR_NAN);
+        acc[0].add(m - 1.f);
+        acc[4].add(phi * rho - 1.f);
+        acc[5].add(phi * mx);
+    }
+}
+
+// The same sums with two x-adjacent cells (x even, x + 1) per thread and the
+// sweep's pair loads: after an even step the two slots of every direction are
+// adjacent and aligned, after an odd step those of the directions with
+// c_x = 0 are, and the others take two loads from one address; the stored
+// values are summed raw (times the storage scale, on packed FP32) and scaled
+// once. Blocks of 128 threads cover 256 cells of a row; the partial rows are
+// those of k_reduce_cells. Needs nx even and 32-bit element indices.
+// The same sums with two x-adjacent cells (x even, x + 1) per thread and the
+// sweep's pair loads: after an even step the two slots of every direction are
+// adjacent and aligned, after an odd step those of the directions with
+// c_x = 0 are, and the others take two loads from one address; the stored
+// values are summed raw (times the storage scale, on packed FP32) and scaled
+// once. Blocks of 128 threads cover 256 cells of a row; the partial rows are
+// those of k_reduce_cells. After an odd step the pairs whose neighbours are
+// not all inside the lattice without wrap (face rows and the pairs at x = 0,
+// nx - 2) are left to k_reduce_edges, so that this kernel carries no boundary
+// code. Needs nx even and 32-bit element indices.
+template <typename S, int LP>
+__global__ void __launch_bounds__(128, 6) k_reduce_pairs(Dev s, double* part) {
+    __shared__ double sh[7][4];
+    KSum acc[6];
+    long long nfluid = 0;
+    const int x = blockIdx.x * 256 + 2 * (int)threadIdx.x;
+    const S* f = static_cast<const S*>(s.f);
+    const unsigned un = (unsigned)s.n;
+    const int nrows = s.ny * s.nz, sxy = s.nx * s.ny;
+    constexpr float UNS = 1.f / Store<S>::scale;
+    if (x < s.nx && (LP == 0 || (x > 0 && x + 1 < s.nx - 1))) {
+        for (int row = blockIdx.y; row < nrows; row += gridDim.y) {
+            const int y = row % s.ny, z = row / s.ny;
+            if (LP == 1 && (y == 0 || y == s.ny - 1 || z == 0 || z == s.nz - 1)) continue;
+            const int cell = x + s.nx * row;
+            const uchar2 fl = *reinterpret_cast<const uchar2*>(s.flags + cell);
+            const int t0 = fl.x & TYPE_MASK, t1 = fl.y & TYPE_MASK;
+            const bool f0 = t0 == T_LIQ || t0 == T_IFC, f1 = t1 == T_LIQ || t1 == T_IFC;
+            if (!f0 && !f1) continue;
+            float2 D = make_float2(0.f, 0.f), JX = D, JY = D, JZ = D;
+#pragma unroll
+            for (int q = 0; q < 27; ++q) {
+                float2 v;
+                if (LP == 0) {
+                    v = Pair<S>::ld2(f + ((unsigned)opp(q) * un + (unsigned)cell));
+                } else {
+                    const unsigned a = (unsigned)q * un + (unsigned)(cell + cx(q) + s.nx * cy(q) + sxy * cz(q));
+                    v = cx(q) == 0 ? Pair<S>::ld2(f + a)
+                                   : make_float2(Store<S>::ld_raw(f + a), Store<S>::ld_raw(f + a + 1));
+                }
+                D = p_add(D, v);
+                if (cx(q)) JX = cx(q) > 0 ? p_add(JX, v) : p_sub(JX, v);
+                if (cy(q)) JY = cy(q) > 0 ? p_add(JY, v) : p_sub(JY, v);
+                if (cz(q)) JZ = cz(q) > 0 ? p_add(JZ, v) : p_sub(JZ, v);
+            }
+            float rd = 0.f, rz = 0.f;   // reference part of sum f and sum c_z f
+            if (Store<S>::HREF) {
+                if (LP == 0) {
+                    rd = s.href[z];
+                } else {
+                    const float hm = s.href[z - 1], h0 = s.href[z], hp = s.href[z + 1];
+                    rd = (hm + hp) * (1.f / 6.f) + h0 * (2.f / 3.f);
+                    rz = (hp - hm) * (1.f / 6.f);
+                }
+            }
+            const float2 us = p_set(UNS);
+            D = p_fma(D, us, p_set(rd));
+            JX = p_mul(JX, us);
+            JY = p_mul(JY, us);
+            JZ = p_fma(JZ, us, p_set(rz));
+            if (f0) reduce_cell(s, acc, nfluid, cell, t0, D.x, JX.x, JY.x, JZ.x);
+            if (f1) reduce_cell(s, acc, nfluid, cell + 1, t1, D.y, JX.y, JY.y, JZ.y);
+        }
+    }
+    block_partials(acc, nfluid, part + 8 * ((long long)blockIdx.y * gridDim.x + blockIdx.x), sh);
+}
+
+// pairs of an odd step that k_reduce_pairs leaves out (as k_liquid_pair_edges
+// lists them: every pair of the y and z face rows, then the pairs at x = 0 and
+// x = nx - 2 of the other rows), one per thread, each slot (q, x + c_q) or
+// (opp q, x) beyond a wall face with its own reference; partial rows from
+// `part` on
+template <typename S>
+__global__ void __launch_bounds__(128) k_reduce_edges(Dev s, double* part) {
+    __shared__ double sh[7][4];
+    KSum acc[6];
+    long long nfluid = 0;
+    const S* f = static_cast<const S*>(s.f);
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int hp = s.nx / 2;
+    const long long nface = 2LL * s.nz + 2LL * (s.ny > 2 ? s.ny - 2 : 0);
+    int y = 0, z = 0, x = 0;
+    bool in = true;
+    if (t < nface * hp) {
+        const int r = (int)(t / hp);
+        x = 2 * (int)(t % hp);
+        if (r < 2 * s.nz) { z = r >> 1; y = (r & 1) ? s.ny - 1 : 0; }
+        else { const int k = r - 2 * s.nz; y = 1 + (k >> 1); z = (k & 1) ? s.nz - 1 : 0; }
+    } else if (t < nface * hp + 2LL * (s.ny - 2) * (s.nz - 2)) {
+        const long long k = t - nface * hp;
+        x = (k & 1) ? s.nx - 2 : 0;
+        const long long r = k >> 1;
+        y = 1 + (int)(r % (s.ny - 2));
+        z = 1 + (int)(r / (s.ny - 2));
+    } else {
+        in = false;
+    }
+    if (in) {
+        const int cell = x + s.nx * (y + s.ny * z);
+#pragma unroll 1
+        for (int k = 0; k < 2; ++k) {
+            const int tk = s.flags[cell + k] & TYPE_MASK;
+            if (tk != T_LIQ && tk != T_IFC) continue;
+            const int xk = x + k;
+            float d = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+            for (int q = 0; q < 27; ++q) {
+                const int tx = shift(xk, cx(q), s.nx, s.per_x), ty = shift(y, cy(q), s.ny, s.per_y),
+                          tz = shift(z, cz(q), s.nz, s.per_z);
+                const bool wall = tx < 0 || ty < 0 || tz < 0;
+                const long long i = wall ? (long long)opp(q) * s.n + cell + k
+                                         : (long long)q * s.n + tx + (long long)s.nx * (ty + (long long)s.ny * tz);
+                float v = Store<S>::ld(f + i);
+                if (Store<S>::HREF) v += wq(q) * s.href[wall ? z : tz];
+                d += v;
+                jx += cx(q) * v;
+                jy += cy(q) * v;
+                jz += cz(q) * v;
+            }
+            reduce_cell(s, acc, nfluid, cell + k, tk, d, jx, jy, jz);
+        }
+    }
+    block_partials(acc, nfluid, part + 8 * (long long)blockIdx.x, sh);
+}
+
+// pairs and blocks of k_reduce_edges
+inline long long reduce_edge_pairs(const Dev& s) {
+    return (2LL * s.nz + 2LL * (s.ny > 2 ? s.ny - 2 : 0)) * (s.nx / 2) +
+           2LL * (s.ny > 2 ? s.ny - 2 : 0) * (s.nz > 2 ? s.nz - 2 : 0);
+}
+
 // out[0..5], out[7] from the blocks' partial rows (fixed order: thread t
 // takes rows t, t + 1024, ..., then a tree over the threads)
 __global__ void __launch_bounds__(1024) k_reduce_sum(const double* part, int blocks, double* out) {
@@ -299,10 +481,12 @@ __global__ void k_reduce_final(Dev s, double* out) {
     if (!isfinite(*s.pool)) set_error(s, ERR_NAN);
 }
 
+// partial rows of the lattice reduction: the row grid's blocks, then those
+// of the edge pairs after an odd step
 int reduce_blocks(const Dev& s) {
     const int bx = (s.nx + 255) / 256;
     const int rows = s.ny * s.nz;
-    return bx * (rows < REDUCE_MAX_BY ? rows : REDUCE_MAX_BY);
+    return bx * (rows < REDUCE_MAX_BY ? rows : REDUCE_MAX_BY) + blocks_for(reduce_edge_pairs(s), 128);
 }
 
 void launch_reduce(const Dev& s, int last_parity, double* out, cudaStream_t st) {
@@ -311,7 +495,27 @@ void launch_reduce(const Dev& s, int last_parity, double* out, cudaStream_t st) 
     const unsigned by = (unsigned)(rows < REDUCE_MAX_BY ? rows : REDUCE_MAX_BY);
     const dim3 grid(bx, by);
     double* part = s.rpart;
-    if (s.storage == FSLBM_STORE_FP32) {
+    int blocks = (int)(bx * by);
+    // pairs (128 threads per 256-cell block); after an odd step the edge
+    // pairs in a kernel of their own, whose listing needs ny, nz >= 3, nx >= 4
+    const bool pairs = s.idx32 && s.nx % 2 == 0 && (last_parity == 0 || (s.nx >= 4 && s.ny >= 3 && s.nz >= 3));
+    if (pairs) {
+        const int eb = last_parity == 1 ? blocks_for(reduce_edge_pairs(s), 128) : 0;
+        if (s.storage == FSLBM_STORE_FP32) {
+            if (last_parity == 0) k_reduce_pairs<float, 0><<<grid, 128, 0, st>>>(s, part);
+            else k_reduce_pairs<float, 1><<<grid, 128, 0, st>>>(s, part);
+            if (eb) k_reduce_edges<float><<<eb, 128, 0, st>>>(s, part + 8LL * blocks);
+        } else if (s.storage == FSLBM_STORE_FP16) {
+            if (last_parity == 0) k_reduce_pairs<__half, 0><<<grid, 128, 0, st>>>(s, part);
+            else k_reduce_pairs<__half, 1><<<grid, 128, 0, st>>>(s, part);
+            if (eb) k_reduce_edges<__half><<<eb, 128, 0, st>>>(s, part + 8LL * blocks);
+        } else {
+            if (last_parity == 0) k_reduce_pairs<__nv_bfloat16, 0><<<grid, 128, 0, st>>>(s, part);
+            else k_reduce_pairs<__nv_bfloat16, 1><<<grid, 128, 0, st>>>(s, part);
+            if (eb) k_reduce_edges<__nv_bfloat16><<<eb, 128, 0, st>>>(s, part + 8LL * blocks);
+        }
+        blocks += eb;
+    } else if (s.storage == FSLBM_STORE_FP32) {
         if (last_parity == 0) k_reduce_cells<float, 0><<<grid, 256, 0, st>>>(s, part);
         else k_reduce_cells<float, 1><<<grid, 256, 0, st>>>(s, part);
     } else if (s.storage == FSLBM_STORE_FP16) {
@@ -321,7 +525,7 @@ void launch_reduce(const Dev& s, int last_parity, double* out, cudaStream_t st) 
         if (last_parity == 0) k_reduce_cells<__nv_bfloat16, 0><<<grid, 256, 0, st>>>(s, part);
         else k_reduce_cells<__nv_bfloat16, 1><<<grid, 256, 0, st>>>(s, part);
     }
-    k_reduce_sum<<<1, 1024, 0, st>>>(part, (int)(bx * by), out);
+    k_reduce_sum<<<1, 1024, 0, st>>>(part, blocks, out);
     k_reduce_particles<<<1, 1024, 0, st>>>(s, out);
     k_reduce_final<<<1, 1, 0, st>>>(s, out);
 }
