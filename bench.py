@@ -187,8 +187,8 @@ COMPARE_FORMS = (("fp32", "fd"), ("fp16", "fd"), ("bf16", "fd"), ("fp32", "mlp")
 # even and odd steps averaged, from one ncu capture on the 1024x64x128 flume.
 # It is valid while the sweep's sources hash to `sources`, and is scaled to a
 # run by its fluid cells.
-SWEEP_TRAFFIC = {"sources": "04486a592246c3d3", "workload": "precision-1024x64x128",
-                 "per_fluid_cell": {"fp16": 195.4, "fp32": 382.6, "bf16": None}}
+SWEEP_TRAFFIC = {"sources": "185368cbc6c46ea7", "workload": "precision-1024x64x128",
+                 "per_fluid_cell": {"fp16": 195.5, "fp32": 381.7, "bf16": 195.8}}
 SWEEP_SOURCES = ("paper_2301_10674_gb300/csrc/stream_collide.cu", "paper_2301_10674_gb300/csrc/fslbm_dev.cuh",
                  "paper_2301_10674_gb300/csrc/collide_pair.cuh")
 
