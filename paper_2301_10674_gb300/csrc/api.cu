@@ -316,7 +316,16 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     long long pc = p->capacity_particles > 0 ? p->capacity_particles : 65536;
     d.np_cap = (int)pc;
     d.X = dalloc<double>(s, 3 * pc, ok); d.U = dalloc<double>(s, 3 * pc, ok); d.W = dalloc<double>(s, 3 * pc, ok);
-    d.X2 = dalloc<double>(s, 3 * pc, ok); d.U2 = dalloc<double>(s, 3 * pc, ok); d.W2 = dalloc<double>(s, 3 * pc, ok);
+    for (int k = 0; k < 2; ++k) {
+        d.dem_dx[k] = dalloc<float>(s, 3 * pc, ok);
+        d.dem_du[k] = dalloc<float>(s, 3 * pc, ok);
+        d.dem_dw[k] = dalloc<float>(s, 3 * pc, ok);
+    }
+    d.nb_d0 = dalloc<float4>(s, pc * NB_SLOTS, ok);
+    d.dem_wall = dalloc<float>(s, 6 * pc, ok);
+    d.dem_c = dalloc<float4>(s, pc, ok);
+    d.Faf = dalloc<float>(s, 3 * pc, ok);
+    d.Taf = dalloc<float>(s, 3 * pc, ok);
     d.R = dalloc<double>(s, pc, ok); d.M = dalloc<double>(s, pc, ok); d.I = dalloc<double>(s, pc, ok);
     d.fixed = dalloc<uint8_t>(s, pc, ok);
     d.Xr = dalloc<float4>(s, pc, ok);
@@ -330,7 +339,7 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     d.hist_partner = dalloc<int>(s, pc * HIST_SLOTS, ok);
     d.nb = dalloc<int>(s, pc * NB_SLOTS, ok);
     d.nb_count = dalloc<int>(s, pc, ok);
-    d.hist_xi = dalloc<double>(s, pc * HIST_SLOTS * 3, ok);
+    d.hist_xi = dalloc<float>(s, pc * HIST_SLOTS * 3, ok);
     d.g_of = dalloc<int>(s, pc, ok);
     d.Xm = dalloc<double>(s, 3 * pc, ok);
     d.margin = dalloc<float>(s, pc, ok);

@@ -113,7 +113,17 @@ struct Dev {
     // particles (FP64 state)
     int np, np_cap;
     double* X; double* U; double* W;            // current state
-    double* X2; double* U2; double* W2;         // sub-step ping-pong
+    // DEM sub-steps in FP32 (R-25): the changes of position, velocity and
+    // angular velocity since the step's start, ping-pong over the sub-steps
+    // (3 per particle each); per neighbour slot the offset of the partner's
+    // centre at the step's start, per particle the distances to the six wall
+    // faces then, (r, m, I) and the averaged hydrodynamic force plus weight
+    // and torque, all in FP32
+    float* dem_dx[2]; float* dem_du[2]; float* dem_dw[2];
+    float4* nb_d0;                              // [np_cap][NB_SLOTS]
+    float* dem_wall;                            // [np_cap][6]: x, L_x - x, y, L_y - y, z, L_z - z
+    float4* dem_c;                              // (r, m, I, 0)
+    float* Faf; float* Taf;                     // [np_cap][3]
     double* R; double* M; double* I;
     uint8_t* fixed;
     float4* Xr;                                 // (X, Y, Z, r) in FP32, r < 0 for fixed spheres
@@ -125,7 +135,7 @@ struct Dev {
     double* Fa; double* Ta;                     // two-step average
     int* nb; int* nb_count;                     // DEM neighbour list [np_cap][NB_SLOTS]
     int* hist_partner;                          // [np_cap][HIST_SLOTS]
-    double* hist_xi;                            // [np_cap][HIST_SLOTS][3]
+    float* hist_xi;                             // [np_cap][HIST_SLOTS][3]
     double rho_p, restitution, friction, poisson, collision_time;
     double kn_coef, dn_coef, kt_ratio;          // contact law constants (host-computed)
     double gxd, gyd, gzd;

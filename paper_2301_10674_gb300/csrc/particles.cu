@@ -136,10 +136,17 @@ __global__ void k_force_avg(Dev s, int have_prev) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= 3 * s.np) return;
     double fh = s.Fh[k], th = s.Th[k];
-    s.Fa[k] = have_prev ? 0.5 * (fh + s.Fp[k]) : fh;
-    s.Ta[k] = have_prev ? 0.5 * (th + s.Tp[k]) : th;
+    const double fa = have_prev ? 0.5 * (fh + s.Fp[k]) : fh;
+    const double ta = have_prev ? 0.5 * (th + s.Tp[k]) : th;
+    s.Fa[k] = fa;
+    s.Ta[k] = ta;
     s.Fp[k] = fh;
     s.Tp[k] = th;
+    // the sub-steps' FP32 copies: averaged hydrodynamic force plus the weight
+    const int a = k % 3;
+    const double g = a == 0 ? s.gxd : (a == 1 ? s.gyd : s.gzd);
+    s.Faf[k] = (float)(fa + s.M[k / 3] * g);
+    s.Taf[k] = (float)ta;
 }
 
 // The history slot of a partner among the particle's slots held in
@@ -162,11 +169,20 @@ __device__ __forceinline__ int hist_slot(const Dev& s, int p, int partner, int (
 #pragma unroll
         for (int k = 0; k < HIST_SLOTS; ++k)
             if (k == found) hpart[k] = partner;
-        double* xi = s.hist_xi + ((long long)p * HIST_SLOTS + found) * 3;
-        xi[0] = xi[1] = xi[2] = 0.0;
+        float* xi = s.hist_xi + ((long long)p * HIST_SLOTS + found) * 3;
+        xi[0] = xi[1] = xi[2] = 0.f;
     }
     seen |= 1u << found;
     return found;
+}
+
+// minimal image of an integer displacement along a periodic axis
+__device__ __forceinline__ int wrap_int(int d, int L, int periodic) {
+    if (periodic) {
+        if (d > L / 2) d -= L;
+        else if (d < -L / 2) d += L;
+    }
+    return d;
 }
 
 // minimal image of a displacement along a periodic axis (|d| < 1.5 L)
@@ -212,11 +228,28 @@ __device__ __forceinline__ void lub_f(const Dev& s, float R, const float n[3], f
 // Neighbour list of every mobile particle for the sub-steps of one LBM
 // step: particles whose surfaces are within 3/4 cell (beyond the
 // lubrication range; the motion within a step is far below the margin).
+// With it the FP32 start of the sub-steps (R-25): per neighbour slot the
+// partner's centre offset (minimal image, formed in FP64), per mobile
+// particle the distances to the wall faces, per particle (r, m, I) and zero
+// changes of position, velocity and angular velocity.
 __global__ void k_dem_neighbours(Dev s) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= s.np) return;
     int cnt = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) s.dem_dx[0][3 * p + a] = s.dem_du[0][3 * p + a] = s.dem_dw[0][3 * p + a] = 0.f;
     if (!s.fixed[p]) {
+        // offsets from the integer part and the FP32 fraction of the centres
+        // (exact integer differences, minimal image on periodic axes): exact to
+        // FP32 rounding and antisymmetric between the two partners
+        const int4 ip = s.Xi[p];
+        const float4 fp = s.Xfr[p];
+        s.dem_wall[6 * p + 0] = (float)ip.x + fp.x;
+        s.dem_wall[6 * p + 1] = (float)(s.nx - ip.x) - fp.x;
+        s.dem_wall[6 * p + 2] = (float)ip.y + fp.y;
+        s.dem_wall[6 * p + 3] = (float)(s.ny - ip.y) - fp.y;
+        s.dem_wall[6 * p + 4] = (float)ip.z + fp.z;
+        s.dem_wall[6 * p + 5] = (float)(s.nz - ip.z) - fp.z;
         const float4 xri = s.Xr[p];
         const int g = s.g_of[p];
         const int ga = g % s.gnx, gb = (g / s.gnx) % s.gny, gc = g / (s.gnx * s.gny);
@@ -236,7 +269,15 @@ __global__ void k_dem_neighbours(Dev s) {
                                     ez = wrapf(xrj.z - xri.z, s.nz, s.per_z);
                         const float reach = fabsf(xri.w) + fabsf(xrj.w) + 0.75f;
                         if (ex * ex + ey * ey + ez * ez > reach * reach) continue;
-                        if (cnt < NB_SLOTS) s.nb[(long long)p * NB_SLOTS + cnt] = j;
+                        if (cnt < NB_SLOTS) {
+                            s.nb[(long long)p * NB_SLOTS + cnt] = j;
+                            const int4 ij = s.Xi[j];
+                            const float4 fj = s.Xfr[j];
+                            s.nb_d0[(long long)p * NB_SLOTS + cnt] =
+                                make_float4((float)wrap_int(ij.x - ip.x, s.nx, s.per_x) + (fj.x - fp.x),
+                                            (float)wrap_int(ij.y - ip.y, s.ny, s.per_y) + (fj.y - fp.y),
+                                            (float)wrap_int(ij.z - ip.z, s.nz, s.per_z) + (fj.z - fp.z), 0.f);
+                        }
                         cnt++;
                     }
                 }
@@ -260,15 +301,15 @@ __global__ void k_particle_copies(Dev s) {
     s.Xfr[p] = make_float4((float)(X - fx), (float)(Y - fy), (float)(Z - fz), 0.f);
     s.Uf[p] = make_float4((float)s.U[3 * p], (float)s.U[3 * p + 1], (float)s.U[3 * p + 2], 0.f);
     s.Wf[p] = make_float4((float)s.W[3 * p], (float)s.W[3 * p + 1], (float)s.W[3 * p + 2], 0.f);
+    s.dem_c[p] = make_float4((float)r, (float)s.M[p], (float)s.I[p], 0.f);
 }
 
 void launch_particle_copies(const Dev& s, cudaStream_t st) {
     if (s.np > 0) k_particle_copies<<<blocks_for(s.np, 128), 128, 0, st>>>(s);
 }
 
-// FP32 linear spring-dashpot with tangential history (same law as above);
-// the offsets come in from FP64 differences, forces are summed in FP64
-__device__ void contact_f(const Dev& s, float meff, const float n[3], float delta, const float vrel[3], double* xi,
+// FP32 linear spring-dashpot with tangential history (same law as above)
+__device__ void contact_f(const Dev& s, float meff, const float n[3], float delta, const float vrel[3], float* xi,
                           float dts, float F[3], float Ft[3]) {
     const float kn = meff * (float)s.kn_coef;
     const float dn = meff * (float)s.dn_coef;
@@ -277,7 +318,7 @@ __device__ void contact_f(const Dev& s, float meff, const float n[3], float delt
     const float vn = vrel[0] * n[0] + vrel[1] * n[1] + vrel[2] * n[2];
     const float vt[3] = {vrel[0] - vn * n[0], vrel[1] - vn * n[1], vrel[2] - vn * n[2]};
     const float fn = kn * delta + dn * vn;
-    float x[3] = {(float)xi[0], (float)xi[1], (float)xi[2]};
+    float x[3] = {xi[0], xi[1], xi[2]};
     const float xn = x[0] * n[0] + x[1] * n[1] + x[2] * n[2];
     for (int a = 0; a < 3; ++a) x[a] = x[a] - xn * n[a] + vt[a] * dts;
     for (int a = 0; a < 3; ++a) Ft[a] = -kt * x[a] - dt_ * vt[a];
@@ -297,28 +338,34 @@ __device__ void contact_f(const Dev& s, float meff, const float n[3], float delt
 }
 
 // One DEM sub-step, a thread per particle over its neighbour list and the
-// walls: contact law in FP32 on offsets formed in FP64, forces and torques
-// summed in FP64, semi-implicit Euler in FP64.
-__global__ void __launch_bounds__(64) k_dem_substep(Dev s, const double* __restrict__ Xa,
-                                                   const double* __restrict__ Ua, const double* __restrict__ Wa,
-                                                   double* Xb, double* Ub, double* Wb, double dts, int last) {
+// walls, in FP32 (R-25): a particle's position, velocity and angular velocity
+// are its FP64 state at the step's start plus the changes dx, du, dw the
+// sub-steps have made (small numbers, exact to FP32 rounding of themselves);
+// the offset to a partner is the start offset (formed in FP64 with the
+// neighbour list) plus the difference of their dx, a wall distance the start
+// distance plus or minus dx. Contact law and sums in FP32, semi-implicit
+// Euler on the changes; the last sub-step adds them to the FP64 state.
+__global__ void __launch_bounds__(64) k_dem_substep(Dev s, const float* __restrict__ dxa,
+                                                   const float* __restrict__ dua, const float* __restrict__ dwa,
+                                                   float* dxb, float* dub, float* dwb, float dts, int last) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= s.np) return;
-    double X[3] = {Xa[3 * p], Xa[3 * p + 1], Xa[3 * p + 2]};
-    double U[3] = {Ua[3 * p], Ua[3 * p + 1], Ua[3 * p + 2]};
-    double W[3] = {Wa[3 * p], Wa[3 * p + 1], Wa[3 * p + 2]};
+    const float dx[3] = {dxa[3 * p], dxa[3 * p + 1], dxa[3 * p + 2]};
+    const float du[3] = {dua[3 * p], dua[3 * p + 1], dua[3 * p + 2]};
+    const float dw[3] = {dwa[3 * p], dwa[3 * p + 1], dwa[3 * p + 2]};
     if (s.fixed[p]) {
-        for (int a = 0; a < 3; ++a) { Xb[3 * p + a] = X[a]; Ub[3 * p + a] = U[a]; Wb[3 * p + a] = W[a]; }
+        for (int a = 0; a < 3; ++a) { dxb[3 * p + a] = dx[a]; dub[3 * p + a] = du[a]; dwb[3 * p + a] = dw[a]; }
         // the top of the particle cells counts the fixed particles too
-        if (last) atomicMax(s.zmax_cell, (int)ceil(X[2] + s.R[p]) + 2);
+        if (last) atomicMax(s.zmax_cell, (int)ceil(s.X[3 * p + 2] + s.R[p]) + 2);
         return;
     }
-    const double ri = s.R[p], mi = s.M[p], Ii = s.I[p];
-    const float rif = (float)ri, mif = (float)mi, dtf = (float)dts;
-    const float Uf[3] = {(float)U[0], (float)U[1], (float)U[2]};
-    const float Wf[3] = {(float)W[0], (float)W[1], (float)W[2]};
-    double F[3] = {s.Fa[3 * p] + mi * s.gxd, s.Fa[3 * p + 1] + mi * s.gyd, s.Fa[3 * p + 2] + mi * s.gzd};
-    double T[3] = {s.Ta[3 * p], s.Ta[3 * p + 1], s.Ta[3 * p + 2]};
+    const float4 cp = s.dem_c[p];
+    const float rif = cp.x, mif = cp.y, Iif = cp.z;
+    const float4 u0 = s.Uf[p], w0 = s.Wf[p];
+    const float Uf[3] = {u0.x + du[0], u0.y + du[1], u0.z + du[2]};
+    const float Wf[3] = {w0.x + dw[0], w0.y + dw[1], w0.z + dw[2]};
+    float F[3] = {s.Faf[3 * p], s.Faf[3 * p + 1], s.Faf[3 * p + 2]};
+    float T[3] = {s.Taf[3 * p], s.Taf[3 * p + 1], s.Taf[3 * p + 2]};
     unsigned seen = 0;
     // the particle's tangential-history partners, held in registers for the
     // sub-step (slot k: partner index, a wall code, or HIST_EMPTY)
@@ -333,24 +380,30 @@ __global__ void __launch_bounds__(64) k_dem_substep(Dev s, const double* __restr
     }
     const int nbc = s.nb_count[p];
     const int* nbl = s.nb + (long long)p * NB_SLOTS;
-    // neighbours four at a time: their indices and positions load together
+    const float4* nd0 = s.nb_d0 + (long long)p * NB_SLOTS;
+    // neighbours four at a time: their indices, offsets and changes load together
     for (int k0 = 0; k0 < nbc; k0 += 4) {
         int jj[4];
-        double xj[4][3];
+        float4 d0[4], cj[4];
+        float dxj[4][3];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) jj[u] = k0 + u < nbc ? nbl[k0 + u] : -1;
+        for (int u = 0; u < 4; ++u) {
+            jj[u] = k0 + u < nbc ? nbl[k0 + u] : -1;
+            d0[u] = k0 + u < nbc ? nd0[k0 + u] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < 4; ++u) {
+            cj[u] = jj[u] >= 0 ? s.dem_c[jj[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-            for (int a = 0; a < 3; ++a) xj[u][a] = jj[u] >= 0 ? Xa[3 * jj[u] + a] : 0.0;
+            for (int a = 0; a < 3; ++a) dxj[u][a] = jj[u] >= 0 ? dxa[3 * jj[u] + a] : 0.f;
+        }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int j = jj[u];
             if (j < 0) continue;
-            const float d[3] = {(float)wrapd(xj[u][0] - X[0], s.nx, s.per_x),
-                                (float)wrapd(xj[u][1] - X[1], s.ny, s.per_y),
-                                (float)wrapd(xj[u][2] - X[2], s.nz, s.per_z)};
-            const float rjf = (float)s.R[j];
+            const float d[3] = {d0[u].x + (dxj[u][0] - dx[0]), d0[u].y + (dxj[u][1] - dx[1]),
+                                d0[u].z + (dxj[u][2] - dx[2])};
+            const float rjf = cj[u].x;
             const float dist2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
             const float rs = rif + rjf;
             const bool touch = dist2 < rs * rs;
@@ -360,39 +413,41 @@ __global__ void __launch_bounds__(64) k_dem_substep(Dev s, const double* __restr
             const float inv = 1.f / dist;
             const float n[3] = {d[0] * inv, d[1] * inv, d[2] * inv};
             const float delta = rs - dist;
+            const float4 uj0 = s.Uf[j], wj0 = s.Wf[j];
+            const float Uj[3] = {uj0.x + dua[3 * j], uj0.y + dua[3 * j + 1], uj0.z + dua[3 * j + 2]};
+            const float Wj[3] = {wj0.x + dwa[3 * j], wj0.y + dwa[3 * j + 1], wj0.z + dwa[3 * j + 2]};
             float wsum[3];
-            for (int a = 0; a < 3; ++a) wsum[a] = rif * Wf[a] + rjf * (float)Wa[3 * j + a];
+            for (int a = 0; a < 3; ++a) wsum[a] = rif * Wf[a] + rjf * Wj[a];
             const float wn[3] = {wsum[1] * n[2] - wsum[2] * n[1], wsum[2] * n[0] - wsum[0] * n[2],
                                  wsum[0] * n[1] - wsum[1] * n[0]};
             float vrel[3];
-            for (int a = 0; a < 3; ++a) vrel[a] = Uf[a] - (float)Ua[3 * j + a] + wn[a];
+            for (int a = 0; a < 3; ++a) vrel[a] = Uf[a] - Uj[a] + wn[a];
             if (lub) {
                 float Fl[3], Ftl[3];
                 lub_f(s, rif * rjf / rs, n, -delta, vrel, Fl, Ftl);
                 const float tq[3] = {rif * (n[1] * Ftl[2] - n[2] * Ftl[1]), rif * (n[2] * Ftl[0] - n[0] * Ftl[2]),
                                      rif * (n[0] * Ftl[1] - n[1] * Ftl[0])};
-                for (int a = 0; a < 3; ++a) { F[a] += (double)Fl[a]; T[a] += (double)tq[a]; }
+                for (int a = 0; a < 3; ++a) { F[a] += Fl[a]; T[a] += tq[a]; }
             }
             if (!touch) continue;
-            const float mj = (float)s.M[j];
+            const float mj = cj[u].y;
             const float meff = mif * mj / (mif + mj);
             const int slot = hist_slot(s, p, j, hpart, seen);
             if (slot < 0) continue;
-            double* xi = s.hist_xi + ((long long)p * HIST_SLOTS + slot) * 3;
+            float* xi = s.hist_xi + ((long long)p * HIST_SLOTS + slot) * 3;
             float Fc[3], Ft[3];
-            contact_f(s, meff, n, delta, vrel, xi, dtf, Fc, Ft);
+            contact_f(s, meff, n, delta, vrel, xi, dts, Fc, Ft);
             const float tq[3] = {rif * (n[1] * Ft[2] - n[2] * Ft[1]), rif * (n[2] * Ft[0] - n[0] * Ft[2]),
                                  rif * (n[0] * Ft[1] - n[1] * Ft[0])};
-            for (int a = 0; a < 3; ++a) { F[a] += (double)Fc[a]; T[a] += (double)tq[a]; }
+            for (int a = 0; a < 3; ++a) { F[a] += Fc[a]; T[a] += tq[a]; }
         }
     }
     // walls on non-periodic axes
-    const int L[3] = {s.nx, s.ny, s.nz};
     const int per[3] = {s.per_x, s.per_y, s.per_z};
     for (int a = 0; a < 3; ++a) {
         if (per[a]) continue;
         for (int side = 0; side < 2; ++side) {
-            const float dist = (float)(side == 0 ? X[a] : (L[a] - X[a]));
+            const float dist = side == 0 ? s.dem_wall[6 * p + 2 * a] + dx[a] : s.dem_wall[6 * p + 2 * a + 1] - dx[a];
             const float delta = rif - dist;
             const bool lub = s.lub && -delta < LUB_HC;
             if (delta <= 0.f && !lub) continue;
@@ -407,17 +462,17 @@ __global__ void __launch_bounds__(64) k_dem_substep(Dev s, const double* __restr
                 lub_f(s, rif, n, -delta, vrel, Fl, Ftl);
                 const float tq[3] = {rif * (n[1] * Ftl[2] - n[2] * Ftl[1]), rif * (n[2] * Ftl[0] - n[0] * Ftl[2]),
                                      rif * (n[0] * Ftl[1] - n[1] * Ftl[0])};
-                for (int b = 0; b < 3; ++b) { F[b] += (double)Fl[b]; T[b] += (double)tq[b]; }
+                for (int b = 0; b < 3; ++b) { F[b] += Fl[b]; T[b] += tq[b]; }
             }
             if (delta <= 0.f) continue;
             const int slot = hist_slot(s, p, -1 - (2 * a + side), hpart, seen);
             if (slot < 0) continue;
-            double* xi = s.hist_xi + ((long long)p * HIST_SLOTS + slot) * 3;
+            float* xi = s.hist_xi + ((long long)p * HIST_SLOTS + slot) * 3;
             float Fc[3], Ft[3];
-            contact_f(s, mif, n, delta, vrel, xi, dtf, Fc, Ft);
+            contact_f(s, mif, n, delta, vrel, xi, dts, Fc, Ft);
             const float tq[3] = {rif * (n[1] * Ft[2] - n[2] * Ft[1]), rif * (n[2] * Ft[0] - n[0] * Ft[2]),
                                  rif * (n[0] * Ft[1] - n[1] * Ft[0])};
-            for (int b = 0; b < 3; ++b) { F[b] += (double)Fc[b]; T[b] += (double)tq[b]; }
+            for (int b = 0; b < 3; ++b) { F[b] += Fc[b]; T[b] += tq[b]; }
         }
     }
     // partners not met in this sub-step lose their springs
@@ -433,17 +488,30 @@ __global__ void __launch_bounds__(64) k_dem_substep(Dev s, const double* __restr
             hp4[k] = v;
         }
     }
-    const double im = 1.0 / mi, iI = 1.0 / Ii;
+    // semi-implicit Euler on the changes
+    const float im = 1.f / mif, iI = 1.f / Iif;
+    float dxn[3], dun[3], dwn[3];
     for (int a = 0; a < 3; ++a) {
-        U[a] += dts * F[a] * im;
-        W[a] += dts * T[a] * iI;
-        double x = X[a] + dts * U[a];
-        if (per[a]) x = x < 0.0 ? x + L[a] : (x >= L[a] ? x - L[a] : x);
-        Xb[3 * p + a] = x;
-        Ub[3 * p + a] = U[a];
-        Wb[3 * p + a] = W[a];
+        dun[a] = du[a] + dts * F[a] * im;
+        dwn[a] = dw[a] + dts * T[a] * iI;
+        const float u0a = a == 0 ? u0.x : (a == 1 ? u0.y : u0.z);
+        dxn[a] = dx[a] + dts * (u0a + dun[a]);
+        dxb[3 * p + a] = dxn[a];
+        dub[3 * p + a] = dun[a];
+        dwb[3 * p + a] = dwn[a];
     }
-    if (last) atomicMax(s.zmax_cell, (int)ceil(X[2] + ri) + 2);
+    if (last) {
+        // the FP64 state of the step's end (positions wrapped on periodic axes)
+        const int L[3] = {s.nx, s.ny, s.nz};
+        for (int a = 0; a < 3; ++a) {
+            double x = s.X[3 * p + a] + (double)dxn[a];
+            if (per[a]) x = x < 0.0 ? x + L[a] : (x >= L[a] ? x - L[a] : x);
+            s.X[3 * p + a] = x;
+            s.U[3 * p + a] += (double)dun[a];
+            s.W[3 * p + a] += (double)dwn[a];
+        }
+        atomicMax(s.zmax_cell, (int)ceil(s.X[3 * p + 2] + s.R[p]) + 2);
+    }
 }
 
 // ------------------------------------------------------------ particle map
@@ -891,11 +959,6 @@ __global__ void k_repair(Dev s) {
     }
 }
 
-__global__ void k_copy3(const double* a, double* b, int n3) {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n3) b[k] = a[k];
-}
-
 // The particle part of a step in two halves. The DEM half (force average,
 // neighbour list, sub-steps, FP32 copies, particle grid) reads and writes
 // particle state only, so it can run beside the free-surface conversion,
@@ -909,18 +972,11 @@ int launch_dem(const Dev& s, int have_prev, cudaStream_t st) {
     k_dem_neighbours<<<blocks_for(s.np, 128), 128, 0, st>>>(s);
     cudaMemsetAsync(s.zmax_cell, 0, sizeof(int), st);
     launches += 2 + ns;
-    const double dts = 1.0 / ns;
+    const float dts = 1.f / (float)ns;
     for (int k = 0; k < ns; ++k) {
-        const bool ev = (k % 2) == 0;
-        k_dem_substep<<<blocks_for(s.np, 64), 64, 0, st>>>(s, ev ? s.X : s.X2, ev ? s.U : s.U2, ev ? s.W : s.W2,
-                                                          ev ? s.X2 : s.X, ev ? s.U2 : s.U, ev ? s.W2 : s.W, dts,
-                                                          k == ns - 1);
-    }
-    if (ns % 2 == 1) {
-        k_copy3<<<blocks_for(n3, 256), 256, 0, st>>>(s.X2, s.X, n3);
-        k_copy3<<<blocks_for(n3, 256), 256, 0, st>>>(s.U2, s.U, n3);
-        k_copy3<<<blocks_for(n3, 256), 256, 0, st>>>(s.W2, s.W, n3);
-        launches += 3;
+        const int a = k % 2, b = 1 - a;
+        k_dem_substep<<<blocks_for(s.np, 64), 64, 0, st>>>(s, s.dem_dx[a], s.dem_du[a], s.dem_dw[a], s.dem_dx[b],
+                                                          s.dem_du[b], s.dem_dw[b], dts, k == ns - 1);
     }
     k_particle_copies<<<blocks_for(s.np, 128), 128, 0, st>>>(s);
     launches += 1 + launch_grid_build(s, st);

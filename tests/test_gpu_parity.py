@@ -499,7 +499,10 @@ def _dry(L=40, **kw):
 @pytest.mark.parametrize("e,r2", [(0.88, 3.0), (0.5, 5.0)])
 def test_dem_restitution_on_gpu(e, r2):
     """Head-on collision in a gas-filled box: the GPU's DEM returns the
-    restitution coefficient and conserves momentum, like the oracle."""
+    restitution coefficient and conserves momentum, like the oracle. The
+    sub-steps run in FP32 on exactly antisymmetric pair forces; each velocity
+    change rounds to FP32, so the pair's momentum holds to FP32 rounding of
+    the collision impulse (1e-6 of m v; 2e-8 observed)."""
     v, r1 = 0.01, 3.0
     w = _dry(restitution=e, diameter=6.0)
     w.xyz = np.array([[10.0, 20, 20], [10.0 + r1 + r2 + 1.0, 20, 20]])
@@ -511,7 +514,7 @@ def test_dem_restitution_on_gpu(e, r2):
     U = sim.get(F.FIELD_P_U)
     assert abs((U[1, 0] - U[0, 0]) / (2 * v) - e) < 0.01 * e
     m = np.array([r1 ** 3, r2 ** 3])
-    assert abs(m @ U[:, 0] - (m[0] - m[1]) * v) < 1e-9
+    assert abs(m @ U[:, 0] - (m[0] - m[1]) * v) < 1e-6 * m.sum() * v
     sim.close()
 
 
