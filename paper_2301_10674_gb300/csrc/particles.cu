@@ -225,68 +225,91 @@ __device__ __forceinline__ void lub_f(const Dev& s, float R, const float n[3], f
     }
 }
 
+// a partner of p for the neighbour list: surfaces within 3/4 cell
+__device__ __forceinline__ bool dem_partner(const Dev& s, int p, int j, const float4& xri) {
+    if (j == p) return false;
+    const float4 xrj = s.Xr[j];
+    const float ex = wrapf(xrj.x - xri.x, s.nx, s.per_x), ey = wrapf(xrj.y - xri.y, s.ny, s.per_y),
+                ez = wrapf(xrj.z - xri.z, s.nz, s.per_z);
+    const float reach = fabsf(xri.w) + fabsf(xrj.w) + 0.75f;
+    return ex * ex + ey * ey + ez * ez <= reach * reach;
+}
+
 // Neighbour list of every mobile particle for the sub-steps of one LBM
 // step: particles whose surfaces are within 3/4 cell (beyond the
 // lubrication range; the motion within a step is far below the margin).
 // With it the FP32 start of the sub-steps (R-25): per neighbour slot the
-// partner's centre offset (minimal image, formed in FP64), per mobile
-// particle the distances to the wall faces, per particle (r, m, I) and zero
-// changes of position, velocity and angular velocity.
+// partner's centre offset, per mobile particle the distances to the wall
+// faces, and zero changes of position, velocity and angular velocity.
+// A warp per particle: lane t scans grid cell t of the (up to) 3x3x3 cells
+// around the particle's, in the order (z, y, x) of the cells and of the
+// particles within a cell; the accepted partners are compacted into the
+// slots in that order (a warp prefix sum over the lanes' counts).
 __global__ void k_dem_neighbours(Dev s) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= s.np) return;
-    int cnt = 0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) s.dem_dx[0][3 * p + a] = s.dem_du[0][3 * p + a] = s.dem_dw[0][3 * p + a] = 0.f;
-    if (!s.fixed[p]) {
-        // offsets from the integer part and the FP32 fraction of the centres
-        // (exact integer differences, minimal image on periodic axes): exact to
-        // FP32 rounding and antisymmetric between the two partners
-        const int4 ip = s.Xi[p];
-        const float4 fp = s.Xfr[p];
+    const unsigned full = 0xffffffffu;
+    const int p = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (p >= s.np) return;   // whole warps leave together
+    if (lane < 3) s.dem_dx[0][3 * p + lane] = s.dem_du[0][3 * p + lane] = s.dem_dw[0][3 * p + lane] = 0.f;
+    if (s.fixed[p]) {
+        if (lane == 0) s.nb_count[p] = 0;
+        return;
+    }
+    // offsets from the integer part and the FP32 fraction of the centres
+    // (exact integer differences, minimal image on periodic axes): exact to
+    // FP32 rounding and antisymmetric between the two partners
+    const int4 ip = s.Xi[p];
+    const float4 fp = s.Xfr[p];
+    if (lane == 0) {
         s.dem_wall[6 * p + 0] = (float)ip.x + fp.x;
         s.dem_wall[6 * p + 1] = (float)(s.nx - ip.x) - fp.x;
         s.dem_wall[6 * p + 2] = (float)ip.y + fp.y;
         s.dem_wall[6 * p + 3] = (float)(s.ny - ip.y) - fp.y;
         s.dem_wall[6 * p + 4] = (float)ip.z + fp.z;
         s.dem_wall[6 * p + 5] = (float)(s.nz - ip.z) - fp.z;
-        const float4 xri = s.Xr[p];
-        const int g = s.g_of[p];
-        const int ga = g % s.gnx, gb = (g / s.gnx) % s.gny, gc = g / (s.gnx * s.gny);
-        GRange ra = grange(ga - 1, ga + 1, s.gnx, s.per_x);
-        GRange rb = grange(gb - 1, gb + 1, s.gny, s.per_y);
-        GRange rc = grange(gc - 1, gc + 1, s.gnz, s.per_z);
-        for (int ic = 0; ic < rc.n; ++ic)
-            for (int ib = 0; ib < rb.n; ++ib)
-                for (int ia = 0; ia < ra.n; ++ia) {
-                    const int gg = ra.v[ia] + s.gnx * (rb.v[ib] + s.gny * rc.v[ic]);
-                    const int b = s.g_start[gg], e = b + s.g_count[gg];
-                    for (int k = b; k < e; ++k) {
-                        const int j = s.g_list[k];
-                        if (j == p) continue;
-                        const float4 xrj = s.Xr[j];
-                        const float ex = wrapf(xrj.x - xri.x, s.nx, s.per_x), ey = wrapf(xrj.y - xri.y, s.ny, s.per_y),
-                                    ez = wrapf(xrj.z - xri.z, s.nz, s.per_z);
-                        const float reach = fabsf(xri.w) + fabsf(xrj.w) + 0.75f;
-                        if (ex * ex + ey * ey + ez * ez > reach * reach) continue;
-                        if (cnt < NB_SLOTS) {
-                            s.nb[(long long)p * NB_SLOTS + cnt] = j;
-                            const int4 ij = s.Xi[j];
-                            const float4 fj = s.Xfr[j];
-                            s.nb_d0[(long long)p * NB_SLOTS + cnt] =
-                                make_float4((float)wrap_int(ij.x - ip.x, s.nx, s.per_x) + (fj.x - fp.x),
-                                            (float)wrap_int(ij.y - ip.y, s.ny, s.per_y) + (fj.y - fp.y),
-                                            (float)wrap_int(ij.z - ip.z, s.nz, s.per_z) + (fj.z - fp.z), 0.f);
-                        }
-                        cnt++;
-                    }
-                }
-        if (cnt > NB_SLOTS) {
-            set_error(s, ERR_HISTORY);
-            cnt = NB_SLOTS;
-        }
     }
-    s.nb_count[p] = cnt;
+    const float4 xri = s.Xr[p];
+    const int g = s.g_of[p];
+    const int ga = g % s.gnx, gb = (g / s.gnx) % s.gny, gc = g / (s.gnx * s.gny);
+    const GRange ra = grange(ga - 1, ga + 1, s.gnx, s.per_x);
+    const GRange rb = grange(gb - 1, gb + 1, s.gny, s.per_y);
+    const GRange rc = grange(gc - 1, gc + 1, s.gnz, s.per_z);
+    const int ncell = ra.n * rb.n * rc.n;
+    int b = 0, e = 0;
+    if (lane < ncell) {
+        const int ia = lane % ra.n, ib = (lane / ra.n) % rb.n, ic = lane / (ra.n * rb.n);
+        const int gg = ra.v[ia] + s.gnx * (rb.v[ib] + s.gny * rc.v[ic]);
+        b = s.g_start[gg];
+        e = b + s.g_count[gg];
+    }
+    int mine = 0;
+    for (int k = b; k < e; ++k) mine += dem_partner(s, p, s.g_list[k], xri) ? 1 : 0;
+    int incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(full, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(full, incl, 31);
+    int slot = incl - mine;
+    for (int k = b; k < e; ++k) {
+        const int j = s.g_list[k];
+        if (!dem_partner(s, p, j, xri)) continue;
+        if (slot < NB_SLOTS) {
+            s.nb[(long long)p * NB_SLOTS + slot] = j;
+            const int4 ij = s.Xi[j];
+            const float4 fj = s.Xfr[j];
+            s.nb_d0[(long long)p * NB_SLOTS + slot] =
+                make_float4((float)wrap_int(ij.x - ip.x, s.nx, s.per_x) + (fj.x - fp.x),
+                            (float)wrap_int(ij.y - ip.y, s.ny, s.per_y) + (fj.y - fp.y),
+                            (float)wrap_int(ij.z - ip.z, s.nz, s.per_z) + (fj.z - fp.z), 0.f);
+        }
+        ++slot;
+    }
+    if (lane == 0) {
+        if (total > NB_SLOTS) set_error(s, ERR_HISTORY);
+        s.nb_count[p] = total > NB_SLOTS ? NB_SLOTS : total;
+    }
 }
 
 // FP32 copies of the particle state used by the lattice kernels
@@ -969,7 +992,7 @@ int launch_dem(const Dev& s, int have_prev, cudaStream_t st) {
     const int n3 = 3 * s.np;
     const int ns = s.dem_substeps;
     k_force_avg<<<blocks_for(n3, 128), 128, 0, st>>>(s, have_prev);
-    k_dem_neighbours<<<blocks_for(s.np, 128), 128, 0, st>>>(s);
+    k_dem_neighbours<<<blocks_for(32LL * s.np, 128), 128, 0, st>>>(s);
     cudaMemsetAsync(s.zmax_cell, 0, sizeof(int), st);
     launches += 2 + ns;
     const float dts = 1.f / (float)ns;
