@@ -276,6 +276,7 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     d.nl_cap = (int)cap;
     d.wl = dalloc<int>(s, cap, ok);
     d.nl = dalloc<int>(s, cap, ok);
+    d.cl = dalloc<int>(s, cap, ok);
     long long tcap = n / 8 + 4096;
     if (tcap > n) tcap = n;
     d.tl_cap = (int)tcap;
@@ -304,6 +305,7 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
         d.sl_count = counts + 7;
         d.tile_count = counts + 8;
         d.bseg_count = counts + 9;
+        d.cl_count = counts + 10;
     }
     double* dd = dalloc<double>(s, 4, ok);
     if (ok) {

@@ -82,7 +82,7 @@ struct Dev {
     float* phi;        // interface fill level
     float4* ru;        // (rho, ux, uy, uz) of the last collision, interface cells
     float4* nrm;       // interface normal used by the next step's boundary condition
-    float4* nrm1;      // interface normal of the current fill levels (excess weights)
+    float4* nrm1;      // normal of the converting cells at the current fill levels (excess weights)
     int* owner;        // owning particle of solid cells
     uint8_t* conv;     // conversion code of interface cells (0 outside a step)
     float* exscale;    // excess mass per unit weight of converting cells
@@ -93,6 +93,7 @@ struct Dev {
     // work lists (device counts)
     int* wl; int* wl_count; int wl_cap;        // interface cells
     int* nl; int* nl_count; int nl_cap;        // cells becoming interface this step
+    int* cl; int* cl_count;                    // interface cells converting this step (capacity wl_cap)
     int* tl; int* tl_count; int tl_cap;        // particle map transitions
     int* sl; int* sl_count; int sl_cap;        // solid cells with a fluid neighbour
     int* tiles; int* tile_count;               // SP_TILE-cell x-tiles holding a liquid cell

@@ -57,9 +57,10 @@ __device__ float4 py_normal(const Dev& s, long long c) {
     return make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-__global__ void k_normals(Dev s, float4* out) {
-    FOR_LIST(i, s.wl_count) {
-        int c = s.wl[i];
+__global__ void k_normals(Dev s, float4* out, const int* list, const int* countp) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x, cnt = min(*countp, s.wl_cap); i < cnt;
+         i += gridDim.x * blockDim.x) {
+        int c = list[i];
         out[c] = py_normal(s, c);
     }
 }
@@ -73,8 +74,8 @@ __global__ void k_normals(Dev s, float4* out) {
 // raw length outside [1/2, 2]) and the check on the network (its normal more
 // than 30 degrees away falls back too). out[c] = (n, curvature), curvature 0 where the fallback is
 // taken.
-__global__ void __launch_bounds__(128) k_mlp_normals(Dev s, float4* out) {
-    const int count = *s.wl_count;
+__global__ void __launch_bounds__(128) k_mlp_normals(Dev s, float4* out, const int* list, const int* countp) {
+    const int count = min(*countp, s.wl_cap);
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const unsigned full = 0xffffffffu;
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(128) k_mlp_normals(Dev s, float4* out) {
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             const int li = base + g + 8 * r;
-            cell[r] = li < count ? s.wl[li] : -1;
+            cell[r] = li < count ? list[li] : -1;
             bad[r] = false;
             gr[r][0] = gr[r][1] = gr[r][2] = 0.f;
             int x = 0, y = 0, z = 0;
@@ -172,9 +173,11 @@ __global__ void __launch_bounds__(128) k_mlp_normals(Dev s, float4* out) {
     }
 }
 
-static int normals_into(const Dev& s, float4* out, cudaStream_t st) {
-    if (s.mlp) k_mlp_normals<<<152 * 8, 128, 0, st>>>(s, out);
-    else k_normals<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(s, out);
+// normals of the cells of a list (the interface list, or the cells that
+// convert in this step)
+static int normals_into(const Dev& s, float4* out, const int* list, const int* count, cudaStream_t st) {
+    if (s.mlp) k_mlp_normals<<<152 * 8, 128, 0, st>>>(s, out, list, count);
+    else k_normals<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(s, out, list, count);
     return 1;
 }
 
@@ -205,27 +208,36 @@ __global__ void k_candidates(Dev s) {
     }
 }
 
-// filling wins: a to-gas cell next to a to-liquid cell stays interface
-__global__ void k_conflict(Dev s) {
-    FOR_LIST(i, s.wl_count) {
-        int c = s.wl[i];
-        if (s.conv[c] != CV_TO_GAS) continue;
-        int x, y, z;
-        coords(s, c, x, y, z);
-        bool clash = false;
-        for (int q = 0; q < 27 && !clash; ++q) {
-            if (q == 13) continue;
-            long long nb = nbr(s, x, y, z, cx(q), cy(q), cz(q));
-            if (nb >= 0 && s.conv[nb] == CV_TO_LIQ) clash = true;
-        }
-        if (clash) s.conv[c] = 0;
-    }
-}
-
 __device__ __forceinline__ void list_push(const Dev& s, int* list, int* count, int cap, int v) {
     int k = atomicAdd(count, 1);
     if (k < cap) list[k] = v;
     else set_error(s, ERR_CAPACITY);
+}
+
+// filling wins: a to-gas cell next to a to-liquid cell stays interface. The
+// cells that still convert are listed (their normals give the excess-mass
+// weights).
+__global__ void k_conflict(Dev s) {
+    FOR_LIST(i, s.wl_count) {
+        int c = s.wl[i];
+        const uint8_t cv = s.conv[c];
+        if (!cv) continue;
+        if (cv == CV_TO_GAS) {
+            int x, y, z;
+            coords(s, c, x, y, z);
+            bool clash = false;
+            for (int q = 0; q < 27 && !clash; ++q) {
+                if (q == 13) continue;
+                long long nb = nbr(s, x, y, z, cx(q), cy(q), cz(q));
+                if (nb >= 0 && s.conv[nb] == CV_TO_LIQ) clash = true;
+            }
+            if (clash) {
+                s.conv[c] = 0;
+                continue;
+            }
+        }
+        list_push(s, s.cl, s.cl_count, s.wl_cap, c);
+    }
 }
 
 // gas neighbours of filled cells and liquid neighbours of emptied cells
@@ -548,13 +560,16 @@ void launch_log_stencils(const Dev& s, long long cap, float* fill, float* target
                                                           reinterpret_cast<float4*>(fd), cells, found);
 }
 
-int launch_normals(const Dev& s, float4* out, cudaStream_t st) { return normals_into(s, out, st); }
+int launch_normals(const Dev& s, float4* out, cudaStream_t st) { return normals_into(s, out, s.wl, s.wl_count, st); }
 
 int launch_conversion(const Dev& s, int last_parity, cudaStream_t st) {
     k_update_phi<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(s);
-    normals_into(s, s.nrm1, st);
     k_candidates<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(s);
+    cudaMemsetAsync(s.cl_count, 0, sizeof(int), st);
     k_conflict<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(s);
+    // the excess-mass weights need the normals of the converting cells only;
+    // fill levels and types are those k_update_phi left
+    normals_into(s, s.nrm1, s.cl, s.cl_count, st);
     cudaMemsetAsync(s.nl_count, 0, sizeof(int), st);
     k_mark<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(s);
     k_init_new<<<LIST_BLOCKS, LIST_THREADS, 0, st>>>(s, last_parity);
