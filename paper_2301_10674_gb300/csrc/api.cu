@@ -515,14 +515,15 @@ static int enqueue_step(fslbm* s, int parity, bool capturing) {
         e1 = s->ev[s->ev_used++];
         cudaEventRecord(e0, st);
     }
-    nl += launch_stream_collide(d, parity, st);
+    nl += launch_stream_collide(d, parity, st, d.np > 0 ? s->ev_fork : nullptr);
     if (capturing)
         cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal);
     else if (s->timing)
         cudaEventRecord(e1, st);
     if (d.np > 0) {
-        // the DEM half on the side stream, beside the conversion
-        cudaEventRecord(s->ev_fork, st);
+        // the DEM half on the side stream, from the end of the link pass:
+        // beside the liquid kernels and the conversion.
+        // Those read no particle state, and the DEM no fluid state.
         cudaStreamWaitEvent(s->side, s->ev_fork, 0);
         nl += launch_dem(d, s->have_prev, s->side);
         cudaEventRecord(s->ev_join, s->side);

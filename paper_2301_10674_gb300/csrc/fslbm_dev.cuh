@@ -570,7 +570,10 @@ __device__ __forceinline__ void post_moments(const Dev& s, const float (&f)[27],
 // ---------------------------------------------------------------- launchers
 // (defined in the translation units, called from the host orchestration)
 // launchers used inside a time step return the number of kernels enqueued
-int launch_stream_collide(const Dev& s, int parity, cudaStream_t st);
+// links_done (may be null) is recorded on st once the particle forces of the
+// step are complete: after the link pass, or after the sweep with fluid-side
+// links
+int launch_stream_collide(const Dev& s, int parity, cudaStream_t st, cudaEvent_t links_done);
 int launch_classify(const Dev& s, cudaStream_t st);
 void launch_check_invariant(const Dev& s, cudaStream_t st);
 int launch_normals(const Dev& s, float4* out, cudaStream_t st);

@@ -1373,12 +1373,16 @@ static int bed_blocks() {
 }
 
 template <typename S>
-static void launch_typed(const Dev& s, int parity, cudaStream_t st) {
+static void launch_typed(const Dev& s, int parity, cudaStream_t st, cudaEvent_t links_done) {
     const int lb = 152 * 8;
+    // the particle forces are complete after the link pass, or with fluid-side
+    // links after the whole sweep
+    const bool early = s.np > 0 && !s.links_fused;
     // liquid kernels: threads along x, blocks over the rows (y, z)
     const dim3 lgrid((unsigned)((s.nx + 255) / 256), (unsigned)(s.ny * s.nz < 65535 ? s.ny * s.nz : 65535));
     if (parity == 0) {
         if (s.np > 0 && !s.links_fused) k_solid_links<S, 0><<<link_blocks<S, 0>(), 256, 0, st>>>(s);
+        if (early && links_done) cudaEventRecord(links_done, st);
         if (use_staged_pairs(s)) {
             if constexpr (sizeof(S) == 2) {
                 cudaMemsetAsync(s.tile_count, 0, sizeof(int), st);
@@ -1394,6 +1398,7 @@ static void launch_typed(const Dev& s, int parity, cudaStream_t st) {
         k_interface<S, 0><<<lb, 128, 0, st>>>(s);
     } else {
         if (s.np > 0 && !s.links_fused) k_solid_links<S, 1><<<link_blocks<S, 1>(), 256, 0, st>>>(s);
+        if (early && links_done) cudaEventRecord(links_done, st);
         if (use_split(s)) {
             k_liquid_pair<S, 1, 1><<<lgrid, 128, 0, st>>>(s);
             const long long ne = (2LL * s.nz + 2LL * (s.ny > 2 ? s.ny - 2 : 0)) * (s.nx / 2) +
@@ -1407,12 +1412,13 @@ static void launch_typed(const Dev& s, int parity, cudaStream_t st) {
         if (s.np > 0 && s.links_fused) k_liquid_pair_bed<S, 1><<<bed_blocks<S, 1>(), 128, 0, st>>>(s);
         k_interface<S, 1><<<lb, 128, 0, st>>>(s);
     }
+    if (!early && links_done) cudaEventRecord(links_done, st);
 }
 
-int launch_stream_collide(const Dev& s, int parity, cudaStream_t st) {
-    if (s.storage == FSLBM_STORE_FP32) launch_typed<float>(s, parity, st);
-    else if (s.storage == FSLBM_STORE_FP16) launch_typed<__half>(s, parity, st);
-    else launch_typed<__nv_bfloat16>(s, parity, st);
+int launch_stream_collide(const Dev& s, int parity, cudaStream_t st, cudaEvent_t links_done) {
+    if (s.storage == FSLBM_STORE_FP32) launch_typed<float>(s, parity, st, links_done);
+    else if (s.storage == FSLBM_STORE_FP16) launch_typed<__half>(s, parity, st, links_done);
+    else launch_typed<__nv_bfloat16>(s, parity, st, links_done);
     const bool staged = parity == 0 && use_staged_pairs(s);
     const bool split = parity == 1 && use_split(s);
     return (s.np > 0 ? 1 : 0) + 2 + (staged ? 1 : 0) + (split ? 1 : 0);
