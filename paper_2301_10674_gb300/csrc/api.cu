@@ -306,6 +306,7 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
         d.tile_count = counts + 8;
         d.bseg_count = counts + 9;
         d.cl_count = counts + 10;
+        d.rtail_count = counts + 11;
     }
     double* dd = dalloc<double>(s, 4, ok);
     if (ok) {
@@ -357,6 +358,7 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     s->stage = dalloc<double>(s, n > 8 ? n : 8, ok);
     s->red = dalloc<double>(s, 8, ok);
     d.rpart = dalloc<double>(s, 8 * (size_t)reduce_blocks(d), ok);
+    d.rtail = dalloc<double>(s, 8 * REDUCE_TAIL_BLOCKS, ok);
     float* href = p->storage != FSLBM_STORE_FP32 ? dalloc<float>(s, p->nz, ok) : nullptr;
     if (ok && (cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess ||
                cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||

@@ -48,6 +48,7 @@ constexpr int SP_TILE = 256;     // cells per x-tile of the staged even step
 constexpr int BED_SEG = 256;     // cells per x-segment of the bed kernel (one block of 128 pairs)
 constexpr int WAIT_LIMIT_DEFAULT = 1 << 22;   // polls of a bounded device wait
 
+constexpr int REDUCE_TAIL_BLOCKS = 64;   // blocks of the reduction's second level
 constexpr int REDUCE_MAX_BY = 1024;   // row blocks of the lattice reduction (several rows per thread)
 constexpr int HIST_SLOTS = 16;   // tangential-spring history slots per particle
 constexpr int NB_SLOTS = 32;     // DEM neighbour-list slots per particle
@@ -109,6 +110,7 @@ struct Dev {
     double* pool;
     double* pool_share;
     double* rpart;     // partial sums of the lattice reduction, 8 per block
+    double* rtail; int* rtail_count;   // the reduction's second level: 8 sums per tail block, blocks done
     int* err;
     unsigned long long* viol;
     // particles (FP64 state)

@@ -2,6 +2,9 @@
 // post-collision PDFs, FP64 scalars) and the FP64 diagnostic reductions of
 // Section 3.2 (liquid mass, momentum, bulk velocity, interface count,
 // bedload rate of Eq. (1)).
+#include <algorithm>
+#include <type_traits>
+
 #include "collide_pair.cuh"
 #include "fslbm_dev.cuh"
 
@@ -141,7 +144,7 @@ struct KSum {
 // Fluid-cell sums: liquid mass (liquid rho + interface m), momentum, and the
 // phi-weighted sums of the bulk velocity. Threads run along x, blocks over
 // rows (a few rows per thread, so that many cells are in flight); every
-// block writes its partial sums to its own row of `part`, and k_reduce_sum
+// block writes its partial sums to its own row of `part`, and k_reduce_tail
 // adds the rows in a fixed order. Each cell's 27 post-collision PDFs come from
 // the slots the last step wrote: (opp q, x) after an even step, (q, x + c_q)
 // after an odd one (constant offsets inside the lattice, the general lookup
@@ -362,13 +365,172 @@ __global__ void __launch_bounds__(128, 6) k_reduce_pairs(Dev s, double* part) {
     block_partials(acc, nfluid, part + 8 * ((long long)blockIdx.y * gridDim.x + blockIdx.x), sh);
 }
 
-// pairs of an odd step that k_reduce_pairs leaves out (as k_liquid_pair_edges
-// lists them: every pair of the y and z face rows, then the pairs at x = 0 and
-// x = nx - 2 of the other rows), one per thread, each slot (q, x + c_q) or
-// (opp q, x) beyond a wall face with its own reference; partial rows from
-// `part` on
+// four x-adjacent 16-bit stored values from an 8-byte aligned address, as
+// two pairs
 template <typename S>
-__global__ void __launch_bounds__(128) k_reduce_edges(Dev s, double* part) {
+__device__ __forceinline__ void ld4(const S* p, float2& lo, float2& hi) {
+    const uint2 w = *reinterpret_cast<const uint2*>(p);
+    if constexpr (std::is_same<S, __half>::value) {
+        lo = __half22float2(*reinterpret_cast<const __half2*>(&w.x));
+        hi = __half22float2(*reinterpret_cast<const __half2*>(&w.y));
+    } else {
+        lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w.x));
+        hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w.y));
+    }
+}
+
+// y and z of face row r of an odd step's reduction (the y face rows of every
+// z, then the z face rows of the inner y)
+__device__ __forceinline__ void face_row(const Dev& s, int r, int& y, int& z) {
+    if (r < 2 * s.nz) {
+        z = r >> 1;
+        y = (r & 1) ? s.ny - 1 : 0;
+    } else {
+        const int k = r - 2 * s.nz;
+        y = 1 + (k >> 1);
+        z = (k & 1) ? s.nz - 1 : 0;
+    }
+}
+
+// The sums of k_reduce_pairs with four x-adjacent cells (x a multiple of 4)
+// per thread, for 16-bit storage: after an even step every direction's four
+// slots are one aligned 8-byte load; after an odd step the slots x + c_q of
+// the directions with c_x = +1 or -1 are three of the aligned four plus one
+// value beyond them, so 45 loads serve four cells (90 for two pairs) and a
+// thread keeps twice the bytes in flight. Blocks of 64 threads cover 256 cells
+// of a row, so the partial rows are those of k_reduce_pairs. After an odd step
+// FACE 0 takes the inner rows and FACE 1 the face rows (y or z on a face),
+// where a direction's source row (y + c_y, z + c_z) is wrapped, or beyond a
+// wall the cell's own slot (opp q, x) is read; either way the same for the
+// whole row, so the quad loads stay aligned and each slot's reference is
+// summed per row. With walls in x the quads at x = 0 and nx - 4 of every row
+// are left to k_reduce_edges; with periodic x they take their value beyond
+// the aligned four across the seam.
+template <typename S, int LP, int FACE>
+__global__ void __launch_bounds__(64, FACE ? 8 : 12) k_reduce_quads(Dev s, double* part) {
+    __shared__ double sh[7][4];
+    KSum acc[6];
+    long long nfluid = 0;
+    const int x = blockIdx.x * 256 + 4 * (int)threadIdx.x;
+    const S* f = static_cast<const S*>(s.f);
+    const unsigned un = (unsigned)s.n;
+    const int nrows = FACE ? 2 * s.nz + 2 * (s.ny - 2) : s.ny * s.nz, sxy = s.nx * s.ny;
+    constexpr float UNS = 1.f / Store<S>::scale;
+    // periodic x: the quads at the x ends take their one value beyond the
+    // aligned four across the seam
+    const unsigned ep = x + 4 < s.nx ? 4u : 4u - (unsigned)s.nx;
+    const unsigned em = x > 0 ? 0u - 1u : (unsigned)s.nx - 1u;
+    if (x < s.nx && (LP == 0 || s.per_x || (x > 0 && x + 4 < s.nx))) {
+        for (int r = blockIdx.y; r < nrows; r += gridDim.y) {
+            int y, z;
+            if (FACE) {
+                face_row(s, r, y, z);
+            } else {
+                y = r % s.ny;
+                z = r / s.ny;
+                if (LP == 1 && (y == 0 || y == s.ny - 1 || z == 0 || z == s.nz - 1)) continue;
+            }
+            const int cell = x + s.nx * (y + s.ny * z);
+            const uchar4 fl = *reinterpret_cast<const uchar4*>(s.flags + cell);
+            const int tk[4] = {fl.x & TYPE_MASK, fl.y & TYPE_MASK, fl.z & TYPE_MASK, fl.w & TYPE_MASK};
+            bool fk[4], any = false;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                fk[k] = tk[k] == T_LIQ || tk[k] == T_IFC;
+                any |= fk[k];
+            }
+            if (!any) continue;
+            float2 D[2], JX[2], JY[2], JZ[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) D[h] = JX[h] = JY[h] = JZ[h] = make_float2(0.f, 0.f);
+            // reference part of sum f and sum c f (face rows: slot by slot,
+            // from the references of z and of its wrapped neighbours)
+            float rd = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
+            float hm = 0.f, h0 = 0.f, hp = 0.f;
+            if (FACE) {
+                const int zm = shift(z, -1, s.nz, s.per_z), zp = shift(z, 1, s.nz, s.per_z);
+                h0 = s.href[z];
+                hm = zm >= 0 ? s.href[zm] : h0;
+                hp = zp >= 0 ? s.href[zp] : h0;
+            }
+#pragma unroll
+            for (int q = 0; q < 27; ++q) {
+                float2 v[2];
+                if (LP == 0) {
+                    ld4<S>(f + ((unsigned)opp(q) * un + (unsigned)cell), v[0], v[1]);
+                } else {
+                    // slots x + c_q .. x + 3 + c_q of the source row
+                    unsigned a;
+                    bool own = false;
+                    if (FACE) {
+                        const int yy = shift(y, cy(q), s.ny, s.per_y), zz = shift(z, cz(q), s.nz, s.per_z);
+                        own = yy < 0 || zz < 0;
+                        a = own ? (unsigned)opp(q) * un + (unsigned)cell
+                                : (unsigned)q * un + (unsigned)(x + s.nx * (yy + s.ny * zz));
+                        const float rq = wq(q) * (own || cz(q) == 0 ? h0 : (cz(q) < 0 ? hm : hp));
+                        rd += rq;
+                        if (cx(q)) rx = cx(q) > 0 ? rx + rq : rx - rq;
+                        if (cy(q)) ry = cy(q) > 0 ? ry + rq : ry - rq;
+                        if (cz(q)) rz = cz(q) > 0 ? rz + rq : rz - rq;
+                    } else {
+                        a = (unsigned)q * un + (unsigned)(cell + s.nx * cy(q) + sxy * cz(q));
+                    }
+                    float2 A0, A1;
+                    ld4<S>(f + a, A0, A1);
+                    if (cx(q) == 0 || own) {
+                        v[0] = A0;
+                        v[1] = A1;
+                    } else if (cx(q) > 0) {
+                        const float e = Store<S>::ld_raw(f + (a + ep));
+                        v[0] = make_float2(A0.y, A1.x);
+                        v[1] = make_float2(A1.y, e);
+                    } else {
+                        const float e = Store<S>::ld_raw(f + (a + em));
+                        v[0] = make_float2(e, A0.x);
+                        v[1] = make_float2(A0.y, A1.x);
+                    }
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    D[h] = p_add(D[h], v[h]);
+                    if (cx(q)) JX[h] = cx(q) > 0 ? p_add(JX[h], v[h]) : p_sub(JX[h], v[h]);
+                    if (cy(q)) JY[h] = cy(q) > 0 ? p_add(JY[h], v[h]) : p_sub(JY[h], v[h]);
+                    if (cz(q)) JZ[h] = cz(q) > 0 ? p_add(JZ[h], v[h]) : p_sub(JZ[h], v[h]);
+                }
+            }
+            if (LP == 0) {
+                rd = s.href[z];
+            } else if (!FACE) {
+                // every slot of direction c_z at z + c_z: per-axis weights 1/6, 2/3, 1/6
+                const float zm = s.href[z - 1], z0 = s.href[z], zp = s.href[z + 1];
+                rd = (zm + zp) * (1.f / 6.f) + z0 * (2.f / 3.f);
+                rz = (zp - zm) * (1.f / 6.f);
+            }
+            const float2 us = p_set(UNS);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                D[h] = p_fma(D[h], us, p_set(rd));
+                JX[h] = p_fma(JX[h], us, p_set(rx));
+                JY[h] = p_fma(JY[h], us, p_set(ry));
+                JZ[h] = p_fma(JZ[h], us, p_set(rz));
+            }
+            if (fk[0]) reduce_cell(s, acc, nfluid, cell, tk[0], D[0].x, JX[0].x, JY[0].x, JZ[0].x);
+            if (fk[1]) reduce_cell(s, acc, nfluid, cell + 1, tk[1], D[0].y, JX[0].y, JY[0].y, JZ[0].y);
+            if (fk[2]) reduce_cell(s, acc, nfluid, cell + 2, tk[2], D[1].x, JX[1].x, JY[1].x, JZ[1].x);
+            if (fk[3]) reduce_cell(s, acc, nfluid, cell + 3, tk[3], D[1].y, JX[1].y, JY[1].y, JZ[1].y);
+        }
+    }
+    block_partials(acc, nfluid, part + 8 * ((long long)blockIdx.y * gridDim.x + blockIdx.x), sh);
+}
+
+// pairs of an odd step that k_reduce_pairs or k_reduce_quads leave out, one
+// per thread: after k_reduce_pairs (as k_liquid_pair_edges lists them) every
+// pair of the y and z face rows, then the pairs at x = 0 and nx - 2 of the
+// other rows; after k_reduce_quads (ends_only) the pairs at x = 0, 2, nx - 4
+// and nx - 2 of every row. Each slot is (q, x + c_q), or (opp q, x) beyond a
+// wall face, with its own reference; partial rows from `part` on
+template <typename S>
+__global__ void __launch_bounds__(128) k_reduce_edges(Dev s, double* part, int xe, int ends_only) {
     __shared__ double sh[7][4];
     KSum acc[6];
     long long nfluid = 0;
@@ -378,15 +540,28 @@ __global__ void __launch_bounds__(128) k_reduce_edges(Dev s, double* part) {
     const long long nface = 2LL * s.nz + 2LL * (s.ny > 2 ? s.ny - 2 : 0);
     int y = 0, z = 0, x = 0;
     bool in = true;
-    if (t < nface * hp) {
+    if (ends_only) {
+        // the xe pairs at the x ends of every row
+        if (t < (long long)xe * s.ny * s.nz) {
+            const int e = (int)(t % xe);
+            x = e < xe / 2 ? 2 * e : s.nx - 2 * (xe - e);
+            const long long r = t / xe;
+            y = (int)(r % s.ny);
+            z = (int)(r / s.ny);
+        } else {
+            in = false;
+        }
+    } else if (t < nface * hp) {
         const int r = (int)(t / hp);
         x = 2 * (int)(t % hp);
         if (r < 2 * s.nz) { z = r >> 1; y = (r & 1) ? s.ny - 1 : 0; }
         else { const int k = r - 2 * s.nz; y = 1 + (k >> 1); z = (k & 1) ? s.nz - 1 : 0; }
-    } else if (t < nface * hp + 2LL * (s.ny - 2) * (s.nz - 2)) {
+    } else if (t < nface * hp + (long long)xe * (s.ny - 2) * (s.nz - 2)) {
+        // xe pairs per row: x = 0, nx - 2, or x = 0, 2, nx - 4, nx - 2
         const long long k = t - nface * hp;
-        x = (k & 1) ? s.nx - 2 : 0;
-        const long long r = k >> 1;
+        const int e = (int)(k % xe);
+        x = e < xe / 2 ? 2 * e : s.nx - 2 * (xe - e);
+        const long long r = k / xe;
         y = 1 + (int)(r % (s.ny - 2));
         z = 1 + (int)(r / (s.ny - 2));
     } else {
@@ -420,65 +595,101 @@ __global__ void __launch_bounds__(128) k_reduce_edges(Dev s, double* part) {
     block_partials(acc, nfluid, part + 8 * (long long)blockIdx.x, sh);
 }
 
-// pairs and blocks of k_reduce_edges
-inline long long reduce_edge_pairs(const Dev& s) {
+// pairs of k_reduce_edges: after k_reduce_pairs (face rows, then two pairs
+// per inner row), or the xe pairs at the x ends of every row
+inline long long reduce_edge_pairs(const Dev& s, int xe, bool ends_only) {
+    if (ends_only) return (long long)xe * s.ny * s.nz;
     return (2LL * s.nz + 2LL * (s.ny > 2 ? s.ny - 2 : 0)) * (s.nx / 2) +
            2LL * (s.ny > 2 ? s.ny - 2 : 0) * (s.nz > 2 ? s.nz - 2 : 0);
 }
+// face rows of an odd step (y or z on a face)
+inline int reduce_face_rows(const Dev& s) { return 2 * s.nz + 2 * (s.ny > 2 ? s.ny - 2 : 0); }
 
-// out[0..5], out[7] from the blocks' partial rows (fixed order: thread t
-// takes rows t, t + 1024, ..., then a tree over the threads)
-__global__ void __launch_bounds__(1024) k_reduce_sum(const double* part, int blocks, double* out) {
-    __shared__ double sh[7][1024];
-    double v[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int b = threadIdx.x; b < blocks; b += blockDim.x)
+// four cells per thread for 16-bit storage where nx is a multiple of 4 (the
+// x ends of a row after an odd step then leave two pairs each to the edges)
+inline bool reduce_quads(const Dev& s) {
+    return s.storage != FSLBM_STORE_FP32 && s.idx32 && s.nx % 4 == 0;
+}
+inline int reduce_xe(const Dev& s) { return s.nx >= 8 ? 4 : 2; }
+
+// The result from the blocks' partial rows and the particles, in a fixed
+// order over REDUCE_TAIL_BLOCKS blocks of 256 threads (FP64 adds are slow on
+// one SM): block b sums its contiguous share of the rows and of the
+// particles (thread t of it items t, t + 256, ...; then the warps' shuffle
+// trees and a pass over the warps) into its row of s.rtail; the block that
+// finishes last sums those rows in order and writes out[0] liquid mass (the
+// fluid-cell count added back, plus the pool), out[1..3] momentum, out[4]
+// bulk velocity, out[5] interface cells, out[6] the bedload rate of Eq. (1)
+// sum u_x,p V_p / (L_x L_y), out[7] pool; it then clears the block counter.
+__global__ void __launch_bounds__(256) k_reduce_tail(Dev s, const double* part, int blocks, double* out) {
+    __shared__ double sh[8][8];
+    __shared__ bool last;
+    // v: mass - count, momentum x, y, z, sum phi rho u_x, sum phi rho - count,
+    // fluid cells; v[7] the particles' sum u_x V
+    double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int nb = gridDim.x;
+    const int rc = (blocks + nb - 1) / nb, r0 = blockIdx.x * rc, r1 = min(blocks, r0 + rc);
+    const int pc = (s.np + nb - 1) / nb, p0 = blockIdx.x * pc, p1 = min(s.np, p0 + pc);
+#pragma unroll 4
+    for (int b = r0 + threadIdx.x; b < r1; b += blockDim.x)
 #pragma unroll
         for (int k = 0; k < 7; ++k) v[k] += part[8 * (long long)b + k];
-#pragma unroll
-    for (int k = 0; k < 7; ++k) sh[k][threadIdx.x] = v[k];
-    __syncthreads();
-    for (int off = 512; off > 0; off >>= 1) {
-        if ((int)threadIdx.x < off)
-#pragma unroll
-            for (int k = 0; k < 7; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + off];
-        __syncthreads();
-    }
-    if (threadIdx.x < 7) out[threadIdx.x == 6 ? 7 : threadIdx.x] = sh[threadIdx.x][0];
-}
-
-// bedload of Eq. (1): sum u_x,p V_p, one block
-__global__ void k_reduce_particles(Dev s, double* out) {
-    __shared__ double sh[32];
-    double qb = 0.0;
-    for (int p = threadIdx.x; p < s.np; p += blockDim.x) {
+    for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
         const double r = s.R[p];
-        qb += s.U[3 * p] * (4.0 / 3.0) * 3.14159265358979323846 * r * r * r;
+        v[7] += s.U[3 * p] * (4.0 / 3.0) * 3.14159265358979323846 * r * r * r;
         if (!isfinite(s.X[3 * p]) || !isfinite(s.U[3 * p])) set_error(s, ERR_NAN);
     }
-    qb = warp_sum(qb);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = qb;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const double w = warp_sum(v[k]);
+        if (lane == 0) sh[k][wid] = w;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        double t = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[threadIdx.x][i];
+        s.rtail[8 * blockIdx.x + threadIdx.x] = t;
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(s.rtail_count, 1) == nb - 1;
+    __syncthreads();
+    if (!last) return;
+    __shared__ double tot[8];
+    if (threadIdx.x < 8) {
+        __threadfence();
+        double t = 0.0;
+        for (int i = 0; i < nb; ++i) t += __ldcg(&s.rtail[8 * i + threadIdx.x]);
+        tot[threadIdx.x] = t;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-        out[6] = t;
+        const double count = tot[6], pool = *s.pool;
+        const double den = tot[5] + count;
+        out[0] = tot[0] + count + pool;
+        out[1] = tot[1];
+        out[2] = tot[2];
+        out[3] = tot[3];
+        out[4] = den > 0 ? tot[4] / den : 0.0;
+        out[5] = (double)*s.wl_count;
+        out[6] = tot[7] / ((double)s.nx * (double)s.ny);
+        out[7] = pool;
+        if (!isfinite(pool)) set_error(s, ERR_NAN);
+        *s.rtail_count = 0;
     }
 }
 
-__global__ void k_reduce_final(Dev s, double* out) {
-    // out[0..5] hold: mass and sum phi rho without the fluid-cell count
-    // (out[7]), mom x, y, z, sum phi rho u_x; out[6] the bedload sum
-    const double qb = out[6];
-    const double count = out[7];
-    out[0] += count;
-    out[5] += count;
-    double num = out[4], den = out[5];
-    out[0] += *s.pool;
-    out[4] = den > 0 ? num / den : 0.0;
-    out[5] = (double)*s.wl_count;
-    out[6] = qb / ((double)s.nx * (double)s.ny);
-    out[7] = *s.pool;
-    if (!isfinite(*s.pool)) set_error(s, ERR_NAN);
+// streaming multiprocessors of the current device (read once)
+static int num_sms() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        n = v > 0 ? v : 1;
+    }
+    return n;
 }
 
 // partial rows of the lattice reduction: the row grid's blocks, then those
@@ -486,7 +697,10 @@ __global__ void k_reduce_final(Dev s, double* out) {
 int reduce_blocks(const Dev& s) {
     const int bx = (s.nx + 255) / 256;
     const int rows = s.ny * s.nz;
-    return bx * (rows < REDUCE_MAX_BY ? rows : REDUCE_MAX_BY) + blocks_for(reduce_edge_pairs(s), 128);
+    const int face = reduce_face_rows(s);
+    const long long edges = reduce_quads(s) ? reduce_edge_pairs(s, reduce_xe(s), true) : reduce_edge_pairs(s, 2, false);
+    return bx * (rows < REDUCE_MAX_BY ? rows : REDUCE_MAX_BY) + (reduce_quads(s) ? bx * (face < REDUCE_MAX_BY ? face : REDUCE_MAX_BY) : 0) +
+           blocks_for(edges, 128);
 }
 
 void launch_reduce(const Dev& s, int last_parity, double* out, cudaStream_t st) {
@@ -499,20 +713,51 @@ void launch_reduce(const Dev& s, int last_parity, double* out, cudaStream_t st) 
     // pairs (128 threads per 256-cell block); after an odd step the edge
     // pairs in a kernel of their own, whose listing needs ny, nz >= 3, nx >= 4
     const bool pairs = s.idx32 && s.nx % 2 == 0 && (last_parity == 0 || (s.nx >= 4 && s.ny >= 3 && s.nz >= 3));
-    if (pairs) {
-        const int eb = last_parity == 1 ? blocks_for(reduce_edge_pairs(s), 128) : 0;
+    if (pairs && reduce_quads(s)) {
+        // 16-bit storage, nx a multiple of 4: quads, the row blocks one
+        // resident wave (12 blocks of 64 threads per SM), so that each thread
+        // strides over rows and the partial rows stay few; after an odd step
+        // the face rows as quads too, and with walls in x the x-end pairs of
+        // every row in the edge kernel
+        const unsigned wave = (unsigned)(12 * num_sms());
+        const unsigned qby = (unsigned)std::min<long long>(std::min(rows, REDUCE_MAX_BY), (wave + bx - 1) / bx);
+        const dim3 qgrid(bx, qby);
+        blocks = (int)(bx * qby);
+        if (last_parity == 0) {
+            if (s.storage == FSLBM_STORE_FP16) k_reduce_quads<__half, 0, 0><<<qgrid, 64, 0, st>>>(s, part);
+            else k_reduce_quads<__nv_bfloat16, 0, 0><<<qgrid, 64, 0, st>>>(s, part);
+        } else {
+            const int face = reduce_face_rows(s);
+            const dim3 fgrid(bx, (unsigned)std::min<long long>(face, qby));
+            const int xe = reduce_xe(s);
+            const int eb = s.per_x ? 0 : blocks_for(reduce_edge_pairs(s, xe, true), 128);
+            double* fpart = part + 8LL * blocks;
+            double* epart = fpart + 8LL * fgrid.x * fgrid.y;
+            if (s.storage == FSLBM_STORE_FP16) {
+                k_reduce_quads<__half, 1, 0><<<qgrid, 64, 0, st>>>(s, part);
+                k_reduce_quads<__half, 1, 1><<<fgrid, 64, 0, st>>>(s, fpart);
+                if (eb) k_reduce_edges<__half><<<eb, 128, 0, st>>>(s, epart, xe, 1);
+            } else {
+                k_reduce_quads<__nv_bfloat16, 1, 0><<<qgrid, 64, 0, st>>>(s, part);
+                k_reduce_quads<__nv_bfloat16, 1, 1><<<fgrid, 64, 0, st>>>(s, fpart);
+                if (eb) k_reduce_edges<__nv_bfloat16><<<eb, 128, 0, st>>>(s, epart, xe, 1);
+            }
+            blocks += (int)(fgrid.x * fgrid.y) + eb;
+        }
+    } else if (pairs) {
+        const int eb = last_parity == 1 ? blocks_for(reduce_edge_pairs(s, 2, false), 128) : 0;
         if (s.storage == FSLBM_STORE_FP32) {
             if (last_parity == 0) k_reduce_pairs<float, 0><<<grid, 128, 0, st>>>(s, part);
             else k_reduce_pairs<float, 1><<<grid, 128, 0, st>>>(s, part);
-            if (eb) k_reduce_edges<float><<<eb, 128, 0, st>>>(s, part + 8LL * blocks);
+            if (eb) k_reduce_edges<float><<<eb, 128, 0, st>>>(s, part + 8LL * blocks, 2, 0);
         } else if (s.storage == FSLBM_STORE_FP16) {
             if (last_parity == 0) k_reduce_pairs<__half, 0><<<grid, 128, 0, st>>>(s, part);
             else k_reduce_pairs<__half, 1><<<grid, 128, 0, st>>>(s, part);
-            if (eb) k_reduce_edges<__half><<<eb, 128, 0, st>>>(s, part + 8LL * blocks);
+            if (eb) k_reduce_edges<__half><<<eb, 128, 0, st>>>(s, part + 8LL * blocks, 2, 0);
         } else {
             if (last_parity == 0) k_reduce_pairs<__nv_bfloat16, 0><<<grid, 128, 0, st>>>(s, part);
             else k_reduce_pairs<__nv_bfloat16, 1><<<grid, 128, 0, st>>>(s, part);
-            if (eb) k_reduce_edges<__nv_bfloat16><<<eb, 128, 0, st>>>(s, part + 8LL * blocks);
+            if (eb) k_reduce_edges<__nv_bfloat16><<<eb, 128, 0, st>>>(s, part + 8LL * blocks, 2, 0);
         }
         blocks += eb;
     } else if (s.storage == FSLBM_STORE_FP32) {
@@ -525,9 +770,7 @@ void launch_reduce(const Dev& s, int last_parity, double* out, cudaStream_t st) 
         if (last_parity == 0) k_reduce_cells<__nv_bfloat16, 0><<<grid, 256, 0, st>>>(s, part);
         else k_reduce_cells<__nv_bfloat16, 1><<<grid, 256, 0, st>>>(s, part);
     }
-    k_reduce_sum<<<1, 1024, 0, st>>>(part, blocks, out);
-    k_reduce_particles<<<1, 1024, 0, st>>>(s, out);
-    k_reduce_final<<<1, 1, 0, st>>>(s, out);
+    k_reduce_tail<<<REDUCE_TAIL_BLOCKS, 256, 0, st>>>(s, part, blocks, out);
 }
 
 // ------------------------------------------------------------ bed height
