@@ -187,8 +187,8 @@ COMPARE_FORMS = (("fp32", "fd"), ("fp16", "fd"), ("bf16", "fd"), ("fp32", "mlp")
 # even and odd steps averaged, from one ncu capture on the 1024x64x128 flume.
 # It is valid while the sweep's sources hash to `sources`, and is scaled to a
 # run by its fluid cells.
-SWEEP_TRAFFIC = {"sources": "185368cbc6c46ea7", "workload": "precision-1024x64x128",
-                 "per_fluid_cell": {"fp16": 195.5, "fp32": 381.7, "bf16": 195.8}}
+SWEEP_TRAFFIC = {"sources": "0566c09866aadf24", "workload": "precision-1024x64x128",
+                 "per_fluid_cell": {"fp16": 194.6, "fp32": 380.2, "bf16": 194.6}}
 SWEEP_SOURCES = ("paper_2301_10674_gb300/csrc/stream_collide.cu", "paper_2301_10674_gb300/csrc/fslbm_dev.cuh",
                  "paper_2301_10674_gb300/csrc/collide_pair.cuh")
 
@@ -456,6 +456,8 @@ def run_ours(args, world, rank, local):
             others[(st_name, nm)] = timed_run(args, w, st_name, theta if nm == "mlp" else None, stream, local,
                                               barrier, world, horizon)
     base = others.get(("fp32", "fd"))
+    runs = dict(others)
+    runs[(args.storage, args.normals)] = head
 
     value = _throughput(world, ncell, args.steps, head["ms"] / 1e3)
     e2e = None
@@ -476,13 +478,20 @@ def run_ours(args, world, rank, local):
     if base is not None:
         vb = _throughput(world, ncell, args.steps, base["ms"] / 1e3)
 
-        def error_vs_base(r):
-            dcol = np.abs(r["column"] - base["column"])
+        def error_vs_base(r, ref=None):
+            ref = base if ref is None else ref
+            dcol = np.abs(r["column"] - ref["column"])
             return {"mass_drift": hdrift(r),
-                    "bed_height_rms_cells": float(np.sqrt(np.mean((r["hb_end"] - base["hb_end"]) ** 2))),
-                    "bulk_ux_rel": float(abs(r["mh"][4] - base["mh"][4]) / max(abs(base["mh"][4]), 1e-30)),
+                    "bed_height_rms_cells": float(np.sqrt(np.mean((r["hb_end"] - ref["hb_end"]) ** 2))),
+                    "bulk_ux_rel": float(abs(r["mh"][4] - ref["mh"][4]) / max(abs(ref["mh"][4]), 1e-30)),
+                    "bulk_ux": float(r["mh"][4]),
                     "surface_profile_cells": {"max_abs": float(dcol.max()), "mean_abs": float(dcol.mean())},
                     "interface_cells": int(r["mh"][5])}
+
+        def error_vs_same_normal(key, r):
+            # the storage's own error: against FP32 storage with the same normal
+            ref = runs.get(("fp32", key[1]))
+            return None if ref is None or ref is r else error_vs_base(r, ref)
 
         forms = []
         for key, r in [((args.storage, args.normals), head)] + list(others.items()):
@@ -492,8 +501,10 @@ def run_ours(args, world, rank, local):
                           "sweep_roofline_frac": _roofline(r, key[0], ncell)["frac"],
                           "bed_spectrum": r["spectrum"],
                           "transport": {k: round(v, 8) for k, v in r["transport"].items()},
-                          "error_vs_fp32_fd": None if r is base else error_vs_base(r)})
+                          "error_vs_fp32_fd": None if r is base else error_vs_base(r),
+                          "error_vs_fp32_same_normal": error_vs_same_normal(key, r) if key[1] == "mlp" else None})
         herr = error_vs_base(head)
+        hsame = error_vs_same_normal((args.storage, args.normals), head)
         comparison = {
             "form": "fp32+fd-normal", "value": round(vb, 2), "unit": UNIT,
             "ms_per_step": round(base["ms"] / args.steps, 4), "speedup": round(value / vb, 4),
@@ -505,6 +516,8 @@ def run_ours(args, world, rank, local):
                 "bulk_ux_rel": herr["bulk_ux_rel"],
                 "bulk_ux": {"head": float(head["mh"][4]), "fp32": float(base["mh"][4])},
                 "interface_cells": {"head": herr["interface_cells"], "fp32": int(base["mh"][5])},
+                # the storage alone: the head form against FP32 storage with the same normal
+                "vs_fp32_same_normal": hsame,
             },
             "forms": forms,
         }
