@@ -95,6 +95,7 @@ def lib():
         L.orc_feq.argtypes = [ctypes.c_double, dp, dp]
         L.orc_normal_stencil.argtypes = [dp, dp]
         L.orc_set_mlp.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+        L.orc_set_mlp_mirror.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.orc_threads.restype = ctypes.c_int
         u8p = ctypes.c_void_p
         L.orc_excess_shares.restype = ctypes.c_int
@@ -252,14 +253,17 @@ class Oracle:
         lib().orc_reduce(self._h, _dp(out))
         return out
 
-    def set_mlp(self, theta, bf16: bool = True) -> None:
+    def set_mlp(self, theta, bf16: bool = True, mirror: bool = False) -> None:
         """Learned normal with parameters theta (6212 values, the layout of
-        oracle.mlp); None restores the finite-difference normal."""
+        oracle.mlp); None restores the finite-difference normal. mirror
+        averages the network over the stencil's mirror images in x and y
+        (R-17g)."""
         if theta is None:
             lib().orc_set_mlp(self._h, None, 0)
             return
         a = np.ascontiguousarray(theta, dtype=np.float64)
         assert a.size == 6212
+        lib().orc_set_mlp_mirror(self._h, int(mirror))
         if lib().orc_set_mlp(self._h, a.ctypes.data, int(bf16)) != 0:
             raise MemoryError("orc_set_mlp")
 

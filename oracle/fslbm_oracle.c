@@ -110,6 +110,7 @@ typedef struct orc {
     int *fixowner;
     double *mlp;              /* learned-normal parameters, NULL: Parker-Youngs */
     int mlp_bf16;             /* round products' operands to bfloat16 */
+    int mlp_mirror;           /* average the network over the x and y mirror images */
 } orc;
 
 /* ---------------------------------------------------------------- tables */
@@ -496,6 +497,41 @@ static double bf16_round(double a)
     return ldexp(nearbyint(ldexp(m, 8)), e - 8);
 }
 
+/* Raw network output (n_x, n_y, n_z, curvature) of one stencil of operand
+ * values */
+static void mlp_raw(const orc* o, const double in[NQ], double out[4])
+{
+    const double *W1 = o->mlp, *b1 = W1 + 64 * 27, *W2 = b1 + 64, *b2 = W2 + 64 * 64, *W3 = b2 + 64,
+                 *b3 = W3 + 4 * 64;
+    const int r = o->mlp_bf16;
+    double h1[64], h2[64];
+    for (int j = 0; j < 64; ++j) {
+        double a = b1[j];
+        for (int i = 0; i < NQ; ++i) a += W1[j * 27 + i] * in[i];
+        h1[j] = a > 0.0 ? (r ? bf16_round(a) : a) : 0.0;
+    }
+    for (int j = 0; j < 64; ++j) {
+        double a = b2[j];
+        for (int i = 0; i < 64; ++i) a += W2[j * 64 + i] * h1[i];
+        h2[j] = a > 0.0 ? (r ? bf16_round(a) : a) : 0.0;
+    }
+    for (int k = 0; k < 4; ++k) {
+        double a = b3[k];
+        for (int i = 0; i < 64; ++i) a += W3[k * 64 + i] * h2[i];
+        out[k] = a;
+    }
+}
+
+/* Stencil index q = (cx+1) + 3(cy+1) + 9(cz+1) under the mirror images of
+ * R-17g: bit 0 of m reverses x, bit 1 reverses y */
+static int mirror_q(int q, int m)
+{
+    int a = q % 3, b = (q / 3) % 3, c = q / 9;
+    if (m & 1) a = 2 - a;
+    if (m & 2) b = 2 - b;
+    return a + 3 * b + 9 * c;
+}
+
 static void mlp_normal(const orc* o, long cell, const double* phi, double n[3], double* kappa)
 {
     int x, y, z;
@@ -514,26 +550,24 @@ static void mlp_normal(const orc* o, long cell, const double* phi, double n[3], 
     if (bad) return;
     /* o->mlp already holds the operand values (weights rounded at set-up
      * when mlp_bf16); inputs and hidden activations are rounded here */
-    const double *W1 = o->mlp, *b1 = W1 + 64 * 27, *W2 = b1 + 64, *b2 = W2 + 64 * 64, *W3 = b2 + 64,
-                 *b3 = W3 + 4 * 64;
-    const int r = o->mlp_bf16;
-    double h1[64], h2[64], out[4];
-    if (r)
+    if (o->mlp_bf16)
         for (int i = 0; i < NQ; ++i) in[i] = bf16_round(in[i]);
-    for (int j = 0; j < 64; ++j) {
-        double a = b1[j];
-        for (int i = 0; i < NQ; ++i) a += W1[j * 27 + i] * in[i];
-        h1[j] = a > 0.0 ? (r ? bf16_round(a) : a) : 0.0;
-    }
-    for (int j = 0; j < 64; ++j) {
-        double a = b2[j];
-        for (int i = 0; i < 64; ++i) a += W2[j * 64 + i] * h1[i];
-        h2[j] = a > 0.0 ? (r ? bf16_round(a) : a) : 0.0;
-    }
-    for (int k = 0; k < 4; ++k) {
-        double a = b3[k];
-        for (int i = 0; i < 64; ++i) a += W3[k * 64 + i] * h2[i];
-        out[k] = a;
+    double out[4];
+    mlp_raw(o, in, out);
+    if (o->mlp_mirror) {
+        /* R-17g: the network on the stencil mirrored in x, in y and in both
+         * (value at q taken from the mirrored index), each output mapped
+         * back (the mirrored components change sign), and the four averaged */
+        for (int m = 1; m < 4; ++m) {
+            double im[NQ], ym[4];
+            for (int q = 0; q < NQ; ++q) im[q] = in[mirror_q(q, m)];
+            mlp_raw(o, im, ym);
+            out[0] += (m & 1) ? -ym[0] : ym[0];
+            out[1] += (m & 2) ? -ym[1] : ym[1];
+            out[2] += ym[2];
+            out[3] += ym[3];
+        }
+        for (int k = 0; k < 4; ++k) out[k] *= 0.25;
     }
     double len = sqrt(out[0] * out[0] + out[1] * out[1] + out[2] * out[2]);
     if (!(len >= 0.5 && len <= 2.0)) return;
@@ -719,6 +753,18 @@ int orc_set_mlp(orc* o, const double* theta, int bf16)
     o->mlp_bf16 = bf16;
     for (long i = 0; i < o->n; ++i)
         if (o->type[i] == T_IFC) normal_at(o, i, o->phi, &o->nrm[3 * i], &o->curv[i]);
+    return 0;
+}
+
+/* Mirror averaging of the learned normal (R-17g): on = 1 averages the
+ * network over the stencil and its mirror images in x, y and both; the
+ * interface normals are recomputed when a network is set. */
+int orc_set_mlp_mirror(orc* o, int on)
+{
+    o->mlp_mirror = on != 0;
+    if (o->mlp)
+        for (long i = 0; i < o->n; ++i)
+            if (o->type[i] == T_IFC) normal_at(o, i, o->phi, &o->nrm[3 * i], &o->curv[i]);
     return 0;
 }
 

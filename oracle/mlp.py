@@ -108,6 +108,32 @@ def adam(theta, g, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
     return theta - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
+def mirror_index(m: int) -> np.ndarray:
+    """Stencil indices under the mirror images of R-17g: index q of the
+    mirrored stencil holds the value at mirror_index(m)[q] of the original
+    (bit 0 of m reverses x, bit 1 reverses y)."""
+    q = np.arange(27)
+    a, b, c = q % 3, (q // 3) % 3, q // 9
+    if m & 1:
+        a = 2 - a
+    if m & 2:
+        b = 2 - b
+    return a + 3 * b + 9 * c
+
+
+def forward_mirror(theta: np.ndarray, X: np.ndarray, bf16: bool = False) -> np.ndarray:
+    """The network averaged over the mirror images in x and y (R-17g): the
+    output for each mirrored stencil, its mirrored components negated back,
+    summed in the order identity, x, y, both, times 1/4."""
+    y = forward(theta, X, bf16)[0].copy()
+    for m in (1, 2, 3):
+        ym = forward(theta, X[:, mirror_index(m)], bf16)[0]
+        y[:, 0] += -ym[:, 0] if m & 1 else ym[:, 0]
+        y[:, 1] += -ym[:, 1] if m & 2 else ym[:, 1]
+        y[:, 2:] += ym[:, 2:]
+    return 0.25 * y
+
+
 def predict_normal(theta, X, bf16: bool = False):
     """Unit normal (toward the gas) and curvature predicted for stencils X."""
     y, _ = forward(theta, X, bf16)

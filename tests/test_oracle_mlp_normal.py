@@ -131,3 +131,81 @@ def test_trained_flavour_forward_matches_numpy():
         assert np.allclose(n_ml[:, z, y, x], n_np[0], atol=1e-12)
         checked += 1
     assert checked > 20
+
+
+# ---------------------------------------------------------------- mirror averaging (R-17g)
+def test_mirror_average_of_a_rotated_gradient_is_its_symmetric_part():
+    """Mirror images M in x and y conjugate the rotation: the average of
+    M R M over the four is (R + R^T)/2, which for a rotation about z by a is
+    diag(cos a, cos a, 1). The oracle must take s diag(cos a, cos a, 1) n_fd
+    normalised, under the same rules as the plain network."""
+    o = _state()
+    n_fd = o.get(F_NORMAL)
+    for deg, s in ((20.0, 0.08), (50.0, 0.08)):
+        R = _rot_z(deg)
+        S = np.diag([math.cos(math.radians(deg)), math.cos(math.radians(deg)), 1.0])
+        o.set_mlp(_network(R, s), bf16=False, mirror=True)
+        n_ml = o.get(F_NORMAL)
+        taken = 0
+        for (z, y, x), (g, clear) in _expected(o, R, s).items():
+            fd = n_fd[:, z, y, x]
+            raw = -s * (S @ g)
+            L = np.linalg.norm(raw)
+            m = raw / L
+            use = clear and 0.5 <= L <= 2.0 and float(m @ fd) >= math.cos(math.radians(30.0))
+            want = m if use else fd
+            assert np.allclose(n_ml[:, z, y, x], want, atol=1e-12), ((z, y, x), deg, use)
+            taken += use
+        assert taken > 0
+        o.set_mlp(None)
+
+
+def _stencil(t, phi, z, y, x):
+    nx = t.shape[2]
+    X = np.zeros(27)
+    for q in range(27):
+        c = C[q].astype(int)
+        tt = t[z + c[2], y + c[1], (x + c[0]) % nx]
+        X[q] = 1.0 if tt == LIQUID else (min(max(phi[z + c[2], y + c[1], (x + c[0]) % nx], 0), 1)
+                                         if tt == INTERFACE else 0.0)
+    return X
+
+
+def test_mirror_averaged_forward_matches_numpy():
+    """Random weights with BF16 operands: where the oracle takes the
+    network, its normal is numpy's mirror-averaged forward, normalised."""
+    o = _state()
+    rng = np.random.default_rng(7)
+    theta = mlp.round_bf16(_network(np.eye(3), 0.08) + rng.normal(0, 0.02, mlp.NPARAM))
+    o.set_mlp(theta, bf16=True, mirror=True)
+    n_ml = o.get(F_NORMAL)
+    t, phi = o.get(F_TYPE), o.get(F_PHI)
+    n_fd = _state().get(F_NORMAL)
+    checked = 0
+    for z, y, x in zip(*np.nonzero(t == INTERFACE)):
+        if np.array_equal(n_ml[:, z, y, x], n_fd[:, z, y, x]):
+            continue
+        yv = mlp.forward_mirror(theta, _stencil(t, phi, z, y, x)[None, :], bf16=True)[0]
+        assert np.allclose(n_ml[:, z, y, x], yv[:3] / np.linalg.norm(yv[:3]), atol=1e-12)
+        checked += 1
+    assert checked > 20
+
+
+def test_flat_layer_keeps_a_vertical_normal_only_with_mirror_averaging():
+    """A flat layer is its own mirror image in x and y, so the averaged
+    normal has no horizontal component at all; the plain network of the
+    same weights tilts it."""
+    nx, ny, nz = 12, 8, 12
+    o = Oracle(OracleParams(nx=nx, ny=ny, nz=nz, omega=1.6, g=(0, 0, 0)))
+    o.init_surface(np.full((ny, nx), 6.37))
+    rng = np.random.default_rng(11)
+    theta = mlp.round_bf16(_network(np.eye(3), 0.08) + rng.normal(0, 0.02, mlp.NPARAM))
+    ifc = o.get(F_TYPE) == INTERFACE
+    assert ifc.sum() == nx * ny
+    ifc[:, [0, ny - 1], :] = False   # blocks with a y wall keep the finite-difference normal
+    o.set_mlp(theta, bf16=True, mirror=False)
+    plain = o.get(F_NORMAL)[:, ifc]
+    o.set_mlp(theta, bf16=True, mirror=True)
+    avg = o.get(F_NORMAL)[:, ifc]
+    assert np.abs(plain[:2]).max() > 1e-3
+    assert np.all(avg[:2] == 0.0) and np.all(avg[2] > 0.99)
