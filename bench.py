@@ -40,6 +40,7 @@ import numpy as np  # noqa: E402
 UNIT = "MLUPS"
 STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
 LINK_MODE = 0   # where the particle links are taken (--links: 0 the library's choice, 1 solid side, 2 fluid side)
+MLP_MIRROR = True   # learned normal averaged over the mirror images in x and y (--no-mlp-mirror: the plain network)
 ELEM = {"fp32": 4, "fp16": 2, "bf16": 2}
 
 
@@ -162,7 +163,7 @@ def run_oracle(w, steps: int, warmup: int, crop_nx: int, theta=None) -> dict:
     if theta is not None:
         from paper_2301_10674_gb300 import fslbm as F
         bits = F.bf16_bits(theta).astype(np.uint32) << 16
-        o.set_mlp(bits.view(np.float32).astype(np.float64), bf16=True)
+        o.set_mlp(bits.view(np.float32).astype(np.float64), bf16=True, mirror=MLP_MIRROR)
     o.step(warmup)
     t0 = time.perf_counter()
     o.step(steps)
@@ -330,7 +331,7 @@ def timed_run(args, w, storage_name, theta, stream, local, barrier, world, horiz
     sim = F.Simulation.from_workload(w, storage=STORAGE[storage_name], stream=stream,
                                      link_mode=LINK_MODE)
     if theta is not None:
-        sim.set_normal_model(theta)
+        sim.set_normal_model(theta, mirror=MLP_MIRROR)
     m0 = sim.reduce()
     sim.step(args.warmup)
     sim.sync()
@@ -529,6 +530,7 @@ def run_ours(args, world, rank, local):
         "config": {"workload": w.name, "form": form, "lattice": [w.nx, w.ny, w.nz], "cells": ncell,
                    "spheres": w.nspheres, "spheres_nominal": w.spheres_nominal, "storage": args.storage,
                    "normals": args.normals,
+                   "normal_mirror_average": bool(MLP_MIRROR) if args.normals == "mlp" else None,
                    "particle_links": {0: "library default", 1: "solid-side pass", 2: "fluid side (bed kernel)"}[LINK_MODE],
                    "cells_by_type": {"gas": int(cb[0]), "liquid": int(cb[1]), "interface": int(cb[2]),
                                      "solid": int(cb[3])},
@@ -570,6 +572,7 @@ def run_e2e(args, w, storage, theta, stream, world):
     t1 = time.perf_counter()
     F._check(F.fslbm_add_spheres(h, xyz, rad, fix), "fslbm_add_spheres")
     if bits is not None:
+        F._check(F.fslbm_set_normal_mirror(h, MLP_MIRROR), "fslbm_set_normal_mirror")
         F._check(F.fslbm_set_normal_model(h, bits), "fslbm_set_normal_model")
     t2 = time.perf_counter()
     t_step = t_red = 0.0
@@ -634,7 +637,7 @@ def run_precision_study(args):
         sim = F.Simulation.from_workload(w, storage=STORAGE[st_name], stream=stream,
                                          link_mode=LINK_MODE)
         if nm == "mlp":
-            sim.set_normal_model(theta)
+            sim.set_normal_model(theta, mirror=MLP_MIRROR)
         m0 = sim.reduce()[0]
         sim.step(steps)
         st = _state(sim.get(F.FIELD_TYPE), sim.get(F.FIELD_PHI), sim.reduce(), sim.get(F.FIELD_U)[0])
@@ -651,7 +654,7 @@ def run_precision_study(args):
         o.add_spheres(w.xyz, w.radius, w.fixed)
         if nm == "mlp":
             bits = F.bf16_bits(theta).astype(np.uint32) << 16
-            o.set_mlp(bits.view(np.float32).astype(np.float64), bf16=True)
+            o.set_mlp(bits.view(np.float32).astype(np.float64), bf16=True, mirror=MLP_MIRROR)
         m0 = o.reduce()[0]
         t0 = time.perf_counter()
         o.step(steps)
@@ -749,6 +752,8 @@ def main():
                     help="steps of the mid-flume run whose logged stencils join the training (0: none)")
     ap.add_argument("--links", type=int, choices=(0, 1, 2), default=0,
                     help="particle links: 0 the library's choice, 1 pass over the solid cells, 2 fluid side")
+    ap.add_argument("--mlp-mirror", action=argparse.BooleanOptionalAction, default=True,
+                    help="average the learned normal over the mirror images in x and y")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=5)
@@ -765,8 +770,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    global LINK_MODE
+    global LINK_MODE, MLP_MIRROR
     LINK_MODE = args.links
+    MLP_MIRROR = args.mlp_mirror
     world, rank, local = _dist()
     if args.precision_study:
         print(json.dumps(run_precision_study(args)), flush=True)

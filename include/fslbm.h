@@ -402,6 +402,22 @@ int fslbm_reduce_fields_noalloc(const double* pdf, const uint8_t* type, const do
  * Stream-ordered; synchronises the stream. FSLBM_EINVAL for another size. */
 int fslbm_set_normal_model(fslbm* s, const uint16_t* w, int64_t n_params);
 
+/* Mirror averaging of the learned normal (a reading for the normal the
+ * free-surface condition of Section 2.1 uses; the paper has no learned
+ * normal): on = 1 evaluates the network on the block and on its mirror
+ * images in x, in y and in both (block index q takes the value of the
+ * mirrored index), negates the mirrored components of each output, and
+ * averages the four raw outputs before the length and angle rules above.
+ * The normal is then exactly equivariant under those mirrors: a block that
+ * is its own mirror image gets no component along the mirrored axis (a flat
+ * horizontal surface keeps a vertical normal), where the plain network can
+ * tilt it by a fraction of a degree. The products remain BF16 operands with
+ * FP32 sums; the averaging is FP32. on = 0 (the default) is the plain
+ * network. Recomputes the interface normals of the current state when a
+ * network is set. Synchronises the stream. FSLBM_EINVAL for another value
+ * of on or a missing handle. */
+int fslbm_set_normal_mirror(fslbm* s, int32_t on);
+
 /* Learned-normal counters since the last fslbm_set_normal_model:
  * out[0] normals evaluated, out[1] normals taken from the network (the rest
  * fell back). Zeros under the finite-difference normal. Synchronises. */

@@ -12,6 +12,7 @@
 
 namespace fsl {
 void mlp_from_bf16_host(const uint16_t* w, MlpBf16& h);
+void mlp_mirror_w1_host(const uint16_t* w, __nv_bfloat16* out);
 }
 
 namespace fsl {
@@ -49,6 +50,7 @@ struct fslbm {
     int64_t ctrl_interval;
     MlpBf16* mlp_dev;              // operand copies of the learned normal
     unsigned long long* mlp_stats;
+    __nv_bfloat16* mlp_w1m_dev;    // first layer of the mirror images (R-17g)
     // side stream of the DEM half of a step (overlapped with the free-surface
     // conversion), and the events that fork it from and join it to st
     cudaStream_t side;
@@ -201,6 +203,9 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     s->ctrl_interval = 0;
     s->mlp_dev = nullptr;
     s->mlp_stats = nullptr;
+    s->mlp_w1m_dev = nullptr;
+    s->d.mlp_w1m = nullptr;
+    s->d.mlp_mirror = 0;
     s->side = nullptr;
     s->ev_fork = s->ev_join = nullptr;
     for (int k = 0; k < 2; ++k) {
@@ -972,28 +977,45 @@ int fslbm_set_normal_model(fslbm* s, const uint16_t* w, int64_t n_params) {
     if (!s) return FSLBM_EINVAL;
     if (s->host_err) return s->host_err;
     Dev& d = s->d;
+    MlpBf16 h;
+    std::vector<__nv_bfloat16> w1m;
     if (!w) {
         if (n_params != 0) return FSLBM_EINVAL;
         d.mlp = nullptr;
         d.mlp_stats = nullptr;
+        d.mlp_w1m = nullptr;
         s->p.normal_model = 0;
     } else {
         if (n_params != MLP_NPARAM) return FSLBM_EINVAL;
         bool ok = true;
         if (!s->mlp_dev) s->mlp_dev = dalloc<MlpBf16>(s, 1, ok);
         if (!s->mlp_stats) s->mlp_stats = dalloc<unsigned long long>(s, 2, ok);
+        if (!s->mlp_w1m_dev) s->mlp_w1m_dev = dalloc<__nv_bfloat16>(s, 3 * MLP_H * 32, ok);
         if (!ok) return FSLBM_ENOMEM;
-        MlpBf16 h;
         mlp_from_bf16_host(w, h);
+        w1m.resize(3 * MLP_H * 32);
+        mlp_mirror_w1_host(w, w1m.data());
         cudaMemcpyAsync(s->mlp_dev, &h, sizeof(h), cudaMemcpyHostToDevice, s->st);
+        cudaMemcpyAsync(s->mlp_w1m_dev, w1m.data(), w1m.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice,
+                        s->st);
         cudaMemsetAsync(s->mlp_stats, 0, 2 * sizeof(unsigned long long), s->st);
         d.mlp = s->mlp_dev;
         d.mlp_stats = s->mlp_stats;
+        d.mlp_w1m = s->mlp_w1m_dev;
         s->p.normal_model = 1;
     }
     s->graph_dirty = true;
     launch_normals(d, d.nrm, s->st);
-    return sync_check(s);   // h stays alive until the copy has completed
+    return sync_check(s);   // h and w1m stay alive until the copies have completed
+}
+
+int fslbm_set_normal_mirror(fslbm* s, int32_t on) {
+    if (!s || (on != 0 && on != 1)) return FSLBM_EINVAL;
+    if (s->host_err) return s->host_err;
+    s->d.mlp_mirror = on;
+    s->graph_dirty = true;
+    if (s->d.mlp) launch_normals(s->d, s->d.nrm, s->st);
+    return sync_check(s);
 }
 
 int fslbm_normal_stats(fslbm* s, uint64_t out[2]) {

@@ -542,6 +542,27 @@ __global__ void __launch_bounds__(128) k_mlp_infer(const MlpBf16* __restrict__ W
     }
 }
 
+// First-layer operands of the mirror images of R-17g, built on the host from
+// BF16 bit patterns: block m - 1 (m = 1 mirrors x, 2 mirrors y, 3 both) is W1
+// with input column q taken from the mirrored column, so that it applied to
+// a stencil gives W1 applied to the mirrored stencil.
+void mlp_mirror_w1_host(const uint16_t* w, __nv_bfloat16* out) {
+    for (int m = 1; m < 4; ++m)
+        for (int r = 0; r < MLP_H; ++r)
+            for (int c = 0; c < 32; ++c) {
+                __nv_bfloat16_raw v;
+                v.x = 0;   // +0.0: the padding columns 27..31
+                if (c < MLP_IN) {
+                    int a = c % 3, b = (c / 3) % 3;
+                    const int z = c / 9;
+                    if (m & 1) a = 2 - a;
+                    if (m & 2) b = 2 - b;
+                    v.x = w[OFF_W1 + r * MLP_IN + a + 3 * b + 9 * z];
+                }
+                out[(m - 1) * MLP_H * 32 + r * 32 + c] = __nv_bfloat16(v);
+            }
+}
+
 // operand copies built on the host from BF16 bit patterns
 void mlp_from_bf16_host(const uint16_t* w, MlpBf16& h) {
     auto f = [](uint16_t b) {

@@ -72,7 +72,10 @@ __device__ __forceinline__ void relu_frag(const float (&z)[8][4], int kk, uint32
 // Forward pass from the input fragments x[kk] (k-tiles 0 and 1: inputs
 // 0..15 and 16..31, inputs 27..31 zero). W may live in global or shared
 // memory.
-__device__ __forceinline__ void mlp_forward(const MlpBf16& W, const uint32_t (&x)[2][4], MlpAct& o) {
+// w1: the first layer's operands (MLP_H x 32, (out, in)); W.w1, or a copy
+// with its input columns permuted (the mirror images of R-17g).
+__device__ __forceinline__ void mlp_forward_w1(const MlpBf16& W, const __nv_bfloat16* w1, const uint32_t (&x)[2][4],
+                                               MlpAct& o) {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
@@ -80,7 +83,7 @@ __device__ __forceinline__ void mlp_forward(const MlpBf16& W, const uint32_t (&x
         float d[4] = {b0, b1, b0, b1};
 #pragma unroll
         for (int kk = 0; kk < 2; ++kk) {
-            const __nv_bfloat16* row = W.w1 + (8 * nt + g) * 32 + 16 * kk + 2 * t;
+            const __nv_bfloat16* row = w1 + (8 * nt + g) * 32 + 16 * kk + 2 * t;
             mma_bf16(d, x[kk][0], x[kk][1], x[kk][2], x[kk][3], ld_pair(row), ld_pair(row + 8));
         }
 #pragma unroll
@@ -114,6 +117,10 @@ __device__ __forceinline__ void mlp_forward(const MlpBf16& W, const uint32_t (&x
 #pragma unroll
         for (int k = 0; k < 4; ++k) o.y[k] = d[k];
     }
+}
+
+__device__ __forceinline__ void mlp_forward(const MlpBf16& W, const uint32_t (&x)[2][4], MlpAct& o) {
+    mlp_forward_w1(W, W.w1, x, o);
 }
 
 // The four outputs of rows g and g + 8, gathered into every lane of group g

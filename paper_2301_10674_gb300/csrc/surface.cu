@@ -74,7 +74,7 @@ __global__ void k_normals(Dev s, float4* out, const int* list, const int* countp
 // raw length outside [1/2, 2]) and the check on the network (its normal more
 // than 30 degrees away falls back too). out[c] = (n, curvature), curvature 0 where the fallback is
 // taken.
-__global__ void __launch_bounds__(128) k_mlp_normals(Dev s, float4* out, const int* list, const int* countp) {
+__global__ void __launch_bounds__(128, 5) k_mlp_normals(Dev s, float4* out, const int* list, const int* countp) {
     const int count = min(*countp, s.wl_cap);
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -139,10 +139,40 @@ __global__ void __launch_bounds__(128) k_mlp_normals(Dev s, float4* out, const i
             xf[kk][2] = pack_bf16(v[0][4 * kk + 2], v[0][4 * kk + 3]);
             xf[kk][3] = pack_bf16(v[1][4 * kk + 2], v[1][4 * kk + 3]);
         }
+        // R-17g with mlp_mirror: the network also on the stencil mirrored in
+        // x, in y and in both (the first layer with permuted columns on the
+        // same inputs), each output mapped back and the four averaged
         MlpAct act;
-        mlp_forward(*s.mlp, xf, act);
         float y[2][4];
-        mlp_outputs(act, y[0], y[1]);
+        const int passes = s.mlp_mirror ? 4 : 1;
+#pragma unroll 1
+        for (int m = 0; m < passes; ++m) {
+            const MlpBf16* W = s.mlp;
+            // the operands are reloaded in every pass rather than held in
+            // registers across passes
+            asm volatile("" : "+l"(W));
+            mlp_forward_w1(*W, m == 0 ? W->w1 : s.mlp_w1m + (m - 1) * MLP_H * 32, xf, act);
+            float ym[2][4];
+            mlp_outputs(act, ym[0], ym[1]);
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                if (m == 0) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) y[r][k] = ym[r][k];
+                } else {
+                    y[r][0] += (m & 1) ? -ym[r][0] : ym[r][0];
+                    y[r][1] += (m & 2) ? -ym[r][1] : ym[r][1];
+                    y[r][2] += ym[r][2];
+                    y[r][3] += ym[r][3];
+                }
+            }
+        }
+        if (passes == 4) {
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) y[r][k] *= 0.25f;
+        }
         if (t < 2 && cell[t] >= 0) {
             const int c = cell[t];
             const float gl = sqrtf(gr[t][0] * gr[t][0] + gr[t][1] * gr[t][1] + gr[t][2] * gr[t][2]);

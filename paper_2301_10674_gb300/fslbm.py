@@ -47,7 +47,7 @@ EXPORTED = (
     "fslbm_get_fields", "fslbm_set_fields", "fslbm_reduce", "fslbm_sync", "fslbm_steps_done",
     "fslbm_num_spheres", "fslbm_invariant_violations", "fslbm_timing", "fslbm_timing_read",
     "fslbm_cell_counts", "fslbm_reduce_fields_noalloc", "fslbm_destroy", "fslbm_strerror",
-    "fslbm_set_normal_model", "fslbm_normal_stats", "fslbm_mlp_stencils", "fslbm_mlp_gradient",
+    "fslbm_set_normal_model", "fslbm_set_normal_mirror", "fslbm_normal_stats", "fslbm_mlp_stencils", "fslbm_mlp_gradient",
     "fslbm_mlp_train", "fslbm_mlp_infer", "fslbm_bed_height", "fslbm_set_body_force",
     "fslbm_get_body_force", "fslbm_set_flow_control", "fslbm_set_wait_limit", "fslbm_transport_numbers",
     "fslbm_bed_spectrum", "fslbm_log_stencils",
@@ -136,6 +136,7 @@ def load():
                                      ctypes.POINTER(ctypes.c_double), vp]
     L.fslbm_reduce_fields_noalloc.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), vp, vp]
     L.fslbm_set_normal_model.argtypes = [vp, vp, ctypes.c_int64]
+    L.fslbm_set_normal_mirror.argtypes = [vp, ctypes.c_int32]
     L.fslbm_normal_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
     L.fslbm_mlp_stencils.argtypes = [vp, ctypes.c_int64, vp, vp, vp]
     L.fslbm_mlp_gradient.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.c_double, ctypes.c_double, vp, vp, vp]
@@ -243,6 +244,10 @@ def fslbm_set_normal_model(h, w_bf16_bits) -> int:
         return load().fslbm_set_normal_model(h, None, 0)
     w = np.ascontiguousarray(w_bf16_bits, np.uint16).reshape(-1)
     return load().fslbm_set_normal_model(h, ctypes.c_void_p(w.ctypes.data), int(w.size))
+
+
+def fslbm_set_normal_mirror(h, on: bool) -> int:
+    return load().fslbm_set_normal_mirror(h, int(bool(on)))
 
 
 def fslbm_normal_stats(h) -> tuple[int, np.ndarray]:
@@ -411,14 +416,17 @@ class Simulation:
         _check(rc, "fslbm_reduce")
         return out
 
-    def set_normal_model(self, theta_or_bits):
+    def set_normal_model(self, theta_or_bits, mirror: bool = False):
         """Learned normal from FP32 parameters (rounded to BF16) or BF16 bit
-        patterns (uint16); None returns to the finite-difference normal."""
+        patterns (uint16); None returns to the finite-difference normal.
+        mirror averages the network over the block's mirror images in x and y
+        (fslbm_set_normal_mirror)."""
         if theta_or_bits is None:
             _check(fslbm_set_normal_model(self.h, None), "fslbm_set_normal_model")
             return
         a = np.asarray(theta_or_bits)
         bits = a if a.dtype == np.uint16 else bf16_bits(a)
+        _check(fslbm_set_normal_mirror(self.h, mirror), "fslbm_set_normal_mirror")
         _check(fslbm_set_normal_model(self.h, bits), "fslbm_set_normal_model")
 
     def normal_stats(self) -> np.ndarray:

@@ -170,15 +170,16 @@ def _wavy(w):
     return 20.0 + 3.0 * np.sin(2 * np.pi * x)[None, :] + 1.5 * np.cos(2 * np.pi * y)[:, None]
 
 
-def _near_threshold(theta, X, fd):
-    y, _ = OM.forward(theta, X[None, :], bf16=True)
+def _near_threshold(theta, X, fd, mirror=False):
+    y = OM.forward_mirror(theta, X[None, :], bf16=True) if mirror else OM.forward(theta, X[None, :], bf16=True)[0]
     n = y[0, :3]
     L = np.linalg.norm(n)
     c = float(n @ fd) / L if L > 0 else 0.0
     return min(abs(L - 0.5), abs(L - 2.0)) < 1e-2 or abs(c - math.cos(math.radians(30))) < 1e-2
 
 
-def test_in_step_normals_match_the_oracle():
+@pytest.mark.parametrize("mirror", [False, True])
+def test_in_step_normals_match_the_oracle(mirror):
     w = W.tiny()
     w.generate()
     rng = np.random.default_rng(5)
@@ -189,8 +190,8 @@ def test_in_step_normals_match_the_oracle():
     sim.init_surface(h)
     o.init_surface(h)
     fd_g = sim.get(F.FIELD_NORMAL)
-    sim.set_normal_model(theta)
-    o.set_mlp(theta, bf16=True)
+    sim.set_normal_model(theta, mirror=mirror)
+    o.set_mlp(theta, bf16=True, mirror=mirror)
     ng, no = sim.get(F.FIELD_NORMAL), o.get(O.F_NORMAL)
     fd_o = oracle_from_workload(w)
     fd_o.init_surface(h)
@@ -213,7 +214,7 @@ def test_in_step_normals_match_the_oracle():
                 tt = t[z + c[2], y + c[1], (x + c[0]) % w.nx]
                 X[q] = 1.0 if tt == O.LIQUID else (min(max(phi[z + c[2], y + c[1], (x + c[0]) % w.nx], 0), 1)
                                                    if tt == O.INTERFACE else 0.0)
-            assert _near_threshold(theta, X, fd[:, z, y, x]), (z, y, x)
+            assert _near_threshold(theta, X, fd[:, z, y, x], mirror), (z, y, x)
             differ += 1
     assert taken > 0.3 * len(ifc) and differ <= 0.01 * len(ifc)
     ev, tk = sim.normal_stats()
@@ -226,6 +227,37 @@ def test_in_step_normals_match_the_oracle():
     m_g = sim.reduce()[0]
     m_o = o.reduce()[0]
     assert abs(m_g - m_o) < 1e-5 * m_o
+    sim.close()
+
+
+def test_mirror_averaged_normal_of_a_flat_layer_is_vertical():
+    """A flat layer is its own mirror image in x and y: with the mirror
+    averaging the learned normal has no horizontal component beyond the FP32
+    sums' rounding, where the plain network of the same weights tilts it;
+    both agree with the oracle."""
+    w = W.tiny()
+    w.generate()
+    rng = np.random.default_rng(11)
+    theta = OM.round_bf16(_py_network() + rng.normal(0.0, 0.02, OM.NPARAM))
+    h = np.full((w.ny, w.nx), 20.37)
+    sim = F.Simulation.from_workload(w)
+    o = oracle_from_workload(w)
+    sim.init_surface(h)
+    o.init_surface(h)
+    ifc = o.get(O.F_TYPE) == O.INTERFACE
+    assert ifc.sum() == w.nx * w.ny
+    ifc[:, [0, w.ny - 1], :] = False        # blocks with a y wall keep the finite-difference normal
+    for mirror in (False, True):
+        sim.set_normal_model(theta, mirror=mirror)
+        o.set_mlp(theta, bf16=True, mirror=mirror)
+        ng = sim.get(F.FIELD_NORMAL)[:, ifc]
+        no = o.get(O.F_NORMAL)[:, ifc]
+        assert np.abs(ng - no).max() < 1e-4, mirror
+        tilt = np.abs(ng[:2]).max()
+        if mirror:
+            assert tilt < 1e-6 and np.all(np.abs(no[:2]) == 0.0)
+        else:
+            assert tilt > 1e-3
     sim.close()
 
 
