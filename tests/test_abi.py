@@ -65,4 +65,5 @@ def test_new_entry_points_reject_a_missing_handle(lib):
     assert lib.fslbm_get_body_force(None, g) == -1
     assert lib.fslbm_set_flow_control(None, 1e-3, 1e-4, 100) == -1
     assert lib.fslbm_set_wait_limit(None, 0) == -1
+    assert lib.fslbm_set_normal_mirror(None, 1) == -1
     assert lib.fslbm_strerror(-8).decode() == "a bounded device wait gave up"

@@ -271,6 +271,7 @@ def test_missing_weights_are_a_state_error():
     sim.set_normal_model(None)
     sim.step(1)
     assert F.fslbm_set_normal_model(sim.h, np.zeros(100, np.uint16)) == -1
+    assert F.load().fslbm_set_normal_mirror(sim.h, 2) == -1     # on must be 0 or 1
     sim.close()
 
 
