@@ -286,6 +286,20 @@ def train_normal_model(stream, n_stencils: int, steps: int, seed: int = 4,
     if log_steps > 0:
         out = torch.empty((len(hf), 4), dtype=torch.float32, device="cuda")
         F._check(F.fslbm_mlp_infer(theta, hf, len(hf), out, stream.cuda_stream), "fslbm_mlp_infer")
+        if MLP_MIRROR:
+            # the network as the step uses it: averaged over the stencils'
+            # mirror images in x, y and both, each output mapped back
+            acc = out.clone()
+            q = np.arange(27)
+            for m in (1, 2, 3):
+                a = 2 - q % 3 if m & 1 else q % 3
+                b = 2 - (q // 3) % 3 if m & 2 else (q // 3) % 3
+                idx = torch.from_numpy(a + 3 * b + 9 * (q // 9)).cuda()
+                hm = hf[:, idx].contiguous()
+                F._check(F.fslbm_mlp_infer(theta, hm, len(hf), out, stream.cuda_stream), "fslbm_mlp_infer")
+                sign = torch.tensor([-1.0 if m & 1 else 1.0, -1.0 if m & 2 else 1.0, 1.0, 1.0], device="cuda")
+                acc += out * sign
+            out = acc * 0.25
         yv = out.cpu().numpy().astype(np.float64)
         lab = ht.cpu().numpy().astype(np.float64)
         fdn = hfd.cpu().numpy().astype(np.float64)[:, :3]
@@ -295,6 +309,7 @@ def train_normal_model(stream, n_stencils: int, steps: int, seed: int = 4,
         e_fd = _angles(fdn, lab[:, :3])
         e_ml = _angles(np.where(use[:, None], nml, fdn), lab[:, :3])
         logged = {"workload": log_name, "steps": log_steps, "train": n_logged, "held_out": int(len(hf)),
+                  "mirror_average": bool(MLP_MIRROR),
                   "label": "height function (3x3 columns of 7 cells)",
                   "fd_deg": round(float(e_fd.mean()), 4), "learned_deg": round(float(e_ml.mean()), 4),
                   "taken": round(float(use.mean()), 4),

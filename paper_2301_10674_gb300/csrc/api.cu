@@ -13,6 +13,7 @@
 namespace fsl {
 void mlp_from_bf16_host(const uint16_t* w, MlpBf16& h);
 void mlp_mirror_w1_host(const uint16_t* w, __nv_bfloat16* out);
+void mlp_frag_host(const MlpBf16& h, const __nv_bfloat16* w1m, MlpFrag& G);
 }
 
 namespace fsl {
@@ -50,7 +51,7 @@ struct fslbm {
     int64_t ctrl_interval;
     MlpBf16* mlp_dev;              // operand copies of the learned normal
     unsigned long long* mlp_stats;
-    __nv_bfloat16* mlp_w1m_dev;    // first layer of the mirror images (R-17g)
+    MlpFrag* mlp_frag_dev;         // in-step weights in fragment order, mirror images included
     // side stream of the DEM half of a step (overlapped with the free-surface
     // conversion), and the events that fork it from and join it to st
     cudaStream_t side;
@@ -203,8 +204,8 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     s->ctrl_interval = 0;
     s->mlp_dev = nullptr;
     s->mlp_stats = nullptr;
-    s->mlp_w1m_dev = nullptr;
-    s->d.mlp_w1m = nullptr;
+    s->mlp_frag_dev = nullptr;
+    s->d.mlp_frag = nullptr;
     s->d.mlp_mirror = 0;
     s->side = nullptr;
     s->ev_fork = s->ev_join = nullptr;
@@ -979,34 +980,36 @@ int fslbm_set_normal_model(fslbm* s, const uint16_t* w, int64_t n_params) {
     Dev& d = s->d;
     MlpBf16 h;
     std::vector<__nv_bfloat16> w1m;
+    std::vector<MlpFrag> frag;
     if (!w) {
         if (n_params != 0) return FSLBM_EINVAL;
         d.mlp = nullptr;
         d.mlp_stats = nullptr;
-        d.mlp_w1m = nullptr;
+        d.mlp_frag = nullptr;
         s->p.normal_model = 0;
     } else {
         if (n_params != MLP_NPARAM) return FSLBM_EINVAL;
         bool ok = true;
         if (!s->mlp_dev) s->mlp_dev = dalloc<MlpBf16>(s, 1, ok);
         if (!s->mlp_stats) s->mlp_stats = dalloc<unsigned long long>(s, 2, ok);
-        if (!s->mlp_w1m_dev) s->mlp_w1m_dev = dalloc<__nv_bfloat16>(s, 3 * MLP_H * 32, ok);
+        if (!s->mlp_frag_dev) s->mlp_frag_dev = dalloc<MlpFrag>(s, 1, ok);
         if (!ok) return FSLBM_ENOMEM;
         mlp_from_bf16_host(w, h);
         w1m.resize(3 * MLP_H * 32);
         mlp_mirror_w1_host(w, w1m.data());
+        frag.resize(1);
+        mlp_frag_host(h, w1m.data(), frag[0]);
         cudaMemcpyAsync(s->mlp_dev, &h, sizeof(h), cudaMemcpyHostToDevice, s->st);
-        cudaMemcpyAsync(s->mlp_w1m_dev, w1m.data(), w1m.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice,
-                        s->st);
+        cudaMemcpyAsync(s->mlp_frag_dev, frag.data(), sizeof(MlpFrag), cudaMemcpyHostToDevice, s->st);
         cudaMemsetAsync(s->mlp_stats, 0, 2 * sizeof(unsigned long long), s->st);
         d.mlp = s->mlp_dev;
         d.mlp_stats = s->mlp_stats;
-        d.mlp_w1m = s->mlp_w1m_dev;
+        d.mlp_frag = s->mlp_frag_dev;
         s->p.normal_model = 1;
     }
     s->graph_dirty = true;
     launch_normals(d, d.nrm, s->st);
-    return sync_check(s);   // h and w1m stay alive until the copies have completed
+    return sync_check(s);   // h and frag stay alive until the copies have completed
 }
 
 int fslbm_set_normal_mirror(fslbm* s, int32_t on) {

@@ -159,10 +159,10 @@ struct Dev {
     // and counters of stencils evaluated / normals taken from the network
     const struct MlpBf16* mlp;
     unsigned long long* mlp_stats;
-    // R-17g: the first layer with its input columns mirrored in x, y and
-    // both (3 x 64 x 32 BF16 operands), and whether the normal averages the
-    // network over those mirror images
-    const __nv_bfloat16* mlp_w1m;
+    // the weights in fragment order for the in-step forward pass, with the
+    // first layers of the mirror images of R-17g, and whether the normal
+    // averages the network over those mirror images
+    const struct MlpFrag* mlp_frag;
     int mlp_mirror;
     int* shared;
     int* act; int* act_count;

@@ -563,6 +563,37 @@ void mlp_mirror_w1_host(const uint16_t* w, __nv_bfloat16* out) {
             }
 }
 
+// The in-step weights in fragment order (MlpFrag), from the operand copies
+// h and the mirrored first layers w1m: lane (g, t) of an mma over n-tile nt
+// and k-tile kk takes row 8 nt + g (g for the output layer) and the column
+// pairs 16 kk + 2t and 16 kk + 2t + 8, packed low element first.
+void mlp_frag_host(const MlpBf16& h, const __nv_bfloat16* w1m, MlpFrag& G) {
+    auto pair = [](const __nv_bfloat16* p) {
+        __nv_bfloat16_raw lo = p[0], hi = p[1];
+        return (uint32_t)lo.x | ((uint32_t)hi.x << 16);
+    };
+    for (int lane = 0; lane < 32; ++lane) {
+        const int g = lane >> 2, t = lane & 3;
+        for (int m = 0; m < 4; ++m) {
+            const __nv_bfloat16* w1 = m == 0 ? h.w1 : w1m + (m - 1) * MLP_H * 32;
+            for (int nt = 0; nt < 8; ++nt)
+                for (int kk = 0; kk < 2; ++kk) {
+                    const __nv_bfloat16* r = w1 + (8 * nt + g) * 32 + 16 * kk + 2 * t;
+                    G.w1[m][nt][kk][lane] = make_uint2(pair(r), pair(r + 8));
+                }
+        }
+        for (int nt = 0; nt < 8; ++nt)
+            for (int kk = 0; kk < 4; ++kk) {
+                const __nv_bfloat16* r = h.w2 + (8 * nt + g) * MLP_H + 16 * kk + 2 * t;
+                G.w2[nt][kk][lane] = make_uint2(pair(r), pair(r + 8));
+            }
+        for (int kk = 0; kk < 4; ++kk) {
+            const __nv_bfloat16* r = h.w3 + g * MLP_H + 16 * kk + 2 * t;
+            G.w3[kk][lane] = make_uint2(pair(r), pair(r + 8));
+        }
+    }
+}
+
 // operand copies built on the host from BF16 bit patterns
 void mlp_from_bf16_host(const uint16_t* w, MlpBf16& h) {
     auto f = [](uint16_t b) {

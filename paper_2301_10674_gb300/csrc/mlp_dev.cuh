@@ -72,10 +72,7 @@ __device__ __forceinline__ void relu_frag(const float (&z)[8][4], int kk, uint32
 // Forward pass from the input fragments x[kk] (k-tiles 0 and 1: inputs
 // 0..15 and 16..31, inputs 27..31 zero). W may live in global or shared
 // memory.
-// w1: the first layer's operands (MLP_H x 32, (out, in)); W.w1, or a copy
-// with its input columns permuted (the mirror images of R-17g).
-__device__ __forceinline__ void mlp_forward_w1(const MlpBf16& W, const __nv_bfloat16* w1, const uint32_t (&x)[2][4],
-                                               MlpAct& o) {
+__device__ __forceinline__ void mlp_forward(const MlpBf16& W, const uint32_t (&x)[2][4], MlpAct& o) {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
@@ -83,7 +80,7 @@ __device__ __forceinline__ void mlp_forward_w1(const MlpBf16& W, const __nv_bflo
         float d[4] = {b0, b1, b0, b1};
 #pragma unroll
         for (int kk = 0; kk < 2; ++kk) {
-            const __nv_bfloat16* row = w1 + (8 * nt + g) * 32 + 16 * kk + 2 * t;
+            const __nv_bfloat16* row = W.w1 + (8 * nt + g) * 32 + 16 * kk + 2 * t;
             mma_bf16(d, x[kk][0], x[kk][1], x[kk][2], x[kk][3], ld_pair(row), ld_pair(row + 8));
         }
 #pragma unroll
@@ -119,8 +116,62 @@ __device__ __forceinline__ void mlp_forward_w1(const MlpBf16& W, const __nv_bflo
     }
 }
 
-__device__ __forceinline__ void mlp_forward(const MlpBf16& W, const uint32_t (&x)[2][4], MlpAct& o) {
-    mlp_forward_w1(W, W.w1, x, o);
+// Weight operands of the in-step forward pass in fragment order: entry
+// [...][lane] is the register pair (b0, b1) that lane feeds one mma, so a
+// warp reads one contiguous 256-byte row per mma. w1[m] is the first layer
+// of mirror image m of R-17g (0 the network itself; 1, 2, 3 its input
+// columns mirrored in x, in y, in both).
+struct MlpFrag {
+    uint2 w1[4][8][2][32];
+    uint2 w2[8][4][32];
+    uint2 w3[4][32];
+};
+
+// The forward pass of mlp_forward with the weights of G (first layer of
+// mirror image m) and the biases of W
+__device__ __forceinline__ void mlp_forward_frag(const MlpBf16& W, const MlpFrag& G, int m,
+                                                 const uint32_t (&x)[2][4], MlpAct& o) {
+    const int lane = threadIdx.x & 31, t = lane & 3;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const float2 b = *reinterpret_cast<const float2*>(W.b1 + 8 * nt + 2 * t);
+        float d[4] = {b.x, b.y, b.x, b.y};
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+            const uint2 w = G.w1[m][nt][kk][lane];
+            mma_bf16(d, x[kk][0], x[kk][1], x[kk][2], x[kk][3], w.x, w.y);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) o.z1[nt][k] = d[k];
+    }
+    uint32_t a[4][4];
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) relu_frag(o.z1, kk, a[kk]);
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const float2 b = *reinterpret_cast<const float2*>(W.b2 + 8 * nt + 2 * t);
+        float d[4] = {b.x, b.y, b.x, b.y};
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            const uint2 w = G.w2[nt][kk][lane];
+            mma_bf16(d, a[kk][0], a[kk][1], a[kk][2], a[kk][3], w.x, w.y);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) o.z2[nt][k] = d[k];
+    }
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) relu_frag(o.z2, kk, a[kk]);
+    {
+        const float2 b = *reinterpret_cast<const float2*>(W.b3 + 2 * t);
+        float d[4] = {b.x, b.y, b.x, b.y};
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            const uint2 w = G.w3[kk][lane];
+            mma_bf16(d, a[kk][0], a[kk][1], a[kk][2], a[kk][3], w.x, w.y);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) o.y[k] = d[k];
+    }
 }
 
 // The four outputs of rows g and g + 8, gathered into every lane of group g

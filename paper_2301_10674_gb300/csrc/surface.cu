@@ -148,10 +148,11 @@ __global__ void __launch_bounds__(128, 5) k_mlp_normals(Dev s, float4* out, cons
 #pragma unroll 1
         for (int m = 0; m < passes; ++m) {
             const MlpBf16* W = s.mlp;
+            const MlpFrag* G = s.mlp_frag;
             // the operands are reloaded in every pass rather than held in
             // registers across passes
-            asm volatile("" : "+l"(W));
-            mlp_forward_w1(*W, m == 0 ? W->w1 : s.mlp_w1m + (m - 1) * MLP_H * 32, xf, act);
+            asm volatile("" : "+l"(W), "+l"(G));
+            mlp_forward_frag(*W, *G, m, xf, act);
             float ym[2][4];
             mlp_outputs(act, ym[0], ym[1]);
 #pragma unroll
