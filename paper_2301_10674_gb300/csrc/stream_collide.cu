@@ -1143,9 +1143,11 @@ __global__ void __launch_bounds__(128, bed_min_blocks<PAR>()) k_liquid_pair_bed(
 
 // Interface cells, from the interface list: gas-pressure reconstruction
 // (Section 2.1), mass exchange, particle links, collision; the cell's own
-// post-collision PDFs come from and go to the side buffer.
+// post-collision PDFs come from and go to the side buffer. Four blocks per
+// SM (128 registers, a few dozen bytes of spills) rather than the two that
+// the compiler's 250 registers leave: the kernel waits on dependent gathers.
 template <typename S, int PAR>
-__global__ void __launch_bounds__(128) k_interface(Dev s) {
+__global__ void __launch_bounds__(128, 4) k_interface(Dev s) {
     const int count = min(*s.wl_count, s.wl_cap);
     const int stride = gridDim.x * blockDim.x;
     for (int base = blockIdx.x * blockDim.x; base < count; base += stride) {
