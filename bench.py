@@ -188,8 +188,8 @@ COMPARE_FORMS = (("fp32", "fd"), ("fp16", "fd"), ("bf16", "fd"), ("fp32", "mlp")
 # even and odd steps averaged, from one ncu capture on the 1024x64x128 flume.
 # It is valid while the sweep's sources hash to `sources`, and is scaled to a
 # run by its fluid cells.
-SWEEP_TRAFFIC = {"sources": "658ae5e7cd933f06", "workload": "precision-1024x64x128",
-                 "per_fluid_cell": {"fp16": 195.1, "fp32": 380.7, "bf16": 195.1}}
+SWEEP_TRAFFIC = {"sources": "5e43e46c80f2ef71", "workload": "precision-1024x64x128",
+                 "per_fluid_cell": {"fp16": 195.0, "fp32": 380.9, "bf16": 195.2}}
 SWEEP_SOURCES = ("paper_2301_10674_gb300/csrc/stream_collide.cu", "paper_2301_10674_gb300/csrc/fslbm_dev.cuh",
                  "paper_2301_10674_gb300/csrc/collide_pair.cuh")
 
