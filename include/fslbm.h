@@ -425,8 +425,8 @@ int fslbm_normal_stats(fslbm* s, uint64_t out[2]);
 
 /* Interface stencils of the current state, labelled by the height-function
  * method: training and test data of the learned normal taken from the
- * method's own runs (the survey's logged stencils; the paper has no learned
- * normal). For every interface cell whose 3x3x3 block holds no wall or
+ * method's own runs (the paper has no learned normal). For every interface
+ * cell whose 3x3x3 block holds no wall or
  * solid cell: the network's input (fill levels of the block, liquid 1,
  * interface phi clamped to [0, 1], gas 0, stencil index
  * (dx+1) + 3(dy+1) + 9(dz+1)) and, where the height function is defined, a
