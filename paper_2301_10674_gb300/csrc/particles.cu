@@ -608,7 +608,8 @@ __global__ void k_fixed_map(Dev s) {
     coords(s, c, x, y, z);
     double best = __longlong_as_double(0x7ff0000000000000LL);
     int bestp = -1;
-    best_cover(s, x, y, z, 1, best, bestp);
+    // above every particle's top (z not periodic) no sphere covers the cell
+    if (s.per_z || z <= *s.zmax_cell) best_cover(s, x, y, z, 1, best, bestp);
     reinterpret_cast<double*>(s.fixkey)[c] = best;
     s.fixowner[c] = bestp;
 }

@@ -986,8 +986,74 @@ __global__ void k_init_surface(Dev s, const double* Hxy) {
     init_cell(s, c, t, H, fk);
 }
 
+// The flat start's values depend on z alone: the hydrostatic density of each
+// z and its 27 stored deviations, by the expressions of init_cell, once per z.
+__global__ void k_init_flat_table(Dev s, double H, double* rho_z, float* f_z) {
+    const int z = blockIdx.x * blockDim.x + threadIdx.x;
+    if (z >= s.nz) return;
+    const double rho = (double)s.rho_gas * exp(3.0 * fabs((double)s.gzd) * (H - (z + 0.5)));
+    rho_z[z] = rho;
+#pragma unroll
+    for (int q = 0; q < 27; ++q) f_z[27 * z + q] = (float)(wqd(q) * (rho - 1.0));
+}
+
+// k_init_flat from the per-z table, with 32-bit cell coordinates (n < 2^31):
+// the same cell types and values without an FP64 exponential and 64-bit
+// divisions per cell
+__global__ void k_init_flat_tab(Dev s, double H, const double* rho_z, const float* f_z) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= s.n) return;
+    int x, y, z;
+    coords32(s, (int)c, x, y, z);
+    double fk = H - z;
+    fk = fk < 0 ? 0 : (fk > 1 ? 1 : fk);
+    int t;
+    if (fk == 0.0) t = T_GAS;
+    else {
+        bool above_gas;
+        if (z + 1 < s.nz) {
+            double fa = H - (z + 1);
+            above_gas = fa <= 0.0;
+        } else {
+            above_gas = s.per_z ? (H <= 0.0) : false;
+        }
+        t = (fk < 1.0 || above_gas) ? T_IFC : T_LIQ;
+    }
+    s.flags[c] = (uint8_t)t;
+    s.owner[c] = -1;
+    s.conv[c] = 0;
+    s.mass[c] = 0.f;
+    s.phi[c] = 0.f;
+    s.ru[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    s.nrm[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (t == T_GAS) return;
+    const double rho = rho_z[z];
+    float f[27];
+#pragma unroll
+    for (int q = 0; q < 27; ++q) f[q] = f_z[27 * z + q];
+#pragma unroll
+    for (int q = 0; q < 27; ++q) st_any(s, s.f, fstar_slot(s, q, x, y, z, c, 1), f[q]);
+    if (t == T_IFC)
+        for (int q = 0; q < 27; ++q) st_any(s, s.fs, (long long)q * s.n + c, f[q]);
+    s.ru[c] = make_float4((float)rho, 0.f, 0.f, 0.f);
+    const double m = rho * fk;
+    s.mass[c] = (float)m;
+    s.phi[c] = (float)(m / rho);
+}
+
 void launch_init_flat(const Dev& s, double H, cudaStream_t st) {
-    k_init_flat<<<blocks_for(s.n, 256), 256, 0, st>>>(s, H);
+    // the table lives for the two launches in the excess-mass normal field
+    // (scratch between steps), which is zeroed again after them
+    const size_t need = (size_t)s.nz * (sizeof(double) + 27 * sizeof(float));
+    if (s.n < (1LL << 31) && need <= (size_t)s.n * sizeof(float4)) {
+        double* rho_z = reinterpret_cast<double*>(s.nrm1);
+        float* f_z = reinterpret_cast<float*>(rho_z + s.nz);
+        k_init_flat_table<<<(s.nz + 127) / 128, 128, 0, st>>>(s, H, rho_z, f_z);
+        k_init_flat_tab<<<blocks_for(s.n, 256), 256, 0, st>>>(s, H, rho_z, f_z);
+        cudaMemsetAsync(s.nrm1, 0, need, st);
+    } else {
+        k_init_flat<<<blocks_for(s.n, 256), 256, 0, st>>>(s, H);
+    }
 }
 void launch_init_surface(const Dev& s, const double* H, cudaStream_t st) {
     k_init_surface<<<blocks_for(s.n, 256), 256, 0, st>>>(s, H);
