@@ -34,6 +34,11 @@ struct fslbm {
     int have_prev;
     bool spheres_added;
     std::vector<void*> allocs;
+    // one device allocation holds the buffers fslbm_create makes (the arena);
+    // planning: the first pass of the creation only adds up their sizes
+    char* arena;
+    size_t arena_size, arena_off;
+    bool planning;
     double* stage;     // n doubles of staging for export/import
     double* red;       // 8 doubles for reductions
     int host_err;
@@ -76,6 +81,16 @@ T* dalloc(fslbm* s, size_t count, bool& ok) {
     void* ptr = nullptr;
     size_t bytes = count * sizeof(T);
     if (bytes == 0) bytes = sizeof(T);
+    const size_t padded = (bytes + 255) & ~(size_t)255;
+    if (s->planning) {
+        s->arena_size += padded;
+        return reinterpret_cast<T*>(static_cast<uintptr_t>(256));   // replaced by the second pass
+    }
+    if (s->arena && s->arena_off + padded <= s->arena_size) {
+        T* part = reinterpret_cast<T*>(s->arena + s->arena_off);
+        s->arena_off += padded;
+        return part;
+    }
     if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
         ok = false;
         cudaGetLastError();
@@ -264,108 +279,131 @@ int fslbm_create(const fslbm_params* p, void* cuda_stream, fslbm** out) {
     d.lub_mu = (1.0 / p->omega - 0.5) / 3.0;
     s->elem = p->storage == FSLBM_STORE_FP32 ? 4 : 2;
 
+    // The buffers of the run are parts of one device allocation: the section
+    // below runs twice, first adding up the sizes, then handing out 256-byte
+    // aligned parts of the arena (one allocation and one release instead of
+    // about eighty; buffers made later use cudaMalloc).
+    int* counts = nullptr;
+    double* dd = nullptr;
+    float* href = nullptr;
+    auto alloc_all = [&](bool& ok) {
+        d.f = dalloc_bytes(s, (size_t)27 * n * s->elem, ok);
+        d.fs = dalloc_bytes(s, (size_t)27 * n * s->elem, ok);
+        d.flags = dalloc<uint8_t>(s, n + 4, ok);   // word-granular atomics on the last bytes
+        d.mass = dalloc<float>(s, n, ok);
+        d.phi = dalloc<float>(s, n, ok);
+        d.ru = dalloc<float4>(s, n, ok);
+        d.nrm = dalloc<float4>(s, n, ok);
+        d.nrm1 = dalloc<float4>(s, n, ok);
+        d.owner = dalloc<int>(s, n, ok);
+        d.conv = dalloc<uint8_t>(s, n, ok);
+        d.exscale = dalloc<float>(s, n, ok);
+        long long cap = p->capacity_interface > 0 ? p->capacity_interface : n / 4 + 4096;
+        if (cap > n) cap = n;
+        d.wl_cap = (int)cap;
+        d.nl_cap = (int)cap;
+        d.wl = dalloc<int>(s, cap, ok);
+        d.nl = dalloc<int>(s, cap, ok);
+        d.cl = dalloc<int>(s, cap, ok);
+        long long tcap = n / 8 + 4096;
+        if (tcap > n) tcap = n;
+        d.tl_cap = (int)tcap;
+        d.tl = dalloc<int>(s, tcap, ok);
+        d.sl_cap = (int)n;
+        d.sl = dalloc<int>(s, n, ok);
+        d.fbits = dalloc<unsigned>(s, n / 32 + 1, ok);
+        d.ibits = dalloc<unsigned>(s, n / 32 + 1, ok);
+        d.sbits = dalloc<unsigned>(s, n / 32 + 1, ok);
+        d.tiles = dalloc<int>(s, n / fsl::SP_TILE + 1, ok);
+        {
+            const long long nseg = (long long)d.nsegx * p->ny * p->nz;
+            d.segflag = dalloc<uint8_t>(s, nseg + 4, ok);
+            d.bseg = dalloc<int>(s, nseg + 1, ok);
+        }
+        d.tl_info = dalloc<int>(s, 2 * tcap, ok);
+        counts = dalloc<int>(s, 16, ok);
+        if (ok) {
+            d.wl_count = counts;
+            d.nl_count = counts + 1;
+            d.tl_count = counts + 2;
+            d.zmax_cell = counts + 3;
+            d.err = counts + 4;
+            d.act_count = counts + 5;
+            d.dl_count = counts + 6;
+            d.sl_count = counts + 7;
+            d.tile_count = counts + 8;
+            d.bseg_count = counts + 9;
+            d.cl_count = counts + 10;
+            d.rtail_count = counts + 11;
+        }
+        dd = dalloc<double>(s, 4, ok);
+        if (ok) {
+            d.pool = dd;
+            d.pool_share = dd + 1;
+        }
+        d.viol = dalloc<unsigned long long>(s, 1, ok);
+        d.fixkey = dalloc<unsigned long long>(s, n, ok);
+        d.fixowner = dalloc<int>(s, n, ok);
+        long long pc = p->capacity_particles > 0 ? p->capacity_particles : 65536;
+        d.np_cap = (int)pc;
+        d.X = dalloc<double>(s, 3 * pc, ok); d.U = dalloc<double>(s, 3 * pc, ok); d.W = dalloc<double>(s, 3 * pc, ok);
+        for (int k = 0; k < 2; ++k) {
+            d.dem_dx[k] = dalloc<float>(s, 3 * pc, ok);
+            d.dem_du[k] = dalloc<float>(s, 3 * pc, ok);
+            d.dem_dw[k] = dalloc<float>(s, 3 * pc, ok);
+        }
+        d.nb_d0 = dalloc<float4>(s, pc * NB_SLOTS, ok);
+        d.dem_wall = dalloc<float>(s, 6 * pc, ok);
+        d.dem_c = dalloc<float4>(s, pc, ok);
+        d.Faf = dalloc<float>(s, 3 * pc, ok);
+        d.Taf = dalloc<float>(s, 3 * pc, ok);
+        d.R = dalloc<double>(s, pc, ok); d.M = dalloc<double>(s, pc, ok); d.I = dalloc<double>(s, pc, ok);
+        d.fixed = dalloc<uint8_t>(s, pc, ok);
+        d.Xr = dalloc<float4>(s, pc, ok);
+        d.Xi = dalloc<int4>(s, pc, ok);
+        d.Xfr = dalloc<float4>(s, pc, ok);
+        d.Uf = dalloc<float4>(s, pc, ok);
+        d.Wf = dalloc<float4>(s, pc, ok);
+        d.Fh = dalloc<double>(s, 3 * pc, ok); d.Th = dalloc<double>(s, 3 * pc, ok);
+        d.Fp = dalloc<double>(s, 3 * pc, ok); d.Tp = dalloc<double>(s, 3 * pc, ok);
+        d.Fa = dalloc<double>(s, 3 * pc, ok); d.Ta = dalloc<double>(s, 3 * pc, ok);
+        d.hist_partner = dalloc<int>(s, pc * HIST_SLOTS, ok);
+        d.nb = dalloc<int>(s, pc * NB_SLOTS, ok);
+        d.nb_count = dalloc<int>(s, pc, ok);
+        d.hist_xi = dalloc<float>(s, pc * HIST_SLOTS * 3, ok);
+        d.g_of = dalloc<int>(s, pc, ok);
+        d.Xm = dalloc<double>(s, 3 * pc, ok);
+        d.margin = dalloc<float>(s, pc, ok);
+        d.shared = dalloc<int>(s, pc, ok);
+        d.act = dalloc<int>(s, pc, ok);
+        d.dirty = dalloc<uint8_t>(s, n + 4, ok);
+        d.scratch_a = dalloc<uint8_t>(s, n, ok);
+        d.scratch_b = dalloc<uint8_t>(s, n, ok);
+        const long long dcap = n;   // the first re-map may touch every cell of the bed
+        d.dl_cap = (int)dcap;
+        d.dl = dalloc<int>(s, dcap, ok);
+        d.g_list = dalloc<int>(s, pc, ok);
+        s->stage = dalloc<double>(s, n > 8 ? n : 8, ok);
+        s->red = dalloc<double>(s, 8, ok);
+        d.rpart = dalloc<double>(s, 8 * (size_t)reduce_blocks(d), ok);
+        d.rtail = dalloc<double>(s, 8 * REDUCE_TAIL_BLOCKS, ok);
+        href = p->storage != FSLBM_STORE_FP32 ? dalloc<float>(s, p->nz, ok) : nullptr;
+    };
+    s->arena = nullptr;
+    s->arena_size = s->arena_off = 0;
+    s->planning = true;
     bool ok = true;
-    d.f = dalloc_bytes(s, (size_t)27 * n * s->elem, ok);
-    d.fs = dalloc_bytes(s, (size_t)27 * n * s->elem, ok);
-    d.flags = dalloc<uint8_t>(s, n + 4, ok);   // word-granular atomics on the last bytes
-    d.mass = dalloc<float>(s, n, ok);
-    d.phi = dalloc<float>(s, n, ok);
-    d.ru = dalloc<float4>(s, n, ok);
-    d.nrm = dalloc<float4>(s, n, ok);
-    d.nrm1 = dalloc<float4>(s, n, ok);
-    d.owner = dalloc<int>(s, n, ok);
-    d.conv = dalloc<uint8_t>(s, n, ok);
-    d.exscale = dalloc<float>(s, n, ok);
-    long long cap = p->capacity_interface > 0 ? p->capacity_interface : n / 4 + 4096;
-    if (cap > n) cap = n;
-    d.wl_cap = (int)cap;
-    d.nl_cap = (int)cap;
-    d.wl = dalloc<int>(s, cap, ok);
-    d.nl = dalloc<int>(s, cap, ok);
-    d.cl = dalloc<int>(s, cap, ok);
-    long long tcap = n / 8 + 4096;
-    if (tcap > n) tcap = n;
-    d.tl_cap = (int)tcap;
-    d.tl = dalloc<int>(s, tcap, ok);
-    d.sl_cap = (int)n;
-    d.sl = dalloc<int>(s, n, ok);
-    d.fbits = dalloc<unsigned>(s, n / 32 + 1, ok);
-    d.ibits = dalloc<unsigned>(s, n / 32 + 1, ok);
-    d.sbits = dalloc<unsigned>(s, n / 32 + 1, ok);
-    d.tiles = dalloc<int>(s, n / fsl::SP_TILE + 1, ok);
-    {
-        const long long nseg = (long long)d.nsegx * p->ny * p->nz;
-        d.segflag = dalloc<uint8_t>(s, nseg + 4, ok);
-        d.bseg = dalloc<int>(s, nseg + 1, ok);
+    alloc_all(ok);
+    s->planning = false;
+    void* arena = nullptr;
+    if (cudaMalloc(&arena, s->arena_size) == cudaSuccess) {
+        s->arena = static_cast<char*>(arena);
+        s->allocs.push_back(arena);
+    } else {
+        cudaGetLastError();   // the second pass allocates buffer by buffer
     }
-    d.tl_info = dalloc<int>(s, 2 * tcap, ok);
-    int* counts = dalloc<int>(s, 16, ok);
-    if (ok) {
-        d.wl_count = counts;
-        d.nl_count = counts + 1;
-        d.tl_count = counts + 2;
-        d.zmax_cell = counts + 3;
-        d.err = counts + 4;
-        d.act_count = counts + 5;
-        d.dl_count = counts + 6;
-        d.sl_count = counts + 7;
-        d.tile_count = counts + 8;
-        d.bseg_count = counts + 9;
-        d.cl_count = counts + 10;
-        d.rtail_count = counts + 11;
-    }
-    double* dd = dalloc<double>(s, 4, ok);
-    if (ok) {
-        d.pool = dd;
-        d.pool_share = dd + 1;
-    }
-    d.viol = dalloc<unsigned long long>(s, 1, ok);
-    d.fixkey = dalloc<unsigned long long>(s, n, ok);
-    d.fixowner = dalloc<int>(s, n, ok);
-    long long pc = p->capacity_particles > 0 ? p->capacity_particles : 65536;
-    d.np_cap = (int)pc;
-    d.X = dalloc<double>(s, 3 * pc, ok); d.U = dalloc<double>(s, 3 * pc, ok); d.W = dalloc<double>(s, 3 * pc, ok);
-    for (int k = 0; k < 2; ++k) {
-        d.dem_dx[k] = dalloc<float>(s, 3 * pc, ok);
-        d.dem_du[k] = dalloc<float>(s, 3 * pc, ok);
-        d.dem_dw[k] = dalloc<float>(s, 3 * pc, ok);
-    }
-    d.nb_d0 = dalloc<float4>(s, pc * NB_SLOTS, ok);
-    d.dem_wall = dalloc<float>(s, 6 * pc, ok);
-    d.dem_c = dalloc<float4>(s, pc, ok);
-    d.Faf = dalloc<float>(s, 3 * pc, ok);
-    d.Taf = dalloc<float>(s, 3 * pc, ok);
-    d.R = dalloc<double>(s, pc, ok); d.M = dalloc<double>(s, pc, ok); d.I = dalloc<double>(s, pc, ok);
-    d.fixed = dalloc<uint8_t>(s, pc, ok);
-    d.Xr = dalloc<float4>(s, pc, ok);
-    d.Xi = dalloc<int4>(s, pc, ok);
-    d.Xfr = dalloc<float4>(s, pc, ok);
-    d.Uf = dalloc<float4>(s, pc, ok);
-    d.Wf = dalloc<float4>(s, pc, ok);
-    d.Fh = dalloc<double>(s, 3 * pc, ok); d.Th = dalloc<double>(s, 3 * pc, ok);
-    d.Fp = dalloc<double>(s, 3 * pc, ok); d.Tp = dalloc<double>(s, 3 * pc, ok);
-    d.Fa = dalloc<double>(s, 3 * pc, ok); d.Ta = dalloc<double>(s, 3 * pc, ok);
-    d.hist_partner = dalloc<int>(s, pc * HIST_SLOTS, ok);
-    d.nb = dalloc<int>(s, pc * NB_SLOTS, ok);
-    d.nb_count = dalloc<int>(s, pc, ok);
-    d.hist_xi = dalloc<float>(s, pc * HIST_SLOTS * 3, ok);
-    d.g_of = dalloc<int>(s, pc, ok);
-    d.Xm = dalloc<double>(s, 3 * pc, ok);
-    d.margin = dalloc<float>(s, pc, ok);
-    d.shared = dalloc<int>(s, pc, ok);
-    d.act = dalloc<int>(s, pc, ok);
-    d.dirty = dalloc<uint8_t>(s, n + 4, ok);
-    d.scratch_a = dalloc<uint8_t>(s, n, ok);
-    d.scratch_b = dalloc<uint8_t>(s, n, ok);
-    const long long dcap = n;   // the first re-map may touch every cell of the bed
-    d.dl_cap = (int)dcap;
-    d.dl = dalloc<int>(s, dcap, ok);
-    d.g_list = dalloc<int>(s, pc, ok);
-    s->stage = dalloc<double>(s, n > 8 ? n : 8, ok);
-    s->red = dalloc<double>(s, 8, ok);
-    d.rpart = dalloc<double>(s, 8 * (size_t)reduce_blocks(d), ok);
-    d.rtail = dalloc<double>(s, 8 * REDUCE_TAIL_BLOCKS, ok);
-    float* href = p->storage != FSLBM_STORE_FP32 ? dalloc<float>(s, p->nz, ok) : nullptr;
+    ok = true;
+    alloc_all(ok);
     if (ok && (cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess ||
                cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
                cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess)) {
