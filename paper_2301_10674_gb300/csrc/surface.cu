@@ -273,9 +273,11 @@ __global__ void k_conflict(Dev s) {
 
 // gas neighbours of filled cells and liquid neighbours of emptied cells
 // become interface cells; each is listed once (first setter of its mark)
+// (over the cells that convert, listed by k_conflict)
 __global__ void k_mark(Dev s) {
-    FOR_LIST(i, s.wl_count) {
-        int c = s.wl[i];
+    const int ncl = min(*s.cl_count, s.wl_cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncl; i += gridDim.x * blockDim.x) {
+        int c = s.cl[i];
         uint8_t cv = s.conv[c];
         if (!cv) continue;
         int x, y, z;
@@ -360,8 +362,9 @@ __device__ __forceinline__ bool is_receiver(const Dev& s, long long c) {
 // even variant is selected, into the FP64 pool if there is no interface
 // neighbour
 __global__ void k_excess_prep(Dev s) {
-    FOR_LIST(i, s.wl_count) {
-        int c = s.wl[i];
+    const int ncl = min(*s.cl_count, s.wl_cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncl; i += gridDim.x * blockDim.x) {
+        int c = s.cl[i];
         uint8_t cv = s.conv[c];
         if (!cv) continue;
         float rho = s.ru[c].x;
@@ -421,6 +424,8 @@ __device__ void gather_excess(const Dev& s, int c) {
 }
 
 __global__ void k_excess_gather(Dev s) {
+    // without a converting cell no receiver gets anything
+    if (*s.cl_count == 0) return;
     FOR_LIST(i, s.wl_count) gather_excess(s, s.wl[i]);
     const int cap = s.nl_cap;
     FOR_LIST(i, s.nl_count) {
@@ -453,8 +458,10 @@ __global__ void k_finalize_new(Dev s) {
         s.phi[c] = s.mass[c] / s.ru[c].x;
     }
 }
+// conversion codes are left only on the cells k_conflict listed
 __global__ void k_clear_conv(Dev s) {
-    FOR_LIST(i, s.wl_count) s.conv[s.wl[i]] = 0;
+    const int ncl = min(*s.cl_count, s.wl_cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncl; i += gridDim.x * blockDim.x) s.conv[s.cl[i]] = 0;
 }
 
 // Interface stencils of the current state with height-function labels (R-17e):
