@@ -621,16 +621,19 @@ int launch_conversion(const Dev& s, int last_parity, cudaStream_t st) {
 
 // ------------------------------------------------------------ work lists
 // Block-aggregated append of the cells c0 + k for the set bits k of a
-// thread's 32-bit mask (one atomic per block). Every thread of the block must
-// call it.
-__device__ __forceinline__ void block_append_mask(const Dev& s, unsigned mask, int c0, int* list, int* count,
-                                                  int cap) {
+// thread's two 32-bit masks, ma to list la and mb to list lb: one scan of
+// both counts (list a in the low 16 bits, list b in the high ones; a block
+// holds at most 32 x 32 bits per warp), one atomic per list and block. The
+// cells of a block keep their order in each list. Every thread of the block
+// must call it.
+__device__ __forceinline__ void block_append_masks(const Dev& s, int c0, unsigned ma, int* la, int* ca, int capa,
+                                                   unsigned mb, int* lb, int* cb, int capb) {
     __shared__ int warp_tot[32];
-    __shared__ int block_base;
+    __shared__ int base_a, base_b;
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int nitems = __popc(mask);
-    int incl = nitems;
+    const int na = __popc(ma), nb = __popc(mb);
+    int incl = na | (nb << 16);
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
         const int t = __shfl_up_sync(full, incl, off);
@@ -639,18 +642,26 @@ __device__ __forceinline__ void block_append_mask(const Dev& s, unsigned mask, i
     if (lane == 31) warp_tot[wid] = incl;
     __syncthreads();
     if (threadIdx.x == 0) {
-        int tot = 0;
+        int ta = 0, tb = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
             const int c = warp_tot[w];
-            warp_tot[w] = tot;
-            tot += c;
+            warp_tot[w] = ta | (tb << 16);
+            ta += c & 0xffff;
+            tb += c >> 16;
         }
-        block_base = tot ? atomicAdd(count, tot) : 0;
+        base_a = ta ? atomicAdd(ca, ta) : 0;
+        base_b = tb ? atomicAdd(cb, tb) : 0;
     }
     __syncthreads();
-    int k = block_base + warp_tot[wid] + incl - nitems;
-    for (unsigned m = mask; m; m &= m - 1, ++k) {
-        if (k < cap) list[k] = c0 + __ffs(m) - 1;
+    const int pre = warp_tot[wid];
+    int ka = base_a + (pre & 0xffff) + (incl & 0xffff) - na;
+    int kb = base_b + (pre >> 16) + (incl >> 16) - nb;
+    for (unsigned m = ma; m; m &= m - 1, ++ka) {
+        if (ka < capa) la[ka] = c0 + __ffs(m) - 1;
+        else set_error(s, ERR_CAPACITY);
+    }
+    for (unsigned m = mb; m; m &= m - 1, ++kb) {
+        if (kb < capb) lb[kb] = c0 + __ffs(m) - 1;
         else set_error(s, ERR_CAPACITY);
     }
     __syncthreads();
@@ -729,8 +740,7 @@ __global__ void k_classify_bits(Dev s) {
         ifc_mask = s.ibits[w];
     }
     const int c0 = (int)(w << 5);
-    block_append_mask(s, ifc_mask, c0, s.wl, s.wl_count, s.wl_cap);
-    block_append_mask(s, sol_mask, c0, s.sl, s.sl_count, s.sl_cap);
+    block_append_masks(s, c0, ifc_mask, s.wl, s.wl_count, s.wl_cap, sol_mask, s.sl, s.sl_count, s.sl_cap);
 }
 
 // Bed segments, for particle links taken from the fluid side: a thread per
